@@ -1,0 +1,698 @@
+/*
+ * sph_oracle.c -- plain FP64 CPU oracle for the implicit two-temperature SPH
+ * thermal-radiative-transfer step of Bassett, Owen & Brunner, "Efficient
+ * smoothed particle radiation hydrodynamics I: Thermal radiative transfer"
+ * (arXiv:2001.11606).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only the test-suite, the smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no code with the CUDA library.
+ *
+ * It is written to be checked against the paper by eye: brute-force neighbours
+ * (with an exact sort-and-sweep prune on x), point-by-point properties, the
+ * Brookshaw operator assembled row by row, backward Euler with the nonlinear
+ * elimination loop of Alg. 1, a scalar Newton solve per particle (Eq. for the
+ * material-energy update), and an unpreconditioned conjugate-gradient solve of
+ * the volume-weighted radiation system.  Everything is FP64; build it with
+ * -ffp-contract=off so that no multiply-add is fused.
+ *
+ * Readings of the paper taken here (each is listed with its reason in the
+ * design notes of the repository):
+ *  - Kernel: M4 cubic B-spline, support 2h (the paper's Wendland C4 is a
+ *    drop-in alternative, not used by the workloads).
+ *  - Neighbour predicate: j != i and r2 < (2 max(h_i,h_j))^2, r2 summed in
+ *    coordinate order x, y, z with no fused multiply-add.
+ *  - Kernel symmetrisation for unequal h: average of the two gradients (Sec. 2.4).
+ *  - Material data (sigma, f, lambda, D) are computed once per step from the
+ *    state at the start of the step (Sec. 3.2, last paragraph of the operator list).
+ *  - Dirichlet ghosts take R = 0 (no gradient is formed for them); copy ghosts
+ *    take every property of the interior particle they copy.
+ *  - Outer convergence: max over interior particles of the pointwise relative
+ *    change (Eq. mat-rad-convergence), denominators floored at 1e-300.
+ *  - Krylov stop: ||b - A E||_2 <= tol ||b||_2 on the unscaled rows.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* Problem constants and solver controls. */
+typedef struct {
+  int32_t dim;
+  double a, c, cv;          /* radiation constant, speed of light, specific heat */
+  int32_t limiter;          /* 0: lambda = 1/3; 1: Levermore; 2: Larsen */
+  double larsen_k;
+  double opacity_exp;       /* sigma = sigma0 * T^p */
+  double T_floor;           /* T used inside sigma and R is max(T, T_floor) */
+  double tol_outer_e, tol_outer_E, tol_inner_e, tol_krylov;
+  int32_t max_outer, max_inner_e, max_krylov;
+} orc_params;
+
+enum { ORC_INTERIOR = 0, ORC_DIRICHLET = 1, ORC_COPY = 2 };
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kernel: M4 cubic B-spline with support 2h, normalised so that its volume   */
+/* integral is one (the normalisation requirement of Sec. 2.3).               */
+/* ------------------------------------------------------------------------ */
+static double kernel_norm(int dim, double h) {
+  if (dim == 1) return (2.0 / 3.0) / h;
+  if (dim == 2) return (10.0 / (7.0 * M_PI)) / (h * h);
+  return (1.0 / M_PI) / (h * h * h);
+}
+
+/* W(r, h) and dW/dr(r, h). */
+void orc_kernel(int dim, double r, double h, double *W, double *dWdr) {
+  double q = r / h;
+  double norm = kernel_norm(dim, h);
+  double w = 0.0, dw = 0.0;
+  if (q < 1.0) {
+    w = 1.0 - 1.5 * q * q + 0.75 * q * q * q;
+    dw = -3.0 * q + 2.25 * q * q;
+  } else if (q < 2.0) {
+    double t = 2.0 - q;
+    w = 0.25 * t * t * t;
+    dw = -0.75 * t * t;
+  }
+  *W = norm * w;
+  *dWdr = norm * dw / h;
+}
+
+/* F_ij = (x_ij . grad_i W_ij) / |x_ij|^2 = W'_ij / r with the two-h average. */
+static double pair_F(int dim, double r, double hi, double hj) {
+  double Wi, dWi, Wj, dWj;
+  orc_kernel(dim, r, hi, &Wi, &dWi);
+  orc_kernel(dim, r, hj, &Wj, &dWj);
+  return 0.5 * (dWi + dWj) / r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neighbours (connectivity).                                                 */
+/* ------------------------------------------------------------------------ */
+static double pair_r2(int dim, const double *xi, const double *xj) {
+  double dx = xi[0] - xj[0];
+  double r2 = dx * dx;
+  if (dim > 1) {
+    double dy = xi[1] - xj[1];
+    r2 = r2 + dy * dy;
+  }
+  if (dim > 2) {
+    double dz = xi[2] - xj[2];
+    r2 = r2 + dz * dz;
+  }
+  return r2;
+}
+
+static int is_neighbour(int dim, const double *pos, const double *h, int64_t i, int64_t j) {
+  if (i == j) return 0;
+  double hmax = h[i] > h[j] ? h[i] : h[j];
+  double cut = 2.0 * hmax;
+  double cut2 = cut * cut;
+  return pair_r2(dim, pos + i * dim, pos + j * dim) < cut2;
+}
+
+static const double *g_sort_pos;
+static int g_sort_dim;
+static int cmp_by_x(const void *a, const void *b) {
+  int64_t ia = *(const int64_t *)a, ib = *(const int64_t *)b;
+  double xa = g_sort_pos[ia * g_sort_dim], xb = g_sort_pos[ib * g_sort_dim];
+  if (xa < xb) return -1;
+  if (xa > xb) return 1;
+  return ia < ib ? -1 : (ia > ib);
+}
+static int cmp_i32(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return x < y ? -1 : (x > y);
+}
+
+/*
+ * Neighbour lists of every interior particle: all j != i (interior or ghost)
+ * with r2 < (2 max(h_i,h_j))^2.  Rows are in caller order over all n particles
+ * (ghost rows are empty); each row's columns are sorted ascending.
+ *
+ * brute = 1 tests every pair.  brute = 0 sorts by x and, for each i, scans
+ * outwards in x while (x_i - x_j)^2 < (2 h_max)^2; this prune is exact because
+ * the rounded r2 is never smaller than the rounded dx*dx.
+ *
+ * Pass cols = NULL to fill rowptr only.  Returns nnz.
+ */
+int64_t orc_neighbors(int64_t n, int dim, const double *pos, const double *h,
+                      const int32_t *kind, int brute, int64_t *rowptr, int32_t *cols) {
+  int64_t *order = NULL, *where = NULL;
+  double hmax = 0.0;
+  for (int64_t i = 0; i < n; ++i) hmax = h[i] > hmax ? h[i] : hmax;
+  double cutmax = 2.0 * hmax, cutmax2 = cutmax * cutmax;
+  if (!brute) {
+    order = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    where = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) order[i] = i;
+    g_sort_pos = pos;
+    g_sort_dim = dim;
+    qsort(order, (size_t)n, sizeof(int64_t), cmp_by_x);
+    for (int64_t k = 0; k < n; ++k) where[order[k]] = k;
+  }
+  int64_t *count = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+  for (int pass = 0; pass < (cols ? 2 : 1); ++pass) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+      if (kind[i] != ORC_INTERIOR) continue;
+      int32_t *out = pass ? cols + rowptr[i] : NULL;
+      int64_t c = 0;
+      if (brute) {
+        for (int64_t j = 0; j < n; ++j)
+          if (is_neighbour(dim, pos, h, i, j)) {
+            if (out) out[c] = (int32_t)j;
+            ++c;
+          }
+      } else {
+        double xi = pos[i * dim];
+        for (int64_t k = where[i] + 1; k < n; ++k) {
+          int64_t j = order[k];
+          double dx = xi - pos[j * dim];
+          if (!(dx * dx < cutmax2)) break;
+          if (is_neighbour(dim, pos, h, i, j)) {
+            if (out) out[c] = (int32_t)j;
+            ++c;
+          }
+        }
+        for (int64_t k = where[i] - 1; k >= 0; --k) {
+          int64_t j = order[k];
+          double dx = xi - pos[j * dim];
+          if (!(dx * dx < cutmax2)) break;
+          if (is_neighbour(dim, pos, h, i, j)) {
+            if (out) out[c] = (int32_t)j;
+            ++c;
+          }
+        }
+        if (out) qsort(out, (size_t)c, sizeof(int32_t), cmp_i32);
+      }
+      count[i] = c;
+    }
+    if (pass == 0) {
+      rowptr[0] = 0;
+      for (int64_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + count[i];
+    }
+  }
+  int64_t nnz = rowptr[n];
+  free(count);
+  free(order);
+  free(where);
+  return nnz;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Material data, frozen for the step (Sec. 3.2).                            */
+/* ------------------------------------------------------------------------ */
+static double limiter_lambda(const orc_params *p, double R) {
+  if (p->limiter == 1) return (2.0 + R) / (6.0 + 3.0 * R + R * R); /* Levermore */
+  if (p->limiter == 2) /* Larsen */
+    return 1.0 / pow(pow(3.0, p->larsen_k) + pow(R, p->larsen_k), 1.0 / p->larsen_k);
+  return 1.0 / 3.0; /* no limiter: Fick's law */
+}
+
+/*
+ * For every particle (caller order), from the state (e, E) at the start of
+ * the step:
+ *   T = e / c_v;  sigma = sigma0 T^p  (sigma_a = sigma_t);
+ *   f = 1 / (1 + c sigma dt 4 a T^3 / (rho c_v))             (Fleck factor)
+ *   grad E_i = sum_j V_j (E_j - E_i) grad_i W_ij              (SPH derivative)
+ *   R = |grad E| / (sigma E);  lambda = limiter(R);  D = c lambda / sigma.
+ * R is only formed when a limiter is active.
+ */
+void orc_properties(const orc_params *p, int64_t n, const double *pos, const double *mass,
+                    const double *rho, const double *h, const double *sigma0,
+                    const int32_t *kind, const int64_t *copy_of, const double *e,
+                    const double *E, double dt, const int64_t *rowptr, const int32_t *cols,
+                    double *T, double *sigma, double *f, double *R, double *lambda, double *D) {
+  int dim = p->dim;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] == ORC_COPY) continue;
+    double Ti = e[i] / p->cv;
+    double Ts = Ti > p->T_floor ? Ti : p->T_floor;
+    double sig = sigma0[i] * pow(Ts, p->opacity_exp);
+    double fi = 1.0 / (1.0 + p->c * sig * dt * 4.0 * p->a * Ti * Ti * Ti / (rho[i] * p->cv));
+    double Ri = 0.0;
+    if (p->limiter != 0 && kind[i] == ORC_INTERIOR) {
+      double g[3] = {0.0, 0.0, 0.0};
+      for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        int64_t j = cols[k];
+        int64_t js = kind[j] == ORC_COPY ? copy_of[j] : j;
+        double xij[3] = {0.0, 0.0, 0.0};
+        for (int d = 0; d < dim; ++d) xij[d] = pos[i * dim + d] - pos[j * dim + d];
+        double r = sqrt(pair_r2(dim, pos + i * dim, pos + j * dim));
+        double Fij = pair_F(dim, r, h[i], h[j]);
+        double Vj = mass[j] / rho[j];
+        /* grad_i W_ij = W'_ij x_ij / r = F_ij x_ij */
+        for (int d = 0; d < dim; ++d) g[d] += Vj * (E[js] - E[i]) * Fij * xij[d];
+      }
+      double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+      double Es = E[i] > 1e-300 ? E[i] : 1e-300;
+      double sigR = sigma0[i] * pow(Ts, p->opacity_exp);
+      Ri = gn / (sigR * Es);
+    }
+    double lam = limiter_lambda(p, Ri);
+    T[i] = Ti;
+    sigma[i] = sig;
+    f[i] = fi;
+    R[i] = Ri;
+    lambda[i] = lam;
+    D[i] = p->c * lam / sig;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != ORC_COPY) continue;
+    int64_t s = copy_of[i];
+    T[i] = T[s];
+    sigma[i] = sigma[s];
+    f[i] = f[s];
+    R[i] = R[s];
+    lambda[i] = lambda[s];
+    D[i] = D[s];
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diffusion operator (Eq. diffusion-solve), one row per interior particle:  */
+/*   (1/dt + c sigma_i f_i) E_i + sum_j w_ij (E_i - E_j) = P_i,               */
+/*   w_ij = -V_j (D_i + D_j) F_ij >= 0   (Brookshaw second derivative).       */
+/* Interior columns stay in the matrix; a copy ghost's column is moved to the */
+/* particle it copies; a Dirichlet ghost's term w_ij E_j goes to gb_i.        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t col;
+  double val;
+} orc_entry;
+static int cmp_entry(const void *a, const void *b) {
+  int32_t x = ((const orc_entry *)a)->col, y = ((const orc_entry *)b)->col;
+  return x < y ? -1 : (x > y);
+}
+
+/*
+ * Output CSR over all n rows (ghost rows empty), columns sorted and merged,
+ * the diagonal kept apart (adiag) and excluded from the off-diagonal list.
+ * arow[n+1], acol/aval sized by the neighbour nnz.  E_ghost holds the
+ * Dirichlet values at the new time level.  Returns the matrix nnz.
+ */
+int64_t orc_assemble(const orc_params *p, int64_t n, const double *pos, const double *mass,
+                     const double *rho, const double *h, const int32_t *kind,
+                     const int64_t *copy_of, double dt, const double *sigma, const double *f,
+                     const double *D, const double *E_ghost, const int64_t *rowptr,
+                     const int32_t *cols, int64_t *arow, int32_t *acol, double *aval,
+                     double *adiag, double *gb) {
+  int dim = p->dim;
+  int64_t *cnt = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+  int64_t nnz_nbr = rowptr[n];
+  orc_entry *tmp = (orc_entry *)malloc(sizeof(orc_entry) * (size_t)(nnz_nbr > 0 ? nnz_nbr : 1));
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    adiag[i] = 0.0;
+    gb[i] = 0.0;
+    if (kind[i] != ORC_INTERIOR) continue;
+    double diag = 1.0 / dt + p->c * sigma[i] * f[i];
+    double gbi = 0.0;
+    orc_entry *row = tmp + rowptr[i];
+    int64_t c = 0;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      int64_t j = cols[k];
+      double r = sqrt(pair_r2(dim, pos + i * dim, pos + j * dim));
+      double Fij = pair_F(dim, r, h[i], h[j]);
+      double Vj = mass[j] / rho[j];
+      double w = -Vj * (D[i] + D[j]) * Fij;
+      diag += w;
+      if (kind[j] == ORC_DIRICHLET) {
+        gbi += w * E_ghost[j];
+      } else {
+        int64_t col = kind[j] == ORC_COPY ? copy_of[j] : j;
+        row[c].col = (int32_t)col;
+        row[c].val = -w;
+        ++c;
+      }
+    }
+    qsort(row, (size_t)c, sizeof(orc_entry), cmp_entry);
+    /* merge duplicates; a column equal to the row folds into the diagonal */
+    int64_t m = 0;
+    for (int64_t k = 0; k < c; ++k) {
+      if (row[k].col == i) {
+        diag += row[k].val;
+      } else if (m > 0 && row[m - 1].col == row[k].col) {
+        row[m - 1].val += row[k].val;
+      } else {
+        row[m++] = row[k];
+      }
+    }
+    cnt[i] = m;
+    adiag[i] = diag;
+    gb[i] = gbi;
+  }
+  arow[0] = 0;
+  for (int64_t i = 0; i < n; ++i) arow[i + 1] = arow[i] + cnt[i];
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = 0; k < cnt[i]; ++k) {
+      acol[arow[i] + k] = tmp[rowptr[i] + k].col;
+      aval[arow[i] + k] = tmp[rowptr[i] + k].val;
+    }
+  int64_t nnz = arow[n];
+  free(tmp);
+  free(cnt);
+  return nnz;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Material energy solve M^{-1}(P) (Eq. material-energy-solve): per particle */
+/*   u(e) = rho/dt (e - e_old) + c sigma a (e/c_v)^4 - P                      */
+/*   J(e) = rho/dt + 4 c sigma a (e/c_v)^3 / c_v                              */
+/*   e <- e - u/J  until |delta e| <= tol |e|.                                */
+/* Returns the largest iteration count; *fails counts particles that hit max. */
+/* ------------------------------------------------------------------------ */
+int orc_material_solve(const orc_params *p, int64_t n, const int32_t *kind, const double *rho,
+                       const double *sigma, double dt, const double *e_old, const double *P,
+                       double *e, int64_t *fails) {
+  int worst = 0;
+  int64_t nf = 0;
+#pragma omp parallel for schedule(static) reduction(max : worst) reduction(+ : nf)
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != ORC_INTERIOR) continue;
+    double ei = e[i];
+    int it = 0, ok = 0;
+    while (it < p->max_inner_e) {
+      double T = ei / p->cv;
+      double u = rho[i] / dt * (ei - e_old[i]) + p->c * sigma[i] * p->a * T * T * T * T - P[i];
+      double J = rho[i] / dt + 4.0 * p->c * sigma[i] * p->a * T * T * T / p->cv;
+      double de = u / J;
+      ei = ei - de;
+      ++it;
+      if (fabs(de) <= p->tol_inner_e * fabs(ei)) {
+        ok = 1;
+        break;
+      }
+    }
+    e[i] = ei;
+    if (it > worst) worst = it;
+    if (!ok) ++nf;
+  }
+  if (fails) *fails = nf;
+  return worst;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Deterministic sums: fixed 4096-element blocks summed in order, then the    */
+/* block sums in order, so results do not depend on the thread count.         */
+/* ------------------------------------------------------------------------ */
+#define ORC_BLK 4096
+static double block_sum(int64_t n, const double *v, double *scratch) {
+  int64_t nb = (n + ORC_BLK - 1) / ORC_BLK;
+#pragma omp parallel for schedule(static)
+  for (int64_t b = 0; b < nb; ++b) {
+    double s = 0.0;
+    int64_t hi = (b + 1) * ORC_BLK < n ? (b + 1) * ORC_BLK : n;
+    for (int64_t i = b * ORC_BLK; i < hi; ++i) s += v[i];
+    scratch[b] = s;
+  }
+  double s = 0.0;
+  for (int64_t b = 0; b < nb; ++b) s += scratch[b];
+  return s;
+}
+
+/* y = A x over interior rows (diagonal + off-diagonal CSR). */
+static void apply_A(int64_t n, const int32_t *kind, const int64_t *arow, const int32_t *acol,
+                    const double *aval, const double *adiag, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != ORC_INTERIOR) {
+      y[i] = 0.0;
+      continue;
+    }
+    double s = adiag[i] * x[i];
+    for (int64_t k = arow[i]; k < arow[i + 1]; ++k) s += aval[k] * x[acol[k]];
+    y[i] = s;
+  }
+}
+
+/*
+ * Solve A x = b (interior rows) by unpreconditioned conjugate gradients on the
+ * symmetric positive definite system (V A) x = V b, V = diag(m/rho).  V A is
+ * symmetric because V_i A_ij = -V_i V_j (D_i + D_j) F_ij.  Starts from x.
+ * Stops when ||b - A x||_2 <= tol ||b||_2.  Returns the iteration count, or
+ * -1 if maxit was reached.
+ */
+/* (u, w)_wt = sum over interior i of wt_i u_i w_i (wt = NULL: unit weights). */
+static double wdot(int64_t n, const int32_t *kind, const double *wt, const double *u,
+                   const double *w, double *t, double *scr) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    t[i] = kind[i] == ORC_INTERIOR ? (wt ? wt[i] : 1.0) * u[i] * w[i] : 0.0;
+  return block_sum(n, t, scr);
+}
+
+int orc_cg(int64_t n, const int32_t *kind, const double *V, const int64_t *arow,
+           const int32_t *acol, const double *aval, const double *adiag, const double *b,
+           double *x, double tol, int maxit, double *relres) {
+  double *r = (double *)calloc((size_t)n, sizeof(double));
+  double *pv = (double *)calloc((size_t)n, sizeof(double));
+  double *q = (double *)calloc((size_t)n, sizeof(double));
+  double *t = (double *)calloc((size_t)n, sizeof(double));
+  double *scr = (double *)calloc((size_t)(n / ORC_BLK + 2), sizeof(double));
+  int it = 0, status = -1;
+
+  double bnorm = sqrt(wdot(n, kind, NULL, b, b, t, scr));
+  apply_A(n, kind, arow, acol, aval, adiag, x, q);
+  for (int64_t i = 0; i < n; ++i) r[i] = kind[i] == ORC_INTERIOR ? b[i] - q[i] : 0.0;
+  double rnorm = sqrt(wdot(n, kind, NULL, r, r, t, scr));
+  double thresh = tol * bnorm;
+  if (rnorm <= thresh) {
+    status = 0;
+  } else {
+    /* CG on V A: the residual of that system is V r */
+    for (int64_t i = 0; i < n; ++i) pv[i] = r[i];
+    double rho_k = wdot(n, kind, V, r, r, t, scr); /* (V r, r) */
+    while (it < maxit) {
+      apply_A(n, kind, arow, acol, aval, adiag, pv, q);
+      double pq = wdot(n, kind, V, pv, q, t, scr); /* (p, V A p) */
+      double alpha = rho_k / pq;
+#pragma omp parallel for schedule(static)
+      for (int64_t i = 0; i < n; ++i) {
+        if (kind[i] != ORC_INTERIOR) continue;
+        x[i] += alpha * pv[i];
+        r[i] -= alpha * q[i];
+      }
+      ++it;
+      rnorm = sqrt(wdot(n, kind, NULL, r, r, t, scr));
+      if (rnorm <= thresh) {
+        status = 0;
+        break;
+      }
+      double rho_new = wdot(n, kind, V, r, r, t, scr);
+      double beta = rho_new / rho_k;
+      rho_k = rho_new;
+#pragma omp parallel for schedule(static)
+      for (int64_t i = 0; i < n; ++i)
+        if (kind[i] == ORC_INTERIOR) pv[i] = r[i] + beta * pv[i];
+    }
+  }
+  if (relres) *relres = bnorm > 0.0 ? rnorm / bnorm : rnorm;
+  free(r);
+  free(pv);
+  free(q);
+  free(t);
+  free(scr);
+  return status == 0 ? it : -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One backward-Euler step with nonlinear elimination (Alg. 1).              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t outer_iters;
+  int32_t krylov_total;
+  int32_t krylov_per_outer[64];
+  int32_t newton_max;
+  int32_t status; /* 0 ok, -3 not converged */
+  double energy_before, energy_after, source_energy, boundary_energy;
+  double last_change_e, last_change_E;
+} orc_stats;
+
+static double total_energy(int64_t n, const int32_t *kind, const double *mass, const double *rho,
+                           const double *e, const double *E, double *scr_vec, double *scr) {
+  for (int64_t i = 0; i < n; ++i)
+    scr_vec[i] = kind[i] == ORC_INTERIOR ? mass[i] * e[i] + mass[i] / rho[i] * E[i] : 0.0;
+  return block_sum(n, scr_vec, scr);
+}
+
+/*
+ * Advance (e, E) over all particles by one step of size dt.  Qe, QE are the
+ * sources at t^n; ghost_e, ghost_E (may be NULL) are the ghost values at t^n
+ * (used for Dirichlet ghosts; copy ghosts follow their source).  On return
+ * e, E hold the new state; ghosts hold their t^n values.  Returns 0, or -3 if
+ * the outer iteration did not converge (then e and E are left unchanged).
+ */
+int orc_step(const orc_params *p, int64_t n, const double *pos, const double *mass,
+             const double *rho, const double *h, const double *sigma0, const int32_t *kind,
+             const int64_t *copy_of, const int64_t *rowptr, const int32_t *cols, double dt,
+             const double *Qe, const double *QE, const double *ghost_e, const double *ghost_E,
+             double *e, double *E, orc_stats *st) {
+  size_t nb = sizeof(double) * (size_t)n;
+  double *T = malloc(nb), *sig = malloc(nb), *f = malloc(nb), *R = malloc(nb),
+         *lam = malloc(nb), *D = malloc(nb), *V = malloc(nb), *Eg = malloc(nb),
+         *e_old = malloc(nb), *E_old = malloc(nb), *e_l = malloc(nb), *E_l = malloc(nb),
+         *b = malloc(nb), *P = malloc(nb), *adiag = malloc(nb), *gb = malloc(nb),
+         *tv = malloc(nb);
+  double *scr = calloc((size_t)(n / ORC_BLK + 2), sizeof(double));
+  int64_t nnz = rowptr[n];
+  int64_t *arow = malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int32_t *acol = malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+  double *aval = malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  orc_stats s;
+  memset(&s, 0, sizeof s);
+
+  for (int64_t i = 0; i < n; ++i) V[i] = mass[i] / rho[i];
+  s.energy_before = total_energy(n, kind, mass, rho, e, E, tv, scr);
+
+  /* material data from the state at the start of the step */
+  orc_properties(p, n, pos, mass, rho, h, sigma0, kind, copy_of, e, E, dt, rowptr, cols, T,
+                 sig, f, R, lam, D);
+  /* ghost values at the new time level */
+  for (int64_t i = 0; i < n; ++i) {
+    Eg[i] = E[i];
+    if (kind[i] == ORC_DIRICHLET && ghost_E) Eg[i] = ghost_E[i];
+  }
+  orc_assemble(p, n, pos, mass, rho, h, kind, copy_of, dt, sig, f, D, Eg, rowptr, cols, arow,
+               acol, aval, adiag, gb);
+
+  memcpy(e_old, e, nb);
+  memcpy(E_old, E, nb);
+  memcpy(e_l, e, nb);
+  memcpy(E_l, E, nb);
+
+  /* initial material solve: m(e, E^{n-1}) = 0 */
+  for (int64_t i = 0; i < n; ++i) P[i] = p->c * sig[i] * E_l[i] + (Qe ? Qe[i] : 0.0);
+  int64_t fails = 0;
+  int nw = orc_material_solve(p, n, kind, rho, sig, dt, e_old, P, e_l, &fails);
+  s.newton_max = nw;
+
+  int converged = 0;
+  double *E_new = malloc(nb), *e_new = malloc(nb);
+  while (s.outer_iters < p->max_outer) {
+    /* right-hand side: S(E^l) + N(e^l) + Dirichlet ghost coupling */
+    for (int64_t i = 0; i < n; ++i) {
+      if (kind[i] != ORC_INTERIOR) {
+        b[i] = 0.0;
+        continue;
+      }
+      double Tl = e_l[i] / p->cv;
+      double B = p->a * Tl * Tl * Tl * Tl;
+      b[i] = E_old[i] / dt + p->c * sig[i] * B - (1.0 - f[i]) * p->c * sig[i] * E_l[i] +
+             (QE ? QE[i] : 0.0) + gb[i];
+    }
+    memcpy(E_new, E_l, nb);
+    double relres = 0.0;
+    int kit = orc_cg(n, kind, V, arow, acol, aval, adiag, b, E_new, p->tol_krylov, p->max_krylov,
+                     &relres);
+    if (kit < 0) break;
+    if (s.outer_iters < 64) s.krylov_per_outer[s.outer_iters] = kit;
+    s.krylov_total += kit;
+    /* material solve with the new radiation energy */
+    memcpy(e_new, e_l, nb);
+    for (int64_t i = 0; i < n; ++i) P[i] = p->c * sig[i] * E_new[i] + (Qe ? Qe[i] : 0.0);
+    nw = orc_material_solve(p, n, kind, rho, sig, dt, e_old, P, e_new, &fails);
+    if (nw > s.newton_max) s.newton_max = nw;
+    s.outer_iters++;
+    /* convergence (Eq. mat-rad-convergence) */
+    double ce = 0.0, cE = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (kind[i] != ORC_INTERIOR) continue;
+      double de = fabs(e_new[i] - e_l[i]) / fmax(fabs(e_new[i]), 1e-300);
+      double dE = fabs(E_new[i] - E_l[i]) / fmax(fabs(E_new[i]), 1e-300);
+      ce = de > ce ? de : ce;
+      cE = dE > cE ? dE : cE;
+    }
+    memcpy(e_l, e_new, nb);
+    memcpy(E_l, E_new, nb);
+    s.last_change_e = ce;
+    s.last_change_E = cE;
+    if (ce < p->tol_outer_e && cE < p->tol_outer_E) {
+      converged = 1;
+      break;
+    }
+  }
+
+  if (converged) {
+    /* sources and boundary inflow over the step, for the energy balance */
+    for (int64_t i = 0; i < n; ++i)
+      tv[i] = kind[i] == ORC_INTERIOR ? V[i] * ((Qe ? Qe[i] : 0.0) + (QE ? QE[i] : 0.0)) : 0.0;
+    s.source_energy = dt * block_sum(n, tv, scr);
+    for (int64_t i = 0; i < n; ++i) {
+      tv[i] = 0.0;
+      if (kind[i] != ORC_INTERIOR) continue;
+      double acc = 0.0;
+      for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        int64_t j = cols[k];
+        if (kind[j] == ORC_INTERIOR) continue;
+        double r = sqrt(pair_r2(p->dim, pos + i * p->dim, pos + j * p->dim));
+        double w = -V[j] * (D[i] + D[j]) * pair_F(p->dim, r, h[i], h[j]);
+        double Ej = kind[j] == ORC_DIRICHLET ? Eg[j] : E_l[copy_of[j]];
+        acc += w * (Ej - E_l[i]);
+      }
+      tv[i] = V[i] * acc;
+    }
+    s.boundary_energy = dt * block_sum(n, tv, scr);
+    for (int64_t i = 0; i < n; ++i) {
+      if (kind[i] == ORC_INTERIOR) {
+        e[i] = e_l[i];
+        E[i] = E_l[i];
+      } else if (kind[i] == ORC_DIRICHLET) {
+        if (ghost_e) e[i] = ghost_e[i];
+        if (ghost_E) E[i] = ghost_E[i];
+      }
+    }
+    for (int64_t i = 0; i < n; ++i)
+      if (kind[i] == ORC_COPY) {
+        e[i] = e[copy_of[i]];
+        E[i] = E[copy_of[i]];
+      }
+    s.energy_after = total_energy(n, kind, mass, rho, e, E, tv, scr);
+    s.status = 0;
+  } else {
+    s.status = -3;
+  }
+  if (st) *st = s;
+  free(T); free(sig); free(f); free(R); free(lam); free(D); free(V); free(Eg);
+  free(e_old); free(E_old); free(e_l); free(E_l); free(b); free(P); free(adiag);
+  free(gb); free(tv); free(scr); free(arow); free(acol); free(aval); free(E_new);
+  free(e_new);
+  return s.status;
+}
+
+/* Totals sum_i m_i e_i and sum_i V_i E_i over interior particles. */
+void orc_totals(int64_t n, const int32_t *kind, const double *mass, const double *rho,
+                const double *e, const double *E, double out[2]) {
+  double *tv = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *scr = calloc((size_t)(n / ORC_BLK + 2), sizeof(double));
+  for (int64_t i = 0; i < n; ++i) tv[i] = kind[i] == ORC_INTERIOR ? mass[i] * e[i] : 0.0;
+  out[0] = block_sum(n, tv, scr);
+  for (int64_t i = 0; i < n; ++i) tv[i] = kind[i] == ORC_INTERIOR ? mass[i] / rho[i] * E[i] : 0.0;
+  out[1] = block_sum(n, tv, scr);
+  free(tv);
+  free(scr);
+}

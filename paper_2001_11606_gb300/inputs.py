@@ -1,0 +1,364 @@
+"""Seeded synthetic inputs for the implicit SPH thermal-radiative-transfer step.
+
+This module only generates problem data: jittered particle lattices with ghost
+layers, per-particle material data, and the continuum manufactured solution with
+its source terms.  It holds none of the discrete method (no SPH kernel, no
+neighbour search, no operator, no solver), so both the CPU oracle and the CUDA
+path can take their inputs from here.
+
+Random numbers come from splitmix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014): the k-th draw of a stream with
+seed s is mix(s + (k+1)*0x9E3779B97F4A7C15) and a uniform double in [0, 1) is
+(draw >> 11) * 2**-53.
+
+Particle layout.  A lattice of n_x x n_y (x n_z) interior points with spacing
+dx is extended by three ghost layers on every face (enough for a cubic B-spline
+support of 2h = 3 dx around an interior point jittered by at most 0.1 dx).
+Points are enumerated lexicographically over the extended lattice, x fastest,
+and each point draws one uniform per coordinate (x, then y, then z); the
+coordinate is (i + 1/2) dx + (0.2 u - 0.1) dx.  The caller order of particles
+is this enumeration order, interior and ghost points interleaved.
+
+Ghost kinds follow the paper's boundary treatment (Sec. 3.1): a Dirichlet
+ghost (kind 1) carries prescribed values; a reflective ghost (kind 2) is a copy
+of the interior point mirrored across the face (its position is the mirror of
+its source's position, its values are its source's values).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+INTERIOR, DIRICHLET, COPY = 0, 1, 2
+GHOST_LAYERS = 3
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Draws offset .. offset+n-1 of the splitmix64 stream with the given seed."""
+    with np.errstate(over="ignore"):
+        k = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed) + k * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    return (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * 2.0**-53
+
+
+@dataclass
+class Particles:
+    """Particle arrays in caller order (what `sph_rt_set_particles` takes)."""
+
+    dim: int
+    dx: float
+    counts: tuple
+    pos: np.ndarray  # [n, dim] float64
+    kind: np.ndarray  # [n] int32
+    copy_of: np.ndarray  # [n] int64 (source interior index for kind 2, else -1)
+    mass: np.ndarray
+    rho: np.ndarray
+    h: np.ndarray
+    sigma0: np.ndarray
+    extents: tuple = field(default=())
+
+    @property
+    def n(self) -> int:
+        return self.pos.shape[0]
+
+    @property
+    def n_interior(self) -> int:
+        return int(np.count_nonzero(self.kind == INTERIOR))
+
+    @property
+    def volume(self) -> np.ndarray:
+        return self.mass / self.rho
+
+
+def make_lattice(dim: int, counts, dx: float, seed: int, jitter: float = 0.1,
+                 faces=None, rho: float = 1.0, h_over_dx: float = 1.5,
+                 sigma0: float = 1.0) -> Particles:
+    """Jittered lattice plus ghost layers.
+
+    faces[d] = (lo, hi) with each entry 'dirichlet' or 'reflect'; default all
+    Dirichlet.  Where a ghost lies outside faces of both kinds, Dirichlet wins.
+    """
+    counts = tuple(int(c) for c in counts)
+    assert len(counts) == dim and dim in (1, 2, 3)
+    if faces is None:
+        faces = [("dirichlet", "dirichlet")] * dim
+    # ghost layer k (1-based, outside the face) can reach an interior point
+    # only if k - 2*jitter < 2h/dx; keep every layer that can.
+    g = max(GHOST_LAYERS, int(math.ceil(2.0 * h_over_dx + 2.0 * jitter)) - 1)
+    ext = [c + 2 * g for c in counts]
+    n_tot = int(np.prod(ext))
+    # lexicographic enumeration of the extended lattice, x fastest
+    grids = np.meshgrid(*[np.arange(-g, c + g) for c in counts], indexing="ij")
+    idx = np.stack([gr.transpose(*range(dim)[::-1]).reshape(-1) for gr in grids], axis=1)
+    # idx[:, d] is the lattice index along dimension d; rows ordered x fastest
+    u = uniform01(seed, n_tot * dim).reshape(n_tot, dim)
+    amp = jitter / 0.1  # 1.0 for the standard +-0.1 dx jitter, 0.0 for a plain lattice
+    pos = (idx.astype(np.float64) + 0.5) * dx + ((0.2 * u - 0.1) * amp) * dx
+    outside_lo = idx < 0
+    outside_hi = idx >= np.array(counts)
+    outside = outside_lo | outside_hi
+    kind = np.full(n_tot, INTERIOR, dtype=np.int32)
+    copy_of = np.full(n_tot, -1, dtype=np.int64)
+    dir_out = np.zeros(n_tot, dtype=bool)
+    ref_out = np.zeros(n_tot, dtype=bool)
+    for d in range(dim):
+        lo, hi = faces[d]
+        for side, mask in ((lo, outside_lo[:, d]), (hi, outside_hi[:, d])):
+            if side == "dirichlet":
+                dir_out |= mask
+            elif side == "reflect":
+                ref_out |= mask
+            else:
+                raise ValueError(side)
+    kind[dir_out] = DIRICHLET
+    is_copy = ref_out & ~dir_out
+    kind[is_copy] = COPY
+    if np.any(is_copy):
+        src = idx[is_copy].copy()
+        cpos = pos[is_copy].copy()
+        for d in range(dim):
+            L = counts[d] * dx
+            lo_m = src[:, d] < 0
+            hi_m = src[:, d] >= counts[d]
+            src[lo_m, d] = -1 - src[lo_m, d]
+            src[hi_m, d] = 2 * counts[d] - 1 - src[hi_m, d]
+        # caller index of the source point
+        strides = np.cumprod([1] + ext[:-1])
+        lin = ((src + g) * np.array(strides)).sum(axis=1)
+        copy_of[is_copy] = lin
+        spos = pos[lin]
+        for d in range(dim):
+            L = counts[d] * dx
+            lo_m = idx[is_copy][:, d] < 0
+            hi_m = idx[is_copy][:, d] >= counts[d]
+            cpos[:, d] = spos[:, d]
+            cpos[lo_m, d] = -spos[lo_m, d]
+            cpos[hi_m, d] = 2.0 * L - spos[hi_m, d]
+        pos[is_copy] = cpos
+    vol = dx ** dim
+    rho_a = np.full(n_tot, rho, dtype=np.float64)
+    return Particles(dim=dim, dx=dx, counts=counts, pos=np.ascontiguousarray(pos),
+                     kind=kind, copy_of=copy_of, mass=rho_a * vol, rho=rho_a,
+                     h=np.full(n_tot, h_over_dx * dx), sigma0=np.full(n_tot, sigma0),
+                     extents=tuple(c * dx for c in counts))
+
+
+# ---------------------------------------------------------------------------
+# Continuum manufactured solution T(x, t) = 1 + amp * prod_a sin(pi x_a) e^{-t}
+# with E = a T^4 and e = c_v T, opacity sigma = sigma0 T^p, flux limiter
+# lambda(R).  Sources come from inserting it into the material-energy and
+# flux-limited diffusion equations (the paper's Eqs. for rho de/dt and dE/dt):
+#   Q_e = rho c_v dT/dt                      (emission and absorption cancel)
+#   Q_E = dE/dt - div(D grad E),  D = c lambda(R) / sigma,  R = |grad E|/(sigma E)
+# ---------------------------------------------------------------------------
+
+
+def _limiter_value_and_slope(R, limiter: int, larsen_k: float):
+    """Continuum flux limiter lambda(R) and d lambda / dR (problem definition)."""
+    if limiter == 0:
+        return np.full_like(R, 1.0 / 3.0), np.zeros_like(R)
+    if limiter == 1:
+        den = 6.0 + 3.0 * R + R * R
+        return (2.0 + R) / den, -R * (4.0 + R) / (den * den)
+    if limiter == 2:
+        k = larsen_k
+        s = 3.0**k + R**k
+        return s ** (-1.0 / k), -(R ** (k - 1.0)) * s ** (-1.0 / k - 1.0)
+    raise ValueError(limiter)
+
+
+@dataclass
+class Manufactured:
+    dim: int
+    amp: float = 0.5
+    a: float = 1.0
+    c: float = 1.0
+    cv: float = 1.0
+    rho: float = 1.0
+    sigma0: float = 1.0
+    p: float = 0.0
+    limiter: int = 0
+    larsen_k: float = 2.0
+
+    def T(self, x, t):
+        s = np.prod(np.sin(np.pi * x), axis=1)
+        return 1.0 + self.amp * s * math.exp(-t)
+
+    def fields(self, x, t):
+        """(e, E) of the manufactured solution at positions x, time t."""
+        T = self.T(x, t)
+        return self.cv * T, self.a * T**4
+
+    def sources(self, x, t):
+        """(Q_e, Q_E) at positions x, time t."""
+        d = self.dim
+        g_t = math.exp(-t)
+        sn = np.sin(np.pi * x)
+        cs = np.cos(np.pi * x)
+        prod = np.prod(sn, axis=1)
+        T = 1.0 + self.amp * prod * g_t
+        dTdt = -self.amp * prod * g_t
+        grad = np.empty_like(x)
+        for al in range(d):
+            others = np.prod(np.delete(sn, al, axis=1), axis=1) if d > 1 else 1.0
+            grad[:, al] = self.amp * g_t * np.pi * cs[:, al] * others
+        H = np.empty((x.shape[0], d, d))
+        for al in range(d):
+            for be in range(d):
+                if al == be:
+                    H[:, al, al] = -np.pi**2 * self.amp * g_t * prod
+                else:
+                    rest = [k for k in range(d) if k not in (al, be)]
+                    o = np.prod(sn[:, rest], axis=1) if rest else 1.0
+                    H[:, al, be] = self.amp * g_t * np.pi**2 * cs[:, al] * cs[:, be] * o
+        a, c, p = self.a, self.c, self.p
+        gnorm = np.sqrt(np.sum(grad * grad, axis=1))
+        sigma = self.sigma0 * T**p
+        R = 4.0 * gnorm / (sigma * T)
+        lam, dlam = _limiter_value_and_slope(R, self.limiter, self.larsen_k)
+        D = c * lam / sigma
+        Hg = np.einsum("nab,nb->na", H, grad)
+        safe = np.where(gnorm > 0.0, gnorm, 1.0)
+        dgnorm = np.where(gnorm[:, None] > 0.0, Hg / safe[:, None], 0.0)
+        # R = (4/sigma0) |g| T^{-(p+1)}
+        dR = (4.0 / self.sigma0) * (dgnorm * T[:, None] ** (-(p + 1.0))
+                                    - (p + 1.0) * gnorm[:, None] * T[:, None] ** (-(p + 2.0)) * grad)
+        dD = (c / sigma)[:, None] * (dlam[:, None] * dR - (lam * p / T)[:, None] * grad)
+        dE = 4.0 * a * (T**3)[:, None] * grad
+        lapE = 4.0 * a * (3.0 * T**2 * gnorm**2 + T**3 * np.trace(H, axis1=1, axis2=2))
+        divflux = np.sum(dD * dE, axis=1) + D * lapE
+        Qe = self.rho * self.cv * dTdt
+        QE = 4.0 * a * T**3 * dTdt - divflux
+        return Qe, QE
+
+
+# ---------------------------------------------------------------------------
+# Named workloads (sizes and physics of the verification problems)
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class Workload:
+    name: str
+    particles: Particles
+    params: dict
+    dt: float
+    steps: int
+    mms: Manufactured | None = None
+    e0: np.ndarray | None = None
+    E0: np.ndarray | None = None
+
+    def step_inputs(self, n: int):
+        """Sources and ghost values for step n (time t^n = n dt), caller order.
+
+        Returns (Qe, QE, ghost_e, ghost_E); arrays over all particles.
+        """
+        P = self.particles
+        if self.mms is None:
+            z = np.zeros(P.n)
+            ge = self.e0.copy()
+            gE = self.E0.copy()
+            return z, z.copy(), ge, gE
+        t = n * self.dt
+        Qe, QE = self.mms.sources(P.pos, t)
+        ge, gE = self.mms.fields(P.pos, t)
+        return Qe, QE, ge, gE
+
+
+def _mms_workload(name, dim, n, seed, p, limiter, dt, steps, jitter=0.1, h_over_dx=1.5,
+                  **tol):
+    P = make_lattice(dim, (n,) * dim, 1.0 / n, seed, jitter=jitter, h_over_dx=h_over_dx)
+    mms = Manufactured(dim=dim, p=p, limiter=limiter)
+    e0, E0 = mms.fields(P.pos, 0.0)
+    params = dict(dim=dim, a=1.0, c=1.0, cv=1.0, limiter=limiter, larsen_k=2.0,
+                  opacity_exp=float(p), T_floor=0.0, tol_outer_e=1e-8, tol_outer_E=1e-8,
+                  tol_inner_e=1e-13, tol_krylov=1e-12, max_outer=50, max_inner_e=50,
+                  max_krylov=2000)
+    params.update(tol)
+    return Workload(name=name, particles=P, params=params, dt=dt, steps=steps, mms=mms,
+                    e0=e0, E0=E0)
+
+
+def mms_2d(n: int = 32, seed: int = 1, jitter: float = 0.1, steps: int = 10, dt: float = 1e-3,
+           h_over_dx: float = 1.5):
+    """2-D manufactured problem: constant opacity, no limiter (lambda = 1/3)."""
+    return _mms_workload(f"mms2d-{n}^2", 2, n, seed, 0.0, 0, dt, steps, jitter=jitter,
+                         h_over_dx=h_over_dx, tol_outer_e=1e-10, tol_outer_E=1e-10)
+
+
+def mms_3d_lp(n: int = 64, seed: int = 2, jitter: float = 0.1, steps: int = 100, dt: float = 1e-3):
+    """3-D manufactured problem: sigma = T^-3, Levermore-Pomraning limiter."""
+    return _mms_workload(f"mms3d-lp-{n}^3", 3, n, seed, -3.0, 1, dt, steps, jitter=jitter)
+
+
+def mms_3d(n: int = 128, seed: int = 3, jitter: float = 0.1, steps: int = 50, dt: float = 1e-3):
+    """3-D manufactured problem: constant opacity, no limiter."""
+    return _mms_workload(f"mms3d-{n}^3", 3, n, seed, 0.0, 0, dt, steps, jitter=jitter)
+
+
+def sphere_3d(n: int = 256, seed: int = 5, steps: int = 20, dt: float = 1e-4):
+    """Unit cube with a dense, opaque, hot sphere (r < 0.25) in a cold medium."""
+    P = make_lattice(3, (n,) * 3, 1.0 / n, seed)
+    r = np.sqrt(np.sum((P.pos - 0.5) ** 2, axis=1))
+    inside = r < 0.25
+    P.rho = np.where(inside, 10.0, 1.0)
+    P.mass = P.rho * P.dx**3
+    P.sigma0 = np.where(inside, 1e3, 1.0)
+    T0 = np.where(inside, 1.0, 0.01)
+    e0 = T0.copy()
+    E0 = T0**4
+    params = dict(dim=3, a=1.0, c=1.0, cv=1.0, limiter=1, larsen_k=2.0, opacity_exp=0.0,
+                  T_floor=0.0, tol_outer_e=1e-8, tol_outer_E=1e-8, tol_inner_e=1e-13,
+                  tol_krylov=1e-12, max_outer=50, max_inner_e=50, max_krylov=2000)
+    return Workload(name=f"sphere3d-{n}^3", particles=P, params=params, dt=dt, steps=steps,
+                    e0=e0, E0=E0)
+
+
+def heating_wave(dim: int, n_target: int, sigma0: float, seed: int, steps: int = 20,
+                 dt: float = 1e-3):
+    """Cold slab on [0,4]x[0,1]^(d-1) at T=1e-3 driven by a T=1 Dirichlet face at x<0.
+
+    Lateral faces reflect (copy ghosts); the far x face holds T=1e-3.
+    Opacity sigma = sigma0 T^-3, Levermore-Pomraning limiter.
+    """
+    ny = max(2, int(round((n_target / 4.0) ** (1.0 / dim))))
+    counts = (4 * ny,) + (ny,) * (dim - 1)
+    dx = 1.0 / ny
+    faces = [("dirichlet", "dirichlet")] + [("reflect", "reflect")] * (dim - 1)
+    P = make_lattice(dim, counts, dx, seed, faces=faces, sigma0=sigma0)
+    T0 = np.where(P.pos[:, 0] < 0.0, 1.0, 1e-3)
+    T0 = np.where(P.kind == COPY, 1e-3, T0)
+    e0 = T0.copy()
+    E0 = T0**4
+    params = dict(dim=dim, a=1.0, c=1.0, cv=1.0, limiter=1, larsen_k=2.0, opacity_exp=-3.0,
+                  T_floor=0.0, tol_outer_e=1e-8, tol_outer_E=1e-8, tol_inner_e=1e-13,
+                  tol_krylov=1e-12, max_outer=50, max_inner_e=50, max_krylov=2000)
+    return Workload(name=f"wave{dim}d-{P.n_interior}", particles=P, params=params, dt=dt,
+                    steps=steps, e0=e0, E0=E0)
+
+
+def serving_stream(n_requests: int = 512, seed: int = 4, mean_interarrival: float = 1.0,
+                   n_min: int = 1000, n_max: int = 256000):
+    """Request descriptors of the serving stream: (arrival, dim, n_target, sigma0).
+
+    Draws come from one splitmix64 stream in request order: inter-arrival time
+    (exponential, mean `mean_interarrival`), dimension (2 or 3, 50/50), particle
+    count (log-uniform in [n_min, n_max]) and sigma0 (log-uniform in [1, 100]).
+    """
+    u = uniform01(seed, 4 * n_requests).reshape(n_requests, 4)
+    gaps = -np.log1p(-u[:, 0]) * mean_interarrival
+    arrival = np.cumsum(gaps)
+    dims = np.where(u[:, 1] < 0.5, 2, 3)
+    n_t = np.exp(np.log(n_min) + u[:, 2] * (np.log(n_max) - np.log(n_min))).astype(np.int64)
+    sig = np.exp(u[:, 3] * np.log(100.0))
+    return [dict(arrival=float(arrival[i]), dim=int(dims[i]), n_target=int(n_t[i]),
+                 sigma0=float(sig[i]), seed=seed * 100003 + i) for i in range(n_requests)]

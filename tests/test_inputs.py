@@ -1,0 +1,70 @@
+"""Checks of the seeded input generators (not of the method)."""
+import numpy as np
+
+from paper_2001_11606_gb300 import inputs as I
+
+
+def test_splitmix64_reference_values():
+    # published splitmix64 outputs for state 0 (first three draws)
+    z = I.splitmix64(0, 3)
+    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_lattice_layout_and_jitter_bounds():
+    P = I.make_lattice(3, (4, 5, 6), 0.1, seed=3)
+    assert P.n == 10 * 11 * 12 and P.n_interior == 4 * 5 * 6
+    idx0 = np.floor(P.pos / 0.1)  # cell of each point
+    frac = P.pos / 0.1 - idx0
+    assert np.all(np.abs(frac - 0.5) <= 0.1 + 1e-12)
+    # x runs fastest in the caller order
+    assert P.pos[1, 0] > P.pos[0, 0] and abs(P.pos[1, 1] - P.pos[0, 1]) < 0.2 * 0.1 + 1e-12
+
+
+def test_reflective_ghosts_mirror_their_source():
+    P = I.make_lattice(2, (6, 4), 0.25, seed=2, faces=[("dirichlet", "dirichlet"),
+                                                        ("reflect", "reflect")])
+    c = np.flatnonzero(P.kind == I.COPY)
+    assert len(c) > 0 and np.all(P.kind[P.copy_of[c]] == I.INTERIOR)
+    src = P.pos[P.copy_of[c]]
+    g = P.pos[c]
+    assert np.allclose(g[:, 0], src[:, 0])
+    lo = g[:, 1] < 0
+    assert np.allclose(g[lo, 1], -src[lo, 1]) and np.allclose(g[~lo, 1], 2.0 - src[~lo, 1])
+
+
+def _fd_sources(m: I.Manufactured, x, t, eps=1e-5):
+    """Sources by finite differences of the continuum fields (independent check)."""
+    d = m.dim
+
+    def E(x, t):
+        return m.a * m.T(x, t) ** 4
+
+    def D(x, t):
+        T = m.T(x, t)
+        g = np.stack([(E(x + eps * np.eye(d)[k], t) - E(x - eps * np.eye(d)[k], t)) / (2 * eps)
+                      for k in range(d)], axis=1)
+        sig = m.sigma0 * T ** m.p
+        R = np.sqrt(np.sum(g * g, axis=1)) / (sig * E(x, t))
+        lam = I._limiter_value_and_slope(R, m.limiter, m.larsen_k)[0]
+        return m.c * lam / sig
+
+    div = np.zeros(x.shape[0])
+    for k in range(d):
+        ek = np.eye(d)[k] * eps
+        fp = D(x + ek / 2, t) * (E(x + ek, t) - E(x, t)) / eps
+        fm = D(x - ek / 2, t) * (E(x, t) - E(x - ek, t)) / eps
+        div += (fp - fm) / eps
+    dEdt = (E(x, t + eps) - E(x, t - eps)) / (2 * eps)
+    dTdt = (m.T(x, t + eps) - m.T(x, t - eps)) / (2 * eps)
+    return m.rho * m.cv * dTdt, dEdt - div
+
+
+def test_manufactured_sources_match_finite_differences():
+    rng = np.random.default_rng(0)
+    for dim, p, lim in ((2, 0.0, 0), (3, -3.0, 1), (3, -3.0, 2)):
+        m = I.Manufactured(dim=dim, p=p, limiter=lim)
+        x = rng.uniform(0.05, 0.95, size=(40, dim))
+        Qe, QE = m.sources(x, 0.3)
+        Qe2, QE2 = _fd_sources(m, x, 0.3, eps=2e-4)
+        assert np.allclose(Qe, Qe2, rtol=1e-6, atol=1e-8)
+        assert np.allclose(QE, QE2, rtol=2e-3, atol=2e-3 * np.max(np.abs(QE)))
