@@ -1,0 +1,363 @@
+"""Benchmark of the implicit SPH thermal-radiative-transfer step on GB300.
+
+One benchmark "step" is one pass of the whole hot path over one job of the
+3-D manufactured workload (64^3 = 262,144 interior particles on a jittered
+lattice plus 80,856 Dirichlet ghosts, h = 1.5 dx, sigma = T^-3, Levermore
+limiter): set the particles (Morton sort, cell list, neighbour search,
+operator sparsity) and advance 100 backward-Euler steps of dt = 1e-3 (material
+data, assembly, AMG set-up, preconditioned Krylov solves inside the
+nonlinear-elimination loop, per-particle Newton).  The metric is
+particle-steps/s = interior particles x time steps / wall time.
+
+  value     inputs resident in HBM before timing (device entry points)
+  e2e       the same job through the host-pointer C ABI: particle arrays and
+            per-step sources copied from pinned host memory, final energies
+            copied back, all inside the timed region
+  roofline  the fine-operator SpMV-class kernels (CG SpMV, residual and
+            Chebyshev smoother sweeps on the finest level), CUDA-event time
+            over the timed region against the measured HBM copy bandwidth
+  cpu_baseline / --impl reference   the CPU oracle (tests only otherwise) on a
+            bounded sample of the same workload, on the host cores
+
+Multi-GPU (torchrun): replicas only -- every rank runs its own job, the
+metric is the sum over ranks, timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2001_11606_gb300 import inputs as I  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[3 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name: str):
+    if name == "mms3d-lp-64":
+        return I.mms_3d_lp(n=64, steps=100)
+    if name == "mms3d-lp-32":
+        return I.mms_3d_lp(n=32, steps=20)
+    if name == "mms2d-32":
+        return I.mms_2d(n=32, steps=10)
+    if name == "mms3d-128":
+        return I.mms_3d(n=128, steps=50)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def cpu_sample(w, steps: int = 1):
+    """Oracle timing on a bounded sample: neighbour set-up plus `steps` steps."""
+    import oracle as O
+
+    t0 = time.perf_counter()
+    pb = O.Problem(w.particles, w.params)
+    t1 = time.perf_counter()
+    e, E = w.e0.copy(), w.E0.copy()
+    t_steps = 0.0
+    for n in range(1, steps + 1):
+        ins = w.step_inputs(n)
+        ts = time.perf_counter()
+        rc, e, E, _ = pb.step(e, E, w.dt, *ins)
+        t_steps += time.perf_counter() - ts
+    return dict(setup_s=t1 - t0, step_s=t_steps / steps, cores=O.num_threads())
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    import oracle as O
+
+    O.build()
+    n_int = w.particles.n_interior
+    pb = O.Problem(w.particles, w.params)
+    e, E = w.e0.copy(), w.E0.copy()
+    inputs = [w.step_inputs(n) for n in range(1, args.warmup + args.steps + 1)]
+    for n in range(args.warmup):
+        rc, e, E, _ = pb.step(e, E, w.dt, *inputs[n])
+    t0 = time.perf_counter()
+    for n in range(args.warmup, args.warmup + args.steps):
+        rc, e, E, _ = pb.step(e, E, w.dt, *inputs[n])
+    dt_s = time.perf_counter() - t0
+    value = n_int * args.steps / dt_s
+    sample = (f"{w.name}: one backward-Euler step per benchmark step (neighbour lists built "
+              f"once before timing), {n_int} interior particles")
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": value,
+            "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": O.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="mms3d-lp-64")
+    ap.add_argument("--time-steps", type=int, default=None,
+                    help="backward-Euler steps per job (default: the workload's)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precond", default="amg", choices=["jacobi", "chebyshev", "amg"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    w = make_workload(args.workload)
+    if args.time_steps:
+        w.steps = args.time_steps
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+
+    from paper_2001_11606_gb300 import sphrt
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    P = w.particles
+    n, n_int, T = P.n, P.n_interior, w.steps
+    stream = torch.cuda.Stream(device=dev)
+    precond = {"jacobi": sphrt.PRECOND_JACOBI, "chebyshev": sphrt.PRECOND_CHEBYSHEV,
+               "amg": sphrt.PRECOND_AMG}[args.precond]
+    prec = sphrt.MIXED if args.precision == "mixed" else sphrt.FP64
+    cfg = sphrt.config_from_params(w.params, device=local, stream=stream.cuda_stream,
+                                   precond=precond, precision=prec, kernel_timing=1)
+    S = sphrt.Solver(cfg)
+
+    # ---- inputs resident in HBM --------------------------------------------
+    f64 = dict(dtype=torch.float64, device=dev)
+    d_pos = torch.as_tensor(P.pos, **f64)
+    d_part = [torch.as_tensor(a, **f64) for a in (P.mass, P.rho, P.h, P.sigma0)]
+    d_kind = torch.as_tensor(P.kind, dtype=torch.int32, device=dev)
+    d_e0, d_E0 = torch.as_tensor(w.e0, **f64), torch.as_tensor(w.E0, **f64)
+    host_inputs = [w.step_inputs(k) for k in range(1, T + 1)]
+    d_inputs = [[torch.as_tensor(a, **f64) for a in ins] for ins in host_inputs]
+    d_e_out = torch.empty(n, **f64)
+    d_E_out = torch.empty(n, **f64)
+    torch.cuda.synchronize(dev)
+
+    def job_device():
+        S.set_particles_device(n, d_pos.data_ptr(), *[a.data_ptr() for a in d_part],
+                               d_kind.data_ptr(), 0, d_e0.data_ptr(), d_E0.data_ptr())
+        outer = krylov = 0
+        for k in range(T):
+            _, st = S.step_device(w.dt, *[a.data_ptr() for a in d_inputs[k]])
+            outer += st.outer_iters
+            krylov += st.krylov_iters_total
+        S.get_energies_device(d_e_out.data_ptr(), d_E_out.data_ptr())
+        return outer, krylov
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        job_device()
+    S.kernel_stats(reset=True)
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    launches0 = S.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        iters.append(job_device())
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    gpu_ms = ev0.elapsed_time(ev1)
+    launches = S.launch_count() - launches0
+    k_launch, k_ms, k_bytes = S.kernel_stats(reset=True)
+    t_local = gpu_ms / 1e3
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    else:
+        t_max = t_local
+    value = world * n_int * T * args.steps / t_max
+
+    # ---- end to end through the host-pointer C ABI ---------------------------
+    e2e = None
+    if not args.no_e2e:
+        pin = dict(dtype=torch.float64, pin_memory=True)
+        h_pos = torch.as_tensor(P.pos, dtype=torch.float64).pin_memory()
+        h_part = [torch.as_tensor(a, dtype=torch.float64).pin_memory() for a in
+                  (P.mass, P.rho, P.h, P.sigma0, w.e0, w.E0)]
+        h_kind = torch.as_tensor(P.kind, dtype=torch.int32).pin_memory()
+        h_inputs = [[torch.as_tensor(a, dtype=torch.float64).pin_memory() for a in ins]
+                    for ins in host_inputs]
+        h_e = torch.empty(n, **pin)
+        h_E = torch.empty(n, **pin)
+        L = sphrt.load()
+        import ctypes as C
+
+        def job_host():
+            rc = L.sph_rt_set_particles(S._h, n, C.c_void_p(h_pos.data_ptr()),
+                                        *[C.c_void_p(a.data_ptr()) for a in h_part[:4]],
+                                        C.c_void_p(h_kind.data_ptr()), None,
+                                        C.c_void_p(h_part[4].data_ptr()),
+                                        C.c_void_p(h_part[5].data_ptr()))
+            if rc != 0:
+                raise RuntimeError(S.last_error())
+            for k in range(T):
+                S.step_host_ptrs(w.dt, *[a.data_ptr() for a in h_inputs[k]])
+            S.get_energies_host_ptrs(h_e.data_ptr(), h_E.data_ptr())
+
+        job_host()
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            job_host()
+        torch.cuda.synchronize(dev)
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+
+            tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        h2d = (P.pos.nbytes + 6 * n * 8 + n * 4) + T * 4 * n * 8
+        e2e = {"value": world * n_int * T * args.steps / t_e2e, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(2 * n * 8)}
+
+    if rank != 0:
+        return
+    hbm, src = peaks()
+    achieved = (k_bytes / (k_ms / 1e3)) / 1e9 if k_ms > 0 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm if achieved else None, "traffic": None,
+            "kernel": "fine-operator SpMV-class kernels (spmv_pq, resid, cheb_step on level 0)",
+            "launches": k_launch, "bytes_per_launch": k_bytes / k_launch if k_launch else None,
+            "peak_source": src}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+
+        O.build()
+        cs = cpu_sample(w, steps=1)
+        per = cs["setup_s"] / T + cs["step_s"]
+        cpu = {"value": n_int / per, "unit": "particle-steps/s", "cores": cs["cores"],
+               "kind": "oracle",
+               "sample": (f"{w.name}: oracle neighbour set-up ({cs['setup_s']:.1f} s, amortised "
+                          f"over {T} steps) plus one backward-Euler step ({cs['step_s']:.1f} s)")}
+    outer = sum(i[0] for i in iters) / (args.steps * T)
+    kry = sum(i[1] for i in iters) / (args.steps * T)
+    line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == sphrt.FP64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "interior_particles": n_int, "ghosts": n - n_int,
+                       "time_steps_per_job": T, "dt": w.dt, "precision": args.precision,
+                       "precond": args.precond, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (operator > 129 MB)",
+                       "outer_iters_per_step": outer, "krylov_iters_per_step": kry,
+                       "ms_per_time_step": 1e3 * t_max / (args.steps * T)},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * sph_rt.h -- C ABI of the GB300 implicit SPH thermal-radiative-transfer step.
+ *
+ * The library advances the grey two-temperature equations of Bassett, Owen &
+ * Brunner (arXiv:2001.11606) -- material energy e and radiation energy E of
+ * SPH particles coupled by emission and absorption, radiation transported by
+ * flux-limited diffusion -- with backward Euler in time and the paper's
+ * nonlinear-elimination (inexact Newton) iteration (Alg. 1).  Space is
+ * discretised with the SPH Brookshaw second derivative (Sec. 2.3-2.4).
+ *
+ * Conventions for every call:
+ *  - Arrays are owned by the caller and only read or written during the call.
+ *    Unless a name ends in `_device`, pointers are HOST pointers.  `_device`
+ *    variants take pointers into device memory of the handle's device; they
+ *    are read on the handle's stream (stream-ordered, no host sync needed by
+ *    the caller beyond normal stream semantics).
+ *  - Particle arrays are in the CALLER'S order, length n_total (interior and
+ *    ghost particles together); positions are row-major [n_total][dim].
+ *  - The handle (sph_rt*) is owned by the library; a stream passed in the
+ *    configuration is borrowed, never destroyed.
+ *  - One handle is used by one host thread at a time.
+ *  - Errors are negative sph_rt_status codes; sph_rt_last_error() gives a
+ *    message.  Input validation happens on the host before any device work,
+ *    so an invalid call leaves the handle unchanged.  A step that does not
+ *    converge returns SPH_RT_ENOTCONV and leaves the state at t^{n-1}.
+ *  - All arithmetic of the FP64 path is IEEE double on the device; FMA
+ *    contraction is disabled where results are compared bit for bit
+ *    (neighbour distances).
+ */
+#ifndef SPH_RT_H
+#define SPH_RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_rt sph_rt; /* opaque handle */
+
+typedef enum {
+  SPH_RT_OK = 0,
+  SPH_RT_EINVAL = -1,   /* invalid argument (checked on the host) */
+  SPH_RT_ENOMEM = -2,   /* device allocation failed */
+  SPH_RT_ENOTCONV = -3, /* outer or Krylov iteration limit reached; state unchanged */
+  SPH_RT_EDEVICE = -4,  /* CUDA error; message has the CUDA error string */
+  SPH_RT_ESTATE = -5    /* call out of order (e.g. step before set_particles) */
+} sph_rt_status;
+
+enum { SPH_RT_INTERIOR = 0, SPH_RT_DIRICHLET = 1, SPH_RT_COPY = 2 };
+enum { SPH_RT_LIMITER_NONE = 0, SPH_RT_LIMITER_LEVERMORE = 1, SPH_RT_LIMITER_LARSEN = 2 };
+enum { SPH_RT_PRECOND_JACOBI = 0, SPH_RT_PRECOND_CHEBYSHEV = 1, SPH_RT_PRECOND_AMG = 2 };
+enum { SPH_RT_FP64 = 0, SPH_RT_MIXED = 1 };
+
+/*
+ * Problem constants and solver controls.
+ * Physics (Sec. 2.1-2.2): B = a T^4, e = c_v T, sigma_a = sigma_t = sigma0 T^p,
+ * D = c lambda(R) / sigma_t with R = |grad E| / (sigma_t E) and lambda from
+ *   none      lambda = 1/3                      (Fick's law, Eq. diffusion with 1/3)
+ *   Levermore lambda = (2+R)/(6+3R+R^2)
+ *   Larsen    lambda = (3^k + R^k)^(-1/k)
+ * Tolerances (Table tab:tolerances, Eq. mat-rad-convergence):
+ *   tol_outer_e / tol_outer_E  max_i |x^{l+1}-x^l| / |x^{l+1}| of the outer loop
+ *   tol_inner_e                per-particle Newton |de| <= tol |e|
+ *   tol_krylov                 ||b - A E||_2 <= tol ||b||_2 (unscaled rows)
+ */
+typedef struct {
+  int32_t dim;          /* 2 or 3 (1 is accepted too) */
+  double a, c, cv;      /* radiation constant, speed of light, specific heat */
+  int32_t limiter;      /* SPH_RT_LIMITER_* */
+  double larsen_k;      /* k of the Larsen limiter (> 0) */
+  double opacity_exp;   /* p in sigma = sigma0 T^p */
+  double T_floor;       /* T inside sigma and R is max(T, T_floor); 0 = off */
+  double tol_outer_e, tol_outer_E, tol_inner_e, tol_krylov;
+  int32_t max_outer, max_inner_e, max_krylov;
+  int32_t precond;      /* SPH_RT_PRECOND_* */
+  int32_t precision;    /* SPH_RT_FP64 or SPH_RT_MIXED */
+  int32_t cheb_degree;  /* Chebyshev smoother / preconditioner degree (>= 1) */
+  int32_t amg_rebuild;  /* 1: redo AMG aggregation every step; 0: keep the first step's */
+  double amg_theta;     /* AMG strength threshold */
+  int32_t check_every;  /* Krylov iterations queued between host convergence reads */
+  int32_t kernel_timing;/* 1: record CUDA events around SpMV launches (sph_rt_kernel_stats) */
+  int32_t device;       /* CUDA device ordinal */
+  void *stream;         /* cudaStream_t to run on (borrowed); NULL = library-owned stream */
+} sph_rt_config;
+
+/* Per-step diagnostics (the paper's columns: outer iterations per step and
+ * Krylov iterations per outer iteration, Sec. 4.3; energy balance, Sec. 2.5). */
+typedef struct {
+  int32_t outer_iters;
+  int32_t krylov_iters_total;
+  int32_t krylov_iters_per_outer[64];
+  int32_t newton_iters_max;
+  double energy_before, energy_after; /* sum_i m_i e_i + V_i E_i over interior particles */
+  double source_energy;               /* dt sum_i V_i (Q_e + Q_E) */
+  double boundary_energy;             /* dt sum_i V_i sum_{j ghost} w_ij (E_j - E_i) */
+  double last_change_e, last_change_E;/* final outer-loop changes */
+  double t_setup_ms, t_assembly_ms, t_amg_ms, t_krylov_ms, t_newton_ms;
+} sph_rt_stats;
+
+/* Fill *cfg with defaults: dim 3, a = c = c_v = 1, no limiter, p = 0,
+ * tolerances of Table tab:tolerances (manufactured problem row) with
+ * tol_inner_e = 1e-13, AMG preconditioner, FP64, device 0, own stream. */
+void sph_rt_default_config(sph_rt_config *cfg);
+
+/* Create a handle.  No device work happens until sph_rt_set_particles.
+ * Returns EINVAL (and *out = NULL) for an out-of-range configuration; the
+ * reason is then available from sph_rt_last_error(NULL) on the same thread. */
+sph_rt_status sph_rt_create(const sph_rt_config *cfg, sph_rt **out);
+
+/*
+ * Set the particles (positions, masses, densities, smoothing lengths, opacity
+ * prefactors, kinds) and the initial state; build the Morton-sorted cell list,
+ * the neighbour lists (j != i with r^2 < (2 max(h_i,h_j))^2, Sec. 3.1), the
+ * fixed geometric weights and the operator's sparsity.  Replaces any previous
+ * particle set.
+ *   kind[i]    SPH_RT_INTERIOR, SPH_RT_DIRICHLET (ghost with prescribed values)
+ *              or SPH_RT_COPY (ghost that copies interior particle copy_of[i])
+ *   copy_of    may be NULL when there are no copy ghosts
+ *   e0, E0     initial material and radiation energy (ghosts: their values)
+ * EINVAL: n_total < 1, no interior particle, non-finite value, m/rho/h <= 0,
+ * sigma0 < 0, kind out of range, copy_of not pointing at an interior particle.
+ */
+sph_rt_status sph_rt_set_particles(sph_rt *s, int64_t n_total, const double *pos,
+                                   const double *mass, const double *rho, const double *h,
+                                   const double *sigma0, const int32_t *kind,
+                                   const int64_t *copy_of, const double *e0, const double *E0);
+
+/* Same, with every array in device memory. */
+sph_rt_status sph_rt_set_particles_device(sph_rt *s, int64_t n_total, const double *pos,
+                                          const double *mass, const double *rho,
+                                          const double *h, const double *sigma0,
+                                          const int32_t *kind, const int64_t *copy_of,
+                                          const double *e0, const double *E0);
+
+/*
+ * One backward-Euler step of size dt (Eq. ne-starting-point, Alg. 1):
+ *   material data from the state at the step's start (Sec. 3.2), operator
+ *   assembly, preconditioner set-up, initial material solve, then outer
+ *   iterations of {diffusion solve (Eq. diffusion-solve), material solve
+ *   (Eq. material-energy-solve)} until Eq. mat-rad-convergence holds.
+ *   Qe, QE    sources at t^n [n_total] (ghost entries ignored); NULL = 0
+ *   ghost_e, ghost_E  Dirichlet-ghost values at t^n [n_total] (other entries
+ *             ignored); NULL = keep the current ghost values
+ *   stats     may be NULL
+ */
+sph_rt_status sph_rt_step(sph_rt *s, double dt, const double *Qe, const double *QE,
+                          const double *ghost_e, const double *ghost_E, sph_rt_stats *stats);
+
+/* Same, with the four arrays in device memory. */
+sph_rt_status sph_rt_step_device(sph_rt *s, double dt, const double *Qe, const double *QE,
+                                 const double *ghost_e, const double *ghost_E,
+                                 sph_rt_stats *stats);
+
+/* Copy the current state out, caller order [n_total] (either may be NULL);
+ * totals[0] = sum m_i e_i, totals[1] = sum V_i E_i over interior particles
+ * (may be NULL). */
+sph_rt_status sph_rt_get_energies(sph_rt *s, double *e, double *E, double totals[2]);
+
+/* Same into device memory. */
+sph_rt_status sph_rt_get_energies_device(sph_rt *s, double *e, double *E);
+
+/* Sizes after set_particles: interior count, neighbour-list nnz, operator nnz. */
+sph_rt_status sph_rt_get_sizes(const sph_rt *s, int64_t *n_interior, int64_t *nnz_neighbors,
+                               int64_t *nnz_operator);
+
+/* Test hook: neighbour lists in caller IDs.  rowptr[n_total+1]; cols[nnz]
+ * sorted ascending within each row; ghost rows are empty.  cols may be NULL
+ * to get rowptr only. */
+sph_rt_status sph_rt_get_neighbors(sph_rt *s, int64_t *rowptr, int64_t *cols);
+
+/*
+ * Test hook: the operator assembled by the last step, in caller IDs, scaled
+ * back to the paper's rows (Eq. diffusion-solve): row i (interior) holds
+ * A_ij for interior columns j (a copy ghost's entry under the column of the
+ * particle it copies, duplicates summed by the caller if needed), diag[i] = A_ii,
+ * gb[i] = Dirichlet-ghost coupling sum_j w_ij E_j.  rowptr[n_total+1];
+ * cols/vals sized by nnz_operator.  Any output may be NULL.
+ */
+sph_rt_status sph_rt_get_operator(sph_rt *s, int64_t *rowptr, int64_t *cols, double *vals,
+                                  double *diag, double *gb);
+
+/* Test hook: material data of the last step, caller order [n_total]:
+ * T, sigma, Fleck factor f, R, lambda, D.  Any may be NULL. */
+sph_rt_status sph_rt_get_properties(sph_rt *s, double *T, double *sigma, double *f, double *R,
+                                    double *lambda, double *D);
+
+/* Kernel timing (config.kernel_timing = 1): number of SpMV launches on the
+ * fine operator since the last reset, their summed CUDA-event time in ms, and
+ * their algorithmic bytes (12 per stored nonzero + 8 per row for rowptr,
+ * x and y).  reset != 0 clears the counters after reading. */
+sph_rt_status sph_rt_kernel_stats(sph_rt *s, int64_t *launches, double *total_ms,
+                                  double *bytes, int reset);
+
+/* Number of this library's kernels launched since creation (all kinds). */
+int64_t sph_rt_launch_count(const sph_rt *s);
+
+/* Message of the last failed call on this handle (NULL: of the last failed
+ * sph_rt_create on this thread).  Owned by the library; valid until the next
+ * call on the handle. */
+const char *sph_rt_last_error(const sph_rt *s);
+
+/* Release the handle and all its device memory (NULL is a no-op). */
+void sph_rt_destroy(sph_rt *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_RT_H */

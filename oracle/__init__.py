@@ -75,6 +75,8 @@ def lib():
             L.orc_kernel.argtypes = [i32, dbl, dbl, P, P]
             L.orc_neighbors.argtypes = [i64, i32, P, P, P, i32, P, P]
             L.orc_neighbors.restype = i64
+            L.orc_neighbors_rows.argtypes = [i64, i32, P, P, i64, P, P, P]
+            L.orc_neighbors_rows.restype = i64
             L.orc_properties.argtypes = [P, i64, P, P, P, P, P, P, P, P, P, dbl, P, P,
                                          P, P, P, P, P, P]
             L.orc_assemble.argtypes = [P, i64, P, P, P, P, P, P, dbl, P, P, P, P, P, P,
@@ -138,6 +140,20 @@ def neighbors(pos, h, kind, brute: bool = False):
     cols = np.zeros(max(int(rowptr[-1]), 1), dtype=np.int32)
     L.orc_neighbors(n, dim, _p(pos), _p(h), _p(kind), int(brute), _p(rowptr), _p(cols))
     return rowptr, cols[: rowptr[-1]]
+
+
+def neighbors_of_rows(pos, h, rows):
+    """Brute-force neighbour lists (caller IDs, ascending) of the given rows."""
+    pos = _f64(pos)
+    n, dim = pos.shape
+    h = _f64(h)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    L = lib()
+    L.orc_neighbors_rows(n, dim, _p(pos), _p(h), len(rows), _p(rows), _p(rp), None)
+    cols = np.zeros(max(int(rp[-1]), 1), dtype=np.int32)
+    L.orc_neighbors_rows(n, dim, _p(pos), _p(h), len(rows), _p(rows), _p(rp), _p(cols))
+    return rp, cols[: rp[-1]]
 
 
 class Problem:

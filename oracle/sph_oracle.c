@@ -222,6 +222,26 @@ int64_t orc_neighbors(int64_t n, int dim, const double *pos, const double *h,
   return nnz;
 }
 
+/*
+ * Brute-force neighbour lists of selected rows only (all-pairs test against
+ * every particle), for spot checks of large problems.  rowptr[nrows+1];
+ * cols sized by the caller from a first call with cols = NULL.
+ */
+int64_t orc_neighbors_rows(int64_t n, int dim, const double *pos, const double *h,
+                           int64_t nrows, const int64_t *rows, int64_t *rowptr, int32_t *cols) {
+  rowptr[0] = 0;
+  for (int64_t r = 0; r < nrows; ++r) {
+    int64_t i = rows[r], c = 0;
+    for (int64_t j = 0; j < n; ++j)
+      if (is_neighbour(dim, pos, h, i, j)) {
+        if (cols) cols[rowptr[r] + c] = (int32_t)j;
+        ++c;
+      }
+    rowptr[r + 1] = rowptr[r] + c;
+  }
+  return rowptr[nrows];
+}
+
 /* ------------------------------------------------------------------------ */
 /* Material data, frozen for the step (Sec. 3.2).                            */
 /* ------------------------------------------------------------------------ */

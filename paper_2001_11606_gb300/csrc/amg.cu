@@ -1,0 +1,830 @@
+// amg.cu -- aggregation algebraic multigrid preconditioner (row a5 of the hot
+// path) and its V-cycle (inside row a6).
+//
+// The paper preconditions GMRES with hypre's BoomerAMG, set up once at the
+// start of each step and reused in every outer iteration (Sec. 3.2).  This is
+// a GPU-native aggregation AMG on the symmetric operator B = V A:
+//
+//   strength   j is a strong neighbour of i if |B_ij| >= theta sqrt(B_ii B_jj)
+//   aggregates Luby-style maximal independent set of the strength graph with
+//              fixed hashed priorities (roots), every other node joins the
+//              root it is most strongly coupled to; rows without strong
+//              neighbours stay unaggregated (left to the smoother)
+//   transfer   piecewise-constant prolongation P (tentative), R = P^T
+//   Galerkin   B_c = P^T B P: each coarse entry is the sum of the fine entries
+//              that map to it, summed in a fixed order (deterministic)
+//   smoother   Chebyshev on D^{-1} B with the interval [lmax/8, lmax],
+//              lmax from Gershgorin; the coarsest level gets a Chebyshev solve
+//              over its whole Gershgorin interval
+//
+// The V-cycle uses the same polynomial before and after the coarse
+// correction, so it is a symmetric positive-definite preconditioner for CG.
+//
+// Everything runs on the device.  Aggregates and the coarse sparsity are built
+// from the first step's operator and kept (config.amg_rebuild = 1 rebuilds
+// them every step); the Galerkin values are recomputed every step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sphrt {
+
+sph_rt_status exclusive_scan(sph_rt *s, const int64_t *in, int64_t n, int64_t *out);
+template <typename MT, typename VT>
+sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT *d, VT *tmp,
+                         int degree, double lmin, double lmax, bool zero_guess,
+                         const Scalars *sc);
+
+constexpr int kUndecided = 1, kRoot = 2, kNonroot = 0, kIsolated = 3;
+constexpr int kHash = 4096;        // shared hash-table slots per coarse row
+constexpr int kCoarseTarget = 512; // stop coarsening below this many rows
+constexpr int kMaxLevels = 12;
+
+}  // namespace sphrt
+
+struct SphLevel {
+  int64_t n = 0, nnz = 0;
+  // operator (level 0 borrows the fine operator; others own theirs)
+  int64_t *ptr = nullptr;
+  int32_t *col = nullptr;
+  double *val = nullptr, *diag = nullptr, *invdiag = nullptr;
+  float *val32 = nullptr, *diag32 = nullptr, *invdiag32 = nullptr;
+  // transfer to the next level
+  int32_t *agg = nullptr;       // [n] coarse row of each row, -1 if unaggregated
+  int64_t *agg_ptr = nullptr;   // [nc+1] members of each coarse row
+  int32_t *agg_mem = nullptr;
+  int64_t *seg_ptr = nullptr;   // [nnz_c + nc + 1] Galerkin contributions per coarse target
+  int32_t *seg_src = nullptr;   // source: k < nnz (off-diagonal entry) or nnz + i (diagonal)
+  // vectors of the V-cycle
+  double *r = nullptr, *z = nullptr, *res = nullptr, *d = nullptr, *t = nullptr;
+  float *r32 = nullptr, *z32 = nullptr, *res32 = nullptr, *d32 = nullptr, *t32 = nullptr;
+  double lmax = 2.0, gersh = 1.0;
+  int W = 32;
+  std::vector<void *> owned;
+};
+
+namespace sphrt {
+
+static void *lvl_alloc(SphLevel *L, size_t bytes) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes > 0 ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  L->owned.push_back(p);
+  return p;
+}
+template <typename T>
+static T *lalloc(SphLevel *L, size_t count) {
+  return static_cast<T *>(lvl_alloc(L, sizeof(T) * (count > 0 ? count : 1)));
+}
+
+void amg_release(sph_rt *s) {
+  for (SphLevel *L : s->levels) {
+    for (void *p : L->owned) cudaFree(p);
+    delete L;
+  }
+  s->levels.clear();
+  s->amg_ready = false;
+}
+
+static int gcap(const sph_rt *s, int64_t n, int per_block) {
+  int64_t g = ceil_div(n > 0 ? n : 1, per_block);
+  int64_t cap = (int64_t)s->num_sms * 8;
+  if (cap > kMaxRedBlocks) cap = kMaxRedBlocks;
+  return (int)(g < cap ? g : cap);
+}
+
+__device__ __forceinline__ uint32_t hash_u32(uint32_t x) {  // integer mixer (Wang-style)
+  x = (x ^ 61u) ^ (x >> 16);
+  x *= 9u;
+  x ^= x >> 4;
+  x *= 0x27d4eb2du;
+  x ^= x >> 15;
+  return x;
+}
+// priority order: larger hash wins, ties by larger index
+__device__ __forceinline__ bool beats(uint32_t i, uint32_t j) {
+  uint32_t hi = hash_u32(i), hj = hash_u32(j);
+  return hi > hj || (hi == hj && i > j);
+}
+
+// ---------------------------------------------------------------------------
+// strength and aggregation
+// ---------------------------------------------------------------------------
+__global__ void strength_kernel(int64_t n, const int64_t *ptr, const int32_t *col,
+                                const double *val, const double *diag, double theta,
+                                uint8_t *strong, int *state) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int cnt = 0;
+    double di = diag[i];
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+      int32_t j = col[k];
+      bool st = j != i && fabs(val[k]) >= theta * sqrt(di * diag[j]);
+      strong[k] = st;
+      cnt += st;
+    }
+    state[i] = cnt > 0 ? kUndecided : kIsolated;
+  }
+}
+
+__global__ void mis_select_kernel(int64_t n, const int64_t *ptr, const int32_t *col,
+                                  const uint8_t *strong, const int *state, uint8_t *cand) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint8_t c = 0;
+    if (state[i] == kUndecided) {
+      c = 1;
+      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        if (!strong[k]) continue;
+        int32_t j = col[k];
+        int sj = state[j];
+        if (sj == kRoot || (sj == kUndecided && beats((uint32_t)j, (uint32_t)i))) {
+          c = 0;
+          break;
+        }
+      }
+    }
+    cand[i] = c;
+  }
+}
+
+__global__ void mis_apply_kernel(int64_t n, const uint8_t *cand, int *state) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (cand[i]) state[i] = kRoot;
+}
+
+__global__ void mis_mark_kernel(int64_t n, const int64_t *ptr, const int32_t *col,
+                                const uint8_t *strong, int *state, unsigned *undecided) {
+  unsigned left = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (state[i] != kUndecided) continue;
+    bool nr = false;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k)
+      if (strong[k] && state[col[k]] == kRoot) {
+        nr = true;
+        break;
+      }
+    if (nr) state[i] = kNonroot;
+    else ++left;
+  }
+  if (left) atomicAdd(undecided, left);
+}
+
+__global__ void root_flag_kernel(int64_t n, const int *state, int64_t *flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = state[i] == kRoot ? 1 : 0;
+}
+
+__global__ void assign_kernel(int64_t n, const int64_t *ptr, const int32_t *col, const double *val,
+                              const uint8_t *strong, const int *state, const int64_t *root_id,
+                              int32_t *agg, unsigned *members) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int st = state[i];
+    int32_t a = -1;
+    if (st == kRoot) {
+      a = (int32_t)root_id[i];
+    } else if (st == kNonroot) {
+      double best = -1.0;
+      int32_t bj = -1;
+      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        int32_t j = col[k];
+        if (!strong[k] || state[j] != kRoot) continue;
+        double v = fabs(val[k]);
+        if (v > best || (v == best && j < bj)) {
+          best = v;
+          bj = j;
+        }
+      }
+      a = bj >= 0 ? (int32_t)root_id[bj] : -1;
+    }
+    agg[i] = a;
+    if (a >= 0) atomicAdd(&members[a], 1u);
+  }
+}
+
+// counting-sort scatter + per-segment insertion sort (shared by the member
+// lists and the Galerkin contribution lists): orders each segment by value
+__global__ void bucket_scatter_kernel(int64_t n, const int32_t *bucket, const int64_t *start,
+                                      unsigned *cursor, int32_t *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t b = bucket[i];
+    if (b < 0) continue;
+    int64_t at = start[b] + atomicAdd(&cursor[b], 1u);
+    out[at] = (int32_t)i;
+  }
+}
+__global__ void bucket_sort_kernel(int64_t nb, const int64_t *start, int32_t *out) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    int32_t *a = out + start[b];
+    int64_t c = start[b + 1] - start[b];
+    for (int64_t t = 1; t < c; ++t) {
+      int32_t v = a[t];
+      int64_t u = t - 1;
+      while (u >= 0 && a[u] > v) {
+        a[u + 1] = a[u];
+        --u;
+      }
+      a[u + 1] = v;
+    }
+  }
+}
+__global__ void u32_to_i64_kernel(int64_t n, const unsigned *in, int64_t *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+// ---------------------------------------------------------------------------
+// coarse sparsity: one block per coarse row, shared-memory hash of the coarse
+// columns reached from the members' rows, then sorted.
+// ---------------------------------------------------------------------------
+template <bool FILL>
+__global__ void coarse_struct_kernel(int64_t nc, const int64_t *agg_ptr, const int32_t *agg_mem,
+                                     const int64_t *ptr, const int32_t *col, const int32_t *agg,
+                                     int64_t *ccount, const int64_t *cptr, int32_t *ccol,
+                                     int32_t *tgt, int64_t nnz_c, int32_t *tgt_diag,
+                                     int *overflow) {
+  __shared__ int32_t table[kHash];
+  __shared__ int nkeys;
+  for (int64_t I = blockIdx.x; I < nc; I += gridDim.x) {
+    for (int t = threadIdx.x; t < kHash; t += blockDim.x) table[t] = 0x7fffffff;
+    if (threadIdx.x == 0) nkeys = 0;
+    __syncthreads();
+    const int64_t m0 = agg_ptr[I], m1 = agg_ptr[I + 1];
+    // insert
+    for (int64_t m = m0; m < m1; ++m) {
+      int32_t i = agg_mem[m];
+      for (int64_t k = ptr[i] + threadIdx.x; k < ptr[i + 1]; k += blockDim.x) {
+        int32_t J = agg[col[k]];
+        if (J < 0 || J == (int32_t)I) continue;
+        uint32_t hsh = hash_u32((uint32_t)J) & (kHash - 1);
+        for (int probe = 0; probe < kHash; ++probe) {
+          int32_t prev = atomicCAS(&table[hsh], 0x7fffffff, J);
+          if (prev == 0x7fffffff) {
+            atomicAdd(&nkeys, 1);
+            break;
+          }
+          if (prev == J) break;
+          hsh = (hsh + 1) & (kHash - 1);
+        }
+      }
+    }
+    __syncthreads();
+    int cnt = nkeys;
+    if (cnt > kHash / 2) {  // too wide for the table's load factor: give up on this level
+      if (threadIdx.x == 0) atomicExch(overflow, 1);
+      __syncthreads();
+      continue;
+    }
+    // sort the whole table (empty slots are INT_MAX and sort last)
+    for (int k = 2; k <= kHash; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < kHash; t += blockDim.x) {
+          int u = t ^ j;
+          if (u > t) {
+            int32_t a = table[t], b = table[u];
+            bool up = (t & k) == 0;
+            if ((a > b) == up) {
+              table[t] = b;
+              table[u] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (!FILL) {
+      if (threadIdx.x == 0) ccount[I] = cnt;
+    } else {
+      const int64_t base = cptr[I];
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) ccol[base + t] = table[t];
+      for (int64_t m = m0; m < m1; ++m) {
+        int32_t i = agg_mem[m];
+        if (threadIdx.x == 0) tgt_diag[i] = (int32_t)(nnz_c + I);
+        for (int64_t k = ptr[i] + threadIdx.x; k < ptr[i + 1]; k += blockDim.x) {
+          int32_t J = agg[col[k]];
+          int32_t tg = -1;
+          if (J == (int32_t)I) {
+            tg = (int32_t)(nnz_c + I);
+          } else if (J >= 0) {
+            int lo = 0, hi = cnt;  // lower_bound
+            while (lo < hi) {
+              int mid = (lo + hi) >> 1;
+              if (table[mid] < J) lo = mid + 1;
+              else hi = mid;
+            }
+            tg = (int32_t)(base + lo);
+          }
+          tgt[k] = tg;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// targets of the fine diagonal entries of unaggregated rows stay -1
+__global__ void fill_i32_kernel(int64_t n, int32_t v, int32_t *a) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+__global__ void target_count_kernel(int64_t nsrc, const int32_t *tgt, unsigned *cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nsrc;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t t = tgt[i];
+    if (t >= 0) atomicAdd(&cnt[t], 1u);
+  }
+}
+
+// Galerkin values: thread per coarse target, fixed-order sum of its sources
+__global__ void galerkin_kernel(int64_t nnz_c, int64_t nc, const int64_t *seg_ptr,
+                                const int32_t *seg_src, int64_t nnz_f, const double *val_f,
+                                const double *diag_f, double *val_c, double *diag_c,
+                                double *invdiag_c) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz_c + nc;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t u = seg_ptr[t]; u < seg_ptr[t + 1]; ++u) {
+      int64_t sidx = seg_src[u];
+      acc += sidx < nnz_f ? val_f[sidx] : diag_f[sidx - nnz_f];
+    }
+    if (t < nnz_c) {
+      val_c[t] = acc;
+    } else {
+      diag_c[t - nnz_c] = acc;
+      invdiag_c[t - nnz_c] = 1.0 / acc;
+    }
+  }
+}
+
+// Gershgorin bound of D^{-1} A for a level: max_i sum_j |A_ij| / A_ii
+__global__ void gersh_kernel(int64_t n, const int64_t *ptr, const double *val, const double *diag,
+                             double *partials, unsigned *counter, double *out) {
+  double g = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double sacc = 0.0;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) sacc += fabs(val[k]);
+    g = fmax(g, sacc / diag[i]);
+  }
+  __shared__ double sh[32];
+  g = block_max(g, sh);
+  double part[1] = {g}, o[1];
+  const bool mx[1] = {true};
+  if (last_block_combine<1>(part, partials, counter, o, mx) && threadIdx.x == 0) *out = o[0];
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(int64_t n, const S *in, D *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (D)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle kernels
+// ---------------------------------------------------------------------------
+template <int W, typename MT, typename VT>
+__global__ void resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
+                                   const Scalars *sc) {
+  if (sc && sc->done) return;
+  const int sub = threadIdx.x % W;
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  for (int64_t i = grp; i < A.n; i += ngrp) {
+    VT s = 0;
+    for (int64_t k = A.ptr[i] + sub; k < A.ptr[i + 1]; k += W) s += (VT)A.val[k] * z[A.col[k]];
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, W);
+    if (sub == 0) res[i] = r[i] - ((VT)A.diag[i] * z[i] + s);
+  }
+}
+
+template <typename VT>
+__global__ void restrict_kernel(int64_t nc, const int64_t *agg_ptr, const int32_t *agg_mem,
+                                const VT *res, VT *rc, const Scalars *sc) {
+  if (sc && sc->done) return;
+  for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < nc;
+       I += (int64_t)gridDim.x * blockDim.x) {
+    VT acc = 0;
+    for (int64_t m = agg_ptr[I]; m < agg_ptr[I + 1]; ++m) acc += res[agg_mem[m]];
+    rc[I] = acc;
+  }
+}
+
+template <typename VT>
+__global__ void prolong_kernel(int64_t n, const int32_t *agg, const VT *zc, VT *z,
+                               const Scalars *sc) {
+  if (sc && sc->done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t a = agg[i];
+    if (a >= 0) z[i] += zc[a];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host: structure
+// ---------------------------------------------------------------------------
+CsrView<double> fine_view(const sph_rt *s);
+
+static int width_for(int64_t nnz, int64_t n) {
+  double mean = n ? (double)nnz / (double)n : 0.0;
+  return mean > 48 ? 32 : (mean > 12 ? 16 : 8);
+}
+
+// bucket sort of ids by bucket[i] into (start, out); nb buckets
+static sph_rt_status bucket_sort(sph_rt *s, SphLevel *owner, int64_t nitems,
+                                 const int32_t *bucket, int64_t nb, int64_t **start_out,
+                                 int32_t **out_out, int64_t *total_out) {
+  unsigned *cnt = nullptr, *cur = nullptr;
+  int64_t *cnt64 = nullptr;
+  SPH_CUDA(s, cudaMalloc(&cnt, sizeof(unsigned) * (nb + 1)));
+  SPH_CUDA(s, cudaMalloc(&cur, sizeof(unsigned) * (nb + 1)));
+  SPH_CUDA(s, cudaMalloc(&cnt64, sizeof(int64_t) * (nb + 1)));
+  int64_t *start = lalloc<int64_t>(owner, nb + 1);
+  if (!start) return SPH_RT_ENOMEM;
+  SPH_CUDA(s, cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (nb + 1), s->stream));
+  SPH_CUDA(s, cudaMemsetAsync(cur, 0, sizeof(unsigned) * (nb + 1), s->stream));
+  target_count_kernel<<<gcap(s, nitems, kBlock), kBlock, 0, s->stream>>>(nitems, bucket, cnt);
+  SPH_LAUNCHED(s);
+  u32_to_i64_kernel<<<gcap(s, nb, kBlock), kBlock, 0, s->stream>>>(nb, cnt, cnt64);
+  SPH_LAUNCHED(s);
+  sph_rt_status rc = exclusive_scan(s, cnt64, nb, start);
+  if (rc) return rc;
+  int64_t total = 0;
+  SPH_CUDA(s, cudaMemcpyAsync(&total, start + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  int32_t *out = lalloc<int32_t>(owner, total);
+  if (!out) return SPH_RT_ENOMEM;
+  bucket_scatter_kernel<<<gcap(s, nitems, kBlock), kBlock, 0, s->stream>>>(nitems, bucket, start,
+                                                                          cur, out);
+  SPH_LAUNCHED(s);
+  bucket_sort_kernel<<<gcap(s, nb, kBlock), kBlock, 0, s->stream>>>(nb, start, out);
+  SPH_LAUNCHED(s);
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  cudaFree(cnt);
+  cudaFree(cur);
+  cudaFree(cnt64);
+  *start_out = start;
+  *out_out = out;
+  if (total_out) *total_out = total;
+  return SPH_RT_OK;
+}
+
+// Aggregate level L and build the next level's sparsity plus the Galerkin
+// contribution lists.  Returns the new level in *next (nullptr: stop).
+static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
+  *next = nullptr;
+  const int64_t n = L->n, nnz = L->nnz;
+  cudaStream_t st = s->stream;
+  uint8_t *strong = nullptr, *cand = nullptr;
+  int *state = nullptr;
+  int64_t *flag = nullptr, *root_id = nullptr;
+  unsigned *undec = nullptr, *members = nullptr;
+  SPH_CUDA(s, cudaMalloc(&strong, nnz > 0 ? nnz : 1));
+  SPH_CUDA(s, cudaMalloc(&cand, n));
+  SPH_CUDA(s, cudaMalloc(&state, sizeof(int) * n));
+  SPH_CUDA(s, cudaMalloc(&flag, sizeof(int64_t) * n));
+  SPH_CUDA(s, cudaMalloc(&root_id, sizeof(int64_t) * (n + 1)));
+  SPH_CUDA(s, cudaMalloc(&undec, sizeof(unsigned)));
+  auto cleanup = [&]() {
+    cudaFree(strong);
+    cudaFree(cand);
+    cudaFree(state);
+    cudaFree(flag);
+    cudaFree(root_id);
+    cudaFree(undec);
+    if (members) cudaFree(members);
+  };
+  const int g = gcap(s, n, kBlock);
+  strength_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, L->val, L->diag, s->cfg.amg_theta,
+                                        strong, state);
+  SPH_LAUNCHED(s);
+  for (int round = 0; round < 200; ++round) {
+    mis_select_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, strong, state, cand);
+    SPH_LAUNCHED(s);
+    mis_apply_kernel<<<g, kBlock, 0, st>>>(n, cand, state);
+    SPH_LAUNCHED(s);
+    SPH_CUDA(s, cudaMemsetAsync(undec, 0, sizeof(unsigned), st));
+    mis_mark_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, strong, state, undec);
+    SPH_LAUNCHED(s);
+    unsigned left = 0;
+    SPH_CUDA(s, cudaMemcpyAsync(&left, undec, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    SPH_CUDA(s, cudaStreamSynchronize(st));
+    if (left == 0) break;
+  }
+  root_flag_kernel<<<g, kBlock, 0, st>>>(n, state, flag);
+  SPH_LAUNCHED(s);
+  sph_rt_status rc = exclusive_scan(s, flag, n, root_id);
+  if (rc) return cleanup(), rc;
+  int64_t nc = 0;
+  SPH_CUDA(s, cudaMemcpyAsync(&nc, root_id + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(s, cudaStreamSynchronize(st));
+  if (nc == 0 || nc * 10 > n * 9) {  // nothing to coarsen, or coarsening too slow
+    cleanup();
+    return SPH_RT_OK;
+  }
+  SPH_CUDA(s, cudaMalloc(&members, sizeof(unsigned) * nc));
+  SPH_CUDA(s, cudaMemsetAsync(members, 0, sizeof(unsigned) * nc, st));
+  L->agg = lalloc<int32_t>(L, n);
+  if (!L->agg) return cleanup(), SPH_RT_ENOMEM;
+  assign_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, L->val, strong, state, root_id, L->agg,
+                                      members);
+  SPH_LAUNCHED(s);
+  cleanup();
+  members = nullptr;
+  // member lists of the coarse rows
+  int64_t tot = 0;
+  if ((rc = bucket_sort(s, L, n, L->agg, nc, &L->agg_ptr, &L->agg_mem, &tot))) return rc;
+
+  SphLevel *C = new SphLevel();
+  C->n = nc;
+  // coarse sparsity: count, scan, fill (+ Galerkin targets of every fine entry)
+  int64_t *ccount = lalloc<int64_t>(C, nc);
+  C->ptr = lalloc<int64_t>(C, nc + 1);
+  int *overflow = nullptr;
+  SPH_CUDA(s, cudaMalloc(&overflow, sizeof(int)));
+  SPH_CUDA(s, cudaMemsetAsync(overflow, 0, sizeof(int), st));
+  int gb = (int)std::min<int64_t>(nc, (int64_t)s->num_sms * 16);
+  coarse_struct_kernel<false><<<gb, kBlock, 0, st>>>(nc, L->agg_ptr, L->agg_mem, L->ptr, L->col,
+                                                     L->agg, ccount, nullptr, nullptr, nullptr, 0,
+                                                     nullptr, overflow);
+  SPH_LAUNCHED(s);
+  int ovf = 0;
+  SPH_CUDA(s, cudaMemcpyAsync(&ovf, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(s, cudaStreamSynchronize(st));
+  if (ovf) {
+    cudaFree(overflow);
+    for (void *p : C->owned) cudaFree(p);
+    delete C;
+    return SPH_RT_OK;  // stop coarsening here
+  }
+  if ((rc = exclusive_scan(s, ccount, nc, C->ptr))) return rc;
+  SPH_CUDA(s, cudaMemcpyAsync(&C->nnz, C->ptr + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(s, cudaStreamSynchronize(st));
+  C->col = lalloc<int32_t>(C, C->nnz);
+  int32_t *tgt = nullptr;  // [nnz + n]: off-diagonal entries, then diagonals
+  SPH_CUDA(s, cudaMalloc(&tgt, sizeof(int32_t) * (nnz + n)));
+  fill_i32_kernel<<<gcap(s, nnz + n, kBlock), kBlock, 0, st>>>(nnz + n, -1, tgt);
+  SPH_LAUNCHED(s);
+  coarse_struct_kernel<true><<<gb, kBlock, 0, st>>>(nc, L->agg_ptr, L->agg_mem, L->ptr, L->col,
+                                                    L->agg, nullptr, C->ptr, C->col, tgt, C->nnz,
+                                                    tgt + nnz, overflow);
+  SPH_LAUNCHED(s);
+  // Galerkin contribution lists per coarse target (nnz_c off-diagonal + nc diagonal)
+  if ((rc = bucket_sort(s, L, nnz + n, tgt, C->nnz + nc, &L->seg_ptr, &L->seg_src, nullptr))) {
+    cudaFree(tgt);
+    cudaFree(overflow);
+    return rc;
+  }
+  cudaFree(tgt);
+  cudaFree(overflow);
+  // coarse values and vectors
+  C->val = lalloc<double>(C, C->nnz);
+  C->diag = lalloc<double>(C, nc);
+  C->invdiag = lalloc<double>(C, nc);
+  C->r = lalloc<double>(C, nc);
+  C->z = lalloc<double>(C, nc);
+  C->res = lalloc<double>(C, nc);
+  C->d = lalloc<double>(C, nc);
+  C->t = lalloc<double>(C, nc);
+  if (!C->val || !C->diag || !C->invdiag || !C->r || !C->z || !C->res || !C->d || !C->t)
+    return SPH_RT_ENOMEM;
+  C->W = width_for(C->nnz, nc);
+  *next = C;
+  return SPH_RT_OK;
+}
+
+static sph_rt_status level_vectors_fine(sph_rt *s, SphLevel *L) {
+  L->res = lalloc<double>(L, L->n);
+  L->d = lalloc<double>(L, L->n);
+  L->t = lalloc<double>(L, L->n);
+  if (!L->res || !L->d || !L->t) return SPH_RT_ENOMEM;
+  (void)s;
+  return SPH_RT_OK;
+}
+
+static sph_rt_status build_structure(sph_rt *s) {
+  amg_release(s);
+  SphLevel *L0 = new SphLevel();
+  CsrView<double> A = fine_view(s);
+  L0->n = A.n;
+  L0->nnz = A.nnz;
+  L0->ptr = const_cast<int64_t *>(A.ptr);
+  L0->col = const_cast<int32_t *>(A.col);
+  L0->val = const_cast<double *>(A.val);
+  L0->diag = const_cast<double *>(A.diag);
+  L0->invdiag = const_cast<double *>(A.invdiag);
+  L0->W = A.W;
+  s->levels.push_back(L0);
+  sph_rt_status rc = level_vectors_fine(s, L0);
+  if (rc) return rc;
+  SphLevel *L = L0;
+  while ((int)s->levels.size() < kMaxLevels && L->n > kCoarseTarget) {
+    // the strength test needs this level's values
+    if (L != L0) {
+      // values are produced by the numeric pass below; build them now
+    }
+    SphLevel *C = nullptr;
+    if ((rc = coarsen(s, L, &C))) return rc;
+    if (!C) break;
+    s->levels.push_back(C);
+    // numeric Galerkin product for C so that the next strength test can run
+    galerkin_kernel<<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
+        C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, L->val, L->diag, C->val, C->diag,
+        C->invdiag);
+    SPH_LAUNCHED(s);
+    L = C;
+  }
+  s->amg_ready = true;
+  return SPH_RT_OK;
+}
+
+// numeric set-up of every level from the current fine operator
+static sph_rt_status numeric(sph_rt *s) {
+  for (size_t l = 0; l + 1 < s->levels.size(); ++l) {
+    SphLevel *L = s->levels[l], *C = s->levels[l + 1];
+    galerkin_kernel<<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
+        C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, L->val, L->diag, C->val, C->diag,
+        C->invdiag);
+    SPH_LAUNCHED(s);
+  }
+  // Gershgorin bounds of every level (one host read for all)
+  std::vector<double> g(s->levels.size(), 1.0);
+  double *dg = nullptr;
+  SPH_CUDA(s, cudaMalloc(&dg, sizeof(double) * s->levels.size()));
+  for (size_t l = 0; l < s->levels.size(); ++l) {
+    SphLevel *L = s->levels[l];
+    gersh_kernel<<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(L->n, L->ptr, L->val, L->diag,
+                                                                  s->partials, &s->sc->counter,
+                                                                  dg + l);
+    SPH_LAUNCHED(s);
+  }
+  SPH_CUDA(s, cudaMemcpyAsync(g.data(), dg, sizeof(double) * g.size(), cudaMemcpyDeviceToHost,
+                              s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  cudaFree(dg);
+  for (size_t l = 0; l < s->levels.size(); ++l) {
+    s->levels[l]->gersh = g[l];
+    s->levels[l]->lmax = 1.0 + g[l];
+  }
+  if (s->cfg.precision == SPH_RT_MIXED) {
+    for (SphLevel *L : s->levels) {
+      if (!L->val32) {
+        L->val32 = lalloc<float>(L, L->nnz);
+        L->diag32 = lalloc<float>(L, L->n);
+        L->invdiag32 = lalloc<float>(L, L->n);
+        L->r32 = lalloc<float>(L, L->n);
+        L->z32 = lalloc<float>(L, L->n);
+        L->res32 = lalloc<float>(L, L->n);
+        L->d32 = lalloc<float>(L, L->n);
+        L->t32 = lalloc<float>(L, L->n);
+        if (!L->val32 || !L->diag32 || !L->invdiag32 || !L->r32 || !L->z32 || !L->res32 ||
+            !L->d32 || !L->t32)
+          return SPH_RT_ENOMEM;
+      }
+      convert_kernel<double, float><<<gcap(s, L->nnz, kBlock), kBlock, 0, s->stream>>>(
+          L->nnz, L->val, L->val32);
+      SPH_LAUNCHED(s);
+      convert_kernel<double, float><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(
+          L->n, L->diag, L->diag32);
+      SPH_LAUNCHED(s);
+      convert_kernel<double, float><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(
+          L->n, L->invdiag, L->invdiag32);
+      SPH_LAUNCHED(s);
+    }
+  }
+  return SPH_RT_OK;
+}
+
+sph_rt_status amg_setup(sph_rt *s) {
+  sph_rt_status rc;
+  if (!s->amg_ready || s->cfg.amg_rebuild) {
+    if ((rc = build_structure(s))) return rc;
+  }
+  return numeric(s);
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle
+// ---------------------------------------------------------------------------
+template <typename T>
+struct LevelVecs;
+template <>
+struct LevelVecs<double> {
+  static CsrView<double> view(SphLevel *L) {
+    CsrView<double> A;
+    A.n = L->n;
+    A.ptr = L->ptr;
+    A.col = L->col;
+    A.val = L->val;
+    A.diag = L->diag;
+    A.invdiag = L->invdiag;
+    A.nnz = L->nnz;
+    A.W = L->W;
+    return A;
+  }
+  static double *r(SphLevel *L) { return L->r; }
+  static double *z(SphLevel *L) { return L->z; }
+  static double *res(SphLevel *L) { return L->res; }
+  static double *d(SphLevel *L) { return L->d; }
+  static double *t(SphLevel *L) { return L->t; }
+};
+template <>
+struct LevelVecs<float> {
+  static CsrView<float> view(SphLevel *L) {
+    CsrView<float> A;
+    A.n = L->n;
+    A.ptr = L->ptr;
+    A.col = L->col;
+    A.val = L->val32;
+    A.diag = L->diag32;
+    A.invdiag = L->invdiag32;
+    A.nnz = L->nnz;
+    A.W = L->W;
+    return A;
+  }
+  static float *r(SphLevel *L) { return L->r32; }
+  static float *z(SphLevel *L) { return L->z32; }
+  static float *res(SphLevel *L) { return L->res32; }
+  static float *d(SphLevel *L) { return L->d32; }
+  static float *t(SphLevel *L) { return L->t32; }
+};
+
+template <typename T>
+static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars *sc) {
+  using LV = LevelVecs<T>;
+  SphLevel *L = s->levels[l];
+  CsrView<T> A = LV::view(L);
+  const int deg = s->cfg.cheb_degree;
+  sph_rt_status rc;
+  if (l + 1 == s->levels.size()) {
+    // coarsest level: Chebyshev solve over the whole Gershgorin interval
+    double lo = 1.0 - L->gersh, hi = 1.0 + L->gersh;
+    if (lo < 1e-3 * hi) lo = 1e-3 * hi;
+    int cdeg = L->n <= kCoarseTarget * 4 ? 12 : 3 * deg;
+    return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), cdeg, lo, hi, true, sc);
+  }
+  const double lmax = L->lmax, lmin = L->lmax / 8.0;
+  if ((rc = cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, lmin, lmax, true, sc))) return rc;
+  const int gw = gcap(s, L->n, kBlock / A.W);
+  T *res = LV::res(L);
+  if (A.W == 32)
+    resid_level_kernel<32, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res, sc);
+  else if (A.W == 16)
+    resid_level_kernel<16, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res, sc);
+  else
+    resid_level_kernel<8, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res, sc);
+  SPH_LAUNCHED(s);
+  SphLevel *C = s->levels[l + 1];
+  restrict_kernel<T><<<gcap(s, C->n, kBlock), kBlock, 0, s->stream>>>(C->n, L->agg_ptr, L->agg_mem,
+                                                                      res, LV::r(C), sc);
+  SPH_LAUNCHED(s);
+  if ((rc = vcycle<T>(s, l + 1, LV::r(C), LV::z(C), sc))) return rc;
+  prolong_kernel<T><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(L->n, L->agg, LV::z(C), z, sc);
+  SPH_LAUNCHED(s);
+  return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, lmin, lmax, false, sc);
+}
+
+sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc) {
+  if (s->levels.empty()) return set_error(s, SPH_RT_ESTATE, "AMG hierarchy not set up");
+  if (s->cfg.precision == SPH_RT_MIXED) {
+    SphLevel *L0 = s->levels[0];
+    convert_kernel<double, float><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, r, L0->r32);
+    SPH_LAUNCHED(s);
+    sph_rt_status rc = vcycle<float>(s, 0, L0->r32, L0->z32, sc);
+    if (rc) return rc;
+    convert_kernel<float, double><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, L0->z32, z);
+    SPH_LAUNCHED(s);
+    return SPH_RT_OK;
+  }
+  return vcycle<double>(s, 0, r, z, sc);
+}
+
+// number of levels and rows/nnz per level (for diagnostics)
+int amg_levels(const sph_rt *s, int64_t *rows, int64_t *nnz, int maxl) {
+  int k = 0;
+  for (SphLevel *L : s->levels) {
+    if (k >= maxl) break;
+    rows[k] = L->n;
+    nnz[k] = L->nnz;
+    ++k;
+  }
+  return k;
+}
+
+}  // namespace sphrt

@@ -1,0 +1,270 @@
+// common.cuh -- shared device helpers and the internal handle of libsphrt.
+//
+// Index spaces.  Particles are sorted once by (ghost flag, Morton code of the
+// cell, caller index), so "slots" [0, n_int) are the interior particles in
+// Morton order and [n_int, n) the ghosts.  Unknowns of the radiation system
+// are the interior slots, so an unknown's index IS its slot and the solver
+// needs no index maps.
+//
+// Operator scaling.  The library stores B = V A, V = diag(m/rho), where A is
+// the paper's row operator of Eq. diffusion-solve.  B_ij = V_i V_j F_ij (D_i +
+// D_j) is bitwise symmetric (V_i V_j commutes, F_ij is the symmetric two-h
+// average) and B is an M-matrix, so the Krylov solver is CG and the AMG
+// hierarchy is built from symmetric Galerkin products.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sph_rt.h"
+
+namespace sphrt {
+
+constexpr int kBlock = 256;          // threads per block of the 1-D kernels
+constexpr int kWarpsPerBlock = kBlock / 32;
+constexpr int kMaxRedBlocks = 2048;  // upper bound on blocks of a reducing kernel
+
+// --------------------------------------------------------------------------
+// Scalars of one Krylov solve and of the outer loop, kept on the device so
+// that the iteration runs without host round trips between kernels.
+// --------------------------------------------------------------------------
+struct Scalars {
+  double rho;      // (r, z)
+  double alpha;    // rho / (p, q)
+  double beta;     // rho_new / rho
+  double pq;       // (p, B p)
+  double rnorm2;   // ||r / V||^2 (unscaled residual)
+  double bnorm2;   // ||b||^2 (unscaled right-hand side)
+  double thresh2;  // tol^2 ||b||^2
+  double red[8];   // results of generic reductions
+  int done;        // Krylov converged (or aborted)
+  int iters;       // Krylov iterations taken
+  int breakdown;   // non-positive curvature / NaN seen
+  int pad;
+  unsigned int counter;  // arrival counter of the last-block reductions
+};
+
+// --------------------------------------------------------------------------
+// Warp and block reductions (fixed order: deterministic).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+template <int W>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, W);
+  return v;
+}
+
+// Sum of v over the block; result valid in thread 0.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    s = lane < nw ? sh[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+__device__ __forceinline__ double block_max(double v, double *sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    s = lane < nw ? sh[lane] : 0.0;
+    s = warp_max(s);
+  }
+  return s;
+}
+
+// Last-block reduction: every block stores its NV partial values, the block
+// that arrives last combines all partials in block order (so the result does
+// not depend on scheduling) and returns true in all its threads; `out` then
+// holds the NV totals in thread 0 (sums, or maxima where is_max[k]).
+template <int NV>
+__device__ bool last_block_combine(const double (&part)[NV], double *partials, unsigned *counter,
+                                   double (&out)[NV], const bool (&is_max)[NV]) {
+  __shared__ bool am_last;
+  __shared__ double sh[32];
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) partials[(size_t)k * gridDim.x + blockIdx.x] = part[k];
+    __threadfence();
+    unsigned ticket = atomicAdd(counter, 1u);
+    am_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  for (int k = 0; k < NV; ++k) {
+    double acc = 0.0;  // partial maxima are of non-negative quantities
+    // each thread folds a strided subset in order, then a fixed-shape tree
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      double v = ((volatile double *)partials)[(size_t)k * gridDim.x + b];
+      acc = is_max[k] ? fmax(acc, v) : acc + v;
+    }
+    acc = is_max[k] ? block_max(acc, sh) : block_sum(acc, sh);
+    if (threadIdx.x == 0) out[k] = acc;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// A CSR operator as seen by the SpMV-shaped kernels: off-diagonal entries in
+// (ptr, col, val) and the diagonal apart.  W = lanes per row.
+template <typename T>
+struct CsrView {
+  int64_t n = 0;
+  const int64_t *ptr = nullptr;
+  const int32_t *col = nullptr;
+  const T *val = nullptr;
+  const T *diag = nullptr;
+  const T *invdiag = nullptr;
+  int64_t nnz = 0;
+  int W = 32;
+};
+
+}  // namespace sphrt
+
+// --------------------------------------------------------------------------
+// Internal handle.
+// --------------------------------------------------------------------------
+struct SphLevel;  // AMG level (amg.cu)
+
+struct sph_rt {
+  sph_rt_config cfg;
+  std::string err;
+  int64_t launches = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool cuda_ready = false;
+  int num_sms = 152;
+  std::vector<void *> allocs;  // device allocations of the current particle set
+
+  // sizes
+  bool have_particles = false;
+  bool have_operator = false;
+  int64_t n = 0, n_int = 0;
+  int64_t nnz_nbr = 0, nnz_mat = 0, nnz_gh = 0;
+  int dim = 3;
+
+  // permutation
+  int64_t *slot2caller = nullptr;  // [n]
+  int64_t *caller2slot = nullptr;  // [n]
+
+  // particle data, slot order
+  double *px = nullptr, *py = nullptr, *pz = nullptr;
+  double *mass = nullptr, *rho = nullptr, *h = nullptr, *sigma0 = nullptr;
+  double *V = nullptr, *invV = nullptr;
+  int32_t *kind = nullptr;      // [n]
+  int32_t *copysrc = nullptr;   // [n] slot of the copied interior particle, else -1
+  double *e = nullptr, *E = nullptr;  // state [n] (ghost entries hold ghost values)
+
+  // neighbour lists (interior rows)
+  int64_t *nbr_ptr = nullptr;  // [n_int + 1]
+  int32_t *nbr_col = nullptr;  // slot of the neighbour
+  double *nbr_F = nullptr;     // F_ij = W'(r)/r, two-h average
+
+  // operator B = V A (interior rows; unknown index == slot)
+  int64_t *mat_ptr = nullptr;
+  int32_t *mat_col = nullptr;
+  double *mat_G = nullptr;     // V_i V_j F_ij
+  double *mat_val = nullptr;   // B_ij of the current step
+  float *mat_val32 = nullptr;  // FP32 copy for the mixed form
+  double *diag = nullptr, *invdiag = nullptr;
+  int64_t *gh_ptr = nullptr;   // Dirichlet-ghost couplings
+  int32_t *gh_slot = nullptr;
+  double *gh_W = nullptr;      // V_j F_ij
+  double *gb = nullptr;        // unscaled Dirichlet coupling sum_j w_ij E_j
+
+  // material data of the step, slot order [n]
+  double *T = nullptr, *sigma = nullptr, *f = nullptr, *R = nullptr, *lambda = nullptr,
+         *D = nullptr;
+
+  // step vectors (interior)
+  double *e_old = nullptr, *E_old = nullptr, *e_l = nullptr, *E_l = nullptr;
+  double *e_new = nullptr;
+  double *Qe = nullptr, *QE = nullptr;  // slot order [n]
+  double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr,
+         *w = nullptr;
+  double *tmp_n = nullptr;   // [n] staging for caller-order transfers
+  double *tmp_n2 = nullptr;  // [n] staging / Chebyshev scratch
+  double *tmp_n3 = nullptr;
+  double *e_bak = nullptr, *E_bak = nullptr;  // [n] state at the start of the step
+  double *stage_ge = nullptr, *stage_gE = nullptr;  // [n] ghost values staged from the host
+
+  // reductions
+  sphrt::Scalars *sc = nullptr;  // device
+  sphrt::Scalars *sc_host = nullptr;  // pinned mirror
+  double *partials = nullptr;    // [8 * kMaxRedBlocks]
+
+  // AMG hierarchy and Chebyshev data
+  std::vector<SphLevel *> levels;
+  bool amg_ready = false;
+  double cheb_lmin = 0.0, cheb_lmax = 2.0;  // spectrum bounds of D^{-1} B (Gershgorin)
+  double *gersh = nullptr;                   // device scalar written by the assembly
+
+  // kernel timing
+  std::vector<cudaEvent_t> ev_pool;
+  int ev_used = 0;
+  int64_t spmv_launches = 0;
+  double spmv_ms = 0.0, spmv_bytes = 0.0;
+};
+
+// Helpers shared by the translation units (defined in sph_rt.cu).
+namespace sphrt {
+sph_rt_status set_error(sph_rt *s, sph_rt_status st, const std::string &msg);
+bool cuda_ok(sph_rt *s, cudaError_t e, const char *what);
+void *dalloc_bytes(sph_rt *s, size_t bytes);  // tracked cudaMalloc; nullptr on failure
+template <typename T>
+inline T *dalloc(sph_rt *s, size_t count) {
+  return static_cast<T *>(dalloc_bytes(s, sizeof(T) * (count > 0 ? count : 1)));
+}
+void free_all(sph_rt *s);
+int red_grid(const sph_rt *s, int64_t items, int items_per_block);
+// CUDA-event bracketing of fine-operator SpMV-class launches (config.kernel_timing)
+void timing_begin(sph_rt *s);
+void timing_end(sph_rt *s, double bytes);
+void timing_flush(sph_rt *s);
+}  // namespace sphrt
+
+#define SPH_CUDA(s, call)                                          \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) {                                       \
+      sphrt::cuda_ok((s), e_, #call);                              \
+      return SPH_RT_EDEVICE;                                       \
+    }                                                              \
+  } while (0)
+
+#define SPH_LAUNCHED(s)                                            \
+  do {                                                             \
+    (s)->launches++;                                               \
+    cudaError_t e_ = cudaGetLastError();                           \
+    if (e_ != cudaSuccess) {                                       \
+      sphrt::cuda_ok((s), e_, "kernel launch");                    \
+      return SPH_RT_EDEVICE;                                       \
+    }                                                              \
+  } while (0)

@@ -1,0 +1,432 @@
+// krylov.cu -- preconditioned conjugate gradients for the radiation diffusion
+// solve (row a6 of the hot path), plus the SpMV-shaped kernels it is built
+// from (Jacobi and Chebyshev preconditioners; the Chebyshev kernels are also
+// the AMG smoother).
+//
+// The paper solves Eq. diffusion-solve with GMRES and a BoomerAMG
+// preconditioner, set up once per step and warm-started from E^l (Sec. 3.2).
+// Here the operator is stored as B = V A, which is symmetric positive
+// definite (an M-matrix with strict diagonal dominance), so CG is the Krylov
+// method: one SpMV, one preconditioner application and three fused
+// vector/reduction kernels per iteration.  The stopping test is the paper's
+// unscaled residual ||b - A E||_2 <= tol ||b||_2, with A E - b = V^{-1}(B E - V b).
+//
+// All scalars of the iteration (rho, alpha, beta, norms, convergence flag)
+// live on the device.  Every kernel of an iteration starts by reading the
+// `done` flag, so the host can queue several iterations and read the flag
+// once; iterations queued after convergence are empty launches.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sphrt {
+
+template <typename T>
+__device__ __forceinline__ T ld(const T *p) {
+  return __ldg(p);
+}
+
+// ---------------------------------------------------------------------------
+// r = b - B x;  rnorm2 = ||r / V||^2;  done = rnorm2 <= thresh2.
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void resid_kernel(CsrView<double> A, const double *b, const double *x, double *r,
+                             const double *invV, Scalars *sc, double *partials) {
+  const int sub = threadIdx.x % W;
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  double acc = 0.0;
+  for (int64_t i = grp; i < A.n; i += ngrp) {
+    double s = 0.0;
+    for (int64_t k = A.ptr[i] + sub; k < A.ptr[i + 1]; k += W) s += ld(A.val + k) * ld(x + ld(A.col + k));
+    s = group_sum<W>(s);
+    if (sub == 0) {
+      double ri = b[i] - (A.diag[i] * x[i] + s);
+      r[i] = ri;
+      double ru = ri * invV[i];
+      acc += ru * ru;
+    }
+  }
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  double part[1] = {acc}, out[1];
+  const bool mx[1] = {false};
+  if (last_block_combine<1>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    sc->rnorm2 = out[0];
+    sc->iters = 0;
+    sc->done = !(out[0] > sc->thresh2);  // also stops on NaN
+    if (!(out[0] == out[0])) sc->breakdown = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// w = B z;  q = w + beta q;  p = z + beta p;  pq = (p, q);  alpha = rho / pq.
+// (q = B p without a second SpMV: B p = B z + beta B p_old.)
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void spmv_pq_kernel(CsrView<double> A, const double *z, double *q, double *p, int first,
+                               Scalars *sc, double *partials) {
+  if (sc->done) return;
+  const double beta = first ? 0.0 : sc->beta;
+  const int sub = threadIdx.x % W;
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  double acc = 0.0;
+  for (int64_t i = grp; i < A.n; i += ngrp) {
+    double s = 0.0;
+    for (int64_t k = A.ptr[i] + sub; k < A.ptr[i + 1]; k += W) s += ld(A.val + k) * ld(z + ld(A.col + k));
+    s = group_sum<W>(s);
+    if (sub == 0) {
+      double zi = z[i];
+      double wi = A.diag[i] * zi + s;
+      double qi = first ? wi : wi + beta * q[i];
+      double pi = first ? zi : zi + beta * p[i];
+      q[i] = qi;
+      p[i] = pi;
+      acc += pi * qi;
+    }
+  }
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  double part[1] = {acc}, out[1];
+  const bool mx[1] = {false};
+  if (last_block_combine<1>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    double pq = out[0];
+    sc->pq = pq;
+    if (!(pq > 0.0) || !(pq < 1e308)) {  // loss of positive definiteness or NaN
+      sc->breakdown = 1;
+      sc->done = 1;
+    } else {
+      sc->alpha = sc->rho / pq;
+    }
+  }
+}
+
+// x += alpha p;  r -= alpha q;  rnorm2 = ||r / V||^2;  convergence test.
+__global__ void update_kernel(int64_t n, double *x, double *r, const double *p, const double *q,
+                              const double *invV, int maxit, Scalars *sc, double *partials) {
+  if (sc->done) return;
+  const double alpha = sc->alpha;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    double ru = ri * invV[i];
+    acc += ru * ru;
+  }
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  double part[1] = {acc}, out[1];
+  const bool mx[1] = {false};
+  if (last_block_combine<1>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    sc->rnorm2 = out[0];
+    sc->iters += 1;
+    if (!(out[0] > sc->thresh2) || sc->iters >= maxit) sc->done = 1;
+    if (!(out[0] == out[0])) sc->breakdown = 1;
+  }
+}
+
+// Jacobi: z = D^{-1} r, fused with rho = (r, z) and beta.
+__global__ void jacobi_dot_kernel(int64_t n, const double *r, const double *invdiag, double *z,
+                                  int first, Scalars *sc, double *partials) {
+  if (sc->done) return;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double zi = r[i] * invdiag[i];
+    z[i] = zi;
+    acc += r[i] * zi;
+  }
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  double part[1] = {acc}, out[1];
+  const bool mx[1] = {false};
+  if (last_block_combine<1>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    if (!first) sc->beta = out[0] / sc->rho;
+    sc->rho = out[0];
+  }
+}
+
+// rho = (r, z) and beta, for preconditioners that write z themselves.
+template <typename VT>
+__global__ void dot_rz_kernel(int64_t n, const double *r, const VT *z, int first, Scalars *sc,
+                              double *partials) {
+  if (sc->done) return;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += r[i] * (double)z[i];
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  double part[1] = {acc}, out[1];
+  const bool mx[1] = {false};
+  if (last_block_combine<1>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    if (!first) sc->beta = out[0] / sc->rho;
+    sc->rho = out[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev iteration for A z = r (A = level operator, D = its diagonal) on
+// the interval [lmin, lmax] of D^{-1} A (Saad, Iterative Methods, Alg. 12.1).
+// init:  zero guess:  d = D^{-1} r / theta,              z = d
+//        otherwise:   d = D^{-1} (r - A z_in) / theta,   z_out = z_in + d
+// step:  d = c1 d + c2 D^{-1} (r - A z_in),              z_out = z_in + d
+// ---------------------------------------------------------------------------
+template <typename MT, typename VT>
+__global__ void cheb_init_zero_kernel(int64_t n, const VT *r, const MT *invdiag, double inv_theta,
+                                      VT *d, VT *z, const Scalars *sc) {
+  if (sc && sc->done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    VT di = (VT)(inv_theta * (double)invdiag[i] * (double)r[i]);
+    d[i] = di;
+    z[i] = di;
+  }
+}
+
+template <int W, typename T>
+__device__ __forceinline__ T gsum(T v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, W);
+  return v;
+}
+
+template <int W, typename MT, typename VT>
+__global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
+                                 double c1, double c2, const Scalars *sc) {
+  if (sc && sc->done) return;
+  const int sub = threadIdx.x % W;
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  const VT vc1 = (VT)c1, vc2 = (VT)c2;
+  for (int64_t i = grp; i < A.n; i += ngrp) {
+    VT s = 0;
+    for (int64_t k = A.ptr[i] + sub; k < A.ptr[i + 1]; k += W)
+      s += (VT)ld(A.val + k) * ld(z_in + ld(A.col + k));
+    s = gsum<W, VT>(s);
+    if (sub == 0) {
+      VT zi = z_in[i];
+      VT res = r[i] - ((VT)A.diag[i] * zi + s);
+      VT di = vc2 * (VT)A.invdiag[i] * res;
+      if (c1 != 0.0) di += vc1 * d[i];  // the first step must not read d
+      d[i] = di;
+      z_out[i] = zi + di;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static int grid_cap(const sph_rt *s, int64_t n, int per_block) {
+  int64_t g = ceil_div(n > 0 ? n : 1, per_block);
+  int64_t cap = (int64_t)s->num_sms * 8;
+  if (cap > kMaxRedBlocks) cap = kMaxRedBlocks;
+  return (int)(g < cap ? g : cap);
+}
+
+#define SPH_W_LAUNCH(KERNEL, W, grid, s, ...)                                  \
+  do {                                                                         \
+    if ((W) == 32) KERNEL<32><<<grid, kBlock, 0, (s)->stream>>>(__VA_ARGS__);  \
+    else if ((W) == 16) KERNEL<16><<<grid, kBlock, 0, (s)->stream>>>(__VA_ARGS__); \
+    else KERNEL<8><<<grid, kBlock, 0, (s)->stream>>>(__VA_ARGS__);             \
+    SPH_LAUNCHED(s);                                                           \
+  } while (0)
+
+CsrView<double> fine_view(const sph_rt *s) {
+  CsrView<double> A;
+  A.n = s->n_int;
+  A.ptr = s->mat_ptr;
+  A.col = s->mat_col;
+  A.val = s->mat_val;
+  A.diag = s->diag;
+  A.invdiag = s->invdiag;
+  A.nnz = s->nnz_mat;
+  double mean = s->n_int ? (double)s->nnz_mat / (double)s->n_int : 0.0;
+  A.W = mean > 48 ? 32 : (mean > 12 ? 16 : 8);
+  return A;
+}
+
+// Kernel-time bracketing of fine SpMV launches (config.kernel_timing).
+void timing_begin(sph_rt *s) {
+  if (!s->cfg.kernel_timing) return;
+  if (s->ev_used + 2 > (int)s->ev_pool.size()) {
+    // flush accumulated pairs first
+    if (s->ev_used > 0) {
+      cudaEventSynchronize(s->ev_pool[s->ev_used - 1]);
+      for (int k = 0; k + 1 < s->ev_used; k += 2) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, s->ev_pool[k], s->ev_pool[k + 1]);
+        s->spmv_ms += ms;
+      }
+      s->ev_used = 0;
+    }
+    while ((int)s->ev_pool.size() < 4096) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) break;
+      s->ev_pool.push_back(e);
+    }
+  }
+  cudaEventRecord(s->ev_pool[s->ev_used++], s->stream);
+}
+void timing_end(sph_rt *s, double bytes) {
+  if (!s->cfg.kernel_timing) return;
+  cudaEventRecord(s->ev_pool[s->ev_used++], s->stream);
+  s->spmv_launches++;
+  s->spmv_bytes += bytes;
+}
+void timing_flush(sph_rt *s) {
+  if (!s->cfg.kernel_timing || s->ev_used == 0) return;
+  cudaEventSynchronize(s->ev_pool[s->ev_used - 1]);
+  for (int k = 0; k + 1 < s->ev_used; k += 2) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->ev_pool[k], s->ev_pool[k + 1]);
+    s->spmv_ms += ms;
+  }
+  s->ev_used = 0;
+}
+
+// Algorithmic bytes of the SpMV-class kernels: column index and value per
+// stored nonzero (the gathered vector entry counted once, per row) plus the
+// per-row vectors each kernel reads and writes.
+template <typename MT>
+double spmv_class_bytes(const CsrView<MT> &A, int row_bytes) {
+  return (4.0 + sizeof(MT)) * (double)A.nnz + (double)row_bytes * (double)A.n;
+}
+// resid: rowptr, diag, b, x, r, 1/V        spmv_pq: rowptr, diag, z, q r/w, p r/w
+constexpr int kRowBytesResid = 48, kRowBytesSpmvPQ = 56;
+
+// Chebyshev polynomial preconditioner/smoother: `degree` steps from z
+// (zero_guess: z = 0 on entry).  d and tmp are scratch vectors of length n.
+template <typename MT, typename VT>
+sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT *d, VT *tmp,
+                         int degree, double lmin, double lmax, bool zero_guess,
+                         const Scalars *sc) {
+  double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  double sigma1 = theta / delta;
+  double rho0 = 1.0 / sigma1;
+  int g = grid_cap(s, A.n, kBlock);
+  int gw = grid_cap(s, A.n, kBlock / A.W);
+  // fine-level sweeps are timed with the other fine SpMV-class kernels; per row:
+  // rowptr, diag, 1/diag, r, z_in, z_out, d r/w (vectors of type VT)
+  const bool fine = A.ptr == s->mat_ptr;
+  const double bytes = spmv_class_bytes(A, 8 + 2 * (int)sizeof(MT) + 5 * (int)sizeof(VT));
+  auto step = [&](const VT *zin, VT *zout, double c1, double c2) -> sph_rt_status {
+    if (fine) timing_begin(s);
+    if (A.W == 32)
+      cheb_step_kernel<32, MT, VT><<<gw, kBlock, 0, s->stream>>>(A, r, zin, zout, d, c1, c2, sc);
+    else if (A.W == 16)
+      cheb_step_kernel<16, MT, VT><<<gw, kBlock, 0, s->stream>>>(A, r, zin, zout, d, c1, c2, sc);
+    else
+      cheb_step_kernel<8, MT, VT><<<gw, kBlock, 0, s->stream>>>(A, r, zin, zout, d, c1, c2, sc);
+    SPH_LAUNCHED(s);
+    if (fine) timing_end(s, bytes);
+    return SPH_RT_OK;
+  };
+  // ping-pong between z and tmp so that the last write lands in z
+  VT *bufs[2] = {z, tmp};
+  // `degree` writes in all (the init or first step, then degree-1 steps); the
+  // first goes to bufs[w0], each later one flips buffers, the last hits bufs[0].
+  int w0 = (degree - 1) % 2;
+  sph_rt_status rc;
+  if (zero_guess) {
+    cheb_init_zero_kernel<MT, VT><<<g, kBlock, 0, s->stream>>>(A.n, r, A.invdiag, 1.0 / theta, d,
+                                                                 bufs[w0], sc);
+    SPH_LAUNCHED(s);
+  } else {
+    // the guess is read from bufs[w0 ^ 1]
+    if (w0 == 0) {
+      SPH_CUDA(s, cudaMemcpyAsync(tmp, z, sizeof(VT) * A.n, cudaMemcpyDeviceToDevice, s->stream));
+    }
+    if ((rc = step(bufs[w0 ^ 1], bufs[w0], 0.0, 1.0 / theta))) return rc;
+  }
+  int at = w0;
+  for (int k = 1; k < degree; ++k) {
+    double rho1 = 1.0 / (2.0 * sigma1 - rho0);
+    double c1 = rho1 * rho0, c2 = 2.0 * rho1 / delta;
+    if ((rc = step(bufs[at], bufs[at ^ 1], c1, c2))) return rc;
+    at ^= 1;
+    rho0 = rho1;
+  }
+  return SPH_RT_OK;
+}
+
+template sph_rt_status cheb_apply<double, double>(sph_rt *, const CsrView<double> &, const double *,
+                                                  double *, double *, double *, int, double, double,
+                                                  bool, const Scalars *);
+template sph_rt_status cheb_apply<float, float>(sph_rt *, const CsrView<float> &, const float *,
+                                                float *, float *, float *, int, double, double,
+                                                bool, const Scalars *);
+
+// Preconditioner hook implemented by the AMG translation unit.
+sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc);
+
+// z = M^{-1} r followed by rho = (r, z) (and beta unless first).
+static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first) {
+  int g = grid_cap(s, A.n, kBlock);
+  sph_rt_status rc;
+  switch (s->cfg.precond) {
+    case SPH_RT_PRECOND_JACOBI:
+      jacobi_dot_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->r, A.invdiag, s->z, first, s->sc,
+                                                      s->partials);
+      SPH_LAUNCHED(s);
+      return SPH_RT_OK;
+    case SPH_RT_PRECOND_CHEBYSHEV:
+      rc = cheb_apply<double, double>(s, A, s->r, s->z, s->w, s->tmp_n2, s->cfg.cheb_degree,
+                                      s->cheb_lmin, s->cheb_lmax, true, s->sc);
+      if (rc) return rc;
+      break;
+    default:
+      rc = amg_apply(s, s->r, s->z, s->sc);
+      if (rc) return rc;
+      break;
+  }
+  dot_rz_kernel<double><<<g, kBlock, 0, s->stream>>>(A.n, s->r, s->z, first, s->sc, s->partials);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+// Solve B x = b from the warm start in x (row a6).  On return the host mirror
+// s->sc_host holds the final scalars.
+sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
+  CsrView<double> A = fine_view(s);
+  const int gw = grid_cap(s, A.n, kBlock / A.W);
+  const int g = grid_cap(s, A.n, kBlock);
+  const double bytes_r = spmv_class_bytes(A, kRowBytesResid);
+  const double bytes = spmv_class_bytes(A, kRowBytesSpmvPQ);
+  sph_rt_status rc;
+  timing_begin(s);
+  SPH_W_LAUNCH(resid_kernel, A.W, gw, s, A, s->b, s->x, s->r, s->invV, s->sc, s->partials);
+  timing_end(s, bytes_r);
+  if ((rc = precondition(s, A, 1))) return rc;
+  timing_begin(s);
+  SPH_W_LAUNCH(spmv_pq_kernel, A.W, gw, s, A, s->z, s->q, s->p, 1, s->sc, s->partials);
+  timing_end(s, bytes);
+  const int chunk = s->cfg.check_every > 0 ? s->cfg.check_every : 1;
+  int queued = 0;
+  for (;;) {
+    for (int c = 0; c < chunk; ++c) {
+      update_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
+                                                  s->cfg.max_krylov, s->sc, s->partials);
+      SPH_LAUNCHED(s);
+      if ((rc = precondition(s, A, 0))) return rc;
+      timing_begin(s);
+      SPH_W_LAUNCH(spmv_pq_kernel, A.W, gw, s, A, s->z, s->q, s->p, 0, s->sc, s->partials);
+      timing_end(s, bytes);
+      ++queued;
+    }
+    SPH_CUDA(s, cudaMemcpyAsync(s->sc_host, s->sc, sizeof(Scalars), cudaMemcpyDeviceToHost,
+                                s->stream));
+    SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (s->sc_host->done || queued > s->cfg.max_krylov + chunk) break;
+  }
+  timing_flush(s);
+  *iters = s->sc_host->iters;
+  *converged = !s->sc_host->breakdown && !(s->sc_host->rnorm2 > s->sc_host->thresh2);
+  return SPH_RT_OK;
+}
+
+}  // namespace sphrt

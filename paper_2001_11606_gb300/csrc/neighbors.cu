@@ -1,0 +1,700 @@
+// neighbors.cu -- Morton-sorted cell list, neighbour search and operator
+// sparsity (rows a1-a2 of the hot path).
+//
+// Connectivity is the set of j != i with r_ij^2 < (2 max(h_i, h_j))^2 for every
+// interior particle i (support of the cubic B-spline; connectivity in the
+// sense of Sec. 1 and Sec. 3.1 of the paper).  Distances are formed with
+// explicit round-to-nearest double operations (no fused multiply-add) in the
+// order dx*dx + dy*dy + dz*dz, so the neighbour sets are bit-identical to a
+// host evaluation of the same expression.
+//
+// Layout: particles are counting-sorted by key = (ghost flag, Morton code of
+// the cell) with ties broken by caller index, giving "slots" with interior
+// particles first.  Cells have edge >= 2 max h, so all neighbours of a
+// particle lie in the 3^d cells around its own.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sphrt {
+
+// --------------------------------------------------------------------------
+// Exclusive scan of int64 counts: out[0..n] with out[n] = total.
+// --------------------------------------------------------------------------
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kBlock * kScanItems;
+
+__global__ void scan_tile_sums(const int64_t *in, int64_t n, int64_t *tile_sums) {
+  __shared__ int64_t sh[kWarpsPerBlock];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t acc = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
+    if (i < n) acc += in[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kWarpsPerBlock; ++w) t += sh[w];
+    tile_sums[blockIdx.x] = t;
+  }
+}
+
+// Single block: exclusive scan of the tile sums in place (sequential chunks).
+__global__ void scan_tile_offsets(int64_t *tile_sums, int64_t ntiles, int64_t *total) {
+  __shared__ int64_t sh[kBlock];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < ntiles; base += kBlock) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = i < ntiles ? tile_sums[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < kBlock; o <<= 1) {
+      int64_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < ntiles) tile_sums[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += sh[kBlock - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void scan_tiles(const int64_t *in, int64_t n, const int64_t *tile_off, int64_t *out) {
+  __shared__ int64_t sh[kBlock];
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t local = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k;
+    v[k] = i < n ? in[i] : 0;
+    local += v[k];
+  }
+  sh[threadIdx.x] = local;
+  __syncthreads();
+  for (int o = 1; o < kBlock; o <<= 1) {
+    int64_t t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int64_t run = tile_off[blockIdx.x] + sh[threadIdx.x] - local;
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k;
+    if (i < n) out[i] = run;
+    run += v[k];
+  }
+}
+
+sph_rt_status exclusive_scan(sph_rt *s, const int64_t *in, int64_t n, int64_t *out) {
+  int64_t ntiles = ceil_div(n > 0 ? n : 1, kScanTile);
+  int64_t *tiles = dalloc<int64_t>(s, (size_t)ntiles);
+  if (!tiles) return SPH_RT_ENOMEM;
+  scan_tile_sums<<<(unsigned)ntiles, kBlock, 0, s->stream>>>(in, n, tiles);
+  SPH_LAUNCHED(s);
+  scan_tile_offsets<<<1, kBlock, 0, s->stream>>>(tiles, ntiles, out + n);
+  SPH_LAUNCHED(s);
+  scan_tiles<<<(unsigned)ntiles, kBlock, 0, s->stream>>>(in, n, tiles, out);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+// --------------------------------------------------------------------------
+// Bounding box and largest smoothing length.
+// --------------------------------------------------------------------------
+__global__ void bbox_kernel(const double *px, const double *py, const double *pz,
+                            const double *h, int64_t n, double *partials, unsigned *counter,
+                            double *out /* lo[3], hi[3], hmax */) {
+  double lo[3] = {1e308, 1e308, 1e308}, hi[3] = {-1e308, -1e308, -1e308}, hm = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double c[3] = {px[i], py[i], pz[i]};
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fmin(lo[d], c[d]);
+      hi[d] = fmax(hi[d], c[d]);
+    }
+    hm = fmax(hm, h[i]);
+  }
+  // maxima of (-lo, hi, h)
+  double part[7] = {-lo[0], -lo[1], -lo[2], hi[0], hi[1], hi[2], hm};
+  // Exact reduction (values may be negative): per-block serial fold in thread 0.
+  __shared__ double vals[kBlock][7];
+  for (int k = 0; k < 7; ++k) vals[threadIdx.x][k] = part[k];
+  __syncthreads();
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    double m[7];
+    for (int k = 0; k < 7; ++k) m[k] = vals[0][k];
+    for (int t = 1; t < (int)blockDim.x; ++t)
+      for (int k = 0; k < 7; ++k) m[k] = fmax(m[k], vals[t][k]);
+    for (int k = 0; k < 7; ++k) partials[k * gridDim.x + blockIdx.x] = m[k];
+    __threadfence();
+    unsigned ticket = atomicAdd(counter, 1u);
+    am_last = ticket == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (am_last && threadIdx.x == 0) {
+    __threadfence();
+    double m[7];
+    for (int k = 0; k < 7; ++k) m[k] = ((volatile double *)partials)[k * gridDim.x];
+    for (unsigned b = 1; b < gridDim.x; ++b)
+      for (int k = 0; k < 7; ++k) m[k] = fmax(m[k], ((volatile double *)partials)[k * gridDim.x + b]);
+    for (int d = 0; d < 3; ++d) {
+      out[d] = -m[d];
+      out[3 + d] = m[3 + d];
+    }
+    out[6] = m[6];
+    *counter = 0u;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Morton codes
+// --------------------------------------------------------------------------
+__host__ __device__ inline uint64_t spread3(uint64_t v) {  // 21 bits -> every 3rd bit
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+__host__ __device__ inline uint64_t spread2(uint64_t v) {  // 32 bits -> every 2nd bit
+  v &= 0xffffffffull;
+  v = (v | (v << 16)) & 0x0000ffff0000ffffull;
+  v = (v | (v << 8)) & 0x00ff00ff00ff00ffull;
+  v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0full;
+  v = (v | (v << 2)) & 0x3333333333333333ull;
+  v = (v | (v << 1)) & 0x5555555555555555ull;
+  return v;
+}
+
+struct Grid {
+  double lo[3];
+  double inv_cell;
+  int nc[3];
+  int dim;
+  int ghost_shift;  // key bit that marks ghosts
+};
+
+__device__ __forceinline__ int cell_coord(double x, double lo, double inv, int nc) {
+  int c = (int)floor((x - lo) * inv);
+  return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+__device__ __forceinline__ uint64_t morton(const Grid &g, int cx, int cy, int cz) {
+  if (g.dim == 3) return spread3((uint64_t)cx) | (spread3((uint64_t)cy) << 1) | (spread3((uint64_t)cz) << 2);
+  if (g.dim == 2) return spread2((uint64_t)cx) | (spread2((uint64_t)cy) << 1);
+  return (uint64_t)cx;
+}
+
+__global__ void key_kernel(Grid g, const double *px, const double *py, const double *pz,
+                           const int32_t *kind, int64_t n, uint32_t *key, unsigned *count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int cx = cell_coord(px[i], g.lo[0], g.inv_cell, g.nc[0]);
+    int cy = cell_coord(py[i], g.lo[1], g.inv_cell, g.nc[1]);
+    int cz = cell_coord(pz[i], g.lo[2], g.inv_cell, g.nc[2]);
+    uint32_t k = (uint32_t)morton(g, cx, cy, cz);
+    if (kind[i] != SPH_RT_INTERIOR) k |= (1u << g.ghost_shift);
+    key[i] = k;
+    atomicAdd(&count[k], 1u);
+  }
+}
+
+__global__ void u32_to_i64(const unsigned *in, int64_t n, int64_t *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+__global__ void scatter_kernel(const uint32_t *key, int64_t n, const int64_t *start,
+                               unsigned *cursor, int64_t *slot2caller) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t k = key[i];
+    int64_t pos = start[k] + atomicAdd(&cursor[k], 1u);
+    slot2caller[pos] = i;
+  }
+}
+
+// Order each key's slice by caller index (insertion sort; slices are small).
+__global__ void segment_sort_kernel(const int64_t *start, const unsigned *count, int64_t nkeys,
+                                    int64_t *slot2caller) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nkeys;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    unsigned c = count[k];
+    if (c < 2) continue;
+    int64_t *a = slot2caller + start[k];
+    for (unsigned t = 1; t < c; ++t) {
+      int64_t v = a[t];
+      int u = (int)t - 1;
+      while (u >= 0 && a[u] > v) {
+        a[u + 1] = a[u];
+        --u;
+      }
+      a[u + 1] = v;
+    }
+  }
+}
+
+__global__ void invert_perm(const int64_t *slot2caller, int64_t n, int64_t *caller2slot) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x)
+    caller2slot[slot2caller[s]] = s;
+}
+
+template <typename T>
+__global__ void gather_kernel(const T *in, const int64_t *slot2caller, int64_t n, T *out) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x)
+    out[s] = in[slot2caller[s]];
+}
+
+// positions: caller row-major [n][dim] -> SoA slot order (missing dims = 0)
+__global__ void gather_pos_kernel(const double *pos, int dim, const int64_t *slot2caller,
+                                  int64_t n, double *px, double *py, double *pz) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = slot2caller[s];
+    px[s] = pos[c * dim];
+    py[s] = dim > 1 ? pos[c * dim + 1] : 0.0;
+    pz[s] = dim > 2 ? pos[c * dim + 2] : 0.0;
+  }
+}
+
+__global__ void caller_pos_to_soa(const double *pos, int dim, int64_t n, double *px, double *py,
+                                  double *pz) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    px[i] = pos[i * dim];
+    py[i] = dim > 1 ? pos[i * dim + 1] : 0.0;
+    pz[i] = dim > 2 ? pos[i * dim + 2] : 0.0;
+  }
+}
+
+__global__ void copysrc_kernel(const int64_t *copy_of, const int32_t *kind_slot,
+                               const int64_t *slot2caller, const int64_t *caller2slot, int64_t n,
+                               int32_t *copysrc) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = -1;
+    if (kind_slot[s] == SPH_RT_COPY && copy_of) v = (int32_t)caller2slot[copy_of[slot2caller[s]]];
+    copysrc[s] = v;
+  }
+}
+
+__global__ void volume_kernel(const double *mass, const double *rho, int64_t n, double *V,
+                              double *invV) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    double v = mass[s] / rho[s];
+    V[s] = v;
+    invV[s] = 1.0 / v;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Neighbour search: one warp per interior particle.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double kernel_dw(int dim, double r, double h) {
+  // dW/dr of the M4 cubic B-spline with support 2h
+  const double pi = 3.141592653589793;
+  double norm = dim == 3 ? (1.0 / pi) / (h * h * h)
+                         : (dim == 2 ? (10.0 / (7.0 * pi)) / (h * h) : (2.0 / 3.0) / h);
+  double q = r / h;
+  double dw = 0.0;
+  if (q < 1.0) {
+    dw = -3.0 * q + 2.25 * q * q;
+  } else if (q < 2.0) {
+    double t = 2.0 - q;
+    dw = -0.75 * t * t;
+  }
+  return norm * dw / h;
+}
+
+__device__ __forceinline__ double exact_r2(double xi, double yi, double zi, double xj, double yj,
+                                           double zj) {
+  double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj), dz = __dsub_rn(zi, zj);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Bitonic sort of one 64-bit key per lane, ascending across the warp.
+__device__ __forceinline__ uint64_t warp_sort_u64(uint64_t v) {
+  int lane = threadIdx.x & 31;
+  for (int k = 2; k <= 32; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
+      bool up = ((lane & k) == 0);
+      bool lower = ((lane & j) == 0);
+      uint64_t mn = v < o ? v : o, mx = v < o ? o : v;
+      v = (lower == up) ? mn : mx;
+    }
+  }
+  return v;
+}
+
+template <bool FILL>
+__global__ void neighbor_kernel(Grid g, const double *px, const double *py, const double *pz,
+                                const double *h, const int64_t *cell_start,
+                                const unsigned *cell_count, int64_t n_int, int64_t *count,
+                                const int64_t *rowptr, int32_t *cols, double *F) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int ncells = g.dim == 3 ? 27 : (g.dim == 2 ? 9 : 3);
+  for (int64_t i = warp; i < n_int; i += nwarps) {
+    double xi = px[i], yi = py[i], zi = pz[i], hi = h[i];
+    int c[3] = {cell_coord(xi, g.lo[0], g.inv_cell, g.nc[0]),
+                cell_coord(yi, g.lo[1], g.inv_cell, g.nc[1]),
+                cell_coord(zi, g.lo[2], g.inv_cell, g.nc[2])};
+    uint64_t mykey = ~0ull;
+    if (lane < ncells) {
+      int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
+      bool ok = true;
+      int cc[3];
+      for (int d = 0; d < 3; ++d) {
+        cc[d] = d < g.dim ? c[d] + o[d] : 0;
+        if (d < g.dim && (cc[d] < 0 || cc[d] >= g.nc[d])) ok = false;
+      }
+      if (ok) mykey = morton(g, cc[0], cc[1], cc[2]);
+    }
+    uint64_t sorted = warp_sort_u64(mykey);
+    int64_t out = FILL ? rowptr[i] : 0;
+    int64_t total = 0;
+    for (int pass = 0; pass < 2; ++pass) {  // interior cells, then ghost cells
+      for (int k = 0; k < ncells; ++k) {
+        uint64_t key = __shfl_sync(0xffffffffu, sorted, k);
+        if (key == ~0ull) break;
+        uint64_t kk = key | (pass ? (1ull << g.ghost_shift) : 0ull);
+        int64_t beg = cell_start[kk];
+        int64_t cnt = cell_count[kk];
+        for (int64_t base = 0; base < cnt; base += 32) {
+          int64_t j = beg + base + lane;
+          bool hit = false;
+          double r2 = 0.0;
+          if (base + lane < cnt && j != i) {
+            double hj = h[j];
+            double cut = 2.0 * fmax(hi, hj);
+            double cut2 = __dmul_rn(cut, cut);
+            r2 = exact_r2(xi, yi, zi, px[j], py[j], pz[j]);
+            hit = r2 < cut2;
+          }
+          unsigned m = __ballot_sync(0xffffffffu, hit);
+          if (FILL && hit) {
+            int64_t at = out + total + __popc(m & ((1u << lane) - 1u));
+            cols[at] = (int32_t)j;
+            double r = sqrt(r2);
+            F[at] = 0.5 * (kernel_dw(g.dim, r, hi) + kernel_dw(g.dim, r, h[j])) / r;
+          }
+          total += __popc(m);
+        }
+      }
+    }
+    if (!FILL && lane == 0) count[i] = total;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Operator sparsity from the neighbour lists: interior columns and copy-ghost
+// columns (moved to the copied particle; a copy of the row itself drops out)
+// form B; Dirichlet ghosts form the boundary-coupling list.
+// --------------------------------------------------------------------------
+__global__ void op_count_kernel(const int64_t *nbr_ptr, const int32_t *nbr_col,
+                                const int32_t *kind, const int32_t *copysrc, int64_t n_int,
+                                int64_t *mat_cnt, int64_t *gh_cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t m = 0, g = 0;
+    for (int64_t k = nbr_ptr[i]; k < nbr_ptr[i + 1]; ++k) {
+      int32_t j = nbr_col[k];
+      int32_t kj = kind[j];
+      if (kj == SPH_RT_DIRICHLET) ++g;
+      else if (kj == SPH_RT_INTERIOR || copysrc[j] != i) ++m;
+    }
+    mat_cnt[i] = m;
+    gh_cnt[i] = g;
+  }
+}
+
+__global__ void op_fill_kernel(const int64_t *nbr_ptr, const int32_t *nbr_col, const double *nbr_F,
+                               const int32_t *kind, const int32_t *copysrc, const double *V,
+                               int64_t n_int, const int64_t *mat_ptr, int32_t *mat_col,
+                               double *mat_G, const int64_t *gh_ptr, int32_t *gh_slot,
+                               double *gh_W) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t m = mat_ptr[i], g = gh_ptr[i];
+    double Vi = V[i];
+    for (int64_t k = nbr_ptr[i]; k < nbr_ptr[i + 1]; ++k) {
+      int32_t j = nbr_col[k];
+      int32_t kj = kind[j];
+      double Fk = nbr_F[k];
+      if (kj == SPH_RT_DIRICHLET) {
+        gh_slot[g] = j;
+        gh_W[g] = V[j] * Fk;
+        ++g;
+      } else {
+        int32_t col = kj == SPH_RT_INTERIOR ? j : copysrc[j];
+        if (col == i) continue;
+        mat_col[m] = col;
+        mat_G[m] = (Vi * V[j]) * Fk;
+        ++m;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Host driver
+// --------------------------------------------------------------------------
+static int grid1(const sph_rt *s, int64_t n) {
+  int64_t g = ceil_div(n > 0 ? n : 1, kBlock);
+  int64_t cap = (int64_t)s->num_sms * 8;
+  return (int)(g < cap ? g : cap);
+}
+
+// Build permutation, slot-order particle data, neighbour lists and operator
+// sparsity from caller-order device arrays.
+sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const double *mass_c,
+                              const double *rho_c, const double *h_c, const double *sig0_c,
+                              const int32_t *kind_c, const int64_t *copy_of_c,
+                              const double *e0_c, const double *E0_c, int64_t n_int) {
+  const int dim = s->dim;
+  cudaStream_t st = s->stream;
+  s->n = n;
+  s->n_int = n_int;
+  // caller-order SoA positions for the key pass
+  double *cx = dalloc<double>(s, n), *cy = dalloc<double>(s, n), *cz = dalloc<double>(s, n);
+  double *hc = dalloc<double>(s, n);
+  double *bbox = dalloc<double>(s, 8);
+  s->partials = dalloc<double>(s, 8 * kMaxRedBlocks);
+  s->sc = dalloc<Scalars>(s, 1);
+  if (!cx || !cy || !cz || !hc || !bbox || !s->partials || !s->sc) return SPH_RT_ENOMEM;
+  SPH_CUDA(s, cudaMemsetAsync(s->sc, 0, sizeof(Scalars), st));
+  caller_pos_to_soa<<<grid1(s, n), kBlock, 0, st>>>(pos_c, dim, n, cx, cy, cz);
+  SPH_LAUNCHED(s);
+  SPH_CUDA(s, cudaMemcpyAsync(hc, h_c, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  int gb = grid1(s, n);
+  if (gb > kMaxRedBlocks) gb = kMaxRedBlocks;
+  bbox_kernel<<<gb, kBlock, 0, st>>>(cx, cy, cz, hc, n, s->partials, &s->sc->counter, bbox);
+  SPH_LAUNCHED(s);
+  double hb[8];
+  SPH_CUDA(s, cudaMemcpyAsync(hb, bbox, sizeof(double) * 7, cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(s, cudaStreamSynchronize(st));
+
+  Grid g;
+  g.dim = dim;
+  double cell = 2.0 * hb[6] * (1.0 + 1e-9);
+  g.inv_cell = 1.0 / cell;
+  int maxnc = 1;
+  for (int d = 0; d < 3; ++d) {
+    g.lo[d] = hb[d];
+    double ext = hb[3 + d] - hb[d];
+    int nc = d < dim ? (int)(ext / cell) + 1 : 1;
+    g.nc[d] = nc;
+    maxnc = nc > maxnc ? nc : maxnc;
+  }
+  int bits = 0;
+  while ((1 << bits) < maxnc) ++bits;
+  int keybits = bits * dim;
+  if (keybits + 1 > 27) {
+    return set_error(s, SPH_RT_EINVAL,
+                     "particle extent is too large relative to 2 max(h) for the Morton cell "
+                     "grid (more than 2^26 cells)");
+  }
+  g.ghost_shift = keybits;
+  int64_t nkeys = (int64_t)1 << (keybits + 1);
+
+  uint32_t *key = dalloc<uint32_t>(s, n);
+  unsigned *cnt = dalloc<unsigned>(s, nkeys);
+  unsigned *cur = dalloc<unsigned>(s, nkeys);
+  int64_t *cnt64 = dalloc<int64_t>(s, nkeys);
+  int64_t *start = dalloc<int64_t>(s, nkeys + 1);
+  s->slot2caller = dalloc<int64_t>(s, n);
+  s->caller2slot = dalloc<int64_t>(s, n);
+  if (!key || !cnt || !cur || !cnt64 || !start || !s->slot2caller || !s->caller2slot)
+    return SPH_RT_ENOMEM;
+  SPH_CUDA(s, cudaMemsetAsync(cnt, 0, sizeof(unsigned) * nkeys, st));
+  SPH_CUDA(s, cudaMemsetAsync(cur, 0, sizeof(unsigned) * nkeys, st));
+  key_kernel<<<grid1(s, n), kBlock, 0, st>>>(g, cx, cy, cz, kind_c, n, key, cnt);
+  SPH_LAUNCHED(s);
+  u32_to_i64<<<grid1(s, nkeys), kBlock, 0, st>>>(cnt, nkeys, cnt64);
+  SPH_LAUNCHED(s);
+  sph_rt_status rc = exclusive_scan(s, cnt64, nkeys, start);
+  if (rc) return rc;
+  scatter_kernel<<<grid1(s, n), kBlock, 0, st>>>(key, n, start, cur, s->slot2caller);
+  SPH_LAUNCHED(s);
+  segment_sort_kernel<<<grid1(s, nkeys), kBlock, 0, st>>>(start, cnt, nkeys, s->slot2caller);
+  SPH_LAUNCHED(s);
+  invert_perm<<<grid1(s, n), kBlock, 0, st>>>(s->slot2caller, n, s->caller2slot);
+  SPH_LAUNCHED(s);
+
+  // slot-order particle data
+  s->px = dalloc<double>(s, n);
+  s->py = dalloc<double>(s, n);
+  s->pz = dalloc<double>(s, n);
+  s->mass = dalloc<double>(s, n);
+  s->rho = dalloc<double>(s, n);
+  s->h = dalloc<double>(s, n);
+  s->sigma0 = dalloc<double>(s, n);
+  s->V = dalloc<double>(s, n);
+  s->invV = dalloc<double>(s, n);
+  s->kind = dalloc<int32_t>(s, n);
+  s->copysrc = dalloc<int32_t>(s, n);
+  s->e = dalloc<double>(s, n);
+  s->E = dalloc<double>(s, n);
+  if (!s->px || !s->py || !s->pz || !s->mass || !s->rho || !s->h || !s->sigma0 || !s->V ||
+      !s->invV || !s->kind || !s->copysrc || !s->e || !s->E)
+    return SPH_RT_ENOMEM;
+  int gg = grid1(s, n);
+  gather_pos_kernel<<<gg, kBlock, 0, st>>>(pos_c, dim, s->slot2caller, n, s->px, s->py, s->pz);
+  SPH_LAUNCHED(s);
+  gather_kernel<double><<<gg, kBlock, 0, st>>>(mass_c, s->slot2caller, n, s->mass);
+  SPH_LAUNCHED(s);
+  gather_kernel<double><<<gg, kBlock, 0, st>>>(rho_c, s->slot2caller, n, s->rho);
+  SPH_LAUNCHED(s);
+  gather_kernel<double><<<gg, kBlock, 0, st>>>(h_c, s->slot2caller, n, s->h);
+  SPH_LAUNCHED(s);
+  gather_kernel<double><<<gg, kBlock, 0, st>>>(sig0_c, s->slot2caller, n, s->sigma0);
+  SPH_LAUNCHED(s);
+  gather_kernel<int32_t><<<gg, kBlock, 0, st>>>(kind_c, s->slot2caller, n, s->kind);
+  SPH_LAUNCHED(s);
+  gather_kernel<double><<<gg, kBlock, 0, st>>>(e0_c, s->slot2caller, n, s->e);
+  SPH_LAUNCHED(s);
+  gather_kernel<double><<<gg, kBlock, 0, st>>>(E0_c, s->slot2caller, n, s->E);
+  SPH_LAUNCHED(s);
+  copysrc_kernel<<<gg, kBlock, 0, st>>>(copy_of_c, s->kind, s->slot2caller, s->caller2slot, n,
+                                        s->copysrc);
+  SPH_LAUNCHED(s);
+  volume_kernel<<<gg, kBlock, 0, st>>>(s->mass, s->rho, n, s->V, s->invV);
+  SPH_LAUNCHED(s);
+
+  // neighbour lists
+  int64_t *nc = dalloc<int64_t>(s, n_int);
+  s->nbr_ptr = dalloc<int64_t>(s, n_int + 1);
+  if (!nc || !s->nbr_ptr) return SPH_RT_ENOMEM;
+  int64_t warps = n_int;
+  int gw = (int)ceil_div(warps, kWarpsPerBlock);
+  int gcap = s->num_sms * 8;
+  if (gw > gcap) gw = gcap;
+  neighbor_kernel<false><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, start, cnt, n_int,
+                                                nc, nullptr, nullptr, nullptr);
+  SPH_LAUNCHED(s);
+  rc = exclusive_scan(s, nc, n_int, s->nbr_ptr);
+  if (rc) return rc;
+  int64_t nnz = 0;
+  SPH_CUDA(s, cudaMemcpyAsync(&nnz, s->nbr_ptr + n_int, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(s, cudaStreamSynchronize(st));
+  if (nnz >= ((int64_t)1 << 31) - 1)
+    return set_error(s, SPH_RT_EINVAL, "more than 2^31 neighbour pairs");
+  s->nnz_nbr = nnz;
+  s->nbr_col = dalloc<int32_t>(s, nnz);
+  s->nbr_F = dalloc<double>(s, nnz);
+  if (!s->nbr_col || !s->nbr_F) return SPH_RT_ENOMEM;
+  neighbor_kernel<true><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, start, cnt, n_int,
+                                               nullptr, s->nbr_ptr, s->nbr_col, s->nbr_F);
+  SPH_LAUNCHED(s);
+
+  // operator sparsity
+  int64_t *mc = dalloc<int64_t>(s, n_int), *gc = dalloc<int64_t>(s, n_int);
+  s->mat_ptr = dalloc<int64_t>(s, n_int + 1);
+  s->gh_ptr = dalloc<int64_t>(s, n_int + 1);
+  if (!mc || !gc || !s->mat_ptr || !s->gh_ptr) return SPH_RT_ENOMEM;
+  int gi = grid1(s, n_int);
+  op_count_kernel<<<gi, kBlock, 0, st>>>(s->nbr_ptr, s->nbr_col, s->kind, s->copysrc, n_int, mc, gc);
+  SPH_LAUNCHED(s);
+  if ((rc = exclusive_scan(s, mc, n_int, s->mat_ptr))) return rc;
+  if ((rc = exclusive_scan(s, gc, n_int, s->gh_ptr))) return rc;
+  int64_t sizes[2];
+  SPH_CUDA(s, cudaMemcpyAsync(&sizes[0], s->mat_ptr + n_int, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(s, cudaMemcpyAsync(&sizes[1], s->gh_ptr + n_int, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(s, cudaStreamSynchronize(st));
+  s->nnz_mat = sizes[0];
+  s->nnz_gh = sizes[1];
+  s->mat_col = dalloc<int32_t>(s, s->nnz_mat);
+  s->mat_G = dalloc<double>(s, s->nnz_mat);
+  s->mat_val = dalloc<double>(s, s->nnz_mat);
+  s->gh_slot = dalloc<int32_t>(s, s->nnz_gh);
+  s->gh_W = dalloc<double>(s, s->nnz_gh);
+  if (!s->mat_col || !s->mat_G || !s->mat_val || !s->gh_slot || !s->gh_W) return SPH_RT_ENOMEM;
+  op_fill_kernel<<<gi, kBlock, 0, st>>>(s->nbr_ptr, s->nbr_col, s->nbr_F, s->kind, s->copysrc,
+                                        s->V, n_int, s->mat_ptr, s->mat_col, s->mat_G, s->gh_ptr,
+                                        s->gh_slot, s->gh_W);
+  SPH_LAUNCHED(s);
+  SPH_CUDA(s, cudaStreamSynchronize(st));
+  return SPH_RT_OK;
+}
+
+// --------------------------------------------------------------------------
+// Validation of caller arrays that are already on the device (the checks of
+// the host path): error bits in flags[0], interior count in flags[1].
+// --------------------------------------------------------------------------
+__global__ void validate_kernel(int64_t n, int dim, const double *pos, const double *mass,
+                                const double *rho, const double *h, const double *sigma0,
+                                const int32_t *kind, const int64_t *copy_of, const double *e0,
+                                const double *E0, unsigned long long *flags) {
+  unsigned long long bad = 0, ni = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int d = 0; d < dim; ++d)
+      if (!isfinite(pos[i * dim + d])) bad |= 1ull;
+    if (!(isfinite(mass[i]) && mass[i] > 0) || !(isfinite(rho[i]) && rho[i] > 0) ||
+        !(isfinite(h[i]) && h[i] > 0))
+      bad |= 2ull;
+    if (!isfinite(sigma0[i]) || sigma0[i] < 0) bad |= 4ull;
+    if (!isfinite(e0[i]) || !isfinite(E0[i])) bad |= 8ull;
+    int32_t k = kind[i];
+    if (k < 0 || k > 2) bad |= 16ull;
+    if (k == SPH_RT_INTERIOR) ++ni;
+    if (k == SPH_RT_COPY) {
+      if (!copy_of) {
+        bad |= 32ull;
+      } else {
+        int64_t c = copy_of[i];
+        if (c < 0 || c >= n || kind[c] != SPH_RT_INTERIOR) bad |= 32ull;
+      }
+    }
+  }
+  if (bad) atomicOr(&flags[0], bad);
+  if (ni) atomicAdd(&flags[1], ni);
+}
+
+sph_rt_status validate_device_particles(sph_rt *s, int64_t n, const double *pos,
+                                        const double *mass, const double *rho, const double *h,
+                                        const double *sigma0, const int32_t *kind,
+                                        const int64_t *copy_of, const double *e0,
+                                        const double *E0, int64_t *n_int_out) {
+  unsigned long long *flags = nullptr;
+  SPH_CUDA(s, cudaMalloc(&flags, 2 * sizeof(unsigned long long)));
+  cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned long long), s->stream);
+  validate_kernel<<<grid1(s, n), kBlock, 0, s->stream>>>(n, s->dim, pos, mass, rho, h, sigma0,
+                                                         kind, copy_of, e0, E0, flags);
+  s->launches++;
+  unsigned long long hf[2] = {0, 0};
+  cudaError_t e1 = cudaGetLastError();
+  cudaError_t e2 = cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s->stream);
+  cudaError_t e3 = cudaStreamSynchronize(s->stream);
+  cudaFree(flags);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    cuda_ok(s, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "validate_kernel");
+    return SPH_RT_EDEVICE;
+  }
+  static const char *what[] = {"non-finite position", "mass, rho and h must be finite and positive",
+                               "sigma0 must be finite and >= 0", "non-finite initial energy",
+                               "kind out of range", "copy_of must name an interior particle"};
+  for (int b = 0; b < 6; ++b)
+    if (hf[0] & (1ull << b)) return set_error(s, SPH_RT_EINVAL, what[b]);
+  if (hf[1] == 0) return set_error(s, SPH_RT_EINVAL, "no interior particle");
+  *n_int_out = (int64_t)hf[1];
+  return SPH_RT_OK;
+}
+
+}  // namespace sphrt

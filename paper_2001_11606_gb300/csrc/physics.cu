@@ -1,0 +1,498 @@
+// physics.cu -- per-particle and per-row kernels of one time step
+// (rows a3, a4, a7, a8, a9 of the hot path).
+//
+//  a3  material data, frozen for the step (Sec. 3.2):
+//        T = e/c_v, sigma = sigma0 T^p, Fleck factor f = 1/(1 + c sigma dt 4aT^3/(rho c_v))
+//        (Sec. 2.2), SPH gradient grad E_i = sum_j V_j (E_j - E_i) F_ij x_ij (Sec. 2.3),
+//        R = |grad E|/(sigma E), flux limiter lambda(R) (Sec. 2.1), D = c lambda / sigma.
+//  a4  operator of Eq. diffusion-solve scaled by V:  B_ij = V_i V_j F_ij (D_i + D_j) for
+//        j != i, B_ii = V_i (1/dt + c sigma_i f_i) + sum over all neighbours of
+//        V_i w_ij, w_ij = -V_j (D_i + D_j) F_ij >= 0; Dirichlet neighbours move to
+//        the right-hand side as gb_i = sum_j w_ij E_j.
+//  a7  right-hand side (Sec. 3.2, operators S and N):
+//        b_i = E_i^{n-1}/dt + c sigma_i a T_i^4 - (1 - f_i) c sigma_i E_i + Q_E,i + gb_i.
+//  a8  material solve M^{-1} (Eq. material-energy-update), one thread per particle.
+//  a9  outer convergence (Eq. mat-rad-convergence) and energy totals (Sec. 2.5).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace sphrt {
+
+struct Phys {
+  double a, c, cv, p, T_floor, larsen_k, dt;
+  double tol_inner;
+  int limiter, max_inner;
+};
+
+__device__ __forceinline__ double opacity(double sigma0, double Ts, double p) {
+  if (p == 0.0) return sigma0;
+  if (p == -3.0) return sigma0 / (Ts * Ts * Ts);
+  return sigma0 * pow(Ts, p);
+}
+
+__device__ __forceinline__ double limiter_lambda(int limiter, double k, double R) {
+  if (limiter == SPH_RT_LIMITER_LEVERMORE) return (2.0 + R) / (6.0 + 3.0 * R + R * R);
+  if (limiter == SPH_RT_LIMITER_LARSEN) {
+    if (k == 2.0) return 1.0 / sqrt(9.0 + R * R);
+    return 1.0 / pow(pow(3.0, k) + pow(R, k), 1.0 / k);
+  }
+  return 1.0 / 3.0;
+}
+
+// a3, point part: every non-copy slot (interior and Dirichlet ghosts).
+__global__ void props_point_kernel(Phys ph, int64_t n, const int32_t *kind, const double *rho,
+                                   const double *sigma0, const double *e, double *T,
+                                   double *sigma, double *f, double *R, double *lambda,
+                                   double *D) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (kind[i] == SPH_RT_COPY) continue;
+    double Ti = e[i] / ph.cv;
+    double Ts = Ti > ph.T_floor ? Ti : ph.T_floor;
+    double sig = opacity(sigma0[i], Ts, ph.p);
+    double fi = 1.0 / (1.0 + ph.c * sig * ph.dt * 4.0 * ph.a * Ti * Ti * Ti / (rho[i] * ph.cv));
+    T[i] = Ti;
+    sigma[i] = sig;
+    f[i] = fi;
+    // R = 0 here; interior rows with a limiter are overwritten by the gradient kernel
+    double lam = limiter_lambda(ph.limiter, ph.larsen_k, 0.0);
+    R[i] = 0.0;
+    lambda[i] = lam;
+    D[i] = ph.c * lam / sig;
+  }
+}
+
+// a3, gradient part: one group of W lanes per interior row.
+template <int W>
+__global__ void props_grad_kernel(Phys ph, int64_t n_int, const int64_t *nbr_ptr,
+                                  const int32_t *nbr_col, const double *nbr_F, const double *px,
+                                  const double *py, const double *pz, const double *V,
+                                  const int32_t *kind, const int32_t *copysrc, const double *E,
+                                  const double *sigma, double *R, double *lambda, double *D) {
+  const int sub = threadIdx.x % W;
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  for (int64_t i = grp; i < n_int; i += ngrp) {
+    double xi = px[i], yi = py[i], zi = pz[i], Ei = E[i];
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int64_t k = nbr_ptr[i] + sub; k < nbr_ptr[i + 1]; k += W) {
+      int32_t j = nbr_col[k];
+      int32_t js = kind[j] == SPH_RT_COPY ? copysrc[j] : j;
+      double s = V[j] * (E[js] - Ei) * nbr_F[k];
+      gx += s * (xi - px[j]);
+      gy += s * (yi - py[j]);
+      gz += s * (zi - pz[j]);
+    }
+    gx = group_sum<W>(gx);
+    gy = group_sum<W>(gy);
+    gz = group_sum<W>(gz);
+    if (sub == 0) {
+      double gn = sqrt(gx * gx + gy * gy + gz * gz);
+      double Es = Ei > 1e-300 ? Ei : 1e-300;
+      double Ri = gn / (sigma[i] * Es);
+      double lam = limiter_lambda(ph.limiter, ph.larsen_k, Ri);
+      R[i] = Ri;
+      lambda[i] = lam;
+      D[i] = ph.c * lam / sigma[i];
+    }
+  }
+}
+
+// copy ghosts take every property of the particle they copy
+__global__ void props_copy_kernel(int64_t n_int, int64_t n, const int32_t *copysrc, double *T,
+                                  double *sigma, double *f, double *R, double *lambda, double *D) {
+  for (int64_t i = n_int + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t s = copysrc[i];
+    if (s < 0) continue;
+    T[i] = T[s];
+    sigma[i] = sigma[s];
+    f[i] = f[s];
+    R[i] = R[s];
+    lambda[i] = lambda[s];
+    D[i] = D[s];
+  }
+}
+
+// a4: values of B for the step; W lanes per row.
+template <int W>
+__global__ void assemble_kernel(Phys ph, int64_t n_int, const int64_t *mat_ptr,
+                                const int32_t *mat_col, const double *mat_G, double *mat_val,
+                                const int64_t *gh_ptr, const int32_t *gh_slot, const double *gh_W,
+                                const double *V, const double *sigma, const double *f,
+                                const double *D, const double *E, double *diag,
+                                double *invdiag, double *gb, double *partials,
+                                unsigned *counter, double *gersh_out) {
+  // gersh_out = max_i sum_{j != i} |B_ij| / B_ii: the eigenvalues of D^{-1} B
+  // lie in [1 - gersh, 1 + gersh] (Gershgorin; B is symmetric, so real).
+  const int sub = threadIdx.x % W;
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  double gmax = 0.0;
+  for (int64_t i = grp; i < n_int; i += ngrp) {
+    double Di = D[i];
+    double offsum = 0.0;
+    for (int64_t k = mat_ptr[i] + sub; k < mat_ptr[i + 1]; k += W) {
+      double v = mat_G[k] * (Di + D[mat_col[k]]);
+      mat_val[k] = v;
+      offsum += v;
+    }
+    double wsum = 0.0, gbs = 0.0;
+    for (int64_t k = gh_ptr[i] + sub; k < gh_ptr[i + 1]; k += W) {
+      int32_t j = gh_slot[k];
+      double wk = -gh_W[k] * (Di + D[j]);
+      wsum += wk;
+      gbs += wk * E[j];
+    }
+    offsum = group_sum<W>(offsum);
+    wsum = group_sum<W>(wsum);
+    gbs = group_sum<W>(gbs);
+    if (sub == 0) {
+      double d = V[i] * (1.0 / ph.dt + ph.c * sigma[i] * f[i] + wsum) - offsum;
+      diag[i] = d;
+      invdiag[i] = 1.0 / d;
+      gb[i] = gbs;
+      gmax = fmax(gmax, -offsum / d);  // off-diagonals are <= 0
+    }
+  }
+  __shared__ double sh[32];
+  gmax = block_max(gmax, sh);
+  double part[1] = {gmax}, out[1];
+  const bool mx[1] = {true};
+  if (last_block_combine<1>(part, partials, counter, out, mx) && threadIdx.x == 0)
+    *gersh_out = out[0];
+}
+
+// a7: right-hand side of the diffusion solve (B-scaled), the warm start x = E^l,
+// ||b||^2 of the unscaled rows, and reset of the Krylov scalars.
+__global__ void rhs_kernel(Phys ph, int64_t n_int, const double *V, const double *sigma,
+                           const double *f, const double *E_old, const double *e_l,
+                           const double *E_l, const double *QE, const double *gb, double *b,
+                           double *x, double tol, Scalars *sc, double *partials) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double Tl = e_l[i] / ph.cv;
+    double B = ph.a * Tl * Tl * Tl * Tl;
+    double cs = ph.c * sigma[i];
+    double bi = E_old[i] / ph.dt + cs * B - (1.0 - f[i]) * cs * E_l[i] + QE[i] + gb[i];
+    b[i] = V[i] * bi;
+    x[i] = E_l[i];
+    acc += bi * bi;
+  }
+  __shared__ double sh[32];
+  double bs = block_sum(acc, sh);
+  double part[1] = {bs}, out[1];
+  const bool mx[1] = {false};
+  if (last_block_combine<1>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    sc->bnorm2 = out[0];
+    sc->thresh2 = tol * tol * out[0];
+    sc->done = 0;
+    sc->iters = 0;
+    sc->breakdown = 0;
+  }
+}
+
+// a8 + a9: material solve with the new radiation energy and the outer
+// convergence measures.  P_i = c sigma_i E_i + Q_e,i (Eq. material-energy-solve);
+// Newton from e_start.  red[0] = max |e_new - e_start|/|e_new|,
+// red[1] = max |E_new - E_prev|/|E_new|, red[2] = max Newton iterations,
+// red[3] = number of particles that hit the iteration limit.
+__global__ void newton_kernel(Phys ph, int64_t n_int, const double *rho, const double *sigma,
+                              const double *e_old, const double *Qe, const double *E_new,
+                              const double *E_prev, const double *e_start, double *e_new,
+                              Scalars *sc, double *partials) {
+  double ce = 0.0, cE = 0.0, itmax = 0.0, fails = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double cs = ph.c * sigma[i];
+    double P = cs * E_new[i] + Qe[i];
+    double rdt = rho[i] / ph.dt;
+    double eo = e_old[i];
+    double e0 = e_start[i];
+    double ei = e0;
+    int it = 0;
+    bool ok = false;
+    while (it < ph.max_inner) {
+      double T = ei / ph.cv;
+      double T3 = T * T * T;
+      double u = rdt * (ei - eo) + cs * ph.a * T3 * T - P;
+      double J = rdt + 4.0 * cs * ph.a * T3 / ph.cv;
+      double de = u / J;
+      ei = ei - de;
+      ++it;
+      if (fabs(de) <= ph.tol_inner * fabs(ei)) {
+        ok = true;
+        break;
+      }
+    }
+    e_new[i] = ei;
+    ce = fmax(ce, fabs(ei - e0) / fmax(fabs(ei), 1e-300));
+    cE = fmax(cE, fabs(E_new[i] - E_prev[i]) / fmax(fabs(E_new[i]), 1e-300));
+    itmax = fmax(itmax, (double)it);
+    if (!ok) fails += 1.0;
+  }
+  __shared__ double sh[32];
+  double p0 = block_max(ce, sh);
+  __syncthreads();
+  double p1 = block_max(cE, sh);
+  __syncthreads();
+  double p2 = block_max(itmax, sh);
+  __syncthreads();
+  double p3 = block_sum(fails, sh);
+  double part[4] = {p0, p1, p2, p3}, out[4];
+  const bool mx[4] = {true, true, true, false};
+  if (last_block_combine<4>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    sc->red[0] = out[0];
+    sc->red[1] = out[1];
+    sc->red[2] = out[2];
+    sc->red[3] = out[3];
+  }
+}
+
+// Totals over interior particles: red[4] = sum m e, red[5] = sum V E.
+__global__ void totals_kernel(int64_t n_int, const double *mass, const double *V, const double *e,
+                              const double *E, Scalars *sc, double *partials) {
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    a += mass[i] * e[i];
+    b += V[i] * E[i];
+  }
+  __shared__ double sh[32];
+  double pa = block_sum(a, sh);
+  __syncthreads();
+  double pb = block_sum(b, sh);
+  double part[2] = {pa, pb}, out[2];
+  const bool mx[2] = {false, false};
+  if (last_block_combine<2>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    sc->red[4] = out[0];
+    sc->red[5] = out[1];
+  }
+}
+
+// Energy added over the step: red[6] = dt sum V (Q_e + Q_E);
+// red[7] = dt sum_i V_i sum_{Dirichlet j} w_ij (E_j - E_i).
+__global__ void balance_kernel(Phys ph, int64_t n_int, const double *V, const double *Qe,
+                               const double *QE, const int64_t *gh_ptr, const int32_t *gh_slot,
+                               const double *gh_W, const double *D, const double *E,
+                               Scalars *sc, double *partials) {
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    a += V[i] * (Qe[i] + QE[i]);
+    double acc = 0.0;
+    for (int64_t k = gh_ptr[i]; k < gh_ptr[i + 1]; ++k) {
+      int32_t j = gh_slot[k];
+      acc += -gh_W[k] * (D[i] + D[j]) * (E[j] - E[i]);
+    }
+    b += V[i] * acc;
+  }
+  __shared__ double sh[32];
+  double pa = block_sum(a, sh);
+  __syncthreads();
+  double pb = block_sum(b, sh);
+  double part[2] = {pa, pb}, out[2];
+  const bool mx[2] = {false, false};
+  if (last_block_combine<2>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    sc->red[6] = ph.dt * out[0];
+    sc->red[7] = ph.dt * out[1];
+  }
+}
+
+// Install Dirichlet ghost values (slot order) from caller-order arrays.
+__global__ void ghost_install_kernel(int64_t n_int, int64_t n, const int32_t *kind,
+                                     const int64_t *slot2caller, const double *ge_c,
+                                     const double *gE_c, double *e, double *E) {
+  for (int64_t s = n_int + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    if (kind[s] != SPH_RT_DIRICHLET) continue;
+    int64_t c = slot2caller[s];
+    if (ge_c) e[s] = ge_c[c];
+    if (gE_c) E[s] = gE_c[c];
+  }
+}
+
+__global__ void copy_ghost_sync_kernel(int64_t n_int, int64_t n, const int32_t *copysrc,
+                                       double *e, double *E) {
+  for (int64_t s = n_int + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int32_t c = copysrc[s];
+    if (c < 0) continue;
+    e[s] = e[c];
+    E[s] = E[c];
+  }
+}
+
+// caller-order source -> slot order (interior part); NULL source gives zeros
+__global__ void gather_interior_kernel(const double *in_c, const int64_t *slot2caller,
+                                       int64_t n_int, double *out) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_int;
+       s += (int64_t)gridDim.x * blockDim.x)
+    out[s] = in_c ? in_c[slot2caller[s]] : 0.0;
+}
+
+__global__ void scatter_caller_kernel(const double *in_s, const int64_t *slot2caller, int64_t n,
+                                      double *out_c) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x)
+    out_c[slot2caller[s]] = in_s[s];
+}
+
+__global__ void commit_kernel(int64_t n_int, const double *e_new, const double *E_new, double *e,
+                              double *E) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    e[i] = e_new[i];
+    E[i] = E_new[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static int grid_items(const sph_rt *s, int64_t n, int per_block) {
+  int64_t g = ceil_div(n > 0 ? n : 1, per_block);
+  int64_t cap = (int64_t)s->num_sms * 8;
+  if (cap > kMaxRedBlocks) cap = kMaxRedBlocks;
+  return (int)(g < cap ? g : cap);
+}
+
+Phys make_phys(const sph_rt *s, double dt) {
+  Phys ph;
+  ph.a = s->cfg.a;
+  ph.c = s->cfg.c;
+  ph.cv = s->cfg.cv;
+  ph.p = s->cfg.opacity_exp;
+  ph.T_floor = s->cfg.T_floor;
+  ph.larsen_k = s->cfg.larsen_k;
+  ph.dt = dt;
+  ph.tol_inner = s->cfg.tol_inner_e;
+  ph.limiter = s->cfg.limiter;
+  ph.max_inner = s->cfg.max_inner_e;
+  return ph;
+}
+
+// rows per group of the warp-per-row kernels, from the mean row length
+int row_width(int64_t nnz, int64_t rows) {
+  double mean = rows > 0 ? (double)nnz / (double)rows : 0.0;
+  if (mean > 48) return 32;
+  if (mean > 12) return 16;
+  return 8;
+}
+
+#define SPH_ROWS_LAUNCH(KERNEL, W, grid, s, ...)                              \
+  do {                                                                        \
+    if ((W) == 32) KERNEL<32><<<grid, kBlock, 0, (s)->stream>>>(__VA_ARGS__); \
+    else if ((W) == 16) KERNEL<16><<<grid, kBlock, 0, (s)->stream>>>(__VA_ARGS__); \
+    else KERNEL<8><<<grid, kBlock, 0, (s)->stream>>>(__VA_ARGS__);            \
+    SPH_LAUNCHED(s);                                                          \
+  } while (0)
+
+sph_rt_status launch_properties(sph_rt *s, double dt) {
+  Phys ph = make_phys(s, dt);
+  int g = grid_items(s, s->n, kBlock);
+  props_point_kernel<<<g, kBlock, 0, s->stream>>>(ph, s->n, s->kind, s->rho, s->sigma0, s->e,
+                                                   s->T, s->sigma, s->f, s->R, s->lambda, s->D);
+  SPH_LAUNCHED(s);
+  if (s->cfg.limiter != SPH_RT_LIMITER_NONE) {
+    int W = row_width(s->nnz_nbr, s->n_int);
+    int gr = grid_items(s, s->n_int, kBlock / W);
+    SPH_ROWS_LAUNCH(props_grad_kernel, W, gr, s, ph, s->n_int, s->nbr_ptr, s->nbr_col, s->nbr_F,
+                    s->px, s->py, s->pz, s->V, s->kind, s->copysrc, s->E, s->sigma, s->R,
+                    s->lambda, s->D);
+  }
+  if (s->n > s->n_int) {
+    props_copy_kernel<<<grid_items(s, s->n - s->n_int, kBlock), kBlock, 0, s->stream>>>(
+        s->n_int, s->n, s->copysrc, s->T, s->sigma, s->f, s->R, s->lambda, s->D);
+    SPH_LAUNCHED(s);
+  }
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_assembly(sph_rt *s, double dt, double *gersh_out) {
+  Phys ph = make_phys(s, dt);
+  int W = row_width(s->nnz_mat, s->n_int);
+  int gr = grid_items(s, s->n_int, kBlock / W);
+  SPH_ROWS_LAUNCH(assemble_kernel, W, gr, s, ph, s->n_int, s->mat_ptr, s->mat_col, s->mat_G,
+                  s->mat_val, s->gh_ptr, s->gh_slot, s->gh_W, s->V, s->sigma, s->f, s->D, s->E,
+                  s->diag, s->invdiag, s->gb, s->partials, &s->sc->counter, gersh_out);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_rhs(sph_rt *s, double dt) {
+  Phys ph = make_phys(s, dt);
+  int g = grid_items(s, s->n_int, kBlock);
+  rhs_kernel<<<g, kBlock, 0, s->stream>>>(ph, s->n_int, s->V, s->sigma, s->f, s->E_old, s->e_l,
+                                           s->E_l, s->QE, s->gb, s->b, s->x, s->cfg.tol_krylov,
+                                           s->sc, s->partials);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_newton(sph_rt *s, double dt, const double *E_new, const double *E_prev,
+                            const double *e_start, double *e_out) {
+  Phys ph = make_phys(s, dt);
+  int g = grid_items(s, s->n_int, kBlock);
+  newton_kernel<<<g, kBlock, 0, s->stream>>>(ph, s->n_int, s->rho, s->sigma, s->e_old, s->Qe,
+                                              E_new, E_prev, e_start, e_out, s->sc, s->partials);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_totals(sph_rt *s, const double *e, const double *E) {
+  int g = grid_items(s, s->n_int, kBlock);
+  totals_kernel<<<g, kBlock, 0, s->stream>>>(s->n_int, s->mass, s->V, e, E, s->sc, s->partials);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_balance(sph_rt *s, double dt, const double *E) {
+  Phys ph = make_phys(s, dt);
+  int g = grid_items(s, s->n_int, kBlock);
+  balance_kernel<<<g, kBlock, 0, s->stream>>>(ph, s->n_int, s->V, s->Qe, s->QE, s->gh_ptr,
+                                               s->gh_slot, s->gh_W, s->D, E, s->sc, s->partials);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_ghost_install(sph_rt *s, const double *ge_c, const double *gE_c) {
+  if (s->n == s->n_int || (!ge_c && !gE_c)) return SPH_RT_OK;
+  int g = grid_items(s, s->n - s->n_int, kBlock);
+  ghost_install_kernel<<<g, kBlock, 0, s->stream>>>(s->n_int, s->n, s->kind, s->slot2caller,
+                                                     ge_c, gE_c, s->e, s->E);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_copy_sync(sph_rt *s) {
+  if (s->n == s->n_int) return SPH_RT_OK;
+  int g = grid_items(s, s->n - s->n_int, kBlock);
+  copy_ghost_sync_kernel<<<g, kBlock, 0, s->stream>>>(s->n_int, s->n, s->copysrc, s->e, s->E);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_gather_interior(sph_rt *s, const double *in_c, double *out) {
+  int g = grid_items(s, s->n_int, kBlock);
+  gather_interior_kernel<<<g, kBlock, 0, s->stream>>>(in_c, s->slot2caller, s->n_int, out);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_scatter_caller(sph_rt *s, const double *in_s, int64_t count, double *out_c) {
+  int g = grid_items(s, count, kBlock);
+  scatter_caller_kernel<<<g, kBlock, 0, s->stream>>>(in_s, s->slot2caller, count, out_c);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_commit(sph_rt *s, const double *e_new, const double *E_new) {
+  int g = grid_items(s, s->n_int, kBlock);
+  commit_kernel<<<g, kBlock, 0, s->stream>>>(s->n_int, e_new, E_new, s->e, s->E);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+}  // namespace sphrt

@@ -1,0 +1,694 @@
+// sph_rt.cu -- the C ABI of include/sph_rt.h: handle lifecycle, host-side
+// validation, and the step driver that follows Alg. 1 of the paper
+// (initial material solve, then outer iterations of diffusion solve and
+// material solve until Eq. mat-rad-convergence holds).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sphrt {
+
+// defined in the other translation units
+sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const double *mass_c,
+                              const double *rho_c, const double *h_c, const double *sig0_c,
+                              const int32_t *kind_c, const int64_t *copy_of_c, const double *e0_c,
+                              const double *E0_c, int64_t n_int);
+sph_rt_status launch_properties(sph_rt *s, double dt);
+sph_rt_status launch_assembly(sph_rt *s, double dt, double *gersh_out);
+sph_rt_status launch_rhs(sph_rt *s, double dt);
+sph_rt_status launch_newton(sph_rt *s, double dt, const double *E_new, const double *E_prev,
+                            const double *e_start, double *e_out);
+sph_rt_status launch_totals(sph_rt *s, const double *e, const double *E);
+sph_rt_status launch_balance(sph_rt *s, double dt, const double *E);
+sph_rt_status launch_ghost_install(sph_rt *s, const double *ge_c, const double *gE_c);
+sph_rt_status launch_copy_sync(sph_rt *s);
+sph_rt_status launch_gather_interior(sph_rt *s, const double *in_c, double *out);
+sph_rt_status launch_scatter_caller(sph_rt *s, const double *in_s, int64_t count, double *out_c);
+sph_rt_status launch_commit(sph_rt *s, const double *e_new, const double *E_new);
+sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged);
+sph_rt_status amg_setup(sph_rt *s);
+void amg_release(sph_rt *s);
+sph_rt_status validate_device_particles(sph_rt *s, int64_t n, const double *pos,
+                                        const double *mass, const double *rho, const double *h,
+                                        const double *sigma0, const int32_t *kind,
+                                        const int64_t *copy_of, const double *e0,
+                                        const double *E0, int64_t *n_int_out);
+
+sph_rt_status set_error(sph_rt *s, sph_rt_status st, const std::string &msg) {
+  if (s) s->err = msg;
+  return st;
+}
+
+bool cuda_ok(sph_rt *s, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return true;
+  if (s) s->err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  return false;
+}
+
+void *dalloc_bytes(sph_rt *s, size_t bytes) {
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    s->err = "device allocation of " + std::to_string(bytes) + " bytes failed: " +
+             cudaGetErrorString(e);
+    return nullptr;
+  }
+  s->allocs.push_back(p);
+  return p;
+}
+
+void free_all(sph_rt *s) {
+  if (s->cuda_ready) cudaStreamSynchronize(s->stream);
+  amg_release(s);
+  for (void *p : s->allocs) cudaFree(p);
+  s->allocs.clear();
+  s->have_particles = false;
+  s->have_operator = false;
+  s->amg_ready = false;
+}
+
+}  // namespace sphrt
+
+using namespace sphrt;
+
+// ---------------------------------------------------------------------------
+// configuration
+// ---------------------------------------------------------------------------
+extern "C" void sph_rt_default_config(sph_rt_config *c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->dim = 3;
+  c->a = 1.0;
+  c->c = 1.0;
+  c->cv = 1.0;
+  c->limiter = SPH_RT_LIMITER_NONE;
+  c->larsen_k = 2.0;
+  c->opacity_exp = 0.0;
+  c->T_floor = 0.0;
+  c->tol_outer_e = 1e-8;
+  c->tol_outer_E = 1e-8;
+  c->tol_inner_e = 1e-13;
+  c->tol_krylov = 1e-12;
+  c->max_outer = 50;
+  c->max_inner_e = 50;
+  c->max_krylov = 2000;
+  c->precond = SPH_RT_PRECOND_AMG;
+  c->precision = SPH_RT_FP64;
+  c->cheb_degree = 2;
+  c->amg_rebuild = 0;
+  c->amg_theta = 0.08;
+  c->check_every = 4;
+  c->kernel_timing = 0;
+  c->device = 0;
+  c->stream = nullptr;
+}
+
+static bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
+  if (c->dim < 1 || c->dim > 3) return why = "dim must be 1, 2 or 3", SPH_RT_EINVAL;
+  if (!finite_pos(c->a) || !finite_pos(c->c) || !finite_pos(c->cv))
+    return why = "a, c and cv must be finite and positive", SPH_RT_EINVAL;
+  if (c->limiter < 0 || c->limiter > 2) return why = "limiter out of range", SPH_RT_EINVAL;
+  if (c->limiter == SPH_RT_LIMITER_LARSEN && !finite_pos(c->larsen_k))
+    return why = "larsen_k must be positive", SPH_RT_EINVAL;
+  if (!isfinite(c->opacity_exp)) return why = "opacity_exp must be finite", SPH_RT_EINVAL;
+  if (!isfinite(c->T_floor) || c->T_floor < 0) return why = "T_floor must be >= 0", SPH_RT_EINVAL;
+  if (!finite_pos(c->tol_outer_e) || !finite_pos(c->tol_outer_E) || !finite_pos(c->tol_inner_e) ||
+      !finite_pos(c->tol_krylov))
+    return why = "tolerances must be finite and positive", SPH_RT_EINVAL;
+  if (c->max_outer < 1 || c->max_outer > 64 || c->max_inner_e < 1 || c->max_krylov < 1)
+    return why = "iteration limits must be >= 1 (max_outer <= 64)", SPH_RT_EINVAL;
+  if (c->precond < 0 || c->precond > 2) return why = "precond out of range", SPH_RT_EINVAL;
+  if (c->precision < 0 || c->precision > 1) return why = "precision out of range", SPH_RT_EINVAL;
+  if (c->cheb_degree < 1 || c->cheb_degree > 16)
+    return why = "cheb_degree must be in [1, 16]", SPH_RT_EINVAL;
+  if (!(c->amg_theta >= 0.0 && c->amg_theta < 1.0))
+    return why = "amg_theta must be in [0, 1)", SPH_RT_EINVAL;
+  if (c->check_every < 1) return why = "check_every must be >= 1", SPH_RT_EINVAL;
+  if (c->device < 0) return why = "device must be >= 0", SPH_RT_EINVAL;
+  return SPH_RT_OK;
+}
+
+static thread_local std::string g_create_error;  // why the last sph_rt_create failed
+
+extern "C" sph_rt_status sph_rt_create(const sph_rt_config *cfg, sph_rt **out) {
+  if (!out) return SPH_RT_EINVAL;
+  *out = nullptr;
+  if (!cfg) {
+    g_create_error = "cfg is NULL";
+    return SPH_RT_EINVAL;
+  }
+  std::string why;
+  if (check_config(cfg, why) != SPH_RT_OK) {
+    g_create_error = why;
+    return SPH_RT_EINVAL;
+  }
+  sph_rt *s = new (std::nothrow) sph_rt();
+  if (!s) {
+    g_create_error = "out of host memory";
+    return SPH_RT_ENOMEM;
+  }
+  s->cfg = *cfg;
+  s->dim = cfg->dim;
+  *out = s;
+  return SPH_RT_OK;
+}
+
+static sph_rt_status ensure_cuda(sph_rt *s) {
+  if (s->cuda_ready) return SPH_RT_OK;
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  int sms = 0;
+  SPH_CUDA(s, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->cfg.device));
+  s->num_sms = sms > 0 ? sms : 152;
+  if (s->cfg.stream) {
+    s->stream = (cudaStream_t)s->cfg.stream;
+    s->own_stream = false;
+  } else {
+    SPH_CUDA(s, cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  SPH_CUDA(s, cudaMallocHost(&s->sc_host, sizeof(Scalars)));
+  s->cuda_ready = true;
+  return SPH_RT_OK;
+}
+
+extern "C" void sph_rt_destroy(sph_rt *s) {
+  if (!s) return;
+  if (s->cuda_ready) {
+    cudaSetDevice(s->cfg.device);
+    free_all(s);
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    if (s->sc_host) cudaFreeHost(s->sc_host);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  }
+  delete s;
+}
+
+extern "C" const char *sph_rt_last_error(const sph_rt *s) {
+  return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" int64_t sph_rt_launch_count(const sph_rt *s) { return s ? s->launches : 0; }
+
+// ---------------------------------------------------------------------------
+// particles
+// ---------------------------------------------------------------------------
+static sph_rt_status validate_host_particles(sph_rt *s, int64_t n, const double *pos,
+                                             const double *mass, const double *rho,
+                                             const double *h, const double *sigma0,
+                                             const int32_t *kind, const int64_t *copy_of,
+                                             const double *e0, const double *E0,
+                                             int64_t *n_int) {
+  if (n < 1) return set_error(s, SPH_RT_EINVAL, "n_total must be >= 1");
+  if (n >= ((int64_t)1 << 31) - 1) return set_error(s, SPH_RT_EINVAL, "n_total must be < 2^31");
+  if (!pos || !mass || !rho || !h || !sigma0 || !kind || !e0 || !E0)
+    return set_error(s, SPH_RT_EINVAL, "a required particle array is NULL");
+  int64_t ni = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int d = 0; d < s->dim; ++d)
+      if (!isfinite(pos[i * s->dim + d]))
+        return set_error(s, SPH_RT_EINVAL, "non-finite position at particle " + std::to_string(i));
+    if (!finite_pos(mass[i]) || !finite_pos(rho[i]) || !finite_pos(h[i]))
+      return set_error(s, SPH_RT_EINVAL,
+                       "mass, rho and h must be finite and positive (particle " +
+                           std::to_string(i) + ")");
+    if (!isfinite(sigma0[i]) || sigma0[i] < 0)
+      return set_error(s, SPH_RT_EINVAL, "sigma0 must be finite and >= 0 (particle " +
+                                             std::to_string(i) + ")");
+    if (!isfinite(e0[i]) || !isfinite(E0[i]))
+      return set_error(s, SPH_RT_EINVAL, "non-finite initial energy at particle " +
+                                             std::to_string(i));
+    if (kind[i] < 0 || kind[i] > 2)
+      return set_error(s, SPH_RT_EINVAL, "kind out of range at particle " + std::to_string(i));
+    if (kind[i] == SPH_RT_INTERIOR) ++ni;
+    if (kind[i] == SPH_RT_COPY) {
+      if (!copy_of) return set_error(s, SPH_RT_EINVAL, "copy ghosts need copy_of");
+      int64_t c = copy_of[i];
+      if (c < 0 || c >= n || kind[c] != SPH_RT_INTERIOR)
+        return set_error(s, SPH_RT_EINVAL,
+                         "copy_of must name an interior particle (particle " + std::to_string(i) +
+                             ")");
+    }
+  }
+  if (ni == 0) return set_error(s, SPH_RT_EINVAL, "no interior particle");
+  *n_int = ni;
+  return SPH_RT_OK;
+}
+
+static sph_rt_status alloc_step_vectors(sph_rt *s) {
+  int64_t n = s->n, ni = s->n_int;
+  double **full[] = {&s->T, &s->sigma, &s->f, &s->R, &s->lambda, &s->D, &s->tmp_n, &s->tmp_n2,
+                     &s->tmp_n3, &s->e_bak, &s->E_bak, &s->stage_ge, &s->stage_gE};
+  for (double **p : full)
+    if (!(*p = dalloc<double>(s, n))) return SPH_RT_ENOMEM;
+  double **inner[] = {&s->e_old, &s->E_old, &s->e_l, &s->E_l, &s->e_new, &s->Qe, &s->QE, &s->b,
+                      &s->x, &s->r, &s->z, &s->p, &s->q, &s->w, &s->diag, &s->invdiag, &s->gb};
+  for (double **p : inner)
+    if (!(*p = dalloc<double>(s, ni))) return SPH_RT_ENOMEM;
+  if (!(s->gersh = dalloc<double>(s, 1))) return SPH_RT_ENOMEM;
+  SPH_CUDA(s, cudaMemsetAsync(s->Qe, 0, sizeof(double) * ni, s->stream));
+  SPH_CUDA(s, cudaMemsetAsync(s->QE, 0, sizeof(double) * ni, s->stream));
+  return SPH_RT_OK;
+}
+
+static sph_rt_status set_particles_common(sph_rt *s, int64_t n, const double *pos,
+                                          const double *mass, const double *rho, const double *h,
+                                          const double *sigma0, const int32_t *kind,
+                                          const int64_t *copy_of, const double *e0,
+                                          const double *E0, bool device) {
+  if (!s) return SPH_RT_EINVAL;
+  int64_t n_int = 0;
+  sph_rt_status rc;
+  if (!device) {
+    rc = validate_host_particles(s, n, pos, mass, rho, h, sigma0, kind, copy_of, e0, E0, &n_int);
+    if (rc) return rc;
+  }
+  if ((rc = ensure_cuda(s))) return rc;
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  if (device) {
+    if (n < 1 || n >= ((int64_t)1 << 31) - 1)
+      return set_error(s, SPH_RT_EINVAL, "n_total must be in [1, 2^31)");
+    if (!pos || !mass || !rho || !h || !sigma0 || !kind || !e0 || !E0)
+      return set_error(s, SPH_RT_EINVAL, "a required particle array is NULL");
+    rc = validate_device_particles(s, n, pos, mass, rho, h, sigma0, kind, copy_of, e0, E0, &n_int);
+    if (rc) return rc;
+  }
+  free_all(s);
+  s->err.clear();
+  const double *dpos = pos, *dm = mass, *dr = rho, *dh = h, *ds = sigma0, *de = e0, *dE = E0;
+  const int32_t *dk = kind;
+  const int64_t *dc = copy_of;
+  if (!device) {
+    // upload caller-order arrays into temporaries
+    double *b_pos = dalloc<double>(s, (size_t)n * s->dim);
+    double *b7 = dalloc<double>(s, (size_t)n * 6);
+    int32_t *b_kind = dalloc<int32_t>(s, n);
+    int64_t *b_copy = copy_of ? dalloc<int64_t>(s, n) : nullptr;
+    if (!b_pos || !b7 || !b_kind || (copy_of && !b_copy)) return SPH_RT_ENOMEM;
+    SPH_CUDA(s, cudaMemcpyAsync(b_pos, pos, sizeof(double) * n * s->dim, cudaMemcpyHostToDevice, s->stream));
+    const double *src[6] = {mass, rho, h, sigma0, e0, E0};
+    for (int k = 0; k < 6; ++k)
+      SPH_CUDA(s, cudaMemcpyAsync(b7 + (size_t)k * n, src[k], sizeof(double) * n,
+                                  cudaMemcpyHostToDevice, s->stream));
+    SPH_CUDA(s, cudaMemcpyAsync(b_kind, kind, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s->stream));
+    if (copy_of)
+      SPH_CUDA(s, cudaMemcpyAsync(b_copy, copy_of, sizeof(int64_t) * n, cudaMemcpyHostToDevice, s->stream));
+    dpos = b_pos;
+    dm = b7;
+    dr = b7 + n;
+    dh = b7 + 2 * n;
+    ds = b7 + 3 * n;
+    de = b7 + 4 * n;
+    dE = b7 + 5 * n;
+    dk = b_kind;
+    dc = b_copy;
+  }
+  rc = build_particles(s, n, dpos, dm, dr, dh, ds, dk, dc, de, dE, n_int);
+  if (rc) {
+    free_all(s);
+    return rc;
+  }
+  if ((rc = alloc_step_vectors(s))) {
+    free_all(s);
+    return rc;
+  }
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  s->have_particles = true;
+  s->have_operator = false;
+  s->amg_ready = false;
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_set_particles(sph_rt *s, int64_t n_total, const double *pos,
+                                              const double *mass, const double *rho,
+                                              const double *h, const double *sigma0,
+                                              const int32_t *kind, const int64_t *copy_of,
+                                              const double *e0, const double *E0) {
+  return set_particles_common(s, n_total, pos, mass, rho, h, sigma0, kind, copy_of, e0, E0, false);
+}
+
+extern "C" sph_rt_status sph_rt_set_particles_device(sph_rt *s, int64_t n_total,
+                                                     const double *pos, const double *mass,
+                                                     const double *rho, const double *h,
+                                                     const double *sigma0, const int32_t *kind,
+                                                     const int64_t *copy_of, const double *e0,
+                                                     const double *E0) {
+  return set_particles_common(s, n_total, pos, mass, rho, h, sigma0, kind, copy_of, e0, E0, true);
+}
+
+extern "C" sph_rt_status sph_rt_get_sizes(const sph_rt *s, int64_t *n_interior,
+                                          int64_t *nnz_neighbors, int64_t *nnz_operator) {
+  if (!s) return SPH_RT_EINVAL;
+  if (!s->have_particles) return SPH_RT_ESTATE;
+  if (n_interior) *n_interior = s->n_int;
+  if (nnz_neighbors) *nnz_neighbors = s->nnz_nbr;
+  if (nnz_operator) *nnz_operator = s->nnz_mat;
+  return SPH_RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// step
+// ---------------------------------------------------------------------------
+struct PhaseTimer {
+  sph_rt *s;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  void begin(int phase) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s->stream);
+    ev.push_back({phase, {a, b}});
+  }
+  void end() { cudaEventRecord(ev.back().second.second, s->stream); }
+  void collect(double *ms5) {
+    for (auto &p : ev) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p.second.first, p.second.second) == cudaSuccess)
+        ms5[p.first] += t;
+      cudaEventDestroy(p.second.first);
+      cudaEventDestroy(p.second.second);
+    }
+    ev.clear();
+  }
+  ~PhaseTimer() {
+    for (auto &p : ev) {
+      cudaEventDestroy(p.second.first);
+      cudaEventDestroy(p.second.second);
+    }
+  }
+};
+
+static sph_rt_status read_scalars(sph_rt *s) {
+  SPH_CUDA(s, cudaMemcpyAsync(s->sc_host, s->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  return SPH_RT_OK;
+}
+
+static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const double *QE_c,
+                                 const double *ge_c, const double *gE_c, sph_rt_stats *stats) {
+  sph_rt_status rc;
+  PhaseTimer tm{s, {}};
+  double ms[5] = {0, 0, 0, 0, 0};  // setup, assembly, amg, krylov, newton
+  sph_rt_stats st;
+  memset(&st, 0, sizeof st);
+  const int64_t ni = s->n_int;
+  const size_t nb = sizeof(double) * ni;
+
+  // energy before the step
+  if ((rc = launch_totals(s, s->e, s->E))) return rc;
+  if ((rc = read_scalars(s))) return rc;
+  st.energy_before = s->sc_host->red[4] + s->sc_host->red[5];
+
+  tm.begin(0);
+  // snapshot of the state (restored if the step does not converge)
+  SPH_CUDA(s, cudaMemcpyAsync(s->e_bak, s->e, sizeof(double) * s->n, cudaMemcpyDeviceToDevice, s->stream));
+  SPH_CUDA(s, cudaMemcpyAsync(s->E_bak, s->E, sizeof(double) * s->n, cudaMemcpyDeviceToDevice, s->stream));
+  // sources (interior, slot order)
+  if ((rc = launch_gather_interior(s, Qe_c, s->Qe))) return rc;
+  if ((rc = launch_gather_interior(s, QE_c, s->QE))) return rc;
+  // material data from the state at the start of the step (a3)
+  if ((rc = launch_properties(s, dt))) return rc;
+  // Dirichlet ghost values at t^n
+  if ((rc = launch_ghost_install(s, ge_c, gE_c))) return rc;
+  tm.end();
+
+  tm.begin(1);
+  if ((rc = launch_assembly(s, dt, s->gersh))) return rc;  // a4
+  tm.end();
+  double gersh = 0.0;
+  SPH_CUDA(s, cudaMemcpyAsync(&gersh, s->gersh, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  s->cheb_lmin = 1.0 - gersh;
+  s->cheb_lmax = 1.0 + gersh;
+  s->have_operator = true;
+
+  if (s->cfg.precond == SPH_RT_PRECOND_AMG) {  // a5
+    tm.begin(2);
+    if ((rc = amg_setup(s))) return rc;
+    tm.end();
+  }
+
+  // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}; material solve with E^{n,0}
+  SPH_CUDA(s, cudaMemcpyAsync(s->e_old, s->e, nb, cudaMemcpyDeviceToDevice, s->stream));
+  SPH_CUDA(s, cudaMemcpyAsync(s->E_old, s->E, nb, cudaMemcpyDeviceToDevice, s->stream));
+  SPH_CUDA(s, cudaMemcpyAsync(s->E_l, s->E, nb, cudaMemcpyDeviceToDevice, s->stream));
+  tm.begin(4);
+  if ((rc = launch_newton(s, dt, s->E_l, s->E_l, s->e_old, s->e_l))) return rc;  // a8
+  tm.end();
+  if ((rc = read_scalars(s))) return rc;
+  st.newton_iters_max = (int32_t)s->sc_host->red[2];
+
+  bool converged = false;
+  bool krylov_fail = false;
+  while (st.outer_iters < s->cfg.max_outer) {
+    tm.begin(3);
+    if ((rc = launch_rhs(s, dt))) return rc;  // a7 (also x = E^l)
+    int kit = 0;
+    bool kconv = false;
+    if ((rc = pcg_solve(s, &kit, &kconv))) return rc;  // a6
+    tm.end();
+    if (!kconv) {
+      krylov_fail = true;
+      break;
+    }
+    st.krylov_iters_per_outer[st.outer_iters] = kit;
+    st.krylov_iters_total += kit;
+    tm.begin(4);
+    if ((rc = launch_newton(s, dt, s->x, s->E_l, s->e_l, s->e_new))) return rc;  // a8
+    tm.end();
+    if ((rc = read_scalars(s))) return rc;  // a9
+    st.outer_iters++;
+    double ce = s->sc_host->red[0], cE = s->sc_host->red[1];
+    st.newton_iters_max = std::max(st.newton_iters_max, (int32_t)s->sc_host->red[2]);
+    std::swap(s->e_l, s->e_new);
+    std::swap(s->E_l, s->x);
+    st.last_change_e = ce;
+    st.last_change_E = cE;
+    if (ce < s->cfg.tol_outer_e && cE < s->cfg.tol_outer_E) {
+      converged = true;
+      break;
+    }
+  }
+
+  if (!converged) {
+    // restore the ghost values; interior state was never written
+    SPH_CUDA(s, cudaMemcpyAsync(s->e, s->e_bak, sizeof(double) * s->n, cudaMemcpyDeviceToDevice, s->stream));
+    SPH_CUDA(s, cudaMemcpyAsync(s->E, s->E_bak, sizeof(double) * s->n, cudaMemcpyDeviceToDevice, s->stream));
+    SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+    tm.collect(ms);
+    if (stats) *stats = st;
+    return set_error(s, SPH_RT_ENOTCONV,
+                     krylov_fail ? "Krylov solve did not converge (max_krylov or breakdown)"
+                                 : "outer iteration did not converge within max_outer");
+  }
+  if ((rc = launch_commit(s, s->e_l, s->E_l))) return rc;
+  if ((rc = launch_copy_sync(s))) return rc;
+  if ((rc = launch_balance(s, dt, s->E))) return rc;
+  if ((rc = read_scalars(s))) return rc;
+  st.source_energy = s->sc_host->red[6];
+  st.boundary_energy = s->sc_host->red[7];
+  if ((rc = launch_totals(s, s->e, s->E))) return rc;
+  if ((rc = read_scalars(s))) return rc;
+  st.energy_after = s->sc_host->red[4] + s->sc_host->red[5];
+  tm.collect(ms);
+  st.t_setup_ms = ms[0];
+  st.t_assembly_ms = ms[1];
+  st.t_amg_ms = ms[2];
+  st.t_krylov_ms = ms[3];
+  st.t_newton_ms = ms[4];
+  if (stats) *stats = st;
+  return SPH_RT_OK;
+}
+
+static sph_rt_status step_entry(sph_rt *s, double dt, const double *Qe, const double *QE,
+                                const double *ge, const double *gE, sph_rt_stats *stats,
+                                bool device) {
+  if (!s) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "step before set_particles");
+  if (!isfinite(dt) || dt <= 0.0) return set_error(s, SPH_RT_EINVAL, "dt must be finite and > 0");
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  const int64_t n = s->n;
+  if (!device) {
+    const double *arrs[4] = {Qe, QE, ge, gE};
+    for (int k = 0; k < 4; ++k) {
+      if (!arrs[k]) continue;
+      for (int64_t i = 0; i < n; ++i)
+        if (!isfinite(arrs[k][i]))
+          return set_error(s, SPH_RT_EINVAL, "non-finite source or ghost value at particle " +
+                                                 std::to_string(i));
+    }
+    // stage host arrays on the device (caller order)
+    double *stage[4] = {s->tmp_n, s->tmp_n2, s->stage_ge, s->stage_gE};
+    const double *dptr[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 4; ++k) {
+      if (!arrs[k]) continue;
+      SPH_CUDA(s, cudaMemcpyAsync(stage[k], arrs[k], sizeof(double) * n, cudaMemcpyHostToDevice,
+                                  s->stream));
+      dptr[k] = stage[k];
+    }
+    sph_rt_status rc = step_common(s, dt, dptr[0], dptr[1], dptr[2], dptr[3], stats);
+    return rc;
+  }
+  return step_common(s, dt, Qe, QE, ge, gE, stats);
+}
+
+extern "C" sph_rt_status sph_rt_step(sph_rt *s, double dt, const double *Qe, const double *QE,
+                                     const double *ghost_e, const double *ghost_E,
+                                     sph_rt_stats *stats) {
+  return step_entry(s, dt, Qe, QE, ghost_e, ghost_E, stats, false);
+}
+
+extern "C" sph_rt_status sph_rt_step_device(sph_rt *s, double dt, const double *Qe,
+                                            const double *QE, const double *ghost_e,
+                                            const double *ghost_E, sph_rt_stats *stats) {
+  return step_entry(s, dt, Qe, QE, ghost_e, ghost_E, stats, true);
+}
+
+// ---------------------------------------------------------------------------
+// read-out
+// ---------------------------------------------------------------------------
+extern "C" sph_rt_status sph_rt_get_energies_device(sph_rt *s, double *e, double *E) {
+  if (!s) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  sph_rt_status rc;
+  if (e && (rc = launch_scatter_caller(s, s->e, s->n, e))) return rc;
+  if (E && (rc = launch_scatter_caller(s, s->E, s->n, E))) return rc;
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_get_energies(sph_rt *s, double *e, double *E, double totals[2]) {
+  if (!s) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  sph_rt_status rc;
+  if ((rc = sph_rt_get_energies_device(s, e ? s->tmp_n : nullptr, E ? s->tmp_n2 : nullptr)))
+    return rc;
+  if (e) SPH_CUDA(s, cudaMemcpyAsync(e, s->tmp_n, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+  if (E) SPH_CUDA(s, cudaMemcpyAsync(E, s->tmp_n2, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+  if (totals) {
+    if ((rc = launch_totals(s, s->e, s->E))) return rc;
+    if ((rc = read_scalars(s))) return rc;
+    totals[0] = s->sc_host->red[4];
+    totals[1] = s->sc_host->red[5];
+  }
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  return SPH_RT_OK;
+}
+
+template <typename T>
+static sph_rt_status d2h(sph_rt *s, std::vector<T> &out, const T *src, int64_t count) {
+  out.resize((size_t)count);
+  if (count > 0)
+    SPH_CUDA(s, cudaMemcpyAsync(out.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost, s->stream));
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_get_neighbors(sph_rt *s, int64_t *rowptr, int64_t *cols) {
+  if (!s || !rowptr) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  std::vector<int64_t> s2c, ptr;
+  std::vector<int32_t> col;
+  sph_rt_status rc;
+  if ((rc = d2h(s, s2c, s->slot2caller, s->n))) return rc;
+  if ((rc = d2h(s, ptr, s->nbr_ptr, s->n_int + 1))) return rc;
+  if (cols && (rc = d2h(s, col, s->nbr_col, s->nnz_nbr))) return rc;
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  const int64_t n = s->n;
+  std::vector<int64_t> cnt((size_t)n, 0);
+  for (int64_t slot = 0; slot < s->n_int; ++slot) cnt[s2c[slot]] = ptr[slot + 1] - ptr[slot];
+  rowptr[0] = 0;
+  for (int64_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + cnt[i];
+  if (cols) {
+    for (int64_t slot = 0; slot < s->n_int; ++slot) {
+      int64_t c = s2c[slot];
+      int64_t *o = cols + rowptr[c];
+      for (int64_t k = ptr[slot]; k < ptr[slot + 1]; ++k) *o++ = s2c[col[k]];
+      std::sort(cols + rowptr[c], cols + rowptr[c + 1]);
+    }
+  }
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_get_operator(sph_rt *s, int64_t *rowptr, int64_t *cols,
+                                             double *vals, double *diag, double *gb) {
+  if (!s) return SPH_RT_EINVAL;
+  if (!s->have_particles || !s->have_operator)
+    return set_error(s, SPH_RT_ESTATE, "no operator assembled yet (call sph_rt_step first)");
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  std::vector<int64_t> s2c, ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val, dg, g, V;
+  sph_rt_status rc;
+  if ((rc = d2h(s, s2c, s->slot2caller, s->n))) return rc;
+  if ((rc = d2h(s, ptr, s->mat_ptr, s->n_int + 1))) return rc;
+  if ((rc = d2h(s, col, s->mat_col, s->nnz_mat))) return rc;
+  if ((rc = d2h(s, val, s->mat_val, s->nnz_mat))) return rc;
+  if ((rc = d2h(s, dg, s->diag, s->n_int))) return rc;
+  if ((rc = d2h(s, g, s->gb, s->n_int))) return rc;
+  if ((rc = d2h(s, V, s->V, s->n_int))) return rc;
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  const int64_t n = s->n;
+  std::vector<int64_t> cnt((size_t)n, 0);
+  for (int64_t slot = 0; slot < s->n_int; ++slot) cnt[s2c[slot]] = ptr[slot + 1] - ptr[slot];
+  std::vector<int64_t> rp((size_t)n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) rp[i + 1] = rp[i] + cnt[i];
+  if (rowptr) memcpy(rowptr, rp.data(), sizeof(int64_t) * (n + 1));
+  if (diag)
+    for (int64_t i = 0; i < n; ++i) diag[i] = 0.0;
+  if (gb)
+    for (int64_t i = 0; i < n; ++i) gb[i] = 0.0;
+  for (int64_t slot = 0; slot < s->n_int; ++slot) {
+    int64_t c = s2c[slot];
+    double invVi = 1.0 / V[slot];
+    for (int64_t k = ptr[slot]; k < ptr[slot + 1]; ++k) {
+      int64_t at = rp[c] + (k - ptr[slot]);
+      if (cols) cols[at] = s2c[col[k]];
+      if (vals) vals[at] = val[k] * invVi;
+    }
+    if (diag) diag[c] = dg[slot] * invVi;
+    if (gb) gb[c] = g[slot];
+  }
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_get_properties(sph_rt *s, double *T, double *sigma, double *f,
+                                               double *R, double *lambda, double *D) {
+  if (!s) return SPH_RT_EINVAL;
+  if (!s->have_particles || !s->have_operator)
+    return set_error(s, SPH_RT_ESTATE, "no step taken yet");
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  double *outs[6] = {T, sigma, f, R, lambda, D};
+  const double *srcs[6] = {s->T, s->sigma, s->f, s->R, s->lambda, s->D};
+  for (int k = 0; k < 6; ++k) {
+    if (!outs[k]) continue;
+    sph_rt_status rc = launch_scatter_caller(s, srcs[k], s->n, s->tmp_n);
+    if (rc) return rc;
+    SPH_CUDA(s, cudaMemcpyAsync(outs[k], s->tmp_n, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+    SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  }
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_kernel_stats(sph_rt *s, int64_t *launches, double *total_ms,
+                                             double *bytes, int reset) {
+  if (!s) return SPH_RT_EINVAL;
+  if (launches) *launches = s->spmv_launches;
+  if (total_ms) *total_ms = s->spmv_ms;
+  if (bytes) *bytes = s->spmv_bytes;
+  if (reset) {
+    s->spmv_launches = 0;
+    s->spmv_ms = 0.0;
+    s->spmv_bytes = 0.0;
+  }
+  return SPH_RT_OK;
+}

@@ -1,0 +1,307 @@
+"""Python binding of libsphrt (include/sph_rt.h): argument marshalling only.
+
+Every computation happens in the CUDA library.  Importing this module does not
+need a GPU; loading the library does (it links the CUDA runtime), and every
+call that touches the device fails loudly if the library or the GPU is missing.
+There is no CPU fallback.
+
+Function names follow the C ABI (`create`, `set_particles`, `step`,
+`get_energies`, ...).  Host arrays are numpy arrays; the `*_device` variants
+take raw device pointers (ints), e.g. `torch.Tensor.data_ptr()`.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ENOTCONV, EDEVICE, ESTATE = 0, -1, -2, -3, -4, -5
+INTERIOR, DIRICHLET, COPY = 0, 1, 2
+LIMITER_NONE, LIMITER_LEVERMORE, LIMITER_LARSEN = 0, 1, 2
+PRECOND_JACOBI, PRECOND_CHEBYSHEV, PRECOND_AMG = 0, 1, 2
+FP64, MIXED = 0, 1
+_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ENOTCONV: "ENOTCONV", EDEVICE: "EDEVICE",
+          ESTATE: "ESTATE"}
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32),
+        ("a", C.c_double), ("c", C.c_double), ("cv", C.c_double),
+        ("limiter", C.c_int32),
+        ("larsen_k", C.c_double),
+        ("opacity_exp", C.c_double),
+        ("T_floor", C.c_double),
+        ("tol_outer_e", C.c_double), ("tol_outer_E", C.c_double),
+        ("tol_inner_e", C.c_double), ("tol_krylov", C.c_double),
+        ("max_outer", C.c_int32), ("max_inner_e", C.c_int32), ("max_krylov", C.c_int32),
+        ("precond", C.c_int32),
+        ("precision", C.c_int32),
+        ("cheb_degree", C.c_int32),
+        ("amg_rebuild", C.c_int32),
+        ("amg_theta", C.c_double),
+        ("check_every", C.c_int32),
+        ("kernel_timing", C.c_int32),
+        ("device", C.c_int32),
+        ("stream", C.c_void_p),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("outer_iters", C.c_int32),
+        ("krylov_iters_total", C.c_int32),
+        ("krylov_iters_per_outer", C.c_int32 * 64),
+        ("newton_iters_max", C.c_int32),
+        ("energy_before", C.c_double), ("energy_after", C.c_double),
+        ("source_energy", C.c_double), ("boundary_energy", C.c_double),
+        ("last_change_e", C.c_double), ("last_change_E", C.c_double),
+        ("t_setup_ms", C.c_double), ("t_assembly_ms", C.c_double), ("t_amg_ms", C.c_double),
+        ("t_krylov_ms", C.c_double), ("t_newton_ms", C.c_double),
+    ]
+
+    def krylov_per_outer(self):
+        return list(self.krylov_iters_per_outer[: self.outer_iters])
+
+
+class SphRtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point in include/sph_rt.h
+_P = C.c_void_p
+_SIGNATURES = [
+    ("sph_rt_default_config", None, [_P]),
+    ("sph_rt_create", C.c_int, [_P, _P]),
+    ("sph_rt_set_particles", C.c_int, [_P, C.c_int64] + [_P] * 9),
+    ("sph_rt_set_particles_device", C.c_int, [_P, C.c_int64] + [_P] * 9),
+    ("sph_rt_step", C.c_int, [_P, C.c_double, _P, _P, _P, _P, _P]),
+    ("sph_rt_step_device", C.c_int, [_P, C.c_double, _P, _P, _P, _P, _P]),
+    ("sph_rt_get_energies", C.c_int, [_P, _P, _P, _P]),
+    ("sph_rt_get_energies_device", C.c_int, [_P, _P, _P]),
+    ("sph_rt_get_sizes", C.c_int, [_P, _P, _P, _P]),
+    ("sph_rt_get_neighbors", C.c_int, [_P, _P, _P]),
+    ("sph_rt_get_operator", C.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("sph_rt_get_properties", C.c_int, [_P] * 7),
+    ("sph_rt_kernel_stats", C.c_int, [_P, _P, _P, _P, C.c_int]),
+    ("sph_rt_launch_count", C.c_int64, [_P]),
+    ("sph_rt_last_error", C.c_char_p, [_P]),
+    ("sph_rt_destroy", None, [_P]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsphrt.so (building it first if needed).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsphrt.so not found at {path}; run paper_2001_11606_gb300.build")
+    L = C.CDLL(path)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    return [name for name, _, _ in _SIGNATURES]
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _f64(a, n=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def default_config(**overrides) -> Config:
+    cfg = Config()
+    load().sph_rt_default_config(C.byref(cfg))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Solver:
+    """One handle of the library (see sph_rt.h for the semantics of each call)."""
+
+    def __init__(self, cfg: Config | None = None, **overrides):
+        self._L = load()
+        cfg = cfg or default_config()
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        h = C.c_void_p()
+        rc = self._L.sph_rt_create(C.byref(cfg), C.byref(h))
+        if rc != OK:
+            raise SphRtError(rc, self._L.sph_rt_last_error(None).decode())
+        self._h = h
+        self.n = 0
+
+    # -- plumbing --------------------------------------------------------------
+    def _check(self, rc):
+        if rc != OK:
+            raise SphRtError(rc, self.last_error())
+        return rc
+
+    def last_error(self) -> str:
+        return self._L.sph_rt_last_error(self._h).decode()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.sph_rt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- C ABI -----------------------------------------------------------------
+    def set_particles(self, pos, mass, rho, h, sigma0, kind, copy_of, e0, E0):
+        pos = _f64(pos)
+        n = pos.shape[0] if pos.ndim == 2 else pos.size // self.cfg.dim
+        kind = np.ascontiguousarray(kind, dtype=np.int32)
+        copy_of = None if copy_of is None else np.ascontiguousarray(copy_of, dtype=np.int64)
+        arrs = [_f64(a, n) for a in (mass, rho, h, sigma0)]
+        e0, E0 = _f64(e0, n), _f64(E0, n)
+        rc = self._L.sph_rt_set_particles(self._h, n, _ptr(pos), *[_ptr(a) for a in arrs],
+                                          _ptr(kind), _ptr(copy_of), _ptr(e0), _ptr(E0))
+        self._check(rc)
+        self.n = n
+        return rc
+
+    def set_particles_device(self, n, pos, mass, rho, h, sigma0, kind, copy_of, e0, E0):
+        ptrs = [C.c_void_p(p) if p else None for p in (pos, mass, rho, h, sigma0, kind, copy_of,
+                                                      e0, E0)]
+        self._check(self._L.sph_rt_set_particles_device(self._h, int(n), *ptrs))
+        self.n = int(n)
+
+    def step(self, dt, Qe=None, QE=None, ghost_e=None, ghost_E=None, raise_on_error=True):
+        st = Stats()
+        arrs = [_f64(a, self.n) for a in (Qe, QE, ghost_e, ghost_E)]
+        rc = self._L.sph_rt_step(self._h, float(dt), *[_ptr(a) for a in arrs], C.byref(st))
+        if raise_on_error:
+            self._check(rc)
+        return rc, st
+
+    def step_host_ptrs(self, dt, Qe=0, QE=0, ghost_e=0, ghost_E=0):
+        """Step with raw HOST pointers (e.g. pinned torch tensors)."""
+        st = Stats()
+        ptrs = [C.c_void_p(p) if p else None for p in (Qe, QE, ghost_e, ghost_E)]
+        self._check(self._L.sph_rt_step(self._h, float(dt), *ptrs, C.byref(st)))
+        return st
+
+    def step_device(self, dt, Qe=0, QE=0, ghost_e=0, ghost_E=0, raise_on_error=True):
+        st = Stats()
+        ptrs = [C.c_void_p(p) if p else None for p in (Qe, QE, ghost_e, ghost_E)]
+        rc = self._L.sph_rt_step_device(self._h, float(dt), *ptrs, C.byref(st))
+        if raise_on_error:
+            self._check(rc)
+        return rc, st
+
+    def get_energies(self):
+        e = np.empty(self.n)
+        E = np.empty(self.n)
+        tot = np.empty(2)
+        self._check(self._L.sph_rt_get_energies(self._h, _ptr(e), _ptr(E), _ptr(tot)))
+        return e, E, tot
+
+    def get_energies_host_ptrs(self, e_ptr, E_ptr):
+        self._check(self._L.sph_rt_get_energies(self._h, C.c_void_p(e_ptr), C.c_void_p(E_ptr),
+                                                None))
+
+    def get_energies_device(self, e_ptr, E_ptr):
+        self._check(self._L.sph_rt_get_energies_device(self._h, C.c_void_p(e_ptr) if e_ptr else None,
+                                                       C.c_void_p(E_ptr) if E_ptr else None))
+
+    def sizes(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self._L.sph_rt_get_sizes(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def get_neighbors(self):
+        rowptr = np.zeros(self.n + 1, dtype=np.int64)
+        self._check(self._L.sph_rt_get_neighbors(self._h, _ptr(rowptr), None))
+        cols = np.zeros(max(int(rowptr[-1]), 1), dtype=np.int64)
+        self._check(self._L.sph_rt_get_neighbors(self._h, _ptr(rowptr), _ptr(cols)))
+        return rowptr, cols[: rowptr[-1]]
+
+    def get_operator(self):
+        _, _, nnz = self.sizes()
+        rowptr = np.zeros(self.n + 1, dtype=np.int64)
+        cols = np.zeros(max(nnz, 1), dtype=np.int64)
+        vals = np.zeros(max(nnz, 1))
+        diag = np.zeros(self.n)
+        gb = np.zeros(self.n)
+        self._check(self._L.sph_rt_get_operator(self._h, _ptr(rowptr), _ptr(cols), _ptr(vals),
+                                                _ptr(diag), _ptr(gb)))
+        return rowptr, cols[:nnz], vals[:nnz], diag, gb
+
+    def get_properties(self):
+        out = {k: np.zeros(self.n) for k in ("T", "sigma", "f", "R", "lambda", "D")}
+        self._check(self._L.sph_rt_get_properties(self._h, *[_ptr(out[k]) for k in
+                                                             ("T", "sigma", "f", "R", "lambda",
+                                                              "D")]))
+        return out
+
+    def kernel_stats(self, reset=False):
+        n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+        self._check(self._L.sph_rt_kernel_stats(self._h, C.byref(n), C.byref(ms), C.byref(by),
+                                                int(reset)))
+        return n.value, ms.value, by.value
+
+    def launch_count(self) -> int:
+        return int(self._L.sph_rt_launch_count(self._h))
+
+
+def config_from_params(params: dict, **overrides) -> Config:
+    """Config from a workload parameter dict (inputs.Workload.params)."""
+    cfg = default_config()
+    for k, v in params.items():
+        if hasattr(cfg, k):
+            setattr(cfg, k, v)
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def solver_for(workload, **overrides) -> Solver:
+    """Solver with the workload's particles set (host arrays)."""
+    P = workload.particles
+    S = Solver(config_from_params(workload.params, **overrides))
+    S.set_particles(P.pos, P.mass, P.rho, P.h, P.sigma0, P.kind,
+                    P.copy_of if np.any(P.kind == COPY) else None, workload.e0, workload.E0)
+    return S

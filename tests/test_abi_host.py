@@ -1,0 +1,105 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol declared in include/sph_rt.h, and rejects invalid input on the host
+before any device work."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2001_11606_gb300 import inputs as I
+from paper_2001_11606_gb300 import sphrt
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "sph_rt.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sph_rt_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = sphrt.load()
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(L, name), name
+    assert sorted(sphrt.exported_symbols()) == names
+
+
+def test_config_struct_matches_defaults():
+    cfg = sphrt.default_config()
+    assert cfg.dim == 3 and cfg.a == 1.0 and cfg.precond == sphrt.PRECOND_AMG
+    assert cfg.tol_outer_e == 1e-8 and cfg.tol_krylov == 1e-12 and cfg.tol_inner_e == 1e-13
+
+
+@pytest.mark.parametrize("field,value", [("dim", 4), ("cv", 0.0), ("limiter", 7),
+                                         ("tol_krylov", -1.0), ("max_outer", 0),
+                                         ("precond", 9), ("cheb_degree", 0),
+                                         ("amg_theta", 1.5)])
+def test_create_rejects_bad_config(field, value):
+    cfg = sphrt.default_config(**{field: value})
+    with pytest.raises(sphrt.SphRtError) as ei:
+        sphrt.Solver(cfg)
+    assert ei.value.status == sphrt.EINVAL
+    assert str(ei.value)
+
+
+def _particles():
+    return I.make_lattice(2, (4, 4), 0.25, seed=1)
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda P, e, E: P.mass.__setitem__(3, -1.0), "mass"),
+    (lambda P, e, E: P.h.__setitem__(0, 0.0), "mass, rho and h"),
+    (lambda P, e, E: P.pos.__setitem__((2, 1), np.nan), "position"),
+    (lambda P, e, E: P.kind.__setitem__(5, 9), "kind"),
+    (lambda P, e, E: P.sigma0.__setitem__(1, -2.0), "sigma0"),
+    (lambda P, e, E: E.__setitem__(4, np.inf), "initial energy"),
+])
+def test_set_particles_rejects_bad_input_on_host(mutate, msg):
+    P = _particles()
+    e = np.ones(P.n)
+    E = np.ones(P.n)
+    mutate(P, e, E)
+    S = sphrt.Solver(sphrt.default_config(dim=2))
+    with pytest.raises(sphrt.SphRtError) as ei:
+        S.set_particles(P.pos, P.mass, P.rho, P.h, P.sigma0, P.kind, None, e, E)
+    assert ei.value.status == sphrt.EINVAL and msg in str(ei.value)
+    S.close()
+
+
+def test_copy_ghost_must_point_at_interior():
+    P = I.make_lattice(2, (4, 4), 0.25, seed=1, faces=[("reflect", "reflect")] * 2)
+    c = np.flatnonzero(P.kind == sphrt.COPY)[0]
+    bad = P.copy_of.copy()
+    bad[c] = c  # a ghost, not an interior particle
+    S = sphrt.Solver(sphrt.default_config(dim=2))
+    with pytest.raises(sphrt.SphRtError) as ei:
+        S.set_particles(P.pos, P.mass, P.rho, P.h, P.sigma0, P.kind, bad, np.ones(P.n),
+                        np.ones(P.n))
+    assert "copy_of" in str(ei.value)
+    with pytest.raises(sphrt.SphRtError):
+        S.set_particles(P.pos, P.mass, P.rho, P.h, P.sigma0, P.kind, None, np.ones(P.n),
+                        np.ones(P.n))
+    S.close()
+
+
+def test_step_before_particles_is_a_state_error():
+    S = sphrt.Solver(sphrt.default_config(dim=2))
+    with pytest.raises(sphrt.SphRtError) as ei:
+        S.step(1e-3)
+    assert ei.value.status == sphrt.ESTATE
+    S.close()
+
+
+def test_no_interior_particle():
+    P = _particles()
+    kind = np.full(P.n, sphrt.DIRICHLET, dtype=np.int32)
+    S = sphrt.Solver(sphrt.default_config(dim=2))
+    with pytest.raises(sphrt.SphRtError) as ei:
+        S.set_particles(P.pos, P.mass, P.rho, P.h, P.sigma0, kind, None, np.ones(P.n),
+                        np.ones(P.n))
+    assert "interior" in str(ei.value)
+    S.close()

@@ -1,0 +1,305 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: neighbour lists bit-exact; material data and operator entries
+1e-13 relative (same formulas, different rounding order); FP64 energies after
+full steps 1e-10 relative (both sides converge to the same discrete fixed
+point; parity runs tighten the Krylov and outer tolerances on both sides so
+that the iteration error is far below that); the mixed-precision form 1e-8.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2001_11606_gb300 import inputs as I
+from paper_2001_11606_gb300 import sphrt
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(tol_krylov=1e-14, tol_outer_e=1e-12, tol_outer_E=1e-12, tol_inner_e=1e-14)
+
+
+def rel_err(a, b, mask):
+    return float(np.max(np.abs(a[mask] - b[mask]) / np.maximum(np.abs(b[mask]), 1e-300)))
+
+
+def run_both(w, steps, gpu_over=None, orc_over=None, check=True):
+    gpu_over = dict(gpu_over or {})
+    prm = dict(w.params, **(orc_over or {}))
+    S = sphrt.solver_for(w, **dict(prm, **gpu_over))
+    pb = O.Problem(w.particles, prm)
+    e, E = w.e0.copy(), w.E0.copy()
+    gstats, ostats = [], []
+    for n in range(1, steps + 1):
+        Qe, QE, ge, gE = w.step_inputs(n)
+        rc, st = S.step(w.dt, Qe, QE, ge, gE)
+        gstats.append(st)
+        rc, e, E, so = pb.step(e, E, w.dt, Qe, QE, ge, gE)
+        assert rc == 0
+        ostats.append(so)
+    eg, Eg, tot = S.get_energies()
+    m = w.particles.kind == 0
+    out = dict(err_e=rel_err(eg, e, m), err_E=rel_err(Eg, E, m), S=S, pb=pb, gstats=gstats,
+               ostats=ostats, e=e, E=E, eg=eg, Eg=Eg, tot=tot)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# a1-a2: neighbour lists
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("make", [lambda: I.mms_2d(n=32), lambda: I.mms_3d_lp(n=12),
+                                  lambda: I.heating_wave(2, 3000, 5.0, seed=9),
+                                  lambda: I.heating_wave(3, 3000, 5.0, seed=9)])
+def test_neighbors_bit_exact(make):
+    w = make()
+    P = w.particles
+    S = sphrt.solver_for(w)
+    rp, cols = S.get_neighbors()
+    orp, ocols = O.neighbors(P.pos, P.h, P.kind)
+    assert np.array_equal(rp, orp)
+    assert np.array_equal(cols, ocols.astype(np.int64))
+
+
+def test_neighbors_bit_exact_varied_h():
+    w = I.mms_3d_lp(n=10)
+    P = w.particles
+    rng = np.random.default_rng(4)
+    P.h = P.h * rng.uniform(0.7, 1.3, P.n)
+    S = sphrt.solver_for(w)
+    rp, cols = S.get_neighbors()
+    orp, ocols = O.neighbors(P.pos, P.h, P.kind)
+    assert np.array_equal(rp, orp) and np.array_equal(cols, ocols.astype(np.int64))
+
+
+def test_neighbors_unjittered_lattice_edge_cases():
+    # pairs at exactly r = 2h must be excluded on both sides (strict inequality)
+    P = I.make_lattice(3, (9, 7, 5), 1.0 / 64, seed=0, jitter=0.0)
+    w = I.Workload("lattice", P, I.mms_3d_lp(n=4).params, 1e-3, 1, e0=np.ones(P.n),
+                   E0=np.ones(P.n))
+    S = sphrt.solver_for(w)
+    rp, cols = S.get_neighbors()
+    orp, ocols = O.neighbors(P.pos, P.h, P.kind)
+    assert np.array_equal(rp, orp) and np.array_equal(cols, ocols.astype(np.int64))
+    interior = np.flatnonzero(P.kind == 0)
+    assert np.all(np.diff(rp)[interior] == 92)
+
+
+def test_single_interior_particle_without_neighbours():
+    P = I.make_lattice(1, (1,), 1.0, seed=0)
+    keep = P.kind == 0
+    P1 = I.Particles(dim=1, dx=1.0, counts=(1,), pos=P.pos[keep], kind=P.kind[keep],
+                     copy_of=P.copy_of[keep], mass=P.mass[keep], rho=P.rho[keep],
+                     h=P.h[keep], sigma0=P.sigma0[keep])
+    prm = dict(dim=1, tol_outer_e=1e-12, tol_outer_E=1e-12, tol_krylov=1e-14,
+               tol_inner_e=1e-14)
+    w = I.Workload("one", P1, prm, 0.1, 3, e0=np.array([1.0]), E0=np.array([1e-16]))
+    r = run_both(w, 3)
+    assert r["err_e"] < 1e-12 and r["err_E"] < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# a3-a4: material data and operator of one step
+# ---------------------------------------------------------------------------
+def _operator_dict(rowptr, cols, vals, diag):
+    d = {}
+    for i in range(len(rowptr) - 1):
+        for k in range(rowptr[i], rowptr[i + 1]):
+            key = (i, int(cols[k]))
+            d[key] = d.get(key, 0.0) + vals[k]
+    return d
+
+
+@pytest.mark.parametrize("make", [lambda: I.mms_2d(n=16), lambda: I.mms_3d_lp(n=8),
+                                  lambda: I.heating_wave(2, 1200, 30.0, seed=3)])
+def test_properties_and_operator_match_oracle(make):
+    w = make()
+    P = w.particles
+    S = sphrt.solver_for(w, precond=sphrt.PRECOND_JACOBI)
+    Qe, QE, ge, gE = w.step_inputs(1)
+    S.step(w.dt, Qe, QE, ge, gE)
+    pg = S.get_properties()
+    pb = O.Problem(P, w.params)
+    po = pb.properties(w.e0, w.E0, w.dt)
+    live = P.kind != sphrt.COPY
+    for k in ("T", "sigma", "f", "R", "lambda", "D"):
+        np.testing.assert_allclose(pg[k][live], po[k][live], rtol=1e-13, atol=1e-300, err_msg=k)
+    # operator of Eq. diffusion-solve, with the Dirichlet ghost values at t^1
+    Eg = w.E0.copy()
+    Eg[P.kind == sphrt.DIRICHLET] = gE[P.kind == sphrt.DIRICHLET]
+    arow, acol, aval, adiag, gb = pb.assemble(po, w.dt, Eg)
+    rowptr, cols, vals, diag, ggb = S.get_operator()
+    m = P.kind == 0
+    np.testing.assert_allclose(diag[m], adiag[m], rtol=1e-13)
+    np.testing.assert_allclose(ggb[m], gb[m], rtol=1e-12, atol=1e-12 * np.max(np.abs(gb)))
+    dg = _operator_dict(rowptr, cols, vals, diag)
+    do = _operator_dict(arow, acol, aval, adiag)
+    # self-copy entries fold into the diagonal on both sides
+    dg = {k: v for k, v in dg.items() if k[0] != k[1]}
+    assert set(dg) == set(do)
+    a = np.array([dg[k] for k in sorted(do)])
+    b = np.array([do[k] for k in sorted(do)])
+    np.testing.assert_allclose(a, b, rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# a5-a9: full steps
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precond", [sphrt.PRECOND_JACOBI, sphrt.PRECOND_CHEBYSHEV,
+                                     sphrt.PRECOND_AMG])
+def test_mms2d_full_run_parity(precond):
+    # 2-D manufactured problem, 1,024 particles, 10 steps of dt = 1e-3
+    w = I.mms_2d()
+    r = run_both(w, w.steps, gpu_over=dict(precond=precond), orc_over=TIGHT)
+    assert r["err_e"] < 1e-10 and r["err_E"] < 1e-10, (r["err_e"], r["err_E"])
+    for g, o in zip(r["gstats"], r["ostats"]):
+        assert g.outer_iters == o.outer_iters
+
+
+def test_mms2d_parity_at_workload_tolerances():
+    # the workload's own tolerances (outer 1e-10, Krylov 1e-12) on both sides
+    w = I.mms_2d()
+    r = run_both(w, w.steps)
+    assert r["err_e"] < 1e-10 and r["err_E"] < 1e-10, (r["err_e"], r["err_E"])
+
+
+@pytest.mark.parametrize("precond", [sphrt.PRECOND_CHEBYSHEV, sphrt.PRECOND_AMG])
+def test_mms3d_levermore_parity(precond):
+    w = I.mms_3d_lp(n=16, steps=3)
+    r = run_both(w, 3, gpu_over=dict(precond=precond), orc_over=TIGHT)
+    assert r["err_e"] < 1e-10 and r["err_E"] < 1e-10, (r["err_e"], r["err_E"])
+
+
+def test_heating_wave_copy_ghosts_parity():
+    w = I.heating_wave(3, 4000, 10.0, seed=21, steps=3)
+    r = run_both(w, 3, orc_over=TIGHT)
+    assert r["err_e"] < 1e-10 and r["err_E"] < 1e-10, (r["err_e"], r["err_E"])
+
+
+def test_energy_balance_on_gpu():
+    w = I.mms_2d(n=32, steps=3)
+    r = run_both(w, 3, orc_over=TIGHT)
+    for g, o in zip(r["gstats"], r["ostats"]):
+        defect = g.energy_after - g.energy_before - g.source_energy - g.boundary_energy
+        assert abs(defect) < 1e-11 * g.energy_after
+        assert abs(g.energy_after - o.energy_after) < 1e-12 * o.energy_after
+
+
+def test_mixed_precision_parity():
+    w = I.mms_3d_lp(n=16, steps=3)
+    r = run_both(w, 3, gpu_over=dict(precision=sphrt.MIXED, precond=sphrt.PRECOND_AMG),
+                 orc_over=TIGHT)
+    assert r["err_e"] < 1e-8 and r["err_E"] < 1e-8, (r["err_e"], r["err_E"])
+
+
+# ---------------------------------------------------------------------------
+# determinism, restart, failure handling, device entry points
+# ---------------------------------------------------------------------------
+def test_repeat_is_bitwise_identical():
+    w = I.mms_3d_lp(n=12, steps=2)
+    outs = []
+    for _ in range(2):
+        S = sphrt.solver_for(w)
+        for n in (1, 2):
+            S.step(w.dt, *w.step_inputs(n))
+        outs.append(S.get_energies())
+        S.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_restart_continues_bitwise():
+    w = I.mms_2d(n=16, steps=3)
+    P = w.particles
+    S = sphrt.solver_for(w, amg_rebuild=1)
+    for n in (1, 2, 3):
+        S.step(w.dt, *w.step_inputs(n))
+    e3, E3, _ = S.get_energies()
+    S2 = sphrt.solver_for(w, amg_rebuild=1)
+    for n in (1, 2):
+        S2.step(w.dt, *w.step_inputs(n))
+    e2, E2, _ = S2.get_energies()
+    S3 = sphrt.Solver(sphrt.config_from_params(w.params, amg_rebuild=1))
+    S3.set_particles(P.pos, P.mass, P.rho, P.h, P.sigma0, P.kind, None, e2, E2)
+    S3.step(w.dt, *w.step_inputs(3))
+    e3b, E3b, _ = S3.get_energies()
+    assert np.array_equal(e3, e3b) and np.array_equal(E3, E3b)
+
+
+def test_not_converged_leaves_state_unchanged():
+    w = I.mms_2d(n=16)
+    S = sphrt.solver_for(w, max_outer=1, tol_outer_e=1e-15, tol_outer_E=1e-15)
+    e0, E0, _ = S.get_energies()
+    rc, st = S.step(w.dt, *w.step_inputs(1), raise_on_error=False)
+    assert rc == sphrt.ENOTCONV
+    e1, E1, _ = S.get_energies()
+    assert np.array_equal(e0, e1) and np.array_equal(E0, E1)
+    # Krylov limit too
+    S2 = sphrt.solver_for(w, max_krylov=1, precond=sphrt.PRECOND_JACOBI)
+    rc, st = S2.step(w.dt, *w.step_inputs(1), raise_on_error=False)
+    assert rc == sphrt.ENOTCONV and "Krylov" in S2.last_error()
+
+
+def test_device_entry_points_match_host():
+    torch = pytest.importorskip("torch")
+    w = I.mms_2d(n=16, steps=2)
+    P = w.particles
+    S = sphrt.solver_for(w)
+    for n in (1, 2):
+        S.step(w.dt, *w.step_inputs(n))
+    eh, Eh, _ = S.get_energies()
+    dev = torch.device("cuda:0")
+    T = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    arrs = [T(P.pos), T(P.mass), T(P.rho), T(P.h), T(P.sigma0), T(P.kind, torch.int32), None,
+            T(w.e0), T(w.E0)]
+    S2 = sphrt.Solver(sphrt.config_from_params(w.params))
+    torch.cuda.synchronize()
+    S2.set_particles_device(P.n, *[a.data_ptr() if a is not None else 0 for a in arrs])
+    for n in (1, 2):
+        ins = [T(a) for a in w.step_inputs(n)]
+        torch.cuda.synchronize()
+        S2.step_device(w.dt, *[a.data_ptr() for a in ins])
+    e_out = torch.empty(P.n, dtype=torch.float64, device=dev)
+    E_out = torch.empty(P.n, dtype=torch.float64, device=dev)
+    S2.get_energies_device(e_out.data_ptr(), E_out.data_ptr())
+    S2_e, S2_E, _ = S2.get_energies()
+    assert np.array_equal(S2_e, eh) and np.array_equal(S2_E, Eh)
+    torch.cuda.synchronize()
+    assert np.array_equal(e_out.cpu().numpy(), eh)
+
+
+# ---------------------------------------------------------------------------
+# the benchmark's workload at full size: 64^3 manufactured problem, Levermore
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def full_size():
+    w = I.mms_3d_lp(n=64, steps=100)
+    S = sphrt.solver_for(w)
+    return w, S
+
+
+def test_full_size_neighbors_sampled(full_size):
+    w, S = full_size
+    P = w.particles
+    rp, cols = S.get_neighbors()
+    rng = np.random.default_rng(0)
+    interior = np.flatnonzero(P.kind == 0)
+    rows = np.concatenate([rng.choice(interior, 48, replace=False), interior[:8], interior[-8:]])
+    orp, ocols = O.neighbors_of_rows(P.pos, P.h, rows)
+    for k, i in enumerate(rows):
+        assert np.array_equal(cols[rp[i]:rp[i + 1]], ocols[orp[k]:orp[k + 1]].astype(np.int64))
+    n_int, nnz_nbr, nnz_op = S.sizes()
+    assert n_int == 64**3 and 28_000_000 < nnz_nbr < 31_000_000
+
+
+def test_full_size_two_steps_match_oracle(full_size):
+    w, S = full_size
+    prm = dict(w.params, **TIGHT)
+    S2 = sphrt.solver_for(w, **TIGHT)
+    pb = O.Problem(w.particles, prm)
+    e, E = w.e0.copy(), w.E0.copy()
+    for n in (1, 2):
+        ins = w.step_inputs(n)
+        S2.step(w.dt, *ins)
+        rc, e, E, _ = pb.step(e, E, w.dt, *ins)
+        assert rc == 0
+    eg, Eg, _ = S2.get_energies()
+    m = w.particles.kind == 0
+    assert rel_err(eg, e, m) < 1e-10 and rel_err(Eg, E, m) < 1e-10
