@@ -171,6 +171,68 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Serving stream: Poisson arrivals of heating-wave problems (2-D/3-D,
+    1k..256k particles, 20 steps each) through the continuous-batching loop.
+    Measures the saturated service rate mu (all requests queued at once), then
+    replays the stream at 0.5, 0.8 and 1.2 mu and reports p50/p99 latency."""
+    from paper_2001_11606_gb300 import sphrt
+
+    n_req = args.requests
+    descs = I.serving_stream(n_req, seed=4)
+    problems = []
+    for d in descs:
+        w = I.heating_wave(d["dim"], d["n_target"], d["sigma0"], seed=d["seed"], steps=20)
+        problems.append(w)
+    total_ps = sum(w.particles.n_interior * w.steps for w in problems)
+    cfgs = [sphrt.config_from_params(w.params) for w in problems]
+
+    def play(rate, workers):
+        srv = sphrt.Server(workers=workers, max_resident=args.max_resident,
+                           hbm_budget_bytes=120e9)
+        gaps = np.diff([0.0] + [d["arrival"] for d in descs])  # mean 1
+        t0 = time.perf_counter()
+        ids, t_arr = [], []
+        t_next = t0
+        for k, w in enumerate(problems):
+            if rate is not None:
+                t_next += gaps[k] / rate
+                delay = t_next - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            t_arr.append(time.perf_counter())
+            ids.append(srv.submit(cfgs[k], w.particles, w.e0, w.E0, w.steps, w.dt))
+        lat = []
+        for k, rid in enumerate(ids):
+            rc = srv.wait(rid)
+            if rc != sphrt.OK:
+                raise RuntimeError(f"request {k} failed: {rc}")
+            st, t = srv.poll(rid)
+            lat.append(t[2] - t[1] + (t[1] - t[0]))  # done - submit
+        info = srv.info()
+        makespan = info.t_last_done - info.t_first_submit
+        srv.close()
+        lat = np.array(lat)
+        return dict(p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+                    mean_s=float(lat.mean()), makespan_s=makespan,
+                    throughput=total_ps / makespan, req_per_s=n_req / makespan,
+                    peak_resident=info.peak_resident, peak_bytes=info.peak_bytes)
+
+    sat = play(None, args.workers)
+    mu = sat["req_per_s"]
+    loads = {}
+    for f in (0.5, 0.8, 1.2):
+        loads[str(f)] = play(f * mu, args.workers)
+    line = {"metric": "serving p99 latency", "value": loads["0.8"]["p99_s"], "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"serving stream: {n_req} heating-wave requests, 2-D/3-D, "
+                                   "1k..256k particles, 20 steps of dt = 1e-3",
+                       "workers": args.workers, "max_resident": args.max_resident,
+                       "hbm_budget_bytes": 120e9, "particle_steps": total_ps},
+            "saturated": sat, "mu_req_per_s": mu, "loads": loads}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,7 +246,13 @@ def main():
     ap.add_argument("--precond", default="amg", choices=["jacobi", "chebyshev", "amg"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--requests", type=int, default=512, help="serving: number of requests")
+    ap.add_argument("--workers", type=int, default=8, help="serving: worker threads")
+    ap.add_argument("--max-resident", type=int, default=32, help="serving: resident cap")
     args = ap.parse_args()
+    if args.workload == "serving":
+        run_serving(args)
+        return
 
     w = make_workload(args.workload)
     if args.time_steps:

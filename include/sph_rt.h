@@ -78,7 +78,7 @@ typedef struct {
   int32_t precision;    /* SPH_RT_FP64 or SPH_RT_MIXED */
   int32_t cheb_degree;  /* Chebyshev smoother / preconditioner degree (>= 1) */
   int32_t amg_rebuild;  /* 1: redo AMG aggregation every step; 0: keep the first step's */
-  double amg_theta;     /* AMG strength threshold */
+  double amg_theta;     /* AMG strength threshold: j strong for i if |B_ij| >= theta sqrt(B_ii B_jj) */
   int32_t check_every;  /* Krylov iterations queued between host convergence reads */
   int32_t kernel_timing;/* 1: record CUDA events around SpMV launches (sph_rt_kernel_stats) */
   int32_t device;       /* CUDA device ordinal */
@@ -101,7 +101,8 @@ typedef struct {
 
 /* Fill *cfg with defaults: dim 3, a = c = c_v = 1, no limiter, p = 0,
  * tolerances of Table tab:tolerances (manufactured problem row) with
- * tol_inner_e = 1e-13, AMG preconditioner, FP64, device 0, own stream. */
+ * tol_inner_e = 1e-13, AMG preconditioner (theta 0.02, Chebyshev degree 2),
+ * FP64, device 0, own stream. */
 void sph_rt_default_config(sph_rt_config *cfg);
 
 /* Create a handle.  No device work happens until sph_rt_set_particles.
@@ -193,8 +194,79 @@ sph_rt_status sph_rt_get_properties(sph_rt *s, double *T, double *sigma, double 
 sph_rt_status sph_rt_kernel_stats(sph_rt *s, int64_t *launches, double *total_ms,
                                   double *bytes, int reset);
 
+/* AMG hierarchy of the last step: number of levels, and rows and stored
+ * off-diagonal nonzeros per level (arrays of max_levels entries, may be NULL). */
+sph_rt_status sph_rt_get_amg_info(sph_rt *s, int32_t *nlevels, int64_t *rows, int64_t *nnz,
+                                  int32_t max_levels);
+
 /* Number of this library's kernels launched since creation (all kinds). */
 int64_t sph_rt_launch_count(const sph_rt *s);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: a continuous-batching request loop over many independent        */
+/* problems on one GPU.  This is a runtime around the calls above, not part */
+/* of the paper's method (the paper runs one problem at a time).            */
+/*                                                                          */
+/* Every admitted request is resident on the device in its own handle and   */
+/* stream; worker threads advance resident requests `steps_per_tick` steps  */
+/* at a time, so the work of different requests overlaps on the GPU.  Queued */
+/* requests are admitted in FIFO order while the device footprint of the    */
+/* resident ones stays within hbm_budget_bytes (an estimate until a request */
+/* is set up, its measured allocation after).  A request's result does not  */
+/* depend on the other requests (same deterministic kernels on its own data). */
+/* ------------------------------------------------------------------------ */
+typedef struct sph_rt_srv sph_rt_srv;
+enum { SPH_RT_SRV_QUEUED = 0, SPH_RT_SRV_ADMITTED = 1, SPH_RT_SRV_RUNNING = 2,
+       SPH_RT_SRV_DONE = 3, SPH_RT_SRV_FAILED = 4 };
+
+typedef struct {
+  int32_t workers;         /* host threads driving resident requests (>= 1) */
+  int32_t max_resident;    /* cap on resident requests (>= 1) */
+  int32_t steps_per_tick;  /* steps a worker advances a request before rotating */
+  double hbm_budget_bytes; /* admission budget for resident device memory */
+  int32_t device;
+} sph_rt_srv_config;
+
+typedef struct {
+  int32_t queued, resident, peak_resident;
+  int64_t resident_bytes, peak_bytes; /* budget accounting */
+  int64_t particle_steps;             /* completed interior particle-steps */
+  double t_first_submit, t_last_done; /* seconds on the server's steady clock */
+} sph_rt_srv_info_t;
+
+/* Defaults: 8 workers, 64 resident, 1 step per tick, 120e9-byte budget, device 0. */
+void sph_rt_srv_default_config(sph_rt_srv_config *cfg);
+sph_rt_status sph_rt_srv_create(const sph_rt_srv_config *cfg, sph_rt_srv **out);
+
+/* Queue a request: a configuration (its stream and device fields are ignored),
+ * particles and initial state as for sph_rt_set_particles, constant sources
+ * Qe/QE (NULL = 0; ghost values stay as given in e0/E0) and `steps` steps of
+ * size dt.  All arrays are copied before the call returns.  *request_id gets
+ * the request's id. */
+sph_rt_status sph_rt_srv_submit(sph_rt_srv *srv, const sph_rt_config *cfg, int64_t n_total,
+                                const double *pos, const double *mass, const double *rho,
+                                const double *h, const double *sigma0, const int32_t *kind,
+                                const int64_t *copy_of, const double *e0, const double *E0,
+                                const double *Qe, const double *QE, int32_t steps, double dt,
+                                int64_t *request_id);
+
+/* State (SPH_RT_SRV_*) and times {submit, admit, done} of a request. */
+sph_rt_status sph_rt_srv_poll(sph_rt_srv *srv, int64_t request_id, int32_t *state,
+                              double times[3]);
+
+/* Block until the request is done or failed; returns its status. */
+sph_rt_status sph_rt_srv_wait(sph_rt_srv *srv, int64_t request_id);
+
+/* Final state (caller order [n_total], either may be NULL), the stats of its
+ * last step, and the error message of a failed request (msg may be NULL). */
+sph_rt_status sph_rt_srv_result(sph_rt_srv *srv, int64_t request_id, double *e, double *E,
+                                sph_rt_stats *last_stats, char *msg, int64_t msg_len);
+
+sph_rt_status sph_rt_srv_info(sph_rt_srv *srv, sph_rt_srv_info_t *info);
+
+/* Stop the workers (after their current tick), release every resident
+ * request and the server. */
+void sph_rt_srv_destroy(sph_rt_srv *srv);
 
 /* Message of the last failed call on this handle (NULL: of the last failed
  * sph_rt_create on this thread).  Owned by the library; valid until the next

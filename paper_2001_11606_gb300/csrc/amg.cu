@@ -62,29 +62,33 @@ struct SphLevel {
   double *r = nullptr, *z = nullptr, *res = nullptr, *d = nullptr, *t = nullptr;
   float *r32 = nullptr, *z32 = nullptr, *res32 = nullptr, *d32 = nullptr, *t32 = nullptr;
   double lmax = 2.0, gersh = 1.0;
-  int W = 32;
+  int W = 32, U = 4;
   std::vector<void *> owned;
 };
 
 namespace sphrt {
 
-static void *lvl_alloc(SphLevel *L, size_t bytes) {
-  void *p = nullptr;
-  if (cudaMalloc(&p, bytes > 0 ? bytes : 16) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  L->owned.push_back(p);
+// Level buffers come from the handle's caching allocator and go back to it
+// when the hierarchy is released (after a stream synchronisation).
+static void *lvl_alloc(sph_rt *s, SphLevel *L, size_t bytes) {
+  void *p = dalloc_bytes(s, bytes > 0 ? bytes : 16);
+  if (p) L->owned.push_back(p);
   return p;
 }
 template <typename T>
-static T *lalloc(SphLevel *L, size_t count) {
-  return static_cast<T *>(lvl_alloc(L, sizeof(T) * (count > 0 ? count : 1)));
+static T *lalloc(sph_rt *s, SphLevel *L, size_t count) {
+  return static_cast<T *>(lvl_alloc(s, L, sizeof(T) * (count > 0 ? count : 1)));
+}
+// scratch buffer of one set-up phase
+template <typename T>
+static T *scratch(sph_rt *s, size_t count) {
+  return static_cast<T *>(dalloc_bytes(s, sizeof(T) * (count > 0 ? count : 1)));
 }
 
 void amg_release(sph_rt *s) {
+  if (!s->levels.empty() && s->cuda_ready) cudaStreamSynchronize(s->stream);
   for (SphLevel *L : s->levels) {
-    for (void *p : L->owned) cudaFree(p);
+    for (void *p : L->owned) dfree(s, p);
     delete L;
   }
   s->levels.clear();
@@ -256,6 +260,7 @@ __global__ void coarse_struct_kernel(int64_t nc, const int64_t *agg_ptr, const i
                                      int32_t *tgt, int64_t nnz_c, int32_t *tgt_diag,
                                      int *overflow) {
   __shared__ int32_t table[kHash];
+  __shared__ int32_t keys[kHash / 2];
   __shared__ int nkeys;
   for (int64_t I = blockIdx.x; I < nc; I += gridDim.x) {
     for (int t = threadIdx.x; t < kHash; t += blockDim.x) table[t] = 0x7fffffff;
@@ -287,17 +292,29 @@ __global__ void coarse_struct_kernel(int64_t nc, const int64_t *agg_ptr, const i
       __syncthreads();
       continue;
     }
-    // sort the whole table (empty slots are INT_MAX and sort last)
-    for (int k = 2; k <= kHash; k <<= 1) {
+    // compact the keys (any order), pad to a power of two and sort ascending
+    __shared__ int ncomp;
+    if (threadIdx.x == 0) ncomp = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < kHash; t += blockDim.x) {
+      int32_t v = table[t];
+      if (v != 0x7fffffff) keys[atomicAdd(&ncomp, 1)] = v;
+    }
+    int P2 = 1;
+    while (P2 < cnt) P2 <<= 1;
+    __syncthreads();
+    for (int t = cnt + threadIdx.x; t < P2; t += blockDim.x) keys[t] = 0x7fffffff;
+    __syncthreads();
+    for (int k = 2; k <= P2; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int t = threadIdx.x; t < kHash; t += blockDim.x) {
+        for (int t = threadIdx.x; t < P2; t += blockDim.x) {
           int u = t ^ j;
           if (u > t) {
-            int32_t a = table[t], b = table[u];
+            int32_t a = keys[t], b = keys[u];
             bool up = (t & k) == 0;
             if ((a > b) == up) {
-              table[t] = b;
-              table[u] = a;
+              keys[t] = b;
+              keys[u] = a;
             }
           }
         }
@@ -308,7 +325,7 @@ __global__ void coarse_struct_kernel(int64_t nc, const int64_t *agg_ptr, const i
       if (threadIdx.x == 0) ccount[I] = cnt;
     } else {
       const int64_t base = cptr[I];
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) ccol[base + t] = table[t];
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) ccol[base + t] = keys[t];
       for (int64_t m = m0; m < m1; ++m) {
         int32_t i = agg_mem[m];
         if (threadIdx.x == 0) tgt_diag[i] = (int32_t)(nnz_c + I);
@@ -321,7 +338,7 @@ __global__ void coarse_struct_kernel(int64_t nc, const int64_t *agg_ptr, const i
             int lo = 0, hi = cnt;  // lower_bound
             while (lo < hi) {
               int mid = (lo + hi) >> 1;
-              if (table[mid] < J) lo = mid + 1;
+              if (keys[mid] < J) lo = mid + 1;
               else hi = mid;
             }
             tg = (int32_t)(base + lo);
@@ -397,7 +414,7 @@ __global__ void convert_kernel(int64_t n, const S *in, D *out) {
 // ---------------------------------------------------------------------------
 // V-cycle kernels
 // ---------------------------------------------------------------------------
-template <int W, typename MT, typename VT>
+template <int W, int U, typename MT, typename VT>
 __global__ void resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
                                    const Scalars *sc) {
   if (sc && sc->done) return;
@@ -405,10 +422,8 @@ __global__ void resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   for (int64_t i = grp; i < A.n; i += ngrp) {
-    VT s = 0;
-    for (int64_t k = A.ptr[i] + sub; k < A.ptr[i + 1]; k += W) s += (VT)A.val[k] * z[A.col[k]];
-#pragma unroll
-    for (int o = W / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, W);
+    VT s = row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub);
+    s = row_reduce<W>(s);
     if (sub == 0) res[i] = r[i] - ((VT)A.diag[i] * z[i] + s);
   }
 }
@@ -441,21 +456,15 @@ __global__ void prolong_kernel(int64_t n, const int32_t *agg, const VT *zc, VT *
 // ---------------------------------------------------------------------------
 CsrView<double> fine_view(const sph_rt *s);
 
-static int width_for(int64_t nnz, int64_t n) {
-  double mean = n ? (double)nnz / (double)n : 0.0;
-  return mean > 48 ? 32 : (mean > 12 ? 16 : 8);
-}
 
 // bucket sort of ids by bucket[i] into (start, out); nb buckets
 static sph_rt_status bucket_sort(sph_rt *s, SphLevel *owner, int64_t nitems,
                                  const int32_t *bucket, int64_t nb, int64_t **start_out,
                                  int32_t **out_out, int64_t *total_out) {
-  unsigned *cnt = nullptr, *cur = nullptr;
-  int64_t *cnt64 = nullptr;
-  SPH_CUDA(s, cudaMalloc(&cnt, sizeof(unsigned) * (nb + 1)));
-  SPH_CUDA(s, cudaMalloc(&cur, sizeof(unsigned) * (nb + 1)));
-  SPH_CUDA(s, cudaMalloc(&cnt64, sizeof(int64_t) * (nb + 1)));
-  int64_t *start = lalloc<int64_t>(owner, nb + 1);
+  unsigned *cnt = scratch<unsigned>(s, nb + 1), *cur = scratch<unsigned>(s, nb + 1);
+  int64_t *cnt64 = scratch<int64_t>(s, nb + 1);
+  if (!cnt || !cur || !cnt64) return SPH_RT_ENOMEM;
+  int64_t *start = lalloc<int64_t>(s, owner, nb + 1);
   if (!start) return SPH_RT_ENOMEM;
   SPH_CUDA(s, cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (nb + 1), s->stream));
   SPH_CUDA(s, cudaMemsetAsync(cur, 0, sizeof(unsigned) * (nb + 1), s->stream));
@@ -468,7 +477,7 @@ static sph_rt_status bucket_sort(sph_rt *s, SphLevel *owner, int64_t nitems,
   int64_t total = 0;
   SPH_CUDA(s, cudaMemcpyAsync(&total, start + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream));
   SPH_CUDA(s, cudaStreamSynchronize(s->stream));
-  int32_t *out = lalloc<int32_t>(owner, total);
+  int32_t *out = lalloc<int32_t>(s, owner, total);
   if (!out) return SPH_RT_ENOMEM;
   bucket_scatter_kernel<<<gcap(s, nitems, kBlock), kBlock, 0, s->stream>>>(nitems, bucket, start,
                                                                           cur, out);
@@ -476,9 +485,9 @@ static sph_rt_status bucket_sort(sph_rt *s, SphLevel *owner, int64_t nitems,
   bucket_sort_kernel<<<gcap(s, nb, kBlock), kBlock, 0, s->stream>>>(nb, start, out);
   SPH_LAUNCHED(s);
   SPH_CUDA(s, cudaStreamSynchronize(s->stream));
-  cudaFree(cnt);
-  cudaFree(cur);
-  cudaFree(cnt64);
+  dfree(s, cnt);
+  dfree(s, cur);
+  dfree(s, cnt64);
   *start_out = start;
   *out_out = out;
   if (total_out) *total_out = total;
@@ -491,24 +500,20 @@ static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
   *next = nullptr;
   const int64_t n = L->n, nnz = L->nnz;
   cudaStream_t st = s->stream;
-  uint8_t *strong = nullptr, *cand = nullptr;
-  int *state = nullptr;
-  int64_t *flag = nullptr, *root_id = nullptr;
-  unsigned *undec = nullptr, *members = nullptr;
-  SPH_CUDA(s, cudaMalloc(&strong, nnz > 0 ? nnz : 1));
-  SPH_CUDA(s, cudaMalloc(&cand, n));
-  SPH_CUDA(s, cudaMalloc(&state, sizeof(int) * n));
-  SPH_CUDA(s, cudaMalloc(&flag, sizeof(int64_t) * n));
-  SPH_CUDA(s, cudaMalloc(&root_id, sizeof(int64_t) * (n + 1)));
-  SPH_CUDA(s, cudaMalloc(&undec, sizeof(unsigned)));
+  uint8_t *strong = scratch<uint8_t>(s, nnz), *cand = scratch<uint8_t>(s, n);
+  int *state = scratch<int>(s, n);
+  int64_t *flag = scratch<int64_t>(s, n), *root_id = scratch<int64_t>(s, n + 1);
+  unsigned *undec = scratch<unsigned>(s, 1), *members = nullptr;
+  if (!strong || !cand || !state || !flag || !root_id || !undec) return SPH_RT_ENOMEM;
   auto cleanup = [&]() {
-    cudaFree(strong);
-    cudaFree(cand);
-    cudaFree(state);
-    cudaFree(flag);
-    cudaFree(root_id);
-    cudaFree(undec);
-    if (members) cudaFree(members);
+    cudaStreamSynchronize(s->stream);
+    dfree(s, strong);
+    dfree(s, cand);
+    dfree(s, state);
+    dfree(s, flag);
+    dfree(s, root_id);
+    dfree(s, undec);
+    if (members) dfree(s, members);
   };
   const int g = gcap(s, n, kBlock);
   strength_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, L->val, L->diag, s->cfg.amg_theta,
@@ -538,9 +543,10 @@ static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
     cleanup();
     return SPH_RT_OK;
   }
-  SPH_CUDA(s, cudaMalloc(&members, sizeof(unsigned) * nc));
+  members = scratch<unsigned>(s, nc);
+  if (!members) return cleanup(), SPH_RT_ENOMEM;
   SPH_CUDA(s, cudaMemsetAsync(members, 0, sizeof(unsigned) * nc, st));
-  L->agg = lalloc<int32_t>(L, n);
+  L->agg = lalloc<int32_t>(s, L, n);
   if (!L->agg) return cleanup(), SPH_RT_ENOMEM;
   assign_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, L->val, strong, state, root_id, L->agg,
                                       members);
@@ -554,10 +560,10 @@ static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
   SphLevel *C = new SphLevel();
   C->n = nc;
   // coarse sparsity: count, scan, fill (+ Galerkin targets of every fine entry)
-  int64_t *ccount = lalloc<int64_t>(C, nc);
-  C->ptr = lalloc<int64_t>(C, nc + 1);
-  int *overflow = nullptr;
-  SPH_CUDA(s, cudaMalloc(&overflow, sizeof(int)));
+  int64_t *ccount = lalloc<int64_t>(s, C, nc);
+  C->ptr = lalloc<int64_t>(s, C, nc + 1);
+  int *overflow = scratch<int>(s, 1);
+  if (!ccount || !C->ptr || !overflow) return SPH_RT_ENOMEM;
   SPH_CUDA(s, cudaMemsetAsync(overflow, 0, sizeof(int), st));
   int gb = (int)std::min<int64_t>(nc, (int64_t)s->num_sms * 16);
   coarse_struct_kernel<false><<<gb, kBlock, 0, st>>>(nc, L->agg_ptr, L->agg_mem, L->ptr, L->col,
@@ -568,17 +574,17 @@ static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
   SPH_CUDA(s, cudaMemcpyAsync(&ovf, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
   SPH_CUDA(s, cudaStreamSynchronize(st));
   if (ovf) {
-    cudaFree(overflow);
-    for (void *p : C->owned) cudaFree(p);
+    dfree(s, overflow);
+    for (void *p : C->owned) dfree(s, p);
     delete C;
     return SPH_RT_OK;  // stop coarsening here
   }
   if ((rc = exclusive_scan(s, ccount, nc, C->ptr))) return rc;
   SPH_CUDA(s, cudaMemcpyAsync(&C->nnz, C->ptr + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   SPH_CUDA(s, cudaStreamSynchronize(st));
-  C->col = lalloc<int32_t>(C, C->nnz);
-  int32_t *tgt = nullptr;  // [nnz + n]: off-diagonal entries, then diagonals
-  SPH_CUDA(s, cudaMalloc(&tgt, sizeof(int32_t) * (nnz + n)));
+  C->col = lalloc<int32_t>(s, C, C->nnz);
+  int32_t *tgt = scratch<int32_t>(s, nnz + n);  // off-diagonal entries, then diagonals
+  if (!C->col || !tgt) return SPH_RT_ENOMEM;
   fill_i32_kernel<<<gcap(s, nnz + n, kBlock), kBlock, 0, st>>>(nnz + n, -1, tgt);
   SPH_LAUNCHED(s);
   coarse_struct_kernel<true><<<gb, kBlock, 0, st>>>(nc, L->agg_ptr, L->agg_mem, L->ptr, L->col,
@@ -586,33 +592,35 @@ static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
                                                     tgt + nnz, overflow);
   SPH_LAUNCHED(s);
   // Galerkin contribution lists per coarse target (nnz_c off-diagonal + nc diagonal)
-  if ((rc = bucket_sort(s, L, nnz + n, tgt, C->nnz + nc, &L->seg_ptr, &L->seg_src, nullptr))) {
-    cudaFree(tgt);
-    cudaFree(overflow);
-    return rc;
-  }
-  cudaFree(tgt);
-  cudaFree(overflow);
+  rc = bucket_sort(s, L, nnz + n, tgt, C->nnz + nc, &L->seg_ptr, &L->seg_src, nullptr);
+  SPH_CUDA(s, cudaStreamSynchronize(st));
+  dfree(s, tgt);
+  dfree(s, overflow);
+  if (rc) return rc;
   // coarse values and vectors
-  C->val = lalloc<double>(C, C->nnz);
-  C->diag = lalloc<double>(C, nc);
-  C->invdiag = lalloc<double>(C, nc);
-  C->r = lalloc<double>(C, nc);
-  C->z = lalloc<double>(C, nc);
-  C->res = lalloc<double>(C, nc);
-  C->d = lalloc<double>(C, nc);
-  C->t = lalloc<double>(C, nc);
+  C->val = lalloc<double>(s, C, C->nnz);
+  C->diag = lalloc<double>(s, C, nc);
+  C->invdiag = lalloc<double>(s, C, nc);
+  C->r = lalloc<double>(s, C, nc);
+  C->z = lalloc<double>(s, C, nc);
+  C->res = lalloc<double>(s, C, nc);
+  C->d = lalloc<double>(s, C, nc);
+  C->t = lalloc<double>(s, C, nc);
   if (!C->val || !C->diag || !C->invdiag || !C->r || !C->z || !C->res || !C->d || !C->t)
     return SPH_RT_ENOMEM;
-  C->W = width_for(C->nnz, nc);
+  {
+    RowShape sh = shape_for_mean(nc ? (double)C->nnz / (double)nc : 0.0);
+    C->W = sh.W;
+    C->U = sh.U;
+  }
   *next = C;
   return SPH_RT_OK;
 }
 
 static sph_rt_status level_vectors_fine(sph_rt *s, SphLevel *L) {
-  L->res = lalloc<double>(L, L->n);
-  L->d = lalloc<double>(L, L->n);
-  L->t = lalloc<double>(L, L->n);
+  L->res = lalloc<double>(s, L, L->n);
+  L->d = lalloc<double>(s, L, L->n);
+  L->t = lalloc<double>(s, L, L->n);
   if (!L->res || !L->d || !L->t) return SPH_RT_ENOMEM;
   (void)s;
   return SPH_RT_OK;
@@ -630,6 +638,7 @@ static sph_rt_status build_structure(sph_rt *s) {
   L0->diag = const_cast<double *>(A.diag);
   L0->invdiag = const_cast<double *>(A.invdiag);
   L0->W = A.W;
+  L0->U = A.U;
   s->levels.push_back(L0);
   sph_rt_status rc = level_vectors_fine(s, L0);
   if (rc) return rc;
@@ -665,8 +674,9 @@ static sph_rt_status numeric(sph_rt *s) {
   }
   // Gershgorin bounds of every level (one host read for all)
   std::vector<double> g(s->levels.size(), 1.0);
-  double *dg = nullptr;
-  SPH_CUDA(s, cudaMalloc(&dg, sizeof(double) * s->levels.size()));
+  if (!s->amg_gersh) s->amg_gersh = dalloc<double>(s, kMaxLevels);
+  double *dg = s->amg_gersh;
+  if (!dg) return SPH_RT_ENOMEM;
   for (size_t l = 0; l < s->levels.size(); ++l) {
     SphLevel *L = s->levels[l];
     gersh_kernel<<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(L->n, L->ptr, L->val, L->diag,
@@ -677,7 +687,6 @@ static sph_rt_status numeric(sph_rt *s) {
   SPH_CUDA(s, cudaMemcpyAsync(g.data(), dg, sizeof(double) * g.size(), cudaMemcpyDeviceToHost,
                               s->stream));
   SPH_CUDA(s, cudaStreamSynchronize(s->stream));
-  cudaFree(dg);
   for (size_t l = 0; l < s->levels.size(); ++l) {
     s->levels[l]->gersh = g[l];
     s->levels[l]->lmax = 1.0 + g[l];
@@ -685,14 +694,14 @@ static sph_rt_status numeric(sph_rt *s) {
   if (s->cfg.precision == SPH_RT_MIXED) {
     for (SphLevel *L : s->levels) {
       if (!L->val32) {
-        L->val32 = lalloc<float>(L, L->nnz);
-        L->diag32 = lalloc<float>(L, L->n);
-        L->invdiag32 = lalloc<float>(L, L->n);
-        L->r32 = lalloc<float>(L, L->n);
-        L->z32 = lalloc<float>(L, L->n);
-        L->res32 = lalloc<float>(L, L->n);
-        L->d32 = lalloc<float>(L, L->n);
-        L->t32 = lalloc<float>(L, L->n);
+        L->val32 = lalloc<float>(s, L, L->nnz);
+        L->diag32 = lalloc<float>(s, L, L->n);
+        L->invdiag32 = lalloc<float>(s, L, L->n);
+        L->r32 = lalloc<float>(s, L, L->n);
+        L->z32 = lalloc<float>(s, L, L->n);
+        L->res32 = lalloc<float>(s, L, L->n);
+        L->d32 = lalloc<float>(s, L, L->n);
+        L->t32 = lalloc<float>(s, L, L->n);
         if (!L->val32 || !L->diag32 || !L->invdiag32 || !L->r32 || !L->z32 || !L->res32 ||
             !L->d32 || !L->t32)
           return SPH_RT_ENOMEM;
@@ -736,6 +745,7 @@ struct LevelVecs<double> {
     A.invdiag = L->invdiag;
     A.nnz = L->nnz;
     A.W = L->W;
+    A.U = L->U;
     return A;
   }
   static double *r(SphLevel *L) { return L->r; }
@@ -756,6 +766,7 @@ struct LevelVecs<float> {
     A.invdiag = L->invdiag32;
     A.nnz = L->nnz;
     A.W = L->W;
+    A.U = L->U;
     return A;
   }
   static float *r(SphLevel *L) { return L->r32; }
@@ -783,12 +794,9 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
   if ((rc = cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, lmin, lmax, true, sc))) return rc;
   const int gw = gcap(s, L->n, kBlock / A.W);
   T *res = LV::res(L);
-  if (A.W == 32)
-    resid_level_kernel<32, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res, sc);
-  else if (A.W == 16)
-    resid_level_kernel<16, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res, sc);
-  else
-    resid_level_kernel<8, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res, sc);
+  SPH_DISPATCH_SHAPE(A.W, A.U,
+                     (resid_level_kernel<W, U, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res,
+                                                                                    sc)));
   SPH_LAUNCHED(s);
   SphLevel *C = s->levels[l + 1];
   restrict_kernel<T><<<gcap(s, C->n, kBlock), kBlock, 0, s->stream>>>(C->n, L->agg_ptr, L->agg_mem,

@@ -16,7 +16,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/sph_rt.h"
@@ -132,8 +134,78 @@ __device__ bool last_block_combine(const double (&part)[NV], double *partials, u
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Off-diagonal part of one CSR row times a gathered vector, computed by the W
+// lanes of a row group (this lane's partial sum; reduce over the group after).
+// Each pass first issues U independent column/value loads per lane and then U
+// independent gathers, so a row of up to W*U entries costs one dependent
+// memory round trip instead of one per W entries.  Out-of-range slots load
+// nothing and add nothing.
+template <int W, int U, typename MT, typename VT>
+__device__ __forceinline__ VT row_dot(int64_t beg, int64_t end, const int32_t *__restrict__ col,
+                                      const MT *__restrict__ val, const VT *__restrict__ x,
+                                      int sub) {
+  VT s = VT(0);
+  for (int64_t k = beg + sub; k < end; k += (int64_t)W * U) {
+    int32_t c[U];
+    MT v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * W;
+      c[u] = kk < end ? __ldg(col + kk) : -1;
+      v[u] = kk < end ? __ldg(val + kk) : MT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (c[u] >= 0) s += (VT)v[u] * __ldg(x + c[u]);
+  }
+  return s;
+}
+
+// Sum over the W lanes of a row group (W divides 32; groups are aligned).
+template <int W, typename T>
+__device__ __forceinline__ T row_reduce(T v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, W);
+  return v;
+}
+
+// Row-group shape of the SpMV-class kernels: W lanes per row, U loads in flight
+// per lane.  Chosen from the mean row length (or by the autotuner).
+struct RowShape {
+  int W, U;
+};
+__host__ inline RowShape shape_for_mean(double mean) {
+  if (mean <= 32) return {8, 4};
+  if (mean <= 64) return {16, 4};
+  if (mean <= 96) return {16, 6};
+  if (mean <= 128) return {16, 8};
+  return {32, 8};
+}
+
+// Launch CALL with constexpr W and U set to the supported row-group shape
+// nearest to (W_, U_).
+#define SPH_DISPATCH_SHAPE(W_, U_, CALL)                                   \
+  do {                                                                     \
+    if ((W_) <= 8) {                                                       \
+      constexpr int W = 8, U = 4;                                          \
+      CALL;                                                                \
+    } else if ((W_) == 16 && (U_) <= 4) {                                  \
+      constexpr int W = 16, U = 4;                                         \
+      CALL;                                                                \
+    } else if ((W_) == 16 && (U_) <= 6) {                                  \
+      constexpr int W = 16, U = 6;                                         \
+      CALL;                                                                \
+    } else if ((W_) == 16) {                                               \
+      constexpr int W = 16, U = 8;                                         \
+      CALL;                                                                \
+    } else {                                                               \
+      constexpr int W = 32, U = 8;                                         \
+      CALL;                                                                \
+    }                                                                      \
+  } while (0)
+
 // A CSR operator as seen by the SpMV-shaped kernels: off-diagonal entries in
-// (ptr, col, val) and the diagonal apart.  W = lanes per row.
+// (ptr, col, val) and the diagonal apart.  (W, U) = row-group shape.
 template <typename T>
 struct CsrView {
   int64_t n = 0;
@@ -144,6 +216,7 @@ struct CsrView {
   const T *invdiag = nullptr;
   int64_t nnz = 0;
   int W = 32;
+  int U = 4;
 };
 
 }  // namespace sphrt
@@ -162,6 +235,8 @@ struct sph_rt {
   bool cuda_ready = false;
   int num_sms = 152;
   std::vector<void *> allocs;  // device allocations of the current particle set
+  std::unordered_map<void *, size_t> alloc_size;
+  std::multimap<size_t, void *> pool;  // released buffers kept for reuse
 
   // sizes
   bool have_particles = false;
@@ -209,6 +284,7 @@ struct sph_rt {
   double *Qe = nullptr, *QE = nullptr;  // slot order [n]
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr,
          *w = nullptr;
+  double *z_old = nullptr;  // previous preconditioned residual (flexible CG)
   double *tmp_n = nullptr;   // [n] staging for caller-order transfers
   double *tmp_n2 = nullptr;  // [n] staging / Chebyshev scratch
   double *tmp_n3 = nullptr;
@@ -225,6 +301,11 @@ struct sph_rt {
   bool amg_ready = false;
   double cheb_lmin = 0.0, cheb_lmax = 2.0;  // spectrum bounds of D^{-1} B (Gershgorin)
   double *gersh = nullptr;                   // device scalar written by the assembly
+  double *amg_gersh = nullptr;               // per-level Gershgorin bounds
+
+  // row-group shape of the fine SpMV-class kernels (autotuned or from the mean row length)
+  sphrt::RowShape fine_shape{16, 6};
+  bool fine_shape_set = false;
 
   // kernel timing
   std::vector<cudaEvent_t> ev_pool;
@@ -243,6 +324,7 @@ inline T *dalloc(sph_rt *s, size_t count) {
   return static_cast<T *>(dalloc_bytes(s, sizeof(T) * (count > 0 ? count : 1)));
 }
 void free_all(sph_rt *s);
+void dfree(sph_rt *s, void *p);  // back to the free list (stream-ordered users must sync first)
 int red_grid(const sph_rt *s, int64_t items, int items_per_block);
 // CUDA-event bracketing of fine-operator SpMV-class launches (config.kernel_timing)
 void timing_begin(sph_rt *s);

@@ -17,6 +17,8 @@
 // once; iterations queued after convergence are empty launches.
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "common.cuh"
 
 namespace sphrt {
@@ -29,7 +31,7 @@ __device__ __forceinline__ T ld(const T *p) {
 // ---------------------------------------------------------------------------
 // r = b - B x;  rnorm2 = ||r / V||^2;  done = rnorm2 <= thresh2.
 // ---------------------------------------------------------------------------
-template <int W>
+template <int W, int U>
 __global__ void resid_kernel(CsrView<double> A, const double *b, const double *x, double *r,
                              const double *invV, Scalars *sc, double *partials) {
   const int sub = threadIdx.x % W;
@@ -37,9 +39,8 @@ __global__ void resid_kernel(CsrView<double> A, const double *b, const double *x
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   double acc = 0.0;
   for (int64_t i = grp; i < A.n; i += ngrp) {
-    double s = 0.0;
-    for (int64_t k = A.ptr[i] + sub; k < A.ptr[i + 1]; k += W) s += ld(A.val + k) * ld(x + ld(A.col + k));
-    s = group_sum<W>(s);
+    double s = row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, x, sub);
+    s = row_reduce<W>(s);
     if (sub == 0) {
       double ri = b[i] - (A.diag[i] * x[i] + s);
       r[i] = ri;
@@ -63,7 +64,7 @@ __global__ void resid_kernel(CsrView<double> A, const double *b, const double *x
 // w = B z;  q = w + beta q;  p = z + beta p;  pq = (p, q);  alpha = rho / pq.
 // (q = B p without a second SpMV: B p = B z + beta B p_old.)
 // ---------------------------------------------------------------------------
-template <int W>
+template <int W, int U>
 __global__ void spmv_pq_kernel(CsrView<double> A, const double *z, double *q, double *p, int first,
                                Scalars *sc, double *partials) {
   if (sc->done) return;
@@ -73,9 +74,8 @@ __global__ void spmv_pq_kernel(CsrView<double> A, const double *z, double *q, do
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   double acc = 0.0;
   for (int64_t i = grp; i < A.n; i += ngrp) {
-    double s = 0.0;
-    for (int64_t k = A.ptr[i] + sub; k < A.ptr[i + 1]; k += W) s += ld(A.val + k) * ld(z + ld(A.col + k));
-    s = group_sum<W>(s);
+    double s = row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub);
+    s = row_reduce<W>(s);
     if (sub == 0) {
       double zi = z[i];
       double wi = A.diag[i] * zi + s;
@@ -168,6 +168,32 @@ __global__ void dot_rz_kernel(int64_t n, const double *r, const VT *z, int first
   }
 }
 
+// Flexible variant (Polak-Ribiere): beta = ((r, z) - (r, z_old)) / rho_old.
+// Used when the preconditioner is only approximately symmetric (an FP32
+// V-cycle): it keeps CG's short recurrence without assuming exact symmetry.
+__global__ void dot_rz_flex_kernel(int64_t n, const double *r, const double *z,
+                                   const double *z_old, int first, Scalars *sc,
+                                   double *partials) {
+  if (sc->done) return;
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double ri = r[i];
+    a += ri * z[i];
+    if (!first) b += ri * z_old[i];
+  }
+  __shared__ double sh[32];
+  a = block_sum(a, sh);
+  __syncthreads();
+  b = block_sum(b, sh);
+  double part[2] = {a, b}, out[2];
+  const bool mx[2] = {false, false};
+  if (last_block_combine<2>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    if (!first) sc->beta = (out[0] - out[1]) / sc->rho;
+    sc->rho = out[0];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Chebyshev iteration for A z = r (A = level operator, D = its diagonal) on
 // the interval [lmin, lmax] of D^{-1} A (Saad, Iterative Methods, Alg. 12.1).
@@ -187,14 +213,8 @@ __global__ void cheb_init_zero_kernel(int64_t n, const VT *r, const MT *invdiag,
   }
 }
 
-template <int W, typename T>
-__device__ __forceinline__ T gsum(T v) {
-#pragma unroll
-  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, W);
-  return v;
-}
 
-template <int W, typename MT, typename VT>
+template <int W, int U, typename MT, typename VT>
 __global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
                                  double c1, double c2, const Scalars *sc) {
   if (sc && sc->done) return;
@@ -203,10 +223,8 @@ __global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT 
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   const VT vc1 = (VT)c1, vc2 = (VT)c2;
   for (int64_t i = grp; i < A.n; i += ngrp) {
-    VT s = 0;
-    for (int64_t k = A.ptr[i] + sub; k < A.ptr[i + 1]; k += W)
-      s += (VT)ld(A.val + k) * ld(z_in + ld(A.col + k));
-    s = gsum<W, VT>(s);
+    VT s = row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z_in, sub);
+    s = row_reduce<W>(s);
     if (sub == 0) {
       VT zi = z_in[i];
       VT res = r[i] - ((VT)A.diag[i] * zi + s);
@@ -228,13 +246,6 @@ static int grid_cap(const sph_rt *s, int64_t n, int per_block) {
   return (int)(g < cap ? g : cap);
 }
 
-#define SPH_W_LAUNCH(KERNEL, W, grid, s, ...)                                  \
-  do {                                                                         \
-    if ((W) == 32) KERNEL<32><<<grid, kBlock, 0, (s)->stream>>>(__VA_ARGS__);  \
-    else if ((W) == 16) KERNEL<16><<<grid, kBlock, 0, (s)->stream>>>(__VA_ARGS__); \
-    else KERNEL<8><<<grid, kBlock, 0, (s)->stream>>>(__VA_ARGS__);             \
-    SPH_LAUNCHED(s);                                                           \
-  } while (0)
 
 CsrView<double> fine_view(const sph_rt *s) {
   CsrView<double> A;
@@ -245,8 +256,10 @@ CsrView<double> fine_view(const sph_rt *s) {
   A.diag = s->diag;
   A.invdiag = s->invdiag;
   A.nnz = s->nnz_mat;
-  double mean = s->n_int ? (double)s->nnz_mat / (double)s->n_int : 0.0;
-  A.W = mean > 48 ? 32 : (mean > 12 ? 16 : 8);
+  RowShape sh = s->fine_shape_set ? s->fine_shape
+                                  : shape_for_mean(s->n_int ? (double)s->nnz_mat / s->n_int : 0.0);
+  A.W = sh.W;
+  A.U = sh.U;
   return A;
 }
 
@@ -306,7 +319,10 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
                          int degree, double lmin, double lmax, bool zero_guess,
                          const Scalars *sc) {
   double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
-  double sigma1 = theta / delta;
+  // a collapsed interval means D^{-1} A = I (no off-diagonal coupling): one
+  // Jacobi step is then exact and the polynomial recurrence is undefined
+  if (!(delta > 1e-12 * theta)) degree = 1;
+  double sigma1 = degree > 1 ? theta / delta : 1.0;
   double rho0 = 1.0 / sigma1;
   int g = grid_cap(s, A.n, kBlock);
   int gw = grid_cap(s, A.n, kBlock / A.W);
@@ -316,12 +332,9 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
   const double bytes = spmv_class_bytes(A, 8 + 2 * (int)sizeof(MT) + 5 * (int)sizeof(VT));
   auto step = [&](const VT *zin, VT *zout, double c1, double c2) -> sph_rt_status {
     if (fine) timing_begin(s);
-    if (A.W == 32)
-      cheb_step_kernel<32, MT, VT><<<gw, kBlock, 0, s->stream>>>(A, r, zin, zout, d, c1, c2, sc);
-    else if (A.W == 16)
-      cheb_step_kernel<16, MT, VT><<<gw, kBlock, 0, s->stream>>>(A, r, zin, zout, d, c1, c2, sc);
-    else
-      cheb_step_kernel<8, MT, VT><<<gw, kBlock, 0, s->stream>>>(A, r, zin, zout, d, c1, c2, sc);
+    SPH_DISPATCH_SHAPE(A.W, A.U,
+                       (cheb_step_kernel<W, U, MT, VT><<<gw, kBlock, 0, s->stream>>>(
+                           A, r, zin, zout, d, c1, c2, sc)));
     SPH_LAUNCHED(s);
     if (fine) timing_end(s, bytes);
     return SPH_RT_OK;
@@ -384,6 +397,12 @@ static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first
       if (rc) return rc;
       break;
   }
+  if (s->cfg.precision == SPH_RT_MIXED) {
+    dot_rz_flex_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->r, s->z, s->z_old, first, s->sc,
+                                                     s->partials);
+    SPH_LAUNCHED(s);
+    return SPH_RT_OK;
+  }
   dot_rz_kernel<double><<<g, kBlock, 0, s->stream>>>(A.n, s->r, s->z, first, s->sc, s->partials);
   SPH_LAUNCHED(s);
   return SPH_RT_OK;
@@ -399,11 +418,18 @@ sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
   const double bytes = spmv_class_bytes(A, kRowBytesSpmvPQ);
   sph_rt_status rc;
   timing_begin(s);
-  SPH_W_LAUNCH(resid_kernel, A.W, gw, s, A, s->b, s->x, s->r, s->invV, s->sc, s->partials);
+  SPH_DISPATCH_SHAPE(A.W, A.U,
+                     (resid_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->b, s->x, s->r,
+                                                                       s->invV, s->sc,
+                                                                       s->partials)));
+  SPH_LAUNCHED(s);
   timing_end(s, bytes_r);
   if ((rc = precondition(s, A, 1))) return rc;
   timing_begin(s);
-  SPH_W_LAUNCH(spmv_pq_kernel, A.W, gw, s, A, s->z, s->q, s->p, 1, s->sc, s->partials);
+  SPH_DISPATCH_SHAPE(A.W, A.U,
+                     (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->z, s->q, s->p, 1,
+                                                                         s->sc, s->partials)));
+  SPH_LAUNCHED(s);
   timing_end(s, bytes);
   const int chunk = s->cfg.check_every > 0 ? s->cfg.check_every : 1;
   int queued = 0;
@@ -412,9 +438,13 @@ sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
       update_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
                                                   s->cfg.max_krylov, s->sc, s->partials);
       SPH_LAUNCHED(s);
+      if (s->cfg.precision == SPH_RT_MIXED) std::swap(s->z, s->z_old);
       if ((rc = precondition(s, A, 0))) return rc;
       timing_begin(s);
-      SPH_W_LAUNCH(spmv_pq_kernel, A.W, gw, s, A, s->z, s->q, s->p, 0, s->sc, s->partials);
+      SPH_DISPATCH_SHAPE(A.W, A.U,
+                         (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(
+                             A, s->z, s->q, s->p, 0, s->sc, s->partials)));
+      SPH_LAUNCHED(s);
       timing_end(s, bytes);
       ++queued;
     }

@@ -103,6 +103,7 @@ sph_rt_status exclusive_scan(sph_rt *s, const int64_t *in, int64_t n, int64_t *o
   SPH_LAUNCHED(s);
   scan_tiles<<<(unsigned)ntiles, kBlock, 0, s->stream>>>(in, n, tiles, out);
   SPH_LAUNCHED(s);
+  dfree(s, tiles);  // reuse is stream-ordered after the scan
   return SPH_RT_OK;
 }
 
@@ -630,6 +631,9 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
                                         s->gh_slot, s->gh_W);
   SPH_LAUNCHED(s);
   SPH_CUDA(s, cudaStreamSynchronize(st));
+  // set-up scratch back to the free list
+  void *scratch[] = {cx, cy, cz, hc, bbox, key, cnt, cur, cnt64, start, nc, mc, gc};
+  for (void *p : scratch) dfree(s, p);
   return SPH_RT_OK;
 }
 

@@ -51,15 +51,41 @@ bool cuda_ok(sph_rt *s, cudaError_t e, const char *what) {
   return false;
 }
 
+// Device memory of a particle set comes from a per-handle caching allocator:
+// buffers released by free_all() go to a size-keyed free list and are handed
+// out again (best fit, at most twice the request) by the next particle set, so
+// re-setting particles of similar size does no cudaFree/cudaMalloc (both of
+// which synchronise the device).  Everything is returned to CUDA on destroy,
+// or when an allocation fails (then the request is retried once).
+static void pool_release(sph_rt *s) {
+  for (auto &kv : s->pool) cudaFree(kv.second);
+  s->pool.clear();
+}
+
 void *dalloc_bytes(sph_rt *s, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  auto it = s->pool.lower_bound(bytes);
+  if (it != s->pool.end() && it->first <= 2 * bytes) {
+    void *p = it->second;
+    s->alloc_size[p] = it->first;
+    s->pool.erase(it);
+    s->allocs.push_back(p);
+    return p;
+  }
   void *p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pool_release(s);
+    e = cudaMalloc(&p, bytes);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     s->err = "device allocation of " + std::to_string(bytes) + " bytes failed: " +
              cudaGetErrorString(e);
     return nullptr;
   }
+  s->alloc_size[p] = bytes;
   s->allocs.push_back(p);
   return p;
 }
@@ -67,11 +93,27 @@ void *dalloc_bytes(sph_rt *s, size_t bytes) {
 void free_all(sph_rt *s) {
   if (s->cuda_ready) cudaStreamSynchronize(s->stream);
   amg_release(s);
-  for (void *p : s->allocs) cudaFree(p);
+  for (void *p : s->allocs) s->pool.emplace(s->alloc_size[p], p);
   s->allocs.clear();
+  s->alloc_size.clear();
   s->have_particles = false;
   s->have_operator = false;
   s->amg_ready = false;
+}
+
+// Return one buffer of the current particle set to the free list.
+void dfree(sph_rt *s, void *p) {
+  if (!p) return;
+  auto it = std::find(s->allocs.begin(), s->allocs.end(), p);
+  if (it == s->allocs.end()) return;
+  s->allocs.erase(it);
+  s->pool.emplace(s->alloc_size[p], p);
+  s->alloc_size.erase(p);
+}
+
+void free_everything(sph_rt *s) {
+  free_all(s);
+  pool_release(s);
 }
 
 }  // namespace sphrt
@@ -103,7 +145,7 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->precision = SPH_RT_FP64;
   c->cheb_degree = 2;
   c->amg_rebuild = 0;
-  c->amg_theta = 0.08;
+  c->amg_theta = 0.02;
   c->check_every = 4;
   c->kernel_timing = 0;
   c->device = 0;
@@ -184,7 +226,7 @@ extern "C" void sph_rt_destroy(sph_rt *s) {
   if (!s) return;
   if (s->cuda_ready) {
     cudaSetDevice(s->cfg.device);
-    free_all(s);
+    free_everything(s);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     if (s->sc_host) cudaFreeHost(s->sc_host);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -250,7 +292,8 @@ static sph_rt_status alloc_step_vectors(sph_rt *s) {
   for (double **p : full)
     if (!(*p = dalloc<double>(s, n))) return SPH_RT_ENOMEM;
   double **inner[] = {&s->e_old, &s->E_old, &s->e_l, &s->E_l, &s->e_new, &s->Qe, &s->QE, &s->b,
-                      &s->x, &s->r, &s->z, &s->p, &s->q, &s->w, &s->diag, &s->invdiag, &s->gb};
+                      &s->x, &s->r, &s->z, &s->p, &s->q, &s->w, &s->diag, &s->invdiag, &s->gb,
+                      &s->z_old};
   for (double **p : inner)
     if (!(*p = dalloc<double>(s, ni))) return SPH_RT_ENOMEM;
   if (!(s->gersh = dalloc<double>(s, 1))) return SPH_RT_ENOMEM;
@@ -675,6 +718,24 @@ extern "C" sph_rt_status sph_rt_get_properties(sph_rt *s, double *T, double *sig
     if (rc) return rc;
     SPH_CUDA(s, cudaMemcpyAsync(outs[k], s->tmp_n, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
     SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  }
+  return SPH_RT_OK;
+}
+
+namespace sphrt {
+int amg_levels(const sph_rt *s, int64_t *rows, int64_t *nnz, int maxl);
+}
+
+extern "C" sph_rt_status sph_rt_get_amg_info(sph_rt *s, int32_t *nlevels, int64_t *rows,
+                                             int64_t *nnz, int32_t max_levels) {
+  if (!s || !nlevels) return SPH_RT_EINVAL;
+  if (!s->amg_ready) return set_error(s, SPH_RT_ESTATE, "no AMG hierarchy (step with precond AMG first)");
+  int64_t r[64], z[64];
+  int k = amg_levels(s, r, z, 64);
+  *nlevels = k;
+  for (int l = 0; l < k && l < max_levels; ++l) {
+    if (rows) rows[l] = r[l];
+    if (nnz) nnz[l] = z[l];
   }
   return SPH_RT_OK;
 }

@@ -67,6 +67,22 @@ class Stats(C.Structure):
         return list(self.krylov_iters_per_outer[: self.outer_iters])
 
 
+SRV_QUEUED, SRV_ADMITTED, SRV_RUNNING, SRV_DONE, SRV_FAILED = 0, 1, 2, 3, 4
+
+
+class SrvConfig(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("max_resident", C.c_int32),
+                ("steps_per_tick", C.c_int32), ("hbm_budget_bytes", C.c_double),
+                ("device", C.c_int32)]
+
+
+class SrvInfo(C.Structure):
+    _fields_ = [("queued", C.c_int32), ("resident", C.c_int32), ("peak_resident", C.c_int32),
+                ("resident_bytes", C.c_int64), ("peak_bytes", C.c_int64),
+                ("particle_steps", C.c_int64), ("t_first_submit", C.c_double),
+                ("t_last_done", C.c_double)]
+
+
 class SphRtError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_NAMES.get(status, status)}: {msg}")
@@ -91,9 +107,18 @@ _SIGNATURES = [
     ("sph_rt_get_operator", C.c_int, [_P, _P, _P, _P, _P, _P]),
     ("sph_rt_get_properties", C.c_int, [_P] * 7),
     ("sph_rt_kernel_stats", C.c_int, [_P, _P, _P, _P, C.c_int]),
+    ("sph_rt_get_amg_info", C.c_int, [_P, _P, _P, _P, C.c_int32]),
     ("sph_rt_launch_count", C.c_int64, [_P]),
     ("sph_rt_last_error", C.c_char_p, [_P]),
     ("sph_rt_destroy", None, [_P]),
+    ("sph_rt_srv_default_config", None, [_P]),
+    ("sph_rt_srv_create", C.c_int, [_P, _P]),
+    ("sph_rt_srv_submit", C.c_int, [_P, _P, C.c_int64] + [_P] * 11 + [C.c_int32, C.c_double, _P]),
+    ("sph_rt_srv_poll", C.c_int, [_P, C.c_int64, _P, _P]),
+    ("sph_rt_srv_wait", C.c_int, [_P, C.c_int64]),
+    ("sph_rt_srv_result", C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.c_int64]),
+    ("sph_rt_srv_info", C.c_int, [_P, _P]),
+    ("sph_rt_srv_destroy", None, [_P]),
 ]
 
 
@@ -283,6 +308,14 @@ class Solver:
                                                 int(reset)))
         return n.value, ms.value, by.value
 
+    def amg_info(self):
+        nl = C.c_int32()
+        rows = np.zeros(16, dtype=np.int64)
+        nnz = np.zeros(16, dtype=np.int64)
+        self._check(self._L.sph_rt_get_amg_info(self._h, C.byref(nl), _ptr(rows), _ptr(nnz), 16))
+        k = min(nl.value, 16)
+        return list(zip(rows[:k].tolist(), nnz[:k].tolist()))
+
     def launch_count(self) -> int:
         return int(self._L.sph_rt_launch_count(self._h))
 
@@ -305,3 +338,79 @@ def solver_for(workload, **overrides) -> Solver:
     S.set_particles(P.pos, P.mass, P.rho, P.h, P.sigma0, P.kind,
                     P.copy_of if np.any(P.kind == COPY) else None, workload.e0, workload.E0)
     return S
+
+
+class Server:
+    """Continuous-batching request loop (sph_rt_srv_* in sph_rt.h)."""
+
+    def __init__(self, **overrides):
+        self._L = load()
+        cfg = SrvConfig()
+        self._L.sph_rt_srv_default_config(C.byref(cfg))
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        h = C.c_void_p()
+        rc = self._L.sph_rt_srv_create(C.byref(cfg), C.byref(h))
+        if rc != OK:
+            raise SphRtError(rc, "sph_rt_srv_create failed")
+        self._h = h
+        self._n = {}
+
+    def submit(self, cfg: Config, particles, e0, E0, steps: int, dt: float, Qe=None, QE=None):
+        P = particles
+        n = P.pos.shape[0]
+        pos = _f64(P.pos)
+        arrs = [_f64(a, n) for a in (P.mass, P.rho, P.h, P.sigma0)]
+        kind = np.ascontiguousarray(P.kind, dtype=np.int32)
+        copy_of = (np.ascontiguousarray(P.copy_of, dtype=np.int64)
+                   if np.any(kind == COPY) else None)
+        e0, E0 = _f64(e0, n), _f64(E0, n)
+        Qe, QE = _f64(Qe, n), _f64(QE, n)
+        rid = C.c_int64()
+        rc = self._L.sph_rt_srv_submit(self._h, C.byref(cfg), n, _ptr(pos),
+                                       *[_ptr(a) for a in arrs], _ptr(kind), _ptr(copy_of),
+                                       _ptr(e0), _ptr(E0), _ptr(Qe), _ptr(QE), int(steps),
+                                       float(dt), C.byref(rid))
+        if rc != OK:
+            raise SphRtError(rc, "sph_rt_srv_submit failed")
+        self._n[rid.value] = n
+        return rid.value
+
+    def poll(self, rid):
+        st = C.c_int32()
+        t = np.zeros(3)
+        rc = self._L.sph_rt_srv_poll(self._h, int(rid), C.byref(st), _ptr(t))
+        if rc != OK:
+            raise SphRtError(rc, "unknown request")
+        return st.value, t
+
+    def wait(self, rid):
+        return self._L.sph_rt_srv_wait(self._h, int(rid))
+
+    def result(self, rid):
+        n = self._n[rid]
+        e = np.empty(n)
+        E = np.empty(n)
+        st = Stats()
+        msg = C.create_string_buffer(512)
+        rc = self._L.sph_rt_srv_result(self._h, int(rid), _ptr(e), _ptr(E), C.byref(st), msg, 512)
+        if rc != OK:
+            raise SphRtError(rc, msg.value.decode())
+        return e, E, st
+
+    def info(self):
+        inf = SrvInfo()
+        self._L.sph_rt_srv_info(self._h, C.byref(inf))
+        return inf
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.sph_rt_srv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
