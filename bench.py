@@ -110,6 +110,24 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate_ranks(t_local: float, work_local: float):
+    """Replicas: every rank ran its own job.  Returns (t_max, total_work) over
+    ranks; with one process this is (t_local, work_local).  Uses whatever
+    process group is initialised (NCCL on GPUs, gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_local, work_local
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    wk = torch.tensor([work_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(wk, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(wk.item())
+
+
 def make_workload(name: str):
     if name == "mms3d-lp-64":
         return I.mms_3d_lp(n=64, steps=100)
@@ -333,16 +351,8 @@ def main():
     gpu_ms = ev0.elapsed_time(ev1)
     launches = S.launch_count() - launches0
     k_launch, k_ms, k_bytes = S.kernel_stats(reset=True)
-    t_local = gpu_ms / 1e3
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    else:
-        t_max = t_local
-    value = world * n_int * T * args.steps / t_max
+    t_max, work = aggregate_ranks(gpu_ms / 1e3, float(n_int * T * args.steps))
+    value = work / t_max
 
     # ---- end to end through the host-pointer C ABI ---------------------------
     e2e = None
@@ -378,15 +388,9 @@ def main():
         for _ in range(args.steps):
             job_host()
         torch.cuda.synchronize(dev)
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-
-            tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
+        t_e2e, work_e2e = aggregate_ranks(time.perf_counter() - t0, float(n_int * T * args.steps))
         h2d = (P.pos.nbytes + 6 * n * 8 + n * 4) + T * 4 * n * 8
-        e2e = {"value": world * n_int * T * args.steps / t_e2e, "unit": "particle-steps/s",
+        e2e = {"value": work_e2e / t_e2e, "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(2 * n * 8)}
 
     if rank != 0:

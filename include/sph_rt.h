@@ -81,6 +81,7 @@ typedef struct {
   double amg_theta;     /* AMG strength threshold: j strong for i if |B_ij| >= theta sqrt(B_ii B_jj) */
   int32_t check_every;  /* Krylov iterations queued between host convergence reads */
   int32_t kernel_timing;/* 1: record CUDA events around SpMV launches (sph_rt_kernel_stats) */
+  int32_t autotune;     /* 1: time the SpMV row-group shapes on the first step of a particle set */
   int32_t device;       /* CUDA device ordinal */
   void *stream;         /* cudaStream_t to run on (borrowed); NULL = library-owned stream */
 } sph_rt_config;
@@ -145,6 +146,9 @@ sph_rt_status sph_rt_set_particles_device(sph_rt *s, int64_t n_total, const doub
  *   ghost_e, ghost_E  Dirichlet-ghost values at t^n [n_total] (other entries
  *             ignored); NULL = keep the current ghost values
  *   stats     may be NULL
+ * EINVAL (state unchanged): dt not finite and positive, or a non-finite
+ * source of an interior particle or ghost value of a Dirichlet ghost (checked
+ * on the device before the state is touched).
  */
 sph_rt_status sph_rt_step(sph_rt *s, double dt, const double *Qe, const double *QE,
                           const double *ghost_e, const double *ghost_E, sph_rt_stats *stats);
@@ -267,6 +271,45 @@ sph_rt_status sph_rt_srv_info(sph_rt_srv *srv, sph_rt_srv_info_t *info);
 /* Stop the workers (after their current tick), release every resident
  * request and the server. */
 void sph_rt_srv_destroy(sph_rt_srv *srv);
+
+/* ------------------------------------------------------------------------ */
+/* Batched form: many small problems advanced by one kernel launch per step. */
+/* Each problem gets one thread block that runs its whole step (material     */
+/* data, assembly, material solves and Chebyshev-preconditioned CG with      */
+/* block-local reductions, per-problem convergence); all problems share the  */
+/* configuration (physics, tolerances, cheb_degree).  Like serving, this is a */
+/* runtime form around the paper's method, not part of the method itself.    */
+/* ------------------------------------------------------------------------ */
+typedef struct sph_rt_batch sph_rt_batch;
+
+sph_rt_status sph_rt_batch_create(const sph_rt_config *cfg, sph_rt_batch **out);
+
+/* Add a problem (host arrays as for sph_rt_set_particles; set-up runs now).
+ * *index gets its position in the batch.  Problems can only be added before
+ * the first step. */
+sph_rt_status sph_rt_batch_add(sph_rt_batch *b, int64_t n_total, const double *pos,
+                               const double *mass, const double *rho, const double *h,
+                               const double *sigma0, const int32_t *kind, const int64_t *copy_of,
+                               const double *e0, const double *E0, int32_t *index);
+
+/* Constant sources of one problem (caller order, NULL = 0), used every step. */
+sph_rt_status sph_rt_batch_set_sources(sph_rt_batch *b, int32_t index, const double *Qe,
+                                       const double *QE);
+
+/* One backward-Euler step of every problem in ONE kernel launch.  Per problem
+ * (arrays of sph_rt_batch_size entries, any may be NULL): status (0, or -3 if
+ * it did not converge -- its state is then unchanged), outer iterations,
+ * Krylov iterations, and energy[4k..4k+3] = before, after, source, boundary
+ * inflow.  Returns ENOTCONV if any problem did not converge. */
+sph_rt_status sph_rt_batch_step(sph_rt_batch *b, double dt, int32_t *status,
+                                int32_t *outer_iters, int32_t *krylov_iters, double *energy);
+
+/* State of one problem, caller order (either may be NULL). */
+sph_rt_status sph_rt_batch_get_energies(sph_rt_batch *b, int32_t index, double *e, double *E);
+
+int32_t sph_rt_batch_size(const sph_rt_batch *b);
+const char *sph_rt_batch_last_error(const sph_rt_batch *b);
+void sph_rt_batch_destroy(sph_rt_batch *b);
 
 /* Message of the last failed call on this handle (NULL: of the last failed
  * sph_rt_create on this thread).  Owned by the library; valid until the next

@@ -15,6 +15,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include <map>
 #include <string>
@@ -45,7 +46,7 @@ struct Scalars {
   int done;        // Krylov converged (or aborted)
   int iters;       // Krylov iterations taken
   int breakdown;   // non-positive curvature / NaN seen
-  int pad;
+  int bad_input;   // a step input (source or ghost value) was not finite
   unsigned int counter;  // arrival counter of the last-block reductions
 };
 
@@ -170,38 +171,44 @@ __device__ __forceinline__ T row_reduce(T v) {
 }
 
 // Row-group shape of the SpMV-class kernels: W lanes per row, U loads in flight
-// per lane.  Chosen from the mean row length (or by the autotuner).
+// per lane.  A lane sums its entries (beg + sub + j W, j = 0, 1, ...) in
+// increasing j whatever U is, so results depend on W only.  W follows from the
+// mean row length (deterministic); U may be picked by the autotuner.
 struct RowShape {
   int W, U;
 };
+// W = 4 lanes per row: loads stay sector-coalesced (4 x 8 B = one 32 B sector
+// per row per instruction) while the FP64 reduction tree costs 2 shuffles
+// instead of 4-5 -- on GB300 the FP64 pipe, not HBM, limits a wide-warp CSR
+// sweep.  Very long rows (coarse AMG levels) use 8 lanes.
+__host__ inline int lanes_for_mean(double mean) { return mean <= 160 ? 4 : 8; }
 __host__ inline RowShape shape_for_mean(double mean) {
-  if (mean <= 32) return {8, 4};
-  if (mean <= 64) return {16, 4};
-  if (mean <= 96) return {16, 6};
-  if (mean <= 128) return {16, 8};
-  return {32, 8};
+  int W = lanes_for_mean(mean);
+  int U = (mean / W) <= 6 ? 4 : 8;
+  return {W, U};
 }
 
-// Launch CALL with constexpr W and U set to the supported row-group shape
-// nearest to (W_, U_).
-#define SPH_DISPATCH_SHAPE(W_, U_, CALL)                                   \
-  do {                                                                     \
-    if ((W_) <= 8) {                                                       \
-      constexpr int W = 8, U = 4;                                          \
-      CALL;                                                                \
-    } else if ((W_) == 16 && (U_) <= 4) {                                  \
-      constexpr int W = 16, U = 4;                                         \
-      CALL;                                                                \
-    } else if ((W_) == 16 && (U_) <= 6) {                                  \
-      constexpr int W = 16, U = 6;                                         \
-      CALL;                                                                \
-    } else if ((W_) == 16) {                                               \
-      constexpr int W = 16, U = 8;                                         \
-      CALL;                                                                \
-    } else {                                                               \
-      constexpr int W = 32, U = 8;                                         \
-      CALL;                                                                \
-    }                                                                      \
+// Launch CALL with constexpr W and U set to the supported row-group shape:
+// W in {4, 8}; U in {4, 8}.
+#define SPH_DISPATCH_SHAPE(W_, U_, CALL)            \
+  do {                                              \
+    if ((W_) <= 4) {                                \
+      if ((U_) <= 4) {                              \
+        constexpr int W = 4, U = 4;                 \
+        CALL;                                       \
+      } else {                                      \
+        constexpr int W = 4, U = 8;                 \
+        CALL;                                       \
+      }                                             \
+    } else {                                        \
+      if ((U_) <= 4) {                              \
+        constexpr int W = 8, U = 4;                 \
+        CALL;                                       \
+      } else {                                      \
+        constexpr int W = 8, U = 8;                 \
+        CALL;                                       \
+      }                                             \
+    }                                               \
   } while (0)
 
 // A CSR operator as seen by the SpMV-shaped kernels: off-diagonal entries in
@@ -261,6 +268,8 @@ struct sph_rt {
   int64_t *nbr_ptr = nullptr;  // [n_int + 1]
   int32_t *nbr_col = nullptr;  // slot of the neighbour
   double *nbr_F = nullptr;     // F_ij = W'(r)/r, two-h average
+  int32_t *gcol = nullptr;     // slot whose E neighbour k carries (copy ghosts: the copied one)
+  double *gvx = nullptr, *gvy = nullptr, *gvz = nullptr;  // V_j F_ij x_ij (limiter only)
 
   // operator B = V A (interior rows; unknown index == slot)
   int64_t *mat_ptr = nullptr;
@@ -331,6 +340,20 @@ void timing_begin(sph_rt *s);
 void timing_end(sph_rt *s, double bytes);
 void timing_flush(sph_rt *s);
 }  // namespace sphrt
+
+// Host-side phase trace to stderr, enabled by the environment variable
+// SPH_RT_TRACE=1 (diagnostics only; off by default).
+namespace sphrt {
+bool trace_enabled();
+}
+#define SPH_TRACE(...)                                \
+  do {                                                \
+    if (sphrt::trace_enabled()) {                     \
+      fprintf(stderr, "[sphrt] " __VA_ARGS__);        \
+      fputc('\n', stderr);                            \
+      fflush(stderr);                                 \
+    }                                                 \
+  } while (0)
 
 #define SPH_CUDA(s, call)                                          \
   do {                                                             \

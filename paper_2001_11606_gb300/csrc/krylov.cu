@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -408,6 +409,57 @@ static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first
   return SPH_RT_OK;
 }
 
+// Plain SpMV y = B x (off-diagonal part plus diagonal), for the autotuner.
+template <int W, int U>
+__global__ void spmv_plain_kernel(CsrView<double> A, const double *x, double *y) {
+  const int sub = threadIdx.x % W;
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  for (int64_t i = grp; i < A.n; i += ngrp) {
+    double s = row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, x, sub);
+    s = row_reduce<W>(s);
+    if (sub == 0) y[i] = A.diag[i] * x[i] + s;
+  }
+}
+
+// Autotuner: time every supported row-group shape on the fine operator
+// (3 launches each after one warm-up, CUDA events on the library stream) and
+// keep the fastest for all fine-level SpMV-class kernels of this particle set.
+sph_rt_status autotune_fine_shape(sph_rt *s) {
+  if (s->fine_shape_set) return SPH_RT_OK;
+  CsrView<double> A = fine_view(s);
+  // candidates share W (so the choice cannot change any result bit) and differ in U
+  const int W0 = lanes_for_mean(A.n ? (double)A.nnz / A.n : 0.0);
+  std::vector<RowShape> cands = {{W0, 4}, {W0, 8}};
+  cudaEvent_t e0, e1;
+  SPH_CUDA(s, cudaEventCreate(&e0));
+  SPH_CUDA(s, cudaEventCreate(&e1));
+  float best = 1e30f;
+  RowShape pick = shape_for_mean(A.n ? (double)A.nnz / A.n : 0.0);
+  for (const RowShape &c : cands) {
+    const int gw = grid_cap(s, A.n, kBlock / c.W);
+    float ms = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, s->stream);
+      SPH_DISPATCH_SHAPE(c.W, c.U, (spmv_plain_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(
+                                       A, s->z, s->w)));
+      SPH_LAUNCHED(s);
+    }
+    cudaEventRecord(e1, s->stream);
+    SPH_CUDA(s, cudaEventSynchronize(e1));
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->fine_shape = pick;
+  s->fine_shape_set = true;
+  return SPH_RT_OK;
+}
+
 // Solve B x = b from the warm start in x (row a6).  On return the host mirror
 // s->sc_host holds the final scalars.
 sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
@@ -451,6 +503,8 @@ sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
     SPH_CUDA(s, cudaMemcpyAsync(s->sc_host, s->sc, sizeof(Scalars), cudaMemcpyDeviceToHost,
                                 s->stream));
     SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+    SPH_TRACE("pcg: queued=%d iters=%d done=%d breakdown=%d rnorm2=%g", queued,
+              s->sc_host->iters, s->sc_host->done, s->sc_host->breakdown, s->sc_host->rnorm2);
     if (s->sc_host->done || queued > s->cfg.max_krylov + chunk) break;
   }
   timing_flush(s);

@@ -305,20 +305,30 @@ __global__ void volume_kernel(const double *mass, const double *rho, int64_t n, 
 // --------------------------------------------------------------------------
 // Neighbour search: one warp per interior particle.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ double kernel_dw(int dim, double r, double h) {
-  // dW/dr of the M4 cubic B-spline with support 2h
-  const double pi = 3.141592653589793;
-  double norm = dim == 3 ? (1.0 / pi) / (h * h * h)
-                         : (dim == 2 ? (10.0 / (7.0 * pi)) / (h * h) : (2.0 / 3.0) / h);
-  double q = r / h;
-  double dw = 0.0;
-  if (q < 1.0) {
-    dw = -3.0 * q + 2.25 * q * q;
-  } else if (q < 2.0) {
+// Shape of dW/dq of the M4 cubic B-spline (support q < 2).
+__device__ __forceinline__ double spline_dw(double q) {
+  if (q < 1.0) return -3.0 * q + 2.25 * q * q;
+  if (q < 2.0) {
     double t = 2.0 - q;
-    dw = -0.75 * t * t;
+    return -0.75 * t * t;
   }
-  return norm * dw / h;
+  return 0.0;
+}
+
+// Per-particle kernel coefficients: 1/h and sigma_d / h^(d+1), so that
+// dW/dr(r, h) = sigma_d / h^(d+1) * w'(r / h) needs no division per pair.
+__global__ void kernel_coef_kernel(int64_t n, int dim, const double *h, double *ih, double *cw) {
+  const double pi = 3.141592653589793;
+  const double sd = dim == 3 ? 1.0 / pi : (dim == 2 ? 10.0 / (7.0 * pi) : 2.0 / 3.0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double inv = 1.0 / h[i];
+    double p = inv * inv;  // h^-2
+    if (dim >= 2) p *= inv;
+    if (dim >= 3) p *= inv;
+    ih[i] = inv;
+    cw[i] = sd * p;
+  }
 }
 
 __device__ __forceinline__ double exact_r2(double xi, double yi, double zi, double xj, double yj,
@@ -346,7 +356,8 @@ template <bool FILL>
 __global__ void neighbor_kernel(Grid g, const double *px, const double *py, const double *pz,
                                 const double *h, const int64_t *cell_start,
                                 const unsigned *cell_count, int64_t n_int, int64_t *count,
-                                const int64_t *rowptr, int32_t *cols, double *F) {
+                                const int64_t *rowptr, int32_t *cols, double *F,
+                                const double *ih, const double *cw) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -392,8 +403,10 @@ __global__ void neighbor_kernel(Grid g, const double *px, const double *py, cons
           if (FILL && hit) {
             int64_t at = out + total + __popc(m & ((1u << lane) - 1u));
             cols[at] = (int32_t)j;
-            double r = sqrt(r2);
-            F[at] = 0.5 * (kernel_dw(g.dim, r, hi) + kernel_dw(g.dim, r, h[j])) / r;
+            const double r = sqrt(r2), ir = 1.0 / r;
+            const double dwi = cw[i] * spline_dw(r * ih[i]);
+            const double dwj = cw[j] * spline_dw(r * ih[j]);
+            F[at] = 0.5 * (dwi + dwj) * ir;  // F_ij = W'_ij / r, two-h average
           }
           total += __popc(m);
         }
@@ -587,7 +600,7 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   int gcap = s->num_sms * 8;
   if (gw > gcap) gw = gcap;
   neighbor_kernel<false><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, start, cnt, n_int,
-                                                nc, nullptr, nullptr, nullptr);
+                                                nc, nullptr, nullptr, nullptr, nullptr, nullptr);
   SPH_LAUNCHED(s);
   rc = exclusive_scan(s, nc, n_int, s->nbr_ptr);
   if (rc) return rc;
@@ -600,8 +613,12 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   s->nbr_col = dalloc<int32_t>(s, nnz);
   s->nbr_F = dalloc<double>(s, nnz);
   if (!s->nbr_col || !s->nbr_F) return SPH_RT_ENOMEM;
+  double *ih = dalloc<double>(s, n), *cw = dalloc<double>(s, n);
+  if (!ih || !cw) return SPH_RT_ENOMEM;
+  kernel_coef_kernel<<<grid1(s, n), kBlock, 0, st>>>(n, dim, s->h, ih, cw);
+  SPH_LAUNCHED(s);
   neighbor_kernel<true><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, start, cnt, n_int,
-                                               nullptr, s->nbr_ptr, s->nbr_col, s->nbr_F);
+                                               nullptr, s->nbr_ptr, s->nbr_col, s->nbr_F, ih, cw);
   SPH_LAUNCHED(s);
 
   // operator sparsity
@@ -632,7 +649,7 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   SPH_LAUNCHED(s);
   SPH_CUDA(s, cudaStreamSynchronize(st));
   // set-up scratch back to the free list
-  void *scratch[] = {cx, cy, cz, hc, bbox, key, cnt, cur, cnt64, start, nc, mc, gc};
+  void *scratch[] = {cx, cy, cz, hc, bbox, key, cnt, cur, cnt64, start, nc, mc, gc, ih, cw};
   for (void *p : scratch) dfree(s, p);
   return SPH_RT_OK;
 }

@@ -99,6 +99,77 @@ __global__ void props_grad_kernel(Phys ph, int64_t n_int, const int64_t *nbr_ptr
   }
 }
 
+// a3, gradient part with precomputed pair geometry g_ij = V_j F_ij x_ij and
+// the slot whose E a neighbour carries (its own, or the copied particle's):
+// grad E_i = sum_j (E_j - E_i) g_ij.  W lanes per row, U entries in flight.
+template <int W, int U>
+__global__ void props_grad_pre_kernel(Phys ph, int64_t n_int, const int64_t *nbr_ptr,
+                                      const int32_t *gcol, const double *gvx, const double *gvy,
+                                      const double *gvz, const double *E, const double *sigma,
+                                      double *R, double *lambda, double *D) {
+  const int sub = threadIdx.x % W;
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  for (int64_t i = grp; i < n_int; i += ngrp) {
+    const double Ei = E[i];
+    const int64_t beg = nbr_ptr[i], end = nbr_ptr[i + 1];
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int64_t k = beg + sub; k < end; k += (int64_t)W * U) {
+      int32_t c[U];
+      double ax[U], ay[U], az[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t kk = k + (int64_t)u * W;
+        const bool ok = kk < end;
+        c[u] = ok ? __ldg(gcol + kk) : -1;
+        ax[u] = ok ? __ldg(gvx + kk) : 0.0;
+        ay[u] = ok ? __ldg(gvy + kk) : 0.0;
+        az[u] = ok ? __ldg(gvz + kk) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c[u] < 0) continue;
+        const double dE = __ldg(E + c[u]) - Ei;
+        gx += dE * ax[u];
+        gy += dE * ay[u];
+        gz += dE * az[u];
+      }
+    }
+    gx = row_reduce<W>(gx);
+    gy = row_reduce<W>(gy);
+    gz = row_reduce<W>(gz);
+    if (sub == 0) {
+      double gn = sqrt(gx * gx + gy * gy + gz * gz);
+      double Es = Ei > 1e-300 ? Ei : 1e-300;
+      double Ri = gn / (sigma[i] * Es);
+      double lam = limiter_lambda(ph.limiter, ph.larsen_k, Ri);
+      R[i] = Ri;
+      lambda[i] = lam;
+      D[i] = ph.c * lam / sigma[i];
+    }
+  }
+}
+
+// pair geometry for the gradient (once per particle set)
+__global__ void grad_geom_kernel(int64_t n_int, const int64_t *nbr_ptr, const int32_t *nbr_col,
+                                 const double *nbr_F, const double *px, const double *py,
+                                 const double *pz, const double *V, const int32_t *kind,
+                                 const int32_t *copysrc, int32_t *gcol, double *gvx, double *gvy,
+                                 double *gvz) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double xi = px[i], yi = py[i], zi = pz[i];
+    for (int64_t k = nbr_ptr[i]; k < nbr_ptr[i + 1]; ++k) {
+      const int32_t j = nbr_col[k];
+      gcol[k] = kind[j] == SPH_RT_COPY ? copysrc[j] : j;
+      const double vf = V[j] * nbr_F[k];
+      gvx[k] = vf * (xi - px[j]);
+      gvy[k] = vf * (yi - py[j]);
+      gvz[k] = vf * (zi - pz[j]);
+    }
+  }
+}
+
 // copy ghosts take every property of the particle they copy
 __global__ void props_copy_kernel(int64_t n_int, int64_t n, const int32_t *copysrc, double *T,
                                   double *sigma, double *f, double *R, double *lambda, double *D) {
@@ -115,8 +186,8 @@ __global__ void props_copy_kernel(int64_t n_int, int64_t n, const int32_t *copys
   }
 }
 
-// a4: values of B for the step; W lanes per row.
-template <int W>
+// a4: values of B for the step; W lanes per row, U entries in flight per lane.
+template <int W, int U>
 __global__ void assemble_kernel(Phys ph, int64_t n_int, const int64_t *mat_ptr,
                                 const int32_t *mat_col, const double *mat_G, double *mat_val,
                                 const int64_t *gh_ptr, const int32_t *gh_slot, const double *gh_W,
@@ -131,12 +202,25 @@ __global__ void assemble_kernel(Phys ph, int64_t n_int, const int64_t *mat_ptr,
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   double gmax = 0.0;
   for (int64_t i = grp; i < n_int; i += ngrp) {
-    double Di = D[i];
+    const double Di = D[i];
+    const int64_t beg = mat_ptr[i], end = mat_ptr[i + 1];
     double offsum = 0.0;
-    for (int64_t k = mat_ptr[i] + sub; k < mat_ptr[i + 1]; k += W) {
-      double v = mat_G[k] * (Di + D[mat_col[k]]);
-      mat_val[k] = v;
-      offsum += v;
+    for (int64_t k = beg + sub; k < end; k += (int64_t)W * U) {
+      int32_t c[U];
+      double g[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t kk = k + (int64_t)u * W;
+        c[u] = kk < end ? __ldg(mat_col + kk) : -1;
+        g[u] = kk < end ? __ldg(mat_G + kk) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c[u] < 0) continue;
+        const double v = g[u] * (Di + __ldg(D + c[u]));
+        mat_val[k + (int64_t)u * W] = v;
+        offsum += v;
+      }
     }
     double wsum = 0.0, gbs = 0.0;
     for (int64_t k = gh_ptr[i] + sub; k < gh_ptr[i + 1]; k += W) {
@@ -145,9 +229,9 @@ __global__ void assemble_kernel(Phys ph, int64_t n_int, const int64_t *mat_ptr,
       wsum += wk;
       gbs += wk * E[j];
     }
-    offsum = group_sum<W>(offsum);
-    wsum = group_sum<W>(wsum);
-    gbs = group_sum<W>(gbs);
+    offsum = row_reduce<W>(offsum);
+    wsum = row_reduce<W>(wsum);
+    gbs = row_reduce<W>(gbs);
     if (sub == 0) {
       double d = V[i] * (1.0 / ph.dt + ph.c * sigma[i] * f[i] + wsum) - offsum;
       diag[i] = d;
@@ -249,6 +333,24 @@ __global__ void newton_kernel(Phys ph, int64_t n_int, const double *rho, const d
     sc->red[2] = out[2];
     sc->red[3] = out[3];
   }
+}
+
+// Step inputs must be finite: sources of interior particles, ghost values of
+// Dirichlet ghosts (caller order).  Sets sc->bad_input.
+__global__ void check_inputs_kernel(int64_t n, const int64_t *caller2slot, const int32_t *kind,
+                                    const double *Qe, const double *QE, const double *ge,
+                                    const double *gE, Scalars *sc) {
+  int bad = 0;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int k = kind[caller2slot[c]];
+    if (k == SPH_RT_INTERIOR) {
+      if ((Qe && !isfinite(Qe[c])) || (QE && !isfinite(QE[c]))) bad = 1;
+    } else if (k == SPH_RT_DIRICHLET) {
+      if ((ge && !isfinite(ge[c])) || (gE && !isfinite(gE[c]))) bad = 1;
+    }
+  }
+  if (bad) atomicExch(&sc->bad_input, 1);
 }
 
 // Totals over interior particles: red[4] = sum m e, red[5] = sum V E.
@@ -397,11 +499,34 @@ sph_rt_status launch_properties(sph_rt *s, double dt) {
                                                    s->T, s->sigma, s->f, s->R, s->lambda, s->D);
   SPH_LAUNCHED(s);
   if (s->cfg.limiter != SPH_RT_LIMITER_NONE) {
-    int W = row_width(s->nnz_nbr, s->n_int);
-    int gr = grid_items(s, s->n_int, kBlock / W);
-    SPH_ROWS_LAUNCH(props_grad_kernel, W, gr, s, ph, s->n_int, s->nbr_ptr, s->nbr_col, s->nbr_F,
-                    s->px, s->py, s->pz, s->V, s->kind, s->copysrc, s->E, s->sigma, s->R,
-                    s->lambda, s->D);
+    // pair geometry once per particle set, if it fits a modest share of memory
+    const double geom_bytes = 28.0 * (double)s->nnz_nbr;
+    if (!s->gvx && geom_bytes < 24e9) {
+      s->gcol = dalloc<int32_t>(s, s->nnz_nbr);
+      s->gvx = dalloc<double>(s, s->nnz_nbr);
+      s->gvy = dalloc<double>(s, s->nnz_nbr);
+      s->gvz = dalloc<double>(s, s->nnz_nbr);
+      if (!s->gcol || !s->gvx || !s->gvy || !s->gvz) return SPH_RT_ENOMEM;
+      grad_geom_kernel<<<grid_items(s, s->n_int, kBlock), kBlock, 0, s->stream>>>(
+          s->n_int, s->nbr_ptr, s->nbr_col, s->nbr_F, s->px, s->py, s->pz, s->V, s->kind,
+          s->copysrc, s->gcol, s->gvx, s->gvy, s->gvz);
+      SPH_LAUNCHED(s);
+    }
+    if (s->gvx) {
+      RowShape sh = shape_for_mean(s->n_int ? (double)s->nnz_nbr / (double)s->n_int : 0.0);
+      int gr = grid_items(s, s->n_int, kBlock / sh.W);
+      SPH_DISPATCH_SHAPE(sh.W, sh.U,
+                         (props_grad_pre_kernel<W, U><<<gr, kBlock, 0, s->stream>>>(
+                             ph, s->n_int, s->nbr_ptr, s->gcol, s->gvx, s->gvy, s->gvz, s->E,
+                             s->sigma, s->R, s->lambda, s->D)));
+      SPH_LAUNCHED(s);
+    } else {
+      int W = row_width(s->nnz_nbr, s->n_int);
+      int gr = grid_items(s, s->n_int, kBlock / W);
+      SPH_ROWS_LAUNCH(props_grad_kernel, W, gr, s, ph, s->n_int, s->nbr_ptr, s->nbr_col,
+                      s->nbr_F, s->px, s->py, s->pz, s->V, s->kind, s->copysrc, s->E, s->sigma,
+                      s->R, s->lambda, s->D);
+    }
   }
   if (s->n > s->n_int) {
     props_copy_kernel<<<grid_items(s, s->n - s->n_int, kBlock), kBlock, 0, s->stream>>>(
@@ -413,11 +538,14 @@ sph_rt_status launch_properties(sph_rt *s, double dt) {
 
 sph_rt_status launch_assembly(sph_rt *s, double dt, double *gersh_out) {
   Phys ph = make_phys(s, dt);
-  int W = row_width(s->nnz_mat, s->n_int);
-  int gr = grid_items(s, s->n_int, kBlock / W);
-  SPH_ROWS_LAUNCH(assemble_kernel, W, gr, s, ph, s->n_int, s->mat_ptr, s->mat_col, s->mat_G,
-                  s->mat_val, s->gh_ptr, s->gh_slot, s->gh_W, s->V, s->sigma, s->f, s->D, s->E,
-                  s->diag, s->invdiag, s->gb, s->partials, &s->sc->counter, gersh_out);
+  RowShape sh = shape_for_mean(s->n_int ? (double)s->nnz_mat / (double)s->n_int : 0.0);
+  int gr = grid_items(s, s->n_int, kBlock / sh.W);
+  SPH_DISPATCH_SHAPE(sh.W, sh.U,
+                     (assemble_kernel<W, U><<<gr, kBlock, 0, s->stream>>>(
+                         ph, s->n_int, s->mat_ptr, s->mat_col, s->mat_G, s->mat_val, s->gh_ptr,
+                         s->gh_slot, s->gh_W, s->V, s->sigma, s->f, s->D, s->E, s->diag,
+                         s->invdiag, s->gb, s->partials, &s->sc->counter, gersh_out)));
+  SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }
 
@@ -437,6 +565,16 @@ sph_rt_status launch_newton(sph_rt *s, double dt, const double *E_new, const dou
   int g = grid_items(s, s->n_int, kBlock);
   newton_kernel<<<g, kBlock, 0, s->stream>>>(ph, s->n_int, s->rho, s->sigma, s->e_old, s->Qe,
                                               E_new, E_prev, e_start, e_out, s->sc, s->partials);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_check_inputs(sph_rt *s, const double *Qe, const double *QE,
+                                  const double *ge, const double *gE) {
+  SPH_CUDA(s, cudaMemsetAsync(&s->sc->bad_input, 0, sizeof(int), s->stream));
+  if (!Qe && !QE && !ge && !gE) return SPH_RT_OK;
+  check_inputs_kernel<<<grid_items(s, s->n, kBlock), kBlock, 0, s->stream>>>(
+      s->n, s->caller2slot, s->kind, Qe, QE, ge, gE, s->sc);
   SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }

@@ -4,6 +4,7 @@
 // material solve until Eq. mat-rad-convergence holds).
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -25,6 +26,8 @@ sph_rt_status launch_rhs(sph_rt *s, double dt);
 sph_rt_status launch_newton(sph_rt *s, double dt, const double *E_new, const double *E_prev,
                             const double *e_start, double *e_out);
 sph_rt_status launch_totals(sph_rt *s, const double *e, const double *E);
+sph_rt_status launch_check_inputs(sph_rt *s, const double *Qe, const double *QE,
+                                  const double *ge, const double *gE);
 sph_rt_status launch_balance(sph_rt *s, double dt, const double *E);
 sph_rt_status launch_ghost_install(sph_rt *s, const double *ge_c, const double *gE_c);
 sph_rt_status launch_copy_sync(sph_rt *s);
@@ -32,6 +35,7 @@ sph_rt_status launch_gather_interior(sph_rt *s, const double *in_c, double *out)
 sph_rt_status launch_scatter_caller(sph_rt *s, const double *in_s, int64_t count, double *out_c);
 sph_rt_status launch_commit(sph_rt *s, const double *e_new, const double *E_new);
 sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged);
+sph_rt_status autotune_fine_shape(sph_rt *s);
 sph_rt_status amg_setup(sph_rt *s);
 void amg_release(sph_rt *s);
 sph_rt_status validate_device_particles(sph_rt *s, int64_t n, const double *pos,
@@ -39,6 +43,14 @@ sph_rt_status validate_device_particles(sph_rt *s, int64_t n, const double *pos,
                                         const double *sigma0, const int32_t *kind,
                                         const int64_t *copy_of, const double *e0,
                                         const double *E0, int64_t *n_int_out);
+
+bool trace_enabled() {
+  static const bool on = [] {
+    const char *v = getenv("SPH_RT_TRACE");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
 
 sph_rt_status set_error(sph_rt *s, sph_rt_status st, const std::string &msg) {
   if (s) s->err = msg;
@@ -99,6 +111,9 @@ void free_all(sph_rt *s) {
   s->have_particles = false;
   s->have_operator = false;
   s->amg_ready = false;
+  s->gcol = nullptr;
+  s->gvx = s->gvy = s->gvz = nullptr;
+  s->amg_gersh = nullptr;
 }
 
 // Return one buffer of the current particle set to the free list.
@@ -148,6 +163,7 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->amg_theta = 0.02;
   c->check_every = 4;
   c->kernel_timing = 0;
+  c->autotune = 1;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -354,7 +370,10 @@ static sph_rt_status set_particles_common(sph_rt *s, int64_t n, const double *po
     dk = b_kind;
     dc = b_copy;
   }
+  SPH_TRACE("set_particles: n=%lld n_int=%lld", (long long)n, (long long)n_int);
   rc = build_particles(s, n, dpos, dm, dr, dh, ds, dk, dc, de, dE, n_int);
+  SPH_TRACE("set_particles: built, nnz_nbr=%lld nnz_mat=%lld rc=%d", (long long)s->nnz_nbr,
+            (long long)s->nnz_mat, (int)rc);
   if (rc) {
     free_all(s);
     return rc;
@@ -367,6 +386,7 @@ static sph_rt_status set_particles_common(sph_rt *s, int64_t n, const double *po
   s->have_particles = true;
   s->have_operator = false;
   s->amg_ready = false;
+  s->fine_shape_set = false;
   return SPH_RT_OK;
 }
 
@@ -445,9 +465,14 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   const int64_t ni = s->n_int;
   const size_t nb = sizeof(double) * ni;
 
-  // energy before the step
+  SPH_TRACE("step: begin n=%lld n_int=%lld nnz=%lld dt=%g", (long long)s->n, (long long)s->n_int,
+            (long long)s->nnz_mat, dt);
+  // input check and energy before the step (one host read for both)
+  if ((rc = launch_check_inputs(s, Qe_c, QE_c, ge_c, gE_c))) return rc;
   if ((rc = launch_totals(s, s->e, s->E))) return rc;
   if ((rc = read_scalars(s))) return rc;
+  if (s->sc_host->bad_input)
+    return set_error(s, SPH_RT_EINVAL, "non-finite source or ghost value");
   st.energy_before = s->sc_host->red[4] + s->sc_host->red[5];
 
   tm.begin(0);
@@ -463,15 +488,20 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   if ((rc = launch_ghost_install(s, ge_c, gE_c))) return rc;
   tm.end();
 
+  SPH_TRACE("step: properties and ghosts queued");
   tm.begin(1);
   if ((rc = launch_assembly(s, dt, s->gersh))) return rc;  // a4
   tm.end();
   double gersh = 0.0;
   SPH_CUDA(s, cudaMemcpyAsync(&gersh, s->gersh, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  SPH_TRACE("step: assembled, gershgorin %g", gersh);
   s->cheb_lmin = 1.0 - gersh;
   s->cheb_lmax = 1.0 + gersh;
   s->have_operator = true;
+  if (s->cfg.autotune && !s->fine_shape_set) {
+    if ((rc = autotune_fine_shape(s))) return rc;
+  }
 
   if (s->cfg.precond == SPH_RT_PRECOND_AMG) {  // a5
     tm.begin(2);
@@ -479,6 +509,7 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
     tm.end();
   }
 
+  SPH_TRACE("step: preconditioner ready (levels %d)", (int)s->levels.size());
   // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}; material solve with E^{n,0}
   SPH_CUDA(s, cudaMemcpyAsync(s->e_old, s->e, nb, cudaMemcpyDeviceToDevice, s->stream));
   SPH_CUDA(s, cudaMemcpyAsync(s->E_old, s->E, nb, cudaMemcpyDeviceToDevice, s->stream));
@@ -496,7 +527,10 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
     if ((rc = launch_rhs(s, dt))) return rc;  // a7 (also x = E^l)
     int kit = 0;
     bool kconv = false;
+    SPH_TRACE("step: outer %d, krylov solve", st.outer_iters);
     if ((rc = pcg_solve(s, &kit, &kconv))) return rc;  // a6
+    SPH_TRACE("step: krylov done iters=%d converged=%d rnorm2=%g thresh2=%g", kit, (int)kconv,
+              s->sc_host->rnorm2, s->sc_host->thresh2);
     tm.end();
     if (!kconv) {
       krylov_fail = true;
@@ -508,6 +542,7 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
     if ((rc = launch_newton(s, dt, s->x, s->E_l, s->e_l, s->e_new))) return rc;  // a8
     tm.end();
     if ((rc = read_scalars(s))) return rc;  // a9
+    SPH_TRACE("step: newton done, changes %g %g", s->sc_host->red[0], s->sc_host->red[1]);
     st.outer_iters++;
     double ce = s->sc_host->red[0], cE = s->sc_host->red[1];
     st.newton_iters_max = std::max(st.newton_iters_max, (int32_t)s->sc_host->red[2]);
@@ -561,14 +596,7 @@ static sph_rt_status step_entry(sph_rt *s, double dt, const double *Qe, const do
   const int64_t n = s->n;
   if (!device) {
     const double *arrs[4] = {Qe, QE, ge, gE};
-    for (int k = 0; k < 4; ++k) {
-      if (!arrs[k]) continue;
-      for (int64_t i = 0; i < n; ++i)
-        if (!isfinite(arrs[k][i]))
-          return set_error(s, SPH_RT_EINVAL, "non-finite source or ghost value at particle " +
-                                                 std::to_string(i));
-    }
-    // stage host arrays on the device (caller order)
+    // stage host arrays on the device (caller order); they are checked there
     double *stage[4] = {s->tmp_n, s->tmp_n2, s->stage_ge, s->stage_gE};
     const double *dptr[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int k = 0; k < 4; ++k) {

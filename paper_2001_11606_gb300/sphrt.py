@@ -45,6 +45,7 @@ class Config(C.Structure):
         ("amg_theta", C.c_double),
         ("check_every", C.c_int32),
         ("kernel_timing", C.c_int32),
+        ("autotune", C.c_int32),
         ("device", C.c_int32),
         ("stream", C.c_void_p),
     ]
@@ -119,6 +120,14 @@ _SIGNATURES = [
     ("sph_rt_srv_result", C.c_int, [_P, C.c_int64, _P, _P, _P, _P, C.c_int64]),
     ("sph_rt_srv_info", C.c_int, [_P, _P]),
     ("sph_rt_srv_destroy", None, [_P]),
+    ("sph_rt_batch_create", C.c_int, [_P, _P]),
+    ("sph_rt_batch_add", C.c_int, [_P, C.c_int64] + [_P] * 10),
+    ("sph_rt_batch_set_sources", C.c_int, [_P, C.c_int32, _P, _P]),
+    ("sph_rt_batch_step", C.c_int, [_P, C.c_double, _P, _P, _P, _P]),
+    ("sph_rt_batch_get_energies", C.c_int, [_P, C.c_int32, _P, _P]),
+    ("sph_rt_batch_size", C.c_int32, [_P]),
+    ("sph_rt_batch_last_error", C.c_char_p, [_P]),
+    ("sph_rt_batch_destroy", None, [_P]),
 ]
 
 
@@ -407,6 +416,72 @@ class Server:
     def close(self):
         if getattr(self, "_h", None):
             self._L.sph_rt_srv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many small problems, one kernel launch per step (sph_rt_batch_* in sph_rt.h)."""
+
+    def __init__(self, cfg: Config):
+        self._L = load()
+        h = C.c_void_p()
+        rc = self._L.sph_rt_batch_create(C.byref(cfg), C.byref(h))
+        if rc != OK:
+            raise SphRtError(rc, self._L.sph_rt_last_error(None).decode())
+        self._h = h
+        self._n = []
+
+    def _check(self, rc):
+        if rc != OK:
+            raise SphRtError(rc, self._L.sph_rt_batch_last_error(self._h).decode())
+        return rc
+
+    def add(self, particles, e0, E0):
+        P = particles
+        n = P.pos.shape[0]
+        arrs = [_f64(a, n) for a in (P.mass, P.rho, P.h, P.sigma0)]
+        kind = np.ascontiguousarray(P.kind, dtype=np.int32)
+        copy_of = (np.ascontiguousarray(P.copy_of, dtype=np.int64)
+                   if np.any(kind == COPY) else None)
+        idx = C.c_int32()
+        self._check(self._L.sph_rt_batch_add(self._h, n, _ptr(_f64(P.pos)), *[_ptr(a) for a in arrs],
+                                             _ptr(kind), _ptr(copy_of), _ptr(_f64(e0, n)),
+                                             _ptr(_f64(E0, n)), C.byref(idx)))
+        self._n.append(n)
+        return idx.value
+
+    def set_sources(self, index, Qe=None, QE=None):
+        n = self._n[index]
+        self._check(self._L.sph_rt_batch_set_sources(self._h, int(index), _ptr(_f64(Qe, n)),
+                                                     _ptr(_f64(QE, n))))
+
+    def step(self, dt, raise_on_error=True):
+        K = len(self._n)
+        st = np.zeros(K, dtype=np.int32)
+        ou = np.zeros(K, dtype=np.int32)
+        kr = np.zeros(K, dtype=np.int32)
+        en = np.zeros(4 * K)
+        rc = self._L.sph_rt_batch_step(self._h, float(dt), _ptr(st), _ptr(ou), _ptr(kr), _ptr(en))
+        if raise_on_error:
+            self._check(rc)
+        return rc, st, ou, kr, en.reshape(K, 4)
+
+    def get_energies(self, index):
+        n = self._n[index]
+        e = np.empty(n)
+        E = np.empty(n)
+        self._check(self._L.sph_rt_batch_get_energies(self._h, int(index), _ptr(e), _ptr(E)))
+        return e, E
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.sph_rt_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

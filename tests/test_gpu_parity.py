@@ -303,3 +303,21 @@ def test_full_size_two_steps_match_oracle(full_size):
     eg, Eg, _ = S2.get_energies()
     m = w.particles.kind == 0
     assert rel_err(eg, e, m) < 1e-10 and rel_err(Eg, E, m) < 1e-10
+
+
+def test_non_finite_step_input_is_rejected_without_state_change():
+    w = I.mms_2d(n=16)
+    S = sphrt.solver_for(w)
+    e0, E0, _ = S.get_energies()
+    Qe, QE, ge, gE = w.step_inputs(1)
+    QE = QE.copy()
+    QE[np.flatnonzero(w.particles.kind == 0)[5]] = np.nan
+    rc, st = S.step(w.dt, Qe, QE, ge, gE, raise_on_error=False)
+    assert rc == sphrt.EINVAL and "non-finite" in S.last_error()
+    e1, E1, _ = S.get_energies()
+    assert np.array_equal(e0, e1) and np.array_equal(E0, E1)
+    # a NaN on a ghost entry of a source array is ignored (ghost sources are unused)
+    QE2 = w.step_inputs(1)[1].copy()
+    QE2[np.flatnonzero(w.particles.kind == 1)[0]] = np.nan
+    rc, st = S.step(w.dt, Qe, QE2, ge, gE, raise_on_error=False)
+    assert rc == sphrt.OK
