@@ -36,7 +36,9 @@ def sources():
 def _fingerprint() -> str:
     h = hashlib.sha256()
     files = sources() + [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))
-                         if f.endswith(".cuh")] + [os.path.join(INCLUDE, "sph_rt.h")]
+                         if f.endswith(".cuh")] + [os.path.join(INCLUDE, f)
+                                                   for f in sorted(os.listdir(INCLUDE))
+                                                   if f.endswith(".h")]
     for f in files:
         with open(f, "rb") as fh:
             h.update(f.encode())

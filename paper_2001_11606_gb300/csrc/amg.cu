@@ -421,10 +421,12 @@ __global__ void resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *
   const int sub = threadIdx.x % W;
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
-  for (int64_t i = grp; i < A.n; i += ngrp) {
-    VT s = row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub);
+  for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < A.n;
+    VT s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub) : VT(0);
     s = row_reduce<W>(s);
-    if (sub == 0) res[i] = r[i] - ((VT)A.diag[i] * z[i] + s);
+    if (active && sub == 0) res[i] = r[i] - ((VT)A.diag[i] * z[i] + s);
   }
 }
 
@@ -449,6 +451,59 @@ __global__ void prolong_kernel(int64_t n, const int32_t *agg, const VT *zc, VT *
     int32_t a = agg[i];
     if (a >= 0) z[i] += zc[a];
   }
+}
+
+// Coarsest level: the whole Chebyshev solve (zero guess, `degree` steps over
+// [lo, hi]) in ONE block, with r, z, the direction and the ping-pong buffer in
+// shared memory (4 n values); replaces `degree` separate tiny launches.
+constexpr int kCoarseBlockRows = 1536;  // 4 x 1536 doubles = 48 KiB of shared memory
+template <int W, typename MT, typename VT>
+__global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const VT *r_g, VT *z_g,
+                                                           int degree, double lo, double hi,
+                                                           const Scalars *sc) {
+  if (sc && sc->done) return;
+  extern __shared__ unsigned char smem_raw[];
+  VT *r = reinterpret_cast<VT *>(smem_raw);
+  VT *zb0 = r + A.n, *zb1 = zb0 + A.n, *d = zb1 + A.n;
+  const int64_t n = A.n;
+  double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  if (!(delta > 1e-12 * theta)) degree = 1;
+  double sigma1 = degree > 1 ? theta / delta : 1.0, rho0 = 1.0 / sigma1;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    VT ri = r_g[i];
+    r[i] = ri;
+    VT di = (VT)(A.invdiag[i] * ri / theta);
+    d[i] = di;
+    zb0[i] = di;
+  }
+  __syncthreads();
+  VT *zin = zb0, *zout = zb1;
+  const int sub = threadIdx.x % W, grp = threadIdx.x / W, ngrp = blockDim.x / W;
+  for (int k = 1; k < degree; ++k) {
+    double rho1 = 1.0 / (2.0 * sigma1 - rho0);
+    const VT c1 = (VT)(rho1 * rho0), c2 = (VT)(2.0 * rho1 / delta);
+    for (int64_t wb = warp_first_group<W>(grp); wb < n; wb += ngrp) {
+      const int64_t i = wb + group_in_warp<W>(grp);
+      const bool active = i < n;
+      VT s = 0;
+      if (active)
+        for (int64_t kk = A.ptr[i] + sub; kk < A.ptr[i + 1]; kk += W)
+          s += (VT)A.val[kk] * zin[A.col[kk]];
+      s = row_reduce<W>(s);
+      if (active && sub == 0) {
+        VT res = r[i] - ((VT)A.diag[i] * zin[i] + s);
+        VT di = c1 * d[i] + c2 * (VT)A.invdiag[i] * res;
+        d[i] = di;
+        zout[i] = zin[i] + di;
+      }
+    }
+    __syncthreads();
+    VT *t = zin;
+    zin = zout;
+    zout = t;
+    rho0 = rho1;
+  }
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) z_g[i] = zin[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -788,6 +843,12 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
     double lo = 1.0 - L->gersh, hi = 1.0 + L->gersh;
     if (lo < 1e-3 * hi) lo = 1e-3 * hi;
     int cdeg = L->n <= kCoarseTarget * 4 ? 12 : 3 * deg;
+    if (L->n <= kCoarseBlockRows && l > 0) {
+      const size_t smem = 4 * sizeof(T) * (size_t)L->n;
+      coarse_cheb_kernel<8, T, T><<<1, 1024, smem, s->stream>>>(A, r, z, cdeg, lo, hi, sc);
+      SPH_LAUNCHED(s);
+      return SPH_RT_OK;
+    }
     return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), cdeg, lo, hi, true, sc);
   }
   const double lmax = L->lmax, lmin = L->lmax / 8.0;

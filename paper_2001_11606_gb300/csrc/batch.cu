@@ -98,10 +98,13 @@ __device__ void b_spmv(const BatchView &v, int64_t r0, int64_t r1, const double 
                        const double *rhs, double *y, int mode) {
   const int sub = threadIdx.x % W;
   const int grp = threadIdx.x / W, ngrp = blockDim.x / W;
-  for (int64_t i = r0 + grp; i < r1; i += ngrp) {
-    double s = row_dot<W, U>(v.mat_ptr[i], v.mat_ptr[i + 1], v.mat_col, v.mat_val, xin, sub);
+  for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < r1;
+    double s = active ? row_dot<W, U>(v.mat_ptr[i], v.mat_ptr[i + 1], v.mat_col, v.mat_val, xin, sub)
+                      : 0.0;
     s = row_reduce<W>(s);
-    if (sub == 0) {
+    if (active && sub == 0) {
       double bx = v.diag[i] * xin[i] + s;
       y[i] = mode ? rhs[i] - bx : bx;
     }
@@ -132,10 +135,14 @@ __device__ void b_cheb(const BatchView &v, int64_t r0, int64_t r1, const double 
     double c1 = rho1 * rho0, c2 = 2.0 * rho1 / delta;
     const double *zin = buf[at];
     double *zout = buf[at ^ 1];
-    for (int64_t i = r0 + grp; i < r1; i += ngrp) {
-      double s = row_dot<W, U>(v.mat_ptr[i], v.mat_ptr[i + 1], v.mat_col, v.mat_val, zin, sub);
+    for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
+      const int64_t i = wb + group_in_warp<W>(grp);
+      const bool active = i < r1;
+      double s = active ? row_dot<W, U>(v.mat_ptr[i], v.mat_ptr[i + 1], v.mat_col, v.mat_val, zin,
+                                        sub)
+                        : 0.0;
       s = row_reduce<W>(s);
-      if (sub == 0) {
+      if (active && sub == 0) {
         double res = r[i] - (v.diag[i] * zin[i] + s);
         double di = c1 * v.d[i] + c2 * v.invdiag[i] * res;
         v.d[i] = di;
@@ -181,10 +188,14 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
   }
   __syncthreads();
   if (ph.limiter != SPH_RT_LIMITER_NONE) {
-    for (int64_t i = r0 + grp; i < r1; i += ngrp) {
-      double xi = v.px[i], yi = v.py[i], zi = v.pz[i], Ei = v.E[i];
+    for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
+      const int64_t i = wb + group_in_warp<W>(grp);
+      const bool active = i < r1;
+      const int64_t ia = active ? i : r0;
+      double xi = v.px[ia], yi = v.py[ia], zi = v.pz[ia], Ei = v.E[ia];
       double gx = 0.0, gy = 0.0, gz = 0.0;
-      for (int64_t kk = v.nbr_ptr[i] + sub; kk < v.nbr_ptr[i + 1]; kk += W) {
+      const int64_t kb = active ? v.nbr_ptr[i] : 0, ke = active ? v.nbr_ptr[i + 1] : 0;
+      for (int64_t kk = kb + sub; kk < ke; kk += W) {
         int32_t j = v.nbr_col[kk];
         int32_t js = v.kind[j] == SPH_RT_COPY ? v.copysrc[j] : j;
         double s = v.V[j] * (v.E[js] - Ei) * v.nbr_F[kk];
@@ -195,7 +206,7 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
       gx = row_reduce<W>(gx);
       gy = row_reduce<W>(gy);
       gz = row_reduce<W>(gz);
-      if (sub == 0) {
+      if (active && sub == 0) {
         double gn = sqrt(gx * gx + gy * gy + gz * gz);
         double Es = Ei > 1e-300 ? Ei : 1e-300;
         double Ri = gn / (v.sigma[i] * Es);
@@ -221,15 +232,19 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
 
   // a4: operator values, diagonal, Dirichlet coupling, Gershgorin bound
   double gmax = 0.0;
-  for (int64_t i = r0 + grp; i < r1; i += ngrp) {
-    double Di = v.D[i], off = 0.0;
-    for (int64_t kk = v.mat_ptr[i] + sub; kk < v.mat_ptr[i + 1]; kk += W) {
+  for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < r1;
+    double Di = active ? v.D[i] : 0.0, off = 0.0;
+    const int64_t mb = active ? v.mat_ptr[i] : 0, me = active ? v.mat_ptr[i + 1] : 0;
+    for (int64_t kk = mb + sub; kk < me; kk += W) {
       double val = v.mat_G[kk] * (Di + v.D[v.mat_col[kk]]);
       v.mat_val[kk] = val;
       off += val;
     }
     double wsum = 0.0, gbs = 0.0;
-    for (int64_t kk = v.gh_ptr[i] + sub; kk < v.gh_ptr[i + 1]; kk += W) {
+    const int64_t hb = active ? v.gh_ptr[i] : 0, he = active ? v.gh_ptr[i + 1] : 0;
+    for (int64_t kk = hb + sub; kk < he; kk += W) {
       int32_t j = v.gh_slot[kk];
       double wk = -v.gh_W[kk] * (Di + v.D[j]);
       wsum += wk;
@@ -238,7 +253,7 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
     off = row_reduce<W>(off);
     wsum = row_reduce<W>(wsum);
     gbs = row_reduce<W>(gbs);
-    if (sub == 0) {
+    if (active && sub == 0) {
       double dd = v.V[i] * (1.0 / ph.dt + ph.c * v.sigma[i] * v.f[i] + wsum) - off;
       v.diag[i] = dd;
       v.invdiag[i] = 1.0 / dd;

@@ -162,6 +162,23 @@ __device__ __forceinline__ VT row_dot(int64_t beg, int64_t end, const int32_t *_
   return s;
 }
 
+// Row loops of W-lane row groups must be WARP-UNIFORM: row_reduce's full-mask
+// shuffles need every lane of the warp, so all the groups of a warp make the
+// same number of passes.  Loop over the warp's base row (the row of its first
+// group) and give each group its offset; a group past the end of the range is
+// inactive (an empty row) but still takes part in the shuffles.
+//   for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
+//     const int64_t i = wb + group_in_warp<W>(grp);
+//     const bool active = i < r1;  ...
+template <int W>
+__device__ __forceinline__ int64_t group_in_warp(int64_t grp) {
+  return grp % (32 / W);
+}
+template <int W>
+__device__ __forceinline__ int64_t warp_first_group(int64_t grp) {
+  return grp - group_in_warp<W>(grp);
+}
+
 // Sum over the W lanes of a row group (W divides 32; groups are aligned).
 template <int W, typename T>
 __device__ __forceinline__ T row_reduce(T v) {

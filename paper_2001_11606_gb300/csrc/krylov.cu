@@ -39,10 +39,12 @@ __global__ void resid_kernel(CsrView<double> A, const double *b, const double *x
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   double acc = 0.0;
-  for (int64_t i = grp; i < A.n; i += ngrp) {
-    double s = row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, x, sub);
+  for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < A.n;
+    double s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, x, sub) : 0.0;
     s = row_reduce<W>(s);
-    if (sub == 0) {
+    if (active && sub == 0) {
       double ri = b[i] - (A.diag[i] * x[i] + s);
       r[i] = ri;
       double ru = ri * invV[i];
@@ -74,10 +76,12 @@ __global__ void spmv_pq_kernel(CsrView<double> A, const double *z, double *q, do
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   double acc = 0.0;
-  for (int64_t i = grp; i < A.n; i += ngrp) {
-    double s = row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub);
+  for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < A.n;
+    double s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub) : 0.0;
     s = row_reduce<W>(s);
-    if (sub == 0) {
+    if (active && sub == 0) {
       double zi = z[i];
       double wi = A.diag[i] * zi + s;
       double qi = first ? wi : wi + beta * q[i];
@@ -223,10 +227,12 @@ __global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT 
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   const VT vc1 = (VT)c1, vc2 = (VT)c2;
-  for (int64_t i = grp; i < A.n; i += ngrp) {
-    VT s = row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z_in, sub);
+  for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < A.n;
+    VT s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z_in, sub) : VT(0);
     s = row_reduce<W>(s);
-    if (sub == 0) {
+    if (active && sub == 0) {
       VT zi = z_in[i];
       VT res = r[i] - ((VT)A.diag[i] * zi + s);
       VT di = vc2 * (VT)A.invdiag[i] * res;
@@ -415,10 +421,12 @@ __global__ void spmv_plain_kernel(CsrView<double> A, const double *x, double *y)
   const int sub = threadIdx.x % W;
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
-  for (int64_t i = grp; i < A.n; i += ngrp) {
-    double s = row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, x, sub);
+  for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < A.n;
+    double s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, x, sub) : 0.0;
     s = row_reduce<W>(s);
-    if (sub == 0) y[i] = A.diag[i] * x[i] + s;
+    if (active && sub == 0) y[i] = A.diag[i] * x[i] + s;
   }
 }
 

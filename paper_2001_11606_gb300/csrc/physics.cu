@@ -73,10 +73,14 @@ __global__ void props_grad_kernel(Phys ph, int64_t n_int, const int64_t *nbr_ptr
   const int sub = threadIdx.x % W;
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
-  for (int64_t i = grp; i < n_int; i += ngrp) {
-    double xi = px[i], yi = py[i], zi = pz[i], Ei = E[i];
+  for (int64_t wb = warp_first_group<W>(grp); wb < n_int; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < n_int;
+    const int64_t ia = active ? i : 0;
+    double xi = px[ia], yi = py[ia], zi = pz[ia], Ei = E[ia];
     double gx = 0.0, gy = 0.0, gz = 0.0;
-    for (int64_t k = nbr_ptr[i] + sub; k < nbr_ptr[i + 1]; k += W) {
+    const int64_t kbeg = active ? nbr_ptr[i] : 0, kend = active ? nbr_ptr[i + 1] : 0;
+    for (int64_t k = kbeg + sub; k < kend; k += W) {
       int32_t j = nbr_col[k];
       int32_t js = kind[j] == SPH_RT_COPY ? copysrc[j] : j;
       double s = V[j] * (E[js] - Ei) * nbr_F[k];
@@ -87,7 +91,7 @@ __global__ void props_grad_kernel(Phys ph, int64_t n_int, const int64_t *nbr_ptr
     gx = group_sum<W>(gx);
     gy = group_sum<W>(gy);
     gz = group_sum<W>(gz);
-    if (sub == 0) {
+    if (active && sub == 0) {
       double gn = sqrt(gx * gx + gy * gy + gz * gz);
       double Es = Ei > 1e-300 ? Ei : 1e-300;
       double Ri = gn / (sigma[i] * Es);
@@ -110,9 +114,11 @@ __global__ void props_grad_pre_kernel(Phys ph, int64_t n_int, const int64_t *nbr
   const int sub = threadIdx.x % W;
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
-  for (int64_t i = grp; i < n_int; i += ngrp) {
-    const double Ei = E[i];
-    const int64_t beg = nbr_ptr[i], end = nbr_ptr[i + 1];
+  for (int64_t wb = warp_first_group<W>(grp); wb < n_int; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < n_int;
+    const double Ei = active ? E[i] : 0.0;
+    const int64_t beg = active ? nbr_ptr[i] : 0, end = active ? nbr_ptr[i + 1] : 0;
     double gx = 0.0, gy = 0.0, gz = 0.0;
     for (int64_t k = beg + sub; k < end; k += (int64_t)W * U) {
       int32_t c[U];
@@ -138,7 +144,7 @@ __global__ void props_grad_pre_kernel(Phys ph, int64_t n_int, const int64_t *nbr
     gx = row_reduce<W>(gx);
     gy = row_reduce<W>(gy);
     gz = row_reduce<W>(gz);
-    if (sub == 0) {
+    if (active && sub == 0) {
       double gn = sqrt(gx * gx + gy * gy + gz * gz);
       double Es = Ei > 1e-300 ? Ei : 1e-300;
       double Ri = gn / (sigma[i] * Es);
@@ -201,9 +207,11 @@ __global__ void assemble_kernel(Phys ph, int64_t n_int, const int64_t *mat_ptr,
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   double gmax = 0.0;
-  for (int64_t i = grp; i < n_int; i += ngrp) {
-    const double Di = D[i];
-    const int64_t beg = mat_ptr[i], end = mat_ptr[i + 1];
+  for (int64_t wb = warp_first_group<W>(grp); wb < n_int; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < n_int;
+    const double Di = active ? D[i] : 0.0;
+    const int64_t beg = active ? mat_ptr[i] : 0, end = active ? mat_ptr[i + 1] : 0;
     double offsum = 0.0;
     for (int64_t k = beg + sub; k < end; k += (int64_t)W * U) {
       int32_t c[U];
@@ -223,7 +231,8 @@ __global__ void assemble_kernel(Phys ph, int64_t n_int, const int64_t *mat_ptr,
       }
     }
     double wsum = 0.0, gbs = 0.0;
-    for (int64_t k = gh_ptr[i] + sub; k < gh_ptr[i + 1]; k += W) {
+    const int64_t gbeg = active ? gh_ptr[i] : 0, gend = active ? gh_ptr[i + 1] : 0;
+    for (int64_t k = gbeg + sub; k < gend; k += W) {
       int32_t j = gh_slot[k];
       double wk = -gh_W[k] * (Di + D[j]);
       wsum += wk;
@@ -232,7 +241,7 @@ __global__ void assemble_kernel(Phys ph, int64_t n_int, const int64_t *mat_ptr,
     offsum = row_reduce<W>(offsum);
     wsum = row_reduce<W>(wsum);
     gbs = row_reduce<W>(gbs);
-    if (sub == 0) {
+    if (active && sub == 0) {
       double d = V[i] * (1.0 / ph.dt + ph.c * sigma[i] * f[i] + wsum) - offsum;
       diag[i] = d;
       invdiag[i] = 1.0 / d;

@@ -195,7 +195,11 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
   return SPH_RT_OK;
 }
 
-static thread_local std::string g_create_error;  // why the last sph_rt_create failed
+static thread_local std::string g_create_error;  // why the last handle-less call failed
+
+namespace sphrt {
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace sphrt
 
 extern "C" sph_rt_status sph_rt_create(const sph_rt_config *cfg, sph_rt **out) {
   if (!out) return SPH_RT_EINVAL;
