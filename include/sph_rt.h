@@ -87,7 +87,8 @@ typedef struct {
 } sph_rt_config;
 
 /* Per-step diagnostics (the paper's columns: outer iterations per step and
- * Krylov iterations per outer iteration, Sec. 4.3; energy balance, Sec. 2.5). */
+ * Krylov iterations per outer iteration, Sec. 4.3 -- the first 64 outer
+ * iterations are recorded; energy balance, Sec. 2.5). */
 typedef struct {
   int32_t outer_iters;
   int32_t krylov_iters_total;

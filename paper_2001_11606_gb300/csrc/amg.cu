@@ -40,7 +40,7 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
 
 constexpr int kUndecided = 1, kRoot = 2, kNonroot = 0, kIsolated = 3;
 constexpr int kHash = 4096;        // shared hash-table slots per coarse row
-constexpr int kCoarseTarget = 512; // stop coarsening below this many rows
+constexpr int kCoarseTarget = 2048; // stop coarsening at or below this many rows
 constexpr int kMaxLevels = 12;
 
 }  // namespace sphrt
@@ -456,7 +456,7 @@ __global__ void prolong_kernel(int64_t n, const int32_t *agg, const VT *zc, VT *
 // Coarsest level: the whole Chebyshev solve (zero guess, `degree` steps over
 // [lo, hi]) in ONE block, with r, z, the direction and the ping-pong buffer in
 // shared memory (4 n values); replaces `degree` separate tiny launches.
-constexpr int kCoarseBlockRows = 1536;  // 4 x 1536 doubles = 48 KiB of shared memory
+constexpr int kCoarseBlockRows = 2048;  // 4 x 2048 doubles = 64 KiB of shared memory
 template <int W, typename MT, typename VT>
 __global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const VT *r_g, VT *z_g,
                                                            int degree, double lo, double hi,
@@ -845,6 +845,14 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
     int cdeg = L->n <= kCoarseTarget * 4 ? 12 : 3 * deg;
     if (L->n <= kCoarseBlockRows && l > 0) {
       const size_t smem = 4 * sizeof(T) * (size_t)L->n;
+      // opt in to more than 48 KiB of dynamic shared memory (once per handle and type)
+      const int bit = sizeof(T) == 8 ? 1 : 2;
+      if (!(s->coarse_smem_optin & bit)) {
+        SPH_CUDA(s, cudaFuncSetAttribute(coarse_cheb_kernel<8, T, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(4 * sizeof(T) * kCoarseBlockRows)));
+        s->coarse_smem_optin |= bit;
+      }
       coarse_cheb_kernel<8, T, T><<<1, 1024, smem, s->stream>>>(A, r, z, cdeg, lo, hi, sc);
       SPH_LAUNCHED(s);
       return SPH_RT_OK;

@@ -326,6 +326,7 @@ struct sph_rt {
   std::vector<SphLevel *> levels;
   bool amg_ready = false;
   double cheb_lmin = 0.0, cheb_lmax = 2.0;  // spectrum bounds of D^{-1} B (Gershgorin)
+  int coarse_smem_optin = 0;                 // shared-memory opt-in done (bit per value type)
   double *gersh = nullptr;                   // device scalar written by the assembly
   double *amg_gersh = nullptr;               // per-level Gershgorin bounds
 

@@ -161,7 +161,7 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->cheb_degree = 2;
   c->amg_rebuild = 0;
   c->amg_theta = 0.02;
-  c->check_every = 4;
+  c->check_every = 8;
   c->kernel_timing = 0;
   c->autotune = 1;
   c->device = 0;
@@ -182,8 +182,8 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
   if (!finite_pos(c->tol_outer_e) || !finite_pos(c->tol_outer_E) || !finite_pos(c->tol_inner_e) ||
       !finite_pos(c->tol_krylov))
     return why = "tolerances must be finite and positive", SPH_RT_EINVAL;
-  if (c->max_outer < 1 || c->max_outer > 64 || c->max_inner_e < 1 || c->max_krylov < 1)
-    return why = "iteration limits must be >= 1 (max_outer <= 64)", SPH_RT_EINVAL;
+  if (c->max_outer < 1 || c->max_outer > 100000 || c->max_inner_e < 1 || c->max_krylov < 1)
+    return why = "iteration limits must be >= 1 (max_outer <= 100000)", SPH_RT_EINVAL;
   if (c->precond < 0 || c->precond > 2) return why = "precond out of range", SPH_RT_EINVAL;
   if (c->precision < 0 || c->precision > 1) return why = "precision out of range", SPH_RT_EINVAL;
   if (c->cheb_degree < 1 || c->cheb_degree > 16)
@@ -540,7 +540,7 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
       krylov_fail = true;
       break;
     }
-    st.krylov_iters_per_outer[st.outer_iters] = kit;
+    if (st.outer_iters < 64) st.krylov_iters_per_outer[st.outer_iters] = kit;
     st.krylov_iters_total += kit;
     tm.begin(4);
     if ((rc = launch_newton(s, dt, s->x, s->E_l, s->e_l, s->e_new))) return rc;  // a8

@@ -328,7 +328,10 @@ def heating_wave(dim: int, n_target: int, sigma0: float, seed: int, steps: int =
     """Cold slab on [0,4]x[0,1]^(d-1) at T=1e-3 driven by a T=1 Dirichlet face at x<0.
 
     Lateral faces reflect (copy ghosts); the far x face holds T=1e-3.
-    Opacity sigma = sigma0 T^-3, Levermore-Pomraning limiter.
+    Opacity sigma = sigma0 T^-3, Levermore-Pomraning limiter.  With the
+    opacities frozen at T^{n-1} = 1e-3 for the whole first step, that step's
+    nonlinear-elimination loop needs a few hundred outer iterations (later
+    steps a handful), so the outer limit is 1000.
     """
     ny = max(2, int(round((n_target / 4.0) ** (1.0 / dim))))
     counts = (4 * ny,) + (ny,) * (dim - 1)
@@ -341,7 +344,7 @@ def heating_wave(dim: int, n_target: int, sigma0: float, seed: int, steps: int =
     E0 = T0**4
     params = dict(dim=dim, a=1.0, c=1.0, cv=1.0, limiter=1, larsen_k=2.0, opacity_exp=-3.0,
                   T_floor=0.0, tol_outer_e=1e-8, tol_outer_E=1e-8, tol_inner_e=1e-13,
-                  tol_krylov=1e-12, max_outer=50, max_inner_e=50, max_krylov=2000)
+                  tol_krylov=1e-12, max_outer=1000, max_inner_e=50, max_krylov=2000)
     return Workload(name=f"wave{dim}d-{P.n_interior}", particles=P, params=params, dt=dt,
                     steps=steps, e0=e0, E0=E0)
 

@@ -28,6 +28,12 @@ def test_library_exports_every_declared_symbol():
     assert sorted(sphrt.exported_symbols()) == names
 
 
+def test_max_outer_beyond_recorded_stats_is_allowed():
+    # the stats record the first 64 outer iterations; the limit itself is larger
+    S = sphrt.Solver(sphrt.default_config(max_outer=1000))
+    S.close()
+
+
 def test_config_struct_matches_defaults():
     cfg = sphrt.default_config()
     assert cfg.dim == 3 and cfg.a == 1.0 and cfg.precond == sphrt.PRECOND_AMG

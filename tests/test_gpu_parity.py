@@ -135,9 +135,14 @@ def test_properties_and_operator_match_oracle(make):
     # self-copy entries fold into the diagonal on both sides
     dg = {k: v for k, v in dg.items() if k[0] != k[1]}
     assert set(dg) == set(do)
-    a = np.array([dg[k] for k in sorted(do)])
-    b = np.array([do[k] for k in sorted(do)])
-    np.testing.assert_allclose(a, b, rtol=1e-13)
+    keys = sorted(do)
+    a = np.array([dg[k] for k in keys])
+    b = np.array([do[k] for k in keys])
+    # entries near the edge of the kernel's support, where W'(q) vanishes like
+    # (2 - q)^2, lose relative precision to cancellation; bound every entry
+    # relative to its row's diagonal
+    scale = np.array([abs(adiag[k[0]]) for k in keys])
+    assert np.all(np.abs(a - b) <= 1e-13 * scale)
 
 
 # ---------------------------------------------------------------------------
