@@ -10,11 +10,12 @@ import pytest
 from paper_2001_11606_gb300 import inputs as I
 from paper_2001_11606_gb300 import sphrt
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "sph_rt.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
+HEADER = os.path.join(INCLUDE, "sph_rt.h")
 
 
-def declared_functions():
-    src = open(HEADER).read()
+def declared_functions(path=HEADER):
+    src = open(path).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(sph_rt_[a-z_0-9]+)\s*\(", src)))
 
@@ -26,6 +27,11 @@ def test_library_exports_every_declared_symbol():
     for name in names:
         assert hasattr(L, name), name
     assert sorted(sphrt.exported_symbols()) == names
+    # every other public header's entry points are exported too
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            for name in declared_functions(os.path.join(INCLUDE, h)):
+                assert hasattr(L, name), (h, name)
 
 
 def test_max_outer_beyond_recorded_stats_is_allowed():
