@@ -40,7 +40,7 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
 
 constexpr int kUndecided = 1, kRoot = 2, kNonroot = 0, kIsolated = 3;
 constexpr int kHash = 4096;        // shared hash-table slots per coarse row
-constexpr int kCoarseTarget = 2048; // stop coarsening at or below this many rows
+constexpr int kCoarseTarget = 512;  // stop coarsening at or below this many rows
 constexpr int kMaxLevels = 12;
 
 }  // namespace sphrt
@@ -416,8 +416,12 @@ __global__ void convert_kernel(int64_t n, const S *in, D *out) {
 // ---------------------------------------------------------------------------
 template <int W, int U, typename MT, typename VT>
 __global__ void resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
-                                   const Scalars *sc) {
-  if (sc && sc->done) return;
+                                   const Scalars *sc, int *wflag) {
+  if (sc && sc->done) {
+    mark_work(wflag, 0);
+    return;
+  }
+  mark_work(wflag, 1);
   const int sub = threadIdx.x % W;
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
@@ -454,48 +458,59 @@ __global__ void prolong_kernel(int64_t n, const int32_t *agg, const VT *zc, VT *
 }
 
 // Coarsest level: the whole Chebyshev solve (zero guess, `degree` steps over
-// [lo, hi]) in ONE block, with r, z, the direction and the ping-pong buffer in
-// shared memory (4 n values); replaces `degree` separate tiny launches.
-constexpr int kCoarseBlockRows = 2048;  // 4 x 2048 doubles = 64 KiB of shared memory
-template <int W, typename MT, typename VT>
+// [lo, hi]) in ONE block with the level's operator AND vectors staged in
+// shared memory, so every step is a few shared-memory passes instead of a
+// separate launch.  Used when the level fits (coarse_smem_bytes <= 200 KiB).
+__host__ inline size_t coarse_smem_bytes(int64_t n, int64_t nnz, size_t mt, size_t vt) {
+  size_t b = (size_t)nnz * (mt + 4) + (size_t)(n + 1) * 4 + (size_t)n * (2 * mt + 4 * vt);
+  return (b + 15) & ~(size_t)15;
+}
+constexpr size_t kCoarseSmemMax = 200 * 1024;
+
+template <typename MT, typename VT>
 __global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const VT *r_g, VT *z_g,
                                                            int degree, double lo, double hi,
                                                            const Scalars *sc) {
   if (sc && sc->done) return;
-  extern __shared__ unsigned char smem_raw[];
-  VT *r = reinterpret_cast<VT *>(smem_raw);
-  VT *zb0 = r + A.n, *zb1 = zb0 + A.n, *d = zb1 + A.n;
-  const int64_t n = A.n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = (int)A.n, nnz = (int)A.nnz;
+  // layout: values, diag, invdiag (MT) | r, z0, z1, d (VT) | cols, ptr (int32)
+  MT *val = reinterpret_cast<MT *>(smem_raw);
+  MT *dg = val + nnz, *idg = dg + n;
+  VT *r = reinterpret_cast<VT *>(idg + n);
+  VT *zb0 = r + n, *zb1 = zb0 + n, *d = zb1 + n;
+  int *col = reinterpret_cast<int *>(d + n);
+  int *ptr = col + nnz;
+  const int64_t base = A.ptr[0];
+  for (int k = threadIdx.x; k < nnz; k += blockDim.x) {
+    val[k] = A.val[base + k];
+    col[k] = A.col[base + k];
+  }
   double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
   if (!(delta > 1e-12 * theta)) degree = 1;
   double sigma1 = degree > 1 ? theta / delta : 1.0, rho0 = 1.0 / sigma1;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) ptr[i] = (int)(A.ptr[i] - base);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    dg[i] = A.diag[i];
+    idg[i] = A.invdiag[i];
     VT ri = r_g[i];
     r[i] = ri;
-    VT di = (VT)(A.invdiag[i] * ri / theta);
+    VT di = (VT)((double)A.invdiag[i] * (double)ri / theta);
     d[i] = di;
     zb0[i] = di;
   }
   __syncthreads();
   VT *zin = zb0, *zout = zb1;
-  const int sub = threadIdx.x % W, grp = threadIdx.x / W, ngrp = blockDim.x / W;
   for (int k = 1; k < degree; ++k) {
     double rho1 = 1.0 / (2.0 * sigma1 - rho0);
     const VT c1 = (VT)(rho1 * rho0), c2 = (VT)(2.0 * rho1 / delta);
-    for (int64_t wb = warp_first_group<W>(grp); wb < n; wb += ngrp) {
-      const int64_t i = wb + group_in_warp<W>(grp);
-      const bool active = i < n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {  // thread per row: no shuffles
       VT s = 0;
-      if (active)
-        for (int64_t kk = A.ptr[i] + sub; kk < A.ptr[i + 1]; kk += W)
-          s += (VT)A.val[kk] * zin[A.col[kk]];
-      s = row_reduce<W>(s);
-      if (active && sub == 0) {
-        VT res = r[i] - ((VT)A.diag[i] * zin[i] + s);
-        VT di = c1 * d[i] + c2 * (VT)A.invdiag[i] * res;
-        d[i] = di;
-        zout[i] = zin[i] + di;
-      }
+      for (int kk = ptr[i]; kk < ptr[i + 1]; ++kk) s += (VT)val[kk] * zin[col[kk]];
+      VT res = r[i] - ((VT)dg[i] * zin[i] + s);
+      VT di = c1 * d[i] + c2 * (VT)idg[i] * res;
+      d[i] = di;
+      zout[i] = zin[i] + di;
     }
     __syncthreads();
     VT *t = zin;
@@ -503,7 +518,7 @@ __global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const 
     zout = t;
     rho0 = rho1;
   }
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) z_g[i] = zin[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) z_g[i] = zin[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -843,17 +858,17 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
     double lo = 1.0 - L->gersh, hi = 1.0 + L->gersh;
     if (lo < 1e-3 * hi) lo = 1e-3 * hi;
     int cdeg = L->n <= kCoarseTarget * 4 ? 12 : 3 * deg;
-    if (L->n <= kCoarseBlockRows && l > 0) {
-      const size_t smem = 4 * sizeof(T) * (size_t)L->n;
+    const size_t smem = coarse_smem_bytes(L->n, L->nnz, sizeof(T), sizeof(T));
+    if (l > 0 && smem <= kCoarseSmemMax) {
       // opt in to more than 48 KiB of dynamic shared memory (once per handle and type)
       const int bit = sizeof(T) == 8 ? 1 : 2;
       if (!(s->coarse_smem_optin & bit)) {
-        SPH_CUDA(s, cudaFuncSetAttribute(coarse_cheb_kernel<8, T, T>,
+        SPH_CUDA(s, cudaFuncSetAttribute(coarse_cheb_kernel<T, T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(4 * sizeof(T) * kCoarseBlockRows)));
+                                         (int)kCoarseSmemMax));
         s->coarse_smem_optin |= bit;
       }
-      coarse_cheb_kernel<8, T, T><<<1, 1024, smem, s->stream>>>(A, r, z, cdeg, lo, hi, sc);
+      coarse_cheb_kernel<T, T><<<1, 1024, smem, s->stream>>>(A, r, z, cdeg, lo, hi, sc);
       SPH_LAUNCHED(s);
       return SPH_RT_OK;
     }
@@ -863,10 +878,14 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
   if ((rc = cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, lmin, lmax, true, sc))) return rc;
   const int gw = gcap(s, L->n, kBlock / A.W);
   T *res = LV::res(L);
+  // fine-level residual sweeps are timed with the other fine SpMV-class kernels;
+  // per row: rowptr, diag, r, z, res
+  int *wf = l == 0 ? timing_begin(s) : nullptr;
   SPH_DISPATCH_SHAPE(A.W, A.U,
                      (resid_level_kernel<W, U, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res,
-                                                                                    sc)));
+                                                                                    sc, wf)));
   SPH_LAUNCHED(s);
+  if (l == 0) timing_end(s, (4.0 + sizeof(T)) * (double)A.nnz + (8.0 + 4.0 * sizeof(T)) * (double)A.n);
   SphLevel *C = s->levels[l + 1];
   restrict_kernel<T><<<gcap(s, C->n, kBlock), kBlock, 0, s->stream>>>(C->n, L->agg_ptr, L->agg_mem,
                                                                       res, LV::r(C), sc);

@@ -336,6 +336,8 @@ struct sph_rt {
 
   // kernel timing
   std::vector<cudaEvent_t> ev_pool;
+  std::vector<double> ev_bytes;   // bytes of each event pair
+  int *ev_flags = nullptr;        // device: work flag of each event pair
   int ev_used = 0;
   int64_t spmv_launches = 0;
   double spmv_ms = 0.0, spmv_bytes = 0.0;
@@ -353,10 +355,16 @@ inline T *dalloc(sph_rt *s, size_t count) {
 void free_all(sph_rt *s);
 void dfree(sph_rt *s, void *p);  // back to the free list (stream-ordered users must sync first)
 int red_grid(const sph_rt *s, int64_t items, int items_per_block);
-// CUDA-event bracketing of fine-operator SpMV-class launches (config.kernel_timing)
-void timing_begin(sph_rt *s);
+// CUDA-event bracketing of fine-operator SpMV-class launches (config.kernel_timing).
+// timing_begin returns the work flag of the launch (nullptr when timing is off):
+// the kernel writes 1 there if it does work and 0 if it returns at once because
+// the solve has converged; only launches that worked are counted.
+int *timing_begin(sph_rt *s);
 void timing_end(sph_rt *s, double bytes);
 void timing_flush(sph_rt *s);
+__device__ __forceinline__ void mark_work(int *wflag, int worked) {
+  if (wflag && blockIdx.x == 0 && threadIdx.x == 0) *wflag = worked;
+}
 }  // namespace sphrt
 
 // Host-side phase trace to stderr, enabled by the environment variable

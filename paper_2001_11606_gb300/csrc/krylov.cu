@@ -34,7 +34,8 @@ __device__ __forceinline__ T ld(const T *p) {
 // ---------------------------------------------------------------------------
 template <int W, int U>
 __global__ void resid_kernel(CsrView<double> A, const double *b, const double *x, double *r,
-                             const double *invV, Scalars *sc, double *partials) {
+                             const double *invV, Scalars *sc, double *partials, int *wflag) {
+  mark_work(wflag, 1);
   const int sub = threadIdx.x % W;
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
@@ -69,8 +70,12 @@ __global__ void resid_kernel(CsrView<double> A, const double *b, const double *x
 // ---------------------------------------------------------------------------
 template <int W, int U>
 __global__ void spmv_pq_kernel(CsrView<double> A, const double *z, double *q, double *p, int first,
-                               Scalars *sc, double *partials) {
-  if (sc->done) return;
+                               Scalars *sc, double *partials, int *wflag) {
+  if (sc->done) {
+    mark_work(wflag, 0);
+    return;
+  }
+  mark_work(wflag, 1);
   const double beta = first ? 0.0 : sc->beta;
   const int sub = threadIdx.x % W;
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
@@ -221,8 +226,12 @@ __global__ void cheb_init_zero_kernel(int64_t n, const VT *r, const MT *invdiag,
 
 template <int W, int U, typename MT, typename VT>
 __global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
-                                 double c1, double c2, const Scalars *sc) {
-  if (sc && sc->done) return;
+                                 double c1, double c2, const Scalars *sc, int *wflag) {
+  if (sc && sc->done) {
+    mark_work(wflag, 0);
+    return;
+  }
+  mark_work(wflag, 1);
   const int sub = threadIdx.x % W;
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
@@ -270,43 +279,45 @@ CsrView<double> fine_view(const sph_rt *s) {
   return A;
 }
 
-// Kernel-time bracketing of fine SpMV launches (config.kernel_timing).
-void timing_begin(sph_rt *s) {
-  if (!s->cfg.kernel_timing) return;
-  if (s->ev_used + 2 > (int)s->ev_pool.size()) {
-    // flush accumulated pairs first
-    if (s->ev_used > 0) {
-      cudaEventSynchronize(s->ev_pool[s->ev_used - 1]);
-      for (int k = 0; k + 1 < s->ev_used; k += 2) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, s->ev_pool[k], s->ev_pool[k + 1]);
-        s->spmv_ms += ms;
-      }
-      s->ev_used = 0;
-    }
-    while ((int)s->ev_pool.size() < 4096) {
+// Kernel-time bracketing of fine SpMV-class launches (config.kernel_timing).
+constexpr int kEventPairs = 2048;
+void timing_flush(sph_rt *s) {
+  if (!s->cfg.kernel_timing || s->ev_used == 0) return;
+  const int pairs = s->ev_used / 2;
+  std::vector<int> flags(pairs, 1);
+  cudaEventSynchronize(s->ev_pool[s->ev_used - 1]);
+  if (s->ev_flags)
+    cudaMemcpy(flags.data(), s->ev_flags, sizeof(int) * pairs, cudaMemcpyDeviceToHost);
+  for (int k = 0; k < pairs; ++k) {
+    if (!flags[k]) continue;  // returned at once: the solve had converged
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->ev_pool[2 * k], s->ev_pool[2 * k + 1]);
+    s->spmv_ms += ms;
+    s->spmv_launches++;
+    s->spmv_bytes += s->ev_bytes[k];
+  }
+  s->ev_used = 0;
+}
+int *timing_begin(sph_rt *s) {
+  if (!s->cfg.kernel_timing) return nullptr;
+  if (s->ev_pool.empty()) {
+    for (int k = 0; k < 2 * kEventPairs; ++k) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) != cudaSuccess) break;
       s->ev_pool.push_back(e);
     }
+    s->ev_bytes.assign(kEventPairs, 0.0);
   }
+  if (!s->ev_flags) s->ev_flags = dalloc<int>(s, kEventPairs);
+  if (s->ev_used + 2 > (int)s->ev_pool.size()) timing_flush(s);
+  const int pair = s->ev_used / 2;
   cudaEventRecord(s->ev_pool[s->ev_used++], s->stream);
+  return s->ev_flags ? s->ev_flags + pair : nullptr;
 }
 void timing_end(sph_rt *s, double bytes) {
   if (!s->cfg.kernel_timing) return;
+  s->ev_bytes[(s->ev_used - 1) / 2] = bytes;
   cudaEventRecord(s->ev_pool[s->ev_used++], s->stream);
-  s->spmv_launches++;
-  s->spmv_bytes += bytes;
-}
-void timing_flush(sph_rt *s) {
-  if (!s->cfg.kernel_timing || s->ev_used == 0) return;
-  cudaEventSynchronize(s->ev_pool[s->ev_used - 1]);
-  for (int k = 0; k + 1 < s->ev_used; k += 2) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, s->ev_pool[k], s->ev_pool[k + 1]);
-    s->spmv_ms += ms;
-  }
-  s->ev_used = 0;
 }
 
 // Algorithmic bytes of the SpMV-class kernels: column index and value per
@@ -338,10 +349,10 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
   const bool fine = A.ptr == s->mat_ptr;
   const double bytes = spmv_class_bytes(A, 8 + 2 * (int)sizeof(MT) + 5 * (int)sizeof(VT));
   auto step = [&](const VT *zin, VT *zout, double c1, double c2) -> sph_rt_status {
-    if (fine) timing_begin(s);
+    int *wf = fine ? timing_begin(s) : nullptr;
     SPH_DISPATCH_SHAPE(A.W, A.U,
                        (cheb_step_kernel<W, U, MT, VT><<<gw, kBlock, 0, s->stream>>>(
-                           A, r, zin, zout, d, c1, c2, sc)));
+                           A, r, zin, zout, d, c1, c2, sc, wf)));
     SPH_LAUNCHED(s);
     if (fine) timing_end(s, bytes);
     return SPH_RT_OK;
@@ -477,18 +488,18 @@ sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
   const double bytes_r = spmv_class_bytes(A, kRowBytesResid);
   const double bytes = spmv_class_bytes(A, kRowBytesSpmvPQ);
   sph_rt_status rc;
-  timing_begin(s);
+  int *wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
                      (resid_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->b, s->x, s->r,
                                                                        s->invV, s->sc,
-                                                                       s->partials)));
+                                                                       s->partials, wf)));
   SPH_LAUNCHED(s);
   timing_end(s, bytes_r);
   if ((rc = precondition(s, A, 1))) return rc;
-  timing_begin(s);
+  wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
                      (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->z, s->q, s->p, 1,
-                                                                         s->sc, s->partials)));
+                                                                         s->sc, s->partials, wf)));
   SPH_LAUNCHED(s);
   timing_end(s, bytes);
   const int chunk = s->cfg.check_every > 0 ? s->cfg.check_every : 1;
@@ -500,10 +511,10 @@ sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
       SPH_LAUNCHED(s);
       if (s->cfg.precision == SPH_RT_MIXED) std::swap(s->z, s->z_old);
       if ((rc = precondition(s, A, 0))) return rc;
-      timing_begin(s);
+      wf = timing_begin(s);
       SPH_DISPATCH_SHAPE(A.W, A.U,
                          (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(
-                             A, s->z, s->q, s->p, 0, s->sc, s->partials)));
+                             A, s->z, s->q, s->p, 0, s->sc, s->partials, wf)));
       SPH_LAUNCHED(s);
       timing_end(s, bytes);
       ++queued;

@@ -114,6 +114,8 @@ void free_all(sph_rt *s) {
   s->gcol = nullptr;
   s->gvx = s->gvy = s->gvz = nullptr;
   s->amg_gersh = nullptr;
+  s->ev_flags = nullptr;
+  s->ev_used = 0;
 }
 
 // Return one buffer of the current particle set to the free list.
