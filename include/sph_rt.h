@@ -58,8 +58,8 @@ enum { SPH_RT_FP64 = 0, SPH_RT_MIXED = 1 };
  * Physics (Sec. 2.1-2.2): B = a T^4, e = c_v T, sigma_a = sigma_t = sigma0 T^p,
  * D = c lambda(R) / sigma_t with R = |grad E| / (sigma_t E) and lambda from
  *   none      lambda = 1/3                      (Fick's law, Eq. diffusion with 1/3)
- *   Levermore lambda = (2+R)/(6+3R+R^2)
- *   Larsen    lambda = (3^k + R^k)^(-1/k)
+ *   Levermore lambda = (2+R)/(6+3R+R^2)          (Sec. 2.1, Levermore limiter)
+ *   Larsen    lambda = (3^k + R^k)^(-1/k)        (Sec. 2.1, Larsen limiter)
  * Tolerances (Table tab:tolerances, Eq. mat-rad-convergence):
  *   tol_outer_e / tol_outer_E  max_i |x^{l+1}-x^l| / |x^{l+1}| of the outer loop
  *   tol_inner_e                per-particle Newton |de| <= tol |e|
@@ -81,7 +81,14 @@ typedef struct {
   double amg_theta;     /* AMG strength threshold: j strong for i if |B_ij| >= theta sqrt(B_ii B_jj) */
   int32_t check_every;  /* Krylov iterations queued between host convergence reads */
   int32_t kernel_timing;/* 1: record CUDA events around SpMV launches (sph_rt_kernel_stats) */
-  int32_t autotune;     /* 1: time the SpMV row-group shapes on the first step of a particle set */
+  int32_t autotune;     /* 1: time the fine SpMV loads-in-flight (U = 4 or 8) on the first step
+                           of a particle set; 0 (default): U from the mean row length.  U never
+                           changes a result bit (the lanes per row, W, follow the row length) */
+  int32_t amg_tail;     /* 1: run the small AMG levels (each <= 600k stored entries) of every
+                           V-cycle as one thread-block-cluster launch (bitwise the same result) */
+  int32_t graphs;       /* 1: run each step's outer loop as one CUDA graph with conditional
+                           WHILE nodes (no host round trip per iteration); ignored while
+                           kernel_timing = 1, which needs per-launch events */
   int32_t device;       /* CUDA device ordinal */
   void *stream;         /* cudaStream_t to run on (borrowed); NULL = library-owned stream */
 } sph_rt_config;
@@ -204,8 +211,14 @@ sph_rt_status sph_rt_kernel_stats(sph_rt *s, int64_t *launches, double *total_ms
 sph_rt_status sph_rt_get_amg_info(sph_rt *s, int32_t *nlevels, int64_t *rows, int64_t *nnz,
                                   int32_t max_levels);
 
-/* Number of this library's kernels launched since creation (all kinds). */
+/* Number of this library's kernels launched since creation (all kinds; the
+ * kernels a loop graph ran are counted from its device trip counters). */
 int64_t sph_rt_launch_count(const sph_rt *s);
+
+/* Device-driven outer loop (config.graphs = 1): how many times the loop graph
+ * was captured (once per particle set / AMG hierarchy / dt while nothing else
+ * changes) and launched (once per step).  Either pointer may be NULL. */
+sph_rt_status sph_rt_loop_graph_info(const sph_rt *s, int64_t *captures, int64_t *launches);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: a continuous-batching request loop over many independent        */
@@ -214,7 +227,12 @@ int64_t sph_rt_launch_count(const sph_rt *s);
 /*                                                                          */
 /* Every admitted request is resident on the device in its own handle and   */
 /* stream; worker threads advance resident requests `steps_per_tick` steps  */
-/* at a time, so the work of different requests overlaps on the GPU.  Queued */
+/* at a time, so the work of different requests overlaps on the GPU.  Small  */
+/* requests (n_total <= fuse_max_n) that are ready together and share the   */
+/* configuration, dt and step count are fused: up to fuse_max_k of them run */
+/* as one sph_rt_batch (one persistent launch per step, all steps in one    */
+/* CUDA-graph launch).  A fused request's result is the batched form's      */
+/* result, the same as in a batch of its own.  Queued */
 /* requests are admitted in FIFO order while the device footprint of the    */
 /* resident ones stays within hbm_budget_bytes (an estimate until a request */
 /* is set up, its measured allocation after).  A request's result does not  */
@@ -230,6 +248,8 @@ typedef struct {
   int32_t steps_per_tick;  /* steps a worker advances a request before rotating */
   double hbm_budget_bytes; /* admission budget for resident device memory */
   int32_t device;
+  int64_t fuse_max_n;      /* largest n_total run in a fused batch; 0 = never fuse */
+  int32_t fuse_max_k;      /* most requests in one fused batch (>= 1) */
 } sph_rt_srv_config;
 
 typedef struct {
@@ -237,9 +257,11 @@ typedef struct {
   int64_t resident_bytes, peak_bytes; /* budget accounting */
   int64_t particle_steps;             /* completed interior particle-steps */
   double t_first_submit, t_last_done; /* seconds on the server's steady clock */
+  int64_t fused_requests, fused_batches; /* requests run fused, and fused batches run */
 } sph_rt_srv_info_t;
 
-/* Defaults: 8 workers, 64 resident, 1 step per tick, 120e9-byte budget, device 0. */
+/* Defaults: 8 workers, 64 resident, 1 step per tick, 120e9-byte budget,
+ * device 0, fuse requests of up to 20,000 particles, 64 per batch. */
 void sph_rt_srv_default_config(sph_rt_srv_config *cfg);
 sph_rt_status sph_rt_srv_create(const sph_rt_srv_config *cfg, sph_rt_srv **out);
 
@@ -304,6 +326,18 @@ sph_rt_status sph_rt_batch_set_sources(sph_rt_batch *b, int32_t index, const dou
  * inflow.  Returns ENOTCONV if any problem did not converge. */
 sph_rt_status sph_rt_batch_step(sph_rt_batch *b, double dt, int32_t *status,
                                 int32_t *outer_iters, int32_t *krylov_iters, double *energy);
+
+/* `steps` backward-Euler steps of size dt of every problem with ONE CUDA-graph
+ * launch: the graph holds the `steps` launches of the batched step kernel and
+ * a per-step accumulation, is captured on the first run and replayed by later
+ * runs with the same dt and steps.  A problem whose step does not converge
+ * keeps the state of its last converged step and skips the remaining steps.
+ * Per problem (arrays of sph_rt_batch_size entries, any may be NULL): status
+ * of the run (0, or -3), and outer and Krylov iterations summed over the steps
+ * it ran.  Returns ENOTCONV if any problem failed.  The results equal those of
+ * `steps` calls of sph_rt_batch_step. */
+sph_rt_status sph_rt_batch_run(sph_rt_batch *b, double dt, int32_t steps, int32_t *status,
+                               int32_t *outer_total, int32_t *krylov_total);
 
 /* State of one problem, caller order (either may be NULL). */
 sph_rt_status sph_rt_batch_get_energies(sph_rt_batch *b, int32_t index, double *e, double *E);

@@ -28,20 +28,26 @@
 #include <algorithm>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sphrt {
 
 sph_rt_status exclusive_scan(sph_rt *s, const int64_t *in, int64_t n, int64_t *out);
 template <typename MT, typename VT>
 sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT *d, VT *tmp,
-                         int degree, double lmin, double lmax, bool zero_guess,
-                         const Scalars *sc);
+                         int degree, const ChebCoef *cf, bool zero_guess, const Scalars *sc);
+sph_rt_status launch_cheb_slots(sph_rt *s, int first, const double *gersh_dev,
+                                const std::vector<int> &mode, const std::vector<int> &degree);
 
 constexpr int kUndecided = 1, kRoot = 2, kNonroot = 0, kIsolated = 3;
 constexpr int kHash = 4096;        // shared hash-table slots per coarse row
 constexpr int kCoarseTarget = 512;  // stop coarsening at or below this many rows
 constexpr int kMaxLevels = 12;
+static_assert(1 + kMaxLevels <= kChebSlots, "one Chebyshev slot per AMG level");
 
 }  // namespace sphrt
 
@@ -61,7 +67,6 @@ struct SphLevel {
   // vectors of the V-cycle
   double *r = nullptr, *z = nullptr, *res = nullptr, *d = nullptr, *t = nullptr;
   float *r32 = nullptr, *z32 = nullptr, *res32 = nullptr, *d32 = nullptr, *t32 = nullptr;
-  double lmax = 2.0, gersh = 1.0;
   int W = 32, U = 4;
   std::vector<void *> owned;
 };
@@ -120,7 +125,7 @@ __device__ __forceinline__ bool beats(uint32_t i, uint32_t j) {
 // strength and aggregation
 // ---------------------------------------------------------------------------
 __global__ void strength_kernel(int64_t n, const int64_t *ptr, const int32_t *col,
-                                const double *val, const double *diag, double theta,
+                                const double *val, const double *diag, double theta2,
                                 uint8_t *strong, int *state) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -128,7 +133,8 @@ __global__ void strength_kernel(int64_t n, const int64_t *ptr, const int32_t *co
     double di = diag[i];
     for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
       int32_t j = col[k];
-      bool st = j != i && fabs(val[k]) >= theta * sqrt(di * diag[j]);
+      // |B_ij| >= theta sqrt(B_ii B_jj), squared: no FP64 square root per entry
+      bool st = j != i && val[k] * val[k] >= theta2 * (di * diag[j]);
       strong[k] = st;
       cnt += st;
     }
@@ -367,16 +373,26 @@ __global__ void target_count_kernel(int64_t nsrc, const int32_t *tgt, unsigned *
 }
 
 // Galerkin values: thread per coarse target, fixed-order sum of its sources
+// (8 source indices loaded before their gathers, so the gathers overlap).
 __global__ void galerkin_kernel(int64_t nnz_c, int64_t nc, const int64_t *seg_ptr,
                                 const int32_t *seg_src, int64_t nnz_f, const double *val_f,
                                 const double *diag_f, double *val_c, double *diag_c,
                                 double *invdiag_c) {
+  constexpr int G = 8;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz_c + nc;
        t += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
-    for (int64_t u = seg_ptr[t]; u < seg_ptr[t + 1]; ++u) {
-      int64_t sidx = seg_src[u];
-      acc += sidx < nnz_f ? val_f[sidx] : diag_f[sidx - nnz_f];
+    const int64_t u1 = seg_ptr[t + 1];
+    for (int64_t u = seg_ptr[t]; u < u1; u += G) {
+      int32_t src[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) src[g] = u + g < u1 ? __ldg(seg_src + u + g) : -1;
+      double v[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        v[g] = src[g] < 0 ? 0.0 : (src[g] < nnz_f ? __ldg(val_f + src[g]) : __ldg(diag_f + (src[g] - nnz_f)));
+#pragma unroll
+      for (int g = 0; g < G; ++g) acc += v[g];  // sources in order; padding adds +0.0
     }
     if (t < nnz_c) {
       val_c[t] = acc;
@@ -467,12 +483,12 @@ __host__ inline size_t coarse_smem_bytes(int64_t n, int64_t nnz, size_t mt, size
 }
 constexpr size_t kCoarseSmemMax = 200 * 1024;
 
+// Body of the coarsest-level solve for one block (blockDim.x threads, the
+// shared-memory buffer of coarse_smem_bytes); also run by one block of the
+// cluster-resident V-cycle tail.
 template <typename MT, typename VT>
-__global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const VT *r_g, VT *z_g,
-                                                           int degree, double lo, double hi,
-                                                           const Scalars *sc) {
-  if (sc && sc->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void coarse_cheb_body(const CsrView<MT> &A, const VT *r_g, VT *z_g, const ChebCoef *cf,
+                                 int degree, unsigned char *smem_raw) {
   const int n = (int)A.n, nnz = (int)A.nnz;
   // layout: values, diag, invdiag (MT) | r, z0, z1, d (VT) | cols, ptr (int32)
   MT *val = reinterpret_cast<MT *>(smem_raw);
@@ -482,28 +498,25 @@ __global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const 
   int *col = reinterpret_cast<int *>(d + n);
   int *ptr = col + nnz;
   const int64_t base = A.ptr[0];
+  const double inv_theta = cf->inv_theta;
   for (int k = threadIdx.x; k < nnz; k += blockDim.x) {
     val[k] = A.val[base + k];
     col[k] = A.col[base + k];
   }
-  double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
-  if (!(delta > 1e-12 * theta)) degree = 1;
-  double sigma1 = degree > 1 ? theta / delta : 1.0, rho0 = 1.0 / sigma1;
   for (int i = threadIdx.x; i <= n; i += blockDim.x) ptr[i] = (int)(A.ptr[i] - base);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     dg[i] = A.diag[i];
     idg[i] = A.invdiag[i];
     VT ri = r_g[i];
     r[i] = ri;
-    VT di = (VT)((double)A.invdiag[i] * (double)ri / theta);
+    VT di = (VT)(inv_theta * (double)A.invdiag[i] * (double)ri);
     d[i] = di;
     zb0[i] = di;
   }
   __syncthreads();
   VT *zin = zb0, *zout = zb1;
   for (int k = 1; k < degree; ++k) {
-    double rho1 = 1.0 / (2.0 * sigma1 - rho0);
-    const VT c1 = (VT)(rho1 * rho0), c2 = (VT)(2.0 * rho1 / delta);
+    const VT c1 = (VT)cf->c1[k], c2 = (VT)cf->c2[k];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {  // thread per row: no shuffles
       VT s = 0;
       for (int kk = ptr[i]; kk < ptr[i + 1]; ++kk) s += (VT)val[kk] * zin[col[kk]];
@@ -516,9 +529,191 @@ __global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const 
     VT *t = zin;
     zin = zout;
     zout = t;
-    rho0 = rho1;
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) z_g[i] = zin[i];
+}
+
+template <typename MT, typename VT>
+__global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const VT *r_g, VT *z_g,
+                                                           const ChebCoef *cf, int degree,
+                                                           const Scalars *sc) {
+  if (sc && sc->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  coarse_cheb_body<MT, VT>(A, r_g, z_g, cf, degree, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Cluster-resident V-cycle tail: the levels from `tail_level` down (small
+// operators that live in L2) run as ONE launch of one thread-block cluster.
+// Phases that depend on other rows are separated by cluster barriers instead
+// of kernel boundaries, so a small level costs a few barrier round trips
+// instead of several launches.  Rows of a level are split into contiguous
+// ranges, one per block; every phase repeats the arithmetic of the per-level
+// kernels exactly (same W-lane row sums, same update expressions, same
+// restriction order), so the result is bitwise that of the launched V-cycle.
+// Vectors written inside the launch are read with L2 (.cg) loads.  All
+// control flow is uniform over the cluster: every block passes every barrier.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct TailLevel {
+  CsrView<T> A;
+  const int32_t *agg;      // [n] row of the next level (-1: unaggregated)
+  const int64_t *agg_ptr;  // [n_next + 1] members of each next-level row
+  const int32_t *agg_mem;
+  T *r, *z, *res, *d, *t;
+  const ChebCoef *cf;
+  int deg;
+};
+template <typename T>
+struct TailParams {
+  int nlev;        // levels in the tail; the last one is the coarsest
+  int coarse_smem; // 1: the coarsest solve runs in block 0 from shared memory
+  TailLevel<T> L[kMaxLevels];
+};
+
+template <int W, typename MT, typename VT>
+__device__ __forceinline__ VT row_dot_cg(int64_t beg, int64_t end, const int32_t *__restrict__ col,
+                                         const MT *__restrict__ val, const VT *x, int sub) {
+  constexpr int U = 4;
+  VT s = VT(0);
+  for (int64_t k = beg + sub; k < end; k += (int64_t)W * U) {
+    int32_t c[U];
+    MT v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * W;
+      c[u] = kk < end ? __ldg(col + kk) : -1;
+      v[u] = kk < end ? __ldg(val + kk) : MT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (c[u] >= 0) s += (VT)v[u] * __ldcg(x + c[u]);
+  }
+  return s;
+}
+
+// f(i, s) for the rows [r0, r1) of this block, s = sum_j A_ij x_j (off-diagonal)
+template <int W, typename T, typename F>
+__device__ __forceinline__ void tail_rows(const CsrView<T> &A, const T *x, int64_t r0, int64_t r1,
+                                          F &&f) {
+  const int sub = threadIdx.x % W;
+  const int64_t grp = threadIdx.x / W, ngrp = blockDim.x / W;
+  for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < r1;
+    T s = active ? row_dot_cg<W, T, T>(__ldg(A.ptr + i), __ldg(A.ptr + i + 1), A.col, A.val, x,
+                                       sub)
+                 : T(0);
+    s = row_reduce<W>(s);
+    if (active && sub == 0) f(i, s);
+  }
+}
+template <typename T, typename F>
+__device__ __forceinline__ void tail_rows_w(const CsrView<T> &A, const T *x, int64_t r0,
+                                            int64_t r1, F &&f) {
+  if (A.W <= 4)
+    tail_rows<4>(A, x, r0, r1, f);
+  else
+    tail_rows<8>(A, x, r0, r1, f);
+}
+
+// Chebyshev step k of a level (cheb_step_kernel's arithmetic) on this block's rows
+template <typename T>
+__device__ __forceinline__ void tail_cheb_step(const TailLevel<T> &L, const T *zin, T *zout,
+                                               int k, int64_t r0, int64_t r1) {
+  const double c1 = k > 0 ? L.cf->c1[k] : 0.0, c2 = k > 0 ? L.cf->c2[k] : L.cf->inv_theta;
+  const T vc1 = (T)c1, vc2 = (T)c2;
+  tail_rows_w(L.A, zin, r0, r1, [&](int64_t i, T s) {
+    T zi = __ldcg(zin + i);
+    T res = __ldcg(L.r + i) - ((T)L.A.diag[i] * zi + s);
+    T di = vc2 * (T)L.A.invdiag[i] * res;
+    if (k > 0) di += vc1 * __ldcg(L.d + i);
+    L.d[i] = di;
+    zout[i] = zi + di;
+  });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) vcycle_tail_kernel(const __grid_constant__ TailParams<T> P,
+                                                              const Scalars *sc) {
+  if (sc && sc->done) return;  // uniform: nothing in this launch writes `done`
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int64_t cb = cl.block_rank(), nb = cl.num_blocks();
+  auto lo = [&](int64_t n) { return n * cb / nb; };
+  auto hi = [&](int64_t n) { return n * (cb + 1) / nb; };
+  // Chebyshev from a zero guess over `deg` steps, result in z (cheb_apply's ping-pong)
+  auto cheb_zero = [&](const TailLevel<T> &L, int deg) {
+    T *bufs[2] = {L.z, L.t};
+    const int w0 = (deg - 1) % 2;
+    const int64_t r0 = lo(L.A.n), r1 = hi(L.A.n);
+    const double inv_theta = L.cf->inv_theta;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      T di = (T)(inv_theta * (double)L.A.invdiag[i] * (double)__ldcg(L.r + i));
+      L.d[i] = di;
+      bufs[w0][i] = di;
+    }
+    cl.sync();
+    int at = w0;
+    for (int k = 1; k < deg; ++k) {
+      tail_cheb_step(L, bufs[at], bufs[at ^ 1], k, r0, r1);
+      cl.sync();
+      at ^= 1;
+    }
+  };
+  const int last = P.nlev - 1;
+  // down: pre-smoothing, residual, restriction
+  for (int l = 0; l < last; ++l) {
+    const TailLevel<T> &L = P.L[l];
+    const TailLevel<T> &C = P.L[l + 1];
+    cheb_zero(L, L.deg);
+    const int64_t r0 = lo(L.A.n), r1 = hi(L.A.n);
+    tail_rows_w(L.A, L.z, r0, r1, [&](int64_t i, T s) {
+      L.res[i] = __ldcg(L.r + i) - ((T)L.A.diag[i] * __ldcg(L.z + i) + s);
+    });
+    cl.sync();
+    for (int64_t I = lo(C.A.n) + threadIdx.x; I < hi(C.A.n); I += blockDim.x) {
+      T acc = 0;
+      for (int64_t m = L.agg_ptr[I]; m < L.agg_ptr[I + 1]; ++m) acc += __ldcg(L.res + L.agg_mem[m]);
+      C.r[I] = acc;
+    }
+    cl.sync();
+  }
+  // coarsest level
+  {
+    const TailLevel<T> &L = P.L[last];
+    if (P.coarse_smem) {
+      if (cb == 0) coarse_cheb_body<T, T>(L.A, L.r, L.z, L.cf, L.deg, smem_raw);
+      cl.sync();
+    } else {
+      cheb_zero(L, L.deg);
+    }
+  }
+  // up: prolongation, post-smoothing from the corrected guess
+  for (int l = last - 1; l >= 0; --l) {
+    const TailLevel<T> &L = P.L[l];
+    const TailLevel<T> &C = P.L[l + 1];
+    const int64_t r0 = lo(L.A.n), r1 = hi(L.A.n);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      int32_t a = L.agg[i];
+      if (a >= 0) L.z[i] = __ldcg(L.z + i) + __ldcg(C.z + a);
+    }
+    cl.sync();
+    T *bufs[2] = {L.z, L.t};
+    const int w0 = (L.deg - 1) % 2;
+    if (w0 == 0) {  // the guess is read from bufs[1]
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) L.t[i] = __ldcg(L.z + i);
+      cl.sync();
+    }
+    tail_cheb_step(L, bufs[w0 ^ 1], bufs[w0], 0, r0, r1);
+    cl.sync();
+    int at = w0;
+    for (int k = 1; k < L.deg; ++k) {
+      tail_cheb_step(L, bufs[at], bufs[at ^ 1], k, r0, r1);
+      cl.sync();
+      at ^= 1;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -586,7 +781,8 @@ static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
     if (members) dfree(s, members);
   };
   const int g = gcap(s, n, kBlock);
-  strength_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, L->val, L->diag, s->cfg.amg_theta,
+  strength_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, L->val, L->diag,
+                                        s->cfg.amg_theta * s->cfg.amg_theta,
                                         strong, state);
   SPH_LAUNCHED(s);
   for (int round = 0; round < 200; ++round) {
@@ -734,6 +930,11 @@ static sph_rt_status build_structure(sph_rt *s) {
 }
 
 // numeric set-up of every level from the current fine operator
+// Chebyshev degree of the coarsest-level solve
+static int coarse_degree(const sph_rt *s, const SphLevel *L) {
+  return L->n <= kCoarseTarget * 4 ? 12 : 3 * s->cfg.cheb_degree;
+}
+
 static sph_rt_status numeric(sph_rt *s) {
   for (size_t l = 0; l + 1 < s->levels.size(); ++l) {
     SphLevel *L = s->levels[l], *C = s->levels[l + 1];
@@ -742,8 +943,8 @@ static sph_rt_status numeric(sph_rt *s) {
         C->invdiag);
     SPH_LAUNCHED(s);
   }
-  // Gershgorin bounds of every level (one host read for all)
-  std::vector<double> g(s->levels.size(), 1.0);
+  // Gershgorin bounds of every level, turned into Chebyshev coefficients on
+  // the device (slot 1 + l): no host read
   if (!s->amg_gersh) s->amg_gersh = dalloc<double>(s, kMaxLevels);
   double *dg = s->amg_gersh;
   if (!dg) return SPH_RT_ENOMEM;
@@ -754,13 +955,14 @@ static sph_rt_status numeric(sph_rt *s) {
                                                                   dg + l);
     SPH_LAUNCHED(s);
   }
-  SPH_CUDA(s, cudaMemcpyAsync(g.data(), dg, sizeof(double) * g.size(), cudaMemcpyDeviceToHost,
-                              s->stream));
-  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  std::vector<int> mode(s->levels.size()), degree(s->levels.size());
   for (size_t l = 0; l < s->levels.size(); ++l) {
-    s->levels[l]->gersh = g[l];
-    s->levels[l]->lmax = 1.0 + g[l];
+    const bool coarsest = l + 1 == s->levels.size();
+    mode[l] = coarsest ? 2 : 1;
+    degree[l] = coarsest ? coarse_degree(s, s->levels[l]) : s->cfg.cheb_degree;
   }
+  sph_rt_status rc = launch_cheb_slots(s, 1, dg, mode, degree);
+  if (rc) return rc;
   if (s->cfg.precision == SPH_RT_MIXED) {
     for (SphLevel *L : s->levels) {
       if (!L->val32) {
@@ -790,10 +992,17 @@ static sph_rt_status numeric(sph_rt *s) {
   return SPH_RT_OK;
 }
 
+template <typename T>
+static void tail_setup(sph_rt *s);
+
 sph_rt_status amg_setup(sph_rt *s) {
   sph_rt_status rc;
   if (!s->amg_ready || s->cfg.amg_rebuild) {
     if ((rc = build_structure(s))) return rc;
+    if (s->cfg.precision == SPH_RT_MIXED)
+      tail_setup<float>(s);
+    else
+      tail_setup<double>(s);
   }
   return numeric(s);
 }
@@ -846,18 +1055,109 @@ struct LevelVecs<float> {
   static float *t(SphLevel *L) { return L->t32; }
 };
 
+// Levels at or below this many stored entries (~7 MB in FP64) may run in the
+// cluster-resident tail; the tail must hold at least two levels.
+constexpr int64_t kTailMaxNnz = 600000;
+
+template <typename T>
+static sph_rt_status launch_tail(sph_rt *s, size_t l0, const T *r, T *z, const Scalars *sc) {
+  using LV = LevelVecs<T>;
+  TailParams<T> P;
+  memset(&P, 0, sizeof P);
+  P.nlev = (int)(s->levels.size() - l0);
+  for (int m = 0; m < P.nlev; ++m) {
+    SphLevel *L = s->levels[l0 + m];
+    TailLevel<T> &t = P.L[m];
+    t.A = LV::view(L);
+    t.agg = L->agg;
+    t.agg_ptr = L->agg_ptr;
+    t.agg_mem = L->agg_mem;
+    t.r = m == 0 ? const_cast<T *>(r) : LV::r(L);
+    t.z = m == 0 ? z : LV::z(L);
+    t.res = LV::res(L);
+    t.d = LV::d(L);
+    t.t = LV::t(L);
+    t.cf = s->cheb_slots + 1 + l0 + m;
+    t.deg = m + 1 == P.nlev ? coarse_degree(s, L) : s->cfg.cheb_degree;
+  }
+  SphLevel *Lc = s->levels.back();
+  const size_t smem = coarse_smem_bytes(Lc->n, Lc->nnz, sizeof(T), sizeof(T));
+  P.coarse_smem = 1;  // tail_setup only enables the tail when the coarsest level fits
+  cudaLaunchConfig_t lc;
+  memset(&lc, 0, sizeof lc);
+  lc.gridDim = dim3((unsigned)s->tail_cluster);
+  lc.blockDim = dim3(1024);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)s->tail_cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  SPH_CUDA(s, cudaLaunchKernelEx(&lc, vcycle_tail_kernel<T>, P, sc));
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+// Decide where the cluster tail starts (0 = no tail) and its cluster size:
+// 16 blocks where the device can co-schedule them, else 8.
+template <typename T>
+static void tail_setup(sph_rt *s) {
+  s->tail_level = 0;
+  s->tail_cluster = 0;
+  const int nl = (int)s->levels.size();
+  if (nl < 3 || !s->cfg.amg_tail) return;
+  int l0 = nl;
+  while (l0 > 1 && s->levels[l0 - 1]->nnz <= kTailMaxNnz) --l0;
+  if (nl - l0 < 2) return;
+  SphLevel *Lc = s->levels.back();
+  const size_t smem = coarse_smem_bytes(Lc->n, Lc->nnz, sizeof(T), sizeof(T));
+  if (smem > kCoarseSmemMax) return;
+  auto kern = vcycle_tail_kernel<T>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kCoarseSmemMax) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaGetLastError();
+  for (int cl : {16, 8}) {
+    cudaLaunchConfig_t lc;
+    memset(&lc, 0, sizeof lc);
+    lc.gridDim = dim3((unsigned)cl);
+    lc.blockDim = dim3(1024);
+    lc.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kern, &lc) == cudaSuccess && clusters >= 1) {
+      s->tail_level = l0;
+      s->tail_cluster = cl;
+      return;
+    }
+    cudaGetLastError();
+  }
+}
+
 template <typename T>
 static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars *sc) {
   using LV = LevelVecs<T>;
+  if (s->tail_level > 0 && l == (size_t)s->tail_level) return launch_tail<T>(s, l, r, z, sc);
   SphLevel *L = s->levels[l];
   CsrView<T> A = LV::view(L);
   const int deg = s->cfg.cheb_degree;
   sph_rt_status rc;
   if (l + 1 == s->levels.size()) {
     // coarsest level: Chebyshev solve over the whole Gershgorin interval
-    double lo = 1.0 - L->gersh, hi = 1.0 + L->gersh;
-    if (lo < 1e-3 * hi) lo = 1e-3 * hi;
-    int cdeg = L->n <= kCoarseTarget * 4 ? 12 : 3 * deg;
+    const int cdeg = coarse_degree(s, L);
+    const ChebCoef *cf = s->cheb_slots + 1 + l;
     const size_t smem = coarse_smem_bytes(L->n, L->nnz, sizeof(T), sizeof(T));
     if (l > 0 && smem <= kCoarseSmemMax) {
       // opt in to more than 48 KiB of dynamic shared memory (once per handle and type)
@@ -868,14 +1168,14 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
                                          (int)kCoarseSmemMax));
         s->coarse_smem_optin |= bit;
       }
-      coarse_cheb_kernel<T, T><<<1, 1024, smem, s->stream>>>(A, r, z, cdeg, lo, hi, sc);
+      coarse_cheb_kernel<T, T><<<1, 1024, smem, s->stream>>>(A, r, z, cf, cdeg, sc);
       SPH_LAUNCHED(s);
       return SPH_RT_OK;
     }
-    return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), cdeg, lo, hi, true, sc);
+    return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), cdeg, cf, true, sc);
   }
-  const double lmax = L->lmax, lmin = L->lmax / 8.0;
-  if ((rc = cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, lmin, lmax, true, sc))) return rc;
+  const ChebCoef *cf = s->cheb_slots + 1 + l;
+  if ((rc = cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, true, sc))) return rc;
   const int gw = gcap(s, L->n, kBlock / A.W);
   T *res = LV::res(L);
   // fine-level residual sweeps are timed with the other fine SpMV-class kernels;
@@ -893,7 +1193,7 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
   if ((rc = vcycle<T>(s, l + 1, LV::r(C), LV::z(C), sc))) return rc;
   prolong_kernel<T><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(L->n, L->agg, LV::z(C), z, sc);
   SPH_LAUNCHED(s);
-  return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, lmin, lmax, false, sc);
+  return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, false, sc);
 }
 
 sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc) {
@@ -909,6 +1209,42 @@ sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc
     return SPH_RT_OK;
   }
   return vcycle<double>(s, 0, r, z, sc);
+}
+
+// Launch-relevant layout of the hierarchy (sizes, shapes and every buffer the
+// V-cycle touches), appended to the signature of a captured loop graph.
+void amg_signature(const sph_rt *s, std::vector<uint64_t> &sig) {
+  sig.push_back(s->levels.size());
+  sig.push_back((uint64_t)s->tail_level);
+  sig.push_back((uint64_t)s->tail_cluster);
+  for (const SphLevel *L : s->levels) {
+    const uint64_t v[] = {(uint64_t)L->n,
+                          (uint64_t)L->nnz,
+                          (uint64_t)L->W,
+                          (uint64_t)L->U,
+                          (uint64_t)(uintptr_t)L->ptr,
+                          (uint64_t)(uintptr_t)L->col,
+                          (uint64_t)(uintptr_t)L->val,
+                          (uint64_t)(uintptr_t)L->diag,
+                          (uint64_t)(uintptr_t)L->invdiag,
+                          (uint64_t)(uintptr_t)L->val32,
+                          (uint64_t)(uintptr_t)L->diag32,
+                          (uint64_t)(uintptr_t)L->invdiag32,
+                          (uint64_t)(uintptr_t)L->agg,
+                          (uint64_t)(uintptr_t)L->agg_ptr,
+                          (uint64_t)(uintptr_t)L->agg_mem,
+                          (uint64_t)(uintptr_t)L->r,
+                          (uint64_t)(uintptr_t)L->z,
+                          (uint64_t)(uintptr_t)L->res,
+                          (uint64_t)(uintptr_t)L->d,
+                          (uint64_t)(uintptr_t)L->t,
+                          (uint64_t)(uintptr_t)L->r32,
+                          (uint64_t)(uintptr_t)L->z32,
+                          (uint64_t)(uintptr_t)L->res32,
+                          (uint64_t)(uintptr_t)L->d32,
+                          (uint64_t)(uintptr_t)L->t32};
+    sig.insert(sig.end(), v, v + sizeof v / sizeof v[0]);
+  }
 }
 
 // number of levels and rows/nnz per level (for diagnostics)

@@ -52,6 +52,7 @@ struct BatchView {
   int32_t *outer;    // [K]
   int32_t *krylov;   // [K] total Krylov iterations of the step
   double *energy;    // [K*4] before, after, source, boundary
+  const int32_t *run_status;  // [K] multi-step run: nonzero = failed earlier, skip (or NULL)
 };
 
 struct BatchPhys {
@@ -116,14 +117,12 @@ __device__ void b_spmv(const BatchView &v, int64_t r0, int64_t r1, const double 
 // ping-pong between z and v.t, result in z.  Ends with __syncthreads.
 template <int W, int U>
 __device__ void b_cheb(const BatchView &v, int64_t r0, int64_t r1, const double *r, double *z,
-                       int degree, double lo, double hi) {
-  double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
-  if (!(delta > 1e-12 * theta)) degree = 1;
-  double sigma1 = degree > 1 ? theta / delta : 1.0, rho0 = 1.0 / sigma1;
+                       const ChebCoef &cf) {
+  const int degree = cf.degree;
   double *buf[2] = {z, v.t};
   int at = (degree - 1) % 2;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    double di = v.invdiag[i] * r[i] / theta;
+    double di = cf.inv_theta * v.invdiag[i] * r[i];
     v.d[i] = di;
     buf[at][i] = di;
   }
@@ -131,8 +130,7 @@ __device__ void b_cheb(const BatchView &v, int64_t r0, int64_t r1, const double 
   const int sub = threadIdx.x % W;
   const int grp = threadIdx.x / W, ngrp = blockDim.x / W;
   for (int k = 1; k < degree; ++k) {
-    double rho1 = 1.0 / (2.0 * sigma1 - rho0);
-    double c1 = rho1 * rho0, c2 = 2.0 * rho1 / delta;
+    const double c1 = cf.c1[k], c2 = cf.c2[k];
     const double *zin = buf[at];
     double *zout = buf[at ^ 1];
     for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
@@ -151,8 +149,16 @@ __device__ void b_cheb(const BatchView &v, int64_t r0, int64_t r1, const double 
     }
     __syncthreads();
     at ^= 1;
-    rho0 = rho1;
   }
+}
+
+// num / den computed once and broadcast (one FP64 division per block, not per thread)
+__device__ __forceinline__ double bdiv(double num, double den, double *bc) {
+  if (threadIdx.x == 0) *bc = num / den;
+  __syncthreads();
+  double out = *bc;
+  __syncthreads();
+  return out;
 }
 
 template <int W, int U>
@@ -161,6 +167,7 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
   __shared__ double bc;
   const int k = blockIdx.x;
   if (k >= v.K) return;
+  if (v.run_status && v.run_status[k] != 0) return;  // failed in an earlier step of the run
   const int64_t s0 = v.slot_off[k], s1 = v.slot_off[k + 1];
   const int64_t r0 = s0, r1 = s0 + v.n_int[k];
   const int sub = threadIdx.x % W;
@@ -262,7 +269,9 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
     }
   }
   const double gersh = bmax(gmax, sh, &bc);
-  const double lo = 1.0 - gersh, hi = 1.0 + gersh;
+  __shared__ ChebCoef cf;
+  if (threadIdx.x == 0) cheb_coefficients(ph.cheb_degree, 1.0 - gersh, 1.0 + gersh, &cf);
+  __syncthreads();
 
   // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}, material solve with E^{n,0}
   auto newton = [&](const double *E_new, const double *E_prev, const double *e_start,
@@ -321,7 +330,7 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
     int it = 0;
     bool kconv = rr <= thresh2;
     if (!kconv) {
-      b_cheb<W, U>(v, r0, r1, v.r, v.z, ph.cheb_degree, lo, hi);
+      b_cheb<W, U>(v, r0, r1, v.r, v.z, cf);
       double rz = 0.0;
       for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         v.p[i] = v.z[i];
@@ -334,7 +343,7 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) pq += v.p[i] * v.q[i];
         pq = bsum(pq, sh, &bc);
         if (!(pq > 0.0) || !(pq < 1e308)) break;  // breakdown
-        double alpha = rho_k / pq;
+        double alpha = bdiv(rho_k, pq, &bc);
         rr = 0.0;
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
           v.x[i] += alpha * v.p[i];
@@ -349,11 +358,11 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
           kconv = true;
           break;
         }
-        b_cheb<W, U>(v, r0, r1, v.r, v.z, ph.cheb_degree, lo, hi);
+        b_cheb<W, U>(v, r0, r1, v.r, v.z, cf);
         rz = 0.0;
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) rz += v.r[i] * v.z[i];
         double rho_new = bsum(rz, sh, &bc);
-        double beta = rho_new / rho_k;
+        double beta = bdiv(rho_new, rho_k, &bc);
         rho_k = rho_new;
         for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x)
           v.p[i] = v.z[i] + beta * v.p[i];
@@ -417,6 +426,18 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
 // ---------------------------------------------------------------------------
 // host: packing problems into a batch
 // ---------------------------------------------------------------------------
+// After each step of a multi-step run: per-problem totals; a problem that did
+// not converge is marked and skipped by the remaining steps.
+__global__ void batch_accumulate_kernel(int K, const int32_t *status, const int32_t *outer,
+                                        const int32_t *krylov, int32_t *run_status,
+                                        int32_t *run_outer, int32_t *run_krylov) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K || run_status[k] != 0) return;
+  run_outer[k] += outer[k];
+  run_krylov[k] += krylov[k];
+  if (status[k] != 0) run_status[k] = status[k];
+}
+
 __global__ void pack_ptr_kernel(const int64_t *ptr_k, int64_t n_int, int64_t n, int64_t nnz_k,
                                 int64_t nnz_off, int64_t *ptr_out /* at slot offset */) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
@@ -452,7 +473,21 @@ struct sph_rt_batch {
   int32_t *d_status = nullptr, *d_outer = nullptr, *d_krylov = nullptr;
   double *d_energy = nullptr;
   int W = 16, U = 6;
+  // multi-step runs (sph_rt_batch_run): accumulators and the captured graph
+  int32_t *d_run_status = nullptr, *d_run_outer = nullptr, *d_run_krylov = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  double graph_dt = 0.0;
+  int32_t graph_steps = 0;
+  int64_t graph_kernels = 0;
 };
+
+static void batch_graph_release(sph_rt_batch *B) {
+  if (B->graph_exec) cudaGraphExecDestroy(B->graph_exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  B->graph_exec = nullptr;
+  B->graph = nullptr;
+}
 
 extern "C" sph_rt_status sph_rt_batch_create(const sph_rt_config *cfg, sph_rt_batch **out) {
   if (!cfg || !out) return SPH_RT_EINVAL;
@@ -663,16 +698,8 @@ extern "C" sph_rt_status sph_rt_batch_set_sources(sph_rt_batch *B, int32_t index
   return SPH_RT_OK;
 }
 
-extern "C" sph_rt_status sph_rt_batch_step(sph_rt_batch *B, double dt, int32_t *status,
-                                           int32_t *outer_iters, int32_t *krylov_iters,
-                                           double *energy) {
-  if (!B) return SPH_RT_EINVAL;
-  if (!isfinite(dt) || dt <= 0.0) return set_error(B->h, SPH_RT_EINVAL, "dt must be finite and > 0");
-  sph_rt_status rc;
-  if (!B->packed && (rc = batch_pack(B))) return rc;
-  sph_rt *s = B->h;
-  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
-  const sph_rt_config &c = s->cfg;
+static BatchPhys batch_phys(const sph_rt_batch *B, double dt) {
+  const sph_rt_config &c = B->h->cfg;
   BatchPhys ph;
   ph.a = c.a;
   ph.c = c.c;
@@ -690,13 +717,106 @@ extern "C" sph_rt_status sph_rt_batch_step(sph_rt_batch *B, double dt, int32_t *
   ph.max_outer = c.max_outer;
   ph.max_krylov = c.max_krylov;
   ph.cheb_degree = c.cheb_degree;
-  const int K = B->view.K;
-  // the failed problems keep their state: batch_step_kernel only commits on success
+  return ph;
+}
+
+static sph_rt_status launch_batch_step(sph_rt_batch *B, const BatchView &v, const BatchPhys &ph) {
+  sph_rt *s = B->h;
   if (B->W <= 4)
-    batch_step_kernel<4, 8><<<K, 512, 0, s->stream>>>(B->view, ph);
+    batch_step_kernel<4, 8><<<v.K, 512, 0, s->stream>>>(v, ph);
   else
-    batch_step_kernel<8, 8><<<K, 512, 0, s->stream>>>(B->view, ph);
+    batch_step_kernel<8, 8><<<v.K, 512, 0, s->stream>>>(v, ph);
   SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_batch_run(sph_rt_batch *B, double dt, int32_t steps,
+                                          int32_t *status, int32_t *outer_total,
+                                          int32_t *krylov_total) {
+  if (!B) return SPH_RT_EINVAL;
+  if (!isfinite(dt) || dt <= 0.0) return set_error(B->h, SPH_RT_EINVAL, "dt must be finite and > 0");
+  if (steps < 1) return set_error(B->h, SPH_RT_EINVAL, "steps must be >= 1");
+  sph_rt_status rc;
+  if (!B->packed && (rc = batch_pack(B))) return rc;
+  sph_rt *s = B->h;
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  const int K = B->view.K;
+  if (!B->d_run_status) {
+    B->d_run_status = dalloc<int32_t>(s, K);
+    B->d_run_outer = dalloc<int32_t>(s, K);
+    B->d_run_krylov = dalloc<int32_t>(s, K);
+    if (!B->d_run_status || !B->d_run_outer || !B->d_run_krylov) return SPH_RT_ENOMEM;
+  }
+  if (!B->graph_exec || B->graph_dt != dt || B->graph_steps != steps) {
+    batch_graph_release(B);
+    BatchView v = B->view;
+    v.run_status = B->d_run_status;
+    const BatchPhys ph = batch_phys(B, dt);
+    const int64_t l0 = s->launches;
+    SPH_CUDA(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeRelaxed));
+    auto body = [&]() -> sph_rt_status {
+      SPH_CUDA(s, cudaMemsetAsync(B->d_run_status, 0, sizeof(int32_t) * K, s->stream));
+      SPH_CUDA(s, cudaMemsetAsync(B->d_run_outer, 0, sizeof(int32_t) * K, s->stream));
+      SPH_CUDA(s, cudaMemsetAsync(B->d_run_krylov, 0, sizeof(int32_t) * K, s->stream));
+      for (int32_t k = 0; k < steps; ++k) {
+        sph_rt_status r2 = launch_batch_step(B, v, ph);
+        if (r2) return r2;
+        batch_accumulate_kernel<<<(K + 255) / 256, 256, 0, s->stream>>>(
+            K, B->d_status, B->d_outer, B->d_krylov, B->d_run_status, B->d_run_outer,
+            B->d_run_krylov);
+        SPH_LAUNCHED(s);
+      }
+      return SPH_RT_OK;
+    };
+    rc = body();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    B->graph_kernels = s->launches - l0;
+    s->launches = l0;
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) {
+      cuda_ok(s, e, "cudaStreamEndCapture");
+      return SPH_RT_EDEVICE;
+    }
+    B->graph = g;
+    SPH_CUDA(s, cudaGraphInstantiate(&B->graph_exec, g, 0));
+    B->graph_dt = dt;
+    B->graph_steps = steps;
+  }
+  SPH_CUDA(s, cudaGraphLaunch(B->graph_exec, s->stream));
+  s->launches += B->graph_kernels;
+  std::vector<int32_t> st(K), ou(K), kr(K);
+  SPH_CUDA(s, cudaMemcpyAsync(st.data(), B->d_run_status, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, s->stream));
+  SPH_CUDA(s, cudaMemcpyAsync(ou.data(), B->d_run_outer, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, s->stream));
+  SPH_CUDA(s, cudaMemcpyAsync(kr.data(), B->d_run_krylov, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  bool all_ok = true;
+  for (int k = 0; k < K; ++k) {
+    if (status) status[k] = st[k];
+    if (outer_total) outer_total[k] = ou[k];
+    if (krylov_total) krylov_total[k] = kr[k];
+    all_ok = all_ok && st[k] == 0;
+  }
+  return all_ok ? SPH_RT_OK : set_error(s, SPH_RT_ENOTCONV, "some problems did not converge");
+}
+
+extern "C" sph_rt_status sph_rt_batch_step(sph_rt_batch *B, double dt, int32_t *status,
+                                           int32_t *outer_iters, int32_t *krylov_iters,
+                                           double *energy) {
+  if (!B) return SPH_RT_EINVAL;
+  if (!isfinite(dt) || dt <= 0.0) return set_error(B->h, SPH_RT_EINVAL, "dt must be finite and > 0");
+  sph_rt_status rc;
+  if (!B->packed && (rc = batch_pack(B))) return rc;
+  sph_rt *s = B->h;
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  const int K = B->view.K;
+  BatchView v = B->view;
+  v.run_status = nullptr;
+  // the failed problems keep their state: batch_step_kernel only commits on success
+  if ((rc = launch_batch_step(B, v, batch_phys(B, dt)))) return rc;
   std::vector<int32_t> st(K), ou(K), kr(K);
   SPH_CUDA(s, cudaMemcpyAsync(st.data(), B->d_status, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, s->stream));
   SPH_CUDA(s, cudaMemcpyAsync(ou.data(), B->d_outer, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, s->stream));
@@ -748,6 +868,10 @@ extern "C" const char *sph_rt_batch_last_error(const sph_rt_batch *B) {
 
 extern "C" void sph_rt_batch_destroy(sph_rt_batch *B) {
   if (!B) return;
+  if (B->graph_exec || B->graph) {
+    cudaSetDevice(B->h->cfg.device);
+    batch_graph_release(B);
+  }
   for (sph_rt *t : B->staging)
     if (t) sph_rt_destroy(t);
   sph_rt_destroy(B->h);

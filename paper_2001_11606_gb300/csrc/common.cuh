@@ -48,6 +48,16 @@ struct Scalars {
   int breakdown;   // non-positive curvature / NaN seen
   int bad_input;   // a step input (source or ghost value) was not finite
   unsigned int counter;  // arrival counter of the last-block reductions
+  // outer (nonlinear-elimination) loop of Alg. 1, advanced by outer_check_kernel
+  int outer_iters;       // completed outer iterations
+  int outer_status;      // 0 running, 1 converged, 2 Krylov failure, 3 max_outer reached
+  int outer_trips;       // loop trips (termination guard of the device-driven loop)
+  int krylov_total;      // Krylov iterations over the converged outer iterations
+  int krylov_trips;      // Krylov loop trips over all outer iterations (launch count)
+  int krylov_solve_trips;  // Krylov loop trips of the current solve (termination guard)
+  int newton_max;        // largest material Newton iteration count
+  int krylov_per_outer[64];
+  double last_change_e, last_change_E;
 };
 
 // --------------------------------------------------------------------------
@@ -187,6 +197,51 @@ __device__ __forceinline__ T row_reduce(T v) {
   return v;
 }
 
+// Chebyshev iteration coefficients on [lo, hi] (Saad, Iterative Methods,
+// Alg. 12.1): the first step scales by 1/theta, step k >= 1 uses
+// d = c1[k] d + c2[k] D^{-1} res.  Computed once per interval (host, or one
+// thread) rather than per thread: an FP64 division costs tens of FP64-pipe
+// operations, and the FP64 pipe is narrow on this part.
+constexpr int kChebMaxDeg = 48;
+struct ChebCoef {
+  int degree;        // number of steps (the requested degree, clamped to [1, kChebMaxDeg])
+  double inv_theta;  // 1 / theta, theta = (hi + lo) / 2
+  double c1[kChebMaxDeg], c2[kChebMaxDeg];
+};
+// A collapsed interval means D^{-1} A = I (no off-diagonal coupling): the
+// first (Jacobi) step is then exact and the recurrence is undefined, so the
+// later steps get c1 = c2 = 0 (d = 0, z unchanged).  The number of steps never
+// depends on the data, so a captured launch sequence stays valid.
+__host__ __device__ inline void cheb_coefficients(int degree, double lo, double hi,
+                                                  ChebCoef *cf) {
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  const bool collapsed = !(delta > 1e-12 * theta);
+  if (degree > kChebMaxDeg) degree = kChebMaxDeg;
+  if (degree < 1) degree = 1;
+  cf->degree = degree;
+  cf->inv_theta = 1.0 / theta;
+  const double sigma1 = collapsed ? 1.0 : theta / delta;
+  double rho0 = 1.0 / sigma1;
+  cf->c1[0] = 0.0;
+  cf->c2[0] = cf->inv_theta;
+  for (int k = 1; k < degree; ++k) {
+    if (collapsed) {
+      cf->c1[k] = 0.0;
+      cf->c2[k] = 0.0;
+      continue;
+    }
+    const double rho1 = 1.0 / (2.0 * sigma1 - rho0);
+    cf->c1[k] = rho1 * rho0;
+    cf->c2[k] = 2.0 * rho1 / delta;
+    rho0 = rho1;
+  }
+}
+
+// Chebyshev coefficient slots of a handle (device array): slot 0 belongs to
+// the fine-level Chebyshev preconditioner, slot 1 + l to AMG level l (its
+// smoother, or the coarse solve on the last level).
+constexpr int kChebSlots = 1 + 32;
+
 // Row-group shape of the SpMV-class kernels: W lanes per row, U loads in flight
 // per lane.  A lane sums its entries (beg + sub + j W, j = 0, 1, ...) in
 // increasing j whatever U is, so results depend on W only.  W follows from the
@@ -325,10 +380,20 @@ struct sph_rt {
   // AMG hierarchy and Chebyshev data
   std::vector<SphLevel *> levels;
   bool amg_ready = false;
-  double cheb_lmin = 0.0, cheb_lmax = 2.0;  // spectrum bounds of D^{-1} B (Gershgorin)
   int coarse_smem_optin = 0;                 // shared-memory opt-in done (bit per value type)
+  int tail_level = 0;    // first AMG level of the cluster-resident V-cycle tail (0 = none)
+  int tail_cluster = 0;  // thread blocks in the tail's cluster
   double *gersh = nullptr;                   // device scalar written by the assembly
   double *amg_gersh = nullptr;               // per-level Gershgorin bounds
+  sphrt::ChebCoef *cheb_slots = nullptr;     // device [kChebSlots] (see kChebSlots)
+
+  // device-driven outer loop: one CUDA graph with conditional WHILE nodes
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<uint64_t> graph_sig;  // launch parameters the graph was captured with
+  cudaStream_t cap_stream = nullptr;
+  int64_t graph_l_init = 0, graph_l_outer = 0, graph_l_inner = 0;  // kernels per part
+  int64_t graph_builds = 0, graph_launches = 0;
 
   // row-group shape of the fine SpMV-class kernels (autotuned or from the mean row length)
   sphrt::RowShape fine_shape{16, 6};
@@ -354,7 +419,6 @@ inline T *dalloc(sph_rt *s, size_t count) {
 }
 void free_all(sph_rt *s);
 void dfree(sph_rt *s, void *p);  // back to the free list (stream-ordered users must sync first)
-int red_grid(const sph_rt *s, int64_t items, int items_per_block);
 // CUDA-event bracketing of fine-operator SpMV-class launches (config.kernel_timing).
 // timing_begin returns the work flag of the launch (nullptr when timing is off):
 // the kernel writes 1 there if it does work and 0 if it returns at once because

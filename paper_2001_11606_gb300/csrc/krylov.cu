@@ -13,10 +13,13 @@
 //
 // All scalars of the iteration (rho, alpha, beta, norms, convergence flag)
 // live on the device.  Every kernel of an iteration starts by reading the
-// `done` flag, so the host can queue several iterations and read the flag
-// once; iterations queued after convergence are empty launches.
+// `done` flag.  The iteration is driven either from the host (several
+// iterations queued per read of the flag; iterations queued after
+// convergence are empty launches) or, inside the step's CUDA graph, by a
+// conditional WHILE node that stops exactly at convergence (graph.cu).
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <utility>
 #include <vector>
 
@@ -212,9 +215,10 @@ __global__ void dot_rz_flex_kernel(int64_t n, const double *r, const double *z,
 // step:  d = c1 d + c2 D^{-1} (r - A z_in),              z_out = z_in + d
 // ---------------------------------------------------------------------------
 template <typename MT, typename VT>
-__global__ void cheb_init_zero_kernel(int64_t n, const VT *r, const MT *invdiag, double inv_theta,
-                                      VT *d, VT *z, const Scalars *sc) {
+__global__ void cheb_init_zero_kernel(int64_t n, const VT *r, const MT *invdiag,
+                                      const ChebCoef *cf, VT *d, VT *z, const Scalars *sc) {
   if (sc && sc->done) return;
+  const double inv_theta = cf->inv_theta;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     VT di = (VT)(inv_theta * (double)invdiag[i] * (double)r[i]);
@@ -226,7 +230,7 @@ __global__ void cheb_init_zero_kernel(int64_t n, const VT *r, const MT *invdiag,
 
 template <int W, int U, typename MT, typename VT>
 __global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
-                                 double c1, double c2, const Scalars *sc, int *wflag) {
+                                 const ChebCoef *cf, int k, const Scalars *sc, int *wflag) {
   if (sc && sc->done) {
     mark_work(wflag, 0);
     return;
@@ -235,6 +239,8 @@ __global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT 
   const int sub = threadIdx.x % W;
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  // step k of the recurrence; k = 0 is the first step from a nonzero guess
+  const double c1 = k > 0 ? cf->c1[k] : 0.0, c2 = k > 0 ? cf->c2[k] : cf->inv_theta;
   const VT vc1 = (VT)c1, vc2 = (VT)c2;
   for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
     const int64_t i = wb + group_in_warp<W>(grp);
@@ -245,7 +251,7 @@ __global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT 
       VT zi = z_in[i];
       VT res = r[i] - ((VT)A.diag[i] * zi + s);
       VT di = vc2 * (VT)A.invdiag[i] * res;
-      if (c1 != 0.0) di += vc1 * d[i];  // the first step must not read d
+      if (k > 0) di += vc1 * d[i];  // the first step must not read d
       d[i] = di;
       z_out[i] = zi + di;
     }
@@ -265,6 +271,7 @@ static int grid_cap(const sph_rt *s, int64_t n, int per_block) {
 
 CsrView<double> fine_view(const sph_rt *s) {
   CsrView<double> A;
+  memset(&A, 0, sizeof A);  // no indeterminate padding (the view is part of a graph signature)
   A.n = s->n_int;
   A.ptr = s->mat_ptr;
   A.col = s->mat_col;
@@ -331,28 +338,25 @@ double spmv_class_bytes(const CsrView<MT> &A, int row_bytes) {
 constexpr int kRowBytesResid = 48, kRowBytesSpmvPQ = 56;
 
 // Chebyshev polynomial preconditioner/smoother: `degree` steps from z
-// (zero_guess: z = 0 on entry).  d and tmp are scratch vectors of length n.
+// (zero_guess: z = 0 on entry), coefficients from the device slot `cf`
+// (filled on the device from the Gershgorin bounds of the step, so no host
+// read of the bounds is needed).  d and tmp are scratch vectors of length n.
 template <typename MT, typename VT>
 sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT *d, VT *tmp,
-                         int degree, double lmin, double lmax, bool zero_guess,
-                         const Scalars *sc) {
-  double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
-  // a collapsed interval means D^{-1} A = I (no off-diagonal coupling): one
-  // Jacobi step is then exact and the polynomial recurrence is undefined
-  if (!(delta > 1e-12 * theta)) degree = 1;
-  double sigma1 = degree > 1 ? theta / delta : 1.0;
-  double rho0 = 1.0 / sigma1;
+                         int degree, const ChebCoef *cf, bool zero_guess, const Scalars *sc) {
+  if (degree < 1) degree = 1;
+  if (degree > kChebMaxDeg) degree = kChebMaxDeg;
   int g = grid_cap(s, A.n, kBlock);
   int gw = grid_cap(s, A.n, kBlock / A.W);
   // fine-level sweeps are timed with the other fine SpMV-class kernels; per row:
   // rowptr, diag, 1/diag, r, z_in, z_out, d r/w (vectors of type VT)
   const bool fine = A.ptr == s->mat_ptr;
   const double bytes = spmv_class_bytes(A, 8 + 2 * (int)sizeof(MT) + 5 * (int)sizeof(VT));
-  auto step = [&](const VT *zin, VT *zout, double c1, double c2) -> sph_rt_status {
+  auto step = [&](const VT *zin, VT *zout, int k) -> sph_rt_status {
     int *wf = fine ? timing_begin(s) : nullptr;
     SPH_DISPATCH_SHAPE(A.W, A.U,
                        (cheb_step_kernel<W, U, MT, VT><<<gw, kBlock, 0, s->stream>>>(
-                           A, r, zin, zout, d, c1, c2, sc, wf)));
+                           A, r, zin, zout, d, cf, k, sc, wf)));
     SPH_LAUNCHED(s);
     if (fine) timing_end(s, bytes);
     return SPH_RT_OK;
@@ -364,7 +368,7 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
   int w0 = (degree - 1) % 2;
   sph_rt_status rc;
   if (zero_guess) {
-    cheb_init_zero_kernel<MT, VT><<<g, kBlock, 0, s->stream>>>(A.n, r, A.invdiag, 1.0 / theta, d,
+    cheb_init_zero_kernel<MT, VT><<<g, kBlock, 0, s->stream>>>(A.n, r, A.invdiag, cf, d,
                                                                  bufs[w0], sc);
     SPH_LAUNCHED(s);
   } else {
@@ -372,24 +376,21 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
     if (w0 == 0) {
       SPH_CUDA(s, cudaMemcpyAsync(tmp, z, sizeof(VT) * A.n, cudaMemcpyDeviceToDevice, s->stream));
     }
-    if ((rc = step(bufs[w0 ^ 1], bufs[w0], 0.0, 1.0 / theta))) return rc;
+    if ((rc = step(bufs[w0 ^ 1], bufs[w0], 0))) return rc;
   }
   int at = w0;
   for (int k = 1; k < degree; ++k) {
-    double rho1 = 1.0 / (2.0 * sigma1 - rho0);
-    double c1 = rho1 * rho0, c2 = 2.0 * rho1 / delta;
-    if ((rc = step(bufs[at], bufs[at ^ 1], c1, c2))) return rc;
+    if ((rc = step(bufs[at], bufs[at ^ 1], k))) return rc;
     at ^= 1;
-    rho0 = rho1;
   }
   return SPH_RT_OK;
 }
 
 template sph_rt_status cheb_apply<double, double>(sph_rt *, const CsrView<double> &, const double *,
-                                                  double *, double *, double *, int, double, double,
-                                                  bool, const Scalars *);
+                                                  double *, double *, double *, int,
+                                                  const ChebCoef *, bool, const Scalars *);
 template sph_rt_status cheb_apply<float, float>(sph_rt *, const CsrView<float> &, const float *,
-                                                float *, float *, float *, int, double, double,
+                                                float *, float *, float *, int, const ChebCoef *,
                                                 bool, const Scalars *);
 
 // Preconditioner hook implemented by the AMG translation unit.
@@ -407,7 +408,7 @@ static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first
       return SPH_RT_OK;
     case SPH_RT_PRECOND_CHEBYSHEV:
       rc = cheb_apply<double, double>(s, A, s->r, s->z, s->w, s->tmp_n2, s->cfg.cheb_degree,
-                                      s->cheb_lmin, s->cheb_lmax, true, s->sc);
+                                      s->cheb_slots, true, s->sc);
       if (rc) return rc;
       break;
     default:
@@ -453,25 +454,33 @@ sph_rt_status autotune_fine_shape(sph_rt *s) {
   cudaEvent_t e0, e1;
   SPH_CUDA(s, cudaEventCreate(&e0));
   SPH_CUDA(s, cudaEventCreate(&e1));
-  float best = 1e30f;
   RowShape pick = shape_for_mean(A.n ? (double)A.nnz / A.n : 0.0);
-  for (const RowShape &c : cands) {
-    const int gw = grid_cap(s, A.n, kBlock / c.W);
-    float ms = 0.f;
-    for (int rep = 0; rep < 4; ++rep) {
-      if (rep == 1) cudaEventRecord(e0, s->stream);
-      SPH_DISPATCH_SHAPE(c.W, c.U, (spmv_plain_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(
-                                       A, s->z, s->w)));
-      SPH_LAUNCHED(s);
-    }
-    cudaEventRecord(e1, s->stream);
-    SPH_CUDA(s, cudaEventSynchronize(e1));
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      pick = c;
+  // candidates alternate over 3 rounds of 6 back-to-back launches (the way the
+  // solver issues them), on the current E; the smallest round total wins
+  std::vector<float> best(cands.size(), 1e30f);
+  for (int round = 0; round < 3; ++round) {
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+      const RowShape &c = cands[ci];
+      const int gw = grid_cap(s, A.n, kBlock / c.W);
+      float ms = 0.f;
+      for (int rep = 0; rep < 7; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, s->stream);
+        SPH_DISPATCH_SHAPE(c.W, c.U, (spmv_plain_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(
+                                         A, s->E, s->w)));
+        SPH_LAUNCHED(s);
+      }
+      cudaEventRecord(e1, s->stream);
+      SPH_CUDA(s, cudaEventSynchronize(e1));
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best[ci]) best[ci] = ms;
     }
   }
+  float bm = 1e30f;
+  for (size_t ci = 0; ci < cands.size(); ++ci)
+    if (best[ci] < bm) {
+      bm = best[ci];
+      pick = cands[ci];
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   s->fine_shape = pick;
@@ -481,12 +490,10 @@ sph_rt_status autotune_fine_shape(sph_rt *s) {
 
 // Solve B x = b from the warm start in x (row a6).  On return the host mirror
 // s->sc_host holds the final scalars.
-sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
+// First part of a solve: r = b - B x, z = M^{-1} r, q = B p with p = z.
+sph_rt_status pcg_prologue(sph_rt *s) {
   CsrView<double> A = fine_view(s);
   const int gw = grid_cap(s, A.n, kBlock / A.W);
-  const int g = grid_cap(s, A.n, kBlock);
-  const double bytes_r = spmv_class_bytes(A, kRowBytesResid);
-  const double bytes = spmv_class_bytes(A, kRowBytesSpmvPQ);
   sph_rt_status rc;
   int *wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
@@ -494,29 +501,59 @@ sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
                                                                        s->invV, s->sc,
                                                                        s->partials, wf)));
   SPH_LAUNCHED(s);
-  timing_end(s, bytes_r);
+  timing_end(s, spmv_class_bytes(A, kRowBytesResid));
   if ((rc = precondition(s, A, 1))) return rc;
   wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
                      (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->z, s->q, s->p, 1,
                                                                          s->sc, s->partials, wf)));
   SPH_LAUNCHED(s);
-  timing_end(s, bytes);
+  timing_end(s, spmv_class_bytes(A, kRowBytesSpmvPQ));
+  return SPH_RT_OK;
+}
+
+__global__ void copy_vec_kernel(int64_t n, const double *src, double *dst, const Scalars *sc) {
+  if (sc && sc->done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// One CG iteration: x, r update and the convergence test, z = M^{-1} r, the
+// new direction and q = B p.  The flexible (mixed-precision) variant keeps the
+// previous z in z_old.  All launches are empty once `done` is set.
+sph_rt_status pcg_iteration(sph_rt *s) {
+  CsrView<double> A = fine_view(s);
+  const int gw = grid_cap(s, A.n, kBlock / A.W);
+  const int g = grid_cap(s, A.n, kBlock);
+  sph_rt_status rc;
+  update_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
+                                              s->cfg.max_krylov, s->sc, s->partials);
+  SPH_LAUNCHED(s);
+  if (s->cfg.precision == SPH_RT_MIXED) {
+    copy_vec_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->z, s->z_old, s->sc);
+    SPH_LAUNCHED(s);
+  }
+  if ((rc = precondition(s, A, 0))) return rc;
+  int *wf = timing_begin(s);
+  SPH_DISPATCH_SHAPE(A.W, A.U,
+                     (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->z, s->q, s->p, 0,
+                                                                         s->sc, s->partials, wf)));
+  SPH_LAUNCHED(s);
+  timing_end(s, spmv_class_bytes(A, kRowBytesSpmvPQ));
+  return SPH_RT_OK;
+}
+
+// Host-driven solve: iterations are queued in chunks of check_every and the
+// device flag is read after each chunk.
+sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
+  sph_rt_status rc;
+  if ((rc = pcg_prologue(s))) return rc;
   const int chunk = s->cfg.check_every > 0 ? s->cfg.check_every : 1;
   int queued = 0;
   for (;;) {
     for (int c = 0; c < chunk; ++c) {
-      update_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
-                                                  s->cfg.max_krylov, s->sc, s->partials);
-      SPH_LAUNCHED(s);
-      if (s->cfg.precision == SPH_RT_MIXED) std::swap(s->z, s->z_old);
-      if ((rc = precondition(s, A, 0))) return rc;
-      wf = timing_begin(s);
-      SPH_DISPATCH_SHAPE(A.W, A.U,
-                         (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(
-                             A, s->z, s->q, s->p, 0, s->sc, s->partials, wf)));
-      SPH_LAUNCHED(s);
-      timing_end(s, bytes);
+      if ((rc = pcg_iteration(s))) return rc;
       ++queued;
     }
     SPH_CUDA(s, cudaMemcpyAsync(s->sc_host, s->sc, sizeof(Scalars), cudaMemcpyDeviceToHost,
@@ -529,6 +566,42 @@ sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
   timing_flush(s);
   *iters = s->sc_host->iters;
   *converged = !s->sc_host->breakdown && !(s->sc_host->rnorm2 > s->sc_host->thresh2);
+  return SPH_RT_OK;
+}
+
+// Chebyshev coefficient slots from device Gershgorin bounds g (no host read):
+// mode 0: [1 - g, 1 + g] (fine-level Chebyshev preconditioner);
+// mode 1: [(1 + g) / 8, 1 + g] (AMG smoother);
+// mode 2: [max(1 - g, 1e-3 (1 + g)), 1 + g] (coarsest-level solve).
+struct SlotSpec {
+  int count;
+  int mode[kChebSlots], degree[kChebSlots];
+};
+__global__ void cheb_slots_kernel(ChebCoef *slots, const double *gersh, const SlotSpec spec) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= spec.count) return;
+  const double g = gersh[t], hi = 1.0 + g;
+  double lo = 1.0 - g;
+  if (spec.mode[t] == 1) lo = hi / 8.0;
+  if (spec.mode[t] == 2 && lo < 1e-3 * hi) lo = 1e-3 * hi;
+  cheb_coefficients(spec.degree[t], lo, hi, slots + t);
+}
+
+// Fill slots first .. first + mode.size() - 1 from the device bounds
+// gersh_dev[0 ..]; mode[k] and degree[k] describe slot first + k.
+sph_rt_status launch_cheb_slots(sph_rt *s, int first, const double *gersh_dev,
+                                const std::vector<int> &mode, const std::vector<int> &degree) {
+  SlotSpec spec;
+  spec.count = (int)mode.size();
+  if (spec.count == 0) return SPH_RT_OK;
+  if (first + spec.count > kChebSlots)
+    return set_error(s, SPH_RT_EINVAL, "too many Chebyshev slots");
+  for (int k = 0; k < spec.count; ++k) {
+    spec.mode[k] = mode[k];
+    spec.degree[k] = degree[k];
+  }
+  cheb_slots_kernel<<<1, 64, 0, s->stream>>>(s->cheb_slots + first, gersh_dev, spec);
+  SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }
 

@@ -17,6 +17,10 @@
 //            put it back; work of different problems overlaps on the device
 //   retire   a finished problem's state is copied out and its device memory
 //            released, which lets the next queued request in
+//   fuse     small requests (n_total <= fuse_max_n) that are ready at the
+//            same time and share configuration, dt and step count run as one
+//            sph_rt_batch: one persistent kernel launch per step for all of
+//            them, all steps in one CUDA-graph launch
 //
 // Each problem's kernels are the library's deterministic kernels on its own
 // data, so a request's result does not depend on what else is resident.
@@ -63,6 +67,8 @@ struct Request {
   int64_t reserved = 0;  // bytes counted against the budget
   sph_rt *handle = nullptr;
   int64_t particle_steps = 0;
+  int64_t n_int = 0;   // interior particles
+  bool fused = false;  // ran in a fused batch
 };
 
 int64_t estimate_bytes(int dim, int64_t n) {
@@ -91,6 +97,7 @@ struct sph_rt_srv {
   std::string err;
   double t_first = 0, t_last = 0;
   int64_t total_particle_steps = 0;
+  int64_t fused_requests = 0, fused_batches = 0;
 };
 
 namespace {
@@ -218,6 +225,88 @@ void finish_request(sph_rt_srv *S, const std::shared_ptr<Request> &R, sph_rt_sta
   S->cv.notify_all();
 }
 
+bool fusable(const sph_rt_srv *S, const Request &R) {
+  return S->cfg.fuse_max_n > 0 && R.n <= S->cfg.fuse_max_n && !R.handle && R.done_steps == 0;
+}
+
+// Requests that can share one batch: same configuration (device and stream
+// aside), dt and number of steps.
+bool same_batch_key(const Request &a, const Request &b) {
+  sph_rt_config ca, cb;
+  memcpy(&ca, &a.cfg, sizeof ca);
+  memcpy(&cb, &b.cfg, sizeof cb);
+  ca.stream = cb.stream = nullptr;
+  ca.device = cb.device = 0;
+  return memcmp(&ca, &cb, sizeof ca) == 0 && a.dt == b.dt && a.steps == b.steps;
+}
+
+// Run a group of fused requests to completion as one batch (worker thread,
+// no lock held).  Every member is finished here.
+void run_fused(sph_rt_srv *S, std::vector<std::shared_ptr<Request>> &group) {
+  sph_rt_config c = group[0]->cfg;
+  c.device = S->cfg.device;
+  c.stream = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (auto &R : group) {
+      R->state = SPH_RT_SRV_RUNNING;
+      R->fused = true;
+    }
+  }
+  sph_rt_batch *B = nullptr;
+  sph_rt_status rc = sph_rt_batch_create(&c, &B);
+  if (rc) {
+    for (auto &R : group) {
+      R->err = sph_rt_last_error(nullptr);
+      finish_request(S, R, rc);
+    }
+    return;
+  }
+  std::vector<std::shared_ptr<Request>> members;
+  std::vector<int32_t> index;
+  for (auto &R : group) {
+    int32_t k = -1;
+    sph_rt_status r2 = sph_rt_batch_add(B, R->n, R->pos.data(), R->mass.data(), R->rho.data(),
+                                        R->h.data(), R->sigma0.data(), R->kind.data(),
+                                        R->has_copy ? R->copy_of.data() : nullptr,
+                                        R->e0.data(), R->E0.data(), &k);
+    if (!r2 && (R->has_Qe || R->has_QE))
+      r2 = sph_rt_batch_set_sources(B, k, R->has_Qe ? R->Qe.data() : nullptr,
+                                    R->has_QE ? R->QE.data() : nullptr);
+    if (r2) {
+      R->err = sph_rt_batch_last_error(B);
+      finish_request(S, R, r2);
+      continue;
+    }
+    members.push_back(R);
+    index.push_back(k);
+  }
+  if (!members.empty()) {
+    const size_t K = (size_t)sph_rt_batch_size(B);
+    std::vector<int32_t> st(K, 0), ou(K, 0), kr(K, 0);
+    rc = sph_rt_batch_run(B, members[0]->dt, members[0]->steps, st.data(), ou.data(), kr.data());
+    const bool hard = rc != SPH_RT_OK && rc != SPH_RT_ENOTCONV;
+    const std::string msg = rc ? sph_rt_batch_last_error(B) : "";
+    for (size_t m = 0; m < members.size(); ++m) {
+      auto &R = members[m];
+      const int32_t k = index[m];
+      sph_rt_status r2 = hard ? rc : (st[k] == 0 ? SPH_RT_OK : SPH_RT_ENOTCONV);
+      if (r2 == SPH_RT_OK) {
+        R->e.resize(R->n);
+        R->E.resize(R->n);
+        r2 = sph_rt_batch_get_energies(B, k, R->e.data(), R->E.data());
+        R->last.outer_iters = ou[k];  // totals over the run for a fused request
+        R->last.krylov_iters_total = kr[k];
+        R->done_steps = R->steps;
+        R->particle_steps = R->n_int * R->steps;
+      }
+      if (r2) R->err = hard ? msg : (r2 == SPH_RT_ENOTCONV ? "step did not converge" : sph_rt_batch_last_error(B));
+      finish_request(S, R, r2);
+    }
+  }
+  sph_rt_batch_destroy(B);
+}
+
 void worker_main(sph_rt_srv *S) {
   cudaSetDevice(S->cfg.device);
   for (;;) {
@@ -229,6 +318,27 @@ void worker_main(sph_rt_srv *S) {
       R = S->ready.front();
       S->ready.pop_front();
       S->busy++;
+    }
+    if (fusable(S, *R)) {
+      std::vector<std::shared_ptr<Request>> group{R};
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (auto it = S->ready.begin();
+             it != S->ready.end() && (int)group.size() < S->cfg.fuse_max_k;) {
+          if (fusable(S, **it) && same_batch_key(*R, **it)) {
+            group.push_back(*it);
+            it = S->ready.erase(it);
+          } else {
+            ++it;
+          }
+        }
+        S->fused_batches++;
+        S->fused_requests += (int64_t)group.size();
+      }
+      run_fused(S, group);
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->busy--;
+      continue;
     }
     sph_rt_status rc = SPH_RT_OK;
     if (!R->handle) {
@@ -277,13 +387,16 @@ extern "C" void sph_rt_srv_default_config(sph_rt_srv_config *c) {
   c->steps_per_tick = 1;
   c->hbm_budget_bytes = 120e9;
   c->device = 0;
+  c->fuse_max_n = 20000;
+  c->fuse_max_k = 64;
 }
 
 extern "C" sph_rt_status sph_rt_srv_create(const sph_rt_srv_config *cfg, sph_rt_srv **out) {
   if (!out || !cfg) return SPH_RT_EINVAL;
   *out = nullptr;
   if (cfg->workers < 1 || cfg->workers > 256 || cfg->max_resident < 1 ||
-      cfg->steps_per_tick < 1 || !(cfg->hbm_budget_bytes > 0) || cfg->device < 0)
+      cfg->steps_per_tick < 1 || !(cfg->hbm_budget_bytes > 0) || cfg->device < 0 ||
+      cfg->fuse_max_n < 0 || cfg->fuse_max_k < 1)
     return SPH_RT_EINVAL;
   sph_rt_srv *S = new (std::nothrow) sph_rt_srv();
   if (!S) return SPH_RT_ENOMEM;
@@ -322,6 +435,7 @@ extern "C" sph_rt_status sph_rt_srv_submit(sph_rt_srv *S, const sph_rt_config *c
   R->h.assign(h, h + n_total);
   R->sigma0.assign(sigma0, sigma0 + n_total);
   R->kind.assign(kind, kind + n_total);
+  for (int64_t i = 0; i < n_total; ++i) R->n_int += kind[i] == SPH_RT_INTERIOR;
   R->e0.assign(e0, e0 + n_total);
   R->E0.assign(E0, E0 + n_total);
   if (copy_of) {
@@ -406,6 +520,8 @@ extern "C" sph_rt_status sph_rt_srv_info(sph_rt_srv *S, sph_rt_srv_info_t *info)
   info->particle_steps = S->total_particle_steps;
   info->t_first_submit = S->t_first;
   info->t_last_done = S->t_last;
+  info->fused_requests = S->fused_requests;
+  info->fused_batches = S->fused_batches;
   return SPH_RT_OK;
 }
 

@@ -36,6 +36,11 @@ sph_rt_status launch_scatter_caller(sph_rt *s, const double *in_s, int64_t count
 sph_rt_status launch_commit(sph_rt *s, const double *e_new, const double *E_new);
 sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged);
 sph_rt_status autotune_fine_shape(sph_rt *s);
+sph_rt_status outer_loop(sph_rt *s, double dt);
+void outer_loop_account(sph_rt *s, const Scalars &h);
+void loop_graph_release(sph_rt *s);
+sph_rt_status launch_cheb_slots(sph_rt *s, int first, const double *gersh_dev,
+                                const std::vector<int> &mode, const std::vector<int> &degree);
 sph_rt_status amg_setup(sph_rt *s);
 void amg_release(sph_rt *s);
 sph_rt_status validate_device_particles(sph_rt *s, int64_t n, const double *pos,
@@ -104,6 +109,7 @@ void *dalloc_bytes(sph_rt *s, size_t bytes) {
 
 void free_all(sph_rt *s) {
   if (s->cuda_ready) cudaStreamSynchronize(s->stream);
+  loop_graph_release(s);  // its launches refer to the buffers released below
   amg_release(s);
   for (void *p : s->allocs) s->pool.emplace(s->alloc_size[p], p);
   s->allocs.clear();
@@ -114,6 +120,7 @@ void free_all(sph_rt *s) {
   s->gcol = nullptr;
   s->gvx = s->gvy = s->gvz = nullptr;
   s->amg_gersh = nullptr;
+  s->cheb_slots = nullptr;
   s->ev_flags = nullptr;
   s->ev_used = 0;
 }
@@ -165,7 +172,9 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->amg_theta = 0.02;
   c->check_every = 8;
   c->kernel_timing = 0;
-  c->autotune = 1;
+  c->autotune = 0;
+  c->amg_tail = 1;
+  c->graphs = 1;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -193,6 +202,8 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
   if (!(c->amg_theta >= 0.0 && c->amg_theta < 1.0))
     return why = "amg_theta must be in [0, 1)", SPH_RT_EINVAL;
   if (c->check_every < 1) return why = "check_every must be >= 1", SPH_RT_EINVAL;
+  if (c->graphs < 0 || c->graphs > 1) return why = "graphs must be 0 or 1", SPH_RT_EINVAL;
+  if (c->amg_tail < 0 || c->amg_tail > 1) return why = "amg_tail must be 0 or 1", SPH_RT_EINVAL;
   if (c->device < 0) return why = "device must be >= 0", SPH_RT_EINVAL;
   return SPH_RT_OK;
 }
@@ -249,6 +260,7 @@ extern "C" void sph_rt_destroy(sph_rt *s) {
   if (s->cuda_ready) {
     cudaSetDevice(s->cfg.device);
     free_everything(s);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     if (s->sc_host) cudaFreeHost(s->sc_host);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -261,6 +273,14 @@ extern "C" const char *sph_rt_last_error(const sph_rt *s) {
 }
 
 extern "C" int64_t sph_rt_launch_count(const sph_rt *s) { return s ? s->launches : 0; }
+
+extern "C" sph_rt_status sph_rt_loop_graph_info(const sph_rt *s, int64_t *captures,
+                                                int64_t *launches) {
+  if (!s) return SPH_RT_EINVAL;
+  if (captures) *captures = s->graph_builds;
+  if (launches) *launches = s->graph_launches;
+  return SPH_RT_OK;
+}
 
 // ---------------------------------------------------------------------------
 // particles
@@ -319,6 +339,7 @@ static sph_rt_status alloc_step_vectors(sph_rt *s) {
   for (double **p : inner)
     if (!(*p = dalloc<double>(s, ni))) return SPH_RT_ENOMEM;
   if (!(s->gersh = dalloc<double>(s, 1))) return SPH_RT_ENOMEM;
+  if (!(s->cheb_slots = dalloc<ChebCoef>(s, kChebSlots))) return SPH_RT_ENOMEM;
   SPH_CUDA(s, cudaMemsetAsync(s->Qe, 0, sizeof(double) * ni, s->stream));
   SPH_CUDA(s, cudaMemsetAsync(s->QE, 0, sizeof(double) * ni, s->stream));
   return SPH_RT_OK;
@@ -498,13 +519,11 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   tm.begin(1);
   if ((rc = launch_assembly(s, dt, s->gersh))) return rc;  // a4
   tm.end();
-  double gersh = 0.0;
-  SPH_CUDA(s, cudaMemcpyAsync(&gersh, s->gersh, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
-  SPH_TRACE("step: assembled, gershgorin %g", gersh);
-  s->cheb_lmin = 1.0 - gersh;
-  s->cheb_lmax = 1.0 + gersh;
   s->have_operator = true;
+  if (s->cfg.precond == SPH_RT_PRECOND_CHEBYSHEV) {
+    // coefficients on [1 - g, 1 + g] straight from the device Gershgorin bound
+    if ((rc = launch_cheb_slots(s, 0, s->gersh, {0}, {s->cfg.cheb_degree}))) return rc;
+  }
   if (s->cfg.autotune && !s->fine_shape_set) {
     if ((rc = autotune_fine_shape(s))) return rc;
   }
@@ -523,44 +542,28 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   tm.begin(4);
   if ((rc = launch_newton(s, dt, s->E_l, s->E_l, s->e_old, s->e_l))) return rc;  // a8
   tm.end();
-  if ((rc = read_scalars(s))) return rc;
-  st.newton_iters_max = (int32_t)s->sc_host->red[2];
 
-  bool converged = false;
-  bool krylov_fail = false;
-  while (st.outer_iters < s->cfg.max_outer) {
-    tm.begin(3);
-    if ((rc = launch_rhs(s, dt))) return rc;  // a7 (also x = E^l)
-    int kit = 0;
-    bool kconv = false;
-    SPH_TRACE("step: outer %d, krylov solve", st.outer_iters);
-    if ((rc = pcg_solve(s, &kit, &kconv))) return rc;  // a6
-    SPH_TRACE("step: krylov done iters=%d converged=%d rnorm2=%g thresh2=%g", kit, (int)kconv,
-              s->sc_host->rnorm2, s->sc_host->thresh2);
-    tm.end();
-    if (!kconv) {
-      krylov_fail = true;
-      break;
-    }
-    if (st.outer_iters < 64) st.krylov_iters_per_outer[st.outer_iters] = kit;
-    st.krylov_iters_total += kit;
-    tm.begin(4);
-    if ((rc = launch_newton(s, dt, s->x, s->E_l, s->e_l, s->e_new))) return rc;  // a8
-    tm.end();
-    if ((rc = read_scalars(s))) return rc;  // a9
-    SPH_TRACE("step: newton done, changes %g %g", s->sc_host->red[0], s->sc_host->red[1]);
-    st.outer_iters++;
-    double ce = s->sc_host->red[0], cE = s->sc_host->red[1];
-    st.newton_iters_max = std::max(st.newton_iters_max, (int32_t)s->sc_host->red[2]);
-    std::swap(s->e_l, s->e_new);
-    std::swap(s->E_l, s->x);
-    st.last_change_e = ce;
-    st.last_change_E = cE;
-    if (ce < s->cfg.tol_outer_e && cE < s->cfg.tol_outer_E) {
-      converged = true;
-      break;
-    }
+  // Alg. 1 outer loop: rhs (a7), Krylov solve (a6), material solve (a8) and the
+  // convergence test (a9), as one device-driven CUDA graph or host-driven
+  tm.begin(3);
+  if ((rc = outer_loop(s, dt))) return rc;
+  tm.end();
+  if ((rc = read_scalars(s))) return rc;
+  {
+    const Scalars &h = *s->sc_host;
+    outer_loop_account(s, h);
+    st.outer_iters = h.outer_iters;
+    st.krylov_iters_total = h.krylov_total;
+    for (int k = 0; k < 64 && k < h.outer_iters; ++k)
+      st.krylov_iters_per_outer[k] = h.krylov_per_outer[k];
+    st.newton_iters_max = h.newton_max;
+    st.last_change_e = h.last_change_e;
+    st.last_change_E = h.last_change_E;
+    SPH_TRACE("step: outer loop status %d, %d outer, %d krylov", h.outer_status, h.outer_iters,
+              h.krylov_total);
   }
+  const bool converged = s->sc_host->outer_status == 1;
+  const bool krylov_fail = s->sc_host->outer_status == 2;
 
   if (!converged) {
     // restore the ghost values; interior state was never written

@@ -46,6 +46,8 @@ class Config(C.Structure):
         ("check_every", C.c_int32),
         ("kernel_timing", C.c_int32),
         ("autotune", C.c_int32),
+        ("amg_tail", C.c_int32),
+        ("graphs", C.c_int32),
         ("device", C.c_int32),
         ("stream", C.c_void_p),
     ]
@@ -74,14 +76,15 @@ SRV_QUEUED, SRV_ADMITTED, SRV_RUNNING, SRV_DONE, SRV_FAILED = 0, 1, 2, 3, 4
 class SrvConfig(C.Structure):
     _fields_ = [("workers", C.c_int32), ("max_resident", C.c_int32),
                 ("steps_per_tick", C.c_int32), ("hbm_budget_bytes", C.c_double),
-                ("device", C.c_int32)]
+                ("device", C.c_int32), ("fuse_max_n", C.c_int64), ("fuse_max_k", C.c_int32)]
 
 
 class SrvInfo(C.Structure):
     _fields_ = [("queued", C.c_int32), ("resident", C.c_int32), ("peak_resident", C.c_int32),
                 ("resident_bytes", C.c_int64), ("peak_bytes", C.c_int64),
                 ("particle_steps", C.c_int64), ("t_first_submit", C.c_double),
-                ("t_last_done", C.c_double)]
+                ("t_last_done", C.c_double), ("fused_requests", C.c_int64),
+                ("fused_batches", C.c_int64)]
 
 
 class SphRtError(RuntimeError):
@@ -109,6 +112,7 @@ _SIGNATURES = [
     ("sph_rt_get_properties", C.c_int, [_P] * 7),
     ("sph_rt_kernel_stats", C.c_int, [_P, _P, _P, _P, C.c_int]),
     ("sph_rt_get_amg_info", C.c_int, [_P, _P, _P, _P, C.c_int32]),
+    ("sph_rt_loop_graph_info", C.c_int, [_P, _P, _P]),
     ("sph_rt_launch_count", C.c_int64, [_P]),
     ("sph_rt_last_error", C.c_char_p, [_P]),
     ("sph_rt_destroy", None, [_P]),
@@ -124,6 +128,7 @@ _SIGNATURES = [
     ("sph_rt_batch_add", C.c_int, [_P, C.c_int64] + [_P] * 10),
     ("sph_rt_batch_set_sources", C.c_int, [_P, C.c_int32, _P, _P]),
     ("sph_rt_batch_step", C.c_int, [_P, C.c_double, _P, _P, _P, _P]),
+    ("sph_rt_batch_run", C.c_int, [_P, C.c_double, C.c_int32, _P, _P, _P]),
     ("sph_rt_batch_get_energies", C.c_int, [_P, C.c_int32, _P, _P]),
     ("sph_rt_batch_size", C.c_int32, [_P]),
     ("sph_rt_batch_last_error", C.c_char_p, [_P]),
@@ -328,6 +333,12 @@ class Solver:
     def launch_count(self) -> int:
         return int(self._L.sph_rt_launch_count(self._h))
 
+    def loop_graph_info(self):
+        """(captures, launches) of the device-driven outer-loop graph."""
+        cap, lau = C.c_int64(), C.c_int64()
+        self._check(self._L.sph_rt_loop_graph_info(self._h, C.byref(cap), C.byref(lau)))
+        return cap.value, lau.value
+
 
 def config_from_params(params: dict, **overrides) -> Config:
     """Config from a workload parameter dict (inputs.Workload.params)."""
@@ -471,6 +482,18 @@ class Batch:
         if raise_on_error:
             self._check(rc)
         return rc, st, ou, kr, en.reshape(K, 4)
+
+    def run(self, dt, steps, raise_on_error=True):
+        """`steps` steps of every problem in one CUDA-graph launch."""
+        K = len(self._n)
+        st = np.zeros(K, dtype=np.int32)
+        ou = np.zeros(K, dtype=np.int32)
+        kr = np.zeros(K, dtype=np.int32)
+        rc = self._L.sph_rt_batch_run(self._h, float(dt), int(steps), _ptr(st), _ptr(ou),
+                                      _ptr(kr))
+        if raise_on_error:
+            self._check(rc)
+        return rc, st, ou, kr
 
     def get_energies(self, index):
         n = self._n[index]

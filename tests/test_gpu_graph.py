@@ -1,0 +1,84 @@
+"""Device-driven outer loop: the step's loop as one CUDA graph with conditional
+WHILE nodes gives bitwise the same results and statistics as the host-driven
+loop, is captured once and replayed, and ends on every failure path."""
+import numpy as np
+import pytest
+
+from paper_2001_11606_gb300 import inputs as I
+from paper_2001_11606_gb300 import sphrt
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(w, steps, **cfg):
+    S = sphrt.solver_for(w, **cfg)
+    stats = []
+    for n in range(1, steps + 1):
+        _, st = S.step(w.dt, *w.step_inputs(n))
+        stats.append((st.outer_iters, st.krylov_iters_total,
+                      tuple(st.krylov_iters_per_outer[:st.outer_iters]), st.newton_iters_max))
+    e, E, _ = S.get_energies()
+    info = S.loop_graph_info()
+    launches = S.launch_count()
+    S.close()
+    return e, E, stats, info, launches
+
+
+@pytest.mark.parametrize("precond,precision", [(sphrt.PRECOND_AMG, sphrt.FP64),
+                                               (sphrt.PRECOND_AMG, sphrt.MIXED),
+                                               (sphrt.PRECOND_CHEBYSHEV, sphrt.FP64),
+                                               (sphrt.PRECOND_JACOBI, sphrt.FP64)])
+def test_graph_loop_matches_host_loop_bitwise(precond, precision):
+    w = I.mms_3d_lp(n=12, steps=3)
+    g = _run(w, 3, precond=precond, precision=precision, graphs=1)
+    h = _run(w, 3, precond=precond, precision=precision, graphs=0)
+    assert np.array_equal(g[0], h[0]) and np.array_equal(g[1], h[1])
+    assert g[2] == h[2]
+    assert g[3] == (1, 3)  # captured once, launched every step
+    assert h[3] == (0, 0)
+
+
+def test_graph_recaptured_when_dt_changes():
+    w = I.mms_2d(n=16, steps=3)
+    S = sphrt.solver_for(w)
+    S.step(w.dt, *w.step_inputs(1))
+    S.step(w.dt, *w.step_inputs(2))
+    assert S.loop_graph_info() == (1, 2)
+    S.step(0.5 * w.dt, *w.step_inputs(3))
+    assert S.loop_graph_info() == (2, 3)
+    S.close()
+
+
+def test_graph_krylov_failure_ends_step_unchanged():
+    w = I.mms_2d(n=16, steps=1)
+    S = sphrt.solver_for(w, max_krylov=1, tol_krylov=1e-15)
+    e0, E0, _ = S.get_energies()
+    with pytest.raises(sphrt.SphRtError) as ei:
+        S.step(w.dt, *w.step_inputs(1))
+    assert ei.value.status == sphrt.ENOTCONV and "Krylov" in str(ei.value)
+    e1, E1, _ = S.get_energies()
+    assert np.array_equal(e0, e1) and np.array_equal(E0, E1)
+    S.close()
+
+
+def test_graph_outer_limit_ends_step_unchanged():
+    w = I.mms_2d(n=16, steps=1)
+    S = sphrt.solver_for(w, max_outer=2, tol_outer_e=1e-300, tol_outer_E=1e-300)
+    e0, E0, _ = S.get_energies()
+    with pytest.raises(sphrt.SphRtError) as ei:
+        S.step(w.dt, *w.step_inputs(1))
+    assert ei.value.status == sphrt.ENOTCONV and "max_outer" in str(ei.value)
+    e1, E1, _ = S.get_energies()
+    assert np.array_equal(e0, e1) and np.array_equal(E0, E1)
+    S.close()
+
+
+@pytest.mark.parametrize("precision", [sphrt.FP64, sphrt.MIXED])
+def test_cluster_tail_vcycle_bitwise_and_fewer_launches(precision):
+    # 32^3: levels of ~420k, 80k, 19k, 5k stored entries run in the cluster tail
+    w = I.mms_3d_lp(n=32, steps=2)
+    on = _run(w, 2, precision=precision, amg_tail=1)
+    off = _run(w, 2, precision=precision, amg_tail=0)
+    assert np.array_equal(on[0], off[0]) and np.array_equal(on[1], off[1])
+    assert on[2] == off[2]
+    assert on[4] < off[4]  # the tail replaces several launches per V-cycle

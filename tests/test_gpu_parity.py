@@ -188,6 +188,14 @@ def test_energy_balance_on_gpu():
         assert abs(g.energy_after - o.energy_after) < 1e-12 * o.energy_after
 
 
+@pytest.mark.parametrize("precision,tol", [(sphrt.FP64, 1e-10), (sphrt.MIXED, 1e-8)])
+def test_heterogeneous_sphere_parity(precision, tol):
+    # dense opaque hot sphere (rho x10, sigma x1e3) in a cold medium: strong coefficient jumps
+    w = I.sphere_3d(n=12, steps=2, dt=1e-4)
+    r = run_both(w, 2, gpu_over=dict(precision=precision), orc_over=TIGHT)
+    assert r["err_e"] < tol and r["err_E"] < tol, (r["err_e"], r["err_E"])
+
+
 def test_mixed_precision_parity():
     w = I.mms_3d_lp(n=16, steps=3)
     r = run_both(w, 3, gpu_over=dict(precision=sphrt.MIXED, precond=sphrt.PRECOND_AMG),
