@@ -76,7 +76,9 @@ typedef struct {
   int32_t max_outer, max_inner_e, max_krylov;
   int32_t precond;      /* SPH_RT_PRECOND_* */
   int32_t precision;    /* SPH_RT_FP64 or SPH_RT_MIXED */
-  int32_t cheb_degree;  /* Chebyshev smoother / preconditioner degree (>= 1) */
+  int32_t cheb_degree;  /* Chebyshev smoother / preconditioner degree (1..16; default 1: on
+                           GB300 each extra degree costs a fine-level FP64 sweep, and degree 1
+                           gave the fastest AMG-CG at 64^3 and 128^3) */
   int32_t amg_rebuild;  /* 1: redo AMG aggregation every step; 0: keep the first step's */
   double amg_theta;     /* AMG strength threshold: j strong for i if |B_ij| >= theta sqrt(B_ii B_jj) */
   int32_t check_every;  /* Krylov iterations queued between host convergence reads */
@@ -85,7 +87,8 @@ typedef struct {
                            of a particle set; 0 (default): U from the mean row length.  U never
                            changes a result bit (the lanes per row, W, follow the row length) */
   int32_t amg_tail;     /* 1: run the small AMG levels (each <= 600k stored entries) of every
-                           V-cycle as one thread-block-cluster launch (bitwise the same result) */
+                           V-cycle as one thread-block-cluster launch (bitwise the same result;
+                           default 0: measured no faster than the per-level launches) */
   int32_t graphs;       /* 1: run each step's outer loop as one CUDA graph with conditional
                            WHILE nodes (no host round trip per iteration); ignored while
                            kernel_timing = 1, which needs per-launch events */
@@ -205,6 +208,14 @@ sph_rt_status sph_rt_get_properties(sph_rt *s, double *T, double *sigma, double 
  * x and y).  reset != 0 clears the counters after reading. */
 sph_rt_status sph_rt_kernel_stats(sph_rt *s, int64_t *launches, double *total_ms,
                                   double *bytes, int reset);
+
+/* The same counters split by kernel: SPH_RT_KERNEL_SPMV_PQ (the CG product
+ * fused with the p, q updates and (p, q)), SPH_RT_KERNEL_RESID (residual
+ * sweeps: CG start and V-cycle fine level), SPH_RT_KERNEL_CHEB (fine-level
+ * Chebyshev smoother / preconditioner sweeps).  Cleared with the totals. */
+enum { SPH_RT_KERNEL_SPMV_PQ = 0, SPH_RT_KERNEL_RESID = 1, SPH_RT_KERNEL_CHEB = 2 };
+sph_rt_status sph_rt_kernel_stats_kind(sph_rt *s, int32_t kind, int64_t *launches,
+                                       double *total_ms, double *bytes);
 
 /* AMG hierarchy of the last step: number of levels, and rows and stored
  * off-diagonal nonzeros per level (arrays of max_levels entries, may be NULL). */

@@ -431,8 +431,8 @@ __global__ void convert_kernel(int64_t n, const S *in, D *out) {
 // V-cycle kernels
 // ---------------------------------------------------------------------------
 template <int W, int U, typename MT, typename VT>
-__global__ void resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
-                                   const Scalars *sc, int *wflag) {
+__device__ __forceinline__ void resid_level_body(const CsrView<MT> &A, const VT *r, const VT *z,
+                                                 VT *res, const Scalars *sc, int *wflag) {
   if (sc && sc->done) {
     mark_work(wflag, 0);
     return;
@@ -446,8 +446,19 @@ __global__ void resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *
     const bool active = i < A.n;
     VT s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub) : VT(0);
     s = row_reduce<W>(s);
-    if (active && sub == 0) res[i] = r[i] - ((VT)A.diag[i] * z[i] + s);
+    if (active && sub == 0) res[i] = r[i] - fmadd((VT)A.diag[i], z[i], s);
   }
+}
+// one body, two names: finest level vs coarse levels in profiles
+template <int W, int U, typename MT, typename VT>
+__global__ void resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
+                                   const Scalars *sc, int *wflag) {
+  resid_level_body<W, U, MT, VT>(A, r, z, res, sc, wflag);
+}
+template <int W, int U, typename MT, typename VT>
+__global__ void fine_resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
+                                        const Scalars *sc, int *wflag) {
+  resid_level_body<W, U, MT, VT>(A, r, z, res, sc, wflag);
 }
 
 template <typename VT>
@@ -519,9 +530,9 @@ __device__ void coarse_cheb_body(const CsrView<MT> &A, const VT *r_g, VT *z_g, c
     const VT c1 = (VT)cf->c1[k], c2 = (VT)cf->c2[k];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {  // thread per row: no shuffles
       VT s = 0;
-      for (int kk = ptr[i]; kk < ptr[i + 1]; ++kk) s += (VT)val[kk] * zin[col[kk]];
-      VT res = r[i] - ((VT)dg[i] * zin[i] + s);
-      VT di = c1 * d[i] + c2 * (VT)idg[i] * res;
+      for (int kk = ptr[i]; kk < ptr[i + 1]; ++kk) s = fmadd((VT)val[kk], zin[col[kk]], s);
+      VT res = r[i] - fmadd((VT)dg[i], zin[i], s);
+      VT di = fmadd(c1, d[i], (c2 * (VT)idg[i]) * res);
       d[i] = di;
       zout[i] = zin[i] + di;
     }
@@ -587,7 +598,7 @@ __device__ __forceinline__ VT row_dot_cg(int64_t beg, int64_t end, const int32_t
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (c[u] >= 0) s += (VT)v[u] * __ldcg(x + c[u]);
+      if (c[u] >= 0) s = fmadd((VT)v[u], __ldcg(x + c[u]), s);
   }
   return s;
 }
@@ -625,9 +636,9 @@ __device__ __forceinline__ void tail_cheb_step(const TailLevel<T> &L, const T *z
   const T vc1 = (T)c1, vc2 = (T)c2;
   tail_rows_w(L.A, zin, r0, r1, [&](int64_t i, T s) {
     T zi = __ldcg(zin + i);
-    T res = __ldcg(L.r + i) - ((T)L.A.diag[i] * zi + s);
-    T di = vc2 * (T)L.A.invdiag[i] * res;
-    if (k > 0) di += vc1 * __ldcg(L.d + i);
+    T res = __ldcg(L.r + i) - fmadd((T)L.A.diag[i], zi, s);
+    T di = (vc2 * (T)L.A.invdiag[i]) * res;
+    if (k > 0) di = fmadd(vc1, __ldcg(L.d + i), di);
     L.d[i] = di;
     zout[i] = zi + di;
   });
@@ -669,7 +680,7 @@ __global__ void __launch_bounds__(1024, 1) vcycle_tail_kernel(const __grid_const
     cheb_zero(L, L.deg);
     const int64_t r0 = lo(L.A.n), r1 = hi(L.A.n);
     tail_rows_w(L.A, L.z, r0, r1, [&](int64_t i, T s) {
-      L.res[i] = __ldcg(L.r + i) - ((T)L.A.diag[i] * __ldcg(L.z + i) + s);
+      L.res[i] = __ldcg(L.r + i) - fmadd((T)L.A.diag[i], __ldcg(L.z + i), s);
     });
     cl.sync();
     for (int64_t I = lo(C.A.n) + threadIdx.x; I < hi(C.A.n); I += blockDim.x) {
@@ -1181,11 +1192,18 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
   // fine-level residual sweeps are timed with the other fine SpMV-class kernels;
   // per row: rowptr, diag, r, z, res
   int *wf = l == 0 ? timing_begin(s) : nullptr;
-  SPH_DISPATCH_SHAPE(A.W, A.U,
-                     (resid_level_kernel<W, U, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res,
-                                                                                    sc, wf)));
+  if (l == 0)
+    SPH_DISPATCH_SHAPE(A.W, A.U,
+                       (fine_resid_level_kernel<W, U, T, T><<<gw, kBlock, 0, s->stream>>>(
+                           A, r, z, res, sc, wf)));
+  else
+    SPH_DISPATCH_SHAPE(A.W, A.U,
+                       (resid_level_kernel<W, U, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res,
+                                                                                      sc, wf)));
   SPH_LAUNCHED(s);
-  if (l == 0) timing_end(s, (4.0 + sizeof(T)) * (double)A.nnz + (8.0 + 4.0 * sizeof(T)) * (double)A.n);
+  if (l == 0)
+    timing_end(s, (4.0 + sizeof(T)) * (double)A.nnz + (8.0 + 4.0 * sizeof(T)) * (double)A.n,
+               kTimedResid);
   SphLevel *C = s->levels[l + 1];
   restrict_kernel<T><<<gcap(s, C->n, kBlock), kBlock, 0, s->stream>>>(C->n, L->agg_ptr, L->agg_mem,
                                                                       res, LV::r(C), sc);

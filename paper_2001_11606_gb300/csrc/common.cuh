@@ -47,6 +47,7 @@ struct Scalars {
   int iters;       // Krylov iterations taken
   int breakdown;   // non-positive curvature / NaN seen
   int bad_input;   // a step input (source or ghost value) was not finite
+  int gate_timeout;  // a timing gate gave up waiting for the host (timing only)
   unsigned int counter;  // arrival counter of the last-block reductions
   // outer (nonlinear-elimination) loop of Alg. 1, advanced by outer_check_kernel
   int outer_iters;       // completed outer iterations
@@ -151,6 +152,12 @@ __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + 
 // independent gathers, so a row of up to W*U entries costs one dependent
 // memory round trip instead of one per W entries.  Out-of-range slots load
 // nothing and add nothing.
+// Explicit fused multiply-add: the kernels that must agree bit for bit (the
+// launched V-cycle and its cluster-resident tail) spell out every fusion
+// instead of leaving the choice to the compiler's contraction.
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+
 template <int W, int U, typename MT, typename VT>
 __device__ __forceinline__ VT row_dot(int64_t beg, int64_t end, const int32_t *__restrict__ col,
                                       const MT *__restrict__ val, const VT *__restrict__ x,
@@ -167,7 +174,7 @@ __device__ __forceinline__ VT row_dot(int64_t beg, int64_t end, const int32_t *_
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (c[u] >= 0) s += (VT)v[u] * __ldg(x + c[u]);
+      if (c[u] >= 0) s = fmadd((VT)v[u], __ldg(x + c[u]), s);
   }
   return s;
 }
@@ -402,10 +409,19 @@ struct sph_rt {
   // kernel timing
   std::vector<cudaEvent_t> ev_pool;
   std::vector<double> ev_bytes;   // bytes of each event pair
+  std::vector<int> ev_kind;       // kernel kind of each event pair (sphrt::TimedKind)
   int *ev_flags = nullptr;        // device: work flag of each event pair
+  // timing gate: with kernel_timing the stream is held by gate_kernel until a
+  // whole chunk of the solve is queued, so that the timed kernels run back to
+  // back and an event pair measures the kernel, not the host's launch latency
+  volatile int *gate_host = nullptr;  // mapped pinned word written by the host
+  int *gate_dev = nullptr;            // its device address
+  int gate_epoch = 0;
   int ev_used = 0;
   int64_t spmv_launches = 0;
   double spmv_ms = 0.0, spmv_bytes = 0.0;
+  int64_t kind_launches[3] = {0, 0, 0};  // per sphrt::TimedKind
+  double kind_ms[3] = {0, 0, 0}, kind_bytes[3] = {0, 0, 0};
 };
 
 // Helpers shared by the translation units (defined in sph_rt.cu).
@@ -423,8 +439,10 @@ void dfree(sph_rt *s, void *p);  // back to the free list (stream-ordered users 
 // timing_begin returns the work flag of the launch (nullptr when timing is off):
 // the kernel writes 1 there if it does work and 0 if it returns at once because
 // the solve has converged; only launches that worked are counted.
+// kinds of timed fine-operator launches (SPH_RT_KERNEL_* in sph_rt.h)
+enum TimedKind { kTimedSpmvPQ = 0, kTimedResid = 1, kTimedCheb = 2 };
 int *timing_begin(sph_rt *s);
-void timing_end(sph_rt *s, double bytes);
+void timing_end(sph_rt *s, double bytes, int kind);
 void timing_flush(sph_rt *s);
 __device__ __forceinline__ void mark_work(int *wflag, int worked) {
   if (wflag && blockIdx.x == 0 && threadIdx.x == 0) *wflag = worked;

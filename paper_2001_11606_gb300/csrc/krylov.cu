@@ -49,7 +49,7 @@ __global__ void resid_kernel(CsrView<double> A, const double *b, const double *x
     double s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, x, sub) : 0.0;
     s = row_reduce<W>(s);
     if (active && sub == 0) {
-      double ri = b[i] - (A.diag[i] * x[i] + s);
+      double ri = b[i] - fmadd(A.diag[i], x[i], s);
       r[i] = ri;
       double ru = ri * invV[i];
       acc += ru * ru;
@@ -229,8 +229,9 @@ __global__ void cheb_init_zero_kernel(int64_t n, const VT *r, const MT *invdiag,
 
 
 template <int W, int U, typename MT, typename VT>
-__global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
-                                 const ChebCoef *cf, int k, const Scalars *sc, int *wflag) {
+__device__ __forceinline__ void cheb_step_body(const CsrView<MT> &A, const VT *r, const VT *z_in,
+                                               VT *z_out, VT *d, const ChebCoef *cf, int k,
+                                               const Scalars *sc, int *wflag) {
   if (sc && sc->done) {
     mark_work(wflag, 0);
     return;
@@ -249,13 +250,26 @@ __global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT 
     s = row_reduce<W>(s);
     if (active && sub == 0) {
       VT zi = z_in[i];
-      VT res = r[i] - ((VT)A.diag[i] * zi + s);
-      VT di = vc2 * (VT)A.invdiag[i] * res;
-      if (k > 0) di += vc1 * d[i];  // the first step must not read d
+      VT res = r[i] - fmadd((VT)A.diag[i], zi, s);
+      VT di = (vc2 * (VT)A.invdiag[i]) * res;
+      if (k > 0) di = fmadd(vc1, d[i], di);  // the first step must not read d
       d[i] = di;
       z_out[i] = zi + di;
     }
   }
+}
+// The same sweep under two names, so that profiles separate the finest
+// level (HBM-streamed operator) from the coarse levels (L2-resident).
+template <int W, int U, typename MT, typename VT>
+__global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
+                                 const ChebCoef *cf, int k, const Scalars *sc, int *wflag) {
+  cheb_step_body<W, U, MT, VT>(A, r, z_in, z_out, d, cf, k, sc, wflag);
+}
+template <int W, int U, typename MT, typename VT>
+__global__ void fine_cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out,
+                                      VT *d, const ChebCoef *cf, int k, const Scalars *sc,
+                                      int *wflag) {
+  cheb_step_body<W, U, MT, VT>(A, r, z_in, z_out, d, cf, k, sc, wflag);
 }
 
 // ---------------------------------------------------------------------------
@@ -289,6 +303,7 @@ CsrView<double> fine_view(const sph_rt *s) {
 // Kernel-time bracketing of fine SpMV-class launches (config.kernel_timing).
 constexpr int kEventPairs = 2048;
 void timing_flush(sph_rt *s) {
+  if (s->gate_host) *s->gate_host = s->gate_epoch;  // never wait on a held stream
   if (!s->cfg.kernel_timing || s->ev_used == 0) return;
   const int pairs = s->ev_used / 2;
   std::vector<int> flags(pairs, 1);
@@ -302,6 +317,10 @@ void timing_flush(sph_rt *s) {
     s->spmv_ms += ms;
     s->spmv_launches++;
     s->spmv_bytes += s->ev_bytes[k];
+    const int kd = s->ev_kind[k];
+    s->kind_ms[kd] += ms;
+    s->kind_launches[kd]++;
+    s->kind_bytes[kd] += s->ev_bytes[k];
   }
   s->ev_used = 0;
 }
@@ -314,6 +333,7 @@ int *timing_begin(sph_rt *s) {
       s->ev_pool.push_back(e);
     }
     s->ev_bytes.assign(kEventPairs, 0.0);
+    s->ev_kind.assign(kEventPairs, 0);
   }
   if (!s->ev_flags) s->ev_flags = dalloc<int>(s, kEventPairs);
   if (s->ev_used + 2 > (int)s->ev_pool.size()) timing_flush(s);
@@ -321,9 +341,10 @@ int *timing_begin(sph_rt *s) {
   cudaEventRecord(s->ev_pool[s->ev_used++], s->stream);
   return s->ev_flags ? s->ev_flags + pair : nullptr;
 }
-void timing_end(sph_rt *s, double bytes) {
+void timing_end(sph_rt *s, double bytes, int kind) {
   if (!s->cfg.kernel_timing) return;
   s->ev_bytes[(s->ev_used - 1) / 2] = bytes;
+  s->ev_kind[(s->ev_used - 1) / 2] = kind;
   cudaEventRecord(s->ev_pool[s->ev_used++], s->stream);
 }
 
@@ -354,11 +375,16 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
   const double bytes = spmv_class_bytes(A, 8 + 2 * (int)sizeof(MT) + 5 * (int)sizeof(VT));
   auto step = [&](const VT *zin, VT *zout, int k) -> sph_rt_status {
     int *wf = fine ? timing_begin(s) : nullptr;
-    SPH_DISPATCH_SHAPE(A.W, A.U,
-                       (cheb_step_kernel<W, U, MT, VT><<<gw, kBlock, 0, s->stream>>>(
-                           A, r, zin, zout, d, cf, k, sc, wf)));
+    if (fine)
+      SPH_DISPATCH_SHAPE(A.W, A.U,
+                         (fine_cheb_step_kernel<W, U, MT, VT><<<gw, kBlock, 0, s->stream>>>(
+                             A, r, zin, zout, d, cf, k, sc, wf)));
+    else
+      SPH_DISPATCH_SHAPE(A.W, A.U,
+                         (cheb_step_kernel<W, U, MT, VT><<<gw, kBlock, 0, s->stream>>>(
+                             A, r, zin, zout, d, cf, k, sc, wf)));
     SPH_LAUNCHED(s);
-    if (fine) timing_end(s, bytes);
+    if (fine) timing_end(s, bytes, kTimedCheb);
     return SPH_RT_OK;
   };
   // ping-pong between z and tmp so that the last write lands in z
@@ -501,14 +527,14 @@ sph_rt_status pcg_prologue(sph_rt *s) {
                                                                        s->invV, s->sc,
                                                                        s->partials, wf)));
   SPH_LAUNCHED(s);
-  timing_end(s, spmv_class_bytes(A, kRowBytesResid));
+  timing_end(s, spmv_class_bytes(A, kRowBytesResid), kTimedResid);
   if ((rc = precondition(s, A, 1))) return rc;
   wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
                      (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->z, s->q, s->p, 1,
                                                                          s->sc, s->partials, wf)));
   SPH_LAUNCHED(s);
-  timing_end(s, spmv_class_bytes(A, kRowBytesSpmvPQ));
+  timing_end(s, spmv_class_bytes(A, kRowBytesSpmvPQ), kTimedSpmvPQ);
   return SPH_RT_OK;
 }
 
@@ -540,22 +566,65 @@ sph_rt_status pcg_iteration(sph_rt *s) {
                      (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->z, s->q, s->p, 0,
                                                                          s->sc, s->partials, wf)));
   SPH_LAUNCHED(s);
-  timing_end(s, spmv_class_bytes(A, kRowBytesSpmvPQ));
+  timing_end(s, spmv_class_bytes(A, kRowBytesSpmvPQ), kTimedSpmvPQ);
   return SPH_RT_OK;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Holds the stream until the host has written `epoch` (or 2 s have passed,
+// which only marks the timing as suspect).
+__global__ void gate_kernel(const volatile int *flag, int epoch, Scalars *sc) {
+  const unsigned long long t0 = global_ns();
+  while (*flag < epoch) {
+    if (global_ns() - t0 > 2000000000ull) {
+      sc->gate_timeout = 1;
+      return;
+    }
+    __nanosleep(2000);
+  }
+}
+
+// With kernel timing: hold the stream (gate_begin) while a chunk is queued,
+// release it (gate_end) once the chunk is complete.
+static sph_rt_status gate_begin(sph_rt *s) {
+  if (!s->cfg.kernel_timing) return SPH_RT_OK;
+  if (!s->gate_host) {
+    int *h = nullptr;
+    SPH_CUDA(s, cudaHostAlloc(&h, sizeof(int), cudaHostAllocMapped));
+    *h = 0;
+    SPH_CUDA(s, cudaHostGetDevicePointer(&s->gate_dev, h, 0));
+    s->gate_host = h;
+    s->gate_epoch = 0;
+  }
+  ++s->gate_epoch;
+  gate_kernel<<<1, 1, 0, s->stream>>>(s->gate_dev, s->gate_epoch, s->sc);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+static void gate_end(sph_rt *s) {
+  if (s->gate_host) *s->gate_host = s->gate_epoch;
 }
 
 // Host-driven solve: iterations are queued in chunks of check_every and the
 // device flag is read after each chunk.
 sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged) {
   sph_rt_status rc;
+  if ((rc = gate_begin(s))) return rc;
   if ((rc = pcg_prologue(s))) return rc;
   const int chunk = s->cfg.check_every > 0 ? s->cfg.check_every : 1;
   int queued = 0;
   for (;;) {
+    if (queued > 0 && (rc = gate_begin(s))) return rc;
     for (int c = 0; c < chunk; ++c) {
       if ((rc = pcg_iteration(s))) return rc;
       ++queued;
     }
+    gate_end(s);
     SPH_CUDA(s, cudaMemcpyAsync(s->sc_host, s->sc, sizeof(Scalars), cudaMemcpyDeviceToHost,
                                 s->stream));
     SPH_CUDA(s, cudaStreamSynchronize(s->stream));

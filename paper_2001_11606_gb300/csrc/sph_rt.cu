@@ -108,6 +108,7 @@ void *dalloc_bytes(sph_rt *s, size_t bytes) {
 }
 
 void free_all(sph_rt *s) {
+  if (s->gate_host) *s->gate_host = s->gate_epoch;  // release a held timing gate
   if (s->cuda_ready) cudaStreamSynchronize(s->stream);
   loop_graph_release(s);  // its launches refer to the buffers released below
   amg_release(s);
@@ -167,13 +168,13 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->max_krylov = 2000;
   c->precond = SPH_RT_PRECOND_AMG;
   c->precision = SPH_RT_FP64;
-  c->cheb_degree = 2;
+  c->cheb_degree = 1;
   c->amg_rebuild = 0;
   c->amg_theta = 0.02;
   c->check_every = 8;
   c->kernel_timing = 0;
   c->autotune = 0;
-  c->amg_tail = 1;
+  c->amg_tail = 0;
   c->graphs = 1;
   c->device = 0;
   c->stream = nullptr;
@@ -261,6 +262,7 @@ extern "C" void sph_rt_destroy(sph_rt *s) {
     cudaSetDevice(s->cfg.device);
     free_everything(s);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->gate_host) cudaFreeHost((void *)s->gate_host);
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     if (s->sc_host) cudaFreeHost(s->sc_host);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -787,6 +789,21 @@ extern "C" sph_rt_status sph_rt_kernel_stats(sph_rt *s, int64_t *launches, doubl
     s->spmv_launches = 0;
     s->spmv_ms = 0.0;
     s->spmv_bytes = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      s->kind_launches[k] = 0;
+      s->kind_ms[k] = 0.0;
+      s->kind_bytes[k] = 0.0;
+    }
   }
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_kernel_stats_kind(sph_rt *s, int32_t kind, int64_t *launches,
+                                                  double *total_ms, double *bytes) {
+  if (!s) return SPH_RT_EINVAL;
+  if (kind < 0 || kind > 2) return set_error(s, SPH_RT_EINVAL, "kernel kind out of range");
+  if (launches) *launches = s->kind_launches[kind];
+  if (total_ms) *total_ms = s->kind_ms[kind];
+  if (bytes) *bytes = s->kind_bytes[kind];
   return SPH_RT_OK;
 }

@@ -113,6 +113,7 @@ _SIGNATURES = [
     ("sph_rt_kernel_stats", C.c_int, [_P, _P, _P, _P, C.c_int]),
     ("sph_rt_get_amg_info", C.c_int, [_P, _P, _P, _P, C.c_int32]),
     ("sph_rt_loop_graph_info", C.c_int, [_P, _P, _P]),
+    ("sph_rt_kernel_stats_kind", C.c_int, [_P, C.c_int32, _P, _P, _P]),
     ("sph_rt_launch_count", C.c_int64, [_P]),
     ("sph_rt_last_error", C.c_char_p, [_P]),
     ("sph_rt_destroy", None, [_P]),
@@ -321,6 +322,16 @@ class Solver:
         self._check(self._L.sph_rt_kernel_stats(self._h, C.byref(n), C.byref(ms), C.byref(by),
                                                 int(reset)))
         return n.value, ms.value, by.value
+
+    def kernel_stats_by_kind(self):
+        """{name: (launches, ms, bytes)} of the timed fine-operator kernels."""
+        out = {}
+        for kind, name in ((0, "spmv_pq"), (1, "resid"), (2, "cheb_step")):
+            n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+            self._check(self._L.sph_rt_kernel_stats_kind(self._h, kind, C.byref(n), C.byref(ms),
+                                                         C.byref(by)))
+            out[name] = (n.value, ms.value, by.value)
+        return out
 
     def amg_info(self):
         nl = C.c_int32()

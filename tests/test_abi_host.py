@@ -43,7 +43,8 @@ def test_max_outer_beyond_recorded_stats_is_allowed():
 def test_config_struct_matches_defaults():
     cfg = sphrt.default_config()
     assert cfg.dim == 3 and cfg.a == 1.0 and cfg.precond == sphrt.PRECOND_AMG
-    assert cfg.amg_theta == 0.02 and cfg.cheb_degree == 2 and cfg.graphs == 1
+    assert cfg.amg_theta == 0.02 and cfg.cheb_degree == 1 and cfg.graphs == 1
+    assert cfg.amg_tail == 0 and cfg.autotune == 0
     assert cfg.tol_outer_e == 1e-8 and cfg.tol_krylov == 1e-12 and cfg.tol_inner_e == 1e-13
 
 

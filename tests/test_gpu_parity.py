@@ -190,10 +190,16 @@ def test_energy_balance_on_gpu():
 
 @pytest.mark.parametrize("precision,tol", [(sphrt.FP64, 1e-10), (sphrt.MIXED, 1e-8)])
 def test_heterogeneous_sphere_parity(precision, tol):
-    # dense opaque hot sphere (rho x10, sigma x1e3) in a cold medium: strong coefficient jumps
+    # dense opaque hot sphere (rho x10, sigma x1e3, T = 1) in a cold medium (T = 0.01): E spans
+    # 8 decades.  Both solvers stop on ||b - A E|| <= tol ||b||, a norm-wise test, so the
+    # cold entries (E ~ 1e-8) carry absolute errors ~tol ||b|| from either side: the
+    # comparison is relative to max |E| (and elementwise for e, which spans 2 decades).
     w = I.sphere_3d(n=12, steps=2, dt=1e-4)
     r = run_both(w, 2, gpu_over=dict(precision=precision), orc_over=TIGHT)
-    assert r["err_e"] < tol and r["err_E"] < tol, (r["err_e"], r["err_E"])
+    m = w.particles.kind == 0
+    assert r["err_e"] < tol, r["err_e"]
+    errE = np.max(np.abs(r["Eg"][m] - r["E"][m])) / np.max(np.abs(r["E"][m]))
+    assert errE < tol, errE
 
 
 def test_mixed_precision_parity():
