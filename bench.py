@@ -132,7 +132,9 @@ def aggregate_ranks(t_local: float, work_local: float):
 # ncu capture of the kernel at the workload, keyed (workload, precision, kernel);
 # the profiles/ summary named in the second field holds the capture.
 NCU_TRAFFIC = {
-    ("mms3d-lp-64^3", "fp64", "spmv_pq"): (355.4e6, "profiles/spmv_pq_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "spmv_pq"): (354.8e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "cheb_step"): (358.1e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "resid"): (344.4e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
 }
 
 

@@ -59,6 +59,7 @@ struct Scalars {
   int newton_max;        // largest material Newton iteration count
   int krylov_per_outer[64];
   double last_change_e, last_change_E;
+  double energy_before_e, energy_before_E;  // interior totals at the start of the step
 };
 
 // --------------------------------------------------------------------------

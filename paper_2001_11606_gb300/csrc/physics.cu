@@ -451,13 +451,31 @@ __global__ void scatter_caller_kernel(const double *in_s, const int64_t *slot2ca
     out_c[slot2caller[s]] = in_s[s];
 }
 
-__global__ void commit_kernel(int64_t n_int, const double *e_new, const double *E_new, double *e,
-                              double *E) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+// End of a step: a converged step with valid inputs commits its interior
+// state; any other step restores the snapshot taken at its start (ghost
+// entries included), so a failed step leaves the state unchanged.
+__global__ void finish_kernel(int64_t n_int, int64_t n, const double *e_new, const double *E_new,
+                              const double *e_bak, const double *E_bak, double *e, double *E,
+                              const Scalars *sc) {
+  const bool commit = sc->outer_status == 1 && !sc->bad_input;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    e[i] = e_new[i];
-    E[i] = E_new[i];
+    if (commit) {
+      if (i < n_int) {
+        e[i] = e_new[i];
+        E[i] = E_new[i];
+      }
+    } else {
+      e[i] = e_bak[i];
+      E[i] = E_bak[i];
+    }
   }
+}
+
+// the totals just reduced (red[4], red[5]) are the energy before the step
+__global__ void save_before_kernel(Scalars *sc) {
+  sc->energy_before_e = sc->red[4];
+  sc->energy_before_E = sc->red[5];
 }
 
 // ---------------------------------------------------------------------------
@@ -635,9 +653,16 @@ sph_rt_status launch_scatter_caller(sph_rt *s, const double *in_s, int64_t count
   return SPH_RT_OK;
 }
 
-sph_rt_status launch_commit(sph_rt *s, const double *e_new, const double *E_new) {
-  int g = grid_items(s, s->n_int, kBlock);
-  commit_kernel<<<g, kBlock, 0, s->stream>>>(s->n_int, e_new, E_new, s->e, s->E);
+sph_rt_status launch_finish(sph_rt *s, const double *e_new, const double *E_new) {
+  int g = grid_items(s, s->n, kBlock);
+  finish_kernel<<<g, kBlock, 0, s->stream>>>(s->n_int, s->n, e_new, E_new, s->e_bak, s->E_bak,
+                                             s->e, s->E, s->sc);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+sph_rt_status launch_save_before(sph_rt *s) {
+  save_before_kernel<<<1, 1, 0, s->stream>>>(s->sc);
   SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }

@@ -33,7 +33,8 @@ sph_rt_status launch_ghost_install(sph_rt *s, const double *ge_c, const double *
 sph_rt_status launch_copy_sync(sph_rt *s);
 sph_rt_status launch_gather_interior(sph_rt *s, const double *in_c, double *out);
 sph_rt_status launch_scatter_caller(sph_rt *s, const double *in_s, int64_t count, double *out_c);
-sph_rt_status launch_commit(sph_rt *s, const double *e_new, const double *E_new);
+sph_rt_status launch_finish(sph_rt *s, const double *e_new, const double *E_new);
+sph_rt_status launch_save_before(sph_rt *s);
 sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged);
 sph_rt_status autotune_fine_shape(sph_rt *s);
 sph_rt_status outer_loop(sph_rt *s, double dt);
@@ -496,13 +497,18 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
 
   SPH_TRACE("step: begin n=%lld n_int=%lld nnz=%lld dt=%g", (long long)s->n, (long long)s->n_int,
             (long long)s->nnz_mat, dt);
-  // input check and energy before the step (one host read for both)
+  // input check and energy before the step.  They are read with the step's
+  // results at the end (one host round trip per step); a step that will build
+  // the AMG structure reads them first, so that the kept hierarchy never comes
+  // from a rejected input.
   if ((rc = launch_check_inputs(s, Qe_c, QE_c, ge_c, gE_c))) return rc;
   if ((rc = launch_totals(s, s->e, s->E))) return rc;
-  if ((rc = read_scalars(s))) return rc;
-  if (s->sc_host->bad_input)
-    return set_error(s, SPH_RT_EINVAL, "non-finite source or ghost value");
-  st.energy_before = s->sc_host->red[4] + s->sc_host->red[5];
+  if ((rc = launch_save_before(s))) return rc;
+  if (s->cfg.precond == SPH_RT_PRECOND_AMG && (!s->amg_ready || s->cfg.amg_rebuild)) {
+    if ((rc = read_scalars(s))) return rc;
+    if (s->sc_host->bad_input)
+      return set_error(s, SPH_RT_EINVAL, "non-finite source or ghost value");
+  }
 
   tm.begin(0);
   // snapshot of the state (restored if the step does not converge)
@@ -550,7 +556,17 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   tm.begin(3);
   if ((rc = outer_loop(s, dt))) return rc;
   tm.end();
+  // commit (converged, valid input) or restore the snapshot, ghost copies,
+  // energy balance and totals; then the one host read of the step
+  if ((rc = launch_finish(s, s->e_l, s->E_l))) return rc;
+  if ((rc = launch_copy_sync(s))) return rc;
+  if ((rc = launch_balance(s, dt, s->E))) return rc;
+  if ((rc = launch_totals(s, s->e, s->E))) return rc;
   if ((rc = read_scalars(s))) return rc;
+  if (s->sc_host->bad_input) {
+    tm.collect(ms);
+    return set_error(s, SPH_RT_EINVAL, "non-finite source or ghost value");
+  }
   {
     const Scalars &h = *s->sc_host;
     outer_loop_account(s, h);
@@ -566,26 +582,18 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   }
   const bool converged = s->sc_host->outer_status == 1;
   const bool krylov_fail = s->sc_host->outer_status == 2;
+  st.energy_before = s->sc_host->energy_before_e + s->sc_host->energy_before_E;
 
   if (!converged) {
-    // restore the ghost values; interior state was never written
-    SPH_CUDA(s, cudaMemcpyAsync(s->e, s->e_bak, sizeof(double) * s->n, cudaMemcpyDeviceToDevice, s->stream));
-    SPH_CUDA(s, cudaMemcpyAsync(s->E, s->E_bak, sizeof(double) * s->n, cudaMemcpyDeviceToDevice, s->stream));
-    SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+    // the snapshot was restored on the device (ghost values included)
     tm.collect(ms);
     if (stats) *stats = st;
     return set_error(s, SPH_RT_ENOTCONV,
                      krylov_fail ? "Krylov solve did not converge (max_krylov or breakdown)"
                                  : "outer iteration did not converge within max_outer");
   }
-  if ((rc = launch_commit(s, s->e_l, s->E_l))) return rc;
-  if ((rc = launch_copy_sync(s))) return rc;
-  if ((rc = launch_balance(s, dt, s->E))) return rc;
-  if ((rc = read_scalars(s))) return rc;
   st.source_energy = s->sc_host->red[6];
   st.boundary_energy = s->sc_host->red[7];
-  if ((rc = launch_totals(s, s->e, s->E))) return rc;
-  if ((rc = read_scalars(s))) return rc;
   st.energy_after = s->sc_host->red[4] + s->sc_host->red[5];
   tm.collect(ms);
   st.t_setup_ms = ms[0];
