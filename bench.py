@@ -132,9 +132,9 @@ def aggregate_ranks(t_local: float, work_local: float):
 # ncu capture of the kernel at the workload, keyed (workload, precision, kernel);
 # the profiles/ summary named in the second field holds the capture.
 NCU_TRAFFIC = {
-    ("mms3d-lp-64^3", "fp64", "spmv_pq"): (354.8e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
-    ("mms3d-lp-64^3", "fp64", "cheb_step"): (358.1e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
-    ("mms3d-lp-64^3", "fp64", "resid"): (344.4e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "spmv_pq"): (337.1e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "cheb_step"): (337.6e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "resid"): (334.1e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
 }
 
 
@@ -280,6 +280,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven outer loop instead of the per-step CUDA graph")
+    ap.add_argument("--check-every", type=int, default=None,
+                    help="host-driven loop: Krylov iterations queued per convergence read "
+                         "(1: no launch after convergence, the graph's kernel sequence)")
     ap.add_argument("--requests", type=int, default=512, help="serving: number of requests")
     ap.add_argument("--workers", type=int, default=8, help="serving: worker threads")
     ap.add_argument("--max-resident", type=int, default=32, help="serving: resident cap")
@@ -313,8 +316,10 @@ def main():
     precond = {"jacobi": sphrt.PRECOND_JACOBI, "chebyshev": sphrt.PRECOND_CHEBYSHEV,
                "amg": sphrt.PRECOND_AMG}[args.precond]
     prec = sphrt.MIXED if args.precision == "mixed" else sphrt.FP64
+    extra = {"check_every": args.check_every} if args.check_every else {}
     cfg = sphrt.config_from_params(w.params, device=local, stream=stream.cuda_stream,
-                                   precond=precond, precision=prec, graphs=int(not args.no_graphs))
+                                   precond=precond, precision=prec, graphs=int(not args.no_graphs),
+                                   **extra)
     S = sphrt.Solver(cfg)
 
     # ---- inputs resident in HBM --------------------------------------------

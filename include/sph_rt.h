@@ -89,6 +89,10 @@ typedef struct {
   int32_t amg_tail;     /* 1: run the small AMG levels (each <= 600k stored entries) of every
                            V-cycle as one thread-block-cluster launch (bitwise the same result;
                            default 0: measured no faster than the per-level launches) */
+  int32_t coarse_fp32;  /* 1: the coarsest AMG level's Chebyshev solve (<= 2,048 rows, one
+                           thread block) is staged and computed in FP32, also in the FP64 form:
+                           in FP64 it is bound by one SM's FP64 rate.  It is part of the
+                           preconditioner only; residuals and updates stay FP64 */
   int32_t graphs;       /* 1: run each step's outer loop as one CUDA graph with conditional
                            WHILE nodes (no host round trip per iteration); ignored while
                            kernel_timing = 1, which needs per-launch events */

@@ -444,19 +444,22 @@ __device__ __forceinline__ void resid_level_body(const CsrView<MT> &A, const VT 
   for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
     const int64_t i = wb + group_in_warp<W>(grp);
     const bool active = i < A.n;
+    VT pre = VT(0);  // lane 0: r_i, 1: A_ii, 2: z_i (fetched before the row's sum)
+    if (active && sub < 3) pre = sub == 0 ? r[i] : sub == 1 ? (VT)A.diag[i] : z[i];
     VT s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub) : VT(0);
     s = row_reduce<W>(s);
-    if (active && sub == 0) res[i] = r[i] - fmadd((VT)A.diag[i], z[i], s);
+    const VT ri = group_bcast<W>(pre, 0), dg = group_bcast<W>(pre, 1), zi = group_bcast<W>(pre, 2);
+    if (active && sub == 0) res[i] = ri - fmadd(dg, zi, s);
   }
 }
 // one body, two names: finest level vs coarse levels in profiles
 template <int W, int U, typename MT, typename VT>
-__global__ void resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
+__global__ void __launch_bounds__(kBlock, kFineMinBlocks) resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
                                    const Scalars *sc, int *wflag) {
   resid_level_body<W, U, MT, VT>(A, r, z, res, sc, wflag);
 }
 template <int W, int U, typename MT, typename VT>
-__global__ void fine_resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
+__global__ void __launch_bounds__(kBlock, kFineMinBlocks) fine_resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
                                         const Scalars *sc, int *wflag) {
   resid_level_body<W, U, MT, VT>(A, r, z, res, sc, wflag);
 }
@@ -495,15 +498,17 @@ __host__ inline size_t coarse_smem_bytes(int64_t n, int64_t nnz, size_t mt, size
 constexpr size_t kCoarseSmemMax = 200 * 1024;
 
 // Body of the coarsest-level solve for one block (blockDim.x threads, the
-// shared-memory buffer of coarse_smem_bytes); also run by one block of the
-// cluster-resident V-cycle tail.
-template <typename MT, typename VT>
-__device__ void coarse_cheb_body(const CsrView<MT> &A, const VT *r_g, VT *z_g, const ChebCoef *cf,
+// shared-memory buffer of coarse_smem_bytes(n, nnz, sizeof(VT), sizeof(VT)));
+// also run by one block of the cluster-resident V-cycle tail.  MT / GT: type
+// of the level's operator / vectors in global memory; VT: the type the solve
+// is staged and computed in (the operator is converted when it is staged).
+template <typename MT, typename VT, typename GT = VT>
+__device__ void coarse_cheb_body(const CsrView<MT> &A, const GT *r_g, GT *z_g, const ChebCoef *cf,
                                  int degree, unsigned char *smem_raw) {
   const int n = (int)A.n, nnz = (int)A.nnz;
-  // layout: values, diag, invdiag (MT) | r, z0, z1, d (VT) | cols, ptr (int32)
-  MT *val = reinterpret_cast<MT *>(smem_raw);
-  MT *dg = val + nnz, *idg = dg + n;
+  // layout: values, diag, invdiag | r, z0, z1, d (all VT) | cols, ptr (int32)
+  VT *val = reinterpret_cast<VT *>(smem_raw);
+  VT *dg = val + nnz, *idg = dg + n;
   VT *r = reinterpret_cast<VT *>(idg + n);
   VT *zb0 = r + n, *zb1 = zb0 + n, *d = zb1 + n;
   int *col = reinterpret_cast<int *>(d + n);
@@ -511,14 +516,14 @@ __device__ void coarse_cheb_body(const CsrView<MT> &A, const VT *r_g, VT *z_g, c
   const int64_t base = A.ptr[0];
   const double inv_theta = cf->inv_theta;
   for (int k = threadIdx.x; k < nnz; k += blockDim.x) {
-    val[k] = A.val[base + k];
+    val[k] = (VT)A.val[base + k];
     col[k] = A.col[base + k];
   }
   for (int i = threadIdx.x; i <= n; i += blockDim.x) ptr[i] = (int)(A.ptr[i] - base);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    dg[i] = A.diag[i];
-    idg[i] = A.invdiag[i];
-    VT ri = r_g[i];
+    dg[i] = (VT)A.diag[i];
+    idg[i] = (VT)A.invdiag[i];
+    VT ri = (VT)r_g[i];
     r[i] = ri;
     VT di = (VT)(inv_theta * (double)A.invdiag[i] * (double)ri);
     d[i] = di;
@@ -541,16 +546,16 @@ __device__ void coarse_cheb_body(const CsrView<MT> &A, const VT *r_g, VT *z_g, c
     zin = zout;
     zout = t;
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) z_g[i] = zin[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) z_g[i] = (GT)zin[i];
 }
 
-template <typename MT, typename VT>
-__global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const VT *r_g, VT *z_g,
+template <typename MT, typename VT, typename GT>
+__global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const GT *r_g, GT *z_g,
                                                            const ChebCoef *cf, int degree,
                                                            const Scalars *sc) {
   if (sc && sc->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  coarse_cheb_body<MT, VT>(A, r_g, z_g, cf, degree, smem_raw);
+  coarse_cheb_body<MT, VT, GT>(A, r_g, z_g, cf, degree, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -579,6 +584,7 @@ template <typename T>
 struct TailParams {
   int nlev;        // levels in the tail; the last one is the coarsest
   int coarse_smem; // 1: the coarsest solve runs in block 0 from shared memory
+  int coarse_fp32; // 1: that solve is staged and computed in FP32
   TailLevel<T> L[kMaxLevels];
 };
 
@@ -694,7 +700,12 @@ __global__ void __launch_bounds__(1024, 1) vcycle_tail_kernel(const __grid_const
   {
     const TailLevel<T> &L = P.L[last];
     if (P.coarse_smem) {
-      if (cb == 0) coarse_cheb_body<T, T>(L.A, L.r, L.z, L.cf, L.deg, smem_raw);
+      if (cb == 0) {
+        if (P.coarse_fp32)
+          coarse_cheb_body<T, float, T>(L.A, L.r, L.z, L.cf, L.deg, smem_raw);
+        else
+          coarse_cheb_body<T, T, T>(L.A, L.r, L.z, L.cf, L.deg, smem_raw);
+      }
       cl.sync();
     } else {
       cheb_zero(L, L.deg);
@@ -941,6 +952,13 @@ static sph_rt_status build_structure(sph_rt *s) {
 }
 
 // numeric set-up of every level from the current fine operator
+// Bytes per value the coarsest-level solve is staged and computed in: FP32
+// when config.coarse_fp32 (also in the FP64 form), else the level's type.
+template <typename T>
+static size_t coarse_solve_bytes(const sph_rt *s) {
+  return s->cfg.coarse_fp32 ? sizeof(float) : sizeof(T);
+}
+
 // Chebyshev degree of the coarsest-level solve
 static int coarse_degree(const sph_rt *s, const SphLevel *L) {
   return L->n <= kCoarseTarget * 4 ? 12 : 3 * s->cfg.cheb_degree;
@@ -961,6 +979,12 @@ static sph_rt_status numeric(sph_rt *s) {
   if (!dg) return SPH_RT_ENOMEM;
   for (size_t l = 0; l < s->levels.size(); ++l) {
     SphLevel *L = s->levels[l];
+    if (l == 0) {
+      // the finest level's bound was reduced by the assembly of this step
+      SPH_CUDA(s, cudaMemcpyAsync(dg, s->gersh, sizeof(double), cudaMemcpyDeviceToDevice,
+                                  s->stream));
+      continue;
+    }
     gersh_kernel<<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(L->n, L->ptr, L->val, L->diag,
                                                                   s->partials, &s->sc->counter,
                                                                   dg + l);
@@ -1092,8 +1116,10 @@ static sph_rt_status launch_tail(sph_rt *s, size_t l0, const T *r, T *z, const S
     t.deg = m + 1 == P.nlev ? coarse_degree(s, L) : s->cfg.cheb_degree;
   }
   SphLevel *Lc = s->levels.back();
-  const size_t smem = coarse_smem_bytes(Lc->n, Lc->nnz, sizeof(T), sizeof(T));
+  const size_t cs = coarse_solve_bytes<T>(s);
+  const size_t smem = coarse_smem_bytes(Lc->n, Lc->nnz, cs, cs);
   P.coarse_smem = 1;  // tail_setup only enables the tail when the coarsest level fits
+  P.coarse_fp32 = cs == sizeof(float) && sizeof(T) == sizeof(double);
   cudaLaunchConfig_t lc;
   memset(&lc, 0, sizeof lc);
   lc.gridDim = dim3((unsigned)s->tail_cluster);
@@ -1124,7 +1150,8 @@ static void tail_setup(sph_rt *s) {
   while (l0 > 1 && s->levels[l0 - 1]->nnz <= kTailMaxNnz) --l0;
   if (nl - l0 < 2) return;
   SphLevel *Lc = s->levels.back();
-  const size_t smem = coarse_smem_bytes(Lc->n, Lc->nnz, sizeof(T), sizeof(T));
+  const size_t cs = coarse_solve_bytes<T>(s);
+  const size_t smem = coarse_smem_bytes(Lc->n, Lc->nnz, cs, cs);
   if (smem > kCoarseSmemMax) return;
   auto kern = vcycle_tail_kernel<T>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1169,17 +1196,27 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
     // coarsest level: Chebyshev solve over the whole Gershgorin interval
     const int cdeg = coarse_degree(s, L);
     const ChebCoef *cf = s->cheb_slots + 1 + l;
-    const size_t smem = coarse_smem_bytes(L->n, L->nnz, sizeof(T), sizeof(T));
+    const size_t cs = coarse_solve_bytes<T>(s);
+    const size_t smem = coarse_smem_bytes(L->n, L->nnz, cs, cs);
     if (l > 0 && smem <= kCoarseSmemMax) {
-      // opt in to more than 48 KiB of dynamic shared memory (once per handle and type)
-      const int bit = sizeof(T) == 8 ? 1 : 2;
+      // opt in to more than 48 KiB of dynamic shared memory (once per handle and variant)
+      const bool f32 = cs == sizeof(float) && sizeof(T) == sizeof(double);
+      const int bit = f32 ? 4 : (sizeof(T) == 8 ? 1 : 2);
       if (!(s->coarse_smem_optin & bit)) {
-        SPH_CUDA(s, cudaFuncSetAttribute(coarse_cheb_kernel<T, T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kCoarseSmemMax));
+        if (f32)
+          SPH_CUDA(s, cudaFuncSetAttribute(coarse_cheb_kernel<T, float, T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kCoarseSmemMax));
+        else
+          SPH_CUDA(s, cudaFuncSetAttribute(coarse_cheb_kernel<T, T, T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kCoarseSmemMax));
         s->coarse_smem_optin |= bit;
       }
-      coarse_cheb_kernel<T, T><<<1, 1024, smem, s->stream>>>(A, r, z, cf, cdeg, sc);
+      if (f32)
+        coarse_cheb_kernel<T, float, T><<<1, 1024, smem, s->stream>>>(A, r, z, cf, cdeg, sc);
+      else
+        coarse_cheb_kernel<T, T, T><<<1, 1024, smem, s->stream>>>(A, r, z, cf, cdeg, sc);
       SPH_LAUNCHED(s);
       return SPH_RT_OK;
     }
@@ -1187,7 +1224,7 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
   }
   const ChebCoef *cf = s->cheb_slots + 1 + l;
   if ((rc = cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, true, sc))) return rc;
-  const int gw = gcap(s, L->n, kBlock / A.W);
+  const int gw = row_grid(s->num_sms, L->n, A.W);
   T *res = LV::res(L);
   // fine-level residual sweeps are timed with the other fine SpMV-class kernels;
   // per row: rowptr, diag, r, z, res

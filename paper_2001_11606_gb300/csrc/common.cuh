@@ -29,6 +29,11 @@ namespace sphrt {
 constexpr int kBlock = 256;          // threads per block of the 1-D kernels
 constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kMaxRedBlocks = 2048;  // upper bound on blocks of a reducing kernel
+// resident blocks per SM the SpMV-class sweeps are compiled for (register cap)
+#ifndef SPH_FINE_MIN_BLOCKS
+#define SPH_FINE_MIN_BLOCKS 6
+#endif
+constexpr int kFineMinBlocks = SPH_FINE_MIN_BLOCKS;
 
 // --------------------------------------------------------------------------
 // Scalars of one Krylov solve and of the outer loop, kept on the device so
@@ -197,6 +202,16 @@ __device__ __forceinline__ int64_t warp_first_group(int64_t grp) {
   return grp - group_in_warp<W>(grp);
 }
 
+// Row-epilogue operands fetched early: before a row's sum, lane k of the row
+// group loads the k-th per-row operand (diagonal, vector entries), so those
+// loads are in flight together with the row's gathers instead of being
+// issued after the reduction; group_bcast hands them to lane 0 afterwards.
+// Every lane of the warp must call it (full-mask shuffle).
+template <int W, typename T>
+__device__ __forceinline__ T group_bcast(T v, int src) {
+  return __shfl_sync(0xffffffffu, v, src, W);
+}
+
 // Sum over the W lanes of a row group (W divides 32; groups are aligned).
 template <int W, typename T>
 __device__ __forceinline__ T row_reduce(T v) {
@@ -266,6 +281,15 @@ __host__ inline RowShape shape_for_mean(double mean) {
   int W = lanes_for_mean(mean);
   int U = (mean / W) <= 6 ? 4 : 8;
   return {W, U};
+}
+
+// Grid of a row-group sweep (W lanes per row, kBlock threads per block): one
+// wave of kFineMinBlocks resident blocks per SM at most (the sweeps are
+// compiled with that register cap), striding over the rows.
+__host__ inline int row_grid(int num_sms, int64_t n, int W) {
+  int64_t g = ceil_div(n > 0 ? n : 1, kBlock / W);
+  int64_t cap = (int64_t)num_sms * kFineMinBlocks;
+  return (int)(g < cap ? g : cap);
 }
 
 // Launch CALL with constexpr W and U set to the supported row-group shape:

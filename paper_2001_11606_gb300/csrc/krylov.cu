@@ -36,7 +36,7 @@ __device__ __forceinline__ T ld(const T *p) {
 // r = b - B x;  rnorm2 = ||r / V||^2;  done = rnorm2 <= thresh2.
 // ---------------------------------------------------------------------------
 template <int W, int U>
-__global__ void resid_kernel(CsrView<double> A, const double *b, const double *x, double *r,
+__global__ void __launch_bounds__(kBlock, kFineMinBlocks) resid_kernel(CsrView<double> A, const double *b, const double *x, double *r,
                              const double *invV, Scalars *sc, double *partials, int *wflag) {
   mark_work(wflag, 1);
   const int sub = threadIdx.x % W;
@@ -46,12 +46,16 @@ __global__ void resid_kernel(CsrView<double> A, const double *b, const double *x
   for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
     const int64_t i = wb + group_in_warp<W>(grp);
     const bool active = i < A.n;
+    double pre = 0.0;  // lane 0: b_i, 1: B_ii, 2: x_i, 3: 1/V_i
+    if (active && sub < 4) pre = sub == 0 ? b[i] : sub == 1 ? A.diag[i] : sub == 2 ? x[i] : invV[i];
     double s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, x, sub) : 0.0;
     s = row_reduce<W>(s);
+    const double bi = group_bcast<W>(pre, 0), dg = group_bcast<W>(pre, 1);
+    const double xi = group_bcast<W>(pre, 2), iv = group_bcast<W>(pre, 3);
     if (active && sub == 0) {
-      double ri = b[i] - fmadd(A.diag[i], x[i], s);
+      double ri = bi - fmadd(dg, xi, s);
       r[i] = ri;
-      double ru = ri * invV[i];
+      double ru = ri * iv;
       acc += ru * ru;
     }
   }
@@ -72,7 +76,7 @@ __global__ void resid_kernel(CsrView<double> A, const double *b, const double *x
 // (q = B p without a second SpMV: B p = B z + beta B p_old.)
 // ---------------------------------------------------------------------------
 template <int W, int U>
-__global__ void spmv_pq_kernel(CsrView<double> A, const double *z, double *q, double *p, int first,
+__global__ void __launch_bounds__(kBlock, kFineMinBlocks) spmv_pq_kernel(CsrView<double> A, const double *z, double *q, double *p, int first,
                                Scalars *sc, double *partials, int *wflag) {
   if (sc->done) {
     mark_work(wflag, 0);
@@ -87,13 +91,17 @@ __global__ void spmv_pq_kernel(CsrView<double> A, const double *z, double *q, do
   for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
     const int64_t i = wb + group_in_warp<W>(grp);
     const bool active = i < A.n;
+    double pre = 0.0;  // lane 0: z_i, 1: B_ii, 2: q_i, 3: p_i
+    if (active && sub < 4 && (sub < 2 || !first))
+      pre = sub == 0 ? z[i] : sub == 1 ? A.diag[i] : sub == 2 ? q[i] : p[i];
     double s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub) : 0.0;
     s = row_reduce<W>(s);
+    const double zi = group_bcast<W>(pre, 0), dg = group_bcast<W>(pre, 1);
+    const double qo = group_bcast<W>(pre, 2), po = group_bcast<W>(pre, 3);
     if (active && sub == 0) {
-      double zi = z[i];
-      double wi = A.diag[i] * zi + s;
-      double qi = first ? wi : wi + beta * q[i];
-      double pi = first ? zi : zi + beta * p[i];
+      double wi = fmadd(dg, zi, s);
+      double qi = first ? wi : fmadd(beta, qo, wi);
+      double pi = first ? zi : fmadd(beta, po, zi);
       q[i] = qi;
       p[i] = pi;
       acc += pi * qi;
@@ -246,13 +254,20 @@ __device__ __forceinline__ void cheb_step_body(const CsrView<MT> &A, const VT *r
   for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
     const int64_t i = wb + group_in_warp<W>(grp);
     const bool active = i < A.n;
+    // lane 0: r_i and 1/B_ii, 1: z_i, 2: d_i (not on the first step), 3: B_ii
+    VT pre = VT(0), pre2 = VT(0);
+    if (active && sub < 4 && (sub != 2 || k > 0)) {
+      pre = sub == 0 ? r[i] : sub == 1 ? z_in[i] : sub == 2 ? d[i] : (VT)A.diag[i];
+      if (sub == 0) pre2 = (VT)A.invdiag[i];
+    }
     VT s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z_in, sub) : VT(0);
     s = row_reduce<W>(s);
+    const VT ri = group_bcast<W>(pre, 0), zi = group_bcast<W>(pre, 1);
+    const VT dold = group_bcast<W>(pre, 2), dg = group_bcast<W>(pre, 3);
     if (active && sub == 0) {
-      VT zi = z_in[i];
-      VT res = r[i] - fmadd((VT)A.diag[i], zi, s);
-      VT di = (vc2 * (VT)A.invdiag[i]) * res;
-      if (k > 0) di = fmadd(vc1, d[i], di);  // the first step must not read d
+      VT res = ri - fmadd(dg, zi, s);
+      VT di = (vc2 * pre2) * res;
+      if (k > 0) di = fmadd(vc1, dold, di);  // the first step must not read d
       d[i] = di;
       z_out[i] = zi + di;
     }
@@ -261,12 +276,12 @@ __device__ __forceinline__ void cheb_step_body(const CsrView<MT> &A, const VT *r
 // The same sweep under two names, so that profiles separate the finest
 // level (HBM-streamed operator) from the coarse levels (L2-resident).
 template <int W, int U, typename MT, typename VT>
-__global__ void cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
+__global__ void __launch_bounds__(kBlock, kFineMinBlocks) cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
                                  const ChebCoef *cf, int k, const Scalars *sc, int *wflag) {
   cheb_step_body<W, U, MT, VT>(A, r, z_in, z_out, d, cf, k, sc, wflag);
 }
 template <int W, int U, typename MT, typename VT>
-__global__ void fine_cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out,
+__global__ void __launch_bounds__(kBlock, kFineMinBlocks) fine_cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out,
                                       VT *d, const ChebCoef *cf, int k, const Scalars *sc,
                                       int *wflag) {
   cheb_step_body<W, U, MT, VT>(A, r, z_in, z_out, d, cf, k, sc, wflag);
@@ -368,7 +383,7 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
   if (degree < 1) degree = 1;
   if (degree > kChebMaxDeg) degree = kChebMaxDeg;
   int g = grid_cap(s, A.n, kBlock);
-  int gw = grid_cap(s, A.n, kBlock / A.W);
+  int gw = row_grid(s->num_sms, A.n, A.W);
   // fine-level sweeps are timed with the other fine SpMV-class kernels; per row:
   // rowptr, diag, 1/diag, r, z_in, z_out, d r/w (vectors of type VT)
   const bool fine = A.ptr == s->mat_ptr;
@@ -519,7 +534,7 @@ sph_rt_status autotune_fine_shape(sph_rt *s) {
 // First part of a solve: r = b - B x, z = M^{-1} r, q = B p with p = z.
 sph_rt_status pcg_prologue(sph_rt *s) {
   CsrView<double> A = fine_view(s);
-  const int gw = grid_cap(s, A.n, kBlock / A.W);
+  const int gw = row_grid(s->num_sms, A.n, A.W);
   sph_rt_status rc;
   int *wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
@@ -550,7 +565,7 @@ __global__ void copy_vec_kernel(int64_t n, const double *src, double *dst, const
 // previous z in z_old.  All launches are empty once `done` is set.
 sph_rt_status pcg_iteration(sph_rt *s) {
   CsrView<double> A = fine_view(s);
-  const int gw = grid_cap(s, A.n, kBlock / A.W);
+  const int gw = row_grid(s->num_sms, A.n, A.W);
   const int g = grid_cap(s, A.n, kBlock);
   sph_rt_status rc;
   update_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,

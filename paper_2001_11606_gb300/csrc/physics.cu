@@ -21,6 +21,7 @@ namespace sphrt {
 
 struct Phys {
   double a, c, cv, p, T_floor, larsen_k, dt;
+  double inv_cv, inv_dt;  // 1/cv, 1/dt (the Newton loop multiplies instead of dividing)
   double tol_inner;
   int limiter, max_inner;
 };
@@ -301,17 +302,22 @@ __global__ void newton_kernel(Phys ph, int64_t n_int, const double *rho, const d
        i += (int64_t)gridDim.x * blockDim.x) {
     double cs = ph.c * sigma[i];
     double P = cs * E_new[i] + Qe[i];
-    double rdt = rho[i] / ph.dt;
+    // per-particle constants of u(e) = rho/dt (e - e_old) + c sigma a T^4 - P and
+    // J = rho/dt + 4 c sigma a T^3 / cv, hoisted out of the loop: one FP64
+    // division (u / J) per iteration is left, on a part whose FP64 pipe is narrow
+    double rdt = rho[i] * ph.inv_dt;
+    double csa = cs * ph.a;
+    double k4 = 4.0 * csa * ph.inv_cv;
     double eo = e_old[i];
     double e0 = e_start[i];
     double ei = e0;
     int it = 0;
     bool ok = false;
     while (it < ph.max_inner) {
-      double T = ei / ph.cv;
+      double T = ei * ph.inv_cv;
       double T3 = T * T * T;
-      double u = rdt * (ei - eo) + cs * ph.a * T3 * T - P;
-      double J = rdt + 4.0 * cs * ph.a * T3 / ph.cv;
+      double u = rdt * (ei - eo) + csa * T3 * T - P;
+      double J = rdt + k4 * T3;
       double de = u / J;
       ei = ei - de;
       ++it;
@@ -493,6 +499,8 @@ Phys make_phys(const sph_rt *s, double dt) {
   ph.a = s->cfg.a;
   ph.c = s->cfg.c;
   ph.cv = s->cfg.cv;
+  ph.inv_cv = 1.0 / s->cfg.cv;
+  ph.inv_dt = 1.0 / dt;
   ph.p = s->cfg.opacity_exp;
   ph.T_floor = s->cfg.T_floor;
   ph.larsen_k = s->cfg.larsen_k;

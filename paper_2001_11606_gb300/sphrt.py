@@ -47,6 +47,7 @@ class Config(C.Structure):
         ("kernel_timing", C.c_int32),
         ("autotune", C.c_int32),
         ("amg_tail", C.c_int32),
+        ("coarse_fp32", C.c_int32),
         ("graphs", C.c_int32),
         ("device", C.c_int32),
         ("stream", C.c_void_p),

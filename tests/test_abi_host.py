@@ -52,7 +52,7 @@ def test_config_struct_matches_defaults():
                                          ("tol_krylov", -1.0), ("max_outer", 0),
                                          ("precond", 9), ("cheb_degree", 0),
                                          ("amg_theta", 1.5), ("graphs", 2),
-                                         ("amg_tail", -1)])
+                                         ("amg_tail", -1), ("coarse_fp32", 2)])
 def test_create_rejects_bad_config(field, value):
     cfg = sphrt.default_config(**{field: value})
     with pytest.raises(sphrt.SphRtError) as ei:
