@@ -216,8 +216,11 @@ sph_rt_status sph_rt_kernel_stats(sph_rt *s, int64_t *launches, double *total_ms
 /* The same counters split by kernel: SPH_RT_KERNEL_SPMV_PQ (the CG product
  * fused with the p, q updates and (p, q)), SPH_RT_KERNEL_RESID (residual
  * sweeps: CG start and V-cycle fine level), SPH_RT_KERNEL_CHEB (fine-level
- * Chebyshev smoother / preconditioner sweeps).  Cleared with the totals. */
-enum { SPH_RT_KERNEL_SPMV_PQ = 0, SPH_RT_KERNEL_RESID = 1, SPH_RT_KERNEL_CHEB = 2 };
+ * Chebyshev smoother / preconditioner sweeps), SPH_RT_KERNEL_POST (the first
+ * fine-level post-smoothing step, a sweep of A P with the prolongation folded
+ * in).  Cleared with the totals. */
+enum { SPH_RT_KERNEL_SPMV_PQ = 0, SPH_RT_KERNEL_RESID = 1, SPH_RT_KERNEL_CHEB = 2,
+       SPH_RT_KERNEL_POST = 3 };
 sph_rt_status sph_rt_kernel_stats_kind(sph_rt *s, int32_t kind, int64_t *launches,
                                        double *total_ms, double *bytes);
 

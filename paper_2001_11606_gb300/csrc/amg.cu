@@ -39,7 +39,8 @@ namespace sphrt {
 sph_rt_status exclusive_scan(sph_rt *s, const int64_t *in, int64_t n, int64_t *out);
 template <typename MT, typename VT>
 sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT *d, VT *tmp,
-                         int degree, const ChebCoef *cf, bool zero_guess, const Scalars *sc);
+                         int degree, const ChebCoef *cf, bool zero_guess, const Scalars *sc,
+                         bool first_step_done = false);
 sph_rt_status launch_cheb_slots(sph_rt *s, int first, const double *gersh_dev,
                                 const std::vector<int> &mode, const std::vector<int> &degree);
 
@@ -68,6 +69,16 @@ struct SphLevel {
   double *r = nullptr, *z = nullptr, *res = nullptr, *d = nullptr, *t = nullptr;
   float *r32 = nullptr, *z32 = nullptr, *res32 = nullptr, *d32 = nullptr, *t32 = nullptr;
   int W = 32, U = 4;
+  // finest level only: A P (P = this level's aggregation), by fine row
+  int64_t nnz_ap = 0;
+  int64_t *ap_ptr = nullptr;    // [n + 1]
+  int32_t *ap_col = nullptr;    // [nnz_ap] aggregate (next-level row)
+  int64_t *ap_seg_ptr = nullptr;  // [nnz_ap + 1] sources of each A P entry
+  int32_t *ap_seg_src = nullptr;  // source: k < nnz (off-diagonal entry) or nnz + i (diagonal)
+  int64_t *apg_ptr = nullptr;     // [nnz_c + nc + 1] next level's Galerkin sums over A P entries
+  int32_t *apg_src = nullptr;     // (P^T (A P): each A P entry (i, K) adds to (agg[i], K))
+  double *ap_val = nullptr;     // [nnz_ap]
+  float *ap_val32 = nullptr;
   std::vector<void *> owned;
 };
 
@@ -559,6 +570,137 @@ __global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const 
 }
 
 // ---------------------------------------------------------------------------
+// A P of the finest level.  After the coarse correction e_c, the first
+// post-smoothing step needs r - A (z_pre + P e_c) = res - (A P) e_c, where
+// res = r - A z_pre is the residual already formed before the restriction.
+// A P has one entry per (fine row, distinct aggregate among the row's own
+// and its columns' aggregates) -- about a sixth of A's entries -- so that
+// step reads A P instead of A (and absorbs the prolongation).  Its entries
+// are kept in first-occurrence order along the row (own aggregate first).
+// ---------------------------------------------------------------------------
+// structure, pass 1 (per fine row, one thread): distinct aggregates written
+// uncompacted at tmp[ptr[i] + i ..], relative positions in ap_map / ap_dmap
+__global__ void ap_structure_kernel(int64_t n, const int64_t *ptr, const int32_t *col,
+                                    const int32_t *agg, int32_t *tmp, int64_t *cnt,
+                                    int32_t *ap_map, int32_t *ap_dmap) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t *keys = tmp + ptr[i] + i;
+    int32_t m = 0;
+    const int32_t a0 = agg[i];
+    if (a0 >= 0) keys[m++] = a0;
+    ap_dmap[i] = a0 >= 0 ? 0 : -1;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+      const int32_t K = agg[col[k]];
+      int32_t pos = -1;
+      if (K >= 0) {
+        for (int32_t q = 0; q < m; ++q)
+          if (keys[q] == K) {
+            pos = q;
+            break;
+          }
+        if (pos < 0) {
+          pos = m;
+          keys[m++] = K;
+        }
+      }
+      ap_map[k] = pos;
+    }
+    cnt[i] = m;
+  }
+}
+// pass 2: compact the keys and make the positions absolute
+__global__ void ap_compact_kernel(int64_t n, const int64_t *ptr, const int32_t *tmp,
+                                  const int64_t *ap_ptr, int32_t *ap_col, int32_t *ap_map,
+                                  int32_t *ap_dmap) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = ap_ptr[i];
+    const int32_t *keys = tmp + ptr[i] + i;
+    for (int64_t q = 0; q < ap_ptr[i + 1] - b; ++q) ap_col[b + q] = keys[q];
+    if (ap_dmap[i] >= 0) ap_dmap[i] = (int32_t)b + ap_dmap[i];
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k)
+      if (ap_map[k] >= 0) ap_map[k] = (int32_t)b + ap_map[k];
+  }
+}
+// The values (every step) are fixed-order sums of each entry's sources, the
+// same gather-sum as the Galerkin product (galerkin_kernel).  The next
+// level's operator P^T A P = P^T (A P) is then summed from the A P entries
+// (about a sixth as many sources as A's entries): entry (i, K) of A P adds to
+// coarse entry (agg[i], K), the diagonal when K = agg[i].
+__global__ void ap_galerkin_target_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col,
+                                          const int32_t *agg, int64_t nnz_c, const int64_t *cptr,
+                                          const int32_t *ccol, int32_t *tgt, int *missing) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t I = agg[i];
+    for (int64_t q = ap_ptr[i]; q < ap_ptr[i + 1]; ++q) {
+      const int32_t K = ap_col[q];
+      int64_t t = -1;
+      if (I >= 0) {
+        if (K == I) {
+          t = nnz_c + I;
+        } else {  // binary search in the sorted coarse row I
+          int64_t lo = cptr[I], hi = cptr[I + 1];
+          while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (ccol[mid] < K) lo = mid + 1; else hi = mid;
+          }
+          if (lo < cptr[I + 1] && ccol[lo] == K) t = lo;
+          else *missing = 1;
+        }
+      }
+      tgt[q] = (int32_t)t;
+    }
+  }
+}
+
+// First post-smoothing step on the finest level with the prolongation folded
+// in: z = z_pre + P e_c, res2 = res - (A P) e_c (= r - A z), d = c2 D^{-1} res2
+// (step 0 from a nonzero guess), z_out = z + d.  z_out may be z_pre.
+template <int W, int U, typename MT, typename VT>
+__global__ void __launch_bounds__(kBlock, kFineMinBlocks)
+    fine_post_ap_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col,
+                        const MT *ap_val, const int32_t *agg, const VT *ec, const VT *z_pre,
+                        const VT *res, const MT *invdiag, const ChebCoef *cf, VT *d, VT *z_out,
+                        const Scalars *sc, int *wflag) {
+  if (sc && sc->done) {
+    mark_work(wflag, 0);
+    return;
+  }
+  mark_work(wflag, 1);
+  const int sub = threadIdx.x % W;
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  const VT c2 = (VT)cf->inv_theta;
+  for (int64_t wb = warp_first_group<W>(grp); wb < n; wb += ngrp) {
+    const int64_t i = wb + group_in_warp<W>(grp);
+    const bool active = i < n;
+    // lane 0: z_pre_i, 1: res_i, 2: 1/A_ii, 3: (P e_c)_i
+    VT pre = VT(0);
+    if (active && sub < 4) {
+      if (sub == 0) pre = z_pre[i];
+      else if (sub == 1) pre = res[i];
+      else if (sub == 2) pre = (VT)invdiag[i];
+      else {
+        const int32_t a = agg[i];
+        pre = a >= 0 ? ec[a] : VT(0);
+      }
+    }
+    VT s = active ? row_dot<W, U>(ap_ptr[i], ap_ptr[i + 1], ap_col, ap_val, ec, sub) : VT(0);
+    s = row_reduce<W>(s);
+    const VT zp = group_bcast<W>(pre, 0), rs = group_bcast<W>(pre, 1);
+    const VT idg = group_bcast<W>(pre, 2), pe = group_bcast<W>(pre, 3);
+    if (active && sub == 0) {
+      const VT zi = zp + pe;
+      const VT di = (c2 * idg) * (rs - s);
+      d[i] = di;
+      z_out[i] = zi + di;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Cluster-resident V-cycle tail: the levels from `tail_level` down (small
 // operators that live in L2) run as ONE launch of one thread-block cluster.
 // Phases that depend on other rows are separated by cluster barriers instead
@@ -914,6 +1056,63 @@ static sph_rt_status level_vectors_fine(sph_rt *s, SphLevel *L) {
   return SPH_RT_OK;
 }
 
+// structure of A P on the finest level (see ap_structure_kernel)
+static sph_rt_status build_ap(sph_rt *s) {
+  SphLevel *L = s->levels[0];
+  const int64_t n = L->n;
+  int32_t *tmp = scratch<int32_t>(s, (size_t)(L->nnz + n));
+  int64_t *cnt = scratch<int64_t>(s, (size_t)n + 1);
+  // target A P entry of each source: off-diagonal entries, then the diagonals
+  int32_t *map = scratch<int32_t>(s, (size_t)(L->nnz + n));
+  L->ap_ptr = lalloc<int64_t>(s, L, n + 1);
+  if (!tmp || !cnt || !map || !L->ap_ptr) return SPH_RT_ENOMEM;
+  int32_t *dmap = map + L->nnz;
+  ap_structure_kernel<<<gcap(s, n, kBlock), kBlock, 0, s->stream>>>(n, L->ptr, L->col, L->agg,
+                                                                    tmp, cnt, map, dmap);
+  SPH_LAUNCHED(s);
+  sph_rt_status rc = exclusive_scan(s, cnt, n, L->ap_ptr);
+  if (rc) return rc;
+  int64_t total = 0;
+  SPH_CUDA(s, cudaMemcpyAsync(&total, L->ap_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                              s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (total >= ((int64_t)1 << 31)) return set_error(s, SPH_RT_EINVAL, "A P too large");
+  L->nnz_ap = total;
+  L->ap_col = lalloc<int32_t>(s, L, (size_t)total);
+  L->ap_val = lalloc<double>(s, L, (size_t)total);
+  if (!L->ap_col || !L->ap_val) return SPH_RT_ENOMEM;
+  if (s->cfg.precision == SPH_RT_MIXED && !(L->ap_val32 = lalloc<float>(s, L, (size_t)total)))
+    return SPH_RT_ENOMEM;
+  ap_compact_kernel<<<gcap(s, n, kBlock), kBlock, 0, s->stream>>>(n, L->ptr, tmp, L->ap_ptr,
+                                                                  L->ap_col, map, dmap);
+  SPH_LAUNCHED(s);
+  // sources of each A P entry in increasing source order
+  if ((rc = bucket_sort(s, L, L->nnz + n, map, total, &L->ap_seg_ptr, &L->ap_seg_src, nullptr)))
+    return rc;
+  // next level's Galerkin sources: the A P entries of its members' rows
+  SphLevel *C = s->levels[1];
+  int32_t *tgt = scratch<int32_t>(s, (size_t)total);
+  int *missing = scratch<int>(s, 1);
+  if (!tgt || !missing) return SPH_RT_ENOMEM;
+  SPH_CUDA(s, cudaMemsetAsync(missing, 0, sizeof(int), s->stream));
+  ap_galerkin_target_kernel<<<gcap(s, n, kBlock), kBlock, 0, s->stream>>>(
+      n, L->ap_ptr, L->ap_col, L->agg, C->nnz, C->ptr, C->col, tgt, missing);
+  SPH_LAUNCHED(s);
+  if ((rc = bucket_sort(s, L, total, tgt, C->nnz + C->n, &L->apg_ptr, &L->apg_src, nullptr)))
+    return rc;
+  int miss = 0;
+  SPH_CUDA(s, cudaMemcpyAsync(&miss, missing, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  dfree(s, tgt);
+  dfree(s, missing);
+  if (miss) return set_error(s, SPH_RT_EDEVICE, "A P entry outside the coarse sparsity");
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  dfree(s, tmp);
+  dfree(s, cnt);
+  dfree(s, map);
+  return SPH_RT_OK;
+}
+
 static sph_rt_status build_structure(sph_rt *s) {
   amg_release(s);
   SphLevel *L0 = new SphLevel();
@@ -947,6 +1146,7 @@ static sph_rt_status build_structure(sph_rt *s) {
     SPH_LAUNCHED(s);
     L = C;
   }
+  if (s->levels.size() >= 2 && (rc = build_ap(s))) return rc;
   s->amg_ready = true;
   return SPH_RT_OK;
 }
@@ -965,11 +1165,29 @@ static int coarse_degree(const sph_rt *s, const SphLevel *L) {
 }
 
 static sph_rt_status numeric(sph_rt *s) {
+  if (s->levels.size() >= 2 && s->levels[0]->ap_ptr) {
+    SphLevel *L = s->levels[0];
+    galerkin_kernel<<<gcap(s, L->nnz_ap, kBlock), kBlock, 0, s->stream>>>(
+        L->nnz_ap, 0, L->ap_seg_ptr, L->ap_seg_src, L->nnz, L->val, L->diag, L->ap_val, nullptr,
+        nullptr);
+    SPH_LAUNCHED(s);
+    if (L->ap_val32) {
+      convert_kernel<double, float><<<gcap(s, L->nnz_ap, kBlock), kBlock, 0, s->stream>>>(
+          L->nnz_ap, L->ap_val, L->ap_val32);
+      SPH_LAUNCHED(s);
+    }
+  }
   for (size_t l = 0; l + 1 < s->levels.size(); ++l) {
     SphLevel *L = s->levels[l], *C = s->levels[l + 1];
-    galerkin_kernel<<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
-        C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, L->val, L->diag, C->val, C->diag,
-        C->invdiag);
+    if (l == 0 && L->apg_ptr) {  // P^T (A P)
+      galerkin_kernel<<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
+          C->nnz, C->n, L->apg_ptr, L->apg_src, L->nnz_ap, L->ap_val, nullptr, C->val, C->diag,
+          C->invdiag);
+    } else {
+      galerkin_kernel<<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
+          C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, L->val, L->diag, C->val, C->diag,
+          C->invdiag);
+    }
     SPH_LAUNCHED(s);
   }
   // Gershgorin bounds of every level, turned into Chebyshev coefficients on
@@ -1067,6 +1285,7 @@ struct LevelVecs<double> {
   static double *res(SphLevel *L) { return L->res; }
   static double *d(SphLevel *L) { return L->d; }
   static double *t(SphLevel *L) { return L->t; }
+  static const double *ap(SphLevel *L) { return L->ap_val; }
 };
 template <>
 struct LevelVecs<float> {
@@ -1088,6 +1307,7 @@ struct LevelVecs<float> {
   static float *res(SphLevel *L) { return L->res32; }
   static float *d(SphLevel *L) { return L->d32; }
   static float *t(SphLevel *L) { return L->t32; }
+  static const float *ap(SphLevel *L) { return L->ap_val32; }
 };
 
 // Levels at or below this many stored entries (~7 MB in FP64) may run in the
@@ -1246,6 +1466,24 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
                                                                       res, LV::r(C), sc);
   SPH_LAUNCHED(s);
   if ((rc = vcycle<T>(s, l + 1, LV::r(C), LV::z(C), sc))) return rc;
+  if (l == 0 && L->ap_ptr && LV::ap(L)) {
+    // prolongation and the first post-smoothing step in one sweep of A P
+    T *bufs[2] = {z, LV::t(L)};
+    const int w0 = (deg - 1) % 2;
+    const int gp = row_grid(s->num_sms, L->n, 4);
+    int *wf = timing_begin(s);
+    fine_post_ap_kernel<4, 4, T, T><<<gp, kBlock, 0, s->stream>>>(
+        L->n, L->ap_ptr, L->ap_col, LV::ap(L), L->agg, LV::z(C), z, res, A.invdiag, cf,
+        LV::d(L), bufs[w0], sc, wf);
+    SPH_LAUNCHED(s);
+    // A P entry: column + value; per row: ap_ptr, agg, the coarse entry of P e_c,
+    // z_pre, res, 1/diag, d, z_out
+    timing_end(s,
+               (4.0 + sizeof(T)) * (double)L->nnz_ap +
+                   (12.0 + 6.0 * sizeof(T)) * (double)L->n,
+               kTimedPost);
+    return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, false, sc, true);
+  }
   prolong_kernel<T><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(L->n, L->agg, LV::z(C), z, sc);
   SPH_LAUNCHED(s);
   return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, false, sc);
@@ -1297,7 +1535,11 @@ void amg_signature(const sph_rt *s, std::vector<uint64_t> &sig) {
                           (uint64_t)(uintptr_t)L->z32,
                           (uint64_t)(uintptr_t)L->res32,
                           (uint64_t)(uintptr_t)L->d32,
-                          (uint64_t)(uintptr_t)L->t32};
+                          (uint64_t)(uintptr_t)L->t32,
+                          (uint64_t)(uintptr_t)L->ap_ptr,
+                          (uint64_t)(uintptr_t)L->ap_col,
+                          (uint64_t)(uintptr_t)L->ap_val,
+                          (uint64_t)(uintptr_t)L->ap_val32};
     sig.insert(sig.end(), v, v + sizeof v / sizeof v[0]);
   }
 }

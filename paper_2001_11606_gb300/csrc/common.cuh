@@ -445,8 +445,8 @@ struct sph_rt {
   int ev_used = 0;
   int64_t spmv_launches = 0;
   double spmv_ms = 0.0, spmv_bytes = 0.0;
-  int64_t kind_launches[3] = {0, 0, 0};  // per sphrt::TimedKind
-  double kind_ms[3] = {0, 0, 0}, kind_bytes[3] = {0, 0, 0};
+  int64_t kind_launches[4] = {0, 0, 0, 0};  // per sphrt::TimedKind
+  double kind_ms[4] = {0, 0, 0, 0}, kind_bytes[4] = {0, 0, 0, 0};
 };
 
 // Helpers shared by the translation units (defined in sph_rt.cu).
@@ -465,7 +465,8 @@ void dfree(sph_rt *s, void *p);  // back to the free list (stream-ordered users 
 // the kernel writes 1 there if it does work and 0 if it returns at once because
 // the solve has converged; only launches that worked are counted.
 // kinds of timed fine-operator launches (SPH_RT_KERNEL_* in sph_rt.h)
-enum TimedKind { kTimedSpmvPQ = 0, kTimedResid = 1, kTimedCheb = 2 };
+enum TimedKind { kTimedSpmvPQ = 0, kTimedResid = 1, kTimedCheb = 2, kTimedPost = 3 };
+constexpr int kTimedKinds = 4;
 int *timing_begin(sph_rt *s);
 void timing_end(sph_rt *s, double bytes, int kind);
 void timing_flush(sph_rt *s);

@@ -379,7 +379,8 @@ constexpr int kRowBytesResid = 48, kRowBytesSpmvPQ = 56;
 // read of the bounds is needed).  d and tmp are scratch vectors of length n.
 template <typename MT, typename VT>
 sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT *d, VT *tmp,
-                         int degree, const ChebCoef *cf, bool zero_guess, const Scalars *sc) {
+                         int degree, const ChebCoef *cf, bool zero_guess, const Scalars *sc,
+                         bool first_step_done) {
   if (degree < 1) degree = 1;
   if (degree > kChebMaxDeg) degree = kChebMaxDeg;
   int g = grid_cap(s, A.n, kBlock);
@@ -408,7 +409,9 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
   // first goes to bufs[w0], each later one flips buffers, the last hits bufs[0].
   int w0 = (degree - 1) % 2;
   sph_rt_status rc;
-  if (zero_guess) {
+  if (first_step_done) {
+    // the caller has made step 0 from a nonzero guess, result in bufs[w0]
+  } else if (zero_guess) {
     cheb_init_zero_kernel<MT, VT><<<g, kBlock, 0, s->stream>>>(A.n, r, A.invdiag, cf, d,
                                                                  bufs[w0], sc);
     SPH_LAUNCHED(s);
@@ -429,10 +432,10 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
 
 template sph_rt_status cheb_apply<double, double>(sph_rt *, const CsrView<double> &, const double *,
                                                   double *, double *, double *, int,
-                                                  const ChebCoef *, bool, const Scalars *);
+                                                  const ChebCoef *, bool, const Scalars *, bool);
 template sph_rt_status cheb_apply<float, float>(sph_rt *, const CsrView<float> &, const float *,
                                                 float *, float *, float *, int, const ChebCoef *,
-                                                bool, const Scalars *);
+                                                bool, const Scalars *, bool);
 
 // Preconditioner hook implemented by the AMG translation unit.
 sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc);
@@ -449,7 +452,7 @@ static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first
       return SPH_RT_OK;
     case SPH_RT_PRECOND_CHEBYSHEV:
       rc = cheb_apply<double, double>(s, A, s->r, s->z, s->w, s->tmp_n2, s->cfg.cheb_degree,
-                                      s->cheb_slots, true, s->sc);
+                                      s->cheb_slots, true, s->sc, false);
       if (rc) return rc;
       break;
     default:

@@ -800,7 +800,7 @@ extern "C" sph_rt_status sph_rt_kernel_stats(sph_rt *s, int64_t *launches, doubl
     s->spmv_launches = 0;
     s->spmv_ms = 0.0;
     s->spmv_bytes = 0.0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kTimedKinds; ++k) {
       s->kind_launches[k] = 0;
       s->kind_ms[k] = 0.0;
       s->kind_bytes[k] = 0.0;
@@ -812,7 +812,8 @@ extern "C" sph_rt_status sph_rt_kernel_stats(sph_rt *s, int64_t *launches, doubl
 extern "C" sph_rt_status sph_rt_kernel_stats_kind(sph_rt *s, int32_t kind, int64_t *launches,
                                                   double *total_ms, double *bytes) {
   if (!s) return SPH_RT_EINVAL;
-  if (kind < 0 || kind > 2) return set_error(s, SPH_RT_EINVAL, "kernel kind out of range");
+  if (kind < 0 || kind >= kTimedKinds)
+    return set_error(s, SPH_RT_EINVAL, "kernel kind out of range");
   if (launches) *launches = s->kind_launches[kind];
   if (total_ms) *total_ms = s->kind_ms[kind];
   if (bytes) *bytes = s->kind_bytes[kind];

@@ -327,7 +327,7 @@ class Solver:
     def kernel_stats_by_kind(self):
         """{name: (launches, ms, bytes)} of the timed fine-operator kernels."""
         out = {}
-        for kind, name in ((0, "spmv_pq"), (1, "resid"), (2, "cheb_step")):
+        for kind, name in ((0, "spmv_pq"), (1, "resid"), (2, "cheb_step"), (3, "post_ap")):
             n, ms, by = C.c_int64(), C.c_double(), C.c_double()
             self._check(self._L.sph_rt_kernel_stats_kind(self._h, kind, C.byref(n), C.byref(ms),
                                                          C.byref(by)))
