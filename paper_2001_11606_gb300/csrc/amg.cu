@@ -48,6 +48,10 @@ constexpr int kUndecided = 1, kRoot = 2, kNonroot = 0, kIsolated = 3;
 constexpr int kHash = 4096;        // shared hash-table slots per coarse row
 constexpr int kCoarseTarget = 512;  // stop coarsening at or below this many rows
 constexpr int kMaxLevels = 12;
+// Levels at or below this many stored entries (~7 MB in FP64, L2-resident)
+// may run in the cluster-resident tail (which must hold at least two levels);
+// the larger levels post-smooth through A P.
+constexpr int64_t kTailMaxNnz = 600000;
 static_assert(1 + kMaxLevels <= kChebSlots, "one Chebyshev slot per AMG level");
 
 }  // namespace sphrt
@@ -655,15 +659,15 @@ __global__ void ap_galerkin_target_kernel(int64_t n, const int64_t *ap_ptr, cons
   }
 }
 
-// First post-smoothing step on the finest level with the prolongation folded
-// in: z = z_pre + P e_c, res2 = res - (A P) e_c (= r - A z), d = c2 D^{-1} res2
+// First post-smoothing step of a level with the prolongation folded in:
+// z = z_pre + P e_c, res2 = res - (A P) e_c (= r - A z), d = c2 D^{-1} res2
 // (step 0 from a nonzero guess), z_out = z + d.  z_out may be z_pre.
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, kFineMinBlocks)
-    fine_post_ap_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col,
-                        const MT *ap_val, const int32_t *agg, const VT *ec, const VT *z_pre,
-                        const VT *res, const MT *invdiag, const ChebCoef *cf, VT *d, VT *z_out,
-                        const Scalars *sc, int *wflag) {
+__device__ __forceinline__ void post_ap_body(int64_t n, const int64_t *ap_ptr,
+                                             const int32_t *ap_col, const MT *ap_val,
+                                             const int32_t *agg, const VT *ec, const VT *z_pre,
+                                             const VT *res, const MT *invdiag, const ChebCoef *cf,
+                                             VT *d, VT *z_out, const Scalars *sc, int *wflag) {
   if (sc && sc->done) {
     mark_work(wflag, 0);
     return;
@@ -698,6 +702,25 @@ __global__ void __launch_bounds__(kBlock, kFineMinBlocks)
       z_out[i] = zi + di;
     }
   }
+}
+// the same sweep under two names: finest level / coarser levels in profiles
+template <int W, int U, typename MT, typename VT>
+__global__ void __launch_bounds__(kBlock, kFineMinBlocks)
+    fine_post_ap_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col,
+                        const MT *ap_val, const int32_t *agg, const VT *ec, const VT *z_pre,
+                        const VT *res, const MT *invdiag, const ChebCoef *cf, VT *d, VT *z_out,
+                        const Scalars *sc, int *wflag) {
+  post_ap_body<W, U, MT, VT>(n, ap_ptr, ap_col, ap_val, agg, ec, z_pre, res, invdiag, cf, d,
+                             z_out, sc, wflag);
+}
+template <int W, int U, typename MT, typename VT>
+__global__ void __launch_bounds__(kBlock, kFineMinBlocks)
+    post_ap_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col, const MT *ap_val,
+                   const int32_t *agg, const VT *ec, const VT *z_pre, const VT *res,
+                   const MT *invdiag, const ChebCoef *cf, VT *d, VT *z_out, const Scalars *sc,
+                   int *wflag) {
+  post_ap_body<W, U, MT, VT>(n, ap_ptr, ap_col, ap_val, agg, ec, z_pre, res, invdiag, cf, d,
+                             z_out, sc, wflag);
 }
 
 // ---------------------------------------------------------------------------
@@ -1057,8 +1080,8 @@ static sph_rt_status level_vectors_fine(sph_rt *s, SphLevel *L) {
 }
 
 // structure of A P on the finest level (see ap_structure_kernel)
-static sph_rt_status build_ap(sph_rt *s) {
-  SphLevel *L = s->levels[0];
+static sph_rt_status build_ap(sph_rt *s, size_t l) {
+  SphLevel *L = s->levels[l];
   const int64_t n = L->n;
   int32_t *tmp = scratch<int32_t>(s, (size_t)(L->nnz + n));
   int64_t *cnt = scratch<int64_t>(s, (size_t)n + 1);
@@ -1090,7 +1113,7 @@ static sph_rt_status build_ap(sph_rt *s) {
   if ((rc = bucket_sort(s, L, L->nnz + n, map, total, &L->ap_seg_ptr, &L->ap_seg_src, nullptr)))
     return rc;
   // next level's Galerkin sources: the A P entries of its members' rows
-  SphLevel *C = s->levels[1];
+  SphLevel *C = s->levels[l + 1];
   int32_t *tgt = scratch<int32_t>(s, (size_t)total);
   int *missing = scratch<int>(s, 1);
   if (!tgt || !missing) return SPH_RT_ENOMEM;
@@ -1146,7 +1169,6 @@ static sph_rt_status build_structure(sph_rt *s) {
     SPH_LAUNCHED(s);
     L = C;
   }
-  if (s->levels.size() >= 2 && (rc = build_ap(s))) return rc;
   s->amg_ready = true;
   return SPH_RT_OK;
 }
@@ -1165,21 +1187,20 @@ static int coarse_degree(const sph_rt *s, const SphLevel *L) {
 }
 
 static sph_rt_status numeric(sph_rt *s) {
-  if (s->levels.size() >= 2 && s->levels[0]->ap_ptr) {
-    SphLevel *L = s->levels[0];
-    galerkin_kernel<<<gcap(s, L->nnz_ap, kBlock), kBlock, 0, s->stream>>>(
-        L->nnz_ap, 0, L->ap_seg_ptr, L->ap_seg_src, L->nnz, L->val, L->diag, L->ap_val, nullptr,
-        nullptr);
-    SPH_LAUNCHED(s);
-    if (L->ap_val32) {
-      convert_kernel<double, float><<<gcap(s, L->nnz_ap, kBlock), kBlock, 0, s->stream>>>(
-          L->nnz_ap, L->ap_val, L->ap_val32);
-      SPH_LAUNCHED(s);
-    }
-  }
   for (size_t l = 0; l + 1 < s->levels.size(); ++l) {
     SphLevel *L = s->levels[l], *C = s->levels[l + 1];
-    if (l == 0 && L->apg_ptr) {  // P^T (A P)
+    if (L->ap_ptr) {  // A P of this level (its values are final: level l is done)
+      galerkin_kernel<<<gcap(s, L->nnz_ap, kBlock), kBlock, 0, s->stream>>>(
+          L->nnz_ap, 0, L->ap_seg_ptr, L->ap_seg_src, L->nnz, L->val, L->diag, L->ap_val,
+          nullptr, nullptr);
+      SPH_LAUNCHED(s);
+      if (L->ap_val32) {
+        convert_kernel<double, float><<<gcap(s, L->nnz_ap, kBlock), kBlock, 0, s->stream>>>(
+            L->nnz_ap, L->ap_val, L->ap_val32);
+        SPH_LAUNCHED(s);
+      }
+    }
+    if (L->apg_ptr) {  // P^T (A P)
       galerkin_kernel<<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
           C->nnz, C->n, L->apg_ptr, L->apg_src, L->nnz_ap, L->ap_val, nullptr, C->val, C->diag,
           C->invdiag);
@@ -1256,6 +1277,11 @@ sph_rt_status amg_setup(sph_rt *s) {
       tail_setup<float>(s);
     else
       tail_setup<double>(s);
+    // A P of the levels larger than the tail threshold: the smaller ones
+    // post-smooth the same way with or without the cluster tail, so both give
+    // bitwise the same V-cycle
+    for (size_t l = 0; l + 1 < s->levels.size() && s->levels[l]->nnz > kTailMaxNnz; ++l)
+      if ((rc = build_ap(s, l))) return rc;
   }
   return numeric(s);
 }
@@ -1310,9 +1336,6 @@ struct LevelVecs<float> {
   static const float *ap(SphLevel *L) { return L->ap_val32; }
 };
 
-// Levels at or below this many stored entries (~7 MB in FP64) may run in the
-// cluster-resident tail; the tail must hold at least two levels.
-constexpr int64_t kTailMaxNnz = 600000;
 
 template <typename T>
 static sph_rt_status launch_tail(sph_rt *s, size_t l0, const T *r, T *z, const Scalars *sc) {
@@ -1466,22 +1489,31 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
                                                                       res, LV::r(C), sc);
   SPH_LAUNCHED(s);
   if ((rc = vcycle<T>(s, l + 1, LV::r(C), LV::z(C), sc))) return rc;
-  if (l == 0 && L->ap_ptr && LV::ap(L)) {
+  if (L->ap_ptr && LV::ap(L)) {
     // prolongation and the first post-smoothing step in one sweep of A P
     T *bufs[2] = {z, LV::t(L)};
     const int w0 = (deg - 1) % 2;
-    const int gp = row_grid(s->num_sms, L->n, 4);
-    int *wf = timing_begin(s);
-    fine_post_ap_kernel<4, 4, T, T><<<gp, kBlock, 0, s->stream>>>(
-        L->n, L->ap_ptr, L->ap_col, LV::ap(L), L->agg, LV::z(C), z, res, A.invdiag, cf,
-        LV::d(L), bufs[w0], sc, wf);
+    const RowShape sh = shape_for_mean(L->n ? (double)L->nnz_ap / (double)L->n : 0.0);
+    const int gp = row_grid(s->num_sms, L->n, sh.W);
+    int *wf = l == 0 ? timing_begin(s) : nullptr;
+    if (l == 0)
+      SPH_DISPATCH_SHAPE(sh.W, sh.U,
+                         (fine_post_ap_kernel<W, U, T, T><<<gp, kBlock, 0, s->stream>>>(
+                             L->n, L->ap_ptr, L->ap_col, LV::ap(L), L->agg, LV::z(C), z, res,
+                             A.invdiag, cf, LV::d(L), bufs[w0], sc, wf)));
+    else
+      SPH_DISPATCH_SHAPE(sh.W, sh.U,
+                         (post_ap_kernel<W, U, T, T><<<gp, kBlock, 0, s->stream>>>(
+                             L->n, L->ap_ptr, L->ap_col, LV::ap(L), L->agg, LV::z(C), z, res,
+                             A.invdiag, cf, LV::d(L), bufs[w0], sc, nullptr)));
     SPH_LAUNCHED(s);
     // A P entry: column + value; per row: ap_ptr, agg, the coarse entry of P e_c,
     // z_pre, res, 1/diag, d, z_out
-    timing_end(s,
-               (4.0 + sizeof(T)) * (double)L->nnz_ap +
-                   (12.0 + 6.0 * sizeof(T)) * (double)L->n,
-               kTimedPost);
+    if (l == 0)
+      timing_end(s,
+                 (4.0 + sizeof(T)) * (double)L->nnz_ap +
+                     (12.0 + 6.0 * sizeof(T)) * (double)L->n,
+                 kTimedPost);
     return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, false, sc, true);
   }
   prolong_kernel<T><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(L->n, L->agg, LV::z(C), z, sc);
