@@ -491,6 +491,25 @@ __global__ void restrict_kernel(int64_t nc, const int64_t *agg_ptr, const int32_
   }
 }
 
+// Restriction fused with the next level's zero-guess smoother start
+// (cheb_init_zero_kernel's arithmetic): rc = P^T res; d_c = z_c = D_c^{-1} rc / theta_c.
+template <typename MT, typename VT>
+__global__ void restrict_init_kernel(int64_t nc, const int64_t *agg_ptr, const int32_t *agg_mem,
+                                     const VT *res, VT *rc, const MT *invdiag_c,
+                                     const ChebCoef *cf_c, VT *d_c, VT *z_c, const Scalars *sc) {
+  if (sc && sc->done) return;
+  const double inv_theta = cf_c->inv_theta;
+  for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < nc;
+       I += (int64_t)gridDim.x * blockDim.x) {
+    VT acc = 0;
+    for (int64_t m = agg_ptr[I]; m < agg_ptr[I + 1]; ++m) acc += res[agg_mem[m]];
+    rc[I] = acc;
+    VT di = (VT)(inv_theta * (double)invdiag_c[I] * (double)acc);
+    d_c[I] = di;
+    z_c[I] = di;
+  }
+}
+
 template <typename VT>
 __global__ void prolong_kernel(int64_t n, const int32_t *agg, const VT *zc, VT *z,
                                const Scalars *sc) {
@@ -549,8 +568,23 @@ __device__ void coarse_cheb_body(const CsrView<MT> &A, const GT *r_g, GT *z_g, c
   for (int k = 1; k < degree; ++k) {
     const VT c1 = (VT)cf->c1[k], c2 = (VT)cf->c2[k];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {  // thread per row: no shuffles
+      // 8 column / value loads, then 8 gathers in flight, summed in entry order
       VT s = 0;
-      for (int kk = ptr[i]; kk < ptr[i + 1]; ++kk) s = fmadd((VT)val[kk], zin[col[kk]], s);
+      const int e = ptr[i + 1];
+      for (int kk = ptr[i]; kk < e; kk += 8) {
+        int cc[8];
+        VT vv[8], zz[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          cc[u] = kk + u < e ? col[kk + u] : -1;
+          vv[u] = kk + u < e ? val[kk + u] : VT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) zz[u] = cc[u] >= 0 ? zin[cc[u]] : VT(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (cc[u] >= 0) s = fmadd(vv[u], zz[u], s);
+      }
       VT res = r[i] - fmadd((VT)dg[i], zin[i], s);
       VT di = fmadd(c1, d[i], (c2 * (VT)idg[i]) * res);
       d[i] = di;
@@ -1428,7 +1462,8 @@ static void tail_setup(sph_rt *s) {
 }
 
 template <typename T>
-static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars *sc) {
+static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars *sc,
+                            bool init_done = false) {
   using LV = LevelVecs<T>;
   if (s->tail_level > 0 && l == (size_t)s->tail_level) return launch_tail<T>(s, l, r, z, sc);
   SphLevel *L = s->levels[l];
@@ -1466,7 +1501,10 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
     return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), cdeg, cf, true, sc);
   }
   const ChebCoef *cf = s->cheb_slots + 1 + l;
-  if ((rc = cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, true, sc))) return rc;
+  // zero-guess pre-smoothing (its first write was made by the restriction above
+  // when init_done)
+  if ((rc = cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, true, sc, init_done)))
+    return rc;
   const int gw = row_grid(s->num_sms, L->n, A.W);
   T *res = LV::res(L);
   // fine-level residual sweeps are timed with the other fine SpMV-class kernels;
@@ -1485,10 +1523,21 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
     timing_end(s, (4.0 + sizeof(T)) * (double)A.nnz + (8.0 + 4.0 * sizeof(T)) * (double)A.n,
                kTimedResid);
   SphLevel *C = s->levels[l + 1];
-  restrict_kernel<T><<<gcap(s, C->n, kBlock), kBlock, 0, s->stream>>>(C->n, L->agg_ptr, L->agg_mem,
-                                                                      res, LV::r(C), sc);
+  // a launched, non-coarsest next level takes its smoother start from the restriction
+  const bool fuse = l + 2 < s->levels.size() &&
+                    !(s->tail_level > 0 && l + 1 == (size_t)s->tail_level);
+  if (fuse) {
+    const int wc = (deg - 1) % 2;  // cheb_apply's first write goes to bufs[wc]
+    T *zc_first = wc == 0 ? LV::z(C) : LV::t(C);
+    restrict_init_kernel<T, T><<<gcap(s, C->n, kBlock), kBlock, 0, s->stream>>>(
+        C->n, L->agg_ptr, L->agg_mem, res, LV::r(C), LV::view(C).invdiag,
+        s->cheb_slots + 1 + (l + 1), LV::d(C), zc_first, sc);
+  } else {
+    restrict_kernel<T><<<gcap(s, C->n, kBlock), kBlock, 0, s->stream>>>(
+        C->n, L->agg_ptr, L->agg_mem, res, LV::r(C), sc);
+  }
   SPH_LAUNCHED(s);
-  if ((rc = vcycle<T>(s, l + 1, LV::r(C), LV::z(C), sc))) return rc;
+  if ((rc = vcycle<T>(s, l + 1, LV::r(C), LV::z(C), sc, fuse))) return rc;
   if (L->ap_ptr && LV::ap(L)) {
     // prolongation and the first post-smoothing step in one sweep of A P
     T *bufs[2] = {z, LV::t(L)};
