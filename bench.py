@@ -132,9 +132,9 @@ def aggregate_ranks(t_local: float, work_local: float):
 # ncu capture of the kernel at the workload, keyed (workload, precision, kernel);
 # the profiles/ summary named in the second field holds the capture.
 NCU_TRAFFIC = {
-    ("mms3d-lp-64^3", "fp64", "spmv_pq"): (337.1e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
-    ("mms3d-lp-64^3", "fp64", "cheb_step"): (337.6e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
-    ("mms3d-lp-64^3", "fp64", "resid"): (334.1e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "resid"): (338.3e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "spmv_pq"): (341.4e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "post_ap"): (112.9e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
 }
 
 

@@ -453,28 +453,25 @@ __device__ __forceinline__ void resid_level_body(const CsrView<MT> &A, const VT 
     return;
   }
   mark_work(wflag, 1);
-  const int sub = threadIdx.x % W;
-  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
-  for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
-    const int64_t i = wb + group_in_warp<W>(grp);
-    const bool active = i < A.n;
-    VT pre = VT(0);  // lane 0: r_i, 1: A_ii, 2: z_i (fetched before the row's sum)
-    if (active && sub < 3) pre = sub == 0 ? r[i] : sub == 1 ? (VT)A.diag[i] : z[i];
-    VT s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub) : VT(0);
-    s = row_reduce<W>(s);
-    const VT ri = group_bcast<W>(pre, 0), dg = group_bcast<W>(pre, 1), zi = group_bcast<W>(pre, 2);
-    if (active && sub == 0) res[i] = ri - fmadd(dg, zi, s);
+  const int own = tile_own_row<W>(threadIdx.x & 31);
+  int64_t r0, r1;
+  warp_rows<W>(A.n, r0, r1);
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const bool active = own < rows;
+    const VT s = tile_row_sums<W, U, MT, VT>(base, rows, A.ptr, A.col, A.val, z);
+    if (active) res[i] = r[i] - fmadd((VT)A.diag[i], z[i], s);
   }
 }
 // one body, two names: finest level vs coarse levels in profiles
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, kFineMinBlocks) resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
                                    const Scalars *sc, int *wflag) {
   resid_level_body<W, U, MT, VT>(A, r, z, res, sc, wflag);
 }
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, kFineMinBlocks) fine_resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) fine_resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
                                         const Scalars *sc, int *wflag) {
   resid_level_body<W, U, MT, VT>(A, r, z, res, sc, wflag);
 }
@@ -707,29 +704,19 @@ __device__ __forceinline__ void post_ap_body(int64_t n, const int64_t *ap_ptr,
     return;
   }
   mark_work(wflag, 1);
-  const int sub = threadIdx.x % W;
-  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   const VT c2 = (VT)cf->inv_theta;
-  for (int64_t wb = warp_first_group<W>(grp); wb < n; wb += ngrp) {
-    const int64_t i = wb + group_in_warp<W>(grp);
-    const bool active = i < n;
-    // lane 0: z_pre_i, 1: res_i, 2: 1/A_ii, 3: (P e_c)_i
-    VT pre = VT(0);
-    if (active && sub < 4) {
-      if (sub == 0) pre = z_pre[i];
-      else if (sub == 1) pre = res[i];
-      else if (sub == 2) pre = (VT)invdiag[i];
-      else {
-        const int32_t a = agg[i];
-        pre = a >= 0 ? ec[a] : VT(0);
-      }
-    }
-    VT s = active ? row_dot<W, U>(ap_ptr[i], ap_ptr[i + 1], ap_col, ap_val, ec, sub) : VT(0);
-    s = row_reduce<W>(s);
-    const VT zp = group_bcast<W>(pre, 0), rs = group_bcast<W>(pre, 1);
-    const VT idg = group_bcast<W>(pre, 2), pe = group_bcast<W>(pre, 3);
-    if (active && sub == 0) {
+  const int own = tile_own_row<W>(threadIdx.x & 31);
+  int64_t r0, r1;
+  warp_rows<W>(n, r0, r1);
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const bool active = own < rows;
+    const VT s = tile_row_sums<W, U, MT, VT>(base, rows, ap_ptr, ap_col, ap_val, ec);
+    if (active) {
+      const VT zp = z_pre[i], rs = res[i], idg = (VT)invdiag[i];
+      const int32_t a = agg[i];
+      const VT pe = a >= 0 ? ec[a] : VT(0);
       const VT zi = zp + pe;
       const VT di = (c2 * idg) * (rs - s);
       d[i] = di;
@@ -739,7 +726,7 @@ __device__ __forceinline__ void post_ap_body(int64_t n, const int64_t *ap_ptr,
 }
 // the same sweep under two names: finest level / coarser levels in profiles
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, kFineMinBlocks)
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U))
     fine_post_ap_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col,
                         const MT *ap_val, const int32_t *agg, const VT *ec, const VT *z_pre,
                         const VT *res, const MT *invdiag, const ChebCoef *cf, VT *d, VT *z_out,
@@ -748,7 +735,7 @@ __global__ void __launch_bounds__(kBlock, kFineMinBlocks)
                              z_out, sc, wflag);
 }
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, kFineMinBlocks)
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U))
     post_ap_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col, const MT *ap_val,
                    const int32_t *agg, const VT *ec, const VT *z_pre, const VT *res,
                    const MT *invdiag, const ChebCoef *cf, VT *d, VT *z_out, const Scalars *sc,
@@ -1505,7 +1492,7 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
   // when init_done)
   if ((rc = cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, true, sc, init_done)))
     return rc;
-  const int gw = row_grid(s->num_sms, L->n, A.W);
+  const int gw = row_grid(s->num_sms, L->n, A.W, A.U);
   T *res = LV::res(L);
   // fine-level residual sweeps are timed with the other fine SpMV-class kernels;
   // per row: rowptr, diag, r, z, res
@@ -1543,7 +1530,7 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
     T *bufs[2] = {z, LV::t(L)};
     const int w0 = (deg - 1) % 2;
     const RowShape sh = shape_for_mean(L->n ? (double)L->nnz_ap / (double)L->n : 0.0);
-    const int gp = row_grid(s->num_sms, L->n, sh.W);
+    const int gp = row_grid(s->num_sms, L->n, sh.W, sh.U);
     int *wf = l == 0 ? timing_begin(s) : nullptr;
     if (l == 0)
       SPH_DISPATCH_SHAPE(sh.W, sh.U,

@@ -29,11 +29,11 @@ namespace sphrt {
 constexpr int kBlock = 256;          // threads per block of the 1-D kernels
 constexpr int kWarpsPerBlock = kBlock / 32;
 constexpr int kMaxRedBlocks = 2048;  // upper bound on blocks of a reducing kernel
-// resident blocks per SM the SpMV-class sweeps are compiled for (register cap)
-#ifndef SPH_FINE_MIN_BLOCKS
-#define SPH_FINE_MIN_BLOCKS 6
-#endif
-constexpr int kFineMinBlocks = SPH_FINE_MIN_BLOCKS;
+// Resident blocks per SM the SpMV-class sweeps are compiled for, i.e. their
+// register cap (65536 / (kBlock * blocks)): 5 blocks (48 registers) with U = 4
+// loads in flight per lane, 4 blocks (64 registers) with U = 8.  Their grids
+// never exceed this many blocks per SM (row_grid), so one wave covers all rows.
+__host__ __device__ constexpr int sweep_min_blocks(int U) { return U >= 8 ? 4 : 5; }
 
 // --------------------------------------------------------------------------
 // Scalars of one Krylov solve and of the outer loop, kept on the device so
@@ -220,6 +220,164 @@ __device__ __forceinline__ T row_reduce(T v) {
   return v;
 }
 
+// ---------------------------------------------------------------------------
+// Row tiles: the layout of the SpMV-class sweeps.
+//
+// On this part an FP64 warp instruction occupies the narrow FP64 pipe for all
+// 32 lanes whether or not a lane is active, so lanes left idle by a sweep cost
+// as much as busy ones.  A warp therefore works on tiles of 32 consecutive rows
+// in W rounds; in round t its G = 32/W row groups (W lanes each) take rows
+// t G + g.  Per round the warp issues exactly as many FMA instructions as its
+// longest row needs (not a multiple of the load batch); after the W rounds a
+// transposed shuffle reduction leaves the sum of row (l mod W) G + l/W in lane
+// l with W - 1 adds per lane instead of log2(W) adds per lane and row; and the
+// row epilogue (diagonal term, vector updates, reductions) runs on all 32
+// lanes instead of one lane per group, with its loads and stores coalesced.
+//
+// The arithmetic of a row is that of row_dot + row_reduce exactly: each lane
+// sums its entries beg + sub + j W in increasing j, and the reduction adds the
+// lane partials in the same tree (lanes W/2 apart first), so every row sum is
+// bitwise that of the one-row-per-group form.
+// ---------------------------------------------------------------------------
+
+// Offset, within its tile, of the row whose sum and epilogue lane `lane` holds.
+template <int W>
+__device__ __forceinline__ int tile_own_row(int lane) {
+  return (lane % W) * (32 / W) + lane / W;
+}
+
+// Contiguous rows [r0, r1) of this warp: the rows are cut into units of G =
+// 32/W (one round of a tile) and the units are spread as evenly as possible
+// over all warps of the grid.  Warp-uniform.
+template <int W>
+__device__ __forceinline__ void warp_rows(int64_t n, int64_t &r0, int64_t &r1) {
+  constexpr int G = 32 / W;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t units = ceil_div(n, G), q = units / nwarps, rem = units % nwarps;
+  const int64_t u0 = w * q + (w < rem ? w : rem);
+  const int64_t u1 = u0 + q + (w < rem ? 1 : 0);
+  r0 = u0 * G < n ? u0 * G : n;
+  r1 = u1 * G < n ? u1 * G : n;
+}
+
+// Off-diagonal sum of one row by its W-lane group with a warp-uniform trip
+// count: nmax = the largest per-lane entry count over the warp, so the warp
+// issues nmax FMA instructions.  Full passes keep U column/value loads and U
+// gathers in flight per lane; the last, partial pass loads its slots at once
+// and then runs its FMAs in a loop of exactly (nmax mod U) trips, shifting the
+// loaded slots down.  Slots past a lane's row end load nothing and contribute
+// fma(0, 0, s) = s.
+template <int W, int U, typename MT, typename VT>
+__device__ __forceinline__ VT row_dot_n(int64_t beg, int64_t end, const int32_t *__restrict__ col,
+                                        const MT *__restrict__ val, const VT *__restrict__ x,
+                                        int sub, int nmax) {
+  VT s = VT(0);
+  int64_t k = beg + sub;
+  int j = 0;
+  for (; j + U <= nmax; j += U, k += (int64_t)W * U) {
+    int32_t c[U];
+    MT v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * W;
+      c[u] = kk < end ? __ldg(col + kk) : -1;
+      v[u] = kk < end ? __ldg(val + kk) : MT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (c[u] >= 0) s = fmadd((VT)v[u], __ldg(x + c[u]), s);
+  }
+  const int rem = nmax - j;  // warp-uniform, < U
+  if (rem > 0) {
+    VT a[U], g[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * W;
+      const int32_t c = kk < end ? __ldg(col + kk) : -1;
+      a[u] = c >= 0 ? (VT)__ldg(val + kk) : VT(0);
+      g[u] = c >= 0 ? __ldg(x + c) : VT(0);
+    }
+#pragma unroll 1
+    for (int u = 0; u < rem; ++u) {
+      s = fmadd(a[0], g[0], s);
+#pragma unroll
+      for (int q = 0; q + 1 < U; ++q) {
+        a[q] = a[q + 1];
+        g[q] = g[q + 1];
+      }
+    }
+  }
+  return s;
+}
+
+// One step of the transposed reduction at lane distance o: `lo` and `hi` are
+// this lane's partials of two rounds that differ in bit o (lo: bit clear).
+// The lane with bit o of its group index clear keeps round `lo` and adds its
+// partner's partial of it; the partner keeps `hi`.  Both sides add the same
+// two numbers, the lower lane's first, as row_reduce does.
+template <int W, typename VT>
+__device__ __forceinline__ VT tile_combine(VT lo, VT hi, int o, int sub) {
+  const bool up = (sub & o) != 0;
+  const VT keep = up ? hi : lo, send = up ? lo : hi;
+  const VT recv = __shfl_xor_sync(0xffffffffu, send, o, W);
+  return up ? recv + keep : keep + recv;
+}
+
+// Row sums of round t of a tile (see tile_row_sums): this lane's partial of
+// row base + t G + g.  Every lane of the warp calls it.
+template <int W, int U, typename MT, typename VT>
+__device__ __forceinline__ VT tile_round(int t, int rows, int64_t b, int64_t e,
+                                         const int32_t *__restrict__ col,
+                                         const MT *__restrict__ val, const VT *__restrict__ x,
+                                         int sub) {
+  constexpr int G = 32 / W;
+  if (t * G >= rows) return VT(0);  // warp-uniform
+  // round t's row of group g has its extents in lane g W + t
+  const int64_t rb = __shfl_sync(0xffffffffu, b, t, W);
+  const int64_t re = __shfl_sync(0xffffffffu, e, t, W);
+  const int cnt = (int)((re - rb - sub + W - 1) / W);  // >= 0
+  const int nmax = __reduce_max_sync(0xffffffffu, cnt);
+  return row_dot_n<W, U, MT, VT>(rb, re, col, val, x, sub, nmax);
+}
+
+// The reduction tree over the W rounds, evaluated depth first: the rounds are
+// visited in bit-reversed order and each pair is combined as soon as both are
+// done, so at most log2(W) + 1 partials are live at a time.  Rounds t0 + j O
+// (j = 0, 1, ...) are the subtree below bit O.
+template <int W, int O, int U, typename MT, typename VT>
+__device__ __forceinline__ VT tile_tree(int t0, int rows, int64_t b, int64_t e,
+                                        const int32_t *__restrict__ col,
+                                        const MT *__restrict__ val, const VT *__restrict__ x,
+                                        int sub) {
+  if constexpr (O == W) {
+    return tile_round<W, U, MT, VT>(t0, rows, b, e, col, val, x, sub);
+  } else {
+    const VT lo = tile_tree<W, 2 * O, U, MT, VT>(t0, rows, b, e, col, val, x, sub);
+    const VT hi = tile_tree<W, 2 * O, U, MT, VT>(t0 + O, rows, b, e, col, val, x, sub);
+    return tile_combine<W, VT>(lo, hi, O, sub);
+  }
+}
+
+// Row sums of the tile of `rows` (<= 32) rows starting at `base`: lane l gets
+// the off-diagonal sum of row base + tile_own_row<W>(l) (0 past `rows`).  Every
+// lane of the warp must call it with the same base and rows.  The reduction
+// (tile_combine at distances 1, 2, ..., W/2 from the root) ends with lane sub
+// of a group holding round sub, i.e. row sub G + g.
+template <int W, int U, typename MT, typename VT>
+__device__ __forceinline__ VT tile_row_sums(int64_t base, int rows, const int64_t *__restrict__ ptr,
+                                            const int32_t *__restrict__ col,
+                                            const MT *__restrict__ val, const VT *__restrict__ x) {
+  const int lane = threadIdx.x & 31, sub = lane % W;
+  const int own = tile_own_row<W>(lane);
+  int64_t b = 0, e = 0;  // row extents, one coalesced load per lane
+  if (own < rows) {
+    b = __ldg(ptr + base + own);
+    e = __ldg(ptr + base + own + 1);
+  }
+  return tile_tree<W, 1, U, MT, VT>(0, rows, b, e, col, val, x, sub);
+}
+
 // Chebyshev iteration coefficients on [lo, hi] (Saad, Iterative Methods,
 // Alg. 12.1): the first step scales by 1/theta, step k >= 1 uses
 // d = c1[k] d + c2[k] D^{-1} res.  Computed once per interval (host, or one
@@ -273,22 +431,23 @@ struct RowShape {
   int W, U;
 };
 // W = 4 lanes per row: loads stay sector-coalesced (4 x 8 B = one 32 B sector
-// per row per instruction) while the FP64 reduction tree costs 2 shuffles
-// instead of 4-5 -- on GB300 the FP64 pipe, not HBM, limits a wide-warp CSR
-// sweep.  Very long rows (coarse AMG levels) use 8 lanes.
+// per row per instruction) while the FP64 reduction costs W - 1 = 3 adds per
+// lane and tile (tile_row_sums) -- on GB300 the FP64 pipe, not HBM, limits a
+// wide-warp CSR sweep.  Very long rows (coarse AMG levels) use 8 lanes.
 __host__ inline int lanes_for_mean(double mean) { return mean <= 160 ? 4 : 8; }
+// U = 4: with row tiles the sweeps are FP64-pipe-bound before they are
+// latency-bound, and U = 4 keeps them at 48 registers (5 resident blocks per SM
+// instead of 4 at U = 8); on the 64^3 and 128^3 operators it is 2-3 % faster.
 __host__ inline RowShape shape_for_mean(double mean) {
-  int W = lanes_for_mean(mean);
-  int U = (mean / W) <= 6 ? 4 : 8;
-  return {W, U};
+  return {lanes_for_mean(mean), 4};
 }
 
-// Grid of a row-group sweep (W lanes per row, kBlock threads per block): one
-// wave of kFineMinBlocks resident blocks per SM at most (the sweeps are
-// compiled with that register cap), striding over the rows.
-__host__ inline int row_grid(int num_sms, int64_t n, int W) {
+// Grid of a row-tile sweep (W lanes per row, kBlock threads per block): one
+// wave of sweep_min_blocks(U) resident blocks per SM at most (the sweeps are
+// compiled with that register cap); warp_rows splits the rows over its warps.
+__host__ inline int row_grid(int num_sms, int64_t n, int W, int U) {
   int64_t g = ceil_div(n > 0 ? n : 1, kBlock / W);
-  int64_t cap = (int64_t)num_sms * kFineMinBlocks;
+  int64_t cap = (int64_t)num_sms * sweep_min_blocks(U);
   return (int)(g < cap ? g : cap);
 }
 

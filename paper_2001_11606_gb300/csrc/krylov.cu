@@ -36,23 +36,20 @@ __device__ __forceinline__ T ld(const T *p) {
 // r = b - B x;  rnorm2 = ||r / V||^2;  done = rnorm2 <= thresh2.
 // ---------------------------------------------------------------------------
 template <int W, int U>
-__global__ void __launch_bounds__(kBlock, kFineMinBlocks) resid_kernel(CsrView<double> A, const double *b, const double *x, double *r,
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) resid_kernel(CsrView<double> A, const double *b, const double *x, double *r,
                              const double *invV, Scalars *sc, double *partials, int *wflag) {
   mark_work(wflag, 1);
-  const int sub = threadIdx.x % W;
-  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  const int own = tile_own_row<W>(threadIdx.x & 31);
+  int64_t r0, r1;
+  warp_rows<W>(A.n, r0, r1);
   double acc = 0.0;
-  for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
-    const int64_t i = wb + group_in_warp<W>(grp);
-    const bool active = i < A.n;
-    double pre = 0.0;  // lane 0: b_i, 1: B_ii, 2: x_i, 3: 1/V_i
-    if (active && sub < 4) pre = sub == 0 ? b[i] : sub == 1 ? A.diag[i] : sub == 2 ? x[i] : invV[i];
-    double s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, x, sub) : 0.0;
-    s = row_reduce<W>(s);
-    const double bi = group_bcast<W>(pre, 0), dg = group_bcast<W>(pre, 1);
-    const double xi = group_bcast<W>(pre, 2), iv = group_bcast<W>(pre, 3);
-    if (active && sub == 0) {
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const bool active = own < rows;
+    const double s = tile_row_sums<W, U, double, double>(base, rows, A.ptr, A.col, A.val, x);
+    if (active) {
+      const double bi = b[i], dg = A.diag[i], xi = x[i], iv = invV[i];
       double ri = bi - fmadd(dg, xi, s);
       r[i] = ri;
       double ru = ri * iv;
@@ -76,7 +73,7 @@ __global__ void __launch_bounds__(kBlock, kFineMinBlocks) resid_kernel(CsrView<d
 // (q = B p without a second SpMV: B p = B z + beta B p_old.)
 // ---------------------------------------------------------------------------
 template <int W, int U>
-__global__ void __launch_bounds__(kBlock, kFineMinBlocks) spmv_pq_kernel(CsrView<double> A, const double *z, double *q, double *p, int first,
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) spmv_pq_kernel(CsrView<double> A, const double *z, double *q, double *p, int first,
                                Scalars *sc, double *partials, int *wflag) {
   if (sc->done) {
     mark_work(wflag, 0);
@@ -84,21 +81,18 @@ __global__ void __launch_bounds__(kBlock, kFineMinBlocks) spmv_pq_kernel(CsrView
   }
   mark_work(wflag, 1);
   const double beta = first ? 0.0 : sc->beta;
-  const int sub = threadIdx.x % W;
-  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
+  const int own = tile_own_row<W>(threadIdx.x & 31);
+  int64_t r0, r1;
+  warp_rows<W>(A.n, r0, r1);
   double acc = 0.0;
-  for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
-    const int64_t i = wb + group_in_warp<W>(grp);
-    const bool active = i < A.n;
-    double pre = 0.0;  // lane 0: z_i, 1: B_ii, 2: q_i, 3: p_i
-    if (active && sub < 4 && (sub < 2 || !first))
-      pre = sub == 0 ? z[i] : sub == 1 ? A.diag[i] : sub == 2 ? q[i] : p[i];
-    double s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z, sub) : 0.0;
-    s = row_reduce<W>(s);
-    const double zi = group_bcast<W>(pre, 0), dg = group_bcast<W>(pre, 1);
-    const double qo = group_bcast<W>(pre, 2), po = group_bcast<W>(pre, 3);
-    if (active && sub == 0) {
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const bool active = own < rows;
+    const double s = tile_row_sums<W, U, double, double>(base, rows, A.ptr, A.col, A.val, z);
+    if (active) {
+      const double zi = z[i], dg = A.diag[i];
+      const double qo = first ? 0.0 : q[i], po = first ? 0.0 : p[i];
       double wi = fmadd(dg, zi, s);
       double qi = first ? wi : fmadd(beta, qo, wi);
       double pi = first ? zi : fmadd(beta, po, zi);
@@ -245,29 +239,23 @@ __device__ __forceinline__ void cheb_step_body(const CsrView<MT> &A, const VT *r
     return;
   }
   mark_work(wflag, 1);
-  const int sub = threadIdx.x % W;
-  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
   // step k of the recurrence; k = 0 is the first step from a nonzero guess
   const double c1 = k > 0 ? cf->c1[k] : 0.0, c2 = k > 0 ? cf->c2[k] : cf->inv_theta;
   const VT vc1 = (VT)c1, vc2 = (VT)c2;
-  for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
-    const int64_t i = wb + group_in_warp<W>(grp);
-    const bool active = i < A.n;
-    // lane 0: r_i and 1/B_ii, 1: z_i, 2: d_i (not on the first step), 3: B_ii
-    VT pre = VT(0), pre2 = VT(0);
-    if (active && sub < 4 && (sub != 2 || k > 0)) {
-      pre = sub == 0 ? r[i] : sub == 1 ? z_in[i] : sub == 2 ? d[i] : (VT)A.diag[i];
-      if (sub == 0) pre2 = (VT)A.invdiag[i];
-    }
-    VT s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, z_in, sub) : VT(0);
-    s = row_reduce<W>(s);
-    const VT ri = group_bcast<W>(pre, 0), zi = group_bcast<W>(pre, 1);
-    const VT dold = group_bcast<W>(pre, 2), dg = group_bcast<W>(pre, 3);
-    if (active && sub == 0) {
+  const int own = tile_own_row<W>(threadIdx.x & 31);
+  int64_t r0, r1;
+  warp_rows<W>(A.n, r0, r1);
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const bool active = own < rows;
+    const VT s = tile_row_sums<W, U, MT, VT>(base, rows, A.ptr, A.col, A.val, z_in);
+    if (active) {
+      const VT ri = r[i], zi = z_in[i], dg = (VT)A.diag[i], idg = (VT)A.invdiag[i];
+      const VT dold = k > 0 ? d[i] : VT(0);  // the first step must not read d
       VT res = ri - fmadd(dg, zi, s);
-      VT di = (vc2 * pre2) * res;
-      if (k > 0) di = fmadd(vc1, dold, di);  // the first step must not read d
+      VT di = (vc2 * idg) * res;
+      if (k > 0) di = fmadd(vc1, dold, di);
       d[i] = di;
       z_out[i] = zi + di;
     }
@@ -276,12 +264,12 @@ __device__ __forceinline__ void cheb_step_body(const CsrView<MT> &A, const VT *r
 // The same sweep under two names, so that profiles separate the finest
 // level (HBM-streamed operator) from the coarse levels (L2-resident).
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, kFineMinBlocks) cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
                                  const ChebCoef *cf, int k, const Scalars *sc, int *wflag) {
   cheb_step_body<W, U, MT, VT>(A, r, z_in, z_out, d, cf, k, sc, wflag);
 }
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, kFineMinBlocks) fine_cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out,
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) fine_cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out,
                                       VT *d, const ChebCoef *cf, int k, const Scalars *sc,
                                       int *wflag) {
   cheb_step_body<W, U, MT, VT>(A, r, z_in, z_out, d, cf, k, sc, wflag);
@@ -384,7 +372,7 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
   if (degree < 1) degree = 1;
   if (degree > kChebMaxDeg) degree = kChebMaxDeg;
   int g = grid_cap(s, A.n, kBlock);
-  int gw = row_grid(s->num_sms, A.n, A.W);
+  int gw = row_grid(s->num_sms, A.n, A.W, A.U);
   // fine-level sweeps are timed with the other fine SpMV-class kernels; per row:
   // rowptr, diag, 1/diag, r, z_in, z_out, d r/w (vectors of type VT)
   const bool fine = A.ptr == s->mat_ptr;
@@ -473,16 +461,16 @@ static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first
 
 // Plain SpMV y = B x (off-diagonal part plus diagonal), for the autotuner.
 template <int W, int U>
-__global__ void spmv_plain_kernel(CsrView<double> A, const double *x, double *y) {
-  const int sub = threadIdx.x % W;
-  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
-  for (int64_t wb = warp_first_group<W>(grp); wb < A.n; wb += ngrp) {
-    const int64_t i = wb + group_in_warp<W>(grp);
-    const bool active = i < A.n;
-    double s = active ? row_dot<W, U>(A.ptr[i], A.ptr[i + 1], A.col, A.val, x, sub) : 0.0;
-    s = row_reduce<W>(s);
-    if (active && sub == 0) y[i] = A.diag[i] * x[i] + s;
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U))
+    spmv_plain_kernel(CsrView<double> A, const double *x, double *y) {
+  const int own = tile_own_row<W>(threadIdx.x & 31);
+  int64_t r0, r1;
+  warp_rows<W>(A.n, r0, r1);
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const double s = tile_row_sums<W, U, double, double>(base, rows, A.ptr, A.col, A.val, x);
+    if (own < rows) y[i] = A.diag[i] * x[i] + s;
   }
 }
 
@@ -505,7 +493,7 @@ sph_rt_status autotune_fine_shape(sph_rt *s) {
   for (int round = 0; round < 3; ++round) {
     for (size_t ci = 0; ci < cands.size(); ++ci) {
       const RowShape &c = cands[ci];
-      const int gw = grid_cap(s, A.n, kBlock / c.W);
+      const int gw = row_grid(s->num_sms, A.n, c.W, c.U);
       float ms = 0.f;
       for (int rep = 0; rep < 7; ++rep) {
         if (rep == 1) cudaEventRecord(e0, s->stream);
@@ -537,7 +525,7 @@ sph_rt_status autotune_fine_shape(sph_rt *s) {
 // First part of a solve: r = b - B x, z = M^{-1} r, q = B p with p = z.
 sph_rt_status pcg_prologue(sph_rt *s) {
   CsrView<double> A = fine_view(s);
-  const int gw = row_grid(s->num_sms, A.n, A.W);
+  const int gw = row_grid(s->num_sms, A.n, A.W, A.U);
   sph_rt_status rc;
   int *wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
@@ -568,7 +556,7 @@ __global__ void copy_vec_kernel(int64_t n, const double *src, double *dst, const
 // previous z in z_old.  All launches are empty once `done` is set.
 sph_rt_status pcg_iteration(sph_rt *s) {
   CsrView<double> A = fine_view(s);
-  const int gw = row_grid(s->num_sms, A.n, A.W);
+  const int gw = row_grid(s->num_sms, A.n, A.W, A.U);
   const int g = grid_cap(s, A.n, kBlock);
   sph_rt_status rc;
   update_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
