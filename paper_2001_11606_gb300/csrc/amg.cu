@@ -388,7 +388,11 @@ __global__ void target_count_kernel(int64_t nsrc, const int32_t *tgt, unsigned *
 }
 
 // Galerkin values: thread per coarse target, fixed-order sum of its sources
-// (8 source indices loaded before their gathers, so the gathers overlap).
+// (8 source indices loaded before their gathers, so the gathers overlap).  A
+// warp adds as many slots of a batch as its longest segment has left (most
+// A P targets have 3-4 sources): the additions a lane skips would add +0.0,
+// and a sum that starts at +0.0 is unchanged by them, so the result is that of
+// adding all 8 slots.
 __global__ void galerkin_kernel(int64_t nnz_c, int64_t nc, const int64_t *seg_ptr,
                                 const int32_t *seg_src, int64_t nnz_f, const double *val_f,
                                 const double *diag_f, double *val_c, double *diag_c,
@@ -396,9 +400,13 @@ __global__ void galerkin_kernel(int64_t nnz_c, int64_t nc, const int64_t *seg_pt
   constexpr int G = 8;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz_c + nc;
        t += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned mask = __activemask();
     double acc = 0.0;
     const int64_t u1 = seg_ptr[t + 1];
-    for (int64_t u = seg_ptr[t]; u < u1; u += G) {
+    for (int64_t u = seg_ptr[t];; u += G) {
+      const int64_t left = u1 - u;
+      const int m = __reduce_max_sync(mask, left <= 0 ? 0 : (left < G ? (int)left : G));
+      if (m == 0) break;  // uniform over the lanes of `mask`
       int32_t src[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) src[g] = u + g < u1 ? __ldg(seg_src + u + g) : -1;
@@ -406,8 +414,12 @@ __global__ void galerkin_kernel(int64_t nnz_c, int64_t nc, const int64_t *seg_pt
 #pragma unroll
       for (int g = 0; g < G; ++g)
         v[g] = src[g] < 0 ? 0.0 : (src[g] < nnz_f ? __ldg(val_f + src[g]) : __ldg(diag_f + (src[g] - nnz_f)));
+#pragma unroll 1
+      for (int g = 0; g < m; ++g) {
+        acc += v[0];  // sources in order; a shorter segment's padding adds +0.0
 #pragma unroll
-      for (int g = 0; g < G; ++g) acc += v[g];  // sources in order; padding adds +0.0
+        for (int q = 0; q + 1 < G; ++q) v[q] = v[q + 1];
+      }
     }
     if (t < nnz_c) {
       val_c[t] = acc;
@@ -1556,6 +1568,18 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
   SPH_LAUNCHED(s);
   return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, false, sc);
 }
+
+// Mixed form without the last conversion: r is rounded to FP32 and the FP32
+// V-cycle leaves z in levels[0]->z32 (amg_z32), for a caller that widens it
+// itself (the fused flexible-CG inner product).
+sph_rt_status amg_apply_to32(sph_rt *s, const double *r, const Scalars *sc) {
+  if (s->levels.empty()) return set_error(s, SPH_RT_ESTATE, "AMG hierarchy not set up");
+  SphLevel *L0 = s->levels[0];
+  convert_kernel<double, float><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, r, L0->r32);
+  SPH_LAUNCHED(s);
+  return vcycle<float>(s, 0, L0->r32, L0->z32, sc);
+}
+const float *amg_z32(const sph_rt *s) { return s->levels.empty() ? nullptr : s->levels[0]->z32; }
 
 sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc) {
   if (s->levels.empty()) return set_error(s, SPH_RT_ESTATE, "AMG hierarchy not set up");

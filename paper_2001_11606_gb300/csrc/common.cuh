@@ -311,59 +311,70 @@ __device__ __forceinline__ VT row_dot_n(int64_t beg, int64_t end, const int32_t 
   return s;
 }
 
+// Partial of a tile round that holds three sums (the gradient's components,
+// or the assembly's off-diagonal, ghost-weight and ghost right-hand-side sums);
+// added and shuffled component by component.
+struct Sum3 {
+  double a, b, c;
+};
+__device__ __forceinline__ Sum3 operator+(const Sum3 &x, const Sum3 &y) {
+  return {x.a + y.a, x.b + y.b, x.c + y.c};
+}
+template <int W>
+__device__ __forceinline__ double tile_shfl(double v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o, W);
+}
+template <int W>
+__device__ __forceinline__ float tile_shfl(float v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o, W);
+}
+template <int W>
+__device__ __forceinline__ Sum3 tile_shfl(const Sum3 &v, int o) {
+  return {tile_shfl<W>(v.a, o), tile_shfl<W>(v.b, o), tile_shfl<W>(v.c, o)};
+}
+
 // One step of the transposed reduction at lane distance o: `lo` and `hi` are
 // this lane's partials of two rounds that differ in bit o (lo: bit clear).
 // The lane with bit o of its group index clear keeps round `lo` and adds its
 // partner's partial of it; the partner keeps `hi`.  Both sides add the same
 // two numbers, the lower lane's first, as row_reduce does.
-template <int W, typename VT>
-__device__ __forceinline__ VT tile_combine(VT lo, VT hi, int o, int sub) {
+template <int W, typename R>
+__device__ __forceinline__ R tile_combine(const R &lo, const R &hi, int o, int sub) {
   const bool up = (sub & o) != 0;
-  const VT keep = up ? hi : lo, send = up ? lo : hi;
-  const VT recv = __shfl_xor_sync(0xffffffffu, send, o, W);
+  const R keep = up ? hi : lo, send = up ? lo : hi;
+  const R recv = tile_shfl<W>(send, o);
   return up ? recv + keep : keep + recv;
 }
 
-// Row sums of round t of a tile (see tile_row_sums): this lane's partial of
-// row base + t G + g.  Every lane of the warp calls it.
-template <int W, int U, typename MT, typename VT>
-__device__ __forceinline__ VT tile_round(int t, int rows, int64_t b, int64_t e,
-                                         const int32_t *__restrict__ col,
-                                         const MT *__restrict__ val, const VT *__restrict__ x,
-                                         int sub) {
-  constexpr int G = 32 / W;
-  if (t * G >= rows) return VT(0);  // warp-uniform
-  // round t's row of group g has its extents in lane g W + t
-  const int64_t rb = __shfl_sync(0xffffffffu, b, t, W);
-  const int64_t re = __shfl_sync(0xffffffffu, e, t, W);
-  const int cnt = (int)((re - rb - sub + W - 1) / W);  // >= 0
-  const int nmax = __reduce_max_sync(0xffffffffu, cnt);
-  return row_dot_n<W, U, MT, VT>(rb, re, col, val, x, sub, nmax);
+// The reduction tree over the W rounds of a tile, evaluated depth first: the
+// rounds are visited in bit-reversed order and each pair is combined as soon
+// as both are done, so at most log2(W) + 1 partials are live at a time.
+// Rounds t0 + j O (j = 0, 1, ...) are the subtree below bit O.  round(t)
+// returns this lane's partial of round t; it is called by every lane of the
+// warp, and only for rounds that hold rows (t G < rows, warp-uniform).  The
+// result: lane sub of a group holds round sub, i.e. row sub G + g of the tile.
+template <int W, int O, typename R, typename F>
+__device__ __forceinline__ R tile_tree(int t0, int rows, int sub, const F &round) {
+  if constexpr (O == W) {
+    return t0 * (32 / W) < rows ? round(t0) : R{};
+  } else {
+    const R lo = tile_tree<W, 2 * O, R>(t0, rows, sub, round);
+    const R hi = tile_tree<W, 2 * O, R>(t0 + O, rows, sub, round);
+    return tile_combine<W, R>(lo, hi, O, sub);
+  }
 }
 
-// The reduction tree over the W rounds, evaluated depth first: the rounds are
-// visited in bit-reversed order and each pair is combined as soon as both are
-// done, so at most log2(W) + 1 partials are live at a time.  Rounds t0 + j O
-// (j = 0, 1, ...) are the subtree below bit O.
-template <int W, int O, int U, typename MT, typename VT>
-__device__ __forceinline__ VT tile_tree(int t0, int rows, int64_t b, int64_t e,
-                                        const int32_t *__restrict__ col,
-                                        const MT *__restrict__ val, const VT *__restrict__ x,
-                                        int sub) {
-  if constexpr (O == W) {
-    return tile_round<W, U, MT, VT>(t0, rows, b, e, col, val, x, sub);
-  } else {
-    const VT lo = tile_tree<W, 2 * O, U, MT, VT>(t0, rows, b, e, col, val, x, sub);
-    const VT hi = tile_tree<W, 2 * O, U, MT, VT>(t0 + O, rows, b, e, col, val, x, sub);
-    return tile_combine<W, VT>(lo, hi, O, sub);
-  }
+// Warp-uniform trip count of round t: the largest number of entries a lane
+// of the warp has in its row [rb, re) (entries rb + sub + j W).
+template <int W>
+__device__ __forceinline__ int tile_nmax(int64_t rb, int64_t re, int sub) {
+  const int cnt = (int)((re - rb - sub + W - 1) / W);  // >= 0
+  return __reduce_max_sync(0xffffffffu, cnt);
 }
 
 // Row sums of the tile of `rows` (<= 32) rows starting at `base`: lane l gets
 // the off-diagonal sum of row base + tile_own_row<W>(l) (0 past `rows`).  Every
-// lane of the warp must call it with the same base and rows.  The reduction
-// (tile_combine at distances 1, 2, ..., W/2 from the root) ends with lane sub
-// of a group holding round sub, i.e. row sub G + g.
+// lane of the warp must call it with the same base and rows.
 template <int W, int U, typename MT, typename VT>
 __device__ __forceinline__ VT tile_row_sums(int64_t base, int rows, const int64_t *__restrict__ ptr,
                                             const int32_t *__restrict__ col,
@@ -375,7 +386,12 @@ __device__ __forceinline__ VT tile_row_sums(int64_t base, int rows, const int64_
     b = __ldg(ptr + base + own);
     e = __ldg(ptr + base + own + 1);
   }
-  return tile_tree<W, 1, U, MT, VT>(0, rows, b, e, col, val, x, sub);
+  return tile_tree<W, 1, VT>(0, rows, sub, [&](int t) -> VT {
+    // round t's row of group g has its extents in lane g W + t
+    const int64_t rb = __shfl_sync(0xffffffffu, b, t, W);
+    const int64_t re = __shfl_sync(0xffffffffu, e, t, W);
+    return row_dot_n<W, U, MT, VT>(rb, re, col, val, x, sub, tile_nmax<W>(rb, re, sub));
+  });
 }
 
 // Chebyshev iteration coefficients on [lo, hi] (Saad, Iterative Methods,
@@ -445,10 +461,13 @@ __host__ inline RowShape shape_for_mean(double mean) {
 // Grid of a row-tile sweep (W lanes per row, kBlock threads per block): one
 // wave of sweep_min_blocks(U) resident blocks per SM at most (the sweeps are
 // compiled with that register cap); warp_rows splits the rows over its warps.
-__host__ inline int row_grid(int num_sms, int64_t n, int W, int U) {
+__host__ inline int row_grid_blocks(int num_sms, int64_t n, int W, int blocks_per_sm) {
   int64_t g = ceil_div(n > 0 ? n : 1, kBlock / W);
-  int64_t cap = (int64_t)num_sms * sweep_min_blocks(U);
+  int64_t cap = (int64_t)num_sms * blocks_per_sm;
   return (int)(g < cap ? g : cap);
+}
+__host__ inline int row_grid(int num_sms, int64_t n, int W, int U) {
+  return row_grid_blocks(num_sms, n, W, sweep_min_blocks(U));
 }
 
 // Launch CALL with constexpr W and U set to the supported row-group shape:

@@ -209,6 +209,35 @@ __global__ void dot_rz_flex_kernel(int64_t n, const double *r, const double *z,
   }
 }
 
+// The same for the FP32 V-cycle of the mixed form, fused with widening its
+// result: z32 is the new preconditioned residual, z still holds the previous
+// one (the FP32 V-cycle never writes z), so (r, z_old) is read from z before
+// z = (double) z32 overwrites it.  Same sums in the same order as widening,
+// copying z to z_old and dot_rz_flex_kernel, in one pass instead of three.
+__global__ void dot_rz_flex32_kernel(int64_t n, const double *r, const float *z32, double *z,
+                                     int first, Scalars *sc, double *partials) {
+  if (sc->done) return;
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    const double zn = (double)z32[i];
+    if (!first) b += ri * z[i];
+    a += ri * zn;
+    z[i] = zn;
+  }
+  __shared__ double sh[32];
+  a = block_sum(a, sh);
+  __syncthreads();
+  b = block_sum(b, sh);
+  double part[2] = {a, b}, out[2];
+  const bool mx[2] = {false, false};
+  if (last_block_combine<2>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    if (!first) sc->beta = (out[0] - out[1]) / sc->rho;
+    sc->rho = out[0];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Chebyshev iteration for A z = r (A = level operator, D = its diagonal) on
 // the interval [lmin, lmax] of D^{-1} A (Saad, Iterative Methods, Alg. 12.1).
@@ -425,8 +454,16 @@ template sph_rt_status cheb_apply<float, float>(sph_rt *, const CsrView<float> &
                                                 float *, float *, float *, int, const ChebCoef *,
                                                 bool, const Scalars *, bool);
 
-// Preconditioner hook implemented by the AMG translation unit.
+// Preconditioner hooks implemented by the AMG translation unit.
 sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc);
+sph_rt_status amg_apply_to32(sph_rt *s, const double *r, const Scalars *sc);
+const float *amg_z32(const sph_rt *s);
+
+// The mixed form with the AMG preconditioner widens the V-cycle's FP32 result
+// inside the flexible inner product (no z_old copy).
+static bool fused_flex(const sph_rt *s) {
+  return s->cfg.precision == SPH_RT_MIXED && s->cfg.precond == SPH_RT_PRECOND_AMG;
+}
 
 // z = M^{-1} r followed by rho = (r, z) (and beta unless first).
 static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first) {
@@ -444,6 +481,13 @@ static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first
       if (rc) return rc;
       break;
     default:
+      if (fused_flex(s)) {
+        if ((rc = amg_apply_to32(s, s->r, s->sc))) return rc;
+        dot_rz_flex32_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->r, amg_z32(s), s->z, first,
+                                                           s->sc, s->partials);
+        SPH_LAUNCHED(s);
+        return SPH_RT_OK;
+      }
       rc = amg_apply(s, s->r, s->z, s->sc);
       if (rc) return rc;
       break;
@@ -553,7 +597,8 @@ __global__ void copy_vec_kernel(int64_t n, const double *src, double *dst, const
 
 // One CG iteration: x, r update and the convergence test, z = M^{-1} r, the
 // new direction and q = B p.  The flexible (mixed-precision) variant keeps the
-// previous z in z_old.  All launches are empty once `done` is set.
+// previous z in z_old (with the AMG preconditioner: in z itself until the fused
+// inner product widens the new one).  All launches are empty once `done` is set.
 sph_rt_status pcg_iteration(sph_rt *s) {
   CsrView<double> A = fine_view(s);
   const int gw = row_grid(s->num_sms, A.n, A.W, A.U);
@@ -562,7 +607,7 @@ sph_rt_status pcg_iteration(sph_rt *s) {
   update_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
                                               s->cfg.max_krylov, s->sc, s->partials);
   SPH_LAUNCHED(s);
-  if (s->cfg.precision == SPH_RT_MIXED) {
+  if (s->cfg.precision == SPH_RT_MIXED && !fused_flex(s)) {
     copy_vec_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->z, s->z_old, s->sc);
     SPH_LAUNCHED(s);
   }

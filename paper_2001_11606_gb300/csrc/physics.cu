@@ -104,50 +104,111 @@ __global__ void props_grad_kernel(Phys ph, int64_t n_int, const int64_t *nbr_ptr
   }
 }
 
-// a3, gradient part with precomputed pair geometry g_ij = V_j F_ij x_ij and
-// the slot whose E a neighbour carries (its own, or the copied particle's):
-// grad E_i = sum_j (E_j - E_i) g_ij.  W lanes per row, U entries in flight.
+// Gradient sums of one row by its W-lane group (a row-tile round): entries
+// beg + sub + j W, j < nmax (nmax warp-uniform; see row_dot_n), each adding
+// (E_j - E_i) g_ij to the three components.  Slots past the row's end add
+// fma(0, 0, g) = g.
 template <int W, int U>
-__global__ void props_grad_pre_kernel(Phys ph, int64_t n_int, const int64_t *nbr_ptr,
-                                      const int32_t *gcol, const double *gvx, const double *gvy,
-                                      const double *gvz, const double *E, const double *sigma,
-                                      double *R, double *lambda, double *D) {
-  const int sub = threadIdx.x % W;
-  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
-  for (int64_t wb = warp_first_group<W>(grp); wb < n_int; wb += ngrp) {
-    const int64_t i = wb + group_in_warp<W>(grp);
-    const bool active = i < n_int;
-    const double Ei = active ? E[i] : 0.0;
-    const int64_t beg = active ? nbr_ptr[i] : 0, end = active ? nbr_ptr[i + 1] : 0;
-    double gx = 0.0, gy = 0.0, gz = 0.0;
-    for (int64_t k = beg + sub; k < end; k += (int64_t)W * U) {
-      int32_t c[U];
-      double ax[U], ay[U], az[U];
+__device__ __forceinline__ Sum3 grad_row_n(int64_t beg, int64_t end, const int32_t *__restrict__ gcol,
+                                           const double *__restrict__ gvx,
+                                           const double *__restrict__ gvy,
+                                           const double *__restrict__ gvz,
+                                           const double *__restrict__ E, double Ei, int sub,
+                                           int nmax) {
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  int64_t k = beg + sub;
+  int j = 0;
+  for (; j + U <= nmax; j += U, k += (int64_t)W * U) {
+    int32_t c[U];
+    double ax[U], ay[U], az[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t kk = k + (int64_t)u * W;
-        const bool ok = kk < end;
-        c[u] = ok ? __ldg(gcol + kk) : -1;
-        ax[u] = ok ? __ldg(gvx + kk) : 0.0;
-        ay[u] = ok ? __ldg(gvy + kk) : 0.0;
-        az[u] = ok ? __ldg(gvz + kk) : 0.0;
-      }
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * W;
+      const bool ok = kk < end;
+      c[u] = ok ? __ldg(gcol + kk) : -1;
+      ax[u] = ok ? __ldg(gvx + kk) : 0.0;
+      ay[u] = ok ? __ldg(gvy + kk) : 0.0;
+      az[u] = ok ? __ldg(gvz + kk) : 0.0;
+    }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (c[u] < 0) continue;
-        const double dE = __ldg(E + c[u]) - Ei;
-        gx += dE * ax[u];
-        gy += dE * ay[u];
-        gz += dE * az[u];
+    for (int u = 0; u < U; ++u) {
+      if (c[u] < 0) continue;
+      const double dE = __ldg(E + c[u]) - Ei;
+      gx = fmadd(dE, ax[u], gx);
+      gy = fmadd(dE, ay[u], gy);
+      gz = fmadd(dE, az[u], gz);
+    }
+  }
+  const int rem = nmax - j;  // warp-uniform, < U
+  if (rem > 0) {
+    double dE[U], ax[U], ay[U], az[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * W;
+      const bool ok = kk < end;
+      const int32_t c = ok ? __ldg(gcol + kk) : -1;
+      ax[u] = ok ? __ldg(gvx + kk) : 0.0;
+      ay[u] = ok ? __ldg(gvy + kk) : 0.0;
+      az[u] = ok ? __ldg(gvz + kk) : 0.0;
+      dE[u] = c >= 0 ? __ldg(E + c) - Ei : 0.0;
+    }
+#pragma unroll 1
+    for (int u = 0; u < rem; ++u) {
+      gx = fmadd(dE[0], ax[0], gx);
+      gy = fmadd(dE[0], ay[0], gy);
+      gz = fmadd(dE[0], az[0], gz);
+#pragma unroll
+      for (int q = 0; q + 1 < U; ++q) {
+        dE[q] = dE[q + 1];
+        ax[q] = ax[q + 1];
+        ay[q] = ay[q + 1];
+        az[q] = az[q + 1];
       }
     }
-    gx = row_reduce<W>(gx);
-    gy = row_reduce<W>(gy);
-    gz = row_reduce<W>(gz);
-    if (active && sub == 0) {
+  }
+  return {gx, gy, gz};
+}
+
+// a3, gradient part with precomputed pair geometry g_ij = V_j F_ij x_ij and
+// the slot whose E a neighbour carries (its own, or the copied particle's):
+// grad E_i = sum_j (E_j - E_i) g_ij.  Row tiles (common.cuh): 32 rows per warp,
+// the row epilogue (|grad E|, R, the limiter, D) on all 32 lanes.
+// Resident blocks per SM the row-tile gradient and assembly kernels are
+// compiled for (80 registers: their rounds carry three sums and, at the end of
+// a row, up to U slots of pair data).
+constexpr int kPairMinBlocks = 3;
+
+template <int W, int U>
+__global__ void __launch_bounds__(kBlock, kPairMinBlocks)
+    props_grad_pre_kernel(Phys ph, int64_t n_int, const int64_t *nbr_ptr, const int32_t *gcol,
+                          const double *gvx, const double *gvy, const double *gvz,
+                          const double *E, const double *sigma, double *R, double *lambda,
+                          double *D) {
+  const int lane = threadIdx.x & 31, sub = lane % W, own = tile_own_row<W>(lane);
+  int64_t r0, r1;
+  warp_rows<W>(n_int, r0, r1);
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const bool active = own < rows;
+    int64_t b = 0, e = 0;
+    double Eo = 0.0;
+    if (active) {
+      b = nbr_ptr[i];
+      e = nbr_ptr[i + 1];
+      Eo = E[i];
+    }
+    const Sum3 g = tile_tree<W, 1, Sum3>(0, rows, sub, [&](int t) -> Sum3 {
+      const int64_t rb = __shfl_sync(0xffffffffu, b, t, W);
+      const int64_t re = __shfl_sync(0xffffffffu, e, t, W);
+      const double Ei = __shfl_sync(0xffffffffu, Eo, t, W);
+      return grad_row_n<W, U>(rb, re, gcol, gvx, gvy, gvz, E, Ei, sub,
+                              tile_nmax<W>(rb, re, sub));
+    });
+    if (active) {
+      const double gx = g.a, gy = g.b, gz = g.c;
       double gn = sqrt(gx * gx + gy * gy + gz * gz);
-      double Es = Ei > 1e-300 ? Ei : 1e-300;
+      double Es = Eo > 1e-300 ? Eo : 1e-300;
       double Ri = gn / (sigma[i] * Es);
       double lam = limiter_lambda(ph.limiter, ph.larsen_k, Ri);
       R[i] = Ri;
@@ -193,56 +254,118 @@ __global__ void props_copy_kernel(int64_t n_int, int64_t n, const int32_t *copys
   }
 }
 
-// a4: values of B for the step; W lanes per row, U entries in flight per lane.
+// Off-diagonal values of one row of B by its W-lane group (a row-tile round):
+// B_ij = G_ij (D_i + D_j) written for entries beg + sub + j W, j < nmax
+// (nmax warp-uniform), and this lane's sum of them.  Slots past the row's end
+// store nothing and add +0.
 template <int W, int U>
-__global__ void assemble_kernel(Phys ph, int64_t n_int, const int64_t *mat_ptr,
-                                const int32_t *mat_col, const double *mat_G, double *mat_val,
-                                const int64_t *gh_ptr, const int32_t *gh_slot, const double *gh_W,
-                                const double *V, const double *sigma, const double *f,
-                                const double *D, const double *E, double *diag,
-                                double *invdiag, double *gb, double *partials,
-                                unsigned *counter, double *gersh_out) {
-  // gersh_out = max_i sum_{j != i} |B_ij| / B_ii: the eigenvalues of D^{-1} B
-  // lie in [1 - gersh, 1 + gersh] (Gershgorin; B is symmetric, so real).
-  const int sub = threadIdx.x % W;
-  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
-  double gmax = 0.0;
-  for (int64_t wb = warp_first_group<W>(grp); wb < n_int; wb += ngrp) {
-    const int64_t i = wb + group_in_warp<W>(grp);
-    const bool active = i < n_int;
-    const double Di = active ? D[i] : 0.0;
-    const int64_t beg = active ? mat_ptr[i] : 0, end = active ? mat_ptr[i + 1] : 0;
-    double offsum = 0.0;
-    for (int64_t k = beg + sub; k < end; k += (int64_t)W * U) {
-      int32_t c[U];
-      double g[U];
+__device__ __forceinline__ double assemble_row_n(int64_t beg, int64_t end,
+                                                 const int32_t *__restrict__ mat_col,
+                                                 const double *__restrict__ mat_G,
+                                                 const double *__restrict__ D, double Di,
+                                                 double *__restrict__ mat_val, int sub, int nmax) {
+  double offsum = 0.0;
+  int64_t k = beg + sub;
+  int j = 0;
+  for (; j + U <= nmax; j += U, k += (int64_t)W * U) {
+    int32_t c[U];
+    double g[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t kk = k + (int64_t)u * W;
-        c[u] = kk < end ? __ldg(mat_col + kk) : -1;
-        g[u] = kk < end ? __ldg(mat_G + kk) : 0.0;
-      }
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * W;
+      c[u] = kk < end ? __ldg(mat_col + kk) : -1;
+      g[u] = kk < end ? __ldg(mat_G + kk) : 0.0;
+    }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (c[u] < 0) continue;
-        const double v = g[u] * (Di + __ldg(D + c[u]));
-        mat_val[k + (int64_t)u * W] = v;
+    for (int u = 0; u < U; ++u) {
+      if (c[u] < 0) continue;
+      const double v = g[u] * (Di + __ldg(D + c[u]));
+      mat_val[k + (int64_t)u * W] = v;
+      offsum += v;
+    }
+  }
+  const int rem = nmax - j;  // warp-uniform, < U
+  if (rem > 0) {
+    double g[U], dj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * W;
+      const int32_t c = kk < end ? __ldg(mat_col + kk) : -1;
+      g[u] = c >= 0 ? __ldg(mat_G + kk) : 0.0;
+      dj[u] = c >= 0 ? __ldg(D + c) : 0.0;
+    }
+#pragma unroll 1
+    for (int u = 0; u < rem; ++u, k += W) {
+      if (k < end) {
+        const double v = g[0] * (Di + dj[0]);
+        mat_val[k] = v;
         offsum += v;
       }
+#pragma unroll
+      for (int q = 0; q + 1 < U; ++q) {
+        g[q] = g[q + 1];
+        dj[q] = dj[q + 1];
+      }
     }
-    double wsum = 0.0, gbs = 0.0;
-    const int64_t gbeg = active ? gh_ptr[i] : 0, gend = active ? gh_ptr[i + 1] : 0;
-    for (int64_t k = gbeg + sub; k < gend; k += W) {
-      int32_t j = gh_slot[k];
-      double wk = -gh_W[k] * (Di + D[j]);
-      wsum += wk;
-      gbs += wk * E[j];
+  }
+  return offsum;
+}
+
+// a4: values of B for the step.  Row tiles (common.cuh): in each round a
+// W-lane group writes one row's off-diagonal values and sums them, then adds
+// up its Dirichlet-ghost couplings (few rows have any); the diagonal, its
+// inverse, the ghost right-hand side and the Gershgorin ratio are computed on
+// all 32 lanes.
+template <int W, int U>
+__global__ void __launch_bounds__(kBlock, kPairMinBlocks)
+    assemble_kernel(Phys ph, int64_t n_int, const int64_t *mat_ptr, const int32_t *mat_col,
+                    const double *mat_G, double *mat_val, const int64_t *gh_ptr,
+                    const int32_t *gh_slot, const double *gh_W, const double *V,
+                    const double *sigma, const double *f, const double *D, const double *E,
+                    double *diag, double *invdiag, double *gb, double *partials,
+                    unsigned *counter, double *gersh_out) {
+  // gersh_out = max_i sum_{j != i} |B_ij| / B_ii: the eigenvalues of D^{-1} B
+  // lie in [1 - gersh, 1 + gersh] (Gershgorin; B is symmetric, so real).
+  const int lane = threadIdx.x & 31, sub = lane % W, own = tile_own_row<W>(lane);
+  int64_t r0, r1;
+  warp_rows<W>(n_int, r0, r1);
+  double gmax = 0.0;
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const bool active = own < rows;
+    int64_t b = 0, e = 0, hb = 0, he = 0;
+    double Do = 0.0;
+    if (active) {
+      b = mat_ptr[i];
+      e = mat_ptr[i + 1];
+      hb = gh_ptr[i];
+      he = gh_ptr[i + 1];
+      Do = D[i];
     }
-    offsum = row_reduce<W>(offsum);
-    wsum = row_reduce<W>(wsum);
-    gbs = row_reduce<W>(gbs);
-    if (active && sub == 0) {
+    const Sum3 acc = tile_tree<W, 1, Sum3>(0, rows, sub, [&](int t) -> Sum3 {
+      const int64_t rb = __shfl_sync(0xffffffffu, b, t, W);
+      const int64_t re = __shfl_sync(0xffffffffu, e, t, W);
+      const int64_t gb0 = __shfl_sync(0xffffffffu, hb, t, W);
+      const int64_t ge0 = __shfl_sync(0xffffffffu, he, t, W);
+      const double Di = __shfl_sync(0xffffffffu, Do, t, W);
+      const double offsum = assemble_row_n<W, U>(rb, re, mat_col, mat_G, D, Di, mat_val, sub,
+                                                 tile_nmax<W>(rb, re, sub));
+      double wsum = 0.0, gbs = 0.0;
+      const int ng = tile_nmax<W>(gb0, ge0, sub);
+      for (int jj = 0; jj < ng; ++jj) {
+        const int64_t k = gb0 + sub + (int64_t)jj * W;
+        if (k < ge0) {
+          const int32_t j = gh_slot[k];
+          const double wk = -gh_W[k] * (Di + D[j]);
+          wsum += wk;
+          gbs += wk * E[j];
+        }
+      }
+      return {offsum, wsum, gbs};
+    });
+    if (active) {
+      const double offsum = acc.a, wsum = acc.b, gbs = acc.c;
       double d = V[i] * (1.0 / ph.dt + ph.c * sigma[i] * f[i] + wsum) - offsum;
       diag[i] = d;
       invdiag[i] = 1.0 / d;
@@ -549,7 +672,7 @@ sph_rt_status launch_properties(sph_rt *s, double dt) {
     }
     if (s->gvx) {
       RowShape sh = shape_for_mean(s->n_int ? (double)s->nnz_nbr / (double)s->n_int : 0.0);
-      int gr = grid_items(s, s->n_int, kBlock / sh.W);
+      int gr = row_grid_blocks(s->num_sms, s->n_int, sh.W, kPairMinBlocks);
       SPH_DISPATCH_SHAPE(sh.W, sh.U,
                          (props_grad_pre_kernel<W, U><<<gr, kBlock, 0, s->stream>>>(
                              ph, s->n_int, s->nbr_ptr, s->gcol, s->gvx, s->gvy, s->gvz, s->E,
@@ -574,7 +697,7 @@ sph_rt_status launch_properties(sph_rt *s, double dt) {
 sph_rt_status launch_assembly(sph_rt *s, double dt, double *gersh_out) {
   Phys ph = make_phys(s, dt);
   RowShape sh = shape_for_mean(s->n_int ? (double)s->nnz_mat / (double)s->n_int : 0.0);
-  int gr = grid_items(s, s->n_int, kBlock / sh.W);
+  int gr = row_grid_blocks(s->num_sms, s->n_int, sh.W, kPairMinBlocks);
   SPH_DISPATCH_SHAPE(sh.W, sh.U,
                      (assemble_kernel<W, U><<<gr, kBlock, 0, s->stream>>>(
                          ph, s->n_int, s->mat_ptr, s->mat_col, s->mat_G, s->mat_val, s->gh_ptr,
