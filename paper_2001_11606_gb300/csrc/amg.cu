@@ -457,7 +457,9 @@ __global__ void convert_kernel(int64_t n, const S *in, D *out) {
 // ---------------------------------------------------------------------------
 // V-cycle kernels
 // ---------------------------------------------------------------------------
-template <int W, int U, typename MT, typename VT>
+// PRE: load the row operands before the row sums (coarse levels) or after
+// them (finest level), as in cheb_step_body.
+template <int W, int U, typename MT, typename VT, bool PRE>
 __device__ __forceinline__ void resid_level_body(const CsrView<MT> &A, const VT *r, const VT *z,
                                                  VT *res, const Scalars *sc, int *wflag) {
   if (sc && sc->done) {
@@ -472,20 +474,53 @@ __device__ __forceinline__ void resid_level_body(const CsrView<MT> &A, const VT 
     const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
     const int64_t i = base + own;
     const bool active = own < rows;
+    VT ri = VT(0), dg = VT(0), zi = VT(0);
+    auto operands = [&]() {
+      ri = r[i];
+      dg = (VT)A.diag[i];
+      zi = z[i];
+    };
+    if (PRE && active) operands();
     const VT s = tile_row_sums<W, U, MT, VT>(base, rows, A.ptr, A.col, A.val, z);
-    if (active) res[i] = r[i] - fmadd((VT)A.diag[i], z[i], s);
+    if (active) {
+      if (!PRE) operands();
+      res[i] = ri - fmadd(dg, zi, s);
+    }
   }
 }
 // one body, two names: finest level vs coarse levels in profiles
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
+__global__ void __launch_bounds__(kBlock, kCoarseMinBlocks) resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
                                    const Scalars *sc, int *wflag) {
-  resid_level_body<W, U, MT, VT>(A, r, z, res, sc, wflag);
+  resid_level_body<W, U, MT, VT, true>(A, r, z, res, sc, wflag);
 }
 template <int W, int U, typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) fine_resid_level_kernel(CsrView<MT> A, const VT *r, const VT *z, VT *res,
                                         const Scalars *sc, int *wflag) {
-  resid_level_body<W, U, MT, VT>(A, r, z, res, sc, wflag);
+  resid_level_body<W, U, MT, VT, false>(A, r, z, res, sc, wflag);
+}
+
+// Sum of res over the members [m0, m1) of an aggregate, in member order.
+// Aggregates have ~6 members: 8 member indices are loaded before their
+// gathers, so an aggregate costs two dependent round trips instead of two per
+// member.
+template <typename VT>
+__device__ __forceinline__ VT aggregate_sum(int64_t m0, int64_t m1, const int32_t *agg_mem,
+                                            const VT *res) {
+  constexpr int G = 8;
+  VT acc = 0;
+  for (int64_t m = m0; m < m1; m += G) {
+    int32_t j[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) j[g] = m + g < m1 ? agg_mem[m + g] : -1;
+    VT v[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = j[g] >= 0 ? res[j[g]] : VT(0);
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (j[g] >= 0) acc += v[g];
+  }
+  return acc;
 }
 
 template <typename VT>
@@ -494,8 +529,7 @@ __global__ void restrict_kernel(int64_t nc, const int64_t *agg_ptr, const int32_
   if (sc && sc->done) return;
   for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < nc;
        I += (int64_t)gridDim.x * blockDim.x) {
-    VT acc = 0;
-    for (int64_t m = agg_ptr[I]; m < agg_ptr[I + 1]; ++m) acc += res[agg_mem[m]];
+    const VT acc = aggregate_sum(agg_ptr[I], agg_ptr[I + 1], agg_mem, res);
     rc[I] = acc;
   }
 }
@@ -510,8 +544,7 @@ __global__ void restrict_init_kernel(int64_t nc, const int64_t *agg_ptr, const i
   const double inv_theta = cf_c->inv_theta;
   for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < nc;
        I += (int64_t)gridDim.x * blockDim.x) {
-    VT acc = 0;
-    for (int64_t m = agg_ptr[I]; m < agg_ptr[I + 1]; ++m) acc += res[agg_mem[m]];
+    const VT acc = aggregate_sum(agg_ptr[I], agg_ptr[I + 1], agg_mem, res);
     rc[I] = acc;
     VT di = (VT)(inv_theta * (double)invdiag_c[I] * (double)acc);
     d_c[I] = di;
@@ -558,6 +591,13 @@ __device__ void coarse_cheb_body(const CsrView<MT> &A, const GT *r_g, GT *z_g, c
   int *ptr = col + nnz;
   const int64_t base = A.ptr[0];
   const double inv_theta = cf->inv_theta;
+  // the step coefficients, staged once: a global load per step would put an
+  // L2 round trip on the critical path of every step
+  __shared__ VT cs1[kChebMaxDeg], cs2[kChebMaxDeg];
+  for (int k = threadIdx.x; k < degree && k < kChebMaxDeg; k += blockDim.x) {
+    cs1[k] = (VT)cf->c1[k];
+    cs2[k] = (VT)cf->c2[k];
+  }
   for (int k = threadIdx.x; k < nnz; k += blockDim.x) {
     val[k] = (VT)A.val[base + k];
     col[k] = A.col[base + k];
@@ -575,7 +615,7 @@ __device__ void coarse_cheb_body(const CsrView<MT> &A, const GT *r_g, GT *z_g, c
   __syncthreads();
   VT *zin = zb0, *zout = zb1;
   for (int k = 1; k < degree; ++k) {
-    const VT c1 = (VT)cf->c1[k], c2 = (VT)cf->c2[k];
+    const VT c1 = cs1[k], c2 = cs2[k];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {  // thread per row: no shuffles
       // 8 column / value loads, then 8 gathers in flight, summed in entry order
       VT s = 0;
@@ -705,12 +745,15 @@ __global__ void ap_galerkin_target_kernel(int64_t n, const int64_t *ap_ptr, cons
 // First post-smoothing step of a level with the prolongation folded in:
 // z = z_pre + P e_c, res2 = res - (A P) e_c (= r - A z), d = c2 D^{-1} res2
 // (step 0 from a nonzero guess), z_out = z + d.  z_out may be z_pre.
-template <int W, int U, typename MT, typename VT>
+// DOT (finest level, smoother degree 1, where this is the V-cycle's last
+// sweep): also the preconditioned inner product of DotFuse over the new z.
+template <int W, int U, typename MT, typename VT, bool PRE, bool DOT>
 __device__ __forceinline__ void post_ap_body(int64_t n, const int64_t *ap_ptr,
                                              const int32_t *ap_col, const MT *ap_val,
                                              const int32_t *agg, const VT *ec, const VT *z_pre,
                                              const VT *res, const MT *invdiag, const ChebCoef *cf,
-                                             VT *d, VT *z_out, const Scalars *sc, int *wflag) {
+                                             VT *d, VT *z_out, const Scalars *sc, int *wflag,
+                                             const DotFuse &df) {
   if (sc && sc->done) {
     mark_work(wflag, 0);
     return;
@@ -720,19 +763,49 @@ __device__ __forceinline__ void post_ap_body(int64_t n, const int64_t *ap_ptr,
   const int own = tile_own_row<W>(threadIdx.x & 31);
   int64_t r0, r1;
   warp_rows<W>(n, r0, r1);
+  double da = 0.0, db = 0.0;  // (r, z) and (r, z_old) partials (DOT)
   for (int64_t base = r0; base < r1; base += 32) {
     const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
     const int64_t i = base + own;
     const bool active = own < rows;
+    VT zp = VT(0), rs = VT(0), idg = VT(0), pe = VT(0);
+    auto operands = [&]() {
+      zp = z_pre[i];
+      rs = res[i];
+      idg = (VT)invdiag[i];
+      const int32_t a = agg[i];
+      pe = a >= 0 ? ec[a] : VT(0);
+    };
+    if (PRE && active) operands();
     const VT s = tile_row_sums<W, U, MT, VT>(base, rows, ap_ptr, ap_col, ap_val, ec);
     if (active) {
-      const VT zp = z_pre[i], rs = res[i], idg = (VT)invdiag[i];
-      const int32_t a = agg[i];
-      const VT pe = a >= 0 ? ec[a] : VT(0);
+      if (!PRE) operands();
       const VT zi = zp + pe;
       const VT di = (c2 * idg) * (rs - s);
+      const VT zo = zi + di;
       d[i] = di;
-      z_out[i] = zi + di;
+      z_out[i] = zo;
+      if (DOT) {
+        const double ri = df.r[i], zn = (double)zo;
+        if (df.flex) {
+          if (!df.first) db += ri * df.z64[i];
+          df.z64[i] = zn;
+        }
+        da += ri * zn;
+      }
+    }
+  }
+  if (DOT) {
+    __shared__ double sh[32];
+    da = block_sum(da, sh);
+    __syncthreads();
+    db = block_sum(db, sh);
+    double part[2] = {da, db}, out[2];
+    const bool mx[2] = {false, false};
+    if (last_block_combine<2>(part, df.partials, &df.sc->counter, out, mx) && threadIdx.x == 0) {
+      Scalars *w = df.sc;
+      if (!df.first) w->beta = (df.flex ? out[0] - out[1] : out[0]) / w->rho;
+      w->rho = out[0];
     }
   }
 }
@@ -743,17 +816,26 @@ __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U))
                         const MT *ap_val, const int32_t *agg, const VT *ec, const VT *z_pre,
                         const VT *res, const MT *invdiag, const ChebCoef *cf, VT *d, VT *z_out,
                         const Scalars *sc, int *wflag) {
-  post_ap_body<W, U, MT, VT>(n, ap_ptr, ap_col, ap_val, agg, ec, z_pre, res, invdiag, cf, d,
-                             z_out, sc, wflag);
+  post_ap_body<W, U, MT, VT, false, false>(n, ap_ptr, ap_col, ap_val, agg, ec, z_pre, res,
+                                           invdiag, cf, d, z_out, sc, wflag, DotFuse{});
 }
 template <int W, int U, typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U))
+    fine_post_ap_dot_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col,
+                            const MT *ap_val, const int32_t *agg, const VT *ec, const VT *z_pre,
+                            const VT *res, const MT *invdiag, const ChebCoef *cf, VT *d,
+                            VT *z_out, const Scalars *sc, int *wflag, const DotFuse df) {
+  post_ap_body<W, U, MT, VT, false, true>(n, ap_ptr, ap_col, ap_val, agg, ec, z_pre, res, invdiag,
+                                          cf, d, z_out, sc, wflag, df);
+}
+template <int W, int U, typename MT, typename VT>
+__global__ void __launch_bounds__(kBlock, kCoarseMinBlocks)
     post_ap_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col, const MT *ap_val,
                    const int32_t *agg, const VT *ec, const VT *z_pre, const VT *res,
                    const MT *invdiag, const ChebCoef *cf, VT *d, VT *z_out, const Scalars *sc,
                    int *wflag) {
-  post_ap_body<W, U, MT, VT>(n, ap_ptr, ap_col, ap_val, agg, ec, z_pre, res, invdiag, cf, d,
-                             z_out, sc, wflag);
+  post_ap_body<W, U, MT, VT, true, false>(n, ap_ptr, ap_col, ap_val, agg, ec, z_pre, res, invdiag,
+                                          cf, d, z_out, sc, wflag, DotFuse{});
 }
 
 // ---------------------------------------------------------------------------
@@ -1462,7 +1544,8 @@ static void tail_setup(sph_rt *s) {
 
 template <typename T>
 static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars *sc,
-                            bool init_done = false) {
+                            bool init_done = false, const DotFuse *df = nullptr,
+                            bool *dot_done = nullptr) {
   using LV = LevelVecs<T>;
   if (s->tail_level > 0 && l == (size_t)s->tail_level) return launch_tail<T>(s, l, r, z, sc);
   SphLevel *L = s->levels[l];
@@ -1504,7 +1587,8 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
   // when init_done)
   if ((rc = cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, true, sc, init_done)))
     return rc;
-  const int gw = row_grid(s->num_sms, L->n, A.W, A.U);
+  const int gw = l == 0 ? row_grid(s->num_sms, L->n, A.W, A.U)
+                        : row_grid_blocks(s->num_sms, L->n, A.W, kCoarseMinBlocks);
   T *res = LV::res(L);
   // fine-level residual sweeps are timed with the other fine SpMV-class kernels;
   // per row: rowptr, diag, r, z, res
@@ -1542,9 +1626,18 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
     T *bufs[2] = {z, LV::t(L)};
     const int w0 = (deg - 1) % 2;
     const RowShape sh = shape_for_mean(L->n ? (double)L->nnz_ap / (double)L->n : 0.0);
-    const int gp = row_grid(s->num_sms, L->n, sh.W, sh.U);
+    const int gp = l == 0 ? row_grid(s->num_sms, L->n, sh.W, sh.U)
+                          : row_grid_blocks(s->num_sms, L->n, sh.W, kCoarseMinBlocks);
     int *wf = l == 0 ? timing_begin(s) : nullptr;
-    if (l == 0)
+    // with degree 1 this sweep is the V-cycle's last: the inner product rides along
+    const bool dot = l == 0 && df && dot_done && deg == 1;
+    if (dot) {
+      SPH_DISPATCH_SHAPE(sh.W, sh.U,
+                         (fine_post_ap_dot_kernel<W, U, T, T><<<gp, kBlock, 0, s->stream>>>(
+                             L->n, L->ap_ptr, L->ap_col, LV::ap(L), L->agg, LV::z(C), z, res,
+                             A.invdiag, cf, LV::d(L), bufs[w0], sc, wf, *df)));
+      *dot_done = true;
+    } else if (l == 0)
       SPH_DISPATCH_SHAPE(sh.W, sh.U,
                          (fine_post_ap_kernel<W, U, T, T><<<gp, kBlock, 0, s->stream>>>(
                              L->n, L->ap_ptr, L->ap_col, LV::ap(L), L->agg, LV::z(C), z, res,
@@ -1556,11 +1649,13 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
                              A.invdiag, cf, LV::d(L), bufs[w0], sc, nullptr)));
     SPH_LAUNCHED(s);
     // A P entry: column + value; per row: ap_ptr, agg, the coarse entry of P e_c,
-    // z_pre, res, 1/diag, d, z_out
+    // z_pre, res, 1/diag, d, z_out; with the inner product also r (and, flexible,
+    // the FP64 z read and written)
     if (l == 0)
       timing_end(s,
                  (4.0 + sizeof(T)) * (double)L->nnz_ap +
-                     (12.0 + 6.0 * sizeof(T)) * (double)L->n,
+                     (12.0 + 6.0 * sizeof(T) + (dot ? (df->flex ? 24.0 : 8.0) : 0.0)) *
+                         (double)L->n,
                  kTimedPost);
     return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, false, sc, true);
   }
@@ -1571,29 +1666,56 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
 
 // Mixed form without the last conversion: r is rounded to FP32 and the FP32
 // V-cycle leaves z in levels[0]->z32 (amg_z32), for a caller that widens it
-// itself (the fused flexible-CG inner product).
-sph_rt_status amg_apply_to32(sph_rt *s, const double *r, const Scalars *sc) {
+// itself (the fused flexible-CG inner product).  init_done: r32 and the finest
+// level's smoother start were written by the CG update.
+sph_rt_status amg_apply_to32(sph_rt *s, const double *r, const Scalars *sc, bool init_done,
+                             const DotFuse *df, bool *dot_done) {
   if (s->levels.empty()) return set_error(s, SPH_RT_ESTATE, "AMG hierarchy not set up");
   SphLevel *L0 = s->levels[0];
-  convert_kernel<double, float><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, r, L0->r32);
-  SPH_LAUNCHED(s);
-  return vcycle<float>(s, 0, L0->r32, L0->z32, sc);
+  if (!init_done) {
+    convert_kernel<double, float><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, r,
+                                                                                    L0->r32);
+    SPH_LAUNCHED(s);
+  }
+  return vcycle<float>(s, 0, L0->r32, L0->z32, sc, init_done, df, dot_done);
 }
 const float *amg_z32(const sph_rt *s) { return s->levels.empty() ? nullptr : s->levels[0]->z32; }
 
-sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc) {
+// The finest level's zero-guess smoother start for the CG update to write
+// (FineInit): in FP64 into the preconditioner output z (or the ping-pong
+// buffer the start goes to), in FP32 into the level's FP32 vectors together
+// with the narrowed residual.  False where the V-cycle takes no such start
+// (a single level: the finest level is then the coarsest).
+bool amg_fine_init(sph_rt *s, FineInit<double> *f64, FineInit<float> *f32) {
+  if (s->levels.size() < 2) return false;
+  SphLevel *L0 = s->levels[0];
+  const int w0 = (s->cfg.cheb_degree - 1) % 2;  // cheb_apply's first write: bufs[w0]
+  const ChebCoef *cf = s->cheb_slots + 1;
+  if (s->cfg.precision == SPH_RT_MIXED) {
+    *f32 = {L0->r32, L0->invdiag32, cf, L0->d32, w0 == 0 ? L0->z32 : L0->t32};
+  } else {
+    *f64 = {nullptr, L0->invdiag, cf, L0->d, w0 == 0 ? s->z : L0->t};
+  }
+  return true;
+}
+
+sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc, bool init_done,
+                        const DotFuse *df, bool *dot_done) {
   if (s->levels.empty()) return set_error(s, SPH_RT_ESTATE, "AMG hierarchy not set up");
   if (s->cfg.precision == SPH_RT_MIXED) {
     SphLevel *L0 = s->levels[0];
-    convert_kernel<double, float><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, r, L0->r32);
-    SPH_LAUNCHED(s);
-    sph_rt_status rc = vcycle<float>(s, 0, L0->r32, L0->z32, sc);
+    if (!init_done) {
+      convert_kernel<double, float><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, r,
+                                                                                      L0->r32);
+      SPH_LAUNCHED(s);
+    }
+    sph_rt_status rc = vcycle<float>(s, 0, L0->r32, L0->z32, sc, init_done);
     if (rc) return rc;
     convert_kernel<float, double><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, L0->z32, z);
     SPH_LAUNCHED(s);
     return SPH_RT_OK;
   }
-  return vcycle<double>(s, 0, r, z, sc);
+  return vcycle<double>(s, 0, r, z, sc, init_done, df, dot_done);
 }
 
 // Launch-relevant layout of the hierarchy (sizes, shapes and every buffer the

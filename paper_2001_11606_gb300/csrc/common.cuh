@@ -34,6 +34,10 @@ constexpr int kMaxRedBlocks = 2048;  // upper bound on blocks of a reducing kern
 // loads in flight per lane, 4 blocks (64 registers) with U = 8.  Their grids
 // never exceed this many blocks per SM (row_grid), so one wave covers all rows.
 __host__ __device__ constexpr int sweep_min_blocks(int U) { return U >= 8 ? 4 : 5; }
+// The coarse levels' sweeps (a few thousand to a few tens of thousands of
+// L2-resident rows: latency-bound, not throughput-bound) also load their row
+// operands before the row sums, which takes them to 64 registers.
+constexpr int kCoarseMinBlocks = 4;
 
 // --------------------------------------------------------------------------
 // Scalars of one Krylov solve and of the outer loop, kept on the device so
@@ -433,6 +437,31 @@ __host__ __device__ inline void cheb_coefficients(int degree, double lo, double 
     rho0 = rho1;
   }
 }
+
+// Fusions at the two ends of an AMG preconditioner application on the finest
+// level (launches saved per CG iteration).
+// FineInit: the zero-guess smoother start of the finest level
+// (cheb_init_zero_kernel's arithmetic) fused into the CG update, in the
+// V-cycle's precision IT; r_lo receives the narrowed residual when the V-cycle
+// runs in FP32 (else nullptr).  d == nullptr: no fusion.
+template <typename IT>
+struct FineInit {
+  IT *r_lo;
+  const IT *invdiag;
+  const ChebCoef *cf;
+  IT *d, *z;
+};
+// DotFuse: the preconditioned inner product rho = (r, z) and beta -- for the
+// flexible variant (r, z) - (r, z_old) with z widened from the FP32 V-cycle
+// into z64, whose old contents are z_old -- fused into the last V-cycle sweep.
+struct DotFuse {
+  int first;  // first CG inner product (no beta)
+  int flex;   // flexible (mixed) variant
+  const double *r;
+  double *z64;
+  Scalars *sc;
+  double *partials;
+};
 
 // Chebyshev coefficient slots of a handle (device array): slot 0 belongs to
 // the fine-level Chebyshev preconditioner, slot 1 + l to AMG level l (its

@@ -117,11 +117,17 @@ __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) spmv_pq_kernel(Cs
   }
 }
 
-// x += alpha p;  r -= alpha q;  rnorm2 = ||r / V||^2;  convergence test.
+// x += alpha p;  r -= alpha q;  rnorm2 = ||r / V||^2;  convergence test; and,
+// with fi.d set, the finest level's zero-guess smoother start on the new r
+// (FineInit).  The start is also written when this iteration converges; the
+// V-cycle's launches then return at once and nothing reads it.
+template <typename IT>
 __global__ void update_kernel(int64_t n, double *x, double *r, const double *p, const double *q,
-                              const double *invV, int maxit, Scalars *sc, double *partials) {
+                              const double *invV, int maxit, Scalars *sc, double *partials,
+                              FineInit<IT> fi) {
   if (sc->done) return;
   const double alpha = sc->alpha;
+  const double inv_theta = fi.d ? fi.cf->inv_theta : 0.0;
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -130,6 +136,13 @@ __global__ void update_kernel(int64_t n, double *x, double *r, const double *p, 
     r[i] = ri;
     double ru = ri * invV[i];
     acc += ru * ru;
+    if (fi.d) {
+      const IT rv = (IT)ri;
+      if (fi.r_lo) fi.r_lo[i] = rv;
+      const IT di = (IT)(inv_theta * (double)fi.invdiag[i] * (double)rv);
+      fi.d[i] = di;
+      fi.z[i] = di;
+    }
   }
   __shared__ double sh[32];
   acc = block_sum(acc, sh);
@@ -259,7 +272,9 @@ __global__ void cheb_init_zero_kernel(int64_t n, const VT *r, const MT *invdiag,
 }
 
 
-template <int W, int U, typename MT, typename VT>
+// PRE: load the row operands before the row sums (coarse levels: shorter
+// dependent chain) or after them (finest level: fewer registers, more warps).
+template <int W, int U, typename MT, typename VT, bool PRE>
 __device__ __forceinline__ void cheb_step_body(const CsrView<MT> &A, const VT *r, const VT *z_in,
                                                VT *z_out, VT *d, const ChebCoef *cf, int k,
                                                const Scalars *sc, int *wflag) {
@@ -278,10 +293,18 @@ __device__ __forceinline__ void cheb_step_body(const CsrView<MT> &A, const VT *r
     const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
     const int64_t i = base + own;
     const bool active = own < rows;
+    VT ri = VT(0), zi = VT(0), dg = VT(0), idg = VT(0), dold = VT(0);
+    auto operands = [&]() {
+      ri = r[i];
+      zi = z_in[i];
+      dg = (VT)A.diag[i];
+      idg = (VT)A.invdiag[i];
+      if (k > 0) dold = d[i];  // the first step must not read d
+    };
+    if (PRE && active) operands();
     const VT s = tile_row_sums<W, U, MT, VT>(base, rows, A.ptr, A.col, A.val, z_in);
     if (active) {
-      const VT ri = r[i], zi = z_in[i], dg = (VT)A.diag[i], idg = (VT)A.invdiag[i];
-      const VT dold = k > 0 ? d[i] : VT(0);  // the first step must not read d
+      if (!PRE) operands();
       VT res = ri - fmadd(dg, zi, s);
       VT di = (vc2 * idg) * res;
       if (k > 0) di = fmadd(vc1, dold, di);
@@ -293,15 +316,15 @@ __device__ __forceinline__ void cheb_step_body(const CsrView<MT> &A, const VT *r
 // The same sweep under two names, so that profiles separate the finest
 // level (HBM-streamed operator) from the coarse levels (L2-resident).
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
+__global__ void __launch_bounds__(kBlock, kCoarseMinBlocks) cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out, VT *d,
                                  const ChebCoef *cf, int k, const Scalars *sc, int *wflag) {
-  cheb_step_body<W, U, MT, VT>(A, r, z_in, z_out, d, cf, k, sc, wflag);
+  cheb_step_body<W, U, MT, VT, true>(A, r, z_in, z_out, d, cf, k, sc, wflag);
 }
 template <int W, int U, typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) fine_cheb_step_kernel(CsrView<MT> A, const VT *r, const VT *z_in, VT *z_out,
                                       VT *d, const ChebCoef *cf, int k, const Scalars *sc,
                                       int *wflag) {
-  cheb_step_body<W, U, MT, VT>(A, r, z_in, z_out, d, cf, k, sc, wflag);
+  cheb_step_body<W, U, MT, VT, false>(A, r, z_in, z_out, d, cf, k, sc, wflag);
 }
 
 // ---------------------------------------------------------------------------
@@ -401,10 +424,11 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
   if (degree < 1) degree = 1;
   if (degree > kChebMaxDeg) degree = kChebMaxDeg;
   int g = grid_cap(s, A.n, kBlock);
-  int gw = row_grid(s->num_sms, A.n, A.W, A.U);
   // fine-level sweeps are timed with the other fine SpMV-class kernels; per row:
   // rowptr, diag, 1/diag, r, z_in, z_out, d r/w (vectors of type VT)
   const bool fine = A.ptr == s->mat_ptr;
+  const int gw = fine ? row_grid(s->num_sms, A.n, A.W, A.U)
+                      : row_grid_blocks(s->num_sms, A.n, A.W, kCoarseMinBlocks);
   const double bytes = spmv_class_bytes(A, 8 + 2 * (int)sizeof(MT) + 5 * (int)sizeof(VT));
   auto step = [&](const VT *zin, VT *zout, int k) -> sph_rt_status {
     int *wf = fine ? timing_begin(s) : nullptr;
@@ -454,10 +478,16 @@ template sph_rt_status cheb_apply<float, float>(sph_rt *, const CsrView<float> &
                                                 float *, float *, float *, int, const ChebCoef *,
                                                 bool, const Scalars *, bool);
 
-// Preconditioner hooks implemented by the AMG translation unit.
-sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc);
-sph_rt_status amg_apply_to32(sph_rt *s, const double *r, const Scalars *sc);
+// Preconditioner hooks implemented by the AMG translation unit.  init_done:
+// the finest level's smoother start was written by the CG update (amg_fine_init);
+// df: fuse the inner product into the last sweep where the V-cycle allows it
+// (*dot_done tells whether it did).
+sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc, bool init_done,
+                        const DotFuse *df, bool *dot_done);
+sph_rt_status amg_apply_to32(sph_rt *s, const double *r, const Scalars *sc, bool init_done,
+                             const DotFuse *df, bool *dot_done);
 const float *amg_z32(const sph_rt *s);
+bool amg_fine_init(sph_rt *s, FineInit<double> *f64, FineInit<float> *f32);
 
 // The mixed form with the AMG preconditioner widens the V-cycle's FP32 result
 // inside the flexible inner product (no z_old copy).
@@ -465,8 +495,10 @@ static bool fused_flex(const sph_rt *s) {
   return s->cfg.precision == SPH_RT_MIXED && s->cfg.precond == SPH_RT_PRECOND_AMG;
 }
 
-// z = M^{-1} r followed by rho = (r, z) (and beta unless first).
-static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first) {
+// z = M^{-1} r followed by rho = (r, z) (and beta unless first).  init_done:
+// the update kernel has made the AMG finest level's smoother start.
+static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first,
+                                  bool init_done = false) {
   int g = grid_cap(s, A.n, kBlock);
   sph_rt_status rc;
   switch (s->cfg.precond) {
@@ -480,17 +512,22 @@ static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first
                                       s->cheb_slots, true, s->sc, false);
       if (rc) return rc;
       break;
-    default:
+    default: {
+      const DotFuse df = {first, fused_flex(s) ? 1 : 0, s->r, s->z, s->sc, s->partials};
+      bool dot_done = false;
       if (fused_flex(s)) {
-        if ((rc = amg_apply_to32(s, s->r, s->sc))) return rc;
-        dot_rz_flex32_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->r, amg_z32(s), s->z, first,
-                                                           s->sc, s->partials);
-        SPH_LAUNCHED(s);
+        if ((rc = amg_apply_to32(s, s->r, s->sc, init_done, &df, &dot_done))) return rc;
+        if (!dot_done) {
+          dot_rz_flex32_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->r, amg_z32(s), s->z, first,
+                                                             s->sc, s->partials);
+          SPH_LAUNCHED(s);
+        }
         return SPH_RT_OK;
       }
-      rc = amg_apply(s, s->r, s->z, s->sc);
-      if (rc) return rc;
+      if ((rc = amg_apply(s, s->r, s->z, s->sc, init_done, &df, &dot_done))) return rc;
+      if (dot_done) return SPH_RT_OK;
       break;
+    }
   }
   if (s->cfg.precision == SPH_RT_MIXED) {
     dot_rz_flex_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->r, s->z, s->z_old, first, s->sc,
@@ -604,14 +641,21 @@ sph_rt_status pcg_iteration(sph_rt *s) {
   const int gw = row_grid(s->num_sms, A.n, A.W, A.U);
   const int g = grid_cap(s, A.n, kBlock);
   sph_rt_status rc;
-  update_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
-                                              s->cfg.max_krylov, s->sc, s->partials);
+  FineInit<double> f64 = {};
+  FineInit<float> f32 = {};
+  const bool init = s->cfg.precond == SPH_RT_PRECOND_AMG && amg_fine_init(s, &f64, &f32);
+  if (f32.d)
+    update_kernel<float><<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
+                                                      s->cfg.max_krylov, s->sc, s->partials, f32);
+  else
+    update_kernel<double><<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
+                                                       s->cfg.max_krylov, s->sc, s->partials, f64);
   SPH_LAUNCHED(s);
   if (s->cfg.precision == SPH_RT_MIXED && !fused_flex(s)) {
     copy_vec_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->z, s->z_old, s->sc);
     SPH_LAUNCHED(s);
   }
-  if ((rc = precondition(s, A, 0))) return rc;
+  if ((rc = precondition(s, A, 0, init))) return rc;
   int *wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
                      (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->z, s->q, s->p, 0,
