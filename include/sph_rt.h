@@ -96,6 +96,10 @@ typedef struct {
   int32_t graphs;       /* 1: run each step's outer loop as one CUDA graph with conditional
                            WHILE nodes (no host round trip per iteration); ignored while
                            kernel_timing = 1, which needs per-launch events */
+  int32_t pdl;          /* 1: launch the Krylov iteration's kernels with programmatic
+                           dependent launch (a kernel's blocks are scheduled while its
+                           predecessor drains; each waits for the predecessor's results before
+                           touching them), 0: ordinary stream order.  Same results either way */
   int32_t device;       /* CUDA device ordinal */
   void *stream;         /* cudaStream_t to run on (borrowed); NULL = library-owned stream */
 } sph_rt_config;

@@ -449,6 +449,7 @@ __global__ void gersh_kernel(int64_t n, const int64_t *ptr, const double *val, c
 
 template <typename S, typename D>
 __global__ void convert_kernel(int64_t n, const S *in, D *out) {
+  pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (D)in[i];
@@ -462,6 +463,7 @@ __global__ void convert_kernel(int64_t n, const S *in, D *out) {
 template <int W, int U, typename MT, typename VT, bool PRE>
 __device__ __forceinline__ void resid_level_body(const CsrView<MT> &A, const VT *r, const VT *z,
                                                  VT *res, const Scalars *sc, int *wflag) {
+  pdl_wait();
   if (sc && sc->done) {
     mark_work(wflag, 0);
     return;
@@ -526,6 +528,7 @@ __device__ __forceinline__ VT aggregate_sum(int64_t m0, int64_t m1, const int32_
 template <typename VT>
 __global__ void restrict_kernel(int64_t nc, const int64_t *agg_ptr, const int32_t *agg_mem,
                                 const VT *res, VT *rc, const Scalars *sc) {
+  pdl_wait();
   if (sc && sc->done) return;
   for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < nc;
        I += (int64_t)gridDim.x * blockDim.x) {
@@ -540,6 +543,7 @@ template <typename MT, typename VT>
 __global__ void restrict_init_kernel(int64_t nc, const int64_t *agg_ptr, const int32_t *agg_mem,
                                      const VT *res, VT *rc, const MT *invdiag_c,
                                      const ChebCoef *cf_c, VT *d_c, VT *z_c, const Scalars *sc) {
+  pdl_wait();
   if (sc && sc->done) return;
   const double inv_theta = cf_c->inv_theta;
   for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < nc;
@@ -555,6 +559,7 @@ __global__ void restrict_init_kernel(int64_t nc, const int64_t *agg_ptr, const i
 template <typename VT>
 __global__ void prolong_kernel(int64_t n, const int32_t *agg, const VT *zc, VT *z,
                                const Scalars *sc) {
+  pdl_wait();
   if (sc && sc->done) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -651,6 +656,7 @@ template <typename MT, typename VT, typename GT>
 __global__ void __launch_bounds__(1024) coarse_cheb_kernel(CsrView<MT> A, const GT *r_g, GT *z_g,
                                                            const ChebCoef *cf, int degree,
                                                            const Scalars *sc) {
+  pdl_wait();
   if (sc && sc->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   coarse_cheb_body<MT, VT, GT>(A, r_g, z_g, cf, degree, smem_raw);
@@ -754,6 +760,7 @@ __device__ __forceinline__ void post_ap_body(int64_t n, const int64_t *ap_ptr,
                                              const VT *res, const MT *invdiag, const ChebCoef *cf,
                                              VT *d, VT *z_out, const Scalars *sc, int *wflag,
                                              const DotFuse &df) {
+  pdl_wait();
   if (sc && sc->done) {
     mark_work(wflag, 0);
     return;
@@ -1574,9 +1581,9 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
         s->coarse_smem_optin |= bit;
       }
       if (f32)
-        coarse_cheb_kernel<T, float, T><<<1, 1024, smem, s->stream>>>(A, r, z, cf, cdeg, sc);
+        pdl_launch(s, coarse_cheb_kernel<T, float, T>, 1, 1024, smem, A, r, z, cf, cdeg, sc);
       else
-        coarse_cheb_kernel<T, T, T><<<1, 1024, smem, s->stream>>>(A, r, z, cf, cdeg, sc);
+        pdl_launch(s, coarse_cheb_kernel<T, T, T>, 1, 1024, smem, A, r, z, cf, cdeg, sc);
       SPH_LAUNCHED(s);
       return SPH_RT_OK;
     }
@@ -1595,11 +1602,11 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
   int *wf = l == 0 ? timing_begin(s) : nullptr;
   if (l == 0)
     SPH_DISPATCH_SHAPE(A.W, A.U,
-                       (fine_resid_level_kernel<W, U, T, T><<<gw, kBlock, 0, s->stream>>>(
+                       (pdl_launch(s, fine_resid_level_kernel<W, U, T, T>, gw, kBlock, 0,
                            A, r, z, res, sc, wf)));
   else
     SPH_DISPATCH_SHAPE(A.W, A.U,
-                       (resid_level_kernel<W, U, T, T><<<gw, kBlock, 0, s->stream>>>(A, r, z, res,
+                       (pdl_launch(s, resid_level_kernel<W, U, T, T>, gw, kBlock, 0, A, r, z, res,
                                                                                       sc, wf)));
   SPH_LAUNCHED(s);
   if (l == 0)
@@ -1612,11 +1619,11 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
   if (fuse) {
     const int wc = (deg - 1) % 2;  // cheb_apply's first write goes to bufs[wc]
     T *zc_first = wc == 0 ? LV::z(C) : LV::t(C);
-    restrict_init_kernel<T, T><<<gcap(s, C->n, kBlock), kBlock, 0, s->stream>>>(
+    pdl_launch(s, restrict_init_kernel<T, T>, gcap(s, C->n, kBlock), kBlock, 0,
         C->n, L->agg_ptr, L->agg_mem, res, LV::r(C), LV::view(C).invdiag,
         s->cheb_slots + 1 + (l + 1), LV::d(C), zc_first, sc);
   } else {
-    restrict_kernel<T><<<gcap(s, C->n, kBlock), kBlock, 0, s->stream>>>(
+    pdl_launch(s, restrict_kernel<T>, gcap(s, C->n, kBlock), kBlock, 0,
         C->n, L->agg_ptr, L->agg_mem, res, LV::r(C), sc);
   }
   SPH_LAUNCHED(s);
@@ -1633,18 +1640,18 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
     const bool dot = l == 0 && df && dot_done && deg == 1;
     if (dot) {
       SPH_DISPATCH_SHAPE(sh.W, sh.U,
-                         (fine_post_ap_dot_kernel<W, U, T, T><<<gp, kBlock, 0, s->stream>>>(
+                         (pdl_launch(s, fine_post_ap_dot_kernel<W, U, T, T>, gp, kBlock, 0,
                              L->n, L->ap_ptr, L->ap_col, LV::ap(L), L->agg, LV::z(C), z, res,
                              A.invdiag, cf, LV::d(L), bufs[w0], sc, wf, *df)));
       *dot_done = true;
     } else if (l == 0)
       SPH_DISPATCH_SHAPE(sh.W, sh.U,
-                         (fine_post_ap_kernel<W, U, T, T><<<gp, kBlock, 0, s->stream>>>(
+                         (pdl_launch(s, fine_post_ap_kernel<W, U, T, T>, gp, kBlock, 0,
                              L->n, L->ap_ptr, L->ap_col, LV::ap(L), L->agg, LV::z(C), z, res,
                              A.invdiag, cf, LV::d(L), bufs[w0], sc, wf)));
     else
       SPH_DISPATCH_SHAPE(sh.W, sh.U,
-                         (post_ap_kernel<W, U, T, T><<<gp, kBlock, 0, s->stream>>>(
+                         (pdl_launch(s, post_ap_kernel<W, U, T, T>, gp, kBlock, 0,
                              L->n, L->ap_ptr, L->ap_col, LV::ap(L), L->agg, LV::z(C), z, res,
                              A.invdiag, cf, LV::d(L), bufs[w0], sc, nullptr)));
     SPH_LAUNCHED(s);
@@ -1659,7 +1666,7 @@ static sph_rt_status vcycle(sph_rt *s, size_t l, const T *r, T *z, const Scalars
                  kTimedPost);
     return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, false, sc, true);
   }
-  prolong_kernel<T><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(L->n, L->agg, LV::z(C), z, sc);
+  pdl_launch(s, prolong_kernel<T>, gcap(s, L->n, kBlock), kBlock, 0, L->n, L->agg, LV::z(C), z, sc);
   SPH_LAUNCHED(s);
   return cheb_apply<T, T>(s, A, r, z, LV::d(L), LV::t(L), deg, cf, false, sc);
 }
@@ -1673,7 +1680,7 @@ sph_rt_status amg_apply_to32(sph_rt *s, const double *r, const Scalars *sc, bool
   if (s->levels.empty()) return set_error(s, SPH_RT_ESTATE, "AMG hierarchy not set up");
   SphLevel *L0 = s->levels[0];
   if (!init_done) {
-    convert_kernel<double, float><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, r,
+    pdl_launch(s, convert_kernel<double, float>, gcap(s, L0->n, kBlock), kBlock, 0, L0->n, r,
                                                                                     L0->r32);
     SPH_LAUNCHED(s);
   }
@@ -1705,13 +1712,13 @@ sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc
   if (s->cfg.precision == SPH_RT_MIXED) {
     SphLevel *L0 = s->levels[0];
     if (!init_done) {
-      convert_kernel<double, float><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, r,
+      pdl_launch(s, convert_kernel<double, float>, gcap(s, L0->n, kBlock), kBlock, 0, L0->n, r,
                                                                                       L0->r32);
       SPH_LAUNCHED(s);
     }
     sph_rt_status rc = vcycle<float>(s, 0, L0->r32, L0->z32, sc, init_done);
     if (rc) return rc;
-    convert_kernel<float, double><<<gcap(s, L0->n, kBlock), kBlock, 0, s->stream>>>(L0->n, L0->z32, z);
+    pdl_launch(s, convert_kernel<float, double>, gcap(s, L0->n, kBlock), kBlock, 0, L0->n, L0->z32, z);
     SPH_LAUNCHED(s);
     return SPH_RT_OK;
   }

@@ -17,6 +17,8 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <cstring>
+
 #include <map>
 #include <string>
 #include <unordered_map>
@@ -714,3 +716,36 @@ bool trace_enabled();
       return SPH_RT_EDEVICE;                                       \
     }                                                              \
   } while (0)
+
+namespace sphrt {
+
+// Programmatic dependent launch.  A kernel launched with pdl_launch may be
+// launched while the previous kernel on the stream drains (its last blocks
+// finishing, its writes being flushed); every such kernel calls pdl_wait() as
+// its first statement, which returns once the previous kernel has completed
+// and its writes are visible (at once for a kernel launched the ordinary way).
+// Since every kernel of the chain waits before it does anything, each one still
+// completes after all earlier ones.  (Allowing the next launch early, right
+// after the wait, measured no faster and is not done.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch `kernel` on the handle's stream, with programmatic dependent launch
+// when the configuration asks for it.  The caller checks with SPH_LAUNCHED.
+template <typename... KP, typename... A>
+inline void pdl_launch(const sph_rt *s, void (*kernel)(KP...), dim3 grid, dim3 block, size_t smem,
+                       A... args) {
+  cudaLaunchConfig_t lc;
+  memset(&lc, 0, sizeof lc);
+  lc.gridDim = grid;
+  lc.blockDim = block;
+  lc.dynamicSmemBytes = smem;
+  lc.stream = s->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = s->cfg.pdl ? 1 : 0;
+  cudaLaunchKernelEx(&lc, kernel, args...);
+}
+
+}  // namespace sphrt

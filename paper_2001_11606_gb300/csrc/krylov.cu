@@ -38,6 +38,7 @@ __device__ __forceinline__ T ld(const T *p) {
 template <int W, int U>
 __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) resid_kernel(CsrView<double> A, const double *b, const double *x, double *r,
                              const double *invV, Scalars *sc, double *partials, int *wflag) {
+  pdl_wait();
   mark_work(wflag, 1);
   const int own = tile_own_row<W>(threadIdx.x & 31);
   int64_t r0, r1;
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) resid_kernel(CsrV
 template <int W, int U>
 __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U)) spmv_pq_kernel(CsrView<double> A, const double *z, double *q, double *p, int first,
                                Scalars *sc, double *partials, int *wflag) {
+  pdl_wait();
   if (sc->done) {
     mark_work(wflag, 0);
     return;
@@ -125,6 +127,7 @@ template <typename IT>
 __global__ void update_kernel(int64_t n, double *x, double *r, const double *p, const double *q,
                               const double *invV, int maxit, Scalars *sc, double *partials,
                               FineInit<IT> fi) {
+  pdl_wait();
   if (sc->done) return;
   const double alpha = sc->alpha;
   const double inv_theta = fi.d ? fi.cf->inv_theta : 0.0;
@@ -159,6 +162,7 @@ __global__ void update_kernel(int64_t n, double *x, double *r, const double *p, 
 // Jacobi: z = D^{-1} r, fused with rho = (r, z) and beta.
 __global__ void jacobi_dot_kernel(int64_t n, const double *r, const double *invdiag, double *z,
                                   int first, Scalars *sc, double *partials) {
+  pdl_wait();
   if (sc->done) return;
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -181,6 +185,7 @@ __global__ void jacobi_dot_kernel(int64_t n, const double *r, const double *invd
 template <typename VT>
 __global__ void dot_rz_kernel(int64_t n, const double *r, const VT *z, int first, Scalars *sc,
                               double *partials) {
+  pdl_wait();
   if (sc->done) return;
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -202,6 +207,7 @@ __global__ void dot_rz_kernel(int64_t n, const double *r, const VT *z, int first
 __global__ void dot_rz_flex_kernel(int64_t n, const double *r, const double *z,
                                    const double *z_old, int first, Scalars *sc,
                                    double *partials) {
+  pdl_wait();
   if (sc->done) return;
   double a = 0.0, b = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -229,6 +235,7 @@ __global__ void dot_rz_flex_kernel(int64_t n, const double *r, const double *z,
 // copying z to z_old and dot_rz_flex_kernel, in one pass instead of three.
 __global__ void dot_rz_flex32_kernel(int64_t n, const double *r, const float *z32, double *z,
                                      int first, Scalars *sc, double *partials) {
+  pdl_wait();
   if (sc->done) return;
   double a = 0.0, b = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -261,6 +268,7 @@ __global__ void dot_rz_flex32_kernel(int64_t n, const double *r, const float *z3
 template <typename MT, typename VT>
 __global__ void cheb_init_zero_kernel(int64_t n, const VT *r, const MT *invdiag,
                                       const ChebCoef *cf, VT *d, VT *z, const Scalars *sc) {
+  pdl_wait();
   if (sc && sc->done) return;
   const double inv_theta = cf->inv_theta;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -278,6 +286,7 @@ template <int W, int U, typename MT, typename VT, bool PRE>
 __device__ __forceinline__ void cheb_step_body(const CsrView<MT> &A, const VT *r, const VT *z_in,
                                                VT *z_out, VT *d, const ChebCoef *cf, int k,
                                                const Scalars *sc, int *wflag) {
+  pdl_wait();
   if (sc && sc->done) {
     mark_work(wflag, 0);
     return;
@@ -434,11 +443,11 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
     int *wf = fine ? timing_begin(s) : nullptr;
     if (fine)
       SPH_DISPATCH_SHAPE(A.W, A.U,
-                         (fine_cheb_step_kernel<W, U, MT, VT><<<gw, kBlock, 0, s->stream>>>(
+                         (pdl_launch(s, fine_cheb_step_kernel<W, U, MT, VT>, gw, kBlock, 0,
                              A, r, zin, zout, d, cf, k, sc, wf)));
     else
       SPH_DISPATCH_SHAPE(A.W, A.U,
-                         (cheb_step_kernel<W, U, MT, VT><<<gw, kBlock, 0, s->stream>>>(
+                         (pdl_launch(s, cheb_step_kernel<W, U, MT, VT>, gw, kBlock, 0,
                              A, r, zin, zout, d, cf, k, sc, wf)));
     SPH_LAUNCHED(s);
     if (fine) timing_end(s, bytes, kTimedCheb);
@@ -453,7 +462,7 @@ sph_rt_status cheb_apply(sph_rt *s, const CsrView<MT> &A, const VT *r, VT *z, VT
   if (first_step_done) {
     // the caller has made step 0 from a nonzero guess, result in bufs[w0]
   } else if (zero_guess) {
-    cheb_init_zero_kernel<MT, VT><<<g, kBlock, 0, s->stream>>>(A.n, r, A.invdiag, cf, d,
+    pdl_launch(s, cheb_init_zero_kernel<MT, VT>, g, kBlock, 0, A.n, r, A.invdiag, cf, d,
                                                                  bufs[w0], sc);
     SPH_LAUNCHED(s);
   } else {
@@ -503,7 +512,7 @@ static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first
   sph_rt_status rc;
   switch (s->cfg.precond) {
     case SPH_RT_PRECOND_JACOBI:
-      jacobi_dot_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->r, A.invdiag, s->z, first, s->sc,
+      pdl_launch(s, jacobi_dot_kernel, g, kBlock, 0, A.n, s->r, A.invdiag, s->z, first, s->sc,
                                                       s->partials);
       SPH_LAUNCHED(s);
       return SPH_RT_OK;
@@ -518,7 +527,7 @@ static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first
       if (fused_flex(s)) {
         if ((rc = amg_apply_to32(s, s->r, s->sc, init_done, &df, &dot_done))) return rc;
         if (!dot_done) {
-          dot_rz_flex32_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->r, amg_z32(s), s->z, first,
+          pdl_launch(s, dot_rz_flex32_kernel, g, kBlock, 0, A.n, s->r, amg_z32(s), s->z, first,
                                                              s->sc, s->partials);
           SPH_LAUNCHED(s);
         }
@@ -530,12 +539,12 @@ static sph_rt_status precondition(sph_rt *s, const CsrView<double> &A, int first
     }
   }
   if (s->cfg.precision == SPH_RT_MIXED) {
-    dot_rz_flex_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->r, s->z, s->z_old, first, s->sc,
+    pdl_launch(s, dot_rz_flex_kernel, g, kBlock, 0, A.n, s->r, s->z, s->z_old, first, s->sc,
                                                      s->partials);
     SPH_LAUNCHED(s);
     return SPH_RT_OK;
   }
-  dot_rz_kernel<double><<<g, kBlock, 0, s->stream>>>(A.n, s->r, s->z, first, s->sc, s->partials);
+  pdl_launch(s, dot_rz_kernel<double>, g, kBlock, 0, A.n, s->r, s->z, first, s->sc, s->partials);
   SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }
@@ -610,7 +619,7 @@ sph_rt_status pcg_prologue(sph_rt *s) {
   sph_rt_status rc;
   int *wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
-                     (resid_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->b, s->x, s->r,
+                     (pdl_launch(s, resid_kernel<W, U>, gw, kBlock, 0, A, s->b, s->x, s->r,
                                                                        s->invV, s->sc,
                                                                        s->partials, wf)));
   SPH_LAUNCHED(s);
@@ -618,7 +627,7 @@ sph_rt_status pcg_prologue(sph_rt *s) {
   if ((rc = precondition(s, A, 1))) return rc;
   wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
-                     (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->z, s->q, s->p, 1,
+                     (pdl_launch(s, spmv_pq_kernel<W, U>, gw, kBlock, 0, A, s->z, s->q, s->p, 1,
                                                                          s->sc, s->partials, wf)));
   SPH_LAUNCHED(s);
   timing_end(s, spmv_class_bytes(A, kRowBytesSpmvPQ), kTimedSpmvPQ);
@@ -626,6 +635,7 @@ sph_rt_status pcg_prologue(sph_rt *s) {
 }
 
 __global__ void copy_vec_kernel(int64_t n, const double *src, double *dst, const Scalars *sc) {
+  pdl_wait();
   if (sc && sc->done) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -645,20 +655,20 @@ sph_rt_status pcg_iteration(sph_rt *s) {
   FineInit<float> f32 = {};
   const bool init = s->cfg.precond == SPH_RT_PRECOND_AMG && amg_fine_init(s, &f64, &f32);
   if (f32.d)
-    update_kernel<float><<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
+    pdl_launch(s, update_kernel<float>, g, kBlock, 0, A.n, s->x, s->r, s->p, s->q, s->invV,
                                                       s->cfg.max_krylov, s->sc, s->partials, f32);
   else
-    update_kernel<double><<<g, kBlock, 0, s->stream>>>(A.n, s->x, s->r, s->p, s->q, s->invV,
+    pdl_launch(s, update_kernel<double>, g, kBlock, 0, A.n, s->x, s->r, s->p, s->q, s->invV,
                                                        s->cfg.max_krylov, s->sc, s->partials, f64);
   SPH_LAUNCHED(s);
   if (s->cfg.precision == SPH_RT_MIXED && !fused_flex(s)) {
-    copy_vec_kernel<<<g, kBlock, 0, s->stream>>>(A.n, s->z, s->z_old, s->sc);
+    pdl_launch(s, copy_vec_kernel, g, kBlock, 0, A.n, s->z, s->z_old, s->sc);
     SPH_LAUNCHED(s);
   }
   if ((rc = precondition(s, A, 0, init))) return rc;
   int *wf = timing_begin(s);
   SPH_DISPATCH_SHAPE(A.W, A.U,
-                     (spmv_pq_kernel<W, U><<<gw, kBlock, 0, s->stream>>>(A, s->z, s->q, s->p, 0,
+                     (pdl_launch(s, spmv_pq_kernel<W, U>, gw, kBlock, 0, A, s->z, s->q, s->p, 0,
                                                                          s->sc, s->partials, wf)));
   SPH_LAUNCHED(s);
   timing_end(s, spmv_class_bytes(A, kRowBytesSpmvPQ), kTimedSpmvPQ);

@@ -178,6 +178,7 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->amg_tail = 0;
   c->coarse_fp32 = 1;
   c->graphs = 1;
+  c->pdl = 1;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -206,6 +207,7 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
     return why = "amg_theta must be in [0, 1)", SPH_RT_EINVAL;
   if (c->check_every < 1) return why = "check_every must be >= 1", SPH_RT_EINVAL;
   if (c->graphs < 0 || c->graphs > 1) return why = "graphs must be 0 or 1", SPH_RT_EINVAL;
+  if (c->pdl < 0 || c->pdl > 1) return why = "pdl must be 0 or 1", SPH_RT_EINVAL;
   if (c->amg_tail < 0 || c->amg_tail > 1) return why = "amg_tail must be 0 or 1", SPH_RT_EINVAL;
   if (c->coarse_fp32 < 0 || c->coarse_fp32 > 1)
     return why = "coarse_fp32 must be 0 or 1", SPH_RT_EINVAL;

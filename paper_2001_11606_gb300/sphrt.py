@@ -49,6 +49,7 @@ class Config(C.Structure):
         ("amg_tail", C.c_int32),
         ("coarse_fp32", C.c_int32),
         ("graphs", C.c_int32),
+        ("pdl", C.c_int32),
         ("device", C.c_int32),
         ("stream", C.c_void_p),
     ]

@@ -43,7 +43,7 @@ def test_max_outer_beyond_recorded_stats_is_allowed():
 def test_config_struct_matches_defaults():
     cfg = sphrt.default_config()
     assert cfg.dim == 3 and cfg.a == 1.0 and cfg.precond == sphrt.PRECOND_AMG
-    assert cfg.amg_theta == 0.02 and cfg.cheb_degree == 1 and cfg.graphs == 1
+    assert cfg.amg_theta == 0.02 and cfg.cheb_degree == 1 and cfg.graphs == 1 and cfg.pdl == 1
     assert cfg.amg_tail == 0 and cfg.autotune == 0
     assert cfg.tol_outer_e == 1e-8 and cfg.tol_krylov == 1e-12 and cfg.tol_inner_e == 1e-13
 
@@ -51,7 +51,7 @@ def test_config_struct_matches_defaults():
 @pytest.mark.parametrize("field,value", [("dim", 4), ("cv", 0.0), ("limiter", 7),
                                          ("tol_krylov", -1.0), ("max_outer", 0),
                                          ("precond", 9), ("cheb_degree", 0),
-                                         ("amg_theta", 1.5), ("graphs", 2),
+                                         ("amg_theta", 1.5), ("graphs", 2), ("pdl", 2),
                                          ("amg_tail", -1), ("coarse_fp32", 2)])
 def test_create_rejects_bad_config(field, value):
     cfg = sphrt.default_config(**{field: value})
