@@ -133,7 +133,8 @@ def aggregate_ranks(t_local: float, work_local: float):
 # the profiles/ summary named in the second field holds the capture.
 NCU_TRAFFIC = {
     ("mms3d-lp-64^3", "fp64", "resid"): (338.3e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
-    ("mms3d-lp-64^3", "fp64", "spmv_pq"): (341.4e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "spmv_pq"): (341.8e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-lp-64^3", "fp64", "post_ap"): (115.1e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
 }
 
 
