@@ -295,9 +295,13 @@ def mms_2d(n: int = 32, seed: int = 1, jitter: float = 0.1, steps: int = 10, dt:
                          h_over_dx=h_over_dx, tol_outer_e=1e-10, tol_outer_E=1e-10)
 
 
-def mms_3d_lp(n: int = 64, seed: int = 2, jitter: float = 0.1, steps: int = 100, dt: float = 1e-3):
-    """3-D manufactured problem: sigma = T^-3, Levermore-Pomraning limiter."""
-    return _mms_workload(f"mms3d-lp-{n}^3", 3, n, seed, -3.0, 1, dt, steps, jitter=jitter)
+def mms_3d_lp(n: int = 64, seed: int = 2, jitter: float = 0.1, steps: int = 100, dt: float = 1e-3,
+              h_over_dx: float = 1.5):
+    """3-D manufactured problem: sigma = T^-3, Levermore-Pomraning limiter.  A larger
+    h_over_dx gives longer rows (h = 2.4 dx: ~250 stored entries per row)."""
+    name = f"mms3d-lp-{n}^3" + ("" if h_over_dx == 1.5 else f"-h{h_over_dx:g}")
+    return _mms_workload(name, 3, n, seed, -3.0, 1, dt, steps, jitter=jitter,
+                         h_over_dx=h_over_dx)
 
 
 def mms_3d(n: int = 128, seed: int = 3, jitter: float = 0.1, steps: int = 50, dt: float = 1e-3):

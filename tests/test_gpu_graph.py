@@ -84,3 +84,14 @@ def test_cluster_tail_vcycle_bitwise_and_fewer_launches(precision):
     assert np.array_equal(on[0], off[0]) and np.array_equal(on[1], off[1])
     assert on[2] == off[2]
     assert on[4] < off[4]  # the tail replaces several launches per V-cycle
+
+
+@pytest.mark.parametrize("precision", [sphrt.FP64, sphrt.MIXED])
+def test_dependent_launch_changes_no_bit(precision):
+    # programmatic dependent launch only lets a kernel's launch overlap its
+    # predecessor's drain; every kernel waits for its predecessor's results
+    w = I.mms_3d_lp(n=12, steps=3)
+    on = _run(w, 3, precision=precision, pdl=1)
+    off = _run(w, 3, precision=precision, pdl=0)
+    assert np.array_equal(on[0], off[0]) and np.array_equal(on[1], off[1])
+    assert on[2] == off[2]

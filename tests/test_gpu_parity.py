@@ -202,6 +202,22 @@ def test_heterogeneous_sphere_parity(precision, tol):
     assert errE < tol, errE
 
 
+@pytest.mark.parametrize("n,h,precond,precision,tol", [
+    (10, 2.4, sphrt.PRECOND_JACOBI, sphrt.FP64, 1e-10),
+    (10, 2.4, sphrt.PRECOND_CHEBYSHEV, sphrt.FP64, 1e-10),
+    (10, 2.4, sphrt.PRECOND_AMG, sphrt.FP64, 1e-10),
+    (10, 2.4, sphrt.PRECOND_AMG, sphrt.MIXED, 1e-8),
+    (5, 1.5, sphrt.PRECOND_AMG, sphrt.FP64, 1e-10)])
+def test_row_tile_shapes_parity(n, h, precond, precision, tol):
+    # h = 2.4 dx: ~250 stored entries per row (84-463), so the SpMV-class sweeps, the
+    # gradient and the assembly take their 8-lanes-per-row shape (8 rounds of 4 rows per
+    # 32-row tile); 1,000 rows end in a ragged tile.  5^3 = 125 rows: 4 tiles, the last
+    # with 29 rows, 4-lane shape.
+    w = I.mms_3d_lp(n=n, steps=2, h_over_dx=h)
+    r = run_both(w, 2, gpu_over=dict(precond=precond, precision=precision), orc_over=TIGHT)
+    assert r["err_e"] < tol and r["err_E"] < tol, (r["err_e"], r["err_E"])
+
+
 def test_mixed_precision_parity():
     w = I.mms_3d_lp(n=16, steps=3)
     r = run_both(w, 3, gpu_over=dict(precision=sphrt.MIXED, precond=sphrt.PRECOND_AMG),
