@@ -208,16 +208,6 @@ __device__ __forceinline__ int64_t warp_first_group(int64_t grp) {
   return grp - group_in_warp<W>(grp);
 }
 
-// Row-epilogue operands fetched early: before a row's sum, lane k of the row
-// group loads the k-th per-row operand (diagonal, vector entries), so those
-// loads are in flight together with the row's gathers instead of being
-// issued after the reduction; group_bcast hands them to lane 0 afterwards.
-// Every lane of the warp must call it (full-mask shuffle).
-template <int W, typename T>
-__device__ __forceinline__ T group_bcast(T v, int src) {
-  return __shfl_sync(0xffffffffu, v, src, W);
-}
-
 // Sum over the W lanes of a row group (W divides 32; groups are aligned).
 template <int W, typename T>
 __device__ __forceinline__ T row_reduce(T v) {
