@@ -7,8 +7,11 @@
 // preconditioner, set up once per step and warm-started from E^l (Sec. 3.2).
 // Here the operator is stored as B = V A, which is symmetric positive
 // definite (an M-matrix with strict diagonal dominance), so CG is the Krylov
-// method: one SpMV, one preconditioner application and three fused
-// vector/reduction kernels per iteration.  The stopping test is the paper's
+// method.  Per iteration: the x / r update fused with ||r|| and the
+// convergence test, the preconditioner, the inner product (r, z), and the
+// SpMV fused with the direction update and (p, q).  With the AMG
+// preconditioner the update also writes the V-cycle's first smoother step and
+// (r, z) rides in the V-cycle's last sweep.  The stopping test is the paper's
 // unscaled residual ||b - A E||_2 <= tol ||b||_2, with A E - b = V^{-1}(B E - V b).
 //
 // All scalars of the iteration (rho, alpha, beta, norms, convergence flag)
