@@ -253,3 +253,31 @@ def run(workload, steps: int | None = None, brute: bool = False, params: dict | 
             raise RuntimeError(f"oracle step {n} did not converge (status {rc})")
         stats.append(st)
     return e, E, stats
+
+
+def fractional_change(x_new, x_old, V, target, interior, floor=1e-15):
+    """Fractional energy change over a step (Sec. 3.3, Eq. energy-fractional):
+    eta = max_i |x_i^n - x_i^{n-1}| / (x_i^n + target * xbar^n), where
+    xbar^n = sum_i x_i^n V_i / sum_i V_i is the volume average over the
+    interior particles.  `floor` is added to the denominator, as the paper
+    suggests, for a state whose energy may be zero everywhere."""
+    m = np.asarray(interior, dtype=bool)
+    xn = np.asarray(x_new, dtype=np.float64)[m]
+    xo = np.asarray(x_old, dtype=np.float64)[m]
+    v = np.asarray(V, dtype=np.float64)[m]
+    xbar = float(np.sum(xn * v) / np.sum(v))
+    return float(np.max(np.abs(xn - xo) / (xn + target * xbar + floor)))
+
+
+def next_dt(e_new, e_old, E_new, E_old, V, interior, dt, target=0.05, growth=10.0,
+            dt_min=0.0, dt_max=np.inf):
+    """Time step for the next step (Sec. 3.3): dt_x = dt (target / eta_x)^(1/2) for
+    the material energy e and the radiation energy E, the more restrictive of
+    the two, at most `growth` times the current step (the infinite-medium runs
+    of Sec. 4.1 allow an order of magnitude per step), within [dt_min, dt_max].
+    Returns (dt_next, eta_e, eta_E)."""
+    eta_e = fractional_change(e_new, e_old, V, target, interior)
+    eta_E = fractional_change(E_new, E_old, V, target, interior)
+    cand = [dt * (target / eta) ** 0.5 if eta > 0.0 else np.inf for eta in (eta_e, eta_E)]
+    dt_next = min(min(cand), growth * dt, dt_max)
+    return max(dt_next, dt_min), eta_e, eta_E

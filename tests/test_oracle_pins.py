@@ -302,6 +302,68 @@ def test_infinite_medium_backward_euler_root(case):
     assert rel <= 10 * max(golden()["infinite_energy_error_dt0p1"])
 
 
+@pytest.mark.parametrize("ratio", [1.0 / 50.0, 30.0])
+def test_time_step_controller_converges_like_its_closed_form(ratio):
+    # Sec. 3.3 on an absorbing infinite medium (a = 0: no emission, sigma = c = 1): backward
+    # Euler gives E_n = E_{n-1} / (1 + dt), so the radiation's fractional change is exactly
+    # eta_E = dt / (1 + target) and the square-root update reads dt_{n+1} = sqrt(dt_n dt*)
+    # with dt* = target (1 + target): log(dt_n / dt*) halves every step.  The material energy
+    # (e = 1e12) changes by a negligible fraction and never limits.
+    target = 0.05
+    dt_star = target * (1.0 + target)
+    pb, e, E = _single_particle(1e12, 1.0, dict(a=0.0))
+    dt0 = ratio * dt_star
+    dt = dt0
+    V = pb.mass / pb.rho
+    interior = pb.kind == 0
+    for n in range(1, 9):
+        rc, e1, E1, _ = pb.step(e, E, dt)
+        assert rc == 0
+        assert E1[0] == pytest.approx(E[0] / (1.0 + dt), rel=1e-13, abs=0.0)
+        dt_next, eta_e, eta_E = O.next_dt(e1, e, E1, E, V, interior, dt, target=target,
+                                          growth=1e30)
+        assert eta_e < 1e-6 * eta_E
+        assert dt_next == pytest.approx(dt_star * ratio ** (0.5**n), rel=1e-9, abs=0.0)
+        e, E, dt = e1, E1, dt_next
+
+
+def test_time_step_controller_growth_and_cap():
+    # a state at equilibrium does not change (eta = 0): the step grows by the allowed factor
+    # per step until the hard cap, as in the infinite-medium runs of Sec. 4.1 (x10, 0.1)
+    P = I.make_lattice(2, (6, 6), 1.0 / 6, seed=4)
+    pb = O.Problem(P, dict(dim=2, a=0.7, c=2.0, cv=1.3, limiter=1, opacity_exp=-3.0))
+    T = 1.4
+    e = np.full(P.n, 1.3 * T)
+    E = np.full(P.n, 0.7 * T**4)
+    V = P.mass / P.rho
+    dts = []
+    dt = 1e-6
+    for _ in range(8):
+        rc, e1, E1, _ = pb.step(e, E, dt, ghost_e=e, ghost_E=E)
+        assert rc == 0
+        dt, eta_e, eta_E = O.next_dt(e1, e, E1, E, V, P.kind == 0, dt, growth=10.0, dt_max=0.1)
+        assert eta_e < 1e-12 and eta_E < 1e-12
+        dts.append(dt)
+        e, E = e1, E1
+    assert dts[:5] == pytest.approx([1e-5, 1e-4, 1e-3, 1e-2, 0.1], rel=1e-12, abs=0.0)
+    assert dts[5:] == [0.1, 0.1, 0.1]
+
+
+def test_fractional_change_weights_small_energies_by_the_average():
+    # the average in the denominator keeps a nearly empty particle from setting the step
+    # (Sec. 3.3): the same absolute change counts in proportion to x_i + target * xbar, and
+    # eta is unchanged when every energy is scaled by the same factor
+    V = np.ones(4)
+    inside = np.ones(4, dtype=bool)
+    old = np.array([1.0, 1.0, 1.0, 1e-9])
+    new = np.array([1.0, 1.0, 1.0, 2e-9])   # the near-empty particle doubles
+    eta = O.fractional_change(new, old, V, 0.05, inside)
+    assert eta < 1e-7                       # vs a fractional change of 0.5 without the average
+    for s in (3.0, 1e8):  # (the 1e-15 floor breaks the scaling only for tiny energies)
+        assert O.fractional_change(s * new, s * old, V, 0.05, inside) == pytest.approx(
+            eta, rel=1e-12, abs=0.0)
+
+
 def test_infinite_medium_first_order_in_time():
     from scipy.integrate import solve_ivp
 
