@@ -121,8 +121,9 @@ typedef struct {
 
 /* Fill *cfg with defaults: dim 3, a = c = c_v = 1, no limiter, p = 0,
  * tolerances of Table tab:tolerances (manufactured problem row) with
- * tol_inner_e = 1e-13, AMG preconditioner (theta 0.02, Chebyshev degree 2),
- * FP64, device 0, own stream. */
+ * tol_inner_e = 1e-13, AMG preconditioner (theta 0.02, Chebyshev degree 1,
+ * coarsest solve in FP32), FP64, the per-step CUDA graph and programmatic
+ * dependent launch on, device 0, own stream. */
 void sph_rt_default_config(sph_rt_config *cfg);
 
 /* Create a handle.  No device work happens until sph_rt_set_particles.
