@@ -89,6 +89,8 @@ def lib():
             L.orc_step.argtypes = [P, i64, P, P, P, P, P, P, P, P, P, dbl, P, P, P, P, P, P, P]
             L.orc_step.restype = i32
             L.orc_totals.argtypes = [i64, P, P, P, P, P, P]
+            L.orc_limiter.argtypes = [P, dbl]
+            L.orc_limiter.restype = dbl
             L.orc_num_threads.restype = i32
             L.orc_set_threads.argtypes = [i32]
             _lib = L
@@ -126,6 +128,12 @@ def kernel(dim: int, r: float, h: float):
     W, dW = C.c_double(), C.c_double()
     lib().orc_kernel(dim, float(r), float(h), C.byref(W), C.byref(dW))
     return W.value, dW.value
+
+
+def limiter(R: float, limiter: int, larsen_k: float = 2.0) -> float:
+    """Flux limiter lambda(R) (Sec. 2.1): 0 none (1/3), 1 Levermore, 2 Larsen(k)."""
+    p = make_params(limiter=int(limiter), larsen_k=float(larsen_k))
+    return float(lib().orc_limiter(C.byref(p), float(R)))
 
 
 def neighbors(pos, h, kind, brute: bool = False):

@@ -252,6 +252,10 @@ static double limiter_lambda(const orc_params *p, double R) {
   return 1.0 / 3.0; /* no limiter: Fick's law */
 }
 
+/* lambda(R) of the configured limiter, exported so that the tests can pin it
+ * to values worked by hand from the printed formulas of Sec. 2.1. */
+double orc_limiter(const orc_params *p, double R) { return limiter_lambda(p, R); }
+
 /*
  * For every particle (caller order), from the state (e, E) at the start of
  * the step:

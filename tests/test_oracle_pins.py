@@ -131,6 +131,31 @@ def test_limiters():
         assert np.all(np.abs(lam * R - 1.0) < 4.0 / R + 1e-15)
 
 
+@pytest.mark.parametrize("key,lim,k", [("levermore_R_lambda", 1, 2.0),
+                                       ("larsen_k2_R_lambda", 2, 2.0),
+                                       ("larsen_k1_R_lambda", 2, 1.0),
+                                       ("larsen_k3_R_lambda", 2, 3.0)])
+def test_limiter_values_at_finite_R(key, lim, k):
+    # lambda(R) at finite R against values worked by hand from the printed
+    # formulas of Sec. 2.1 (a swapped coefficient, a wrong power or k fails here)
+    pairs = golden()[key]
+    for R, lam in zip(pairs[0::2], pairs[1::2]):
+        assert O.limiter(R, lim, k) == pytest.approx(lam, rel=2e-16 * 8, abs=0)
+
+
+def test_properties_use_the_limiter_at_their_R():
+    # the material data of a step take lambda from the same limiter at the R they form
+    P = I.make_lattice(2, (8, 8), 1.0 / 8, seed=3)
+    E = 1.0 + 3.0 * P.pos[:, 0] ** 2 + P.pos[:, 1]
+    for lim, k in ((1, 2.0), (2, 2.0), (2, 3.0)):
+        pb = O.Problem(P, dict(dim=2, limiter=lim, larsen_k=k))
+        pr = pb.properties(np.ones(P.n), E, dt=1e-3)
+        m = P.kind == 0
+        assert np.all(pr["R"][m] > 0.1)
+        want = np.array([O.limiter(R, lim, k) for R in pr["R"][m]])
+        assert np.array_equal(pr["lambda"][m], want)
+
+
 def test_gradient_of_linear_field_on_lattice():
     # SPH derivative of a linear field on an unjittered lattice is exact up to the
     # lattice first moment: grad(x) = sum_j V_j (x_j - x_i) F_ij x_ij -> 1 (within the
