@@ -1,23 +1,27 @@
 """Benchmark of the implicit SPH thermal-radiative-transfer step on GB300.
 
-One benchmark "step" is one pass of the whole hot path over one job of the
-3-D manufactured workload (64^3 = 262,144 interior particles on a jittered
-lattice plus 80,856 Dirichlet ghosts, h = 1.5 dx, sigma = T^-3, Levermore
-limiter): set the particles (Morton sort, cell list, neighbour search,
-operator sparsity) and advance 100 backward-Euler steps of dt = 1e-3 (material
-data, assembly, AMG set-up, preconditioned Krylov solves inside the
+One benchmark "step" is one pass of the whole hot path over one job of the 3-D
+manufactured workload mms3d-128^3 (128^3 = 2,097,152 interior particles on a
+jittered lattice plus 308,952 Dirichlet ghosts, h = 1.5 dx, sigma = 1, no
+limiter): set the particles (Morton sort, cell list, neighbour search, operator
+sparsity) and advance 50 backward-Euler steps of dt = 1e-3 (material data,
+assembly, AMG set-up, preconditioned Krylov solves inside the
 nonlinear-elimination loop, per-particle Newton).  The metric is
-particle-steps/s = interior particles x time steps / wall time.
+particle-steps/s = interior particles x time steps / device time.
 
-  value     inputs resident in HBM before timing (device entry points)
-  e2e       the same job through the host-pointer C ABI: particle arrays and
-            per-step sources copied from pinned host memory, final energies
-            copied back, all inside the timed region
-  roofline  the fine-operator SpMV-class kernels (CG SpMV, residual and
-            Chebyshev smoother sweeps on the finest level), CUDA-event time
-            over the timed region against the measured HBM copy bandwidth
+The same jobs run in both arithmetic forms, one after the other:
+  value       the mixed-precision form (FP32 operator copy, FP32 AMG hierarchy
+              and V-cycle inside an FP64 Krylov solve with FP64 residuals)
+  fp64        the plain FP64 form, with mixed_over_fp64 = value / fp64 value and
+              the largest relative difference of the two forms' final energies
+  e2e         the mixed form through the host-pointer C ABI: particle arrays and
+              per-step sources copied from pinned host memory, final energies
+              copied back, all inside the timed region
+  roofline    the fine-operator SpMV-class kernels (CG product, residual and
+              smoother sweeps on the finest level), CUDA-event time per launch
+              against the measured HBM copy bandwidth
   cpu_baseline / --impl reference   the CPU oracle (tests only otherwise) on a
-            bounded sample of the same workload, on the host cores
+              bounded sample of the same workload, on the host cores
 
 Multi-GPU (torchrun): replicas only -- every rank runs its own job, the
 metric is the sum over ranks, timing is the max over ranks.
@@ -145,12 +149,42 @@ def make_workload(name: str):
         return I.mms_3d_lp(n=32, steps=20)
     if name == "mms2d-32":
         return I.mms_2d(n=32, steps=10)
-    if name == "mms3d-128":
-        return I.mms_3d(n=128, steps=50)
+    if name.startswith("mms3d-") and name[6:].isdigit():
+        # 3-D manufactured problem, sigma = 1, no limiter: 50 steps of 1e-3
+        return I.mms_3d(n=int(name[6:]), steps=50)
     if name.startswith("sphere-"):
         # heterogeneous sphere problem, 20 steps of 1e-4 (n^3 interior particles)
         return I.sphere_3d(n=int(name.split("-")[1]), steps=20, dt=1e-4)
     raise SystemExit(f"unknown workload {name}")
+
+
+def sample_block(w, m: int):
+    """A bounded sample of workload w for the CPU oracle: the interior lattice
+    points of the corner block [0, m)^d, with every particle of the workload
+    within the ghost layers around the block as a Dirichlet ghost (holding the
+    workload's values there).  The sample's particles, masses, smoothing
+    lengths and per-step inputs are the workload's own at those positions."""
+    P = w.particles
+    if np.any(P.kind == I.COPY):
+        raise ValueError("sample_block needs a workload without copy ghosts")
+    idx = np.floor(P.pos / P.dx).astype(np.int64)  # lattice cell (jitter < dx / 2)
+    g = I.GHOST_LAYERS
+    inner = np.all((idx >= 0) & (idx < m), axis=1)
+    near = np.all((idx >= -g) & (idx < m + g), axis=1)
+    sel = np.flatnonzero(near)
+    kind = np.where(inner[sel], I.INTERIOR, I.DIRICHLET).astype(np.int32)
+    S = I.Particles(dim=P.dim, dx=P.dx, counts=(m,) * P.dim, pos=np.ascontiguousarray(P.pos[sel]),
+                    kind=kind, copy_of=np.full(len(sel), -1, dtype=np.int64),
+                    mass=P.mass[sel].copy(), rho=P.rho[sel].copy(), h=P.h[sel].copy(),
+                    sigma0=P.sigma0[sel].copy())
+    return I.Workload(name=f"{w.name} corner {m}^{P.dim} block", particles=S,
+                      params=dict(w.params), dt=w.dt, steps=w.steps, mms=w.mms,
+                      e0=w.e0[sel].copy(), E0=w.E0[sel].copy())
+
+
+def cpu_block(w) -> int:
+    """Edge of the sampled block: about 2.6e5 interior particles in 3-D."""
+    return min(64 if w.particles.dim == 3 else 512, min(w.particles.counts))
 
 
 def cpu_sample(w, steps: int = 1):
@@ -171,30 +205,38 @@ def cpu_sample(w, steps: int = 1):
 
 
 def run_reference(args, w):
+    """The oracle on a bounded sample of the workload (sample_block): its
+    neighbour set-up amortised over the job's time steps plus the timed steps."""
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
         return
     import oracle as O
 
     O.build()
-    n_int = w.particles.n_interior
-    pb = O.Problem(w.particles, w.params)
-    e, E = w.e0.copy(), w.E0.copy()
-    inputs = [w.step_inputs(n) for n in range(1, args.warmup + args.steps + 1)]
+    ws = sample_block(w, cpu_block(w))
+    n_int = ws.particles.n_interior
+    t0 = time.perf_counter()
+    pb = O.Problem(ws.particles, ws.params)
+    setup_s = time.perf_counter() - t0
+    e, E = ws.e0.copy(), ws.E0.copy()
+    inputs = [ws.step_inputs(n) for n in range(1, args.warmup + args.steps + 1)]
     for n in range(args.warmup):
-        rc, e, E, _ = pb.step(e, E, w.dt, *inputs[n])
+        rc, e, E, _ = pb.step(e, E, ws.dt, *inputs[n])
     t0 = time.perf_counter()
     for n in range(args.warmup, args.warmup + args.steps):
-        rc, e, E, _ = pb.step(e, E, w.dt, *inputs[n])
-    dt_s = time.perf_counter() - t0
+        rc, e, E, _ = pb.step(e, E, ws.dt, *inputs[n])
+    steps_s = time.perf_counter() - t0
+    dt_s = steps_s + setup_s * args.steps / w.steps
     value = n_int * args.steps / dt_s
-    sample = (f"{w.name}: one backward-Euler step per benchmark step (neighbour lists built "
-              f"once before timing), {n_int} interior particles")
+    sample = (f"{ws.name}: {n_int} interior particles; one backward-Euler step per benchmark "
+              f"step plus the neighbour set-up ({setup_s:.1f} s) amortised over the job's "
+              f"{w.steps} steps")
     line = {"impl": "reference", "metric": "particle-steps/s", "value": value,
             "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "precision": "fp64"},
+            "data": "synthetic", "config": {"workload": w.name, "precision": "fp64",
+                                            "sample": ws.name},
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": O.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
@@ -265,19 +307,45 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def fine_roofline(k_kinds, k_ms, k_bytes, hbm, src, workload, precision):
+    """Roofline object of the fine kernel with the largest total event time."""
+    dom = max(k_kinds, key=lambda k: k_kinds[k][1])
+    d_n, d_ms, d_by = k_kinds[dom]
+    achieved = (d_by / (d_ms / 1e3)) / 1e9 if d_ms > 0 else None
+    traffic = NCU_TRAFFIC.get((workload, precision, dom))
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm if achieved else None,
+            "traffic": traffic[0] if traffic else None,
+            "kernel": f"{dom} (fine level, {precision})",
+            "timing": "CUDA events per launch on the solver stream, the same jobs in a second "
+                      "timed pass with the host-driven loop",
+            "launches": d_n, "bytes_per_launch": d_by / d_n if d_n else None,
+            "us_per_launch": 1e3 * d_ms / d_n if d_n else None,
+            "traffic_source": traffic[1] if traffic else None,
+            "peak_source": src,
+            "fine_kernels": {k: {"launches": v[0],
+                                 "GB/s": (v[2] / (v[1] / 1e3)) / 1e9 if v[1] > 0 else None,
+                                 "us_per_launch": 1e3 * v[1] / v[0] if v[0] else None,
+                                 "share_of_timed": v[1] / k_ms if k_ms > 0 else None}
+                             for k, v in k_kinds.items() if v[0] > 0},
+            "all_fine_GB/s": (k_bytes / (k_ms / 1e3)) / 1e9 if k_ms > 0 else None}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="mms3d-lp-64")
+    ap.add_argument("--workload", default="mms3d-128")
     ap.add_argument("--time-steps", type=int, default=None,
                     help="backward-Euler steps per job (default: the workload's)")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"],
+                    help="both: the mixed form is the value, the FP64 form is timed beside it")
     ap.add_argument("--precond", default="amg", choices=["jacobi", "chebyshev", "amg"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-kernel-timing", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-driven outer loop instead of the per-step CUDA graph")
     ap.add_argument("--check-every", type=int, default=None,
@@ -315,12 +383,14 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     precond = {"jacobi": sphrt.PRECOND_JACOBI, "chebyshev": sphrt.PRECOND_CHEBYSHEV,
                "amg": sphrt.PRECOND_AMG}[args.precond]
-    prec = sphrt.MIXED if args.precision == "mixed" else sphrt.FP64
+    forms = {"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
+    head = forms[0]
+    prec_of = {"mixed": sphrt.MIXED, "fp64": sphrt.FP64}
     extra = {"check_every": args.check_every} if args.check_every else {}
-    cfg = sphrt.config_from_params(w.params, device=local, stream=stream.cuda_stream,
-                                   precond=precond, precision=prec, graphs=int(not args.no_graphs),
-                                   **extra)
-    S = sphrt.Solver(cfg)
+
+    def make_cfg(form, **kw):
+        return sphrt.config_from_params(w.params, device=local, stream=stream.cuda_stream,
+                                        precond=precond, precision=prec_of[form], **extra, **kw)
 
     # ---- inputs resident in HBM --------------------------------------------
     f64 = dict(dtype=torch.float64, device=dev)
@@ -337,11 +407,10 @@ def main():
     else:
         host_inputs = None
         d_ptrs = [[0, 0, 0, 0] for _ in range(T)]
-    d_e_out = torch.empty(n, **f64)
-    d_E_out = torch.empty(n, **f64)
+    d_out = {f: (torch.empty(n, **f64), torch.empty(n, **f64)) for f in forms}
     torch.cuda.synchronize(dev)
 
-    def job_device(S=S):
+    def job_device(S, form):
         S.set_particles_device(n, d_pos.data_ptr(), *[a.data_ptr() for a in d_part],
                                d_kind.data_ptr(), 0, d_e0.data_ptr(), d_E0.data_ptr())
         outer = krylov = 0
@@ -349,7 +418,7 @@ def main():
             _, st = S.step_device(w.dt, *d_ptrs[k])
             outer += st.outer_iters
             krylov += st.krylov_iters_total
-        S.get_energies_device(d_e_out.data_ptr(), d_E_out.data_ptr())
+        S.get_energies_device(d_out[form][0].data_ptr(), d_out[form][1].data_ptr())
         return outer, krylov
 
     def barrier():
@@ -358,48 +427,51 @@ def main():
 
             dist.barrier()
 
-    for _ in range(args.warmup):
-        job_device()
-    S.kernel_stats(reset=True)
+    # ---- timed passes: each form warmed up, then K jobs between events -----
     sampler = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize(dev)
+    timed = {}
     sampler.start()
-    launches0 = S.launch_count()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    iters = []
-    for _ in range(args.steps):
-        iters.append(job_device())
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier()
+    for form in forms:
+        S = sphrt.Solver(make_cfg(form, graphs=int(not args.no_graphs)))
+        for _ in range(args.warmup):
+            job_device(S, form)
+        barrier()
+        torch.cuda.synchronize(dev)
+        launches0 = S.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        iters = [job_device(S, form) for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        gpu_ms = ev0.elapsed_time(ev1)
+        t_max, work = aggregate_ranks(gpu_ms / 1e3, float(n_int * T * args.steps))
+        timed[form] = dict(value=work / t_max, t_max=t_max, launches=S.launch_count() - launches0,
+                           outer=sum(i[0] for i in iters) / (args.steps * T),
+                           krylov=sum(i[1] for i in iters) / (args.steps * T))
+        S.close()
     clocks = sampler.stop()
-    gpu_ms = ev0.elapsed_time(ev1)
-    launches = S.launch_count() - launches0
-    t_max, work = aggregate_ranks(gpu_ms / 1e3, float(n_int * T * args.steps))
-    value = work / t_max
 
     # ---- kernel timing: the same jobs with CUDA events around every fine-operator
     # SpMV-class launch (per-launch events need the host-driven loop) --------------
-    cfg_t = sphrt.config_from_params(w.params, device=local, stream=stream.cuda_stream,
-                                     precond=precond, precision=prec, kernel_timing=1)
-    S_t = sphrt.Solver(cfg_t)
-    job_device(S_t)
-    S_t.kernel_stats(reset=True)
-    barrier()
-    for _ in range(args.steps):
-        job_device(S_t)
-    torch.cuda.synchronize(dev)
-    k_launch, k_ms, k_bytes = S_t.kernel_stats()
-    k_kinds = S_t.kernel_stats_by_kind()
-    S_t.kernel_stats(reset=True)
-    S_t.close()
+    kt = {}
+    if not args.no_kernel_timing:
+        for form in forms:
+            S_t = sphrt.Solver(make_cfg(form, kernel_timing=1))
+            job_device(S_t, form)
+            S_t.kernel_stats(reset=True)
+            barrier()
+            for _ in range(args.steps):
+                job_device(S_t, form)
+            torch.cuda.synchronize(dev)
+            kt[form] = (S_t.kernel_stats(), S_t.kernel_stats_by_kind())
+            S_t.close()
 
-    # ---- end to end through the host-pointer C ABI ---------------------------
+    # ---- end to end through the host-pointer C ABI (the headline form) -------
     e2e = None
     if not args.no_e2e:
+        S = sphrt.Solver(make_cfg(head, graphs=int(not args.no_graphs)))
         pin = dict(dtype=torch.float64, pin_memory=True)
         h_pos = torch.as_tensor(P.pos, dtype=torch.float64).pin_memory()
         h_part = [torch.as_tensor(a, dtype=torch.float64).pin_memory() for a in
@@ -436,58 +508,66 @@ def main():
         t_e2e, work_e2e = aggregate_ranks(time.perf_counter() - t0, float(n_int * T * args.steps))
         h2d = (P.pos.nbytes + 6 * n * 8 + n * 4) + (T * 4 * n * 8 if h_inputs is not None else 0)
         e2e = {"value": work_e2e / t_e2e, "unit": "particle-steps/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(2 * n * 8)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(2 * n * 8),
+               "precision": head}
+        S.close()
 
     if rank != 0:
         return
     hbm, src = peaks()
-    # the dominant kernel: the timed fine-operator kernel with the largest total time
-    dom = max(k_kinds, key=lambda k: k_kinds[k][1])
-    d_n, d_ms, d_by = k_kinds[dom]
-    achieved = (d_by / (d_ms / 1e3)) / 1e9 if d_ms > 0 else None
-    traffic = NCU_TRAFFIC.get((w.name, args.precision, dom))
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm if achieved else None,
-            "traffic": traffic[0] if traffic else None,
-            "kernel": f"{dom} (fine level)",
-            "timing": "CUDA events per launch on the solver stream, the same jobs in a second "
-                      "timed pass with the host-driven loop",
-            "launches": d_n, "bytes_per_launch": d_by / d_n if d_n else None,
-            "us_per_launch": 1e3 * d_ms / d_n if d_n else None,
-            "traffic_source": traffic[1] if traffic else None,
-            "peak_source": src,
-            "fine_kernels": {k: {"launches": v[0],
-                                 "GB/s": (v[2] / (v[1] / 1e3)) / 1e9 if v[1] > 0 else None,
-                                 "share_of_timed": v[1] / k_ms if k_ms > 0 else None}
-                             for k, v in k_kinds.items()},
-            "all_fine_GB/s": (k_bytes / (k_ms / 1e3)) / 1e9 if k_ms > 0 else None}
+    roof = None
+    if kt:
+        (k_launch, k_ms, k_bytes), k_kinds = kt[head]
+        roof = fine_roofline(k_kinds, k_ms, k_bytes, hbm, src, w.name, head)
+        for form in forms[1:]:
+            (_, ms2, by2), kinds2 = kt[form]
+            roof[f"{form}_form"] = fine_roofline(kinds2, ms2, by2, hbm, src, w.name, form)
     cpu = None
     if not args.no_cpu_baseline:
         import oracle as O
 
         O.build()
-        cs = cpu_sample(w, steps=1)
+        ws = sample_block(w, cpu_block(w))
+        cs = cpu_sample(ws, steps=1)
         per = cs["setup_s"] / T + cs["step_s"]
-        cpu = {"value": n_int / per, "unit": "particle-steps/s", "cores": cs["cores"],
-               "kind": "oracle",
-               "sample": (f"{w.name}: oracle neighbour set-up ({cs['setup_s']:.1f} s, amortised "
-                          f"over {T} steps) plus one backward-Euler step ({cs['step_s']:.1f} s)")}
-    outer = sum(i[0] for i in iters) / (args.steps * T)
-    kry = sum(i[1] for i in iters) / (args.steps * T)
-    line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+        cpu = {"value": ws.particles.n_interior / per, "unit": "particle-steps/s",
+               "cores": cs["cores"], "kind": "oracle",
+               "sample": (f"{ws.name} ({ws.particles.n_interior} interior particles): oracle "
+                          f"neighbour set-up ({cs['setup_s']:.1f} s, amortised over {T} steps) "
+                          f"plus one backward-Euler step ({cs['step_s']:.1f} s)")}
+    mask = P.kind == I.INTERIOR
+    hd = timed[head]
+    line = {"metric": "particle-steps/s", "value": hd["value"], "unit": "particle-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == sphrt.FP64 else "f32+f64",
+            "ms_per_step": 1e3 * hd["t_max"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": w.name, "interior_particles": n_int, "ghosts": n - n_int,
-                       "time_steps_per_job": T, "dt": w.dt, "precision": args.precision,
+                       "time_steps_per_job": T, "dt": w.dt, "precision": head,
                        "precond": args.precond, "parallelism": f"replicas{world}",
                        "outer_loop": "host" if args.no_graphs else "cuda-graph",
                        "l2": "inputs larger than L2 (operator > 129 MB)",
-                       "outer_iters_per_step": outer, "krylov_iters_per_step": kry,
-                       "ms_per_time_step": 1e3 * t_max / (args.steps * T)},
-            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+                       "outer_iters_per_step": hd["outer"], "krylov_iters_per_step": hd["krylov"],
+                       "ms_per_time_step": 1e3 * hd["t_max"] / (args.steps * T)},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": hd["launches"], "roofline": roof,
             "cpu_baseline": cpu}
+    if len(forms) > 1:
+        other = forms[1]
+        od = timed[other]
+        eh = d_out[head][0].cpu().numpy()[mask]
+        Eh = d_out[head][1].cpu().numpy()[mask]
+        eo = d_out[other][0].cpu().numpy()[mask]
+        Eo = d_out[other][1].cpu().numpy()[mask]
+        diff = max(float(np.max(np.abs(eh - eo) / np.abs(eo))),
+                   float(np.max(np.abs(Eh - Eo) / np.abs(Eo))))
+        line[other] = {"value": od["value"], "unit": "particle-steps/s",
+                       "ms_per_step": 1e3 * od["t_max"] / args.steps,
+                       "ms_per_time_step": 1e3 * od["t_max"] / (args.steps * T),
+                       "outer_iters_per_step": od["outer"], "krylov_iters_per_step": od["krylov"],
+                       "gpu_launches": od["launches"]}
+        line[f"{head}_over_{other}"] = hd["value"] / od["value"]
+        line[f"{head}_vs_{other}_max_rel_diff"] = diff
     print(json.dumps(line), flush=True)
 
 

@@ -9,7 +9,7 @@
  * cudaFree are forbidden because they synchronise the device, or a process
  * that has handed all free device memory to its own arena.  Such callers keep
  * their particle data in memory they already own and can still ask for the
- * energy totals of Sec. 2.5.
+ * interior energy totals that sph_rt_get_energies reports.
  */
 #ifndef SPH_RT_NOALLOC_H
 #define SPH_RT_NOALLOC_H
@@ -39,12 +39,13 @@ extern "C" {
  *
  * Scratch: a fixed 64 KiB array in the library's static device memory (every
  * GPU that loads the library holds it until the process exits), not a
- * cudaMalloc.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress, with that device current) and clears its
- * arrival counter; make that first call before any stream capture.  Every call
- * on a device shares the one array and leaves it ready for the next, so calls
- * whose kernels overlap on the GPU (different streams, or concurrent host
- * threads) race and give wrong totals: serialise them.
+ * cudaMalloc.  It is zero when the library's device code is loaded, and each
+ * call leaves its arrival counter at zero for the next one.  The first call on
+ * a device does a set-up step: it looks up that array's device address
+ * (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ * first call before any stream capture.  Every call on a device shares the one
+ * array, so calls whose kernels overlap on the GPU (different streams, or
+ * concurrent host threads) race and give wrong totals: serialise them.
  *
  * Returns EINVAL for n_total < 1, n_total > SPH_RT_NOALLOC_MAX_N or a NULL
  * pointer (the reason is in sph_rt_last_error(NULL) on the calling thread),

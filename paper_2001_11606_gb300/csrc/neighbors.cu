@@ -181,6 +181,7 @@ __host__ __device__ inline uint64_t spread2(uint64_t v) {  // 32 bits -> every 2
 struct Grid {
   double lo[3];
   double inv_cell;
+  double cell;  // cell edge (>= 2 max h)
   int nc[3];
   int dim;
   int ghost_shift;  // key bit that marks ghosts
@@ -337,6 +338,54 @@ __device__ __forceinline__ double exact_r2(double xi, double yi, double zi, doub
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// FP32 pre-filter of the neighbour predicate.  GB300 issues FP64 arithmetic at
+// ~1/64 of the FP32 rate, and a 3-D particle has ~729 candidates for ~113
+// neighbours, so the candidate test runs in FP32 on positions relative to the
+// particle's own cell: rel = x - (lo + c cell), |rel| <= ~cell, stored as
+// float with the particle's (2h)^2 (the exact FP64 cut of a pair is
+// max((2h_i)^2, (2h_j)^2), since rounding is monotonic).  For a candidate in
+// the cell at offset o (-1, 0, 1 per axis) from the particle's,
+//   dx = x_i - x_j = (rel_i - rel_j) - o cell.
+// Error bound (cell = C, unit roundoff u = 2^-24): each rel carries <= 1.01 u C,
+// the difference, the product o cell and the sum add <= 2.02 u C, u C and
+// 3.03 u C, so |dx_f - dx| <= 8.1 u C = 4.8e-7 C; near the cut (r <= C) the
+// squares and sums then differ from the exact r^2 by <= 2 sqrt(3) 4.8e-7 C^2 +
+// 4 u 3 C^2 ~ 2.4e-6 C^2, and the FP32 cut by <= u C^2.  A candidate farther
+// than kNbrBand C^2 (12x that bound) from the cut is decided in FP32; the
+// rest take the exact FP64 predicate, so the neighbour sets are bitwise those
+// of the exact test.
+constexpr float kNbrBand = 3e-5f;
+
+__global__ void rel_kernel(Grid g, const double *px, const double *py, const double *pz,
+                           const double *h, int64_t n, float4 *rel) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double x = px[j], y = py[j], z = pz[j];
+    const int cx = cell_coord(x, g.lo[0], g.inv_cell, g.nc[0]);
+    const int cy = cell_coord(y, g.lo[1], g.inv_cell, g.nc[1]);
+    const int cz = cell_coord(z, g.lo[2], g.inv_cell, g.nc[2]);
+    const double cut = 2.0 * h[j];
+    float4 r;
+    r.x = (float)(x - (g.lo[0] + (double)cx * g.cell));
+    r.y = g.dim > 1 ? (float)(y - (g.lo[1] + (double)cy * g.cell)) : 0.0f;
+    r.z = g.dim > 2 ? (float)(z - (g.lo[2] + (double)cz * g.cell)) : 0.0f;
+    r.w = (float)__dmul_rn(cut, cut);
+    rel[j] = r;
+  }
+}
+
+// 1 / sqrt(r2) in FP64: FP32 seed refined by two Newton steps
+// y <- y (3/2 - r2/2 y^2) (quadratic convergence from ~1e-7 to the FP64
+// rounding level), which costs fewer FP64 operations than an IEEE square
+// root followed by a division.
+__device__ __forceinline__ double rsqrt_fp64(double r2) {
+  double y = (double)rsqrtf((float)r2);
+  const double hr2 = 0.5 * r2;
+  y = y * (1.5 - hr2 * y * y);
+  y = y * (1.5 - hr2 * y * y);
+  return y;
+}
+
 // Bitonic sort of one 64-bit key per lane, ascending across the warp.
 __device__ __forceinline__ uint64_t warp_sort_u64(uint64_t v) {
   int lane = threadIdx.x & 31;
@@ -354,7 +403,7 @@ __device__ __forceinline__ uint64_t warp_sort_u64(uint64_t v) {
 
 template <bool FILL>
 __global__ void neighbor_kernel(Grid g, const double *px, const double *py, const double *pz,
-                                const double *h, const int64_t *cell_start,
+                                const double *h, const float4 *rel, const int64_t *cell_start,
                                 const unsigned *cell_count, int64_t n_int, int64_t *count,
                                 const int64_t *rowptr, int32_t *cols, double *F,
                                 const double *ih, const double *cw) {
@@ -362,11 +411,16 @@ __global__ void neighbor_kernel(Grid g, const double *px, const double *py, cons
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int ncells = g.dim == 3 ? 27 : (g.dim == 2 ? 9 : 3);
+  const float cellf = (float)g.cell;
+  const float band = kNbrBand * cellf * cellf;
   for (int64_t i = warp; i < n_int; i += nwarps) {
-    double xi = px[i], yi = py[i], zi = pz[i], hi = h[i];
+    const double xi = px[i], yi = py[i], zi = pz[i], hi = h[i];
+    const float4 ri = rel[i];
     int c[3] = {cell_coord(xi, g.lo[0], g.inv_cell, g.nc[0]),
                 cell_coord(yi, g.lo[1], g.inv_cell, g.nc[1]),
                 cell_coord(zi, g.lo[2], g.inv_cell, g.nc[2])};
+    // lane k < ncells: the k-th cell around i; sorted by Morton key with the
+    // lane (hence the offset) in the low 5 bits
     uint64_t mykey = ~0ull;
     if (lane < ncells) {
       int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, lane / 9 - 1};
@@ -376,34 +430,46 @@ __global__ void neighbor_kernel(Grid g, const double *px, const double *py, cons
         cc[d] = d < g.dim ? c[d] + o[d] : 0;
         if (d < g.dim && (cc[d] < 0 || cc[d] >= g.nc[d])) ok = false;
       }
-      if (ok) mykey = morton(g, cc[0], cc[1], cc[2]);
+      if (ok) mykey = (morton(g, cc[0], cc[1], cc[2]) << 5) | (uint64_t)lane;
     }
-    uint64_t sorted = warp_sort_u64(mykey);
+    const uint64_t sorted = warp_sort_u64(mykey);
     int64_t out = FILL ? rowptr[i] : 0;
     int64_t total = 0;
     for (int pass = 0; pass < 2; ++pass) {  // interior cells, then ghost cells
       for (int k = 0; k < ncells; ++k) {
-        uint64_t key = __shfl_sync(0xffffffffu, sorted, k);
-        if (key == ~0ull) break;
-        uint64_t kk = key | (pass ? (1ull << g.ghost_shift) : 0ull);
-        int64_t beg = cell_start[kk];
-        int64_t cnt = cell_count[kk];
+        const uint64_t v = __shfl_sync(0xffffffffu, sorted, k);
+        if (v == ~0ull) break;
+        const int ol = (int)(v & 31ull);
+        const uint64_t kk = (v >> 5) | (pass ? (1ull << g.ghost_shift) : 0ull);
+        // -o cell per axis (axes beyond dim stay 0)
+        const float ox = -(float)(ol % 3 - 1) * cellf;
+        const float oy = g.dim > 1 ? -(float)((ol / 3) % 3 - 1) * cellf : 0.0f;
+        const float oz = g.dim > 2 ? -(float)(ol / 9 - 1) * cellf : 0.0f;
+        const int64_t beg = cell_start[kk];
+        const int64_t cnt = cell_count[kk];
         for (int64_t base = 0; base < cnt; base += 32) {
-          int64_t j = beg + base + lane;
+          const int64_t j = beg + base + lane;
           bool hit = false;
-          double r2 = 0.0;
           if (base + lane < cnt && j != i) {
-            double hj = h[j];
-            double cut = 2.0 * fmax(hi, hj);
-            double cut2 = __dmul_rn(cut, cut);
-            r2 = exact_r2(xi, yi, zi, px[j], py[j], pz[j]);
-            hit = r2 < cut2;
+            const float4 rj = rel[j];
+            const float dx = (ri.x - rj.x) + ox;
+            const float dy = (ri.y - rj.y) + oy;
+            const float dz = (ri.z - rj.z) + oz;
+            const float r2f = dx * dx + dy * dy + dz * dz;
+            const float c2f = fmaxf(ri.w, rj.w);
+            if (r2f < c2f - band) {
+              hit = true;
+            } else if (!(r2f > c2f + band)) {  // within the band: the exact test
+              const double cut = 2.0 * fmax(hi, h[j]);
+              hit = exact_r2(xi, yi, zi, px[j], py[j], pz[j]) < __dmul_rn(cut, cut);
+            }
           }
-          unsigned m = __ballot_sync(0xffffffffu, hit);
+          const unsigned m = __ballot_sync(0xffffffffu, hit);
           if (FILL && hit) {
-            int64_t at = out + total + __popc(m & ((1u << lane) - 1u));
+            const int64_t at = out + total + __popc(m & ((1u << lane) - 1u));
             cols[at] = (int32_t)j;
-            const double r = sqrt(r2), ir = 1.0 / r;
+            const double r2 = exact_r2(xi, yi, zi, px[j], py[j], pz[j]);
+            const double ir = rsqrt_fp64(r2), r = r2 * ir;
             const double dwi = cw[i] * spline_dw(r * ih[i]);
             const double dwj = cw[j] * spline_dw(r * ih[j]);
             F[at] = 0.5 * (dwi + dwj) * ir;  // F_ij = W'_ij / r, two-h average
@@ -421,20 +487,34 @@ __global__ void neighbor_kernel(Grid g, const double *px, const double *py, cons
 // columns (moved to the copied particle; a copy of the row itself drops out)
 // form B; Dirichlet ghosts form the boundary-coupling list.
 // --------------------------------------------------------------------------
+// One warp per row: the lanes take 32 consecutive entries at a time, so the
+// list reads and the compacted writes are coalesced; ballots keep the entries
+// in list order.
 __global__ void op_count_kernel(const int64_t *nbr_ptr, const int32_t *nbr_col,
                                 const int32_t *kind, const int32_t *copysrc, int64_t n_int,
                                 int64_t *mat_cnt, int64_t *gh_cnt) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n_int; i += nwarps) {
     int64_t m = 0, g = 0;
-    for (int64_t k = nbr_ptr[i]; k < nbr_ptr[i + 1]; ++k) {
-      int32_t j = nbr_col[k];
-      int32_t kj = kind[j];
-      if (kj == SPH_RT_DIRICHLET) ++g;
-      else if (kj == SPH_RT_INTERIOR || copysrc[j] != i) ++m;
+    const int64_t beg = nbr_ptr[i], end = nbr_ptr[i + 1];
+    for (int64_t k0 = beg; k0 < end; k0 += 32) {
+      const int64_t k = k0 + lane;
+      bool isg = false, ism = false;
+      if (k < end) {
+        const int32_t j = nbr_col[k];
+        const int32_t kj = kind[j];
+        isg = kj == SPH_RT_DIRICHLET;
+        ism = !isg && (kj == SPH_RT_INTERIOR || copysrc[j] != i);
+      }
+      g += __popc(__ballot_sync(0xffffffffu, isg));
+      m += __popc(__ballot_sync(0xffffffffu, ism));
     }
-    mat_cnt[i] = m;
-    gh_cnt[i] = g;
+    if (lane == 0) {
+      mat_cnt[i] = m;
+      gh_cnt[i] = g;
+    }
   }
 }
 
@@ -443,25 +523,49 @@ __global__ void op_fill_kernel(const int64_t *nbr_ptr, const int32_t *nbr_col, c
                                int64_t n_int, const int64_t *mat_ptr, int32_t *mat_col,
                                double *mat_G, const int64_t *gh_ptr, int32_t *gh_slot,
                                double *gh_W) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n_int; i += nwarps) {
     int64_t m = mat_ptr[i], g = gh_ptr[i];
-    double Vi = V[i];
-    for (int64_t k = nbr_ptr[i]; k < nbr_ptr[i + 1]; ++k) {
-      int32_t j = nbr_col[k];
-      int32_t kj = kind[j];
-      double Fk = nbr_F[k];
-      if (kj == SPH_RT_DIRICHLET) {
-        gh_slot[g] = j;
-        gh_W[g] = V[j] * Fk;
-        ++g;
-      } else {
-        int32_t col = kj == SPH_RT_INTERIOR ? j : copysrc[j];
-        if (col == i) continue;
-        mat_col[m] = col;
-        mat_G[m] = (Vi * V[j]) * Fk;
-        ++m;
+    const double Vi = V[i];
+    const int64_t beg = nbr_ptr[i], end = nbr_ptr[i + 1];
+    for (int64_t k0 = beg; k0 < end; k0 += 32) {
+      const int64_t k = k0 + lane;
+      bool isg = false, ism = false;
+      int32_t col = 0;
+      double val = 0.0;
+      if (k < end) {
+        const int32_t j = nbr_col[k];
+        const int32_t kj = kind[j];
+        const double Fk = nbr_F[k];
+        if (kj == SPH_RT_DIRICHLET) {
+          isg = true;
+          col = j;
+          val = V[j] * Fk;
+        } else {
+          col = kj == SPH_RT_INTERIOR ? j : copysrc[j];
+          if (col != i) {  // a copy of the row itself drops out
+            ism = true;
+            val = (Vi * V[j]) * Fk;
+          }
+        }
       }
+      const unsigned bg = __ballot_sync(0xffffffffu, isg);
+      const unsigned bm = __ballot_sync(0xffffffffu, ism);
+      if (isg) {
+        const int64_t at = g + __popc(bg & lt);
+        gh_slot[at] = col;
+        gh_W[at] = val;
+      }
+      if (ism) {
+        const int64_t at = m + __popc(bm & lt);
+        mat_col[at] = col;
+        mat_G[at] = val;
+      }
+      g += __popc(bg);
+      m += __popc(bm);
     }
   }
 }
@@ -507,6 +611,7 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   Grid g;
   g.dim = dim;
   double cell = 2.0 * hb[6] * (1.0 + 1e-9);
+  g.cell = cell;
   g.inv_cell = 1.0 / cell;
   int maxnc = 1;
   for (int d = 0; d < 3; ++d) {
@@ -599,8 +704,13 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   int gw = (int)ceil_div(warps, kWarpsPerBlock);
   int gcap = s->num_sms * 8;
   if (gw > gcap) gw = gcap;
-  neighbor_kernel<false><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, start, cnt, n_int,
-                                                nc, nullptr, nullptr, nullptr, nullptr, nullptr);
+  float4 *rel = dalloc<float4>(s, n);
+  if (!rel) return SPH_RT_ENOMEM;
+  rel_kernel<<<grid1(s, n), kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, n, rel);
+  SPH_LAUNCHED(s);
+  neighbor_kernel<false><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, rel, start, cnt,
+                                                n_int, nc, nullptr, nullptr, nullptr, nullptr,
+                                                nullptr);
   SPH_LAUNCHED(s);
   rc = exclusive_scan(s, nc, n_int, s->nbr_ptr);
   if (rc) return rc;
@@ -617,8 +727,9 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   if (!ih || !cw) return SPH_RT_ENOMEM;
   kernel_coef_kernel<<<grid1(s, n), kBlock, 0, st>>>(n, dim, s->h, ih, cw);
   SPH_LAUNCHED(s);
-  neighbor_kernel<true><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, start, cnt, n_int,
-                                               nullptr, s->nbr_ptr, s->nbr_col, s->nbr_F, ih, cw);
+  neighbor_kernel<true><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, rel, start, cnt,
+                                               n_int, nullptr, s->nbr_ptr, s->nbr_col, s->nbr_F,
+                                               ih, cw);
   SPH_LAUNCHED(s);
 
   // operator sparsity
@@ -626,7 +737,8 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   s->mat_ptr = dalloc<int64_t>(s, n_int + 1);
   s->gh_ptr = dalloc<int64_t>(s, n_int + 1);
   if (!mc || !gc || !s->mat_ptr || !s->gh_ptr) return SPH_RT_ENOMEM;
-  int gi = grid1(s, n_int);
+  int gi = (int)ceil_div(n_int, kWarpsPerBlock);  // a warp per row
+  if (gi > s->num_sms * 8) gi = s->num_sms * 8;
   op_count_kernel<<<gi, kBlock, 0, st>>>(s->nbr_ptr, s->nbr_col, s->kind, s->copysrc, n_int, mc, gc);
   SPH_LAUNCHED(s);
   if ((rc = exclusive_scan(s, mc, n_int, s->mat_ptr))) return rc;
@@ -649,7 +761,7 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   SPH_LAUNCHED(s);
   SPH_CUDA(s, cudaStreamSynchronize(st));
   // set-up scratch back to the free list
-  void *scratch[] = {cx, cy, cz, hc, bbox, key, cnt, cur, cnt64, start, nc, mc, gc, ih, cw};
+  void *scratch[] = {cx, cy, cz, hc, bbox, key, cnt, cur, cnt64, start, nc, mc, gc, ih, cw, rel};
   for (void *p : scratch) dfree(s, p);
   return SPH_RT_OK;
 }

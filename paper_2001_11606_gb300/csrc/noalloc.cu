@@ -26,7 +26,10 @@ constexpr int64_t kNaPerBlock = (int64_t)kNaBlock * kNaItems;  // 8192
 constexpr int kNaMaxBlocks = 4096;
 static_assert(kNaPerBlock * kNaMaxBlocks == SPH_RT_NOALLOC_MAX_N, "size bound");
 
-// Two partial sums per block, then the arrival counter (64 KiB + 256 B).
+// Two partial sums per block, then the arrival counter (64 KiB + 256 B).  Like
+// every __device__ variable without an initialiser the array is zero when the
+// module is loaded, so the counter starts at zero; each call's last block
+// resets it for the next call.
 constexpr int kNaCounterSlot = 2 * kNaMaxBlocks;
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNaMaxBlocks + 32];
 
@@ -93,14 +96,6 @@ extern "C" sph_rt_status sph_rt_energy_totals_noalloc(int64_t n_total, const int
       if (err != cudaSuccess) {
         cudaGetLastError();
         sphrt::set_thread_error(std::string("cudaGetSymbolAddress failed: ") +
-                                cudaGetErrorString(err));
-        return SPH_RT_EDEVICE;
-      }
-      // the arrival counter must start at zero
-      err = cudaMemsetAsync(static_cast<double *>(p) + kNaCounterSlot, 0, sizeof(unsigned), st);
-      if (err != cudaSuccess) {
-        cudaGetLastError();
-        sphrt::set_thread_error(std::string("clearing the scratch counter failed: ") +
                                 cudaGetErrorString(err));
         return SPH_RT_EDEVICE;
       }

@@ -240,6 +240,78 @@ class Manufactured:
         QE = 4.0 * a * T**3 * dTdt - divflux
         return Qe, QE
 
+    def series(self, x):
+        """SourceSeries at fixed positions x: the same sources and fields for
+        many times, with the spatial factors computed once."""
+        return SourceSeries(self, x)
+
+
+class SourceSeries:
+    """Sources and fields of a Manufactured solution at fixed positions.
+
+    T = 1 + amp S(x) g(t) with S = prod_a sin(pi x_a) and g = e^{-t}, so grad T,
+    the Hessian of T and the terms built from them are spatial factors of S
+    times powers of amp g.  They are computed once here; each time then costs
+    a few vector operations.  Same formulas as Manufactured.sources (equal to
+    rounding)."""
+
+    def __init__(self, mms: Manufactured, x):
+        self.m = mms
+        d = mms.dim
+        sn = np.sin(np.pi * x)
+        cs = np.cos(np.pi * x)
+        self.S = np.prod(sn, axis=1)
+        gS = np.empty_like(x)
+        for al in range(d):
+            others = np.prod(np.delete(sn, al, axis=1), axis=1) if d > 1 else 1.0
+            gS[:, al] = np.pi * cs[:, al] * others
+        # H_S grad_S and trace(H_S) (H_S: Hessian of S)
+        HgS = np.zeros_like(x)
+        for al in range(d):
+            for be in range(d):
+                if al == be:
+                    Hab = -np.pi**2 * self.S
+                else:
+                    rest = [k for k in range(d) if k not in (al, be)]
+                    o = np.prod(sn[:, rest], axis=1) if rest else 1.0
+                    Hab = np.pi**2 * cs[:, al] * cs[:, be] * o
+                HgS[:, al] += Hab * gS[:, be]
+        self.trH = -d * np.pi**2 * self.S
+        self.gS = gS
+        self.gnS = np.sqrt(np.sum(gS * gS, axis=1))
+        safe = np.where(self.gnS > 0.0, self.gnS, 1.0)
+        # d|grad S| = H_S grad_S / |grad_S| (0 where grad S = 0)
+        self.dgnS = np.where(self.gnS[:, None] > 0.0, HgS / safe[:, None], 0.0)
+
+    def fields(self, t):
+        m = self.m
+        T = 1.0 + m.amp * self.S * math.exp(-t)
+        return m.cv * T, m.a * T**4
+
+    def sources(self, t):
+        m = self.m
+        ag = m.amp * math.exp(-t)
+        T = 1.0 + ag * self.S
+        dTdt = -ag * self.S
+        a, c, p = m.a, m.c, m.p
+        gnorm = ag * self.gnS
+        sigma = m.sigma0 * T**p
+        R = 4.0 * gnorm / (sigma * T)
+        lam, dlam = _limiter_value_and_slope(R, m.limiter, m.larsen_k)
+        D = c * lam / sigma
+        lapE = 4.0 * a * (3.0 * T**2 * gnorm**2 + T**3 * (ag * self.trH))
+        if m.limiter == 0 and p == 0.0:  # constant D: grad D = 0
+            return m.rho * m.cv * dTdt, 4.0 * a * T**3 * dTdt - D * lapE
+        grad = ag * self.gS
+        dR = (4.0 / m.sigma0) * (ag * self.dgnS * T[:, None] ** (-(p + 1.0))
+                                 - (p + 1.0) * gnorm[:, None] * T[:, None] ** (-(p + 2.0)) * grad)
+        dD = (c / sigma)[:, None] * (dlam[:, None] * dR - (lam * p / T)[:, None] * grad)
+        dE = 4.0 * a * (T**3)[:, None] * grad
+        divflux = np.sum(dD * dE, axis=1) + D * lapE
+        Qe = m.rho * m.cv * dTdt
+        QE = 4.0 * a * T**3 * dTdt - divflux
+        return Qe, QE
+
 
 # ---------------------------------------------------------------------------
 # Named workloads (sizes and physics of the verification problems)
@@ -256,6 +328,7 @@ class Workload:
     mms: Manufactured | None = None
     e0: np.ndarray | None = None
     E0: np.ndarray | None = None
+    _series: SourceSeries | None = field(default=None, repr=False)
 
     def step_inputs(self, n: int):
         """Sources and ghost values for step n (time t^n = n dt), caller order.
@@ -268,9 +341,11 @@ class Workload:
             ge = self.e0.copy()
             gE = self.E0.copy()
             return z, z.copy(), ge, gE
+        if self._series is None:
+            self._series = self.mms.series(P.pos)
         t = n * self.dt
-        Qe, QE = self.mms.sources(P.pos, t)
-        ge, gE = self.mms.fields(P.pos, t)
+        Qe, QE = self._series.sources(t)
+        ge, gE = self._series.fields(t)
         return Qe, QE, ge, gE
 
 

@@ -137,6 +137,15 @@ _SIGNATURES = [
     ("sph_rt_batch_last_error", C.c_char_p, [_P]),
     ("sph_rt_batch_destroy", None, [_P]),
 ]
+# include/sph_rt_noalloc.h
+_SIGNATURES_NOALLOC = [
+    ("sph_rt_energy_totals_noalloc", C.c_int, [C.c_int64] + [_P] * 7),
+]
+
+
+# Largest n_total of sph_rt_energy_totals_noalloc (SPH_RT_NOALLOC_MAX_N in
+# include/sph_rt_noalloc.h): 4096 thread blocks of 8192 particles.
+NOALLOC_MAX_N = 4096 * 8192
 
 
 def library_path() -> str:
@@ -154,12 +163,27 @@ def load(build_if_missing: bool = True):
     if not os.path.exists(path):
         raise RuntimeError(f"libsphrt.so not found at {path}; run paper_2001_11606_gb300.build")
     L = C.CDLL(path)
-    for name, res, args in _SIGNATURES:
+    for name, res, args in _SIGNATURES + _SIGNATURES_NOALLOC:
         fn = getattr(L, name)
         fn.restype = res
         fn.argtypes = args
     _lib = L
     return L
+
+
+def energy_totals_noalloc(n_total, kind, mass, rho, e, E, totals, stream=0):
+    """sph_rt_energy_totals_noalloc (include/sph_rt_noalloc.h) with raw DEVICE
+    pointers (ints, e.g. torch's data_ptr(); 0 = NULL) and a cudaStream_t
+    handle; returns the status code.  The reason of a failure is in
+    last_thread_error()."""
+    fn = load().sph_rt_energy_totals_noalloc
+    ptrs = [C.c_void_p(p) if p else None for p in (kind, mass, rho, e, E, totals)]
+    return fn(int(n_total), *ptrs, C.c_void_p(stream) if stream else None)
+
+
+def last_thread_error() -> str:
+    """Message of the last failed handle-less call on this thread."""
+    return load().sph_rt_last_error(None).decode()
 
 
 def exported_symbols():

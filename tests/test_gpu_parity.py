@@ -218,6 +218,57 @@ def test_row_tile_shapes_parity(n, h, precond, precision, tol):
     assert r["err_e"] < tol and r["err_E"] < tol, (r["err_e"], r["err_E"])
 
 
+def _larsen_workload(n, k, steps):
+    # 3-D manufactured problem with sigma = T^-3 and the Larsen limiter of exponent k
+    # (Sec. 2.1; k = 2 is the paper's default), sources made with the same limiter
+    w = I._mms_workload(f"mms3d-larsen{k:g}-{n}^3", 3, n, 2, -3.0, 2, 1e-3, steps)
+    w.mms.larsen_k = k
+    w.params["larsen_k"] = k
+    return w
+
+
+@pytest.mark.parametrize("k", [2.0, 3.0])
+def test_larsen_properties_and_operator_match_oracle(k):
+    # the Larsen branch of the limiter (k = 2: its square-root form) on the device
+    w = _larsen_workload(8, k, 1)
+    P = w.particles
+    S = sphrt.solver_for(w, precond=sphrt.PRECOND_JACOBI)
+    Qe, QE, ge, gE = w.step_inputs(1)
+    S.step(w.dt, Qe, QE, ge, gE)
+    pg = S.get_properties()
+    po = O.Problem(P, w.params).properties(w.e0, w.E0, w.dt)
+    m = P.kind == 0
+    assert np.min(po["R"][m]) > 0.05  # the limiter is away from its R = 0 value
+    for key in ("R", "lambda", "D"):
+        np.testing.assert_allclose(pg[key][m], po[key][m], rtol=1e-13, atol=0, err_msg=key)
+
+
+@pytest.mark.parametrize("k", [2.0, 3.0])
+def test_larsen_full_steps_parity(k):
+    w = _larsen_workload(16, k, 3)
+    r = run_both(w, 3, orc_over=TIGHT)
+    assert r["err_e"] < 1e-10 and r["err_E"] < 1e-10, (r["err_e"], r["err_E"])
+
+
+@pytest.mark.parametrize("make,precision,tol", [
+    (lambda: I.mms_3d(n=32, steps=3), sphrt.MIXED, 1e-8),
+    (lambda: I.mms_3d_lp(n=32, steps=3), sphrt.MIXED, 1e-8),
+    (lambda: I.mms_3d_lp(n=32, steps=3), sphrt.FP64, 1e-10)])
+def test_parity_where_the_fine_level_takes_its_full_size_path(make, precision, tol):
+    # 32^3 = 32,768 rows with ~101 stored entries each (3.3 M, above the 600k-entry
+    # threshold): the finest level runs the A P post-smoothing sweep with the fused
+    # inner product and the next level is summed from A P, in FP32 in the mixed
+    # form -- the kernels of the 64^3 .. 256^3 workloads.  Element by element
+    # against the oracle over 3 steps, for both manufactured physics (sigma = 1 with
+    # lambda = 1/3, and sigma = T^-3 with the Levermore limiter).
+    w = make()
+    r = run_both(w, w.steps, gpu_over=dict(precision=precision, precond=sphrt.PRECOND_AMG),
+                 orc_over=TIGHT)
+    levels = r["S"].amg_info()
+    assert levels[0][1] > 600_000 and len(levels) >= 3, levels
+    assert r["err_e"] < tol and r["err_E"] < tol, (r["err_e"], r["err_E"])
+
+
 def test_mixed_precision_parity():
     w = I.mms_3d_lp(n=16, steps=3)
     r = run_both(w, 3, gpu_over=dict(precision=sphrt.MIXED, precond=sphrt.PRECOND_AMG),

@@ -68,3 +68,21 @@ def test_manufactured_sources_match_finite_differences():
         Qe2, QE2 = _fd_sources(m, x, 0.3, eps=2e-4)
         assert np.allclose(Qe, Qe2, rtol=1e-6, atol=1e-8)
         assert np.allclose(QE, QE2, rtol=2e-3, atol=2e-3 * np.max(np.abs(QE)))
+
+
+def test_source_series_equals_sources():
+    # the per-step inputs of a workload come from SourceSeries (spatial factors
+    # computed once); they equal Manufactured.sources / fields to rounding
+    rng = np.random.default_rng(1)
+    for dim, p, lim in ((2, 0.0, 0), (3, 0.0, 0), (3, -3.0, 1), (3, -3.0, 2), (2, -3.0, 2)):
+        m = I.Manufactured(dim=dim, p=p, limiter=lim)
+        x = rng.uniform(-0.1, 1.1, size=(300, dim))
+        ser = m.series(x)
+        for t in (0.0, 0.37, 2.0):
+            Qe, QE = m.sources(x, t)
+            Qe2, QE2 = ser.sources(t)
+            assert np.allclose(Qe2, Qe, rtol=1e-14, atol=0)
+            assert np.allclose(QE2, QE, rtol=1e-13, atol=1e-14 * np.max(np.abs(QE)))
+            e, E = m.fields(x, t)
+            e2, E2 = ser.fields(t)
+            assert np.array_equal(e, e2) and np.array_equal(E, E2)
