@@ -343,6 +343,9 @@ def main():
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"],
                     help="both: the mixed form is the value, the FP64 form is timed beside it")
     ap.add_argument("--precond", default="amg", choices=["jacobi", "chebyshev", "amg"])
+    ap.add_argument("--fine-post-smooth", type=int, default=None, choices=[0, 1],
+                    help="AMG finest-level post-smoothing (default: the library's)")
+    ap.add_argument("--reliable-drop", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")
@@ -387,6 +390,10 @@ def main():
     head = forms[0]
     prec_of = {"mixed": sphrt.MIXED, "fp64": sphrt.FP64}
     extra = {"check_every": args.check_every} if args.check_every else {}
+    if args.fine_post_smooth is not None:
+        extra["fine_post_smooth"] = args.fine_post_smooth
+    if args.reliable_drop is not None:
+        extra["reliable_drop"] = args.reliable_drop
 
     def make_cfg(form, **kw):
         return sphrt.config_from_params(w.params, device=local, stream=stream.cuda_stream,

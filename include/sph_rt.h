@@ -100,6 +100,21 @@ typedef struct {
                            dependent launch (a kernel's blocks are scheduled while its
                            predecessor drains; each waits for the predecessor's results before
                            touching them), 0: ordinary stream order.  Same results either way */
+  int32_t fine_post_smooth; /* AMG preconditioner only.  1: the V-cycle smooths before and after
+                           the coarse correction on every level (symmetric; the CG product
+                           B p is a sweep of its own).  0: the finest level only pre-smooths;
+                           its residual sweep and the A P sweep of the coarse correction then
+                           give B z, so the CG (flexible: the V-cycle is not symmetric) needs
+                           no product sweep -- two sweeps of the fine operator per iteration
+                           instead of three, for ~1.4x the iterations.  With 0 and the mixed
+                           precision the CG vectors are FP32 too, and the FP64 residual
+                           replaces the recursive one (see reliable_drop).  Requires
+                           cheb_degree = 1 */
+  double reliable_drop; /* mixed precision with fine_post_smooth = 0: the FP64 residual
+                           b - A x replaces the FP32 recursive one whenever the latter has
+                           dropped by this factor since the last replacement, and before
+                           convergence is accepted (the solve stops on the FP64 residual).
+                           In (0, 1) */
   int32_t device;       /* CUDA device ordinal */
   void *stream;         /* cudaStream_t to run on (borrowed); NULL = library-owned stream */
 } sph_rt_config;
@@ -221,11 +236,14 @@ sph_rt_status sph_rt_kernel_stats(sph_rt *s, int64_t *launches, double *total_ms
 /* The same counters split by kernel: SPH_RT_KERNEL_SPMV_PQ (the CG product
  * fused with the p, q updates and (p, q)), SPH_RT_KERNEL_RESID (residual
  * sweeps: CG start and V-cycle fine level), SPH_RT_KERNEL_CHEB (fine-level
- * Chebyshev smoother / preconditioner sweeps), SPH_RT_KERNEL_POST (the first
- * fine-level post-smoothing step, a sweep of A P with the prolongation folded
- * in).  Cleared with the totals. */
+ * Chebyshev smoother / preconditioner sweeps), SPH_RT_KERNEL_POST (the sweep
+ * of A P on the finest level with the prolongation folded in: the first
+ * post-smoothing step, or with fine_post_smooth = 0 the sweep that forms z and
+ * B z), SPH_RT_KERNEL_TRUE_RESID (with fine_post_smooth = 0: the FP64 residual
+ * b - A x at the start of a solve and at each reliable update).  Cleared with
+ * the totals. */
 enum { SPH_RT_KERNEL_SPMV_PQ = 0, SPH_RT_KERNEL_RESID = 1, SPH_RT_KERNEL_CHEB = 2,
-       SPH_RT_KERNEL_POST = 3 };
+       SPH_RT_KERNEL_POST = 3, SPH_RT_KERNEL_TRUE_RESID = 4 };
 sph_rt_status sph_rt_kernel_stats_kind(sph_rt *s, int32_t kind, int64_t *launches,
                                        double *total_ms, double *bytes);
 

@@ -83,6 +83,9 @@ struct SphLevel {
   int32_t *apg_src = nullptr;     // (P^T (A P): each A P entry (i, K) adds to (agg[i], K))
   double *ap_val = nullptr;     // [nnz_ap]
   float *ap_val32 = nullptr;
+  // finest level, mixed form with the V-cycle's CG product (fine_post_smooth = 0):
+  // the CG's FP32 search direction p, its product q = B p and w = B z
+  float *p32 = nullptr, *q32 = nullptr, *w32 = nullptr;
   std::vector<void *> owned;
 };
 
@@ -846,6 +849,148 @@ __global__ void __launch_bounds__(kBlock, kCoarseMinBlocks)
 }
 
 // ---------------------------------------------------------------------------
+// The finest level without post-smoothing, for the CG whose product comes from
+// the V-cycle (config.fine_post_smooth = 0).  With the zero-guess smoother
+// start z_pre = c0 D^{-1} r, the residual res = r - B z_pre (the V-cycle's
+// first sweep) and the coarse correction e_c, the preconditioned residual is
+// z = z_pre + P e_c, and
+//   B z = B z_pre + (B P) e_c = (r - res) + (res - res2) = r - res2,
+// res2 = res - (A P) e_c -- the A P sweep gives B z without a sweep of B.  The
+// CG then needs no product sweep of its own: q = B p = B z + beta q_old.
+// The sweep also forms the iteration's inner products, so alpha and beta are
+// known when it ends (one reduction per iteration):
+//   a = (r, z), b = (r, z_old), c = (z, B z), d = (z, q_old), e = (p_old, B z)
+//   beta = (a - b) / rho_old     (flexible, Polak-Ribiere: the V-cycle without
+//                                 post-smoothing is not symmetric)
+//   (p, q) = (z + beta p_old, B z + beta q_old) = c + beta (d + e) + beta^2 (p_old, q_old)
+//   alpha = a / (p, q)
+// first = 1 (the first iteration of a solve): p = z, beta = 0, (p, q) = c.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fcg_scalars(const double (&o)[5], int first, Scalars *sc) {
+  const double a = o[0];
+  double beta = 0.0, pq = o[2];
+  if (!first) {
+    beta = (a - o[1]) / sc->rho;
+    pq = o[2] + beta * (o[3] + o[4]) + beta * beta * sc->pq;
+  }
+  sc->beta = beta;
+  sc->rho = a;
+  sc->pq = pq;
+  sc->pfirst = first;
+  if (!(pq > 0.0) || !(pq < 1e308) || !(a == a)) {  // loss of definiteness or NaN
+    sc->breakdown = 1;
+    sc->done = 1;
+  } else {
+    sc->alpha = a / pq;
+  }
+}
+
+// Row epilogue shared by the two forms of the last sweep: z and B z of row i
+// and the five inner-product partials.
+template <typename VT>
+__device__ __forceinline__ void fcg_row(int64_t i, VT zn, VT wn, const VT *r, VT *z, VT *w,
+                                        const VT *p, const VT *q, int first, double (&acc)[5]) {
+  const double ri = (double)r[i], zd = (double)zn, wd = (double)wn;
+  acc[0] += ri * zd;
+  acc[2] += zd * wd;
+  if (!first) {
+    acc[1] += ri * (double)z[i];
+    acc[3] += zd * (double)q[i];
+    acc[4] += (double)p[i] * wd;
+  }
+  z[i] = zn;
+  w[i] = wn;
+}
+
+template <typename VT>
+__device__ __forceinline__ void fcg_reduce(double (&acc)[5], int first, Scalars *sc,
+                                           double *partials) {
+  __shared__ double sh[32];
+  for (int k = 0; k < 5; ++k) {
+    acc[k] = block_sum(acc[k], sh);
+    __syncthreads();
+  }
+  double out[5];
+  const bool mx[5] = {false, false, false, false, false};
+  if (last_block_combine<5>(acc, partials, &sc->counter, out, mx) && threadIdx.x == 0)
+    fcg_scalars(out, first, sc);
+}
+
+// The A P sweep: res2 = res - (A P) e_c, z = z_pre + P e_c, B z = r - res2.
+// (five FP64 partials on top of the row tile: compiled for 3 resident blocks
+// per SM, where the register file holds them without spilling)
+constexpr int kFcgMinBlocks = 3;
+template <int W, int U, typename MT, typename VT>
+__global__ void __launch_bounds__(kBlock, kFcgMinBlocks)
+    fine_ap_cg_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col, const MT *ap_val,
+                      const int32_t *agg, const VT *ec, const VT *z_pre, const VT *res,
+                      const VT *r, VT *z, VT *w, const VT *p, const VT *q, int first, Scalars *sc,
+                      double *partials, int *wflag) {
+  pdl_wait();
+  if (sc->done) {
+    mark_work(wflag, 0);
+    return;
+  }
+  mark_work(wflag, 1);
+  const int own = tile_own_row<W>(threadIdx.x & 31);
+  int64_t r0, r1;
+  warp_rows<W>(n, r0, r1);
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const VT s = tile_row_sums<W, U, MT, VT>(base, rows, ap_ptr, ap_col, ap_val, ec);
+    if (own < rows) {
+      const int32_t a = agg[i];
+      const VT pe = a >= 0 ? ec[a] : VT(0);
+      const VT zn = z_pre[i] + pe;
+      const VT res2 = res[i] - s;
+      fcg_row<VT>(i, zn, r[i] - res2, r, z, w, p, q, first, acc);
+    }
+  }
+  fcg_reduce<VT>(acc, first, sc, partials);
+}
+
+// Without A P (operators below the A P threshold): z = z_pre + P e_c into t,
+// then B z by a sweep of B.
+template <typename VT>
+__global__ void fcg_prolong_kernel(int64_t n, const int32_t *agg, const VT *ec, const VT *z_pre,
+                                   VT *t, const Scalars *sc) {
+  pdl_wait();
+  if (sc->done) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = agg[i];
+    t[i] = z_pre[i] + (a >= 0 ? ec[a] : VT(0));
+  }
+}
+template <int W, int U, typename MT, typename VT>
+__global__ void __launch_bounds__(kBlock, kFcgMinBlocks)
+    fcg_spmv_dot_kernel(CsrView<MT> A, const VT *t, const VT *r, VT *z, VT *w, const VT *p,
+                        const VT *q, int first, Scalars *sc, double *partials, int *wflag) {
+  pdl_wait();
+  if (sc->done) {
+    mark_work(wflag, 0);
+    return;
+  }
+  mark_work(wflag, 1);
+  const int own = tile_own_row<W>(threadIdx.x & 31);
+  int64_t r0, r1;
+  warp_rows<W>(A.n, r0, r1);
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const VT s = tile_row_sums<W, U, MT, VT>(base, rows, A.ptr, A.col, A.val, t);
+    if (own < rows) {
+      const VT ti = t[i];
+      fcg_row<VT>(i, ti, fmadd((VT)A.diag[i], ti, s), r, z, w, p, q, first, acc);
+    }
+  }
+  fcg_reduce<VT>(acc, first, sc, partials);
+}
+
+// ---------------------------------------------------------------------------
 // Cluster-resident V-cycle tail: the levels from `tail_level` down (small
 // operators that live in L2) run as ONE launch of one thread-block cluster.
 // Phases that depend on other rows are separated by cluster barriers instead
@@ -1310,6 +1455,9 @@ static int coarse_degree(const sph_rt *s, const SphLevel *L) {
   return L->n <= kCoarseTarget * 4 ? 6 : 3 * s->cfg.cheb_degree;
 }
 
+bool fcg_active(const sph_rt *s);
+sph_rt_status fcg_vectors(sph_rt *s, FcgVecs *v);
+
 static sph_rt_status numeric(sph_rt *s) {
   for (size_t l = 0; l + 1 < s->levels.size(); ++l) {
     SphLevel *L = s->levels[l], *C = s->levels[l + 1];
@@ -1385,6 +1533,12 @@ static sph_rt_status numeric(sph_rt *s) {
       convert_kernel<double, float><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(
           L->n, L->invdiag, L->invdiag32);
       SPH_LAUNCHED(s);
+    }
+    // FP32 CG vectors of the V-cycle-product CG, allocated here (not while a
+    // loop graph is being captured)
+    if (fcg_active(s)) {
+      FcgVecs v;
+      if ((rc = fcg_vectors(s, &v))) return rc;
     }
   }
   return SPH_RT_OK;
@@ -1725,6 +1879,105 @@ sph_rt_status amg_apply(sph_rt *s, const double *r, double *z, const Scalars *sc
     return SPH_RT_OK;
   }
   return vcycle<double>(s, 0, r, z, sc, init_done, df, dot_done);
+}
+
+// ---------------------------------------------------------------------------
+// The V-cycle of the CG with the V-cycle's product (fine_post_smooth = 0), in
+// the precision T of the hierarchy: from r and the smoother start z_pre (in
+// the finest level's d, written by the CG update or the residual kernel), the
+// finest-level residual sweep, the coarse V-cycle (symmetric, as always) and
+// the last sweep that forms z, w = B z and the CG scalars (see
+// fine_ap_cg_kernel).  The vectors are those of FcgVecs.
+// ---------------------------------------------------------------------------
+bool fcg_active(const sph_rt *s) {
+  return s->cfg.fine_post_smooth == 0 && s->cfg.precond == SPH_RT_PRECOND_AMG &&
+         s->levels.size() >= 2;
+}
+
+sph_rt_status fcg_vectors(sph_rt *s, FcgVecs *v) {
+  SphLevel *L0 = s->levels[0];
+  if (s->cfg.precision == SPH_RT_MIXED) {
+    if (!L0->p32) {
+      L0->p32 = lalloc<float>(s, L0, L0->n);
+      L0->q32 = lalloc<float>(s, L0, L0->n);
+      L0->w32 = lalloc<float>(s, L0, L0->n);
+      if (!L0->p32 || !L0->q32 || !L0->w32) return SPH_RT_ENOMEM;
+    }
+    v->f32 = {L0->r32, L0->z32, L0->w32, L0->p32, L0->q32, L0->d32, L0->invdiag32};
+  } else {
+    v->f64 = {s->r, s->z, s->w, s->p, s->q, L0->d, L0->invdiag};
+  }
+  v->cf = s->cheb_slots + 1;
+  return SPH_RT_OK;
+}
+
+template <typename T>
+static sph_rt_status fcg_cycle_t(sph_rt *s, const FcgSet<T> &v, int first) {
+  using LV = LevelVecs<T>;
+  SphLevel *L = s->levels[0];
+  CsrView<T> A = LV::view(L);
+  const Scalars *sc = s->sc;
+  T *res = LV::res(L);
+  const int gw = row_grid(s->num_sms, L->n, A.W, A.U);
+  int *wf = timing_begin(s);
+  SPH_DISPATCH_SHAPE(A.W, A.U,
+                     (pdl_launch(s, fine_resid_level_kernel<W, U, T, T>, gw, kBlock, 0, A, v.r,
+                                 v.zpre, res, sc, wf)));
+  SPH_LAUNCHED(s);
+  timing_end(s, (4.0 + sizeof(T)) * (double)A.nnz + (8.0 + 4.0 * sizeof(T)) * (double)A.n,
+             kTimedResid);
+  SphLevel *C = s->levels[1];
+  const int deg = s->cfg.cheb_degree;
+  const bool fuse = s->levels.size() > 2 && !(s->tail_level > 0 && s->tail_level == 1);
+  if (fuse) {
+    const int wc = (deg - 1) % 2;
+    T *zc_first = wc == 0 ? LV::z(C) : LV::t(C);
+    pdl_launch(s, restrict_init_kernel<T, T>, gcap(s, C->n, kBlock), kBlock, 0, C->n, L->agg_ptr,
+               L->agg_mem, (const T *)res, LV::r(C), LV::view(C).invdiag, s->cheb_slots + 2,
+               LV::d(C), zc_first, sc);
+  } else {
+    pdl_launch(s, restrict_kernel<T>, gcap(s, C->n, kBlock), kBlock, 0, C->n, L->agg_ptr,
+               L->agg_mem, (const T *)res, LV::r(C), sc);
+  }
+  SPH_LAUNCHED(s);
+  sph_rt_status rc = vcycle<T>(s, 1, LV::r(C), LV::z(C), sc, fuse);
+  if (rc) return rc;
+  if (L->ap_ptr && LV::ap(L)) {
+    const RowShape sh = shape_for_mean(L->n ? (double)L->nnz_ap / (double)L->n : 0.0);
+    const int gp = row_grid_blocks(s->num_sms, L->n, sh.W, kFcgMinBlocks);
+    wf = timing_begin(s);
+    SPH_DISPATCH_SHAPE(sh.W, sh.U,
+                       (pdl_launch(s, fine_ap_cg_kernel<W, U, T, T>, gp, kBlock, 0, L->n,
+                                   L->ap_ptr, L->ap_col, LV::ap(L), L->agg, (const T *)LV::z(C),
+                                   (const T *)v.zpre, (const T *)res, (const T *)v.r, v.z, v.w,
+                                   (const T *)v.p, (const T *)v.q, first, s->sc, s->partials,
+                                   wf)));
+    SPH_LAUNCHED(s);
+    // A P entry: column + value; per row: ap_ptr, agg, P e_c, z_pre, res, r, z r/w, w,
+    // p, q
+    timing_end(s, (4.0 + sizeof(T)) * (double)L->nnz_ap + (12.0 + 10.0 * sizeof(T)) * (double)L->n,
+               kTimedPost);
+    return SPH_RT_OK;
+  }
+  T *t = LV::t(L);
+  pdl_launch(s, fcg_prolong_kernel<T>, gcap(s, L->n, kBlock), kBlock, 0, L->n,
+             (const int32_t *)L->agg, (const T *)LV::z(C), (const T *)v.zpre, t, sc);
+  SPH_LAUNCHED(s);
+  wf = timing_begin(s);
+  const int gd = row_grid_blocks(s->num_sms, L->n, A.W, kFcgMinBlocks);
+  SPH_DISPATCH_SHAPE(A.W, A.U,
+                     (pdl_launch(s, fcg_spmv_dot_kernel<W, U, T, T>, gd, kBlock, 0, A,
+                                 (const T *)t, (const T *)v.r, v.z, v.w, (const T *)v.p,
+                                 (const T *)v.q, first, s->sc, s->partials, wf)));
+  SPH_LAUNCHED(s);
+  timing_end(s, (4.0 + sizeof(T)) * (double)A.nnz + (8.0 + 9.0 * sizeof(T)) * (double)A.n,
+             kTimedSpmvPQ);
+  return SPH_RT_OK;
+}
+
+sph_rt_status fcg_cycle(sph_rt *s, const FcgVecs &v, int first) {
+  if (s->cfg.precision == SPH_RT_MIXED) return fcg_cycle_t<float>(s, v.f32, first);
+  return fcg_cycle_t<double>(s, v.f64, first);
 }
 
 // Launch-relevant layout of the hierarchy (sizes, shapes and every buffer the

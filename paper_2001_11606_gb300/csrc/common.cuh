@@ -71,6 +71,10 @@ struct Scalars {
   int krylov_per_outer[64];
   double last_change_e, last_change_E;
   double energy_before_e, energy_before_E;  // interior totals at the start of the step
+  // CG with the V-cycle's product (fine_post_smooth = 0)
+  int pfirst;      // the next update starts the directions: p = z, q = B z
+  int ru;          // mixed form: the next launch replaces r by the FP64 residual
+  double rmax2;    // mixed form: largest ||r / V||^2 since the last replacement
 };
 
 // --------------------------------------------------------------------------
@@ -455,6 +459,21 @@ struct DotFuse {
   double *partials;
 };
 
+// Vectors of the CG with the V-cycle's product (fine_post_smooth = 0), in the
+// hierarchy's precision T: residual r, preconditioned residual z, w = B z,
+// direction p and q = B p, the finest level's smoother start zpre, and the
+// finest level's 1 / diagonal in T.  The iterate x and b stay FP64.
+template <typename T>
+struct FcgSet {
+  T *r, *z, *w, *p, *q, *zpre;
+  const T *invdiag;
+};
+struct FcgVecs {
+  FcgSet<double> f64;
+  FcgSet<float> f32;
+  const ChebCoef *cf;  // the finest level's smoother coefficients (zpre = cf->inv_theta D^{-1} r)
+};
+
 // Chebyshev coefficient slots of a handle (device array): slot 0 belongs to
 // the fine-level Chebyshev preconditioner, slot 1 + l to AMG level l (its
 // smoother, or the coarse solve on the last level).
@@ -644,8 +663,8 @@ struct sph_rt {
   int ev_used = 0;
   int64_t spmv_launches = 0;
   double spmv_ms = 0.0, spmv_bytes = 0.0;
-  int64_t kind_launches[4] = {0, 0, 0, 0};  // per sphrt::TimedKind
-  double kind_ms[4] = {0, 0, 0, 0}, kind_bytes[4] = {0, 0, 0, 0};
+  int64_t kind_launches[5] = {0, 0, 0, 0, 0};  // per sphrt::TimedKind
+  double kind_ms[5] = {0, 0, 0, 0, 0}, kind_bytes[5] = {0, 0, 0, 0, 0};
 };
 
 // Helpers shared by the translation units (defined in sph_rt.cu).
@@ -664,8 +683,9 @@ void dfree(sph_rt *s, void *p);  // back to the free list (stream-ordered users 
 // the kernel writes 1 there if it does work and 0 if it returns at once because
 // the solve has converged; only launches that worked are counted.
 // kinds of timed fine-operator launches (SPH_RT_KERNEL_* in sph_rt.h)
-enum TimedKind { kTimedSpmvPQ = 0, kTimedResid = 1, kTimedCheb = 2, kTimedPost = 3 };
-constexpr int kTimedKinds = 4;
+enum TimedKind { kTimedSpmvPQ = 0, kTimedResid = 1, kTimedCheb = 2, kTimedPost = 3,
+                 kTimedTrueResid = 4 };
+constexpr int kTimedKinds = 5;
 int *timing_begin(sph_rt *s);
 void timing_end(sph_rt *s, double bytes, int kind);
 void timing_flush(sph_rt *s);

@@ -613,10 +613,188 @@ sph_rt_status autotune_fine_shape(sph_rt *s) {
   return SPH_RT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// CG with the V-cycle's product (config.fine_post_smooth = 0; the V-cycle and
+// the last sweep that yields z, B z and the CG scalars are in amg.cu,
+// fcg_cycle).  The iterate x and the right-hand side b are FP64; the other
+// vectors are in the hierarchy's precision T (FP64, or FP32 in the mixed form).
+// Per iteration: fcg_update_kernel (directions, x, r, ||r||, the smoother start
+// of the next V-cycle), [mixed: fcg_resid_kernel when a residual replacement
+// is due], then the V-cycle.
+//
+// Mixed form.  The FP32 operator and vectors make the recursive residual r
+// drift from the true one b - B x, by about the FP32 rounding of the residual
+// sizes since it was last exact.  So the FP64 residual replaces r (a reliable
+// update, Sleijpen & van der Vorst 1996) whenever ||r|| has dropped by the
+// factor reliable_drop since the last replacement, and before convergence is
+// accepted: the solve stops only on the FP64 residual, ||b - A x||_2 <= tol ||b||_2,
+// the same test as the FP64 form.  The search direction is kept.
+// ---------------------------------------------------------------------------
+bool fcg_active(const sph_rt *s);
+sph_rt_status fcg_vectors(sph_rt *s, FcgVecs *v);
+sph_rt_status fcg_cycle(sph_rt *s, const FcgVecs &v, int first);
+
+// r = b - B x in FP64 (stored in T), the smoother start zpre = c0 D^{-1} r,
+// ||r / V||^2 and the convergence test.  gated: a reliable update, run only
+// when the last update asked for one (sc->ru); else the start of a solve.
+template <int W, int U, typename T>
+__global__ void __launch_bounds__(kBlock, sweep_min_blocks(U))
+    fcg_resid_kernel(CsrView<double> A, const double *b, const double *x, T *r, T *zpre,
+                     const T *invdiag, const ChebCoef *cf, const double *invV, int gated,
+                     Scalars *sc, double *partials, int *wflag) {
+  pdl_wait();
+  if (gated && (sc->done || !sc->ru)) {
+    mark_work(wflag, 0);
+    return;
+  }
+  mark_work(wflag, 1);
+  const double c0 = cf->inv_theta;
+  const int own = tile_own_row<W>(threadIdx.x & 31);
+  int64_t r0, r1;
+  warp_rows<W>(A.n, r0, r1);
+  double acc = 0.0;
+  for (int64_t base = r0; base < r1; base += 32) {
+    const int rows = (int)(r1 - base < 32 ? r1 - base : 32);
+    const int64_t i = base + own;
+    const double s = tile_row_sums<W, U, double, double>(base, rows, A.ptr, A.col, A.val, x);
+    if (own < rows) {
+      const double ri = b[i] - fmadd(A.diag[i], x[i], s);
+      const T rt = (T)ri;
+      r[i] = rt;
+      zpre[i] = (T)(c0 * (double)invdiag[i] * (double)rt);
+      const double ru = ri * invV[i];
+      acc += ru * ru;
+    }
+  }
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  double part[1] = {acc}, out[1];
+  const bool mx[1] = {false};
+  if (last_block_combine<1>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    sc->rnorm2 = out[0];
+    sc->rmax2 = out[0];
+    sc->ru = 0;
+    if (!gated) sc->iters = 0;
+    sc->done = !(out[0] > sc->thresh2);  // also stops on NaN
+    if (!(out[0] == out[0])) sc->breakdown = 1;
+  }
+}
+
+// p = z + beta p, q = B z + beta q (p = z, q = B z when starting), x += alpha p,
+// r -= alpha q, ||r / V||^2, the next smoother start zpre = c0 D^{-1} r, and the
+// convergence test (FP64 form) or the reliable-update request (mixed form:
+// drop2 = reliable_drop^2 > 0).
+template <typename T>
+__global__ void fcg_update_kernel(int64_t n, double *x, T *r, T *p, T *q, const T *z, const T *w,
+                                  T *zpre, const T *invdiag, const ChebCoef *cf,
+                                  const double *invV, int maxit, double drop2, Scalars *sc,
+                                  double *partials) {
+  pdl_wait();
+  if (sc->done) return;
+  const double alpha = sc->alpha;
+  const T beta = (T)sc->beta, ta = (T)alpha;
+  const bool first = sc->pfirst != 0;
+  const double c0 = cf->inv_theta;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T zi = z[i], wi = w[i];
+    const T pi = first ? zi : fmadd(beta, p[i], zi);
+    const T qi = first ? wi : fmadd(beta, q[i], wi);
+    p[i] = pi;
+    q[i] = qi;
+    x[i] += alpha * (double)pi;
+    const T ri = r[i] - ta * qi;
+    r[i] = ri;
+    zpre[i] = (T)(c0 * (double)invdiag[i] * (double)ri);
+    const double ru = (double)ri * invV[i];
+    acc += ru * ru;
+  }
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  double part[1] = {acc}, out[1];
+  const bool mx[1] = {false};
+  if (last_block_combine<1>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    const double rn = out[0];
+    sc->rnorm2 = rn;
+    sc->iters += 1;
+    sc->pfirst = 0;
+    if (!(rn == rn)) {
+      sc->breakdown = 1;
+      sc->done = 1;
+    } else if (drop2 <= 0.0) {  // FP64: the recursive residual is the residual
+      if (!(rn > sc->thresh2) || sc->iters >= maxit) sc->done = 1;
+    } else {
+      if (rn > sc->rmax2) sc->rmax2 = rn;
+      if (!(rn > sc->thresh2) || rn < drop2 * sc->rmax2) sc->ru = 1;
+      if (sc->iters >= maxit) {
+        // stop unverified: report at least the threshold so the solve is not
+        // taken as converged
+        sc->done = 1;
+        if (!(sc->rnorm2 > sc->thresh2)) sc->rnorm2 = 4.0 * sc->thresh2 + 1e-300;
+      }
+    }
+  }
+}
+
+static sph_rt_status fcg_resid_launch(sph_rt *s, const FcgVecs &v, int gated) {
+  CsrView<double> A = fine_view(s);
+  const int gw = row_grid(s->num_sms, A.n, A.W, A.U);
+  int *wf = timing_begin(s);
+  if (s->cfg.precision == SPH_RT_MIXED)
+    SPH_DISPATCH_SHAPE(A.W, A.U,
+                       (pdl_launch(s, fcg_resid_kernel<W, U, float>, gw, kBlock, 0, A, s->b,
+                                   s->x, v.f32.r, v.f32.zpre, v.f32.invdiag, v.cf, s->invV, gated,
+                                   s->sc, s->partials, wf)));
+  else
+    SPH_DISPATCH_SHAPE(A.W, A.U,
+                       (pdl_launch(s, fcg_resid_kernel<W, U, double>, gw, kBlock, 0, A, s->b,
+                                   s->x, v.f64.r, v.f64.zpre, v.f64.invdiag, v.cf, s->invV, gated,
+                                   s->sc, s->partials, wf)));
+  SPH_LAUNCHED(s);
+  // rowptr, diag, b, x, 1/V, r, zpre, 1/diag
+  const double tb = s->cfg.precision == SPH_RT_MIXED ? 4.0 : 8.0;
+  timing_end(s, spmv_class_bytes(A, 40 + (int)(3 * tb)), kTimedTrueResid);
+  return SPH_RT_OK;
+}
+
+static sph_rt_status fcg_prologue(sph_rt *s) {
+  FcgVecs v;
+  sph_rt_status rc;
+  if ((rc = fcg_vectors(s, &v))) return rc;
+  if ((rc = fcg_resid_launch(s, v, 0))) return rc;
+  return fcg_cycle(s, v, 1);
+}
+
+static sph_rt_status fcg_iteration(sph_rt *s) {
+  FcgVecs v;
+  sph_rt_status rc;
+  if ((rc = fcg_vectors(s, &v))) return rc;
+  const int64_t n = s->n_int;
+  const int g = grid_cap(s, n, kBlock);
+  if (s->cfg.precision == SPH_RT_MIXED) {
+    const double drop2 = s->cfg.reliable_drop * s->cfg.reliable_drop;
+    const FcgSet<float> &f = v.f32;
+    pdl_launch(s, fcg_update_kernel<float>, g, kBlock, 0, n, s->x, f.r, f.p, f.q,
+               (const float *)f.z, (const float *)f.w, f.zpre, f.invdiag, v.cf,
+               (const double *)s->invV, s->cfg.max_krylov, drop2, s->sc, s->partials);
+    SPH_LAUNCHED(s);
+    if ((rc = fcg_resid_launch(s, v, 1))) return rc;
+  } else {
+    const FcgSet<double> &f = v.f64;
+    pdl_launch(s, fcg_update_kernel<double>, g, kBlock, 0, n, s->x, f.r, f.p, f.q,
+               (const double *)f.z, (const double *)f.w, f.zpre, f.invdiag, v.cf,
+               (const double *)s->invV, s->cfg.max_krylov, 0.0, s->sc, s->partials);
+    SPH_LAUNCHED(s);
+  }
+  return fcg_cycle(s, v, 0);
+}
+
 // Solve B x = b from the warm start in x (row a6).  On return the host mirror
 // s->sc_host holds the final scalars.
 // First part of a solve: r = b - B x, z = M^{-1} r, q = B p with p = z.
 sph_rt_status pcg_prologue(sph_rt *s) {
+  if (fcg_active(s)) return fcg_prologue(s);
   CsrView<double> A = fine_view(s);
   const int gw = row_grid(s->num_sms, A.n, A.W, A.U);
   sph_rt_status rc;
@@ -650,6 +828,7 @@ __global__ void copy_vec_kernel(int64_t n, const double *src, double *dst, const
 // previous z in z_old (with the AMG preconditioner: in z itself until the fused
 // inner product widens the new one).  All launches are empty once `done` is set.
 sph_rt_status pcg_iteration(sph_rt *s) {
+  if (fcg_active(s)) return fcg_iteration(s);
   CsrView<double> A = fine_view(s);
   const int gw = row_grid(s->num_sms, A.n, A.W, A.U);
   const int g = grid_cap(s, A.n, kBlock);

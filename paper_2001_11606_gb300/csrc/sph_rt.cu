@@ -179,6 +179,8 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->coarse_fp32 = 1;
   c->graphs = 1;
   c->pdl = 1;
+  c->fine_post_smooth = 1;
+  c->reliable_drop = 1e-2;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -211,6 +213,12 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
   if (c->amg_tail < 0 || c->amg_tail > 1) return why = "amg_tail must be 0 or 1", SPH_RT_EINVAL;
   if (c->coarse_fp32 < 0 || c->coarse_fp32 > 1)
     return why = "coarse_fp32 must be 0 or 1", SPH_RT_EINVAL;
+  if (c->fine_post_smooth < 0 || c->fine_post_smooth > 1)
+    return why = "fine_post_smooth must be 0 or 1", SPH_RT_EINVAL;
+  if (c->fine_post_smooth == 0 && c->cheb_degree != 1)
+    return why = "fine_post_smooth = 0 needs cheb_degree = 1", SPH_RT_EINVAL;
+  if (!(c->reliable_drop > 0.0 && c->reliable_drop < 1.0))
+    return why = "reliable_drop must be in (0, 1)", SPH_RT_EINVAL;
   if (c->device < 0) return why = "device must be >= 0", SPH_RT_EINVAL;
   return SPH_RT_OK;
 }

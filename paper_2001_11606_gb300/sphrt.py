@@ -50,6 +50,8 @@ class Config(C.Structure):
         ("coarse_fp32", C.c_int32),
         ("graphs", C.c_int32),
         ("pdl", C.c_int32),
+        ("fine_post_smooth", C.c_int32),
+        ("reliable_drop", C.c_double),
         ("device", C.c_int32),
         ("stream", C.c_void_p),
     ]
@@ -352,7 +354,8 @@ class Solver:
     def kernel_stats_by_kind(self):
         """{name: (launches, ms, bytes)} of the timed fine-operator kernels."""
         out = {}
-        for kind, name in ((0, "spmv_pq"), (1, "resid"), (2, "cheb_step"), (3, "post_ap")):
+        for kind, name in ((0, "spmv_pq"), (1, "resid"), (2, "cheb_step"), (3, "post_ap"),
+                           (4, "true_resid")):
             n, ms, by = C.c_int64(), C.c_double(), C.c_double()
             self._check(self._L.sph_rt_kernel_stats_kind(self._h, kind, C.byref(n), C.byref(ms),
                                                          C.byref(by)))

@@ -52,13 +52,21 @@ def test_config_struct_matches_defaults():
                                          ("tol_krylov", -1.0), ("max_outer", 0),
                                          ("precond", 9), ("cheb_degree", 0),
                                          ("amg_theta", 1.5), ("graphs", 2), ("pdl", 2),
-                                         ("amg_tail", -1), ("coarse_fp32", 2)])
+                                         ("amg_tail", -1), ("coarse_fp32", 2),
+                                         ("fine_post_smooth", 2), ("reliable_drop", 0.0),
+                                         ("reliable_drop", 1.0)])
 def test_create_rejects_bad_config(field, value):
     cfg = sphrt.default_config(**{field: value})
     with pytest.raises(sphrt.SphRtError) as ei:
         sphrt.Solver(cfg)
     assert ei.value.status == sphrt.EINVAL
     assert str(ei.value)
+
+
+def test_vcycle_product_cg_needs_degree_one():
+    with pytest.raises(sphrt.SphRtError) as ei:
+        sphrt.Solver(sphrt.default_config(fine_post_smooth=0, cheb_degree=2))
+    assert ei.value.status == sphrt.EINVAL and "cheb_degree" in str(ei.value)
 
 
 def _particles():

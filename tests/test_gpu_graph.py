@@ -24,14 +24,17 @@ def _run(w, steps, **cfg):
     return e, E, stats, info, launches
 
 
-@pytest.mark.parametrize("precond,precision", [(sphrt.PRECOND_AMG, sphrt.FP64),
-                                               (sphrt.PRECOND_AMG, sphrt.MIXED),
-                                               (sphrt.PRECOND_CHEBYSHEV, sphrt.FP64),
-                                               (sphrt.PRECOND_JACOBI, sphrt.FP64)])
-def test_graph_loop_matches_host_loop_bitwise(precond, precision):
-    w = I.mms_3d_lp(n=12, steps=3)
-    g = _run(w, 3, precond=precond, precision=precision, graphs=1)
-    h = _run(w, 3, precond=precond, precision=precision, graphs=0)
+@pytest.mark.parametrize("precond,precision,post,n", [
+    (sphrt.PRECOND_AMG, sphrt.FP64, 1, 12), (sphrt.PRECOND_AMG, sphrt.MIXED, 1, 12),
+    (sphrt.PRECOND_CHEBYSHEV, sphrt.FP64, 1, 12), (sphrt.PRECOND_JACOBI, sphrt.FP64, 1, 12),
+    # the CG whose product comes from the V-cycle, without and with A P (32^3)
+    (sphrt.PRECOND_AMG, sphrt.FP64, 0, 12), (sphrt.PRECOND_AMG, sphrt.MIXED, 0, 12),
+    (sphrt.PRECOND_AMG, sphrt.MIXED, 0, 32)])
+def test_graph_loop_matches_host_loop_bitwise(precond, precision, post, n):
+    w = I.mms_3d_lp(n=n, steps=3)
+    kw = dict(precond=precond, precision=precision, fine_post_smooth=post)
+    g = _run(w, 3, graphs=1, **kw)
+    h = _run(w, 3, graphs=0, **kw)
     assert np.array_equal(g[0], h[0]) and np.array_equal(g[1], h[1])
     assert g[2] == h[2]
     assert g[3] == (1, 3)  # captured once, launched every step
@@ -86,12 +89,13 @@ def test_cluster_tail_vcycle_bitwise_and_fewer_launches(precision):
     assert on[4] < off[4]  # the tail replaces several launches per V-cycle
 
 
-@pytest.mark.parametrize("precision", [sphrt.FP64, sphrt.MIXED])
-def test_dependent_launch_changes_no_bit(precision):
+@pytest.mark.parametrize("precision,post", [(sphrt.FP64, 1), (sphrt.MIXED, 1), (sphrt.FP64, 0),
+                                            (sphrt.MIXED, 0)])
+def test_dependent_launch_changes_no_bit(precision, post):
     # programmatic dependent launch only lets a kernel's launch overlap its
     # predecessor's drain; every kernel waits for its predecessor's results
     w = I.mms_3d_lp(n=12, steps=3)
-    on = _run(w, 3, precision=precision, pdl=1)
-    off = _run(w, 3, precision=precision, pdl=0)
+    on = _run(w, 3, precision=precision, pdl=1, fine_post_smooth=post)
+    off = _run(w, 3, precision=precision, pdl=0, fine_post_smooth=post)
     assert np.array_equal(on[0], off[0]) and np.array_equal(on[1], off[1])
     assert on[2] == off[2]

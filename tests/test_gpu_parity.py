@@ -269,6 +269,42 @@ def test_parity_where_the_fine_level_takes_its_full_size_path(make, precision, t
     assert r["err_e"] < tol and r["err_E"] < tol, (r["err_e"], r["err_E"])
 
 
+@pytest.mark.parametrize("make,precision,tol", [
+    (lambda: I.mms_2d(), sphrt.FP64, 1e-10),
+    (lambda: I.mms_3d_lp(n=16, steps=3), sphrt.FP64, 1e-10),
+    (lambda: I.mms_3d_lp(n=16, steps=3), sphrt.MIXED, 1e-8),
+    (lambda: I.mms_3d(n=32, steps=3), sphrt.FP64, 1e-10),
+    (lambda: I.mms_3d(n=32, steps=3), sphrt.MIXED, 1e-8),
+    (lambda: I.mms_3d_lp(n=32, steps=3), sphrt.MIXED, 1e-8),
+    (lambda: I.heating_wave(3, 4000, 10.0, seed=21, steps=3), sphrt.MIXED, 1e-8)])
+def test_vcycle_product_cg_parity(make, precision, tol):
+    # fine_post_smooth = 0: the finest level only pre-smooths and the CG takes
+    # B p from the V-cycle's sweeps (flexible CG; in the mixed form FP32 vectors
+    # with FP64 residual replacement).  16^3 takes the form without A P, 32^3
+    # the A P sweep.  Same fixed point, same tolerances as the other forms.
+    w = make()
+    r = run_both(w, w.steps, gpu_over=dict(precision=precision, precond=sphrt.PRECOND_AMG,
+                                           fine_post_smooth=0), orc_over=TIGHT)
+    assert r["err_e"] < tol and r["err_E"] < tol, (r["err_e"], r["err_E"])
+    for g, o in zip(r["gstats"], r["ostats"]):
+        assert g.outer_iters == o.outer_iters
+
+
+@pytest.mark.parametrize("drop", [0.5, 1e-2, 1e-4])
+def test_vcycle_product_cg_stops_on_the_fp64_residual(drop):
+    # whatever the replacement interval, the mixed solve stops only when the FP64
+    # residual meets the tolerance: the energies agree with the FP64 form's
+    w = I.mms_3d(n=32, steps=2)
+    ref = run_both(w, 2, gpu_over=dict(precond=sphrt.PRECOND_AMG), orc_over=TIGHT)
+    S = sphrt.solver_for(w, **dict(w.params, **TIGHT), precision=sphrt.MIXED,
+                         fine_post_smooth=0, reliable_drop=drop)
+    for n in (1, 2):
+        S.step(w.dt, *w.step_inputs(n))
+    eg, Eg, _ = S.get_energies()
+    m = w.particles.kind == 0
+    assert rel_err(eg, ref["e"], m) < 1e-8 and rel_err(Eg, ref["E"], m) < 1e-8
+
+
 def test_mixed_precision_parity():
     w = I.mms_3d_lp(n=16, steps=3)
     r = run_both(w, 3, gpu_over=dict(precision=sphrt.MIXED, precond=sphrt.PRECOND_AMG),
