@@ -67,7 +67,8 @@ enum { SPH_RT_FP64 = 0, SPH_RT_MIXED = 1 };
  */
 typedef struct {
   int32_t dim;          /* 2 or 3 (1 is accepted too) */
-  double a, c, cv;      /* radiation constant, speed of light, specific heat */
+  double a, c, cv;      /* radiation constant (>= 0; 0: no emission), speed of light, specific
+                           heat (both > 0) */
   int32_t limiter;      /* SPH_RT_LIMITER_* */
   double larsen_k;      /* k of the Larsen limiter (> 0) */
   double opacity_exp;   /* p in sigma = sigma0 T^p */
@@ -115,6 +116,18 @@ typedef struct {
                            dropped by this factor since the last replacement, and before
                            convergence is accepted (the solve stops on the FP64 residual).
                            In (0, 1) */
+  /* Time step choice (Sec. 3.3, Eq. energy-fractional).  With dt_target > 0 every
+   * converged step reports in its stats the fractional changes
+   *   eta_x = max_i |x_i^n - x_i^{n-1}| / (x_i^n + dt_target xbar^n + dt_eta_floor)
+   * of x = e and x = E over the interior particles (xbar^n: volume average,
+   * sum x_i V_i / sum V_i) and the proposed next step
+   *   dt_next = min(dt (dt_target / eta_e)^(1/2), dt (dt_target / eta_E)^(1/2),
+   *                 dt_growth dt, dt_max), at least dt_min.
+   * The caller passes dt_next (or any other dt) to the next sph_rt_step. */
+  double dt_target;     /* target fractional change (the paper uses 0.05); 0 = off */
+  double dt_growth;     /* largest factor between consecutive steps (>= 1) */
+  double dt_min, dt_max;
+  double dt_eta_floor;  /* added to the denominator for states that may be zero everywhere */
   int32_t device;       /* CUDA device ordinal */
   void *stream;         /* cudaStream_t to run on (borrowed); NULL = library-owned stream */
 } sph_rt_config;
@@ -132,6 +145,8 @@ typedef struct {
   double boundary_energy;             /* dt sum_i V_i sum_{j ghost} w_ij (E_j - E_i) */
   double last_change_e, last_change_E;/* final outer-loop changes */
   double t_setup_ms, t_assembly_ms, t_amg_ms, t_krylov_ms, t_newton_ms;
+  double eta_e, eta_E;                /* fractional changes of the step (config.dt_target > 0) */
+  double dt_next;                     /* proposed next step (config.dt_target > 0), else 0 */
 } sph_rt_stats;
 
 /* Fill *cfg with defaults: dim 3, a = c = c_v = 1, no limiter, p = 0,

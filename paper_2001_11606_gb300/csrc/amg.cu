@@ -251,22 +251,67 @@ __global__ void bucket_scatter_kernel(int64_t n, const int32_t *bucket, const in
     out[at] = (int32_t)i;
   }
 }
+// Buckets of up to kSmallBucket items are insertion-sorted by one thread
+// (bucket_sort_kernel); larger ones, where a quadratic sort in one thread
+// would dominate the set-up, by a warp (bucket_rank_kernel).
+constexpr int kSmallBucket = 32;
+constexpr int kRankBucket = 1024;  // largest bucket the warp sort stages in shared memory
+__device__ __forceinline__ void insertion_sort(int32_t *a, int64_t c) {
+  for (int64_t t = 1; t < c; ++t) {
+    int32_t v = a[t];
+    int64_t u = t - 1;
+    while (u >= 0 && a[u] > v) {
+      a[u + 1] = a[u];
+      --u;
+    }
+    a[u + 1] = v;
+  }
+}
 __global__ void bucket_sort_kernel(int64_t nb, const int64_t *start, int32_t *out) {
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
        b += (int64_t)gridDim.x * blockDim.x) {
-    int32_t *a = out + start[b];
-    int64_t c = start[b + 1] - start[b];
-    for (int64_t t = 1; t < c; ++t) {
-      int32_t v = a[t];
-      int64_t u = t - 1;
-      while (u >= 0 && a[u] > v) {
-        a[u + 1] = a[u];
-        --u;
+    const int64_t c = start[b + 1] - start[b];
+    if (c <= kSmallBucket) insertion_sort(out + start[b], c);
+  }
+}
+// A warp takes 32 consecutive buckets and sorts each larger one in turn: the
+// items (distinct indices) are staged in shared memory and each is written at
+// its rank, the number of smaller items.  Buckets beyond kRankBucket items
+// (not met by the aggregation levels, whose sources per target are a few
+// hundred at most) fall back to one thread.
+__global__ void bucket_rank_kernel(int64_t nb, const int64_t *start, int32_t *out) {
+  __shared__ int32_t stage[kWarpsPerBlock][kRankBucket];
+  int32_t *sm = stage[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b0 = warp * 32; b0 < nb; b0 += nwarps * 32) {
+    const int64_t b = b0 + lane;
+    const int64_t c = b < nb ? start[b + 1] - start[b] : 0;
+    unsigned m = __ballot_sync(0xffffffffu, c > kSmallBucket);
+    while (m) {
+      const int t = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t bb = b0 + t;
+      const int64_t s0 = start[bb], cc = start[bb + 1] - s0;
+      if (cc > kRankBucket) {
+        if (lane == 0) insertion_sort(out + s0, cc);
+        __syncwarp();
+        continue;
       }
-      a[u + 1] = v;
+      for (int64_t k = lane; k < cc; k += 32) sm[k] = out[s0 + k];
+      __syncwarp();
+      for (int64_t k = lane; k < cc; k += 32) {
+        const int32_t v = sm[k];
+        int rank = 0;
+        for (int q = 0; q < (int)cc; ++q) rank += sm[q] < v;
+        out[s0 + rank] = v;
+      }
+      __syncwarp();
     }
   }
 }
+
 __global__ void u32_to_i64_kernel(int64_t n, const unsigned *in, int64_t *out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -396,15 +441,17 @@ __global__ void target_count_kernel(int64_t nsrc, const int32_t *tgt, unsigned *
 // A P targets have 3-4 sources): the additions a lane skips would add +0.0,
 // and a sum that starts at +0.0 is unchanged by them, so the result is that of
 // adding all 8 slots.
+// T: the hierarchy's value type (FP32 in the mixed form: its sums are formed
+// from the FP32 fine values directly).
+template <typename T>
 __global__ void galerkin_kernel(int64_t nnz_c, int64_t nc, const int64_t *seg_ptr,
-                                const int32_t *seg_src, int64_t nnz_f, const double *val_f,
-                                const double *diag_f, double *val_c, double *diag_c,
-                                double *invdiag_c) {
+                                const int32_t *seg_src, int64_t nnz_f, const T *val_f,
+                                const T *diag_f, T *val_c, T *diag_c, T *invdiag_c) {
   constexpr int G = 8;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz_c + nc;
        t += (int64_t)gridDim.x * blockDim.x) {
     const unsigned mask = __activemask();
-    double acc = 0.0;
+    T acc = T(0);
     const int64_t u1 = seg_ptr[t + 1];
     for (int64_t u = seg_ptr[t];; u += G) {
       const int64_t left = u1 - u;
@@ -413,10 +460,10 @@ __global__ void galerkin_kernel(int64_t nnz_c, int64_t nc, const int64_t *seg_pt
       int32_t src[G];
 #pragma unroll
       for (int g = 0; g < G; ++g) src[g] = u + g < u1 ? __ldg(seg_src + u + g) : -1;
-      double v[G];
+      T v[G];
 #pragma unroll
       for (int g = 0; g < G; ++g)
-        v[g] = src[g] < 0 ? 0.0 : (src[g] < nnz_f ? __ldg(val_f + src[g]) : __ldg(diag_f + (src[g] - nnz_f)));
+        v[g] = src[g] < 0 ? T(0) : (src[g] < nnz_f ? __ldg(val_f + src[g]) : __ldg(diag_f + (src[g] - nnz_f)));
 #pragma unroll 1
       for (int g = 0; g < m; ++g) {
         acc += v[0];  // sources in order; a shorter segment's padding adds +0.0
@@ -428,20 +475,21 @@ __global__ void galerkin_kernel(int64_t nnz_c, int64_t nc, const int64_t *seg_pt
       val_c[t] = acc;
     } else {
       diag_c[t - nnz_c] = acc;
-      invdiag_c[t - nnz_c] = 1.0 / acc;
+      invdiag_c[t - nnz_c] = T(1) / acc;
     }
   }
 }
 
 // Gershgorin bound of D^{-1} A for a level: max_i sum_j |A_ij| / A_ii
-__global__ void gersh_kernel(int64_t n, const int64_t *ptr, const double *val, const double *diag,
+template <typename T>
+__global__ void gersh_kernel(int64_t n, const int64_t *ptr, const T *val, const T *diag,
                              double *partials, unsigned *counter, double *out) {
   double g = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double sacc = 0.0;
-    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) sacc += fabs(val[k]);
-    g = fmax(g, sacc / diag[i]);
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) sacc += fabs((double)val[k]);
+    g = fmax(g, sacc / (double)diag[i]);
   }
   __shared__ double sh[32];
   g = block_max(g, sh);
@@ -1203,6 +1251,9 @@ static sph_rt_status bucket_sort(sph_rt *s, SphLevel *owner, int64_t nitems,
   SPH_LAUNCHED(s);
   bucket_sort_kernel<<<gcap(s, nb, kBlock), kBlock, 0, s->stream>>>(nb, start, out);
   SPH_LAUNCHED(s);
+  bucket_rank_kernel<<<gcap(s, ceil_div(nb, 32), kWarpsPerBlock), kBlock, 0, s->stream>>>(
+      nb, start, out);
+  SPH_LAUNCHED(s);
   SPH_CUDA(s, cudaStreamSynchronize(s->stream));
   dfree(s, cnt);
   dfree(s, cur);
@@ -1430,7 +1481,7 @@ static sph_rt_status build_structure(sph_rt *s) {
     if (!C) break;
     s->levels.push_back(C);
     // numeric Galerkin product for C so that the next strength test can run
-    galerkin_kernel<<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
+    galerkin_kernel<double><<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
         C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, L->val, L->diag, C->val, C->diag,
         C->invdiag);
     SPH_LAUNCHED(s);
@@ -1455,118 +1506,6 @@ static int coarse_degree(const sph_rt *s, const SphLevel *L) {
   return L->n <= kCoarseTarget * 4 ? 6 : 3 * s->cfg.cheb_degree;
 }
 
-bool fcg_active(const sph_rt *s);
-sph_rt_status fcg_vectors(sph_rt *s, FcgVecs *v);
-
-static sph_rt_status numeric(sph_rt *s) {
-  for (size_t l = 0; l + 1 < s->levels.size(); ++l) {
-    SphLevel *L = s->levels[l], *C = s->levels[l + 1];
-    if (L->ap_ptr) {  // A P of this level (its values are final: level l is done)
-      galerkin_kernel<<<gcap(s, L->nnz_ap, kBlock), kBlock, 0, s->stream>>>(
-          L->nnz_ap, 0, L->ap_seg_ptr, L->ap_seg_src, L->nnz, L->val, L->diag, L->ap_val,
-          nullptr, nullptr);
-      SPH_LAUNCHED(s);
-      if (L->ap_val32) {
-        convert_kernel<double, float><<<gcap(s, L->nnz_ap, kBlock), kBlock, 0, s->stream>>>(
-            L->nnz_ap, L->ap_val, L->ap_val32);
-        SPH_LAUNCHED(s);
-      }
-    }
-    if (L->apg_ptr) {  // P^T (A P)
-      galerkin_kernel<<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
-          C->nnz, C->n, L->apg_ptr, L->apg_src, L->nnz_ap, L->ap_val, nullptr, C->val, C->diag,
-          C->invdiag);
-    } else {
-      galerkin_kernel<<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
-          C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, L->val, L->diag, C->val, C->diag,
-          C->invdiag);
-    }
-    SPH_LAUNCHED(s);
-  }
-  // Gershgorin bounds of every level, turned into Chebyshev coefficients on
-  // the device (slot 1 + l): no host read
-  if (!s->amg_gersh) s->amg_gersh = dalloc<double>(s, kMaxLevels);
-  double *dg = s->amg_gersh;
-  if (!dg) return SPH_RT_ENOMEM;
-  for (size_t l = 0; l < s->levels.size(); ++l) {
-    SphLevel *L = s->levels[l];
-    if (l == 0) {
-      // the finest level's bound was reduced by the assembly of this step
-      SPH_CUDA(s, cudaMemcpyAsync(dg, s->gersh, sizeof(double), cudaMemcpyDeviceToDevice,
-                                  s->stream));
-      continue;
-    }
-    gersh_kernel<<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(L->n, L->ptr, L->val, L->diag,
-                                                                  s->partials, &s->sc->counter,
-                                                                  dg + l);
-    SPH_LAUNCHED(s);
-  }
-  std::vector<int> mode(s->levels.size()), degree(s->levels.size());
-  for (size_t l = 0; l < s->levels.size(); ++l) {
-    const bool coarsest = l + 1 == s->levels.size();
-    mode[l] = coarsest ? 2 : 1;
-    degree[l] = coarsest ? coarse_degree(s, s->levels[l]) : s->cfg.cheb_degree;
-  }
-  sph_rt_status rc = launch_cheb_slots(s, 1, dg, mode, degree);
-  if (rc) return rc;
-  if (s->cfg.precision == SPH_RT_MIXED) {
-    for (SphLevel *L : s->levels) {
-      if (!L->val32) {
-        L->val32 = lalloc<float>(s, L, L->nnz);
-        L->diag32 = lalloc<float>(s, L, L->n);
-        L->invdiag32 = lalloc<float>(s, L, L->n);
-        L->r32 = lalloc<float>(s, L, L->n);
-        L->z32 = lalloc<float>(s, L, L->n);
-        L->res32 = lalloc<float>(s, L, L->n);
-        L->d32 = lalloc<float>(s, L, L->n);
-        L->t32 = lalloc<float>(s, L, L->n);
-        if (!L->val32 || !L->diag32 || !L->invdiag32 || !L->r32 || !L->z32 || !L->res32 ||
-            !L->d32 || !L->t32)
-          return SPH_RT_ENOMEM;
-      }
-      convert_kernel<double, float><<<gcap(s, L->nnz, kBlock), kBlock, 0, s->stream>>>(
-          L->nnz, L->val, L->val32);
-      SPH_LAUNCHED(s);
-      convert_kernel<double, float><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(
-          L->n, L->diag, L->diag32);
-      SPH_LAUNCHED(s);
-      convert_kernel<double, float><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(
-          L->n, L->invdiag, L->invdiag32);
-      SPH_LAUNCHED(s);
-    }
-    // FP32 CG vectors of the V-cycle-product CG, allocated here (not while a
-    // loop graph is being captured)
-    if (fcg_active(s)) {
-      FcgVecs v;
-      if ((rc = fcg_vectors(s, &v))) return rc;
-    }
-  }
-  return SPH_RT_OK;
-}
-
-template <typename T>
-static void tail_setup(sph_rt *s);
-
-sph_rt_status amg_setup(sph_rt *s) {
-  sph_rt_status rc;
-  if (!s->amg_ready || s->cfg.amg_rebuild) {
-    if ((rc = build_structure(s))) return rc;
-    if (s->cfg.precision == SPH_RT_MIXED)
-      tail_setup<float>(s);
-    else
-      tail_setup<double>(s);
-    // A P of the levels larger than the tail threshold: the smaller ones
-    // post-smooth the same way with or without the cluster tail, so both give
-    // bitwise the same V-cycle
-    for (size_t l = 0; l + 1 < s->levels.size() && s->levels[l]->nnz > kTailMaxNnz; ++l)
-      if ((rc = build_ap(s, l))) return rc;
-  }
-  return numeric(s);
-}
-
-// ---------------------------------------------------------------------------
-// V-cycle
-// ---------------------------------------------------------------------------
 template <typename T>
 struct LevelVecs;
 template <>
@@ -1615,6 +1554,132 @@ struct LevelVecs<float> {
 };
 
 
+// FP32 storage of every level of the mixed form (level 0 borrows the FP32
+// copy the assembly writes).
+static sph_rt_status level_fp32(sph_rt *s, size_t l) {
+  SphLevel *L = s->levels[l];
+  if (L->r32) return SPH_RT_OK;
+  if (l == 0) {
+    L->val32 = s->mat_val32;
+    L->diag32 = s->diag32;
+    L->invdiag32 = s->invdiag32;
+  } else {
+    L->val32 = lalloc<float>(s, L, L->nnz);
+    L->diag32 = lalloc<float>(s, L, L->n);
+    L->invdiag32 = lalloc<float>(s, L, L->n);
+  }
+  L->r32 = lalloc<float>(s, L, L->n);
+  L->z32 = lalloc<float>(s, L, L->n);
+  L->res32 = lalloc<float>(s, L, L->n);
+  L->d32 = lalloc<float>(s, L, L->n);
+  L->t32 = lalloc<float>(s, L, L->n);
+  if (!L->val32 || !L->diag32 || !L->invdiag32 || !L->r32 || !L->z32 || !L->res32 || !L->d32 ||
+      !L->t32)
+    return SPH_RT_ENOMEM;
+  return SPH_RT_OK;
+}
+
+// Galerkin values of every level from the current fine operator, in the
+// hierarchy's type T: FP64, or FP32 in the mixed form, where the sums are
+// formed from the FP32 fine copy directly.
+template <typename T>
+static sph_rt_status galerkin_levels(sph_rt *s) {
+  using LV = LevelVecs<T>;
+  for (size_t l = 0; l + 1 < s->levels.size(); ++l) {
+    SphLevel *L = s->levels[l], *C = s->levels[l + 1];
+    const CsrView<T> Lv = LV::view(L), Cv = LV::view(C);
+    if (L->ap_ptr) {  // A P of this level (its values are final: level l is done)
+      galerkin_kernel<T><<<gcap(s, L->nnz_ap, kBlock), kBlock, 0, s->stream>>>(
+          L->nnz_ap, 0, L->ap_seg_ptr, L->ap_seg_src, L->nnz, Lv.val, Lv.diag,
+          const_cast<T *>(LV::ap(L)), nullptr, nullptr);
+      SPH_LAUNCHED(s);
+    }
+    T *cval = const_cast<T *>(Cv.val), *cdiag = const_cast<T *>(Cv.diag),
+      *cinv = const_cast<T *>(Cv.invdiag);
+    if (L->apg_ptr)  // P^T (A P)
+      galerkin_kernel<T><<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
+          C->nnz, C->n, L->apg_ptr, L->apg_src, L->nnz_ap, LV::ap(L), nullptr, cval, cdiag, cinv);
+    else
+      galerkin_kernel<T><<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
+          C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, Lv.val, Lv.diag, cval, cdiag, cinv);
+    SPH_LAUNCHED(s);
+  }
+  // Gershgorin bounds of every level, turned into Chebyshev coefficients on
+  // the device (slot 1 + l): no host read
+  if (!s->amg_gersh) s->amg_gersh = dalloc<double>(s, kMaxLevels);
+  double *dg = s->amg_gersh;
+  if (!dg) return SPH_RT_ENOMEM;
+  for (size_t l = 0; l < s->levels.size(); ++l) {
+    SphLevel *L = s->levels[l];
+    if (l == 0) {
+      // the finest level's bound was reduced by the assembly of this step
+      SPH_CUDA(s, cudaMemcpyAsync(dg, s->gersh, sizeof(double), cudaMemcpyDeviceToDevice,
+                                  s->stream));
+      continue;
+    }
+    const CsrView<T> Lv = LV::view(L);
+    gersh_kernel<T><<<gcap(s, L->n, kBlock), kBlock, 0, s->stream>>>(
+        L->n, L->ptr, Lv.val, Lv.diag, s->partials, &s->sc->counter, dg + l);
+    SPH_LAUNCHED(s);
+  }
+  return SPH_RT_OK;
+}
+
+bool fcg_active(const sph_rt *s);
+sph_rt_status fcg_vectors(sph_rt *s, FcgVecs *v);
+
+static sph_rt_status numeric(sph_rt *s) {
+  sph_rt_status rc;
+  const bool mixed = s->cfg.precision == SPH_RT_MIXED;
+  if (mixed) {
+    for (size_t l = 0; l < s->levels.size(); ++l)
+      if ((rc = level_fp32(s, l))) return rc;
+    SphLevel *L0 = s->levels[0];
+    if (L0->ap_ptr && !L0->ap_val32 && !(L0->ap_val32 = lalloc<float>(s, L0, L0->nnz_ap)))
+      return SPH_RT_ENOMEM;
+    if ((rc = galerkin_levels<float>(s))) return rc;
+  } else {
+    if ((rc = galerkin_levels<double>(s))) return rc;
+  }
+  std::vector<int> mode(s->levels.size()), degree(s->levels.size());
+  for (size_t l = 0; l < s->levels.size(); ++l) {
+    const bool coarsest = l + 1 == s->levels.size();
+    mode[l] = coarsest ? 2 : 1;
+    degree[l] = coarsest ? coarse_degree(s, s->levels[l]) : s->cfg.cheb_degree;
+  }
+  if ((rc = launch_cheb_slots(s, 1, s->amg_gersh, mode, degree))) return rc;
+  // FP32 CG vectors of the V-cycle-product CG, allocated here (not while a
+  // loop graph is being captured)
+  if (mixed && fcg_active(s)) {
+    FcgVecs v;
+    if ((rc = fcg_vectors(s, &v))) return rc;
+  }
+  return SPH_RT_OK;
+}
+
+template <typename T>
+static void tail_setup(sph_rt *s);
+
+sph_rt_status amg_setup(sph_rt *s) {
+  sph_rt_status rc;
+  if (!s->amg_ready || s->cfg.amg_rebuild) {
+    if ((rc = build_structure(s))) return rc;
+    if (s->cfg.precision == SPH_RT_MIXED)
+      tail_setup<float>(s);
+    else
+      tail_setup<double>(s);
+    // A P of the levels larger than the tail threshold: the smaller ones
+    // post-smooth the same way with or without the cluster tail, so both give
+    // bitwise the same V-cycle
+    for (size_t l = 0; l + 1 < s->levels.size() && s->levels[l]->nnz > kTailMaxNnz; ++l)
+      if ((rc = build_ap(s, l))) return rc;
+  }
+  return numeric(s);
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle
+// ---------------------------------------------------------------------------
 template <typename T>
 static sph_rt_status launch_tail(sph_rt *s, size_t l0, const T *r, T *z, const Scalars *sc) {
   using LV = LevelVecs<T>;

@@ -75,6 +75,10 @@ struct Scalars {
   int pfirst;      // the next update starts the directions: p = z, q = B z
   int ru;          // mixed form: the next launch replaces r by the FP64 residual
   double rmax2;    // mixed form: largest ||r / V||^2 since the last replacement
+  int yvalid;      // mixed form: the last solve ended on a verified residual whose B x
+                   // (kept in the handle's w) is that of the next solve's start
+  // time step choice of the last converged step (config.dt_target > 0)
+  double dtc_ebar, dtc_Ebar, dtc_eta_e, dtc_eta_E, dtc_next;
 };
 
 // --------------------------------------------------------------------------
@@ -497,7 +501,6 @@ __host__ inline int lanes_for_mean(double mean) { return mean <= 160 ? 4 : 8; }
 __host__ inline RowShape shape_for_mean(double mean) {
   return {lanes_for_mean(mean), 4};
 }
-
 // Grid of a row-tile sweep (W lanes per row, kBlock threads per block): one
 // wave of sweep_min_blocks(U) resident blocks per SM at most (the sweeps are
 // compiled with that register cap); warp_rows splits the rows over its warps.
@@ -598,7 +601,8 @@ struct sph_rt {
   int32_t *mat_col = nullptr;
   double *mat_G = nullptr;     // V_i V_j F_ij
   double *mat_val = nullptr;   // B_ij of the current step
-  float *mat_val32 = nullptr;  // FP32 copy for the mixed form
+  float *mat_val32 = nullptr;  // FP32 copy for the mixed form (written by the assembly)
+  float *diag32 = nullptr, *invdiag32 = nullptr;
   double *diag = nullptr, *invdiag = nullptr;
   int64_t *gh_ptr = nullptr;   // Dirichlet-ghost couplings
   int32_t *gh_slot = nullptr;

@@ -45,6 +45,7 @@ __global__ void outer_init_kernel(Scalars *sc) {
   sc->krylov_trips = 0;
   sc->krylov_solve_trips = 0;
   sc->newton_max = (int)sc->red[2];
+  sc->yvalid = 0;  // a new step has a new operator
   sc->last_change_e = 0.0;
   sc->last_change_E = 0.0;
   for (int k = 0; k < 64; ++k) sc->krylov_per_outer[k] = 0;

@@ -636,14 +636,17 @@ sph_rt_status fcg_cycle(sph_rt *s, const FcgVecs &v, int first);
 
 // r = b - B x in FP64 (stored in T), the smoother start zpre = c0 D^{-1} r,
 // ||r / V||^2 and the convergence test.  gated: a reliable update, run only
-// when the last update asked for one (sc->ru); else the start of a solve.
+// when the last update asked for one (sc->ru); it also keeps B x in y (mixed
+// form), valid for the next solve's start if this replacement ends the solve.
+// Else the start of a solve, skipped when that B x is valid (fcg_start_y_kernel
+// starts from it instead).
 template <int W, int U, typename T>
 __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U))
     fcg_resid_kernel(CsrView<double> A, const double *b, const double *x, T *r, T *zpre,
                      const T *invdiag, const ChebCoef *cf, const double *invV, int gated,
-                     Scalars *sc, double *partials, int *wflag) {
+                     double *y, Scalars *sc, double *partials, int *wflag) {
   pdl_wait();
-  if (gated && (sc->done || !sc->ru)) {
+  if (gated ? (sc->done || !sc->ru) : sc->yvalid) {
     mark_work(wflag, 0);
     return;
   }
@@ -658,10 +661,12 @@ __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U))
     const int64_t i = base + own;
     const double s = tile_row_sums<W, U, double, double>(base, rows, A.ptr, A.col, A.val, x);
     if (own < rows) {
-      const double ri = b[i] - fmadd(A.diag[i], x[i], s);
+      const double bx = fmadd(A.diag[i], x[i], s);
+      const double ri = b[i] - bx;
       const T rt = (T)ri;
       r[i] = rt;
       zpre[i] = (T)(c0 * (double)invdiag[i] * (double)rt);
+      if (y) y[i] = bx;
       const double ru = ri * invV[i];
       acc += ru * ru;
     }
@@ -677,6 +682,42 @@ __global__ void __launch_bounds__(kBlock, sweep_min_blocks(U))
     if (!gated) sc->iters = 0;
     sc->done = !(out[0] > sc->thresh2);  // also stops on NaN
     if (!(out[0] == out[0])) sc->breakdown = 1;
+    sc->yvalid = gated && y && sc->done && !sc->breakdown;
+  }
+}
+
+// Start of a solve from the kept B x (mixed form, after a solve that ended on a
+// verified residual at the same x and operator): r = b - y, with the same
+// smoother start, norm and test as fcg_resid_kernel.  Skipped otherwise.
+template <typename T>
+__global__ void fcg_start_y_kernel(int64_t n, const double *b, const double *y, T *r, T *zpre,
+                                   const T *invdiag, const ChebCoef *cf, const double *invV,
+                                   Scalars *sc, double *partials) {
+  pdl_wait();
+  if (!sc->yvalid) return;
+  const double c0 = cf->inv_theta;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = b[i] - y[i];
+    const T rt = (T)ri;
+    r[i] = rt;
+    zpre[i] = (T)(c0 * (double)invdiag[i] * (double)rt);
+    const double ru = ri * invV[i];
+    acc += ru * ru;
+  }
+  __shared__ double sh[32];
+  acc = block_sum(acc, sh);
+  double part[1] = {acc}, out[1];
+  const bool mx[1] = {false};
+  if (last_block_combine<1>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    sc->rnorm2 = out[0];
+    sc->rmax2 = out[0];
+    sc->ru = 0;
+    sc->iters = 0;
+    sc->done = !(out[0] > sc->thresh2);
+    if (!(out[0] == out[0])) sc->breakdown = 1;
+    sc->yvalid = 0;
   }
 }
 
@@ -740,21 +781,30 @@ __global__ void fcg_update_kernel(int64_t n, double *x, T *r, T *p, T *q, const 
 static sph_rt_status fcg_resid_launch(sph_rt *s, const FcgVecs &v, int gated) {
   CsrView<double> A = fine_view(s);
   const int gw = row_grid(s->num_sms, A.n, A.W, A.U);
+  const bool mixed = s->cfg.precision == SPH_RT_MIXED;
+  // the mixed form keeps B x of its replacements in w (its CG vectors are FP32)
+  double *y = mixed && gated ? s->w : nullptr;
   int *wf = timing_begin(s);
-  if (s->cfg.precision == SPH_RT_MIXED)
+  if (mixed)
     SPH_DISPATCH_SHAPE(A.W, A.U,
                        (pdl_launch(s, fcg_resid_kernel<W, U, float>, gw, kBlock, 0, A, s->b,
                                    s->x, v.f32.r, v.f32.zpre, v.f32.invdiag, v.cf, s->invV, gated,
-                                   s->sc, s->partials, wf)));
+                                   y, s->sc, s->partials, wf)));
   else
     SPH_DISPATCH_SHAPE(A.W, A.U,
                        (pdl_launch(s, fcg_resid_kernel<W, U, double>, gw, kBlock, 0, A, s->b,
                                    s->x, v.f64.r, v.f64.zpre, v.f64.invdiag, v.cf, s->invV, gated,
-                                   s->sc, s->partials, wf)));
+                                   y, s->sc, s->partials, wf)));
   SPH_LAUNCHED(s);
-  // rowptr, diag, b, x, 1/V, r, zpre, 1/diag
-  const double tb = s->cfg.precision == SPH_RT_MIXED ? 4.0 : 8.0;
-  timing_end(s, spmv_class_bytes(A, 40 + (int)(3 * tb)), kTimedTrueResid);
+  // rowptr, diag, b, x, 1/V, r, zpre, 1/diag (+ y)
+  const double tb = mixed ? 4.0 : 8.0;
+  timing_end(s, spmv_class_bytes(A, 40 + (int)(3 * tb) + (y ? 8 : 0)), kTimedTrueResid);
+  if (mixed && !gated) {
+    pdl_launch(s, fcg_start_y_kernel<float>, grid_cap(s, A.n, kBlock), kBlock, 0, A.n, s->b,
+               (const double *)s->w, v.f32.r, v.f32.zpre, v.f32.invdiag, v.cf, s->invV, s->sc,
+               s->partials);
+    SPH_LAUNCHED(s);
+  }
   return SPH_RT_OK;
 }
 

@@ -401,13 +401,36 @@ __device__ __forceinline__ uint64_t warp_sort_u64(uint64_t v) {
   return v;
 }
 
+// Pair weight F_ij = W'_ij / r (two-h average) of neighbour j of i, in FP64.
+__device__ __forceinline__ double pair_weight(double xi, double yi, double zi, double ihi,
+                                              double cwi, int64_t j, const double *px,
+                                              const double *py, const double *pz,
+                                              const double *ih, const double *cw) {
+  const double r2 = exact_r2(xi, yi, zi, px[j], py[j], pz[j]);
+  const double ir = rsqrt_fp64(r2), r = r2 * ir;
+  const double dwi = cwi * spline_dw(r * ihi);
+  const double dwj = cw[j] * spline_dw(r * ih[j]);
+  return 0.5 * (dwi + dwj) * ir;
+}
+
+// One warp per interior particle.  FILL: the hits of each 32-candidate batch
+// (a few of 27 candidates per cell) are appended, in discovery order, to a
+// per-warp buffer, and their FP64 pair weights are computed 32 at a time:
+// an FP64 warp instruction costs the same with 1 or 32 active lanes, so
+// computing the weights per batch would cost ~27 batches of FP64 work per
+// particle instead of ~4.
+constexpr int kHitBuf = 64;  // pending hits per warp (< 32 carried + 32 new)
+
 template <bool FILL>
 __global__ void neighbor_kernel(Grid g, const double *px, const double *py, const double *pz,
                                 const double *h, const float4 *rel, const int64_t *cell_start,
                                 const unsigned *cell_count, int64_t n_int, int64_t *count,
                                 const int64_t *rowptr, int32_t *cols, double *F,
                                 const double *ih, const double *cw) {
+  __shared__ int32_t hitbuf[kWarpsPerBlock][FILL ? kHitBuf : 1];
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int32_t *hb = hitbuf[threadIdx.x >> 5];
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int ncells = g.dim == 3 ? 27 : (g.dim == 2 ? 9 : 3);
@@ -433,8 +456,11 @@ __global__ void neighbor_kernel(Grid g, const double *px, const double *py, cons
       if (ok) mykey = (morton(g, cc[0], cc[1], cc[2]) << 5) | (uint64_t)lane;
     }
     const uint64_t sorted = warp_sort_u64(mykey);
-    int64_t out = FILL ? rowptr[i] : 0;
-    int64_t total = 0;
+    const int64_t out = FILL ? rowptr[i] : 0;
+    const double ihi = FILL ? ih[i] : 0.0, cwi = FILL ? cw[i] : 0.0;
+    int64_t total = 0;  // hits found (warp-uniform)
+    int64_t done = 0;   // hits written (FILL)
+    int pending = 0;    // hits in the buffer (FILL, warp-uniform)
     for (int pass = 0; pass < 2; ++pass) {  // interior cells, then ghost cells
       for (int k = 0; k < ncells; ++k) {
         const uint64_t v = __shfl_sync(0xffffffffu, sorted, k);
@@ -465,18 +491,34 @@ __global__ void neighbor_kernel(Grid g, const double *px, const double *py, cons
             }
           }
           const unsigned m = __ballot_sync(0xffffffffu, hit);
-          if (FILL && hit) {
-            const int64_t at = out + total + __popc(m & ((1u << lane) - 1u));
-            cols[at] = (int32_t)j;
-            const double r2 = exact_r2(xi, yi, zi, px[j], py[j], pz[j]);
-            const double ir = rsqrt_fp64(r2), r = r2 * ir;
-            const double dwi = cw[i] * spline_dw(r * ih[i]);
-            const double dwj = cw[j] * spline_dw(r * ih[j]);
-            F[at] = 0.5 * (dwi + dwj) * ir;  // F_ij = W'_ij / r, two-h average
-          }
           total += __popc(m);
+          if (FILL) {
+            if (hit) hb[pending + __popc(m & lt)] = (int32_t)j;
+            pending += __popc(m);
+            __syncwarp();
+            if (pending >= 32) {  // 32 weights with every lane active
+              const int32_t jj = hb[lane];
+              cols[out + done + lane] = jj;
+              F[out + done + lane] = pair_weight(xi, yi, zi, ihi, cwi, jj, px, py, pz, ih, cw);
+              const int rest = pending - 32;
+              const int32_t carry = lane < rest ? hb[32 + lane] : 0;
+              __syncwarp();
+              if (lane < rest) hb[lane] = carry;
+              __syncwarp();
+              pending = rest;
+              done += 32;
+            }
+          }
         }
       }
+    }
+    if (FILL && pending > 0) {
+      if (lane < pending) {
+        const int32_t jj = hb[lane];
+        cols[out + done + lane] = jj;
+        F[out + done + lane] = pair_weight(xi, yi, zi, ihi, cwi, jj, px, py, pz, ih, cw);
+      }
+      __syncwarp();
     }
     if (!FILL && lane == 0) count[i] = total;
   }

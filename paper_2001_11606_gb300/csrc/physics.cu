@@ -258,12 +258,15 @@ __global__ void props_copy_kernel(int64_t n_int, int64_t n, const int32_t *copys
 // B_ij = G_ij (D_i + D_j) written for entries beg + sub + j W, j < nmax
 // (nmax warp-uniform), and this lane's sum of them.  Slots past the row's end
 // store nothing and add +0.
-template <int W, int U>
+// F32: also write the FP32 copy of the mixed form.
+template <int W, int U, bool F32>
 __device__ __forceinline__ double assemble_row_n(int64_t beg, int64_t end,
                                                  const int32_t *__restrict__ mat_col,
                                                  const double *__restrict__ mat_G,
                                                  const double *__restrict__ D, double Di,
-                                                 double *__restrict__ mat_val, int sub, int nmax) {
+                                                 double *__restrict__ mat_val,
+                                                 float *__restrict__ mat_val32, int sub,
+                                                 int nmax) {
   double offsum = 0.0;
   int64_t k = beg + sub;
   int j = 0;
@@ -281,6 +284,7 @@ __device__ __forceinline__ double assemble_row_n(int64_t beg, int64_t end,
       if (c[u] < 0) continue;
       const double v = g[u] * (Di + __ldg(D + c[u]));
       mat_val[k + (int64_t)u * W] = v;
+      if (F32) mat_val32[k + (int64_t)u * W] = (float)v;
       offsum += v;
     }
   }
@@ -299,6 +303,7 @@ __device__ __forceinline__ double assemble_row_n(int64_t beg, int64_t end,
       if (k < end) {
         const double v = g[0] * (Di + dj[0]);
         mat_val[k] = v;
+        if (F32) mat_val32[k] = (float)v;
         offsum += v;
       }
 #pragma unroll
@@ -316,14 +321,15 @@ __device__ __forceinline__ double assemble_row_n(int64_t beg, int64_t end,
 // up its Dirichlet-ghost couplings (few rows have any); the diagonal, its
 // inverse, the ghost right-hand side and the Gershgorin ratio are computed on
 // all 32 lanes.
-template <int W, int U>
+template <int W, int U, bool F32>
 __global__ void __launch_bounds__(kBlock, kPairMinBlocks)
     assemble_kernel(Phys ph, int64_t n_int, const int64_t *mat_ptr, const int32_t *mat_col,
                     const double *mat_G, double *mat_val, const int64_t *gh_ptr,
                     const int32_t *gh_slot, const double *gh_W, const double *V,
                     const double *sigma, const double *f, const double *D, const double *E,
                     double *diag, double *invdiag, double *gb, double *partials,
-                    unsigned *counter, double *gersh_out) {
+                    unsigned *counter, double *gersh_out, float *mat_val32, float *diag32,
+                    float *invdiag32) {
   // gersh_out = max_i sum_{j != i} |B_ij| / B_ii: the eigenvalues of D^{-1} B
   // lie in [1 - gersh, 1 + gersh] (Gershgorin; B is symmetric, so real).
   const int lane = threadIdx.x & 31, sub = lane % W, own = tile_own_row<W>(lane);
@@ -349,8 +355,8 @@ __global__ void __launch_bounds__(kBlock, kPairMinBlocks)
       const int64_t gb0 = __shfl_sync(0xffffffffu, hb, t, W);
       const int64_t ge0 = __shfl_sync(0xffffffffu, he, t, W);
       const double Di = __shfl_sync(0xffffffffu, Do, t, W);
-      const double offsum = assemble_row_n<W, U>(rb, re, mat_col, mat_G, D, Di, mat_val, sub,
-                                                 tile_nmax<W>(rb, re, sub));
+      const double offsum = assemble_row_n<W, U, F32>(rb, re, mat_col, mat_G, D, Di, mat_val,
+                                                      mat_val32, sub, tile_nmax<W>(rb, re, sub));
       double wsum = 0.0, gbs = 0.0;
       const int ng = tile_nmax<W>(gb0, ge0, sub);
       for (int jj = 0; jj < ng; ++jj) {
@@ -369,6 +375,10 @@ __global__ void __launch_bounds__(kBlock, kPairMinBlocks)
       double d = V[i] * (1.0 / ph.dt + ph.c * sigma[i] * f[i] + wsum) - offsum;
       diag[i] = d;
       invdiag[i] = 1.0 / d;
+      if (F32) {
+        diag32[i] = (float)d;
+        invdiag32[i] = (float)(1.0 / d);
+      }
       gb[i] = gbs;
       gmax = fmax(gmax, -offsum / d);  // off-diagonals are <= 0
     }
@@ -698,11 +708,21 @@ sph_rt_status launch_assembly(sph_rt *s, double dt, double *gersh_out) {
   Phys ph = make_phys(s, dt);
   RowShape sh = shape_for_mean(s->n_int ? (double)s->nnz_mat / (double)s->n_int : 0.0);
   int gr = row_grid_blocks(s->num_sms, s->n_int, sh.W, kPairMinBlocks);
-  SPH_DISPATCH_SHAPE(sh.W, sh.U,
-                     (assemble_kernel<W, U><<<gr, kBlock, 0, s->stream>>>(
-                         ph, s->n_int, s->mat_ptr, s->mat_col, s->mat_G, s->mat_val, s->gh_ptr,
-                         s->gh_slot, s->gh_W, s->V, s->sigma, s->f, s->D, s->E, s->diag,
-                         s->invdiag, s->gb, s->partials, &s->sc->counter, gersh_out)));
+  // the mixed form gets its FP32 copy of the fine operator in the same pass
+  if (s->mat_val32)
+    SPH_DISPATCH_SHAPE(sh.W, sh.U,
+                       (assemble_kernel<W, U, true><<<gr, kBlock, 0, s->stream>>>(
+                           ph, s->n_int, s->mat_ptr, s->mat_col, s->mat_G, s->mat_val, s->gh_ptr,
+                           s->gh_slot, s->gh_W, s->V, s->sigma, s->f, s->D, s->E, s->diag,
+                           s->invdiag, s->gb, s->partials, &s->sc->counter, gersh_out,
+                           s->mat_val32, s->diag32, s->invdiag32)));
+  else
+    SPH_DISPATCH_SHAPE(sh.W, sh.U,
+                       (assemble_kernel<W, U, false><<<gr, kBlock, 0, s->stream>>>(
+                           ph, s->n_int, s->mat_ptr, s->mat_col, s->mat_G, s->mat_val, s->gh_ptr,
+                           s->gh_slot, s->gh_W, s->V, s->sigma, s->f, s->D, s->E, s->diag,
+                           s->invdiag, s->gb, s->partials, &s->sc->counter, gersh_out,
+                           nullptr, nullptr, nullptr)));
   SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }
@@ -733,6 +753,84 @@ sph_rt_status launch_check_inputs(sph_rt *s, const double *Qe, const double *QE,
   if (!Qe && !QE && !ge && !gE) return SPH_RT_OK;
   check_inputs_kernel<<<grid_items(s, s->n, kBlock), kBlock, 0, s->stream>>>(
       s->n, s->caller2slot, s->kind, Qe, QE, ge, gE, s->sc);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Time step choice (Sec. 3.3, Eq. energy-fractional), after a converged step:
+//   xbar = sum_i x_i^n V_i / sum_i V_i                       (volume average)
+//   eta_x = max_i |x_i^n - x_i^{n-1}| / (x_i^n + target xbar + floor)
+//   dt_x = dt (target / eta_x)^(1/2)
+//   dt_next = min(dt_e, dt_E, growth dt, dt_max), at least dt_min
+// for x = e and x = E over the interior particles.  x^{n-1} is the snapshot
+// taken at the start of the step.
+// ---------------------------------------------------------------------------
+__global__ void dtc_sums_kernel(int64_t n_int, const double *V, const double *e, const double *E,
+                                Scalars *sc, double *partials) {
+  double a = 0.0, b = 0.0, v = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double Vi = V[i];
+    a += e[i] * Vi;
+    b += E[i] * Vi;
+    v += Vi;
+  }
+  __shared__ double sh[32];
+  double part[3];
+  part[0] = block_sum(a, sh);
+  __syncthreads();
+  part[1] = block_sum(b, sh);
+  __syncthreads();
+  part[2] = block_sum(v, sh);
+  double out[3];
+  const bool mx[3] = {false, false, false};
+  if (last_block_combine<3>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    sc->dtc_ebar = out[0] / out[2];
+    sc->dtc_Ebar = out[1] / out[2];
+  }
+}
+
+struct DtControl {
+  double dt, target, growth, dt_min, dt_max, floor;
+};
+
+__global__ void dtc_eta_kernel(int64_t n_int, const double *e, const double *E,
+                               const double *e_old, const double *E_old, DtControl c, Scalars *sc,
+                               double *partials) {
+  const double de = c.target * sc->dtc_ebar + c.floor, dE = c.target * sc->dtc_Ebar + c.floor;
+  double me = 0.0, mE = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double en = e[i], En = E[i];
+    me = fmax(me, fabs(en - e_old[i]) / (en + de));
+    mE = fmax(mE, fabs(En - E_old[i]) / (En + dE));
+  }
+  __shared__ double sh[32];
+  double part[2];
+  part[0] = block_max(me, sh);
+  __syncthreads();
+  part[1] = block_max(mE, sh);
+  double out[2];
+  const bool mx[2] = {true, true};
+  if (last_block_combine<2>(part, partials, &sc->counter, out, mx) && threadIdx.x == 0) {
+    double next = fmin(c.growth * c.dt, c.dt_max);
+    if (out[0] > 0.0) next = fmin(next, c.dt * sqrt(c.target / out[0]));
+    if (out[1] > 0.0) next = fmin(next, c.dt * sqrt(c.target / out[1]));
+    sc->dtc_eta_e = out[0];
+    sc->dtc_eta_E = out[1];
+    sc->dtc_next = fmax(next, c.dt_min);
+  }
+}
+
+sph_rt_status launch_dt_control(sph_rt *s, double dt) {
+  const int g = grid_items(s, s->n_int, kBlock);
+  dtc_sums_kernel<<<g, kBlock, 0, s->stream>>>(s->n_int, s->V, s->e, s->E, s->sc, s->partials);
+  SPH_LAUNCHED(s);
+  const DtControl c = {dt, s->cfg.dt_target, s->cfg.dt_growth, s->cfg.dt_min, s->cfg.dt_max,
+                       s->cfg.dt_eta_floor};
+  dtc_eta_kernel<<<g, kBlock, 0, s->stream>>>(s->n_int, s->e, s->E, s->e_bak, s->E_bak, c, s->sc,
+                                              s->partials);
   SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }

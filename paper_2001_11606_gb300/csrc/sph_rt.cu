@@ -35,6 +35,7 @@ sph_rt_status launch_gather_interior(sph_rt *s, const double *in_c, double *out)
 sph_rt_status launch_scatter_caller(sph_rt *s, const double *in_s, int64_t count, double *out_c);
 sph_rt_status launch_finish(sph_rt *s, const double *e_new, const double *E_new);
 sph_rt_status launch_save_before(sph_rt *s);
+sph_rt_status launch_dt_control(sph_rt *s, double dt);
 sph_rt_status pcg_solve(sph_rt *s, int *iters, bool *converged);
 sph_rt_status autotune_fine_shape(sph_rt *s);
 sph_rt_status outer_loop(sph_rt *s, double dt);
@@ -121,6 +122,8 @@ void free_all(sph_rt *s) {
   s->amg_ready = false;
   s->gcol = nullptr;
   s->gvx = s->gvy = s->gvz = nullptr;
+  s->mat_val32 = nullptr;
+  s->diag32 = s->invdiag32 = nullptr;
   s->amg_gersh = nullptr;
   s->cheb_slots = nullptr;
   s->ev_flags = nullptr;
@@ -180,7 +183,12 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->graphs = 1;
   c->pdl = 1;
   c->fine_post_smooth = 1;
-  c->reliable_drop = 1e-2;
+  c->reliable_drop = 1e-4;
+  c->dt_target = 0.0;
+  c->dt_growth = 10.0;
+  c->dt_min = 0.0;
+  c->dt_max = 1e300;
+  c->dt_eta_floor = 1e-15;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -189,8 +197,9 @@ static bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
 static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
   if (c->dim < 1 || c->dim > 3) return why = "dim must be 1, 2 or 3", SPH_RT_EINVAL;
-  if (!finite_pos(c->a) || !finite_pos(c->c) || !finite_pos(c->cv))
-    return why = "a, c and cv must be finite and positive", SPH_RT_EINVAL;
+  if (!(isfinite(c->a) && c->a >= 0.0) || !finite_pos(c->c) || !finite_pos(c->cv))
+    return why = "a must be finite and >= 0 (0: no emission); c and cv finite and positive",
+           SPH_RT_EINVAL;
   if (c->limiter < 0 || c->limiter > 2) return why = "limiter out of range", SPH_RT_EINVAL;
   if (c->limiter == SPH_RT_LIMITER_LARSEN && !finite_pos(c->larsen_k))
     return why = "larsen_k must be positive", SPH_RT_EINVAL;
@@ -219,6 +228,13 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
     return why = "fine_post_smooth = 0 needs cheb_degree = 1", SPH_RT_EINVAL;
   if (!(c->reliable_drop > 0.0 && c->reliable_drop < 1.0))
     return why = "reliable_drop must be in (0, 1)", SPH_RT_EINVAL;
+  if (!(c->dt_target >= 0.0 && c->dt_target < 1e300))
+    return why = "dt_target must be >= 0 (0 = no time step choice)", SPH_RT_EINVAL;
+  if (!(c->dt_growth >= 1.0 && c->dt_growth < 1e300) || !(c->dt_min >= 0.0) ||
+      !(c->dt_max > 0.0) || !(c->dt_min <= c->dt_max) || !(c->dt_eta_floor >= 0.0 &&
+      c->dt_eta_floor < 1e300))
+    return why = "time step limits: dt_growth >= 1, 0 <= dt_min <= dt_max, dt_eta_floor >= 0",
+           SPH_RT_EINVAL;
   if (c->device < 0) return why = "device must be >= 0", SPH_RT_EINVAL;
   return SPH_RT_OK;
 }
@@ -355,6 +371,12 @@ static sph_rt_status alloc_step_vectors(sph_rt *s) {
   for (double **p : inner)
     if (!(*p = dalloc<double>(s, ni))) return SPH_RT_ENOMEM;
   if (!(s->gersh = dalloc<double>(s, 1))) return SPH_RT_ENOMEM;
+  if (s->cfg.precision == SPH_RT_MIXED) {
+    s->mat_val32 = dalloc<float>(s, s->nnz_mat);
+    s->diag32 = dalloc<float>(s, ni);
+    s->invdiag32 = dalloc<float>(s, ni);
+    if (!s->mat_val32 || !s->diag32 || !s->invdiag32) return SPH_RT_ENOMEM;
+  }
   if (!(s->cheb_slots = dalloc<ChebCoef>(s, kChebSlots))) return SPH_RT_ENOMEM;
   SPH_CUDA(s, cudaMemsetAsync(s->Qe, 0, sizeof(double) * ni, s->stream));
   SPH_CUDA(s, cudaMemsetAsync(s->QE, 0, sizeof(double) * ni, s->stream));
@@ -575,6 +597,9 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   if ((rc = launch_copy_sync(s))) return rc;
   if ((rc = launch_balance(s, dt, s->E))) return rc;
   if ((rc = launch_totals(s, s->e, s->E))) return rc;
+  // time step choice (Sec. 3.3) from the committed state; a step that did not
+  // converge restored the snapshot, so its proposal is not reported
+  if (s->cfg.dt_target > 0.0 && (rc = launch_dt_control(s, dt))) return rc;
   if ((rc = read_scalars(s))) return rc;
   if (s->sc_host->bad_input) {
     tm.collect(ms);
@@ -608,6 +633,11 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   st.source_energy = s->sc_host->red[6];
   st.boundary_energy = s->sc_host->red[7];
   st.energy_after = s->sc_host->red[4] + s->sc_host->red[5];
+  if (s->cfg.dt_target > 0.0) {
+    st.eta_e = s->sc_host->dtc_eta_e;
+    st.eta_E = s->sc_host->dtc_eta_E;
+    st.dt_next = s->sc_host->dtc_next;
+  }
   tm.collect(ms);
   st.t_setup_ms = ms[0];
   st.t_assembly_ms = ms[1];

@@ -52,6 +52,8 @@ class Config(C.Structure):
         ("pdl", C.c_int32),
         ("fine_post_smooth", C.c_int32),
         ("reliable_drop", C.c_double),
+        ("dt_target", C.c_double), ("dt_growth", C.c_double), ("dt_min", C.c_double),
+        ("dt_max", C.c_double), ("dt_eta_floor", C.c_double),
         ("device", C.c_int32),
         ("stream", C.c_void_p),
     ]
@@ -68,6 +70,7 @@ class Stats(C.Structure):
         ("last_change_e", C.c_double), ("last_change_E", C.c_double),
         ("t_setup_ms", C.c_double), ("t_assembly_ms", C.c_double), ("t_amg_ms", C.c_double),
         ("t_krylov_ms", C.c_double), ("t_newton_ms", C.c_double),
+        ("eta_e", C.c_double), ("eta_E", C.c_double), ("dt_next", C.c_double),
     ]
 
     def krylov_per_outer(self):

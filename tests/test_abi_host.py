@@ -48,13 +48,15 @@ def test_config_struct_matches_defaults():
     assert cfg.tol_outer_e == 1e-8 and cfg.tol_krylov == 1e-12 and cfg.tol_inner_e == 1e-13
 
 
-@pytest.mark.parametrize("field,value", [("dim", 4), ("cv", 0.0), ("limiter", 7),
+@pytest.mark.parametrize("field,value", [("dim", 4), ("cv", 0.0), ("a", -1.0), ("limiter", 7),
                                          ("tol_krylov", -1.0), ("max_outer", 0),
                                          ("precond", 9), ("cheb_degree", 0),
                                          ("amg_theta", 1.5), ("graphs", 2), ("pdl", 2),
                                          ("amg_tail", -1), ("coarse_fp32", 2),
                                          ("fine_post_smooth", 2), ("reliable_drop", 0.0),
-                                         ("reliable_drop", 1.0)])
+                                         ("reliable_drop", 1.0), ("dt_target", -0.1),
+                                         ("dt_growth", 0.5), ("dt_min", -1.0),
+                                         ("dt_max", 0.0), ("dt_eta_floor", -1.0)])
 def test_create_rejects_bad_config(field, value):
     cfg = sphrt.default_config(**{field: value})
     with pytest.raises(sphrt.SphRtError) as ei:

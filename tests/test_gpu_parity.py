@@ -290,7 +290,7 @@ def test_vcycle_product_cg_parity(make, precision, tol):
         assert g.outer_iters == o.outer_iters
 
 
-@pytest.mark.parametrize("drop", [0.5, 1e-2, 1e-4])
+@pytest.mark.parametrize("drop", [0.5, 1e-2, 1e-4, 1e-6])
 def test_vcycle_product_cg_stops_on_the_fp64_residual(drop):
     # whatever the replacement interval, the mixed solve stops only when the FP64
     # residual meets the tolerance: the energies agree with the FP64 form's
