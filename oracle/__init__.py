@@ -35,6 +35,7 @@ class Params(C.Structure):
         ("tol_outer_e", C.c_double), ("tol_outer_E", C.c_double),
         ("tol_inner_e", C.c_double), ("tol_krylov", C.c_double),
         ("max_outer", C.c_int32), ("max_inner_e", C.c_int32), ("max_krylov", C.c_int32),
+        ("kernel", C.c_int32),
     ]
 
 
@@ -73,9 +74,10 @@ def lib():
             P = C.c_void_p
             i64, i32, dbl = C.c_int64, C.c_int, C.c_double
             L.orc_kernel.argtypes = [i32, dbl, dbl, P, P]
-            L.orc_neighbors.argtypes = [i64, i32, P, P, P, i32, P, P]
+            L.orc_kernel_c4.argtypes = [i32, dbl, dbl, P, P]
+            L.orc_neighbors.argtypes = [i64, i32, P, P, P, i32, i32, P, P]
             L.orc_neighbors.restype = i64
-            L.orc_neighbors_rows.argtypes = [i64, i32, P, P, i64, P, P, P]
+            L.orc_neighbors_rows.argtypes = [i64, i32, P, P, i32, i64, P, P, P]
             L.orc_neighbors_rows.restype = i64
             L.orc_properties.argtypes = [P, i64, P, P, P, P, P, P, P, P, P, dbl, P, P,
                                          P, P, P, P, P, P]
@@ -109,7 +111,7 @@ def make_params(**kw) -> Params:
     p = Params()
     defaults = dict(dim=3, a=1.0, c=1.0, cv=1.0, limiter=0, larsen_k=2.0, opacity_exp=0.0,
                     T_floor=0.0, tol_outer_e=1e-8, tol_outer_E=1e-8, tol_inner_e=1e-13,
-                    tol_krylov=1e-12, max_outer=50, max_inner_e=50, max_krylov=5000)
+                    tol_krylov=1e-12, max_outer=50, max_inner_e=50, max_krylov=5000, kernel=0)
     defaults.update(kw)
     for k, v in defaults.items():
         setattr(p, k, v)
@@ -124,9 +126,12 @@ def set_threads(n: int) -> None:
     lib().orc_set_threads(int(n))
 
 
-def kernel(dim: int, r: float, h: float):
+def kernel(dim: int, r: float, h: float, kern: int = 0):
+    """(W, dW/dr) of the M4 cubic B-spline (kern 0, support 2h) or the Wendland
+    C4 kernel (kern 1, support h; Sec. 2.4)."""
     W, dW = C.c_double(), C.c_double()
-    lib().orc_kernel(dim, float(r), float(h), C.byref(W), C.byref(dW))
+    fn = lib().orc_kernel_c4 if kern == 1 else lib().orc_kernel
+    fn(dim, float(r), float(h), C.byref(W), C.byref(dW))
     return W.value, dW.value
 
 
@@ -136,21 +141,23 @@ def limiter(R: float, limiter: int, larsen_k: float = 2.0) -> float:
     return float(lib().orc_limiter(C.byref(p), float(R)))
 
 
-def neighbors(pos, h, kind, brute: bool = False):
-    """Neighbour CSR over all particles in caller order: (rowptr int64, cols int32)."""
+def neighbors(pos, h, kind, brute: bool = False, kernel: int = 0):
+    """Neighbour CSR over all particles in caller order: (rowptr int64, cols int32).
+    kernel 0: support 2h (M4); 1: support h (Wendland C4)."""
     pos = _f64(pos)
     n, dim = pos.shape
     h = _f64(h)
     kind = np.ascontiguousarray(kind, dtype=np.int32)
     rowptr = np.zeros(n + 1, dtype=np.int64)
     L = lib()
-    L.orc_neighbors(n, dim, _p(pos), _p(h), _p(kind), int(brute), _p(rowptr), None)
+    L.orc_neighbors(n, dim, _p(pos), _p(h), _p(kind), int(brute), int(kernel), _p(rowptr), None)
     cols = np.zeros(max(int(rowptr[-1]), 1), dtype=np.int32)
-    L.orc_neighbors(n, dim, _p(pos), _p(h), _p(kind), int(brute), _p(rowptr), _p(cols))
+    L.orc_neighbors(n, dim, _p(pos), _p(h), _p(kind), int(brute), int(kernel), _p(rowptr),
+                    _p(cols))
     return rowptr, cols[: rowptr[-1]]
 
 
-def neighbors_of_rows(pos, h, rows):
+def neighbors_of_rows(pos, h, rows, kernel: int = 0):
     """Brute-force neighbour lists (caller IDs, ascending) of the given rows."""
     pos = _f64(pos)
     n, dim = pos.shape
@@ -158,9 +165,10 @@ def neighbors_of_rows(pos, h, rows):
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     rp = np.zeros(len(rows) + 1, dtype=np.int64)
     L = lib()
-    L.orc_neighbors_rows(n, dim, _p(pos), _p(h), len(rows), _p(rows), _p(rp), None)
+    L.orc_neighbors_rows(n, dim, _p(pos), _p(h), int(kernel), len(rows), _p(rows), _p(rp), None)
     cols = np.zeros(max(int(rp[-1]), 1), dtype=np.int32)
-    L.orc_neighbors_rows(n, dim, _p(pos), _p(h), len(rows), _p(rows), _p(rp), _p(cols))
+    L.orc_neighbors_rows(n, dim, _p(pos), _p(h), int(kernel), len(rows), _p(rows), _p(rp),
+                         _p(cols))
     return rp, cols[: rp[-1]]
 
 
@@ -180,7 +188,8 @@ class Problem:
         self.copy_of = np.ascontiguousarray(P.copy_of, dtype=np.int64)
         self.n = self.pos.shape[0]
         if nbrs is None:
-            nbrs = neighbors(self.pos, self.h, self.kind, brute=brute)
+            nbrs = neighbors(self.pos, self.h, self.kind, brute=brute,
+                             kernel=self.params.kernel)
         self.rowptr, self.cols = nbrs
 
     def properties(self, e, E, dt):

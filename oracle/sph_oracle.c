@@ -18,8 +18,12 @@
  *
  * Readings of the paper taken here (each is listed with its reason in the
  * design notes of the repository):
- *  - Kernel: M4 cubic B-spline, support 2h (the paper's Wendland C4 is a
- *    drop-in alternative, not used by the workloads).
+ *  - Kernel: M4 cubic B-spline with support 2h (kernel = 0, the workloads'
+ *    choice), or the paper's Wendland C4 with support h (kernel = 1, Sec. 2.4,
+ *    Eq. wendlandc4): the printed polynomial is the one-dimensional C4 form;
+ *    it is used as printed in every dimension, with the constant k of each
+ *    dimension fixed by the normalisation requirement (Sec. 2.3), as the
+ *    paper's definition of k states.
  *  - Neighbour predicate: j != i and r2 < (2 max(h_i,h_j))^2, r2 summed in
  *    coordinate order x, y, z with no fused multiply-add.
  *  - Kernel symmetrisation for unequal h: average of the two gradients (Sec. 2.4).
@@ -53,6 +57,7 @@ typedef struct {
   double T_floor;           /* T used inside sigma and R is max(T, T_floor) */
   double tol_outer_e, tol_outer_E, tol_inner_e, tol_krylov;
   int32_t max_outer, max_inner_e, max_krylov;
+  int32_t kernel;           /* 0: M4 cubic B-spline (support 2h); 1: Wendland C4 (support h) */
 } orc_params;
 
 enum { ORC_INTERIOR = 0, ORC_DIRICHLET = 1, ORC_COPY = 2 };
@@ -100,11 +105,49 @@ void orc_kernel(int dim, double r, double h, double *W, double *dWdr) {
   *dWdr = norm * dw / h;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Kernel: Wendland C4 as printed in Eq. wendlandc4 (Sec. 2.4),               */
+/*   W = k/h^d (1 - q)^5 (8 q^2 + 5 q + 1),  q = r/h <= 1,                    */
+/* with k of each dimension from the normalisation integral (Sec. 2.3):       */
+/*   k S_d int_0^1 (1-q)^5 (8q^2+5q+1) q^(d-1) dq = 1, S_1 = 2, S_2 = 2 pi,    */
+/*   S_3 = 4 pi; the integrals are 1/3, 5/72, 1/45, so k = 3/2, 36/(5 pi),     */
+/*   45/(4 pi).  d/dq of the polynomial is -14 q (1 + 4q) (1 - q)^4.           */
+/* ------------------------------------------------------------------------ */
+static double wendland_norm(int dim, double h) {
+  if (dim == 1) return 1.5 / h;
+  if (dim == 2) return (36.0 / (5.0 * M_PI)) / (h * h);
+  return (45.0 / (4.0 * M_PI)) / (h * h * h);
+}
+
+void orc_kernel_c4(int dim, double r, double h, double *W, double *dWdr) {
+  double q = r / h;
+  double norm = wendland_norm(dim, h);
+  double w = 0.0, dw = 0.0;
+  if (q <= 1.0) {
+    double t = 1.0 - q;
+    double t4 = t * t * t * t;
+    w = t4 * t * (8.0 * q * q + 5.0 * q + 1.0);
+    dw = -14.0 * q * (1.0 + 4.0 * q) * t4;
+  }
+  *W = norm * w;
+  *dWdr = norm * dw / h;
+}
+
+/* Support radius of the kernel in units of h. */
+static double support_factor(int kern) { return kern == 1 ? 1.0 : 2.0; }
+
+static void kernel_eval(int kern, int dim, double r, double h, double *W, double *dWdr) {
+  if (kern == 1)
+    orc_kernel_c4(dim, r, h, W, dWdr);
+  else
+    orc_kernel(dim, r, h, W, dWdr);
+}
+
 /* F_ij = (x_ij . grad_i W_ij) / |x_ij|^2 = W'_ij / r with the two-h average. */
-static double pair_F(int dim, double r, double hi, double hj) {
+static double pair_F(int kern, int dim, double r, double hi, double hj) {
   double Wi, dWi, Wj, dWj;
-  orc_kernel(dim, r, hi, &Wi, &dWi);
-  orc_kernel(dim, r, hj, &Wj, &dWj);
+  kernel_eval(kern, dim, r, hi, &Wi, &dWi);
+  kernel_eval(kern, dim, r, hj, &Wj, &dWj);
   return 0.5 * (dWi + dWj) / r;
 }
 
@@ -125,10 +168,11 @@ static double pair_r2(int dim, const double *xi, const double *xj) {
   return r2;
 }
 
-static int is_neighbour(int dim, const double *pos, const double *h, int64_t i, int64_t j) {
+static int is_neighbour(int kern, int dim, const double *pos, const double *h, int64_t i,
+                        int64_t j) {
   if (i == j) return 0;
   double hmax = h[i] > h[j] ? h[i] : h[j];
-  double cut = 2.0 * hmax;
+  double cut = support_factor(kern) * hmax;
   double cut2 = cut * cut;
   return pair_r2(dim, pos + i * dim, pos + j * dim) < cut2;
 }
@@ -149,21 +193,22 @@ static int cmp_i32(const void *a, const void *b) {
 
 /*
  * Neighbour lists of every interior particle: all j != i (interior or ghost)
- * with r2 < (2 max(h_i,h_j))^2.  Rows are in caller order over all n particles
- * (ghost rows are empty); each row's columns are sorted ascending.
+ * with r2 < (s max(h_i,h_j))^2, s the kernel's support factor (2 for M4, 1
+ * for Wendland C4).  Rows are in caller order over all n particles (ghost rows
+ * are empty); each row's columns are sorted ascending.
  *
  * brute = 1 tests every pair.  brute = 0 sorts by x and, for each i, scans
- * outwards in x while (x_i - x_j)^2 < (2 h_max)^2; this prune is exact because
+ * outwards in x while (x_i - x_j)^2 < (s h_max)^2; this prune is exact because
  * the rounded r2 is never smaller than the rounded dx*dx.
  *
  * Pass cols = NULL to fill rowptr only.  Returns nnz.
  */
 int64_t orc_neighbors(int64_t n, int dim, const double *pos, const double *h,
-                      const int32_t *kind, int brute, int64_t *rowptr, int32_t *cols) {
+                      const int32_t *kind, int brute, int kern, int64_t *rowptr, int32_t *cols) {
   int64_t *order = NULL, *where = NULL;
   double hmax = 0.0;
   for (int64_t i = 0; i < n; ++i) hmax = h[i] > hmax ? h[i] : hmax;
-  double cutmax = 2.0 * hmax, cutmax2 = cutmax * cutmax;
+  double cutmax = support_factor(kern) * hmax, cutmax2 = cutmax * cutmax;
   if (!brute) {
     order = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     where = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
@@ -182,7 +227,7 @@ int64_t orc_neighbors(int64_t n, int dim, const double *pos, const double *h,
       int64_t c = 0;
       if (brute) {
         for (int64_t j = 0; j < n; ++j)
-          if (is_neighbour(dim, pos, h, i, j)) {
+          if (is_neighbour(kern, dim, pos, h, i, j)) {
             if (out) out[c] = (int32_t)j;
             ++c;
           }
@@ -192,7 +237,7 @@ int64_t orc_neighbors(int64_t n, int dim, const double *pos, const double *h,
           int64_t j = order[k];
           double dx = xi - pos[j * dim];
           if (!(dx * dx < cutmax2)) break;
-          if (is_neighbour(dim, pos, h, i, j)) {
+          if (is_neighbour(kern, dim, pos, h, i, j)) {
             if (out) out[c] = (int32_t)j;
             ++c;
           }
@@ -201,7 +246,7 @@ int64_t orc_neighbors(int64_t n, int dim, const double *pos, const double *h,
           int64_t j = order[k];
           double dx = xi - pos[j * dim];
           if (!(dx * dx < cutmax2)) break;
-          if (is_neighbour(dim, pos, h, i, j)) {
+          if (is_neighbour(kern, dim, pos, h, i, j)) {
             if (out) out[c] = (int32_t)j;
             ++c;
           }
@@ -227,13 +272,13 @@ int64_t orc_neighbors(int64_t n, int dim, const double *pos, const double *h,
  * every particle), for spot checks of large problems.  rowptr[nrows+1];
  * cols sized by the caller from a first call with cols = NULL.
  */
-int64_t orc_neighbors_rows(int64_t n, int dim, const double *pos, const double *h,
+int64_t orc_neighbors_rows(int64_t n, int dim, const double *pos, const double *h, int kern,
                            int64_t nrows, const int64_t *rows, int64_t *rowptr, int32_t *cols) {
   rowptr[0] = 0;
   for (int64_t r = 0; r < nrows; ++r) {
     int64_t i = rows[r], c = 0;
     for (int64_t j = 0; j < n; ++j)
-      if (is_neighbour(dim, pos, h, i, j)) {
+      if (is_neighbour(kern, dim, pos, h, i, j)) {
         if (cols) cols[rowptr[r] + c] = (int32_t)j;
         ++c;
       }
@@ -287,7 +332,7 @@ void orc_properties(const orc_params *p, int64_t n, const double *pos, const dou
         double xij[3] = {0.0, 0.0, 0.0};
         for (int d = 0; d < dim; ++d) xij[d] = pos[i * dim + d] - pos[j * dim + d];
         double r = sqrt(pair_r2(dim, pos + i * dim, pos + j * dim));
-        double Fij = pair_F(dim, r, h[i], h[j]);
+        double Fij = pair_F(p->kernel, dim, r, h[i], h[j]);
         double Vj = mass[j] / rho[j];
         /* grad_i W_ij = W'_ij x_ij / r = F_ij x_ij */
         for (int d = 0; d < dim; ++d) g[d] += Vj * (E[js] - E[i]) * Fij * xij[d];
@@ -361,7 +406,7 @@ int64_t orc_assemble(const orc_params *p, int64_t n, const double *pos, const do
     for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
       int64_t j = cols[k];
       double r = sqrt(pair_r2(dim, pos + i * dim, pos + j * dim));
-      double Fij = pair_F(dim, r, h[i], h[j]);
+      double Fij = pair_F(p->kernel, dim, r, h[i], h[j]);
       double Vj = mass[j] / rho[j];
       double w = -Vj * (D[i] + D[j]) * Fij;
       diag += w;
@@ -674,7 +719,7 @@ int orc_step(const orc_params *p, int64_t n, const double *pos, const double *ma
         int64_t j = cols[k];
         if (kind[j] == ORC_INTERIOR) continue;
         double r = sqrt(pair_r2(p->dim, pos + i * p->dim, pos + j * p->dim));
-        double w = -V[j] * (D[i] + D[j]) * pair_F(p->dim, r, h[i], h[j]);
+        double w = -V[j] * (D[i] + D[j]) * pair_F(p->kernel, p->dim, r, h[i], h[j]);
         double Ej = kind[j] == ORC_DIRICHLET ? Eg[j] : E_l[copy_of[j]];
         acc += w * (Ej - E_l[i]);
       }

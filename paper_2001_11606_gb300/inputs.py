@@ -81,19 +81,22 @@ class Particles:
 
 def make_lattice(dim: int, counts, dx: float, seed: int, jitter: float = 0.1,
                  faces=None, rho: float = 1.0, h_over_dx: float = 1.5,
-                 sigma0: float = 1.0) -> Particles:
+                 sigma0: float = 1.0, support: float = 2.0) -> Particles:
     """Jittered lattice plus ghost layers.
 
-    faces[d] = (lo, hi) with each entry 'dirichlet' or 'reflect'; default all
-    Dirichlet.  Where a ghost lies outside faces of both kinds, Dirichlet wins.
+    faces[d] = (lo, hi) with each entry 'dirichlet', 'reflect' or 'periodic';
+    default all Dirichlet.  Where a ghost lies outside faces of several kinds,
+    Dirichlet wins over the copies.  support: the kernel's support radius in
+    units of h (2 for the cubic B-spline, 1 for the Wendland C4 kernel), which
+    sets how many ghost layers are needed.
     """
     counts = tuple(int(c) for c in counts)
     assert len(counts) == dim and dim in (1, 2, 3)
     if faces is None:
         faces = [("dirichlet", "dirichlet")] * dim
     # ghost layer k (1-based, outside the face) can reach an interior point
-    # only if k - 2*jitter < 2h/dx; keep every layer that can.
-    g = max(GHOST_LAYERS, int(math.ceil(2.0 * h_over_dx + 2.0 * jitter)) - 1)
+    # only if k - 2*jitter < support*h/dx; keep every layer that can.
+    g = max(GHOST_LAYERS, int(math.ceil(support * h_over_dx + 2.0 * jitter)) - 1)
     ext = [c + 2 * g for c in counts]
     n_tot = int(np.prod(ext))
     # lexicographic enumeration of the extended lattice, x fastest

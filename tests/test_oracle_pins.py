@@ -56,6 +56,43 @@ def test_kernel_derivative_matches_finite_difference(dim):
     assert O.kernel(dim, 2 * h, h) == (0.0, 0.0)
 
 
+# Wendland C4 (Sec. 2.4, Eq. wendlandc4): the printed polynomial with k from the
+# normalisation requirement in each dimension, support h.
+@pytest.mark.parametrize("dim", [1, 2, 3])
+@pytest.mark.parametrize("h", [0.37, 1.0, 2.5])
+def test_wendland_integrates_to_one(dim, h):
+    from scipy.integrate import quad
+
+    surf = {1: lambda r: 2.0, 2: lambda r: 2.0 * math.pi * r, 3: lambda r: 4.0 * math.pi * r * r}[dim]
+    tot = quad(lambda r: O.kernel(dim, r, h, 1)[0] * surf(r), 0.0, h, epsabs=1e-15, epsrel=1e-13)[0]
+    assert abs(tot - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_wendland_shape_and_derivative(dim):
+    h = 0.8
+    for r in (0.05, 0.3, 0.5, 0.7, 0.79):
+        eps = 1e-6
+        fd = (O.kernel(dim, r + eps, h, 1)[0] - O.kernel(dim, r - eps, h, 1)[0]) / (2 * eps)
+        assert abs(O.kernel(dim, r, h, 1)[1] - fd) < 1e-7 * max(1.0, abs(fd))
+    # the printed polynomial at q = 0 is 1: W(0) = k / h^d
+    k = {1: 1.5, 2: 36.0 / (5.0 * math.pi), 3: 45.0 / (4.0 * math.pi)}[dim]
+    assert O.kernel(dim, 0.0, h, 1)[0] == pytest.approx(k / h**dim, rel=1e-15)
+    # C4 smoothness at the support edge: value and slope vanish at q = 1 and beyond
+    assert O.kernel(dim, h, h, 1) == (0.0, 0.0) and O.kernel(dim, 1.3 * h, h, 1) == (0.0, 0.0)
+    assert O.kernel(dim, 0.0, h, 1)[1] == 0.0
+
+
+@pytest.mark.parametrize("dim,count", [(2, 44), (3, 250)])
+def test_wendland_lattice_neighbour_counts(dim, count):
+    # support h = 4 dx (Sec. 3.1), strict inequality: integer offsets with |o|^2 < 16
+    assert count == sum(1 for o in np.ndindex(*(9,) * dim) if 0 < sum((np.array(o) - 4) ** 2) < 16)
+    P = I.make_lattice(dim, (9,) * dim, 1.0 / 64, seed=0, jitter=0.0, h_over_dx=4.0, support=1.0)
+    rp, cols = O.neighbors(P.pos, P.h, P.kind, kernel=1)
+    interior = np.flatnonzero(P.kind == I.INTERIOR)
+    assert np.all(rp[interior + 1] - rp[interior] == count)
+
+
 # --------------------------------------------------------------------------
 # Neighbours
 # --------------------------------------------------------------------------
@@ -236,6 +273,41 @@ def test_operator_second_order_consistency():
                      + np.dot(aval[arow[i]:arow[i + 1]], E[acol[arow[i]:arow[i + 1]]]) - gb[i])
         exact = D * 2.0 * np.pi**2 * E[m]
         errs.append(np.max(np.abs(LE - exact)))
+    assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.3
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_wendland_operator_reproduces_laplacian_of_quadratic(dim):
+    # with the paper's kernel and smoothing length (Wendland C4, h = 4 dx, Sec. 3.1)
+    # the lattice sum of the Brookshaw second moment is 0.9995 (2-D) and 0.9994 (3-D)
+    # of its integral (the cubic B-spline's at h = 1.5 dx: 1.0067 and 1.0101), so
+    # -div(D grad |x|^2) = -2 d D to within that lattice error
+    n = 12 if dim == 2 else 9
+    P = I.make_lattice(dim, (n,) * dim, 1.0 / n, seed=0, jitter=0.0, h_over_dx=4.0, support=1.0)
+    E = np.sum(P.pos**2, axis=1)
+    pb, pr, arow, acol, aval, adiag, gb = _operator_rows(P, dict(dim=dim, kernel=1), E)
+    D = pr["D"][0]
+    out = []
+    for i in np.flatnonzero(P.kind == 0):
+        s = (adiag[i] - 1.0 - pr["sigma"][i] * pr["f"][i]) * E[i]
+        s += np.dot(aval[arow[i]:arow[i + 1]], E[acol[arow[i]:arow[i + 1]]]) - gb[i]
+        out.append(s)
+    assert np.allclose(out, -2.0 * dim * D, rtol=1e-3)
+
+
+def test_wendland_operator_second_order_consistency():
+    # the same operator on sin(pi x) sin(pi y): max error falls ~4x per halving of dx
+    errs = []
+    for n in (12, 24, 48):
+        P = I.make_lattice(2, (n, n), 1.0 / n, seed=0, jitter=0.0, h_over_dx=4.0, support=1.0)
+        E = np.sin(np.pi * P.pos[:, 0]) * np.sin(np.pi * P.pos[:, 1])
+        pb, pr, arow, acol, aval, adiag, gb = _operator_rows(P, dict(dim=2, kernel=1), E)
+        m = np.flatnonzero(P.kind == 0)
+        LE = np.empty(len(m))
+        for k, i in enumerate(m):
+            LE[k] = ((adiag[i] - 1.0 - pr["sigma"][i] * pr["f"][i]) * E[i]
+                     + np.dot(aval[arow[i]:arow[i + 1]], E[acol[arow[i]:arow[i + 1]]]) - gb[i])
+        errs.append(np.max(np.abs(LE - (1.0 / 3.0) * 2.0 * np.pi**2 * E[m])))
     assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.3
 
 
