@@ -36,6 +36,7 @@ class Params(C.Structure):
         ("tol_inner_e", C.c_double), ("tol_krylov", C.c_double),
         ("max_outer", C.c_int32), ("max_inner_e", C.c_int32), ("max_krylov", C.c_int32),
         ("kernel", C.c_int32),
+        ("sigma_s", C.c_double),
     ]
 
 
@@ -111,7 +112,8 @@ def make_params(**kw) -> Params:
     p = Params()
     defaults = dict(dim=3, a=1.0, c=1.0, cv=1.0, limiter=0, larsen_k=2.0, opacity_exp=0.0,
                     T_floor=0.0, tol_outer_e=1e-8, tol_outer_E=1e-8, tol_inner_e=1e-13,
-                    tol_krylov=1e-12, max_outer=50, max_inner_e=50, max_krylov=5000, kernel=0)
+                    tol_krylov=1e-12, max_outer=50, max_inner_e=50, max_krylov=5000, kernel=0,
+                    sigma_s=0.0)
     defaults.update(kw)
     for k, v in defaults.items():
         setattr(p, k, v)

@@ -58,6 +58,7 @@ typedef struct {
   double tol_outer_e, tol_outer_E, tol_inner_e, tol_krylov;
   int32_t max_outer, max_inner_e, max_krylov;
   int32_t kernel;           /* 0: M4 cubic B-spline (support 2h); 1: Wendland C4 (support h) */
+  double sigma_s;           /* scattering opacity (constant); sigma_t = sigma_a + sigma_s */
 } orc_params;
 
 enum { ORC_INTERIOR = 0, ORC_DIRICHLET = 1, ORC_COPY = 2 };
@@ -304,11 +305,12 @@ double orc_limiter(const orc_params *p, double R) { return limiter_lambda(p, R);
 /*
  * For every particle (caller order), from the state (e, E) at the start of
  * the step:
- *   T = e / c_v;  sigma = sigma0 T^p  (sigma_a = sigma_t);
- *   f = 1 / (1 + c sigma dt 4 a T^3 / (rho c_v))             (Fleck factor)
+ *   T = e / c_v;  sigma = sigma_a = sigma0 T^p;  sigma_t = sigma_a + sigma_s
+ *   f = 1 / (1 + c sigma_a dt 4 a T^3 / (rho c_v))           (Fleck factor)
  *   grad E_i = sum_j V_j (E_j - E_i) grad_i W_ij              (SPH derivative)
- *   R = |grad E| / (sigma E);  lambda = limiter(R);  D = c lambda / sigma.
- * R is only formed when a limiter is active.
+ *   R = |grad E| / (sigma_t E);  lambda = limiter(R);  D = c lambda / sigma_t
+ * (the total opacity sets the diffusion, the absorption opacity the coupling:
+ * Sec. 2.1).  R is only formed when a limiter is active.
  */
 void orc_properties(const orc_params *p, int64_t n, const double *pos, const double *mass,
                     const double *rho, const double *h, const double *sigma0,
@@ -339,7 +341,7 @@ void orc_properties(const orc_params *p, int64_t n, const double *pos, const dou
       }
       double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
       double Es = E[i] > 1e-300 ? E[i] : 1e-300;
-      double sigR = sigma0[i] * pow(Ts, p->opacity_exp);
+      double sigR = sigma0[i] * pow(Ts, p->opacity_exp) + p->sigma_s;
       Ri = gn / (sigR * Es);
     }
     double lam = limiter_lambda(p, Ri);
@@ -348,7 +350,7 @@ void orc_properties(const orc_params *p, int64_t n, const double *pos, const dou
     f[i] = fi;
     R[i] = Ri;
     lambda[i] = lam;
-    D[i] = p->c * lam / sig;
+    D[i] = p->c * lam / (sig + p->sigma_s);
   }
   for (int64_t i = 0; i < n; ++i) {
     if (kind[i] != ORC_COPY) continue;

@@ -150,6 +150,19 @@ def test_fleck_factor_closed_form():
     assert np.allclose(pr["sigma"], 7.0 / e**3, rtol=1e-14)
 
 
+def test_scattering_enters_diffusion_not_coupling():
+    # sigma_t = sigma_a + sigma_s (Sec. 2.1): with lambda = 1/3 the diffusion
+    # coefficient is c / (3 sigma_t), while the Fleck factor keeps sigma_a.  The
+    # paper's manufactured problem has sigma_a = 0.05, sigma_s = 0.95 (Sec. 4.3).
+    P = I.make_lattice(2, (5, 5), 0.2, seed=2)
+    P.sigma0[:] = 0.05
+    pb = O.Problem(P, dict(dim=2, c=3.0, sigma_s=0.95))
+    e = np.full(P.n, 1.3)
+    pr = pb.properties(e, e**4, dt=1e-2)
+    assert np.allclose(pr["D"], 3.0 / (3.0 * 1.0), rtol=1e-15, atol=0)
+    assert np.allclose(pr["f"], 1.0 / (1.0 + 3.0 * 0.05 * 1e-2 * 4.0 * 1.3**3), rtol=1e-15)
+
+
 def test_limiters():
     g = golden()
     P = I.make_lattice(2, (4, 4), 0.25, seed=1)
