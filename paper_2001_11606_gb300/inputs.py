@@ -113,12 +113,15 @@ def make_lattice(dim: int, counts, dx: float, seed: int, jitter: float = 0.1,
     copy_of = np.full(n_tot, -1, dtype=np.int64)
     dir_out = np.zeros(n_tot, dtype=bool)
     ref_out = np.zeros(n_tot, dtype=bool)
+    periodic = [faces[d][0] == "periodic" for d in range(dim)]
     for d in range(dim):
         lo, hi = faces[d]
+        if (lo == "periodic") != (hi == "periodic"):
+            raise ValueError("periodic faces come in pairs")
         for side, mask in ((lo, outside_lo[:, d]), (hi, outside_hi[:, d])):
             if side == "dirichlet":
                 dir_out |= mask
-            elif side == "reflect":
+            elif side in ("reflect", "periodic"):
                 ref_out |= mask
             else:
                 raise ValueError(side)
@@ -126,14 +129,19 @@ def make_lattice(dim: int, counts, dx: float, seed: int, jitter: float = 0.1,
     is_copy = ref_out & ~dir_out
     kind[is_copy] = COPY
     if np.any(is_copy):
+        # source lattice point: mirrored across a reflecting face, wrapped around
+        # a periodic one
         src = idx[is_copy].copy()
         cpos = pos[is_copy].copy()
         for d in range(dim):
-            L = counts[d] * dx
             lo_m = src[:, d] < 0
             hi_m = src[:, d] >= counts[d]
-            src[lo_m, d] = -1 - src[lo_m, d]
-            src[hi_m, d] = 2 * counts[d] - 1 - src[hi_m, d]
+            if periodic[d]:
+                src[lo_m, d] += counts[d]
+                src[hi_m, d] -= counts[d]
+            else:
+                src[lo_m, d] = -1 - src[lo_m, d]
+                src[hi_m, d] = 2 * counts[d] - 1 - src[hi_m, d]
         # caller index of the source point
         strides = np.cumprod([1] + ext[:-1])
         lin = ((src + g) * np.array(strides)).sum(axis=1)
@@ -144,8 +152,12 @@ def make_lattice(dim: int, counts, dx: float, seed: int, jitter: float = 0.1,
             lo_m = idx[is_copy][:, d] < 0
             hi_m = idx[is_copy][:, d] >= counts[d]
             cpos[:, d] = spos[:, d]
-            cpos[lo_m, d] = -spos[lo_m, d]
-            cpos[hi_m, d] = 2.0 * L - spos[hi_m, d]
+            if periodic[d]:  # the image of the source one period away
+                cpos[lo_m, d] = spos[lo_m, d] - L
+                cpos[hi_m, d] = spos[hi_m, d] + L
+            else:  # the mirror image of the source
+                cpos[lo_m, d] = -spos[lo_m, d]
+                cpos[hi_m, d] = 2.0 * L - spos[hi_m, d]
         pos[is_copy] = cpos
     vol = dx ** dim
     rho_a = np.full(n_tot, rho, dtype=np.float64)
@@ -317,6 +329,100 @@ class SourceSeries:
 
 
 # ---------------------------------------------------------------------------
+# The paper's own manufactured problem (Sec. 4.3, Eq. manufactured-solutions):
+# travelling cosines in cgs units on one period [0, d_m]^dim,
+#   e = e0 [1.2 + prod_a cos(2 pi (x_a - v t) / d_m)],
+#   E = E0 [1.2 + prod_a cos(2 pi (x_a + v t) / d_m - omega)],
+# e0 = 1e13 erg/g, E0 = 7 a (e0 / c_v)^4, v = 5e9 cm/s, d_m = 5 cm,
+# omega = 1/16, sigma_a = 0.05 / cm, sigma_s = 0.95 / cm, the ideal-gas relation
+# T = e / c_v with c_v = k_B / ((gamma - 1) mu m_p), gamma = 5/3, mu = 1, and
+# rho = 1 g/cm^3.  Sources from inserting it into the material-energy equation
+# and the flux-limited diffusion equation (Sec. 2.1):
+#   Q_e = rho de/dt - c sigma_a (E - a T^4)
+#   Q_E = dE/dt - div(D grad E) + c sigma_a (E - a T^4),
+#   D = c lambda(R) / sigma_t, R = |grad E| / (sigma_t E), sigma_t = sigma_a + sigma_s.
+# ---------------------------------------------------------------------------
+CGS_A = 4.0 * 5.670374419e-5 / 2.99792458e10  # radiation constant a = 4 sigma_SB / c
+CGS_C = 2.99792458e10                           # speed of light, cm/s
+CGS_CV = 1.380649e-16 / ((5.0 / 3.0 - 1.0) * 1.67262192369e-24)  # k_B / ((gamma-1) m_p)
+
+
+@dataclass
+class TravellingCosine:
+    dim: int
+    e0: float = 1e13
+    v: float = 5e9
+    dm: float = 5.0
+    omega: float = 1.0 / 16.0
+    rho: float = 1.0
+    sigma_a: float = 0.05
+    sigma_s: float = 0.95
+    a: float = CGS_A
+    c: float = CGS_C
+    cv: float = CGS_CV
+    limiter: int = 2
+    larsen_k: float = 2.0
+
+    @property
+    def E0(self) -> float:
+        return 7.0 * self.a * (self.e0 / self.cv) ** 4
+
+    def _phases(self, x, t):
+        k = 2.0 * np.pi / self.dm
+        ue = k * (x - self.v * t)               # material wave, moving with +v
+        uE = k * (x + self.v * t) - self.omega  # radiation wave, moving with -v
+        return k, ue, uE
+
+    def fields(self, x, t):
+        k, ue, uE = self._phases(x, t)
+        e = self.e0 * (1.2 + np.prod(np.cos(ue), axis=1))
+        E = self.E0 * (1.2 + np.prod(np.cos(uE), axis=1))
+        return e, E
+
+    def sources(self, x, t):
+        d = self.dim
+        k, ue, uE = self._phases(x, t)
+        ce, se = np.cos(ue), np.sin(ue)
+        cE, sE = np.cos(uE), np.sin(uE)
+
+        def others(c, a):
+            return np.prod(np.delete(c, a, axis=1), axis=1) if d > 1 else 1.0
+
+        e = self.e0 * (1.2 + np.prod(ce, axis=1))
+        E = self.E0 * (1.2 + np.prod(cE, axis=1))
+        # time derivatives: d/dt cos(k (x - v t)) = k v sin(.), d/dt cos(k (x + v t) - w) = -k v sin(.)
+        dedt = self.e0 * sum(k * self.v * se[:, a] * others(ce, a) for a in range(d))
+        dEdt = self.E0 * sum(-k * self.v * sE[:, a] * others(cE, a) for a in range(d))
+        # gradient and Hessian of E
+        g = np.stack([-self.E0 * k * sE[:, a] * others(cE, a) for a in range(d)], axis=1)
+        H = np.empty((x.shape[0], d, d))
+        for a in range(d):
+            for b in range(d):
+                if a == b:
+                    H[:, a, a] = -self.E0 * k * k * np.prod(cE, axis=1)
+                else:
+                    rest = [m for m in range(d) if m not in (a, b)]
+                    o = np.prod(cE[:, rest], axis=1) if rest else 1.0
+                    H[:, a, b] = self.E0 * k * k * sE[:, a] * sE[:, b] * o
+        st = self.sigma_a + self.sigma_s
+        gn = np.sqrt(np.sum(g * g, axis=1))
+        R = gn / (st * E)
+        lam, dlam = _limiter_value_and_slope(R, self.limiter, self.larsen_k)
+        D = self.c * lam / st
+        Hg = np.einsum("nab,nb->na", H, g)
+        safe = np.where(gn > 0.0, gn, 1.0)
+        dgn = np.where(gn[:, None] > 0.0, Hg / safe[:, None], 0.0)
+        dR = (dgn / E[:, None] - (gn / (E * E))[:, None] * g) / st
+        dD = (self.c / st) * dlam[:, None] * dR
+        divflux = np.sum(dD * g, axis=1) + D * np.trace(H, axis1=1, axis2=2)
+        T = e / self.cv
+        coupling = self.c * self.sigma_a * (E - self.a * T**4)
+        Qe = self.rho * dedt - coupling
+        QE = dEdt - divflux + coupling
+        return Qe, QE
+
+
+# ---------------------------------------------------------------------------
 # Named workloads (sizes and physics of the verification problems)
 # ---------------------------------------------------------------------------
 
@@ -328,7 +434,7 @@ class Workload:
     params: dict
     dt: float
     steps: int
-    mms: Manufactured | None = None
+    mms: "Manufactured | TravellingCosine | None" = None
     e0: np.ndarray | None = None
     E0: np.ndarray | None = None
     _series: SourceSeries | None = field(default=None, repr=False)
@@ -344,9 +450,13 @@ class Workload:
             ge = self.e0.copy()
             gE = self.E0.copy()
             return z, z.copy(), ge, gE
+        t = n * self.dt
+        if not isinstance(self.mms, Manufactured):
+            Qe, QE = self.mms.sources(P.pos, t)
+            ge, gE = self.mms.fields(P.pos, t)
+            return Qe, QE, ge, gE
         if self._series is None:
             self._series = self.mms.series(P.pos)
-        t = n * self.dt
         Qe, QE = self._series.sources(t)
         ge, gE = self._series.fields(t)
         return Qe, QE, ge, gE
@@ -385,6 +495,27 @@ def mms_3d_lp(n: int = 64, seed: int = 2, jitter: float = 0.1, steps: int = 100,
 def mms_3d(n: int = 128, seed: int = 3, jitter: float = 0.1, steps: int = 50, dt: float = 1e-3):
     """3-D manufactured problem: constant opacity, no limiter."""
     return _mms_workload(f"mms3d-{n}^3", 3, n, seed, 0.0, 0, dt, steps, jitter=jitter)
+
+
+def mms_cgs(dim: int, n: int, seed: int = 6, steps: int = 1000, dt: float | None = None,
+            jitter: float = 0.1):
+    """The paper's manufactured problem (Sec. 4.3) on n^dim points of one period,
+    periodic copy ghosts, the Wendland C4 kernel with h = 4 dx (Sec. 3.1), the
+    Larsen limiter with k = 2, tolerances of the manufactured-problem row of the
+    tolerance table, dt = t_end / 1000 (t_end = d_m / v = 1e-9 s) unless given.
+    The paper's points are not jittered; jitter = 0 gives its lattice."""
+    m = TravellingCosine(dim=dim)
+    dx = m.dm / n
+    P = make_lattice(dim, (n,) * dim, dx, seed, jitter=jitter, h_over_dx=4.0, support=1.0,
+                     faces=[("periodic", "periodic")] * dim, rho=m.rho, sigma0=m.sigma_a)
+    e0, E0 = m.fields(P.pos, 0.0)
+    params = dict(dim=dim, kernel=1, a=m.a, c=m.c, cv=m.cv, limiter=m.limiter,
+                  larsen_k=m.larsen_k, opacity_exp=0.0, sigma_s=m.sigma_s, T_floor=0.0,
+                  tol_outer_e=1e-8, tol_outer_E=1e-8, tol_inner_e=1e-12, tol_krylov=1e-12,
+                  max_outer=50, max_inner_e=50, max_krylov=2000)
+    t_end = m.dm / m.v
+    return Workload(name=f"mms-cgs{dim}d-{n}^{dim}", particles=P, params=params,
+                    dt=dt if dt is not None else t_end / 1000.0, steps=steps, mms=m, e0=e0, E0=E0)
 
 
 def sphere_3d(n: int = 256, seed: int = 5, steps: int = 20, dt: float = 1e-4):

@@ -86,3 +86,51 @@ def test_source_series_equals_sources():
             e, E = m.fields(x, t)
             e2, E2 = ser.fields(t)
             assert np.array_equal(e, e2) and np.array_equal(E, E2)
+
+
+def test_travelling_cosine_sources_match_finite_differences():
+    # the paper's cgs manufactured problem (Sec. 4.3): Q_e = rho de/dt - c sigma_a (E - aT^4),
+    # Q_E = dE/dt - div(D grad E) + c sigma_a (E - aT^4), D from the Larsen limiter with
+    # sigma_t = sigma_a + sigma_s; checked against central differences of the fields
+    rng = np.random.default_rng(2)
+    for dim in (1, 2, 3):
+        m = I.TravellingCosine(dim=dim)
+        x = rng.uniform(0.0, m.dm, size=(30, dim))
+        t = 3e-10
+        Qe, QE = m.sources(x, t)
+        ht, hx = 1e-15, 1e-4
+        e_p, E_p = m.fields(x, t + ht)
+        e_m, E_m = m.fields(x, t - ht)
+        e, E = m.fields(x, t)
+        st = m.sigma_a + m.sigma_s
+
+        def D(y):
+            Ey = m.fields(y, t)[1]
+            g = np.stack([(m.fields(y + hx * np.eye(dim)[k], t)[1]
+                           - m.fields(y - hx * np.eye(dim)[k], t)[1]) / (2 * hx)
+                          for k in range(dim)], axis=1)
+            R = np.sqrt(np.sum(g * g, axis=1)) / (st * Ey)
+            return m.c * I._limiter_value_and_slope(R, m.limiter, m.larsen_k)[0] / st
+
+        div = np.zeros(len(x))
+        for k in range(dim):
+            ek = np.eye(dim)[k] * hx
+            fp = D(x + ek / 2) * (m.fields(x + ek, t)[1] - E) / hx
+            fm = D(x - ek / 2) * (E - m.fields(x - ek, t)[1]) / hx
+            div += (fp - fm) / hx
+        coup = m.c * m.sigma_a * (E - m.a * (e / m.cv) ** 4)
+        Qe_fd = m.rho * (e_p - e_m) / (2 * ht) - coup
+        QE_fd = (E_p - E_m) / (2 * ht) - div + coup
+        assert np.allclose(Qe, Qe_fd, rtol=1e-5, atol=1e-6 * np.max(np.abs(Qe)))
+        assert np.allclose(QE, QE_fd, rtol=1e-4, atol=1e-4 * np.max(np.abs(QE)))
+
+
+def test_periodic_ghosts_are_translated_copies():
+    w = I.mms_cgs(2, 12, steps=1)
+    P = w.particles
+    c = np.flatnonzero(P.kind == I.COPY)
+    assert len(c) > 0 and np.all(P.kind == np.where(P.kind == I.COPY, I.COPY, I.INTERIOR))
+    assert np.all(P.kind[P.copy_of[c]] == I.INTERIOR)
+    off = (P.pos[c] - P.pos[P.copy_of[c]]) / 5.0
+    assert np.allclose(off, np.round(off), atol=1e-12)
+    assert np.all(np.abs(np.round(off)).sum(axis=1) >= 1)

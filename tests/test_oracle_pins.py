@@ -578,3 +578,46 @@ def test_iteration_counts_like_the_paper():
     for s in st:
         assert 2 <= s.outer_iters <= 3
         assert s.krylov_per_outer[s.outer_iters - 1] <= 3
+
+
+# --------------------------------------------------------------------------
+# The paper's manufactured problem (Sec. 4.3): travelling cosines in cgs units,
+# periodic, Wendland C4 with h = 4 dx, Larsen limiter (k = 2), sigma_a = 0.05,
+# sigma_s = 0.95.  One-dimensional runs on the paper's unjittered points.
+# --------------------------------------------------------------------------
+def _cgs_l1(n, dt, steps):
+    w = I.mms_cgs(1, n, steps=steps, dt=dt, jitter=0.0)
+    e, E, _ = O.run(w)
+    m = w.particles.kind == 0
+    ea, Ea = w.mms.fields(w.particles.pos, steps * dt)
+    return (np.sum(np.abs(e[m] - ea[m])) / np.sum(ea[m]),
+            np.sum(np.abs(E[m] - Ea[m])) / np.sum(Ea[m]))  # Eq. manufactured-error
+
+
+def test_cgs_manufactured_second_order_in_space():
+    # the radiation energy's L1 error falls at second order with the point spacing
+    errs = [_cgs_l1(n, 1e-13, 20)[1] for n in (32, 64, 128)]
+    assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.3, errs
+
+
+def test_cgs_manufactured_first_order_in_time():
+    # the material energy's error (no spatial coupling of its own) is set by the
+    # time step: halving dt at a fixed end time halves it
+    a = _cgs_l1(64, 1e-13, 20)[0]
+    b = _cgs_l1(64, 5e-14, 40)[0]
+    c = _cgs_l1(64, 2.5e-14, 80)[0]
+    assert 1.8 < a / b < 2.2 and 1.8 < b / c < 2.2, (a, b, c)
+
+
+def test_cgs_manufactured_cycle_conserves_energy():
+    # over one full period (t_end = d_m / v, dt = t_end / 1000) the sources integrate
+    # to ~0 and the total energy changes only by them; the paper reports relative
+    # start-to-end differences of 6.35e-14 .. 4.53e-12 (Sec. 4.3)
+    w = I.mms_cgs(1, 64, steps=1000, jitter=0.0)
+    pb = O.Problem(w.particles, w.params)
+    e, E, st = O.run(w, problem=pb)
+    t0, t1 = pb.totals(w.e0, w.E0).sum(), pb.totals(e, E).sum()
+    src = sum(s.source_energy for s in st)
+    assert abs(t1 - t0 - src) <= 1e-13 * t0
+    assert abs(src) <= 1e-13 * t0
+    assert all(s.outer_iters <= 3 for s in st)
