@@ -52,11 +52,16 @@ enum { SPH_RT_INTERIOR = 0, SPH_RT_DIRICHLET = 1, SPH_RT_COPY = 2 };
 enum { SPH_RT_LIMITER_NONE = 0, SPH_RT_LIMITER_LEVERMORE = 1, SPH_RT_LIMITER_LARSEN = 2 };
 enum { SPH_RT_PRECOND_JACOBI = 0, SPH_RT_PRECOND_CHEBYSHEV = 1, SPH_RT_PRECOND_AMG = 2 };
 enum { SPH_RT_FP64 = 0, SPH_RT_MIXED = 1 };
+/* SPH kernel: the M4 cubic B-spline with support 2h, or the paper's Wendland C4
+ * kernel with support h (Sec. 2.4, Eq. wendlandc4; the printed polynomial in
+ * every dimension, normalised to a unit volume integral, Sec. 2.3). */
+enum { SPH_RT_M4_SPLINE = 0, SPH_RT_WENDLAND_C4 = 1 };
 
 /*
  * Problem constants and solver controls.
- * Physics (Sec. 2.1-2.2): B = a T^4, e = c_v T, sigma_a = sigma_t = sigma0 T^p,
- * D = c lambda(R) / sigma_t with R = |grad E| / (sigma_t E) and lambda from
+ * Physics (Sec. 2.1-2.2): B = a T^4, e = c_v T, sigma_a = sigma0 T^p,
+ * sigma_t = sigma_a + sigma_s, D = c lambda(R) / sigma_t with
+ * R = |grad E| / (sigma_t E) and lambda from
  *   none      lambda = 1/3                      (Fick's law, Eq. diffusion with 1/3)
  *   Levermore lambda = (2+R)/(6+3R+R^2)          (Sec. 2.1, Levermore limiter)
  *   Larsen    lambda = (3^k + R^k)^(-1/k)        (Sec. 2.1, Larsen limiter)
@@ -67,12 +72,15 @@ enum { SPH_RT_FP64 = 0, SPH_RT_MIXED = 1 };
  */
 typedef struct {
   int32_t dim;          /* 2 or 3 (1 is accepted too) */
+  int32_t kernel;       /* SPH_RT_M4_SPLINE (default) or SPH_RT_WENDLAND_C4 */
   double a, c, cv;      /* radiation constant (>= 0; 0: no emission), speed of light, specific
                            heat (both > 0) */
   int32_t limiter;      /* SPH_RT_LIMITER_* */
   double larsen_k;      /* k of the Larsen limiter (> 0) */
   double opacity_exp;   /* p in sigma = sigma0 T^p */
   double T_floor;       /* T inside sigma and R is max(T, T_floor); 0 = off */
+  double sigma_s;       /* scattering opacity (constant, >= 0): sigma_t = sigma_a + sigma_s
+                           sets R and D; sigma_a alone the emission and absorption */
   double tol_outer_e, tol_outer_E, tol_inner_e, tol_krylov;
   int32_t max_outer, max_inner_e, max_krylov;
   int32_t precond;      /* SPH_RT_PRECOND_* */
@@ -164,7 +172,8 @@ sph_rt_status sph_rt_create(const sph_rt_config *cfg, sph_rt **out);
 /*
  * Set the particles (positions, masses, densities, smoothing lengths, opacity
  * prefactors, kinds) and the initial state; build the Morton-sorted cell list,
- * the neighbour lists (j != i with r^2 < (2 max(h_i,h_j))^2, Sec. 3.1), the
+ * the neighbour lists (j != i with r^2 < (s max(h_i,h_j))^2, s = 2 for the
+ * cubic B-spline and 1 for the Wendland C4 kernel, Sec. 3.1), the
  * fixed geometric weights and the operator's sparsity.  Replaces any previous
  * particle set.
  *   kind[i]    SPH_RT_INTERIOR, SPH_RT_DIRICHLET (ghost with prescribed values)

@@ -1,16 +1,17 @@
 // neighbors.cu -- Morton-sorted cell list, neighbour search and operator
 // sparsity (rows a1-a2 of the hot path).
 //
-// Connectivity is the set of j != i with r_ij^2 < (2 max(h_i, h_j))^2 for every
-// interior particle i (support of the cubic B-spline; connectivity in the
-// sense of Sec. 1 and Sec. 3.1 of the paper).  Distances are formed with
+// Connectivity is the set of j != i with r_ij^2 < (s max(h_i, h_j))^2 for every
+// interior particle i, s the kernel's support in units of h (2 for the cubic
+// B-spline, 1 for the paper's Wendland C4 kernel; connectivity in the sense of
+// Sec. 1 and Sec. 3.1 of the paper).  Distances are formed with
 // explicit round-to-nearest double operations (no fused multiply-add) in the
 // order dx*dx + dy*dy + dz*dz, so the neighbour sets are bit-identical to a
 // host evaluation of the same expression.
 //
 // Layout: particles are counting-sorted by key = (ghost flag, Morton code of
 // the cell) with ties broken by caller index, giving "slots" with interior
-// particles first.  Cells have edge >= 2 max h, so all neighbours of a
+// particles first.  Cells have edge >= s max h, so all neighbours of a
 // particle lie in the 3^d cells around its own.
 #include <cuda_runtime.h>
 
@@ -181,10 +182,12 @@ __host__ __device__ inline uint64_t spread2(uint64_t v) {  // 32 bits -> every 2
 struct Grid {
   double lo[3];
   double inv_cell;
-  double cell;  // cell edge (>= 2 max h)
+  double cell;     // cell edge (>= support max h)
+  double support;  // kernel support in units of h: 2 (cubic B-spline) or 1 (Wendland C4)
   int nc[3];
   int dim;
   int ghost_shift;  // key bit that marks ghosts
+  int kernel;       // SPH_RT_M4_SPLINE or SPH_RT_WENDLAND_C4
 };
 
 __device__ __forceinline__ int cell_coord(double x, double lo, double inv, int nc) {
@@ -316,11 +319,29 @@ __device__ __forceinline__ double spline_dw(double q) {
   return 0.0;
 }
 
-// Per-particle kernel coefficients: 1/h and sigma_d / h^(d+1), so that
-// dW/dr(r, h) = sigma_d / h^(d+1) * w'(r / h) needs no division per pair.
-__global__ void kernel_coef_kernel(int64_t n, int dim, const double *h, double *ih, double *cw) {
+// Shape of dW/dq of the Wendland C4 kernel of Sec. 2.4 (Eq. wendlandc4): the
+// printed polynomial (1 - q)^5 (8 q^2 + 5 q + 1) on q <= 1 has the derivative
+// -14 q (1 + 4 q) (1 - q)^4.
+__device__ __forceinline__ double wendland_dw(double q) {
+  if (q <= 1.0) {
+    const double t = 1.0 - q, t2 = t * t;
+    return -14.0 * q * (1.0 + 4.0 * q) * (t2 * t2);
+  }
+  return 0.0;
+}
+
+// Per-particle kernel coefficients: 1/h and k_d / h^(d+1), so that
+// dW/dr(r, h) = k_d / h^(d+1) * w'(r / h) needs no division per pair.  k_d makes
+// the kernel's volume integral one (Sec. 2.3): for the cubic B-spline 2/3,
+// 10/(7 pi), 1/pi; for the Wendland C4 polynomial as printed in every dimension
+// 3/2, 36/(5 pi), 45/(4 pi).
+__global__ void kernel_coef_kernel(int64_t n, int dim, int kern, const double *h, double *ih,
+                                   double *cw) {
   const double pi = 3.141592653589793;
-  const double sd = dim == 3 ? 1.0 / pi : (dim == 2 ? 10.0 / (7.0 * pi) : 2.0 / 3.0);
+  const double sd =
+      kern == SPH_RT_WENDLAND_C4
+          ? (dim == 3 ? 45.0 / (4.0 * pi) : (dim == 2 ? 36.0 / (5.0 * pi) : 1.5))
+          : (dim == 3 ? 1.0 / pi : (dim == 2 ? 10.0 / (7.0 * pi) : 2.0 / 3.0));
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double inv = 1.0 / h[i];
@@ -364,7 +385,7 @@ __global__ void rel_kernel(Grid g, const double *px, const double *py, const dou
     const int cx = cell_coord(x, g.lo[0], g.inv_cell, g.nc[0]);
     const int cy = cell_coord(y, g.lo[1], g.inv_cell, g.nc[1]);
     const int cz = cell_coord(z, g.lo[2], g.inv_cell, g.nc[2]);
-    const double cut = 2.0 * h[j];
+    const double cut = g.support * h[j];
     float4 r;
     r.x = (float)(x - (g.lo[0] + (double)cx * g.cell));
     r.y = g.dim > 1 ? (float)(y - (g.lo[1] + (double)cy * g.cell)) : 0.0f;
@@ -402,14 +423,16 @@ __device__ __forceinline__ uint64_t warp_sort_u64(uint64_t v) {
 }
 
 // Pair weight F_ij = W'_ij / r (two-h average) of neighbour j of i, in FP64.
-__device__ __forceinline__ double pair_weight(double xi, double yi, double zi, double ihi,
-                                              double cwi, int64_t j, const double *px,
-                                              const double *py, const double *pz,
-                                              const double *ih, const double *cw) {
+__device__ __forceinline__ double pair_weight(int kern, double xi, double yi, double zi,
+                                              double ihi, double cwi, int64_t j,
+                                              const double *px, const double *py,
+                                              const double *pz, const double *ih,
+                                              const double *cw) {
   const double r2 = exact_r2(xi, yi, zi, px[j], py[j], pz[j]);
   const double ir = rsqrt_fp64(r2), r = r2 * ir;
-  const double dwi = cwi * spline_dw(r * ihi);
-  const double dwj = cw[j] * spline_dw(r * ih[j]);
+  const double qi = r * ihi, qj = r * ih[j];
+  const double dwi = cwi * (kern == SPH_RT_WENDLAND_C4 ? wendland_dw(qi) : spline_dw(qi));
+  const double dwj = cw[j] * (kern == SPH_RT_WENDLAND_C4 ? wendland_dw(qj) : spline_dw(qj));
   return 0.5 * (dwi + dwj) * ir;
 }
 
@@ -486,7 +509,7 @@ __global__ void neighbor_kernel(Grid g, const double *px, const double *py, cons
             if (r2f < c2f - band) {
               hit = true;
             } else if (!(r2f > c2f + band)) {  // within the band: the exact test
-              const double cut = 2.0 * fmax(hi, h[j]);
+              const double cut = g.support * fmax(hi, h[j]);
               hit = exact_r2(xi, yi, zi, px[j], py[j], pz[j]) < __dmul_rn(cut, cut);
             }
           }
@@ -499,7 +522,7 @@ __global__ void neighbor_kernel(Grid g, const double *px, const double *py, cons
             if (pending >= 32) {  // 32 weights with every lane active
               const int32_t jj = hb[lane];
               cols[out + done + lane] = jj;
-              F[out + done + lane] = pair_weight(xi, yi, zi, ihi, cwi, jj, px, py, pz, ih, cw);
+              F[out + done + lane] = pair_weight(g.kernel, xi, yi, zi, ihi, cwi, jj, px, py, pz, ih, cw);
               const int rest = pending - 32;
               const int32_t carry = lane < rest ? hb[32 + lane] : 0;
               __syncwarp();
@@ -516,7 +539,7 @@ __global__ void neighbor_kernel(Grid g, const double *px, const double *py, cons
       if (lane < pending) {
         const int32_t jj = hb[lane];
         cols[out + done + lane] = jj;
-        F[out + done + lane] = pair_weight(xi, yi, zi, ihi, cwi, jj, px, py, pz, ih, cw);
+        F[out + done + lane] = pair_weight(g.kernel, xi, yi, zi, ihi, cwi, jj, px, py, pz, ih, cw);
       }
       __syncwarp();
     }
@@ -652,7 +675,9 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
 
   Grid g;
   g.dim = dim;
-  double cell = 2.0 * hb[6] * (1.0 + 1e-9);
+  g.kernel = s->cfg.kernel;
+  g.support = s->cfg.kernel == SPH_RT_WENDLAND_C4 ? 1.0 : 2.0;
+  double cell = g.support * hb[6] * (1.0 + 1e-9);
   g.cell = cell;
   g.inv_cell = 1.0 / cell;
   int maxnc = 1;
@@ -767,7 +792,7 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   if (!s->nbr_col || !s->nbr_F) return SPH_RT_ENOMEM;
   double *ih = dalloc<double>(s, n), *cw = dalloc<double>(s, n);
   if (!ih || !cw) return SPH_RT_ENOMEM;
-  kernel_coef_kernel<<<grid1(s, n), kBlock, 0, st>>>(n, dim, s->h, ih, cw);
+  kernel_coef_kernel<<<grid1(s, n), kBlock, 0, st>>>(n, dim, s->cfg.kernel, s->h, ih, cw);
   SPH_LAUNCHED(s);
   neighbor_kernel<true><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, rel, start, cnt,
                                                n_int, nullptr, s->nbr_ptr, s->nbr_col, s->nbr_F,

@@ -4,7 +4,8 @@
 //  a3  material data, frozen for the step (Sec. 3.2):
 //        T = e/c_v, sigma = sigma0 T^p, Fleck factor f = 1/(1 + c sigma dt 4aT^3/(rho c_v))
 //        (Sec. 2.2), SPH gradient grad E_i = sum_j V_j (E_j - E_i) F_ij x_ij (Sec. 2.3),
-//        R = |grad E|/(sigma E), flux limiter lambda(R) (Sec. 2.1), D = c lambda / sigma.
+//        R = |grad E|/(sigma_t E), flux limiter lambda(R) (Sec. 2.1), D = c lambda / sigma_t,
+//        sigma_t = sigma_a + sigma_s (constant scattering opacity sigma_s).
 //  a4  operator of Eq. diffusion-solve scaled by V:  B_ij = V_i V_j F_ij (D_i + D_j) for
 //        j != i, B_ii = V_i (1/dt + c sigma_i f_i) + sum over all neighbours of
 //        V_i w_ij, w_ij = -V_j (D_i + D_j) F_ij >= 0; Dirichlet neighbours move to
@@ -21,6 +22,7 @@ namespace sphrt {
 
 struct Phys {
   double a, c, cv, p, T_floor, larsen_k, dt;
+  double sigma_s;  // scattering opacity: sigma_t = sigma_a + sigma_s (R and D, Sec. 2.1)
   double inv_cv, inv_dt;  // 1/cv, 1/dt (the Newton loop multiplies instead of dividing)
   double tol_inner;
   int limiter, max_inner;
@@ -60,7 +62,7 @@ __global__ void props_point_kernel(Phys ph, int64_t n, const int32_t *kind, cons
     double lam = limiter_lambda(ph.limiter, ph.larsen_k, 0.0);
     R[i] = 0.0;
     lambda[i] = lam;
-    D[i] = ph.c * lam / sig;
+    D[i] = ph.c * lam / (sig + ph.sigma_s);
   }
 }
 
@@ -95,11 +97,12 @@ __global__ void props_grad_kernel(Phys ph, int64_t n_int, const int64_t *nbr_ptr
     if (active && sub == 0) {
       double gn = sqrt(gx * gx + gy * gy + gz * gz);
       double Es = Ei > 1e-300 ? Ei : 1e-300;
-      double Ri = gn / (sigma[i] * Es);
+      const double sig_t = sigma[i] + ph.sigma_s;
+      double Ri = gn / (sig_t * Es);
       double lam = limiter_lambda(ph.limiter, ph.larsen_k, Ri);
       R[i] = Ri;
       lambda[i] = lam;
-      D[i] = ph.c * lam / sigma[i];
+      D[i] = ph.c * lam / sig_t;
     }
   }
 }
@@ -209,11 +212,12 @@ __global__ void __launch_bounds__(kBlock, kPairMinBlocks)
       const double gx = g.a, gy = g.b, gz = g.c;
       double gn = sqrt(gx * gx + gy * gy + gz * gz);
       double Es = Eo > 1e-300 ? Eo : 1e-300;
-      double Ri = gn / (sigma[i] * Es);
+      const double sig_t = sigma[i] + ph.sigma_s;
+      double Ri = gn / (sig_t * Es);
       double lam = limiter_lambda(ph.limiter, ph.larsen_k, Ri);
       R[i] = Ri;
       lambda[i] = lam;
-      D[i] = ph.c * lam / sigma[i];
+      D[i] = ph.c * lam / sig_t;
     }
   }
 }
@@ -637,6 +641,7 @@ Phys make_phys(const sph_rt *s, double dt) {
   ph.p = s->cfg.opacity_exp;
   ph.T_floor = s->cfg.T_floor;
   ph.larsen_k = s->cfg.larsen_k;
+  ph.sigma_s = s->cfg.sigma_s;
   ph.dt = dt;
   ph.tol_inner = s->cfg.tol_inner_e;
   ph.limiter = s->cfg.limiter;

@@ -156,6 +156,7 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   if (!c) return;
   memset(c, 0, sizeof(*c));
   c->dim = 3;
+  c->kernel = SPH_RT_M4_SPLINE;
   c->a = 1.0;
   c->c = 1.0;
   c->cv = 1.0;
@@ -197,6 +198,8 @@ static bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
 static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
   if (c->dim < 1 || c->dim > 3) return why = "dim must be 1, 2 or 3", SPH_RT_EINVAL;
+  if (c->kernel != SPH_RT_M4_SPLINE && c->kernel != SPH_RT_WENDLAND_C4)
+    return why = "kernel must be SPH_RT_M4_SPLINE or SPH_RT_WENDLAND_C4", SPH_RT_EINVAL;
   if (!(isfinite(c->a) && c->a >= 0.0) || !finite_pos(c->c) || !finite_pos(c->cv))
     return why = "a must be finite and >= 0 (0: no emission); c and cv finite and positive",
            SPH_RT_EINVAL;
@@ -205,6 +208,8 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
     return why = "larsen_k must be positive", SPH_RT_EINVAL;
   if (!isfinite(c->opacity_exp)) return why = "opacity_exp must be finite", SPH_RT_EINVAL;
   if (!isfinite(c->T_floor) || c->T_floor < 0) return why = "T_floor must be >= 0", SPH_RT_EINVAL;
+  if (!(isfinite(c->sigma_s) && c->sigma_s >= 0.0))
+    return why = "sigma_s must be finite and >= 0", SPH_RT_EINVAL;
   if (!finite_pos(c->tol_outer_e) || !finite_pos(c->tol_outer_E) || !finite_pos(c->tol_inner_e) ||
       !finite_pos(c->tol_krylov))
     return why = "tolerances must be finite and positive", SPH_RT_EINVAL;

@@ -23,6 +23,7 @@ INTERIOR, DIRICHLET, COPY = 0, 1, 2
 LIMITER_NONE, LIMITER_LEVERMORE, LIMITER_LARSEN = 0, 1, 2
 PRECOND_JACOBI, PRECOND_CHEBYSHEV, PRECOND_AMG = 0, 1, 2
 FP64, MIXED = 0, 1
+M4_SPLINE, WENDLAND_C4 = 0, 1
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ENOTCONV: "ENOTCONV", EDEVICE: "EDEVICE",
           ESTATE: "ESTATE"}
 
@@ -30,11 +31,13 @@ _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ENOTCONV: "ENOTCONV", EDEVICE: "ED
 class Config(C.Structure):
     _fields_ = [
         ("dim", C.c_int32),
+        ("kernel", C.c_int32),
         ("a", C.c_double), ("c", C.c_double), ("cv", C.c_double),
         ("limiter", C.c_int32),
         ("larsen_k", C.c_double),
         ("opacity_exp", C.c_double),
         ("T_floor", C.c_double),
+        ("sigma_s", C.c_double),
         ("tol_outer_e", C.c_double), ("tol_outer_E", C.c_double),
         ("tol_inner_e", C.c_double), ("tol_krylov", C.c_double),
         ("max_outer", C.c_int32), ("max_inner_e", C.c_int32), ("max_krylov", C.c_int32),

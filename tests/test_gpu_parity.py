@@ -305,6 +305,66 @@ def test_vcycle_product_cg_stops_on_the_fp64_residual(drop):
     assert rel_err(eg, ref["e"], m) < 1e-8 and rel_err(Eg, ref["E"], m) < 1e-8
 
 
+# ---------------------------------------------------------------------------
+# the paper's discretisation: Wendland C4 with h = 4 dx (support h), the cgs
+# manufactured problem of Sec. 4.3 with periodic copy ghosts, Larsen limiter,
+# scattering opacity
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("make", [
+    lambda: I.mms_cgs(2, 16, steps=3, jitter=0.0),
+    lambda: I.mms_cgs(2, 16, steps=3),
+    lambda: I.mms_cgs(3, 10, steps=2),
+    lambda: I.mms_cgs(1, 64, steps=5)])
+def test_wendland_neighbors_bit_exact(make):
+    w = make()
+    P = w.particles
+    S = sphrt.solver_for(w)
+    rp, cols = S.get_neighbors()
+    orp, ocols = O.neighbors(P.pos, P.h, P.kind, kernel=1)
+    assert np.array_equal(rp, orp) and np.array_equal(cols, ocols.astype(np.int64))
+
+
+def test_wendland_properties_and_operator_match_oracle():
+    w = I.mms_cgs(2, 16, steps=1)
+    P = w.particles
+    S = sphrt.solver_for(w, precond=sphrt.PRECOND_JACOBI)
+    Qe, QE, ge, gE = w.step_inputs(1)
+    S.step(w.dt, Qe, QE, ge, gE)
+    pg = S.get_properties()
+    pb = O.Problem(P, w.params)
+    po = pb.properties(w.e0, w.E0, w.dt)
+    m = P.kind == 0
+    for k in ("sigma", "f", "R", "lambda", "D"):
+        np.testing.assert_allclose(pg[k][m], po[k][m], rtol=1e-13, atol=0, err_msg=k)
+    arow, acol, aval, adiag, gb = pb.assemble(po, w.dt, w.E0)
+    rowptr, cols, vals, diag, ggb = S.get_operator()
+    np.testing.assert_allclose(diag[m], adiag[m], rtol=1e-13)
+    dg = {k: v for k, v in _operator_dict(rowptr, cols, vals, diag).items() if k[0] != k[1]}
+    do = _operator_dict(arow, acol, aval, adiag)
+    assert set(dg) == set(do)
+    keys = sorted(do)
+    err = np.array([abs(dg[k] - do[k]) / abs(adiag[k[0]]) for k in keys])
+    assert np.all(err <= 1e-13)
+
+
+@pytest.mark.parametrize("make,precision,tol", [
+    (lambda: I.mms_cgs(2, 16, steps=4), sphrt.FP64, 1e-10),
+    (lambda: I.mms_cgs(2, 32, steps=3), sphrt.FP64, 1e-10),
+    (lambda: I.mms_cgs(3, 12, steps=2), sphrt.FP64, 1e-10),
+    (lambda: I.mms_cgs(3, 12, steps=2), sphrt.MIXED, 1e-8),
+    (lambda: I.mms_cgs(1, 64, steps=6), sphrt.FP64, 1e-10)])
+def test_cgs_manufactured_parity(make, precision, tol):
+    w = make()
+    r = run_both(w, w.steps, gpu_over=dict(precision=precision), orc_over=TIGHT)
+    assert r["err_e"] < tol and r["err_E"] < tol, (r["err_e"], r["err_E"])
+    for g, o in zip(r["gstats"], r["ostats"]):
+        assert g.outer_iters == o.outer_iters
+        # periodic: no boundary flux; the energy changes by the sources alone
+        assert abs(g.boundary_energy) <= 1e-14 * g.energy_after
+        defect = g.energy_after - g.energy_before - g.source_energy
+        assert abs(defect) <= 1e-12 * g.energy_after
+
+
 def test_mixed_precision_parity():
     w = I.mms_3d_lp(n=16, steps=3)
     r = run_both(w, 3, gpu_over=dict(precision=sphrt.MIXED, precond=sphrt.PRECOND_AMG),
