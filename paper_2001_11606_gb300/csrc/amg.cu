@@ -965,11 +965,15 @@ __device__ __forceinline__ void fcg_reduce(double (&acc)[5], int first, Scalars 
 }
 
 // The A P sweep: res2 = res - (A P) e_c, z = z_pre + P e_c, B z = r - res2.
-// (five FP64 partials on top of the row tile: compiled for 3 resident blocks
-// per SM, where the register file holds them without spilling)
-constexpr int kFcgMinBlocks = 3;
+// (five FP64 partials on top of the row tile: compiled for the resident blocks
+// per SM at which the register file holds them without spilling -- 4 with FP32
+// vectors (64 registers), 3 with FP64 ones (72))
+template <typename VT>
+__host__ __device__ constexpr int fcg_min_blocks() {
+  return sizeof(VT) == sizeof(float) ? 4 : 3;
+}
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, kFcgMinBlocks)
+__global__ void __launch_bounds__(kBlock, fcg_min_blocks<VT>())
     fine_ap_cg_kernel(int64_t n, const int64_t *ap_ptr, const int32_t *ap_col, const MT *ap_val,
                       const int32_t *agg, const VT *ec, const VT *z_pre, const VT *res,
                       const VT *r, VT *z, VT *w, const VT *p, const VT *q, int first, Scalars *sc,
@@ -1013,7 +1017,7 @@ __global__ void fcg_prolong_kernel(int64_t n, const int32_t *agg, const VT *ec, 
   }
 }
 template <int W, int U, typename MT, typename VT>
-__global__ void __launch_bounds__(kBlock, kFcgMinBlocks)
+__global__ void __launch_bounds__(kBlock, fcg_min_blocks<VT>())
     fcg_spmv_dot_kernel(CsrView<MT> A, const VT *t, const VT *r, VT *z, VT *w, const VT *p,
                         const VT *q, int first, Scalars *sc, double *partials, int *wflag) {
   pdl_wait();
@@ -2009,7 +2013,7 @@ static sph_rt_status fcg_cycle_t(sph_rt *s, const FcgSet<T> &v, int first) {
   if (rc) return rc;
   if (L->ap_ptr && LV::ap(L)) {
     const RowShape sh = shape_for_mean(L->n ? (double)L->nnz_ap / (double)L->n : 0.0);
-    const int gp = row_grid_blocks(s->num_sms, L->n, sh.W, kFcgMinBlocks);
+    const int gp = row_grid_blocks(s->num_sms, L->n, sh.W, fcg_min_blocks<T>());
     wf = timing_begin(s);
     SPH_DISPATCH_SHAPE(sh.W, sh.U,
                        (pdl_launch(s, fine_ap_cg_kernel<W, U, T, T>, gp, kBlock, 0, L->n,
@@ -2029,7 +2033,7 @@ static sph_rt_status fcg_cycle_t(sph_rt *s, const FcgSet<T> &v, int first) {
              (const int32_t *)L->agg, (const T *)LV::z(C), (const T *)v.zpre, t, sc);
   SPH_LAUNCHED(s);
   wf = timing_begin(s);
-  const int gd = row_grid_blocks(s->num_sms, L->n, A.W, kFcgMinBlocks);
+  const int gd = row_grid_blocks(s->num_sms, L->n, A.W, fcg_min_blocks<T>());
   SPH_DISPATCH_SHAPE(A.W, A.U,
                      (pdl_launch(s, fcg_spmv_dot_kernel<W, U, T, T>, gd, kBlock, 0, A,
                                  (const T *)t, (const T *)v.r, v.z, v.w, (const T *)v.p,
