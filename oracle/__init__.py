@@ -92,6 +92,8 @@ def lib():
             L.orc_step.argtypes = [P, i64, P, P, P, P, P, P, P, P, P, dbl, P, P, P, P, P, P, P]
             L.orc_step.restype = i32
             L.orc_totals.argtypes = [i64, P, P, P, P, P, P]
+            L.orc_smoothing_lengths.argtypes = [P, i64, P, P, P, dbl, dbl, i32, P]
+            L.orc_smoothing_lengths.restype = i32
             L.orc_limiter.argtypes = [P, dbl]
             L.orc_limiter.restype = dbl
             L.orc_num_threads.restype = i32
@@ -141,6 +143,22 @@ def limiter(R: float, limiter: int, larsen_k: float = 2.0) -> float:
     """Flux limiter lambda(R) (Sec. 2.1): 0 none (1/3), 1 Levermore, 2 Larsen(k)."""
     p = make_params(limiter=int(limiter), larsen_k=float(larsen_k))
     return float(lib().orc_limiter(C.byref(p), float(R)))
+
+
+def smoothing_lengths(particles, params: dict, eta: float = 4.0, tol: float = 1e-13,
+                      max_iter: int = 100):
+    """Smoothing lengths by the initialisation iteration of Sec. 3.1 (support
+    radius = eta local point spacings), starting from particles.h.  Returns
+    (h, largest number of updates)."""
+    P = particles
+    prm = make_params(**params)
+    pos = _f64(P.pos)
+    h = _f64(P.h).copy()
+    kind = np.ascontiguousarray(P.kind, dtype=np.int32)
+    copy_of = np.ascontiguousarray(P.copy_of, dtype=np.int64)
+    it = lib().orc_smoothing_lengths(C.byref(prm), pos.shape[0], _p(pos), _p(kind), _p(copy_of),
+                                     float(eta), float(tol), int(max_iter), _p(h))
+    return h, int(it)
 
 
 def neighbors(pos, h, kind, brute: bool = False, kernel: int = 0):

@@ -289,6 +289,83 @@ int64_t orc_neighbors_rows(int64_t n, int dim, const double *pos, const double *
 }
 
 /* ------------------------------------------------------------------------ */
+/* Smoothing lengths (Sec. 3.1): the support radius of every interior point   */
+/* is set to eta local point spacings (eta = 4 in the paper) by an iteration  */
+/* run once at initialisation.  Reading of the ASPH method the paper names:   */
+/* the iteration works on the zeroth moment of the kernel,                    */
+/*   S_i(h) = sum_j W(r_ij, h)   (all j within the support, i itself included),*/
+/* the SPH number density: for points of spacing dx, S = dx^-d, so            */
+/* (h^d S_i(h))^(1/d) estimates h / dx.  With s the support radius in units   */
+/* of h (2: cubic B-spline, 1: Wendland C4) the target is h / dx = eta / s,   */
+/* and each point is updated by                                               */
+/*   h_i <- h_i (eta / s) / (h_i^d S_i(h_i))^(1/d),                           */
+/* bounded to [h_i / 2, 2 h_i] per update, until |dh_i| <= tol h_i or        */
+/* max_iter updates.  S_i depends on h_i alone, so the points iterate         */
+/* independently.  Ghosts: a copy ghost takes the h of the point it copies; a */
+/* Dirichlet ghost keeps its own.  Returns the largest number of updates.     */
+/* ------------------------------------------------------------------------ */
+static double number_density(const orc_params *p, int64_t n, const double *pos, int64_t i,
+                             double hi, const int64_t *order, const int64_t *where) {
+  const int dim = p->dim;
+  const double cut = support_factor(p->kernel) * hi, cut2 = cut * cut;
+  double W, dW, S = 0.0;
+  kernel_eval(p->kernel, dim, 0.0, hi, &W, &dW);  /* the point itself */
+  S += W;
+  const double xi = pos[i * dim];
+  for (int dir = -1; dir <= 1; dir += 2) {
+    for (int64_t k = where[i] + dir; k >= 0 && k < n; k += dir) {
+      int64_t j = order[k];
+      double dx = xi - pos[j * dim];
+      if (!(dx * dx < cut2)) break;
+      double r2 = pair_r2(dim, pos + i * dim, pos + j * dim);
+      if (!(r2 < cut2)) continue;
+      kernel_eval(p->kernel, dim, sqrt(r2), hi, &W, &dW);
+      S += W;
+    }
+  }
+  return S;
+}
+
+int orc_smoothing_lengths(const orc_params *p, int64_t n, const double *pos,
+                          const int32_t *kind, const int64_t *copy_of, double eta, double tol,
+                          int max_iter, double *h) {
+  const int dim = p->dim;
+  int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *where = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) order[i] = i;
+  g_sort_pos = pos;
+  g_sort_dim = dim;
+  qsort(order, (size_t)n, sizeof(int64_t), cmp_by_x);
+  for (int64_t k = 0; k < n; ++k) where[order[k]] = k;
+  const double target = eta / support_factor(p->kernel);
+  int most = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : most)
+  for (int64_t i = 0; i < n; ++i) {
+    if (kind[i] != ORC_INTERIOR) continue;
+    double hi = h[i];
+    int it = 0;
+    while (it < max_iter) {
+      double S = number_density(p, n, pos, i, hi, order, where);
+      double ratio = pow(pow(hi, (double)dim) * S, 1.0 / dim);  /* estimate of h / dx */
+      double hn = hi * target / ratio;
+      if (hn > 2.0 * hi) hn = 2.0 * hi;
+      if (hn < 0.5 * hi) hn = 0.5 * hi;
+      ++it;
+      double change = fabs(hn - hi);
+      hi = hn;
+      if (change <= tol * hi) break;
+    }
+    h[i] = hi;
+    if (it > most) most = it;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (kind[i] == ORC_COPY) h[i] = h[copy_of[i]];
+  free(order);
+  free(where);
+  return most;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Material data, frozen for the step (Sec. 3.2).                            */
 /* ------------------------------------------------------------------------ */
 static double limiter_lambda(const orc_params *p, double R) {

@@ -621,3 +621,51 @@ def test_cgs_manufactured_cycle_conserves_energy():
     assert abs(t1 - t0 - src) <= 1e-13 * t0
     assert abs(src) <= 1e-13 * t0
     assert all(s.outer_iters <= 3 for s in st)
+
+
+# --------------------------------------------------------------------------
+# Smoothing lengths (Sec. 3.1): support radius = 4 local point spacings
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,kern,target", [(2, 1, 4.0), (3, 1, 4.0), (2, 0, 2.0), (1, 1, 4.0)])
+def test_smoothing_length_on_a_lattice_is_eta_spacings(dim, kern, target):
+    # support h (Wendland) or 2h (cubic B-spline) spans 4 spacings of a regular lattice,
+    # to within the lattice's own quadrature of the number density; every interior
+    # point has the same neighbourhood (ghosts complete it), so the same h
+    sup = 1.0 if kern == 1 else 2.0
+    P = I.make_lattice(dim, (14,) * dim, 1.0 / 14, seed=0, jitter=0.0, h_over_dx=3.0, support=sup)
+    h, it = O.smoothing_lengths(P, dict(dim=dim, kernel=kern))
+    m = P.kind == 0
+    assert it < 20
+    assert np.all(np.abs(h[m] * 14 - target) < 2e-3 * target)
+    assert np.ptp(h[m]) <= 1e-12 * np.max(h[m])
+
+
+def test_smoothing_length_scales_with_the_point_set():
+    # h is a length: scaling every position (and the starting h) by s scales it by s
+    P = I.make_lattice(2, (10, 10), 0.1, seed=7, h_over_dx=3.0, support=1.0)
+    h1, _ = O.smoothing_lengths(P, dict(dim=2, kernel=1))
+    P.pos = P.pos * 3.5
+    P.h = P.h * 3.5
+    h2, _ = O.smoothing_lengths(P, dict(dim=2, kernel=1))
+    m = P.kind == 0
+    assert np.allclose(h2[m], 3.5 * h1[m], rtol=1e-12, atol=0)
+
+
+def test_smoothing_length_follows_the_local_spacing():
+    # two lattices of spacing 1/16 and 1/32 side by side (x < 0.5 and x > 0.5):
+    # away from the interface h is 4 local spacings on either side
+    Pa = I.make_lattice(2, (8, 16), 1.0 / 16, seed=0, jitter=0.0, support=1.0)
+    Pb = I.make_lattice(2, (16, 32), 1.0 / 32, seed=0, jitter=0.0, support=1.0)
+    ka, kb = Pa.kind == 0, Pb.kind == 0
+    pos = np.concatenate([Pa.pos[ka], Pb.pos[kb] + np.array([0.5, 0.0])])
+    n = len(pos)
+    P = I.Particles(dim=2, dx=1.0 / 32, counts=(0, 0), pos=pos, kind=np.zeros(n, np.int32),
+                    copy_of=np.full(n, -1), mass=np.ones(n), rho=np.ones(n),
+                    h=np.full(n, 0.1), sigma0=np.ones(n))
+    h, _ = O.smoothing_lengths(P, dict(dim=2, kernel=1))
+    x, y = pos[:, 0], pos[:, 1]
+    inner = (y > 0.3) & (y < 0.7)  # far from the open edges of the patch
+    left = inner & (x > 0.1) & (x < 0.2)
+    right = inner & (x > 0.8) & (x < 0.9)
+    assert np.allclose(h[left] * 16, 4.0, rtol=5e-3)
+    assert np.allclose(h[right] * 32, 4.0, rtol=5e-3)
