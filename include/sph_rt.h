@@ -225,6 +225,40 @@ sph_rt_status sph_rt_get_energies(sph_rt *s, double *e, double *E, double totals
 /* Same into device memory. */
 sph_rt_status sph_rt_get_energies_device(sph_rt *s, double *e, double *E);
 
+/*
+ * Smoothing lengths by the initialisation iteration of Sec. 3.1: the support
+ * radius of every interior particle becomes eta local particle spacings (the
+ * paper uses eta = 4 with the Wendland C4 kernel).  Reading of the ASPH method
+ * the paper names: each particle iterates on the kernel's zeroth moment
+ * S_i(h) = sum_j W(r_ij, h) (the SPH number density, i included):
+ *   h_i <- h_i (eta / s) / (h_i^d S_i(h_i))^(1/d),  at most x2 or /2 per update,
+ * s = the kernel's support in units of h, until |dh_i| <= tol h_i or max_iter
+ * updates.  Copy ghosts take the h of the particle they copy, Dirichlet ghosts
+ * keep theirs.  Starts from the current h; then rebuilds the neighbour lists and
+ * operator sparsity (as sph_rt_set_particles) with the state e, E kept.
+ * *iters (may be NULL): the largest number of updates of a particle.
+ * EINVAL: eta or tol not positive, max_iter < 1, or a starting h so large that
+ * one support holds more than 4096 particles; ENOTCONV if the lengths keep
+ * growing past six successive search grids (the particle set is unchanged).
+ */
+sph_rt_status sph_rt_adapt_smoothing_lengths(sph_rt *s, double eta, double tol,
+                                             int32_t max_iter, int32_t *iters);
+
+/* Current smoothing lengths, caller order [n_total] (host). */
+sph_rt_status sph_rt_get_smoothing_lengths(sph_rt *s, double *h);
+
+/*
+ * Moving particles: new positions (caller order, row-major [n_total][dim]) for
+ * the current particle set.  Masses, densities, smoothing lengths, opacities,
+ * kinds, copy sources and the state e, E are kept; the Morton order, the
+ * neighbour lists and the operator sparsity are rebuilt (rows a1-a2 re-run),
+ * and the next step builds a new AMG hierarchy.  EINVAL: a non-finite position.
+ */
+sph_rt_status sph_rt_move_particles(sph_rt *s, const double *pos);
+
+/* Same, with the positions in device memory. */
+sph_rt_status sph_rt_move_particles_device(sph_rt *s, const double *pos);
+
 /* Sizes after set_particles: interior count, neighbour-list nnz, operator nnz. */
 sph_rt_status sph_rt_get_sizes(const sph_rt *s, int64_t *n_interior, int64_t *nnz_neighbors,
                                int64_t *nnz_operator);

@@ -477,6 +477,134 @@ extern "C" sph_rt_status sph_rt_set_particles_device(sph_rt *s, int64_t n_total,
   return set_particles_common(s, n_total, pos, mass, rho, h, sigma0, kind, copy_of, e0, E0, true);
 }
 
+// ---------------------------------------------------------------------------
+// smoothing lengths (Sec. 3.1) and moving particles
+// ---------------------------------------------------------------------------
+namespace sphrt {
+sph_rt_status smoothing_iterate(sph_rt *s, double eta, double tol, int max_iter, int *iters);
+}
+
+// caller-order device copies of the current particle set: positions (unless
+// the caller gives new ones), kinds and copy sources
+__global__ void caller_layout_kernel(int64_t n, int dim, const int64_t *slot2caller,
+                                     const double *px, const double *py, const double *pz,
+                                     const int32_t *kind, const int32_t *copysrc,
+                                     double *pos_c, int32_t *kind_c, int64_t *copy_c) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = slot2caller[t];
+    if (pos_c) {
+      pos_c[c * dim] = px[t];
+      if (dim > 1) pos_c[c * dim + 1] = py[t];
+      if (dim > 2) pos_c[c * dim + 2] = pz[t];
+    }
+    kind_c[c] = kind[t];
+    copy_c[c] = copysrc[t] >= 0 ? slot2caller[copysrc[t]] : -1;
+  }
+}
+
+// Rebuild the particle set (Morton order, neighbour lists, operator sparsity;
+// the AMG hierarchy follows on the next step) from its own device data in
+// caller order, with new positions (device, caller order) or the current ones,
+// keeping masses, densities, smoothing lengths (s->h), opacities, kinds and
+// the state e, E.
+static sph_rt_status rebuild_particles(sph_rt *s, const double *new_pos) {
+  const int64_t n = s->n;
+  const int dim = s->dim;
+  double *pos_c = nullptr, *arr = nullptr;
+  int32_t *kind_c = nullptr;
+  int64_t *copy_c = nullptr;
+  sph_rt_status rc = SPH_RT_OK;
+  if (cudaMalloc(&pos_c, sizeof(double) * n * dim) != cudaSuccess ||
+      cudaMalloc(&arr, sizeof(double) * n * 6) != cudaSuccess ||
+      cudaMalloc(&kind_c, sizeof(int32_t) * n) != cudaSuccess ||
+      cudaMalloc(&copy_c, sizeof(int64_t) * n) != cudaSuccess) {
+    cudaGetLastError();
+    rc = set_error(s, SPH_RT_ENOMEM, "no device memory for the particle rebuild");
+  }
+  if (!rc) {
+    const int g = (int)((n + kBlock - 1) / kBlock < (int64_t)s->num_sms * 8
+                            ? (n + kBlock - 1) / kBlock
+                            : (int64_t)s->num_sms * 8);
+    caller_layout_kernel<<<g, kBlock, 0, s->stream>>>(n, dim, s->slot2caller, s->px, s->py, s->pz,
+                                                      s->kind, s->copysrc,
+                                                      new_pos ? nullptr : pos_c, kind_c, copy_c);
+    s->launches++;
+    const double *src[6] = {s->mass, s->rho, s->h, s->sigma0, s->e, s->E};
+    for (int k = 0; k < 6 && !rc; ++k) rc = launch_scatter_caller(s, src[k], n, arr + (size_t)k * n);
+    if (!rc && new_pos &&
+        cudaMemcpyAsync(pos_c, new_pos, sizeof(double) * n * dim, cudaMemcpyDeviceToDevice,
+                        s->stream) != cudaSuccess)
+      rc = set_error(s, SPH_RT_EDEVICE, "copying the new positions failed");
+    if (!rc && (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess))
+      rc = set_error(s, SPH_RT_EDEVICE, "gathering the particle set failed");
+  }
+  if (!rc)
+    rc = set_particles_common(s, n, pos_c, arr, arr + n, arr + 2 * n, arr + 3 * n, kind_c, copy_c,
+                              arr + 4 * n, arr + 5 * n, true);
+  cudaFree(pos_c);
+  cudaFree(arr);
+  cudaFree(kind_c);
+  cudaFree(copy_c);
+  return rc;
+}
+
+extern "C" sph_rt_status sph_rt_adapt_smoothing_lengths(sph_rt *s, double eta, double tol,
+                                                        int32_t max_iter, int32_t *iters) {
+  if (!s) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
+  if (!(isfinite(eta) && eta > 0.0) || !(isfinite(tol) && tol > 0.0) || max_iter < 1)
+    return set_error(s, SPH_RT_EINVAL, "eta and tol must be positive, max_iter >= 1");
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  int it = 0;
+  sph_rt_status rc = smoothing_iterate(s, eta, tol, max_iter, &it);
+  if (rc) return rc;
+  if (iters) *iters = it;
+  return rebuild_particles(s, nullptr);
+}
+
+extern "C" sph_rt_status sph_rt_get_smoothing_lengths(sph_rt *s, double *h) {
+  if (!s || !h) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  sph_rt_status rc = launch_scatter_caller(s, s->h, s->n, s->tmp_n);
+  if (rc) return rc;
+  SPH_CUDA(s, cudaMemcpyAsync(h, s->tmp_n, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_move_particles_device(sph_rt *s, const double *pos) {
+  if (!s || !pos) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  return rebuild_particles(s, pos);
+}
+
+extern "C" sph_rt_status sph_rt_move_particles(sph_rt *s, const double *pos) {
+  if (!s || !pos) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
+  const int64_t count = s->n * s->dim;
+  for (int64_t k = 0; k < count; ++k)
+    if (!isfinite(pos[k]))
+      return set_error(s, SPH_RT_EINVAL, "non-finite position at particle " +
+                                             std::to_string(k / s->dim));
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  double *d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * count) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(s, SPH_RT_ENOMEM, "no device memory for the new positions");
+  }
+  sph_rt_status rc = SPH_RT_OK;
+  if (cudaMemcpyAsync(d, pos, sizeof(double) * count, cudaMemcpyHostToDevice, s->stream) !=
+      cudaSuccess)
+    rc = set_error(s, SPH_RT_EDEVICE, "copying the new positions failed");
+  if (!rc) rc = rebuild_particles(s, d);
+  cudaStreamSynchronize(s->stream);
+  cudaFree(d);
+  return rc;
+}
+
 extern "C" sph_rt_status sph_rt_get_sizes(const sph_rt *s, int64_t *n_interior,
                                           int64_t *nnz_neighbors, int64_t *nnz_operator) {
   if (!s) return SPH_RT_EINVAL;

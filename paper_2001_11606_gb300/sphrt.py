@@ -117,6 +117,10 @@ _SIGNATURES = [
     ("sph_rt_get_energies", C.c_int, [_P, _P, _P, _P]),
     ("sph_rt_get_energies_device", C.c_int, [_P, _P, _P]),
     ("sph_rt_get_sizes", C.c_int, [_P, _P, _P, _P]),
+    ("sph_rt_adapt_smoothing_lengths", C.c_int, [_P, C.c_double, C.c_double, C.c_int32, _P]),
+    ("sph_rt_get_smoothing_lengths", C.c_int, [_P, _P]),
+    ("sph_rt_move_particles", C.c_int, [_P, _P]),
+    ("sph_rt_move_particles_device", C.c_int, [_P, _P]),
     ("sph_rt_get_neighbors", C.c_int, [_P, _P, _P]),
     ("sph_rt_get_operator", C.c_int, [_P, _P, _P, _P, _P, _P]),
     ("sph_rt_get_properties", C.c_int, [_P] * 7),
@@ -320,6 +324,28 @@ class Solver:
     def get_energies_device(self, e_ptr, E_ptr):
         self._check(self._L.sph_rt_get_energies_device(self._h, C.c_void_p(e_ptr) if e_ptr else None,
                                                        C.c_void_p(E_ptr) if E_ptr else None))
+
+    def adapt_smoothing_lengths(self, eta=4.0, tol=1e-13, max_iter=100):
+        """Smoothing lengths by the iteration of Sec. 3.1; returns the largest
+        number of updates."""
+        it = C.c_int32()
+        self._check(self._L.sph_rt_adapt_smoothing_lengths(self._h, float(eta), float(tol),
+                                                           int(max_iter), C.byref(it)))
+        return it.value
+
+    def get_smoothing_lengths(self):
+        h = np.empty(self.n)
+        self._check(self._L.sph_rt_get_smoothing_lengths(self._h, _ptr(h)))
+        return h
+
+    def move_particles(self, pos):
+        pos = _f64(pos)
+        if pos.size != self.n * self.cfg.dim:
+            raise ValueError(f"expected {self.n * self.cfg.dim} coordinates, got {pos.size}")
+        self._check(self._L.sph_rt_move_particles(self._h, _ptr(pos)))
+
+    def move_particles_device(self, pos_ptr):
+        self._check(self._L.sph_rt_move_particles_device(self._h, C.c_void_p(pos_ptr)))
 
     def sizes(self):
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
