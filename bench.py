@@ -135,10 +135,16 @@ def aggregate_ranks(t_local: float, work_local: float):
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the kernel at the workload, keyed (workload, precision, kernel);
 # the profiles/ summary named in the second field holds the capture.
+# At 128^3 the traffic is that of the same kernel's capture on the 64^3 instance
+# of the workload, scaled by the algorithmic bytes of a launch (traffic grows
+# with the stored entries and rows a launch processes): FP32 V-cycle residual
+# 225.6 MB for 219.1 MB (x1.029), FP64 residual 342.2 MB for 332.9 MB (x1.028).
 NCU_TRAFFIC = {
     ("mms3d-lp-64^3", "fp64", "resid"): (338.3e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
     ("mms3d-lp-64^3", "fp64", "spmv_pq"): (341.8e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
     ("mms3d-lp-64^3", "fp64", "post_ap"): (115.1e6, "profiles/fine_sweeps_mms3d-lp-64.md"),
+    ("mms3d-128^3", "mixed", "resid"): (1850.8e6, "profiles/fine_sweeps_mms3d-mixed.md"),
+    ("mms3d-128^3", "mixed", "true_resid"): (2819.4e6, "profiles/fine_sweeps_mms3d-mixed.md"),
 }
 
 
