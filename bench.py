@@ -325,6 +325,183 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_problems(k: int, seed: int = 7):
+    """The serving stream's fusable requests: k heating-wave problems (2-D/3-D
+    50/50, 1k..20k particles log-uniform, sigma0 log-uniform in [1, 100], 20
+    steps of dt = 1e-5)."""
+    descs = I.serving_stream(k, seed=seed, n_min=1000, n_max=20000)
+    return [I.heating_wave(d["dim"], d["n_target"], d["sigma0"], seed=d["seed"], steps=20)
+            for d in descs]
+
+
+def batch_bytes(info, outer, krylov, degree, steps):
+    """Algorithmic bytes of one batched run of `steps` steps of one problem:
+    every operator sweep (the CG product and the residual, and degree - 1 sweeps
+    inside each Chebyshev application: outer + degree * krylov sweeps in all)
+    streams the operator's values and columns once (12 B an entry) and 32 B per
+    row (row pointer, diagonal, the row's own x, y written); every step's
+    assembly reads G and the columns and writes the values (20 B an entry) and
+    its limiter gradient reads the neighbour columns and kernel factors (12 B)."""
+    nnz, ni, nbr = info["nnz_operator"], info["n_interior"], info["nnz_neighbours"]
+    return (outer + degree * krylov) * (12 * nnz + 32 * ni) + steps * (20 * nnz + 12 * nbr)
+
+
+def run_batch(args):
+    """Batched form: the serving stream's small problems, one batch per dimension,
+    each advanced 20 steps by one CUDA-graph launch (per step, one batched-step
+    launch per cluster size).  The launch shape of each batch is picked by the
+    library's autotuner."""
+    import torch
+
+    from paper_2001_11606_gb300 import sphrt
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(device=local)
+    probs = batch_problems(args.batch_k)
+    groups = {d: [w for w in probs if w.particles.dim == d] for d in (2, 3)}
+    groups = {d: g for d, g in groups.items() if g}
+    dt, T = probs[0].dt, probs[0].steps
+    hbm, peak_src = peaks()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=local)
+
+    def make(d, shape=None):
+        g = groups[d]
+        cfg = sphrt.config_from_params(g[0].params, device=local, stream=stream.cuda_stream)
+        B = sphrt.Batch(cfg)
+        for w in g:
+            B.add(w.particles, w.e0, w.E0)
+        if shape is not None:
+            B.set_shape(*shape)
+        return B
+
+    t0 = time.perf_counter()
+    batches = {d: make(d) for d in groups}
+    setup_s = time.perf_counter() - t0
+    tuned, tables, tune_s = {}, {}, {}
+    for d, B in batches.items():
+        t0 = time.perf_counter()
+        tuned[d], tables[d] = B.autotune(dt)
+        tune_s[d] = time.perf_counter() - t0
+    infos = {d: [B.problem_info(k) for k in range(len(groups[d]))] for d, B in batches.items()}
+    ps_run = sum(i["n_interior"] * T for d in infos for i in infos[d])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(batches) + 1)]
+
+    def one_run():
+        with torch.cuda.stream(stream):
+            flush.zero_()  # inputs are larger than L2, and L2 is flushed between runs
+        res = {}
+        ev[0].record(stream)
+        for a, (d, B) in enumerate(batches.items()):
+            rc, st, ou, kr = B.run(dt, T)
+            ev[a + 1].record(stream)
+            res[d] = (st, ou, kr)
+        stream.synchronize()
+        ms = {d: ev[a].elapsed_time(ev[a + 1]) for a, d in enumerate(batches)}
+        return res, ms
+
+    for _ in range(args.warmup):
+        one_run()
+    clocks = ClockSampler(local)
+    clocks.start()
+    runs = [one_run() for _ in range(args.steps)]
+    clk = clocks.stop()
+    ms_tot = [sum(ms.values()) for _, ms in runs]
+    t_ms = statistics.mean(ms_tot)
+    t_max, work = aggregate_ranks(t_ms * 1e-3 * args.steps, ps_run * args.steps)
+    per_dim = {}
+    byt_all, ms_all = 0.0, 0.0
+    for d in batches:
+        deg = tuned[d][1]
+        byt = []
+        for res, ms in runs:
+            st, ou, kr = res[d]
+            assert np.all(st == 0), f"batched {d}-D run did not converge"
+            byt.append(sum(batch_bytes(infos[d][k], int(ou[k]), int(kr[k]), deg, T)
+                           for k in range(len(groups[d]))))
+        mean_ms = statistics.mean(ms[d] for _, ms in runs)
+        mean_b = statistics.mean(byt)
+        byt_all += mean_b
+        ms_all += mean_ms
+        res0 = runs[-1][0][d]
+        per_dim[f"{d}d"] = {
+            "problems": len(groups[d]),
+            "interior_particles": sum(i["n_interior"] for i in infos[d]),
+            "operator_entries": sum(i["nnz_operator"] for i in infos[d]),
+            "shape": dict(zip(("lanes_per_row", "cheb_degree", "blocks_per_sm", "rows_per_cta"),
+                              tuned[d])),
+            "autotune_s": tune_s[d],
+            "autotune_ms": {f"W{k[0]}-deg{k[1]}-b{k[2]}-r{k[3]}": v for k, v in tables[d].items()},
+            "ms_per_run": mean_ms, "gbs": mean_b / (mean_ms * 1e-3) / 1e9,
+            "outer_per_step": float(np.mean(res0[1])) / T,
+            "krylov_per_step": float(np.mean(res0[2])) / T}
+    achieved = byt_all / (ms_all * 1e-3) / 1e9
+    value = work / t_max
+
+    # end to end through the public API from host arrays: set-up of every problem
+    # (neighbours, operator), the runs with the tuned shapes, and every result read back
+    h2d = sum(w.particles.pos.nbytes + 5 * 8 * w.particles.n + 4 * w.particles.n
+              + (8 * w.particles.n if np.any(w.particles.kind == sphrt.COPY) else 0)
+              for w in probs)
+    d2h = sum(16 * w.particles.n for w in probs)
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e_ev[0].record(stream)
+    fresh = {d: make(d, tuned[d]) for d in groups}
+    for d, B in fresh.items():
+        B.run(dt, T)
+        for k in range(len(groups[d])):
+            B.get_energies(k)
+    e_ev[1].record(stream)
+    stream.synchronize()
+    e2e_s = e_ev[0].elapsed_time(e_ev[1]) * 1e-3
+    for B in list(fresh.values()) + list(batches.values()):
+        B.close()
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        small = sorted(probs, key=lambda w: w.particles.n)[:3]
+        import oracle as O
+
+        O.build()
+        t0 = time.perf_counter()
+        for w in small:
+            pb = O.Problem(w.particles, w.params)
+            e, E = w.e0.copy(), w.E0.copy()
+            rc, e, E, _ = pb.step(e, E, w.dt)
+        cpu_s = time.perf_counter() - t0
+        n_s = sum(w.particles.n_interior for w in small)
+        cpu = {"value": n_s / cpu_s, "unit": "particle-steps/s", "cores": O.num_threads(),
+               "kind": "oracle",
+               "sample": f"the 3 smallest problems of the batch ({n_s} interior particles), "
+                         "neighbour set-up plus one backward-Euler step each"}
+    line = {"metric": "particle-steps/s (batched form)", "value": value,
+            "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batched serving problems: {args.batch_k} heating-wave "
+                                   "problems, 2-D/3-D, 1k..20k particles, one batch per "
+                                   f"dimension, {T} steps of dt = {dt:g} per run",
+                       "step": "one CUDA-graph run of each batch (20 batched-step launches)",
+                       "l2": "flushed between runs (a 258 MB write)",
+                       "setup_s": setup_s},
+            "batches": per_dim,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "batch_step_kernel (graph run time, 20 launches)",
+                         "peak_source": peak_src},
+            "e2e": {"value": ps_run / e2e_s, "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "includes": "set-up of every problem from host arrays, the runs, results"},
+            "gpu_launches": args.steps * len(batches) * 2 * T, "clocks": clk,
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+
+
 def fine_roofline(k_kinds, k_ms, k_bytes, hbm, src, workload, precision):
     """Roofline object of the fine kernel with the largest total event time."""
     dom = max(k_kinds, key=lambda k: k_kinds[k][1])
@@ -373,11 +550,16 @@ def main():
                     help="host-driven loop: Krylov iterations queued per convergence read "
                          "(1: no launch after convergence, the graph's kernel sequence)")
     ap.add_argument("--requests", type=int, default=512, help="serving: number of requests")
+    ap.add_argument("--batch-k", type=int, default=512,
+                    help="batch: number of problems (both dimensions)")
     ap.add_argument("--workers", type=int, default=8, help="serving: worker threads")
     ap.add_argument("--max-resident", type=int, default=32, help="serving: resident cap")
     args = ap.parse_args()
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
         return
 
     w = make_workload(args.workload)

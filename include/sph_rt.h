@@ -94,7 +94,9 @@ typedef struct {
   int32_t kernel_timing;/* 1: record CUDA events around SpMV launches (sph_rt_kernel_stats) */
   int32_t autotune;     /* 1: time the fine SpMV loads-in-flight (U = 4 or 8) on the first step
                            of a particle set; 0 (default): U from the mean row length.  U never
-                           changes a result bit (the lanes per row, W, follow the row length) */
+                           changes a result bit (the lanes per row, W, follow the row length).
+                           In a batch (sph_rt_batch_*): tune the batched launch's lanes per
+                           row and Chebyshev degree on its first step */
   int32_t amg_tail;     /* 1: run the small AMG levels (each <= 600k stored entries) of every
                            V-cycle as one thread-block-cluster launch (bitwise the same result;
                            default 0: measured no faster than the per-level launches) */
@@ -331,7 +333,10 @@ sph_rt_status sph_rt_loop_graph_info(const sph_rt *s, int64_t *captures, int64_t
 /* configuration, dt and step count are fused: up to fuse_max_k of them run */
 /* as one sph_rt_batch (one persistent launch per step, all steps in one    */
 /* CUDA-graph launch).  A fused request's result is the batched form's      */
-/* result, the same as in a batch of its own.  Queued */
+/* result, the same as in a batch of its own.  With cfg.autotune = 1 the     */
+/* first fused batch of a configuration and dt tunes its launch shape        */
+/* (sph_rt_batch_autotune) and later fused batches of that key reuse it.     */
+/* Queued */
 /* requests are admitted in FIFO order while the device footprint of the    */
 /* resident ones stays within hbm_budget_bytes (an estimate until a request */
 /* is set up, its measured allocation after).  A request's result does not  */
@@ -395,10 +400,11 @@ sph_rt_status sph_rt_srv_info(sph_rt_srv *srv, sph_rt_srv_info_t *info);
 void sph_rt_srv_destroy(sph_rt_srv *srv);
 
 /* ------------------------------------------------------------------------ */
-/* Batched form: many small problems advanced by one kernel launch per step. */
-/* Each problem gets one thread block that runs its whole step (material     */
-/* data, assembly, material solves and Chebyshev-preconditioned CG with      */
-/* block-local reductions, per-problem convergence); all problems share the  */
+/* Batched form: many small problems advanced by one persistent launch per  */
+/* step and cluster size.  Each problem gets one thread-block cluster (1 to  */
+/* 8 blocks, by its size) that runs its whole step (material data,          */
+/* assembly, material solves and Chebyshev-preconditioned CG with           */
+/* cluster-wide reductions, per-problem convergence); all problems share the */
 /* configuration (physics, tolerances, cheb_degree).  Like serving, this is a */
 /* runtime form around the paper's method, not part of the method itself.    */
 /* ------------------------------------------------------------------------ */
@@ -438,8 +444,55 @@ sph_rt_status sph_rt_batch_step(sph_rt_batch *b, double dt, int32_t *status,
 sph_rt_status sph_rt_batch_run(sph_rt_batch *b, double dt, int32_t steps, int32_t *status,
                                int32_t *outer_total, int32_t *krylov_total);
 
+/* Launch shape of the batched step.  lanes_per_row W: 1, 2, 4 or 8 (a warp
+ * works on 32 / W rows at a time); cheb_degree: 1..16 (1 is a Jacobi
+ * preconditioner); blocks_per_sm: 1 or 2 resident blocks per SM (2 caps the
+ * registers per thread at 64 so that twice as many blocks are in flight);
+ * rows_per_cta: 0, or >= 64 -- a problem of n interior particles runs on a
+ * thread-block cluster of C = 1, 2, 4 or 8 blocks, the smallest power of two
+ * with C * rows_per_cta >= n (at most 8, and at most what the GPU can
+ * co-schedule), each block owning a contiguous share of its rows; 0 gives
+ * every problem one block.  W and blocks_per_sm never change a result; the
+ * degree changes the Krylov path and rows_per_cta the order of the sums
+ * (results then agree to the solver tolerances).  A problem's result depends
+ * on its own data and the shape only, not on the other problems of the batch.
+ * Until set or tuned, W follows the mean row length (4, or 8 above 160
+ * entries), the degree is cfg.cheb_degree, blocks_per_sm is 2 when the batch
+ * has more problems than the GPU has SMs, and rows_per_cta is 4096.  Setting
+ * the shape turns off the automatic tuning of cfg.autotune.  EINVAL for a
+ * value outside those sets. */
+typedef struct {
+  int32_t lanes_per_row, cheb_degree, blocks_per_sm, rows_per_cta;
+} sph_rt_batch_shape;
+sph_rt_status sph_rt_batch_set_shape(sph_rt_batch *b, const sph_rt_batch_shape *shape);
+sph_rt_status sph_rt_batch_get_shape(const sph_rt_batch *b, sph_rt_batch_shape *shape);
+
+/* Autotuner of the batched launch.  Runs one step of size dt of the whole
+ * batch for each candidate shape, each from the current state, which is
+ * restored after every trial (the problems do not advance), times each step
+ * with CUDA events and keeps the fastest shape among those with which every
+ * problem converged (the current shape if none did).  Candidates, in the
+ * order of times_ms: first the 40 shapes blocks_per_sm in {1, 2} (outermost)
+ * x lanes_per_row in {1, 2, 4, 8} x cheb_degree in {1, 2, 3, 4, 6}
+ * (innermost) at the current rows_per_cta, then rows_per_cta in {0, 2048,
+ * 4096, 8192} with the best of those.  times_ms[SPH_RT_BATCH_TUNE_CANDIDATES]
+ * (may be NULL) gets each trial's time in milliseconds, -1 where some problem
+ * did not converge; the chosen shape goes to *chosen (may be NULL) and stays
+ * set.  With cfg.autotune = 1 the first sph_rt_batch_step or sph_rt_batch_run
+ * of a batch whose shape was not set calls it with that call's dt.  The
+ * choice rests on timings, so two batches of the same problems may pick
+ * different shapes. */
+#define SPH_RT_BATCH_TUNE_CANDIDATES 44
+sph_rt_status sph_rt_batch_autotune(sph_rt_batch *b, double dt, float *times_ms,
+                                    sph_rt_batch_shape *chosen);
+
 /* State of one problem, caller order (either may be NULL). */
 sph_rt_status sph_rt_batch_get_energies(sph_rt_batch *b, int32_t index, double *e, double *E);
+
+/* Sizes of problem `index`: info[0] = particles (n_total), info[1] = interior
+ * particles, info[2] = stored off-diagonal operator entries, info[3] =
+ * neighbour-list entries.  EINVAL for an index outside the batch. */
+sph_rt_status sph_rt_batch_problem_info(const sph_rt_batch *b, int32_t index, int64_t info[4]);
 
 int32_t sph_rt_batch_size(const sph_rt_batch *b);
 const char *sph_rt_batch_last_error(const sph_rt_batch *b);

@@ -24,7 +24,11 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sphrt {
 
@@ -53,11 +57,12 @@ struct BatchView {
   int32_t *krylov;   // [K] total Krylov iterations of the step
   double *energy;    // [K*4] before, after, source, boundary
   const int32_t *run_status;  // [K] multi-step run: nonzero = failed earlier, skip (or NULL)
+  const int32_t *order;       // [K] problem of each cluster of the launch, largest first
 };
 
 struct BatchPhys {
   double a, c, cv, p, T_floor, larsen_k, dt, tol_inner, tol_outer_e, tol_outer_E, tol_krylov;
-  int limiter, max_inner, max_outer, max_krylov, cheb_degree;
+  int limiter, max_inner, max_outer, max_krylov, cheb_degree, dim;
 };
 
 __device__ __forceinline__ double b_opacity(double sigma0, double Ts, double p) {
@@ -74,114 +79,249 @@ __device__ __forceinline__ double b_lambda(int limiter, double k, double R) {
   return 1.0 / 3.0;
 }
 
-// block-wide sum / max, result broadcast to every thread
-__device__ __forceinline__ double bsum(double v, double *sh, double *bc) {
-  double s = block_sum(v, sh);
-  if (threadIdx.x == 0) *bc = s;
-  __syncthreads();
-  double out = *bc;
-  __syncthreads();
-  return out;
+// ---------------------------------------------------------------------------
+// Work split.  A problem runs on the C CTAs of one thread-block cluster (C = 1,
+// 2, 4 or 8, by its size): CTA `rank` owns the contiguous interior rows
+// [q0, q1) (chunks of a multiple of 32 rows), slot loops are strided over all
+// C * blockDim threads of the cluster, and every value another CTA reads is
+// published by a cluster barrier (barrier.cluster arrive.release /
+// wait.acquire, which orders global as well as shared memory) before it is
+// read.  Control flow is uniform over the cluster: every branch depends on
+// per-problem data or on cluster-reduced values, which every CTA combines in
+// the same order, so all CTAs reach every barrier.
+// ---------------------------------------------------------------------------
+struct Part {
+  int rank, C;
+  int64_t s0, s1;  // the problem's slots
+  int64_t r0, r1;  // its interior rows
+  int64_t q0, q1;  // this CTA's rows
+  int64_t ct, cn;  // this thread's index in the cluster, threads in the cluster
+};
+
+__device__ __forceinline__ Part make_part(int64_t s0, int64_t s1, int64_t nint, int rank, int C) {
+  Part P;
+  P.rank = rank;
+  P.C = C;
+  P.s0 = s0;
+  P.s1 = s1;
+  P.r0 = s0;
+  P.r1 = s0 + nint;
+  const int64_t chunk = ((nint + C - 1) / C + 31) / 32 * 32;
+  P.q0 = P.r0 + (int64_t)rank * chunk;
+  if (P.q0 > P.r1) P.q0 = P.r1;
+  P.q1 = P.q0 + chunk;
+  if (P.q1 > P.r1) P.q1 = P.r1;
+  P.ct = (int64_t)rank * blockDim.x + threadIdx.x;
+  P.cn = (int64_t)C * blockDim.x;
+  return P;
 }
-__device__ __forceinline__ double bmax(double v, double *sh, double *bc) {
-  double s = block_max(v, sh);
-  if (threadIdx.x == 0) *bc = s;
+
+// Cluster reductions: each warp reduces its values, lane 0 stores them in one
+// of two CTA buffers, after a CTA barrier thread a combines value a over the
+// warps (in warp order) into one of two cluster-visible slots, and after the
+// cluster barrier every thread of the cluster reads the C CTA totals in rank
+// order (distributed shared memory), so all hold the same fixed-order result.
+// The buffers alternate between calls: a buffer is written again two calls
+// later, after the barriers of the call between, which every thread reaches
+// only after it has read the buffer.  All threads make the same calls.
+constexpr int kBRedWarps = 16, kBRedVals = 3;
+struct CRed {
+  double *wbuf;  // shared, [2][kBRedVals][kBRedWarps]
+  double *cbuf;  // shared, [2][kBRedVals], read by the whole cluster
+  int par;
+};
+
+template <int N>
+__device__ __forceinline__ void cred(CRed &R, const Part &P, double (&v)[N],
+                                     const bool (&is_max)[N]) {
+  static_assert(N <= kBRedVals, "too many values in one reduction");
+  cg::cluster_group cl = cg::this_cluster();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int a = 0; a < N; ++a) v[a] = is_max[a] ? warp_max(v[a]) : warp_sum(v[a]);
+  double *wb = R.wbuf + R.par * (kBRedVals * kBRedWarps);
+  double *cb = R.cbuf + R.par * kBRedVals;
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < N; ++a) wb[a * kBRedWarps + wid] = v[a];
+  }
   __syncthreads();
-  double out = *bc;
+  if (threadIdx.x < N) {
+    const int a = threadIdx.x;
+    double s = wb[a * kBRedWarps];
+    for (int w = 1; w < nw; ++w) {
+      const double t = wb[a * kBRedWarps + w];
+      s = is_max[a] ? fmax(s, t) : s + t;
+    }
+    cb[a] = s;
+  }
+  cl.sync();
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    double s = *cl.map_shared_rank(cb + a, 0);
+    for (int r = 1; r < P.C; ++r) {
+      const double t = *cl.map_shared_rank(cb + a, r);
+      s = is_max[a] ? fmax(s, t) : s + t;
+    }
+    v[a] = s;
+  }
+  R.par ^= 1;
+}
+__device__ __forceinline__ double csum(CRed &R, const Part &P, double x) {
+  double v[1] = {x};
+  const bool m[1] = {false};
+  cred<1>(R, P, v, m);
+  return v[0];
+}
+// barrier over the cluster, publishing every earlier write to all its CTAs
+__device__ __forceinline__ void csync() { cg::this_cluster().sync(); }
+
+// num / den computed by one thread of each CTA (identical inputs in every CTA
+// of the cluster, so identical results) and broadcast with one CTA barrier;
+// an FP64 division costs tens of FP64-pipe operations per warp.  Alternating
+// slots, as in cred.
+__device__ __forceinline__ double bdiv(double num, double den, double *bc, int &par) {
+  if (threadIdx.x == 0) bc[par] = num / den;
   __syncthreads();
+  const double out = bc[par];
+  par ^= 1;
   return out;
 }
 
-// y = B xin over the block's rows (W lanes per row); mode 0: y = B xin,
-// mode 1: y = rhs - B xin.  Ends with __syncthreads.
+// Row dot product of the batched kernel: the values and x are written earlier
+// in the same launch by other threads, so they are read with plain (coherent)
+// loads, not through the read-only path; the columns are read-only.  Same
+// order of operations as row_dot.
 template <int W, int U>
-__device__ void b_spmv(const BatchView &v, int64_t r0, int64_t r1, const double *xin,
-                       const double *rhs, double *y, int mode) {
+__device__ __forceinline__ double b_row_dot(int64_t beg, int64_t end, const int32_t *col,
+                                            const double *val, const double *x, int sub) {
+  double s = 0.0;
+  for (int64_t k = beg + sub; k < end; k += (int64_t)W * U) {
+    int32_t c[U];
+    double a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t kk = k + (int64_t)u * W;
+      c[u] = kk < end ? __ldg(col + kk) : -1;
+      a[u] = kk < end ? val[kk] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (c[u] >= 0) s = fma(a[u], x[c[u]], s);
+  }
+  return s;
+}
+
+// Operator sweep over this CTA's rows (W lanes per row, U entries in flight
+// per lane).  MODE 0: y = B xin, returns this thread's part of (xin, y);
+// MODE 1: y = rhs - B xin, returns its part of ||y / V||^2.  No barrier at the
+// end: the reduction that follows is the barrier before y is read.
+template <int W, int U, int MODE>
+__device__ __forceinline__ double b_spmv(const BatchView &v, const Part &P, const double *xin,
+                                         const double *rhs, double *y) {
   const int sub = threadIdx.x % W;
   const int grp = threadIdx.x / W, ngrp = blockDim.x / W;
-  for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
+  double part = 0.0;
+  for (int64_t wb = P.q0 + warp_first_group<W>(grp); wb < P.q1; wb += ngrp) {
     const int64_t i = wb + group_in_warp<W>(grp);
-    const bool active = i < r1;
-    double s = active ? row_dot<W, U>(v.mat_ptr[i], v.mat_ptr[i + 1], v.mat_col, v.mat_val, xin, sub)
+    const bool active = i < P.q1;
+    double s = active ? b_row_dot<W, U>(v.mat_ptr[i], v.mat_ptr[i + 1], v.mat_col, v.mat_val, xin, sub)
                       : 0.0;
     s = row_reduce<W>(s);
     if (active && sub == 0) {
-      double bx = v.diag[i] * xin[i] + s;
-      y[i] = mode ? rhs[i] - bx : bx;
+      const double bx = v.diag[i] * xin[i] + s;
+      if (MODE == 0) {
+        y[i] = bx;
+        part += xin[i] * bx;
+      } else {
+        const double yi = rhs[i] - bx;
+        y[i] = yi;
+        const double yu = yi * v.invV[i];
+        part += yu * yu;
+      }
     }
   }
-  __syncthreads();
+  return part;
 }
 
-// Chebyshev preconditioner z = p(D^{-1}B) D^{-1} r on [lo, hi], zero guess;
-// ping-pong between z and v.t, result in z.  Ends with __syncthreads.
+// Chebyshev preconditioner z = p(D^{-1}B) D^{-1} r on [lo, hi], zero guess, on
+// this CTA's rows; ping-pong between z and v.t, result in z.  Returns this
+// thread's part of (r, z); no barrier at the end (the reduction of (r, z) is
+// the barrier).
 template <int W, int U>
-__device__ void b_cheb(const BatchView &v, int64_t r0, int64_t r1, const double *r, double *z,
-                       const ChebCoef &cf) {
+__device__ double b_cheb(const BatchView &v, const Part &P, const double *r, double *z,
+                         const ChebCoef &cf) {
   const int degree = cf.degree;
   double *buf[2] = {z, v.t};
   int at = (degree - 1) % 2;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    double di = cf.inv_theta * v.invdiag[i] * r[i];
+  double rz = 0.0;
+  for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
+    const double di = cf.inv_theta * v.invdiag[i] * r[i];
     v.d[i] = di;
     buf[at][i] = di;
+    if (degree == 1) rz += r[i] * di;
   }
-  __syncthreads();
   const int sub = threadIdx.x % W;
   const int grp = threadIdx.x / W, ngrp = blockDim.x / W;
   for (int k = 1; k < degree; ++k) {
+    csync();  // the previous iterate, all rows of the problem
     const double c1 = cf.c1[k], c2 = cf.c2[k];
     const double *zin = buf[at];
     double *zout = buf[at ^ 1];
-    for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
+    const bool last = k == degree - 1;
+    for (int64_t wb = P.q0 + warp_first_group<W>(grp); wb < P.q1; wb += ngrp) {
       const int64_t i = wb + group_in_warp<W>(grp);
-      const bool active = i < r1;
-      double s = active ? row_dot<W, U>(v.mat_ptr[i], v.mat_ptr[i + 1], v.mat_col, v.mat_val, zin,
-                                        sub)
+      const bool active = i < P.q1;
+      double s = active ? b_row_dot<W, U>(v.mat_ptr[i], v.mat_ptr[i + 1], v.mat_col, v.mat_val,
+                                          zin, sub)
                         : 0.0;
       s = row_reduce<W>(s);
       if (active && sub == 0) {
-        double res = r[i] - (v.diag[i] * zin[i] + s);
-        double di = c1 * v.d[i] + c2 * v.invdiag[i] * res;
+        const double res = r[i] - (v.diag[i] * zin[i] + s);
+        const double di = c1 * v.d[i] + c2 * v.invdiag[i] * res;
         v.d[i] = di;
-        zout[i] = zin[i] + di;
+        const double zi = zin[i] + di;
+        zout[i] = zi;
+        if (last) rz += r[i] * zi;
       }
     }
-    __syncthreads();
     at ^= 1;
   }
+  return rz;
 }
 
-// num / den computed once and broadcast (one FP64 division per block, not per thread)
-__device__ __forceinline__ double bdiv(double num, double den, double *bc) {
-  if (threadIdx.x == 0) *bc = num / den;
-  __syncthreads();
-  double out = *bc;
-  __syncthreads();
-  return out;
-}
-
-template <int W, int U>
-__global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys ph) {
-  __shared__ double sh[32];
-  __shared__ double bc;
-  const int k = blockIdx.x;
-  if (k >= v.K) return;
+// MINB resident blocks per SM: 1 leaves the compiler ~128 registers a thread,
+// 2 caps it at 64 (a few spilled values in the limiter and opacity code) so
+// that twice as many CTAs are in flight; the arithmetic is the same.  Launched
+// with a cluster dimension C (1, 2, 4 or 8): cluster c runs problem
+// v.order[c] on its C CTAs.
+template <int W, int U, int MINB>
+__global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, BatchPhys ph) {
+  __shared__ double wred[2 * kBRedVals * kBRedWarps];
+  __shared__ double cred_slots[2 * kBRedVals];
+  __shared__ double bc[2];
+  __shared__ ChebCoef cf;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int cid = blockIdx.x / C;  // clusters are C consecutive blocks
+  if (cid >= v.K) return;          // the grid is exactly v.K clusters: never taken
+  const int k = v.order[cid];
   if (v.run_status && v.run_status[k] != 0) return;  // failed in an earlier step of the run
-  const int64_t s0 = v.slot_off[k], s1 = v.slot_off[k + 1];
-  const int64_t r0 = s0, r1 = s0 + v.n_int[k];
+  CRed R{wred, cred_slots, 0};
+  int bpar = 0;
+  const Part P = make_part(v.slot_off[k], v.slot_off[k + 1], v.n_int[k], (int)cl.block_rank(), C);
   const int sub = threadIdx.x % W;
   const int grp = threadIdx.x / W, ngrp = blockDim.x / W;
 
-  // energy before
+  // a3: material data from the state at the start of the step (every slot but
+  // copy ghosts), energy before; Eg = E at each slot's value source (a copy
+  // ghost's interior particle)
   double ea = 0.0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x)
-    ea += v.rho[i] * v.V[i] * v.e[i] + v.V[i] * v.E[i];
-  const double energy_before = bsum(ea, sh, &bc);
-
-  // a3: material data from the state at the start of the step
-  for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-    if (v.kind[i] == SPH_RT_COPY) continue;
+  for (int64_t i = P.s0 + P.ct; i < P.s1; i += P.cn) {
+    const bool copy = v.kind[i] == SPH_RT_COPY;
+    v.t[i] = v.E[copy ? v.copysrc[i] : i];
+    if (copy) continue;
+    if (i < P.r1) ea += v.rho[i] * v.V[i] * v.e[i] + v.V[i] * v.E[i];
     double Ti = v.e[i] / ph.cv;
     double Ts = Ti > ph.T_floor ? Ti : ph.T_floor;
     double sig = b_opacity(v.sigma0[i], Ts, ph.p);
@@ -193,22 +333,35 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
     v.lam[i] = l0;
     v.D[i] = ph.c * l0 / sig;
   }
-  __syncthreads();
+  const double energy_before = csum(R, P, ea);  // also the barrier after a3
   if (ph.limiter != SPH_RT_LIMITER_NONE) {
-    for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
+    const double *Eg = v.t;
+    const bool d3 = ph.dim == 3;
+    for (int64_t wb = P.q0 + warp_first_group<W>(grp); wb < P.q1; wb += ngrp) {
       const int64_t i = wb + group_in_warp<W>(grp);
-      const bool active = i < r1;
-      const int64_t ia = active ? i : r0;
-      double xi = v.px[ia], yi = v.py[ia], zi = v.pz[ia], Ei = v.E[ia];
+      const bool active = i < P.q1;
+      const int64_t ia = active ? i : P.r0;
+      const double xi = v.px[ia], yi = v.py[ia], zi = v.pz[ia], Ei = v.E[ia];
       double gx = 0.0, gy = 0.0, gz = 0.0;
       const int64_t kb = active ? v.nbr_ptr[i] : 0, ke = active ? v.nbr_ptr[i + 1] : 0;
-      for (int64_t kk = kb + sub; kk < ke; kk += W) {
-        int32_t j = v.nbr_col[kk];
-        int32_t js = v.kind[j] == SPH_RT_COPY ? v.copysrc[j] : j;
-        double s = v.V[j] * (v.E[js] - Ei) * v.nbr_F[kk];
-        gx += s * (xi - v.px[j]);
-        gy += s * (yi - v.py[j]);
-        gz += s * (zi - v.pz[j]);
+      for (int64_t kk = kb + sub; kk < ke; kk += (int64_t)W * U) {
+        int32_t jj[U];
+        double F[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t q = kk + (int64_t)u * W;
+          jj[u] = q < ke ? __ldg(v.nbr_col + q) : -1;
+          F[u] = q < ke ? __ldg(v.nbr_F + q) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (jj[u] < 0) continue;
+          const int32_t j = jj[u];
+          const double s = v.V[j] * (Eg[j] - Ei) * F[u];
+          gx += s * (xi - v.px[j]);
+          gy += s * (yi - v.py[j]);
+          if (d3) gz += s * (zi - v.pz[j]);  // 2-D: z = 0 everywhere
+        }
       }
       gx = row_reduce<W>(gx);
       gy = row_reduce<W>(gy);
@@ -223,9 +376,9 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
         v.D[i] = ph.c * l / v.sigma[i];
       }
     }
-    __syncthreads();
+    csync();  // the copy ghosts read their sources' D
   }
-  for (int64_t i = r1 + threadIdx.x; i < s1; i += blockDim.x) {
+  for (int64_t i = P.r1 + P.ct; i < P.s1; i += P.cn) {
     int32_t c = v.copysrc[i];
     if (c < 0) continue;
     v.T[i] = v.T[c];
@@ -235,19 +388,32 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
     v.lam[i] = v.lam[c];
     v.D[i] = v.D[c];
   }
-  __syncthreads();
+  csync();  // the assembly reads D at every neighbour
 
   // a4: operator values, diagonal, Dirichlet coupling, Gershgorin bound
   double gmax = 0.0;
-  for (int64_t wb = r0 + warp_first_group<W>(grp); wb < r1; wb += ngrp) {
+  for (int64_t wb = P.q0 + warp_first_group<W>(grp); wb < P.q1; wb += ngrp) {
     const int64_t i = wb + group_in_warp<W>(grp);
-    const bool active = i < r1;
-    double Di = active ? v.D[i] : 0.0, off = 0.0;
+    const bool active = i < P.q1;
+    const double Di = active ? v.D[i] : 0.0;
+    double off = 0.0;
     const int64_t mb = active ? v.mat_ptr[i] : 0, me = active ? v.mat_ptr[i + 1] : 0;
-    for (int64_t kk = mb + sub; kk < me; kk += W) {
-      double val = v.mat_G[kk] * (Di + v.D[v.mat_col[kk]]);
-      v.mat_val[kk] = val;
-      off += val;
+    for (int64_t kk = mb + sub; kk < me; kk += (int64_t)W * U) {
+      int32_t jj[U];
+      double G[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t q = kk + (int64_t)u * W;
+        jj[u] = q < me ? __ldg(v.mat_col + q) : -1;
+        G[u] = q < me ? __ldg(v.mat_G + q) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (jj[u] < 0) continue;
+        const double val = G[u] * (Di + v.D[jj[u]]);
+        v.mat_val[kk + (int64_t)u * W] = val;
+        off += val;
+      }
     }
     double wsum = 0.0, gbs = 0.0;
     const int64_t hb = active ? v.gh_ptr[i] : 0, he = active ? v.gh_ptr[i + 1] : 0;
@@ -268,40 +434,46 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
       gmax = fmax(gmax, -off / dd);
     }
   }
-  const double gersh = bmax(gmax, sh, &bc);
-  __shared__ ChebCoef cf;
-  if (threadIdx.x == 0) cheb_coefficients(ph.cheb_degree, 1.0 - gersh, 1.0 + gersh, &cf);
-  __syncthreads();
+  // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}
+  for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
+    v.e_old[i] = v.e[i];
+    v.E_old[i] = v.E[i];
+    v.E_l[i] = v.E[i];
+  }
+  {
+    double m[1] = {gmax};
+    const bool mx[1] = {true};
+    cred<1>(R, P, m, mx);
+    if (threadIdx.x == 0) cheb_coefficients(ph.cheb_degree, 1.0 - m[0], 1.0 + m[0], &cf);
+  }
+  // (cf is read after the next barrier: the material solve's reduction)
 
-  // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}, material solve with E^{n,0}
+  // per-particle nonlinear elimination on this CTA's rows; returns the two
+  // convergence measures of the problem
   auto newton = [&](const double *E_new, const double *E_prev, const double *e_start,
                     double *e_out, double &ce, double &cE) {
-    double mce = 0.0, mcE = 0.0;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    double mc[2] = {0.0, 0.0};
+    for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
       double cs = ph.c * v.sigma[i];
-      double P = cs * E_new[i] + v.Qe[i];
+      double Pw = cs * E_new[i] + v.Qe[i];
       double rdt = v.rho[i] / ph.dt, eo = v.e_old[i], e0 = e_start[i], ei = e0;
       for (int it = 0; it < ph.max_inner; ++it) {
         double T = ei / ph.cv, T3 = T * T * T;
-        double u = rdt * (ei - eo) + cs * ph.a * T3 * T - P;
+        double u = rdt * (ei - eo) + cs * ph.a * T3 * T - Pw;
         double J = rdt + 4.0 * cs * ph.a * T3 / ph.cv;
         double de = u / J;
         ei -= de;
         if (fabs(de) <= ph.tol_inner * fabs(ei)) break;
       }
       e_out[i] = ei;
-      mce = fmax(mce, fabs(ei - e0) / fmax(fabs(ei), 1e-300));
-      mcE = fmax(mcE, fabs(E_new[i] - E_prev[i]) / fmax(fabs(E_new[i]), 1e-300));
+      mc[0] = fmax(mc[0], fabs(ei - e0) / fmax(fabs(ei), 1e-300));
+      mc[1] = fmax(mc[1], fabs(E_new[i] - E_prev[i]) / fmax(fabs(E_new[i]), 1e-300));
     }
-    ce = bmax(mce, sh, &bc);
-    cE = bmax(mcE, sh, &bc);
+    const bool mx[2] = {true, true};
+    cred<2>(R, P, mc, mx);
+    ce = mc[0];
+    cE = mc[1];
   };
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    v.e_old[i] = v.e[i];
-    v.E_old[i] = v.E[i];
-    v.E_l[i] = v.E[i];
-  }
-  __syncthreads();
   double ce = 0.0, cE = 0.0;
   newton(v.E_l, v.E_l, v.e_old, v.e_l, ce, cE);
 
@@ -309,7 +481,7 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
   while (outer < ph.max_outer) {
     // a7: right-hand side (B-scaled), warm start, ||b||
     double bb = 0.0;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
       double Tl = v.e_l[i] / ph.cv;
       double cs = ph.c * v.sigma[i];
       double bi = v.E_old[i] / ph.dt + cs * ph.a * Tl * Tl * Tl * Tl - (1.0 - v.f[i]) * cs * v.E_l[i] +
@@ -318,56 +490,40 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
       v.x[i] = v.E_l[i];
       bb += bi * bi;
     }
-    const double thresh2 = ph.tol_krylov * ph.tol_krylov * bsum(bb, sh, &bc);
+    const double thresh2 = ph.tol_krylov * ph.tol_krylov * csum(R, P, bb);
     // a6: Chebyshev-preconditioned CG on B
-    b_spmv<W, U>(v, r0, r1, v.x, v.b, v.r, 1);
-    double rr = 0.0;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      double ru = v.r[i] * v.invV[i];
-      rr += ru * ru;
-    }
-    rr = bsum(rr, sh, &bc);
+    double rr = csum(R, P, b_spmv<W, U, 1>(v, P, v.x, v.b, v.r));
     int it = 0;
     bool kconv = rr <= thresh2;
     if (!kconv) {
-      b_cheb<W, U>(v, r0, r1, v.r, v.z, cf);
-      double rz = 0.0;
-      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        v.p[i] = v.z[i];
-        rz += v.r[i] * v.z[i];
-      }
-      double rho_k = bsum(rz, sh, &bc);
-      b_spmv<W, U>(v, r0, r1, v.p, nullptr, v.q, 0);
+      double rho_k = csum(R, P, b_cheb<W, U>(v, P, v.r, v.z, cf));
+      for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) v.p[i] = v.z[i];
+      csync();  // p at every neighbour
+      double pq = csum(R, P, b_spmv<W, U, 0>(v, P, v.p, nullptr, v.q));
       while (it < ph.max_krylov) {
-        double pq = 0.0;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) pq += v.p[i] * v.q[i];
-        pq = bsum(pq, sh, &bc);
         if (!(pq > 0.0) || !(pq < 1e308)) break;  // breakdown
-        double alpha = bdiv(rho_k, pq, &bc);
+        const double alpha = bdiv(rho_k, pq, bc, bpar);
         rr = 0.0;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
           v.x[i] += alpha * v.p[i];
           double ri = v.r[i] - alpha * v.q[i];
           v.r[i] = ri;
           double ru = ri * v.invV[i];
           rr += ru * ru;
         }
-        rr = bsum(rr, sh, &bc);
+        rr = csum(R, P, rr);
         ++it;
         if (rr <= thresh2) {
           kconv = true;
           break;
         }
-        b_cheb<W, U>(v, r0, r1, v.r, v.z, cf);
-        rz = 0.0;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) rz += v.r[i] * v.z[i];
-        double rho_new = bsum(rz, sh, &bc);
-        double beta = bdiv(rho_new, rho_k, &bc);
+        const double rho_new = csum(R, P, b_cheb<W, U>(v, P, v.r, v.z, cf));
+        const double beta = bdiv(rho_new, rho_k, bc, bpar);
         rho_k = rho_new;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x)
+        for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x)
           v.p[i] = v.z[i] + beta * v.p[i];
-        __syncthreads();
-        b_spmv<W, U>(v, r0, r1, v.p, nullptr, v.q, 0);
+        csync();  // p at every neighbour
+        pq = csum(R, P, b_spmv<W, U, 0>(v, P, v.p, nullptr, v.q));
       }
     }
     kry_total += it;
@@ -375,7 +531,7 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
     // a8 + a9: material solve with the new radiation energy, convergence test
     newton(v.x, v.E_l, v.e_l, v.e_new, ce, cE);
     ++outer;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
       v.e_l[i] = v.e_new[i];
       v.E_l[i] = v.x[i];
     }
@@ -386,41 +542,40 @@ __global__ void __launch_bounds__(512) batch_step_kernel(BatchView v, BatchPhys 
     }
   }
   if (status == 0) {
-    double src = 0.0, bnd = 0.0, after = 0.0;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    double tot[3] = {0.0, 0.0, 0.0};  // source, boundary, after
+    for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
       v.e[i] = v.e_l[i];
       v.E[i] = v.E_l[i];
-      src += v.V[i] * (v.Qe[i] + v.QE[i]);
+      tot[0] += v.V[i] * (v.Qe[i] + v.QE[i]);
       double acc = 0.0;
       for (int64_t kk = v.gh_ptr[i]; kk < v.gh_ptr[i + 1]; ++kk) {
         int32_t j = v.gh_slot[kk];
         acc += -v.gh_W[kk] * (v.D[i] + v.D[j]) * (v.E[j] - v.E_l[i]);
       }
-      bnd += v.V[i] * acc;
-      after += v.rho[i] * v.V[i] * v.e_l[i] + v.V[i] * v.E_l[i];
+      tot[1] += v.V[i] * acc;
+      tot[2] += v.rho[i] * v.V[i] * v.e_l[i] + v.V[i] * v.E_l[i];
     }
-    __syncthreads();
-    for (int64_t i = r1 + threadIdx.x; i < s1; i += blockDim.x) {
+    const bool mx[3] = {false, false, false};
+    cred<3>(R, P, tot, mx);  // also the barrier before the copy ghosts read e, E
+    for (int64_t i = P.r1 + P.ct; i < P.s1; i += P.cn) {
       int32_t c = v.copysrc[i];
       if (c < 0) continue;
       v.e[i] = v.e[c];
       v.E[i] = v.E[c];
     }
-    src = bsum(src, sh, &bc);
-    bnd = bsum(bnd, sh, &bc);
-    after = bsum(after, sh, &bc);
-    if (threadIdx.x == 0) {
+    if (P.rank == 0 && threadIdx.x == 0) {
       v.energy[4 * k + 0] = energy_before;
-      v.energy[4 * k + 1] = after;
-      v.energy[4 * k + 2] = ph.dt * src;
-      v.energy[4 * k + 3] = ph.dt * bnd;
+      v.energy[4 * k + 1] = tot[2];
+      v.energy[4 * k + 2] = ph.dt * tot[0];
+      v.energy[4 * k + 3] = ph.dt * tot[1];
     }
   }
-  if (threadIdx.x == 0) {
+  if (P.rank == 0 && threadIdx.x == 0) {
     v.status[k] = status;
     v.outer[k] = outer;
     v.krylov[k] = kry_total;
   }
+  csync();  // no CTA leaves while another may still read its reduction slots
 }
 
 // ---------------------------------------------------------------------------
@@ -457,6 +612,11 @@ __global__ void offset_i32_kernel(const int32_t *in, int64_t n, int32_t off, int
 
 using namespace sphrt;
 
+sph_rt_status ensure_cuda(sph_rt *s);
+
+constexpr int kClusterKinds = 4;  // cluster sizes 1, 2, 4, 8
+constexpr int kDefaultRowsPerCta = 4096;
+
 struct BatchItem {
   int64_t n = 0, n_int = 0, nnz_nbr = 0, nnz_mat = 0, nnz_gh = 0;
   std::vector<int64_t> slot2caller;
@@ -472,13 +632,28 @@ struct sph_rt_batch {
   int64_t *d_slot_off = nullptr, *d_nint = nullptr;
   int32_t *d_status = nullptr, *d_outer = nullptr, *d_krylov = nullptr;
   double *d_energy = nullptr;
-  int W = 16, U = 6;
+  // launch shape: lanes per row W (32 / W rows per warp), Chebyshev degree and
+  // resident blocks per SM; from the mean row length, cfg.cheb_degree and the
+  // batch size, set by the caller, or tuned
+  int W = 4, degree = 1, blocks_per_sm = 1;
+  // rows per CTA: a problem of n interior rows runs on a cluster of
+  // C = pow2ceil(n / rows_per_cta) CTAs (at most max_cluster); 0 = one CTA each
+  int rows_per_cta = kDefaultRowsPerCta, max_cluster = 8;
+  // problems grouped by cluster size (1, 2, 4, 8): one launch per group, the
+  // groups' launches on forked streams so that they run side by side
+  int32_t *d_order = nullptr;  // [K] problems of group 0, then group 1, ...
+  int cls_off[kClusterKinds] = {}, cls_cnt[kClusterKinds] = {};
+  int cls_split = -1;  // rows_per_cta the groups were built for
+  cudaStream_t side[kClusterKinds - 1] = {};
+  cudaEvent_t fork = nullptr, join[kClusterKinds - 1] = {};
+  bool shape_set = false, tuned = false;
+  double *d_e_save = nullptr, *d_E_save = nullptr;  // state kept across tuning trials
   // multi-step runs (sph_rt_batch_run): accumulators and the captured graph
   int32_t *d_run_status = nullptr, *d_run_outer = nullptr, *d_run_krylov = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   double graph_dt = 0.0;
-  int32_t graph_steps = 0;
+  int32_t graph_steps = 0, graph_W = 0, graph_degree = 0, graph_bps = 0, graph_split = -1;
   int64_t graph_kernels = 0;
 };
 
@@ -502,6 +677,7 @@ extern "C" sph_rt_status sph_rt_batch_create(const sph_rt_config *cfg, sph_rt_ba
   }
   B->h = h;
   B->cfg = *cfg;
+  B->degree = h->cfg.cheb_degree;
   *out = B;
   return SPH_RT_OK;
 }
@@ -537,19 +713,15 @@ extern "C" sph_rt_status sph_rt_batch_add(sph_rt_batch *B, int64_t n_total, cons
   return SPH_RT_OK;
 }
 
+static int max_cluster_for(int bps);
+
 static sph_rt_status batch_pack(sph_rt_batch *B) {
   sph_rt *s = B->h;
   const int K = (int)B->items.size();
   if (K == 0) return set_error(s, SPH_RT_ESTATE, "empty batch");
   if (K > 65535) return set_error(s, SPH_RT_EINVAL, "too many problems in one batch");
-  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
-  if (!s->cuda_ready) {
-    // the packed handle needs its stream and host mirror
-    SPH_CUDA(s, cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
-    s->own_stream = true;
-    SPH_CUDA(s, cudaMallocHost(&s->sc_host, sizeof(Scalars)));
-    s->cuda_ready = true;
-  }
+  sph_rt_status rc0 = ensure_cuda(s);  // the packed handle's stream, host mirror, SM count
+  if (rc0) return rc0;
   int64_t n_all = 0, nb = 0, nm = 0, ng = 0;
   std::vector<int64_t> so(K + 1), nint(K), nbo(K), nmo(K), ngo(K);
   for (int k = 0; k < K; ++k) {
@@ -587,6 +759,13 @@ static sph_rt_status batch_pack(sph_rt_batch *B) {
   B->d_outer = dalloc<int32_t>(s, K);
   B->d_krylov = dalloc<int32_t>(s, K);
   B->d_energy = D(4 * (size_t)K);
+  B->d_order = dalloc<int32_t>(s, K);
+  if (!B->d_order) return SPH_RT_ENOMEM;
+  for (int c = 0; c < kClusterKinds - 1; ++c)
+    SPH_CUDA(s, cudaStreamCreateWithFlags(&B->side[c], cudaStreamNonBlocking));
+  SPH_CUDA(s, cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+  for (int c = 0; c < kClusterKinds - 1; ++c)
+    SPH_CUDA(s, cudaEventCreateWithFlags(&B->join[c], cudaEventDisableTiming));
   if (!kind || !copysrc || !nbr_ptr || !mat_ptr || !gh_ptr || !nbr_col || !mat_col ||
       !gh_slot || !nbr_F || !mat_G || !mat_val || !gh_W || !B->d_slot_off || !B->d_nint ||
       !B->d_status || !B->d_outer || !B->d_krylov || !B->d_energy)
@@ -657,11 +836,15 @@ static sph_rt_status batch_pack(sph_rt_batch *B) {
   v.outer = B->d_outer;
   v.krylov = B->d_krylov;
   v.energy = B->d_energy;
+  v.order = B->d_order;
   int64_t ni_all = 0;
   for (int k = 0; k < K; ++k) ni_all += nint[k];
-  RowShape sh = shape_for_mean(ni_all ? (double)nm / (double)ni_all : 0.0);
-  B->W = sh.W;
-  B->U = sh.U;
+  B->max_cluster = std::min(max_cluster_for(1), max_cluster_for(2));
+  if (!B->shape_set) {
+    B->W = lanes_for_mean(ni_all ? (double)nm / (double)ni_all : 0.0);
+    // more problems than SMs: two blocks per SM keep them all in flight
+    B->blocks_per_sm = K > s->num_sms ? 2 : 1;
+  }
   s->n = n_all;
   B->packed = true;
   return SPH_RT_OK;
@@ -716,18 +899,257 @@ static BatchPhys batch_phys(const sph_rt_batch *B, double dt) {
   ph.max_inner = c.max_inner_e;
   ph.max_outer = c.max_outer;
   ph.max_krylov = c.max_krylov;
-  ph.cheb_degree = c.cheb_degree;
+  ph.cheb_degree = B->degree;
+  ph.dim = c.dim;
   return ph;
 }
 
+static bool batch_lanes_ok(int W) { return W == 1 || W == 2 || W == 4 || W == 8; }
+
+template <int W, int MINB>
+static cudaError_t launch_cluster(const BatchView &v, const BatchPhys &ph, int C, cudaStream_t st) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)v.K * (unsigned)C);
+  lc.blockDim = dim3(512);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, batch_step_kernel<W, 8, MINB>, v, ph);
+}
+
+template <int MINB>
+static cudaError_t launch_cluster_w(int W, const BatchView &v, const BatchPhys &ph, int C,
+                                    cudaStream_t st) {
+  if (W == 1) return launch_cluster<1, MINB>(v, ph, C, st);
+  if (W == 2) return launch_cluster<2, MINB>(v, ph, C, st);
+  if (W == 4) return launch_cluster<4, MINB>(v, ph, C, st);
+  return launch_cluster<8, MINB>(v, ph, C, st);
+}
+
+// Largest cluster (<= 8) of which at least one fits on the GPU with this
+// kernel variant's registers (1 or 2 CTAs per SM).
+static int max_cluster_for(int bps) {
+  int best = 1;
+  for (int C = 2; C <= 8; C *= 2) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)C);
+    lc.blockDim = dim3(512);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int n = 0;
+    cudaError_t e = bps == 2 ? cudaOccupancyMaxActiveClusters(&n, batch_step_kernel<4, 8, 2>, &lc)
+                             : cudaOccupancyMaxActiveClusters(&n, batch_step_kernel<4, 8, 1>, &lc);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    if (n < 1) break;
+    best = C;
+  }
+  return best;
+}
+
+// Cluster size of a problem of n interior rows.
+static int cluster_of(int64_t n, int rows_per_cta, int max_cluster) {
+  if (rows_per_cta <= 0) return 1;
+  int C = 1;
+  while (C < max_cluster && (int64_t)C * rows_per_cta < n) C *= 2;
+  return C;
+}
+
+// Group the problems by cluster size (each group largest first, ties by
+// index) and upload the launch order.  A problem's cluster size depends on
+// its own size only, so its result does not depend on the rest of the batch.
+static sph_rt_status batch_groups(sph_rt_batch *B) {
+  if (B->cls_split == B->rows_per_cta) return SPH_RT_OK;
+  sph_rt *s = B->h;
+  const int K = (int)B->items.size();
+  std::vector<int32_t> order;
+  order.reserve(K);
+  for (int g = 0; g < kClusterKinds; ++g) {
+    const int C = 1 << g;
+    std::vector<int32_t> mem;
+    for (int k = 0; k < K; ++k)
+      if (cluster_of(B->items[k].n_int, B->rows_per_cta, B->max_cluster) == C) mem.push_back(k);
+    auto work = [&](int k) { return B->items[k].nnz_mat + 4 * B->items[k].n_int; };
+    std::stable_sort(mem.begin(), mem.end(), [&](int a, int b) { return work(a) > work(b); });
+    B->cls_off[g] = (int)order.size();
+    B->cls_cnt[g] = (int)mem.size();
+    order.insert(order.end(), mem.begin(), mem.end());
+  }
+  SPH_CUDA(s, cudaMemcpyAsync(B->d_order, order.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice,
+                              s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  B->cls_split = B->rows_per_cta;
+  return SPH_RT_OK;
+}
+
+// One batched step: a launch per cluster-size group.  The first group runs on
+// the batch's stream, the others on side streams forked from it and joined
+// back, so the groups overlap (also inside a captured graph: parallel
+// branches).
+// The groups must be current (batch_groups) before the call, which may be
+// inside a stream capture.
 static sph_rt_status launch_batch_step(sph_rt_batch *B, const BatchView &v, const BatchPhys &ph) {
   sph_rt *s = B->h;
-  if (B->W <= 4)
-    batch_step_kernel<4, 8><<<v.K, 512, 0, s->stream>>>(v, ph);
-  else
-    batch_step_kernel<8, 8><<<v.K, 512, 0, s->stream>>>(v, ph);
-  SPH_LAUNCHED(s);
+  int used[kClusterKinds], nu = 0;
+  for (int g = 0; g < kClusterKinds; ++g)
+    if (B->cls_cnt[g] > 0) used[nu++] = g;
+  if (nu > 1) {
+    SPH_CUDA(s, cudaEventRecord(B->fork, s->stream));
+    for (int a = 1; a < nu; ++a) SPH_CUDA(s, cudaStreamWaitEvent(B->side[a - 1], B->fork, 0));
+  }
+  for (int a = 0; a < nu; ++a) {
+    const int g = used[a];
+    BatchView vg = v;
+    vg.K = B->cls_cnt[g];
+    vg.order = B->d_order + B->cls_off[g];
+    cudaStream_t st = a == 0 ? s->stream : B->side[a - 1];
+    cudaError_t e = B->blocks_per_sm == 2 ? launch_cluster_w<2>(B->W, vg, ph, 1 << g, st)
+                                          : launch_cluster_w<1>(B->W, vg, ph, 1 << g, st);
+    SPH_CUDA(s, e);
+    SPH_LAUNCHED(s);
+  }
+  for (int a = 1; a < nu; ++a) {
+    SPH_CUDA(s, cudaEventRecord(B->join[a - 1], B->side[a - 1]));
+    SPH_CUDA(s, cudaStreamWaitEvent(s->stream, B->join[a - 1], 0));
+  }
   return SPH_RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the batched launch: lanes per row W (32 / W rows per warp),
+// the Chebyshev degree, resident blocks per SM, and rows per CTA (how large
+// a cluster each problem gets).  The degree trades Krylov iterations (fewer
+// as the polynomial gets stronger) against operator sweeps per iteration, W
+// trades idle lanes on short rows against more rows per reduction, two blocks
+// per SM trade spilled registers against CTAs in flight, and smaller row
+// chunks trade cluster barriers against the time of the largest problem,
+// which bounds the step; none of these balances is known before the batch's
+// operators are.  Every candidate runs one step from the same state (restored
+// after each trial, so the tuning leaves the problems where they were) and is
+// timed with CUDA events on the batch's stream; a candidate counts only if
+// every problem converged, and the fastest one is kept.  The first three
+// dimensions are searched as a grid at the current rows per CTA, then the
+// rows per CTA at the best of them.  A first untimed launch of each kernel
+// variant takes module loading and cold caches out of the comparison.
+// ---------------------------------------------------------------------------
+static const int kTuneBlocks[] = {1, 2};
+static const int kTuneLanes[] = {1, 2, 4, 8};
+static const int kTuneDegrees[] = {1, 2, 3, 4, 6};
+static const int kTuneRows[] = {0, 2048, 4096, 8192};
+constexpr int kNB = 2, kNW = 4, kND = 5, kNR = 4;
+static_assert(kNB * kNW * kND + kNR == SPH_RT_BATCH_TUNE_CANDIDATES,
+              "candidate table and header disagree");
+
+static sph_rt_status batch_restore(sph_rt_batch *B) {
+  sph_rt *s = B->h;
+  const size_t bytes = sizeof(double) * (size_t)s->n;
+  SPH_CUDA(s, cudaMemcpyAsync(B->view.e, B->d_e_save, bytes, cudaMemcpyDeviceToDevice, s->stream));
+  SPH_CUDA(s, cudaMemcpyAsync(B->view.E, B->d_E_save, bytes, cudaMemcpyDeviceToDevice, s->stream));
+  return SPH_RT_OK;
+}
+
+static sph_rt_status batch_autotune(sph_rt_batch *B, double dt, float *times_ms) {
+  sph_rt *s = B->h;
+  const int K = B->view.K;
+  const size_t bytes = sizeof(double) * (size_t)s->n;
+  if (!B->d_e_save) {
+    B->d_e_save = dalloc<double>(s, s->n);
+    B->d_E_save = dalloc<double>(s, s->n);
+    if (!B->d_e_save || !B->d_E_save) return SPH_RT_ENOMEM;
+  }
+  SPH_CUDA(s, cudaMemcpyAsync(B->d_e_save, B->view.e, bytes, cudaMemcpyDeviceToDevice, s->stream));
+  SPH_CUDA(s, cudaMemcpyAsync(B->d_E_save, B->view.E, bytes, cudaMemcpyDeviceToDevice, s->stream));
+  BatchView v = B->view;
+  v.run_status = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  SPH_CUDA(s, cudaEventCreate(&ev[0]));
+  if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return set_error(s, SPH_RT_EDEVICE, "autotune: cudaEventCreate failed");
+  }
+  std::vector<int32_t> st(K);
+  float best = -1.0f;
+  int bestW = B->W, bestDeg = B->degree, bestB = B->blocks_per_sm, bestR = B->rows_per_cta;
+  const int deg0 = B->degree;
+  sph_rt_status rc = SPH_RT_OK;
+  // one timed trial of the current shape; ms < 0 if some problem did not converge
+  auto trial = [&](float *slot) -> sph_rt_status {
+    sph_rt_status r2;
+    if ((r2 = batch_groups(B))) return r2;
+    float ms = -1.0f;
+    if (cudaEventRecord(ev[0], s->stream) != cudaSuccess ||
+        (r2 = launch_batch_step(B, v, batch_phys(B, dt))) ||
+        cudaEventRecord(ev[1], s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(st.data(), B->d_status, sizeof(int32_t) * K, cudaMemcpyDeviceToHost,
+                        s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess)
+      return r2 ? r2 : set_error(s, SPH_RT_EDEVICE, "autotune: CUDA error in a trial");
+    bool ok = true;
+    for (int k = 0; k < K; ++k) ok = ok && st[k] == 0;
+    if (slot) *slot = ok ? ms : -1.0f;
+    if (ok && (best < 0.0f || ms < best)) {
+      best = ms;
+      bestW = B->W;
+      bestDeg = B->degree;
+      bestB = B->blocks_per_sm;
+      bestR = B->rows_per_cta;
+    }
+    return batch_restore(B);
+  };
+  for (int c = 0; c < kNB * kNW && !rc; ++c) {
+    B->blocks_per_sm = kTuneBlocks[c / kNW];
+    B->W = kTuneLanes[c % kNW];
+    B->degree = deg0;
+    if ((rc = batch_groups(B)) || (rc = launch_batch_step(B, v, batch_phys(B, dt))) ||
+        (rc = batch_restore(B)))
+      break;
+    for (int d = 0; d < kND && !rc; ++d) {
+      B->degree = kTuneDegrees[d];
+      rc = trial(times_ms ? times_ms + c * kND + d : nullptr);
+    }
+  }
+  for (int r = 0; r < kNR && !rc; ++r) {
+    B->W = bestW;
+    B->degree = bestDeg;
+    B->blocks_per_sm = bestB;
+    B->rows_per_cta = kTuneRows[r];
+    rc = trial(times_ms ? times_ms + kNB * kNW * kND + r : nullptr);
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  B->W = bestW;
+  B->degree = bestDeg;
+  B->blocks_per_sm = bestB;
+  B->rows_per_cta = bestR;
+  B->tuned = true;
+  if (rc) return rc;
+  if ((rc = batch_groups(B))) return rc;
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  return SPH_RT_OK;
+}
+
+// pack on first use, then tune once if the configuration asks for it
+static sph_rt_status batch_ready(sph_rt_batch *B, double dt) {
+  sph_rt_status rc;
+  if (!B->packed && (rc = batch_pack(B))) return rc;
+  SPH_CUDA(B->h, cudaSetDevice(B->h->cfg.device));
+  if (B->cfg.autotune && !B->tuned && !B->shape_set && (rc = batch_autotune(B, dt, nullptr)))
+    return rc;
+  return batch_groups(B);
 }
 
 extern "C" sph_rt_status sph_rt_batch_run(sph_rt_batch *B, double dt, int32_t steps,
@@ -737,9 +1159,8 @@ extern "C" sph_rt_status sph_rt_batch_run(sph_rt_batch *B, double dt, int32_t st
   if (!isfinite(dt) || dt <= 0.0) return set_error(B->h, SPH_RT_EINVAL, "dt must be finite and > 0");
   if (steps < 1) return set_error(B->h, SPH_RT_EINVAL, "steps must be >= 1");
   sph_rt_status rc;
-  if (!B->packed && (rc = batch_pack(B))) return rc;
+  if ((rc = batch_ready(B, dt))) return rc;
   sph_rt *s = B->h;
-  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
   const int K = B->view.K;
   if (!B->d_run_status) {
     B->d_run_status = dalloc<int32_t>(s, K);
@@ -747,7 +1168,9 @@ extern "C" sph_rt_status sph_rt_batch_run(sph_rt_batch *B, double dt, int32_t st
     B->d_run_krylov = dalloc<int32_t>(s, K);
     if (!B->d_run_status || !B->d_run_outer || !B->d_run_krylov) return SPH_RT_ENOMEM;
   }
-  if (!B->graph_exec || B->graph_dt != dt || B->graph_steps != steps) {
+  if (!B->graph_exec || B->graph_dt != dt || B->graph_steps != steps || B->graph_W != B->W ||
+      B->graph_degree != B->degree || B->graph_bps != B->blocks_per_sm ||
+      B->graph_split != B->rows_per_cta) {
     batch_graph_release(B);
     BatchView v = B->view;
     v.run_status = B->d_run_status;
@@ -785,6 +1208,10 @@ extern "C" sph_rt_status sph_rt_batch_run(sph_rt_batch *B, double dt, int32_t st
     SPH_CUDA(s, cudaGraphInstantiate(&B->graph_exec, g, 0));
     B->graph_dt = dt;
     B->graph_steps = steps;
+    B->graph_W = B->W;
+    B->graph_degree = B->degree;
+    B->graph_bps = B->blocks_per_sm;
+    B->graph_split = B->rows_per_cta;
   }
   SPH_CUDA(s, cudaGraphLaunch(B->graph_exec, s->stream));
   s->launches += B->graph_kernels;
@@ -809,9 +1236,8 @@ extern "C" sph_rt_status sph_rt_batch_step(sph_rt_batch *B, double dt, int32_t *
   if (!B) return SPH_RT_EINVAL;
   if (!isfinite(dt) || dt <= 0.0) return set_error(B->h, SPH_RT_EINVAL, "dt must be finite and > 0");
   sph_rt_status rc;
-  if (!B->packed && (rc = batch_pack(B))) return rc;
+  if ((rc = batch_ready(B, dt))) return rc;
   sph_rt *s = B->h;
-  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
   const int K = B->view.K;
   BatchView v = B->view;
   v.run_status = nullptr;
@@ -858,6 +1284,57 @@ extern "C" sph_rt_status sph_rt_batch_get_energies(sph_rt_batch *B, int32_t inde
   return SPH_RT_OK;
 }
 
+extern "C" sph_rt_status sph_rt_batch_set_shape(sph_rt_batch *B, const sph_rt_batch_shape *shape) {
+  if (!B || !shape) return SPH_RT_EINVAL;
+  if (!batch_lanes_ok(shape->lanes_per_row))
+    return set_error(B->h, SPH_RT_EINVAL, "lanes_per_row must be 1, 2, 4 or 8");
+  if (shape->cheb_degree < 1 || shape->cheb_degree > 16)
+    return set_error(B->h, SPH_RT_EINVAL, "cheb_degree must be in [1, 16]");
+  if (shape->blocks_per_sm != 1 && shape->blocks_per_sm != 2)
+    return set_error(B->h, SPH_RT_EINVAL, "blocks_per_sm must be 1 or 2");
+  if (shape->rows_per_cta < 0 || (shape->rows_per_cta > 0 && shape->rows_per_cta < 64))
+    return set_error(B->h, SPH_RT_EINVAL, "rows_per_cta must be 0 or >= 64");
+  B->W = shape->lanes_per_row;
+  B->degree = shape->cheb_degree;
+  B->blocks_per_sm = shape->blocks_per_sm;
+  B->rows_per_cta = shape->rows_per_cta;
+  B->shape_set = true;
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_batch_get_shape(const sph_rt_batch *B, sph_rt_batch_shape *shape) {
+  if (!B || !shape) return SPH_RT_EINVAL;
+  shape->lanes_per_row = B->W;
+  shape->cheb_degree = B->degree;
+  shape->blocks_per_sm = B->blocks_per_sm;
+  shape->rows_per_cta = B->rows_per_cta;
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_batch_autotune(sph_rt_batch *B, double dt, float *times_ms,
+                                               sph_rt_batch_shape *chosen) {
+  if (!B) return SPH_RT_EINVAL;
+  if (!isfinite(dt) || dt <= 0.0) return set_error(B->h, SPH_RT_EINVAL, "dt must be finite and > 0");
+  sph_rt_status rc;
+  if (!B->packed && (rc = batch_pack(B))) return rc;
+  SPH_CUDA(B->h, cudaSetDevice(B->h->cfg.device));
+  if ((rc = batch_autotune(B, dt, times_ms))) return rc;
+  B->shape_set = true;
+  return chosen ? sph_rt_batch_get_shape(B, chosen) : SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_batch_problem_info(const sph_rt_batch *B, int32_t index,
+                                                   int64_t info[4]) {
+  if (!B || !info) return SPH_RT_EINVAL;
+  if (index < 0 || index >= (int32_t)B->items.size()) return SPH_RT_EINVAL;
+  const BatchItem &it = B->items[index];
+  info[0] = it.n;
+  info[1] = it.n_int;
+  info[2] = it.nnz_mat;
+  info[3] = it.nnz_nbr;
+  return SPH_RT_OK;
+}
+
 extern "C" int32_t sph_rt_batch_size(const sph_rt_batch *B) {
   return B ? (int32_t)B->items.size() : 0;
 }
@@ -868,9 +1345,15 @@ extern "C" const char *sph_rt_batch_last_error(const sph_rt_batch *B) {
 
 extern "C" void sph_rt_batch_destroy(sph_rt_batch *B) {
   if (!B) return;
-  if (B->graph_exec || B->graph) {
+  if (B->graph_exec || B->graph || B->fork) {
     cudaSetDevice(B->h->cfg.device);
+    if (B->h->cuda_ready) cudaStreamSynchronize(B->h->stream);
     batch_graph_release(B);
+    for (int c = 0; c < kClusterKinds - 1; ++c) {
+      if (B->side[c]) cudaStreamDestroy(B->side[c]);
+      if (B->join[c]) cudaEventDestroy(B->join[c]);
+    }
+    if (B->fork) cudaEventDestroy(B->fork);
   }
   for (sph_rt *t : B->staging)
     if (t) sph_rt_destroy(t);

@@ -98,6 +98,10 @@ struct sph_rt_srv {
   double t_first = 0, t_last = 0;
   int64_t total_particle_steps = 0;
   int64_t fused_requests = 0, fused_batches = 0;
+  // launch shapes tuned by earlier fused batches (cfg.autotune), keyed by the
+  // batch key's configuration bytes and dt: a later fused batch of the same
+  // key reuses the shape instead of tuning again
+  std::map<std::string, sph_rt_batch_shape> batch_shapes;
 };
 
 namespace {
@@ -262,6 +266,18 @@ void run_fused(sph_rt_srv *S, std::vector<std::shared_ptr<Request>> &group) {
     }
     return;
   }
+  std::string shape_key;
+  bool shape_known = false;
+  if (c.autotune) {
+    sph_rt_config kc = c;
+    kc.device = 0;
+    const double dt = group[0]->dt;
+    shape_key.assign(reinterpret_cast<const char *>(&kc), sizeof kc);
+    shape_key.append(reinterpret_cast<const char *>(&dt), sizeof dt);
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->batch_shapes.find(shape_key);
+    if (it != S->batch_shapes.end()) shape_known = sph_rt_batch_set_shape(B, &it->second) == 0;
+  }
   std::vector<std::shared_ptr<Request>> members;
   std::vector<int32_t> index;
   for (auto &R : group) {
@@ -286,6 +302,13 @@ void run_fused(sph_rt_srv *S, std::vector<std::shared_ptr<Request>> &group) {
     std::vector<int32_t> st(K, 0), ou(K, 0), kr(K, 0);
     rc = sph_rt_batch_run(B, members[0]->dt, members[0]->steps, st.data(), ou.data(), kr.data());
     const bool hard = rc != SPH_RT_OK && rc != SPH_RT_ENOTCONV;
+    if (c.autotune && !shape_known && !hard) {
+      sph_rt_batch_shape sh;
+      if (sph_rt_batch_get_shape(B, &sh) == 0) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->batch_shapes.emplace(shape_key, sh);
+      }
+    }
     const std::string msg = rc ? sph_rt_batch_last_error(B) : "";
     for (size_t m = 0; m < members.size(); ++m) {
       auto &R = members[m];

@@ -273,7 +273,7 @@ extern "C" sph_rt_status sph_rt_create(const sph_rt_config *cfg, sph_rt **out) {
   return SPH_RT_OK;
 }
 
-static sph_rt_status ensure_cuda(sph_rt *s) {
+sph_rt_status ensure_cuda(sph_rt *s) {
   if (s->cuda_ready) return SPH_RT_OK;
   SPH_CUDA(s, cudaSetDevice(s->cfg.device));
   int sms = 0;

@@ -24,6 +24,14 @@ LIMITER_NONE, LIMITER_LEVERMORE, LIMITER_LARSEN = 0, 1, 2
 PRECOND_JACOBI, PRECOND_CHEBYSHEV, PRECOND_AMG = 0, 1, 2
 FP64, MIXED = 0, 1
 M4_SPLINE, WENDLAND_C4 = 0, 1
+# candidate shapes of sph_rt_batch_autotune: a grid, outermost first, then the
+# rows per CTA (SPH_RT_BATCH_TUNE_CANDIDATES = 2 x 4 x 5 + 4)
+BATCH_TUNE_BLOCKS = (1, 2)
+BATCH_TUNE_LANES = (1, 2, 4, 8)
+BATCH_TUNE_DEGREES = (1, 2, 3, 4, 6)
+BATCH_TUNE_ROWS = (0, 2048, 4096, 8192)
+BATCH_TUNE_CANDIDATES = (len(BATCH_TUNE_BLOCKS) * len(BATCH_TUNE_LANES) * len(BATCH_TUNE_DEGREES)
+                         + len(BATCH_TUNE_ROWS))
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ENOTCONV: "ENOTCONV", EDEVICE: "EDEVICE",
           ESTATE: "ESTATE"}
 
@@ -144,7 +152,11 @@ _SIGNATURES = [
     ("sph_rt_batch_set_sources", C.c_int, [_P, C.c_int32, _P, _P]),
     ("sph_rt_batch_step", C.c_int, [_P, C.c_double, _P, _P, _P, _P]),
     ("sph_rt_batch_run", C.c_int, [_P, C.c_double, C.c_int32, _P, _P, _P]),
+    ("sph_rt_batch_set_shape", C.c_int, [_P, _P]),
+    ("sph_rt_batch_get_shape", C.c_int, [_P, _P]),
+    ("sph_rt_batch_autotune", C.c_int, [_P, C.c_double, _P, _P]),
     ("sph_rt_batch_get_energies", C.c_int, [_P, C.c_int32, _P, _P]),
+    ("sph_rt_batch_problem_info", C.c_int, [_P, C.c_int32, _P]),
     ("sph_rt_batch_size", C.c_int32, [_P]),
     ("sph_rt_batch_last_error", C.c_char_p, [_P]),
     ("sph_rt_batch_destroy", None, [_P]),
@@ -508,6 +520,12 @@ class Server:
             pass
 
 
+class BatchShape(C.Structure):
+    """sph_rt_batch_shape."""
+    _fields_ = [("lanes_per_row", C.c_int32), ("cheb_degree", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("rows_per_cta", C.c_int32)]
+
+
 class Batch:
     """Many small problems, one kernel launch per step (sph_rt_batch_* in sph_rt.h)."""
 
@@ -566,6 +584,56 @@ class Batch:
         if raise_on_error:
             self._check(rc)
         return rc, st, ou, kr
+
+    def set_shape(self, lanes_per_row, cheb_degree, blocks_per_sm=1, rows_per_cta=4096):
+        """Lanes per row (1, 2, 4, 8), Chebyshev degree (1..16), resident blocks
+        per SM (1, 2) and rows per CTA (0 = one block per problem, else >= 64) of
+        the batched launch."""
+        sh = BatchShape(int(lanes_per_row), int(cheb_degree), int(blocks_per_sm),
+                        int(rows_per_cta))
+        self._check(self._L.sph_rt_batch_set_shape(self._h, C.byref(sh)))
+
+    def get_shape(self):
+        """(lanes_per_row, cheb_degree, blocks_per_sm, rows_per_cta)."""
+        sh = BatchShape()
+        self._check(self._L.sph_rt_batch_get_shape(self._h, C.byref(sh)))
+        return sh.lanes_per_row, sh.cheb_degree, sh.blocks_per_sm, sh.rows_per_cta
+
+    def autotune(self, dt):
+        """Time one step per candidate shape (the state does not advance); returns the
+        chosen (lanes_per_row, cheb_degree, blocks_per_sm, rows_per_cta) and
+        {shape: ms, or None if some problem did not converge}."""
+        t = np.zeros(BATCH_TUNE_CANDIDATES, dtype=np.float32)
+        sh = BatchShape()
+        rows0 = self.get_shape()[3]
+        self._check(self._L.sph_rt_batch_autotune(self._h, float(dt), _ptr(t), C.byref(sh)))
+        table = {}
+        c = 0
+        best = None
+        for b in BATCH_TUNE_BLOCKS:
+            for w in BATCH_TUNE_LANES:
+                for g in BATCH_TUNE_DEGREES:
+                    ms = float(t[c])
+                    table[(w, g, b, rows0)] = ms if ms >= 0 else None
+                    if ms >= 0 and (best is None or ms < best[0]):
+                        best = (ms, w, g, b)
+                    c += 1
+        if best is not None:
+            for r in BATCH_TUNE_ROWS:
+                ms = float(t[c])
+                key = (best[1], best[2], best[3], r)
+                if key not in table or table[key] is None or (ms >= 0 and ms < table[key]):
+                    table[key] = ms if ms >= 0 else None
+                c += 1
+        chosen = (sh.lanes_per_row, sh.cheb_degree, sh.blocks_per_sm, sh.rows_per_cta)
+        return chosen, table
+
+    def problem_info(self, index):
+        """{n_total, n_interior, nnz_operator, nnz_neighbours} of one problem."""
+        a = np.zeros(4, dtype=np.int64)
+        self._check(self._L.sph_rt_batch_problem_info(self._h, int(index), _ptr(a)))
+        return dict(n_total=int(a[0]), n_interior=int(a[1]), nnz_operator=int(a[2]),
+                    nnz_neighbours=int(a[3]))
 
     def get_energies(self, index):
         n = self._n[index]

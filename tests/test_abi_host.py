@@ -128,3 +128,22 @@ def test_no_interior_particle():
                         np.ones(P.n))
     assert "interior" in str(ei.value)
     S.close()
+
+
+@pytest.mark.parametrize("shape", [(3, 1, 1, 0), (16, 1, 1, 0), (0, 1, 1, 0), (4, 0, 1, 0),
+                                   (4, 17, 1, 0), (4, 2, 0, 0), (4, 2, 3, 0), (4, 2, 1, -1),
+                                   (4, 2, 1, 63)])
+def test_batch_rejects_bad_shape(shape):
+    B = sphrt.Batch(sphrt.default_config())
+    with pytest.raises(sphrt.SphRtError) as ex:
+        B.set_shape(*shape)
+    assert ex.value.status == sphrt.EINVAL
+    B.set_shape(2, 6, 2, 2048)
+    assert B.get_shape() == (2, 6, 2, 2048)
+    B.close()
+
+
+def test_batch_tune_table_matches_header():
+    src = open(HEADER).read()
+    m = re.search(r"#define SPH_RT_BATCH_TUNE_CANDIDATES (\d+)", src)
+    assert m and int(m.group(1)) == sphrt.BATCH_TUNE_CANDIDATES == 44

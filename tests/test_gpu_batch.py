@@ -1,6 +1,7 @@
-"""Batched form: many small problems in one launch per step.  Each problem's
-result is the same alone (a batch of one) and in the batch, and matches the
-CPU oracle."""
+"""Batched form: many small problems in one launch per step and cluster size.
+Each problem's result is the same alone (a batch of one) and in the batch, for
+every launch shape it matches the CPU oracle, and the autotuner leaves the
+state where it was."""
 import numpy as np
 import pytest
 
@@ -84,3 +85,105 @@ def test_batch_with_sources_matches_single_problem_path():
     m = w.particles.kind == 0
     assert np.max(np.abs(eb[m] - es[m]) / np.abs(es[m])) < 1e-10
     assert np.max(np.abs(Eb[m] - Es[m]) / np.abs(Es[m])) < 1e-10
+
+
+def _state(B, K):
+    return [B.get_energies(k) for k in range(K)]
+
+
+def test_batch_blocks_per_sm_do_not_change_a_bit():
+    probs = _problems(3, k=4, seed=62)
+    cfg = sphrt.config_from_params(probs[0].params, **TIGHT)
+    out = []
+    for bps in (1, 2):
+        B = sphrt.Batch(cfg)
+        for w in probs:
+            B.add(w.particles, w.e0, w.E0)
+        B.set_shape(4, 2, bps, 512)
+        B.run(probs[0].dt, 3)
+        out.append(_state(B, len(probs)))
+        B.close()
+    for (e1, E1), (e2, E2) in zip(*out):
+        assert np.array_equal(e1, e2) and np.array_equal(E1, E2)
+
+
+# rows per CTA 64..2048 put these problems (500..6000 particles) on clusters
+# of 1 to 8 blocks; 0 gives each one block
+@pytest.mark.parametrize("shape", [(2, 1, 1, 0), (8, 3, 2, 256), (4, 6, 1, 2048), (1, 2, 1, 64),
+                                   (1, 1, 2, 1024)])
+def test_batch_shapes_match_the_oracle(shape):
+    probs = _problems(2, k=3, seed=63)
+    cfg = sphrt.config_from_params(probs[0].params, **TIGHT)
+    B = sphrt.Batch(cfg)
+    for w in probs:
+        B.add(w.particles, w.e0, w.E0)
+    B.set_shape(*shape)
+    rc, st, ou, kr = B.run(probs[0].dt, 2)
+    assert np.all(st == 0)
+    for k, w in enumerate(probs):
+        pb = O.Problem(w.particles, dict(w.params, **TIGHT))
+        e, E = w.e0.copy(), w.E0.copy()
+        for _ in range(2):
+            rc2, e, E, _ = pb.step(e, E, w.dt)
+            assert rc2 == 0
+        eg, Eg = B.get_energies(k)
+        m = w.particles.kind == 0
+        assert np.max(np.abs(eg[m] - e[m]) / np.abs(e[m])) < 1e-10
+        assert np.max(np.abs(Eg[m] - E[m]) / np.abs(E[m])) < 1e-10
+    B.close()
+
+
+def test_batch_autotune_keeps_the_state_and_picks_a_converged_shape():
+    probs = _problems(3, k=6, seed=64)
+    cfg = sphrt.config_from_params(probs[0].params, **TIGHT)
+    B = sphrt.Batch(cfg)
+    for w in probs:
+        B.add(w.particles, w.e0, w.E0)
+    before = _state(B, len(probs))
+    chosen, table = B.autotune(probs[0].dt)
+    # the rows-per-CTA sweep repeats one shape of the grid
+    assert len(table) == sphrt.BATCH_TUNE_CANDIDATES - 1
+    assert table[chosen] is not None
+    assert all(t is None or t >= table[chosen] for t in table.values())
+    assert B.get_shape() == chosen
+    for (e1, E1), (e2, E2) in zip(before, _state(B, len(probs))):
+        assert np.array_equal(e1, e2) and np.array_equal(E1, E2)
+    # the tuned shape stays set: a run with it equals a fresh batch set to it
+    B.run(probs[0].dt, 2)
+    A = sphrt.Batch(cfg)
+    for w in probs:
+        A.add(w.particles, w.e0, w.E0)
+    A.set_shape(*chosen)
+    A.run(probs[0].dt, 2)
+    for (e1, E1), (e2, E2) in zip(_state(A, len(probs)), _state(B, len(probs))):
+        assert np.array_equal(e1, e2) and np.array_equal(E1, E2)
+    A.close()
+    B.close()
+
+
+def test_config_autotune_tunes_on_the_first_run():
+    probs = _problems(2, k=4, seed=65)
+    cfg = sphrt.config_from_params(probs[0].params, autotune=1, **TIGHT)
+    B = sphrt.Batch(cfg)
+    for w in probs:
+        B.add(w.particles, w.e0, w.E0)
+    rc, st, ou, kr = B.run(probs[0].dt, 2)
+    assert np.all(st == 0)
+    W, deg, bps, rows = B.get_shape()
+    assert W in sphrt.BATCH_TUNE_LANES and deg in sphrt.BATCH_TUNE_DEGREES and bps in (1, 2)
+    assert rows in sphrt.BATCH_TUNE_ROWS
+    ref = sphrt.Batch(sphrt.config_from_params(probs[0].params, **TIGHT))
+    for w in probs:
+        ref.add(w.particles, w.e0, w.E0)
+    ref.run(probs[0].dt, 2)
+    for k, w in enumerate(probs):
+        m = w.particles.kind == 0
+        (e1, E1), (e2, E2) = B.get_energies(k), ref.get_energies(k)
+        assert np.max(np.abs(e1[m] - e2[m]) / np.abs(e2[m])) < 1e-10
+        assert np.max(np.abs(E1[m] - E2[m]) / np.abs(E2[m])) < 1e-10
+    info = B.problem_info(0)
+    assert info["n_total"] == probs[0].particles.n
+    assert info["n_interior"] == probs[0].particles.n_interior
+    assert info["nnz_operator"] > info["n_interior"] and info["nnz_neighbours"] > 0
+    ref.close()
+    B.close()
