@@ -334,16 +334,19 @@ def batch_problems(k: int, seed: int = 7):
             for d in descs]
 
 
-def batch_bytes(info, outer, krylov, degree, steps):
+def batch_bytes(info, dim, krylov, degree, steps):
     """Algorithmic bytes of one batched run of `steps` steps of one problem:
-    every operator sweep (the CG product and the residual, and degree - 1 sweeps
-    inside each Chebyshev application: outer + degree * krylov sweeps in all)
-    streams the operator's values and columns once (12 B an entry) and 32 B per
-    row (row pointer, diagonal, the row's own x, y written); every step's
-    assembly reads G and the columns and writes the values (20 B an entry) and
-    its limiter gradient reads the neighbour columns and kernel factors (12 B)."""
+    every operator sweep (one residual a step -- later outer iterations take
+    the residual from the B x the CG carries -- and degree sweeps a Krylov
+    iteration: the CG product and degree - 1 inside the Chebyshev
+    application) streams the operator's values and columns once (12 B an
+    entry) and 32 B per row (row pointer, diagonal, the row's own x, y
+    written); every step's assembly reads G and the columns and writes the
+    values (20 B an entry) and its limiter gradient reads the neighbour
+    columns and the dim per-pair weights (4 + 8 dim B an entry)."""
     nnz, ni, nbr = info["nnz_operator"], info["n_interior"], info["nnz_neighbours"]
-    return (outer + degree * krylov) * (12 * nnz + 32 * ni) + steps * (20 * nnz + 12 * nbr)
+    return ((steps + degree * krylov) * (12 * nnz + 32 * ni)
+            + steps * (20 * nnz + (4 + 8 * dim) * nbr))
 
 
 def run_batch(args):
@@ -361,7 +364,8 @@ def run_batch(args):
 
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    stream = torch.cuda.Stream(device=local)
+    streams = {d: torch.cuda.Stream(device=local) for d in (2, 3)}
+    stream = streams[3]
     probs = batch_problems(args.batch_k)
     groups = {d: [w for w in probs if w.particles.dim == d] for d in (2, 3)}
     groups = {d: g for d, g in groups.items() if g}
@@ -371,7 +375,7 @@ def run_batch(args):
 
     def make(d, shape=None):
         g = groups[d]
-        cfg = sphrt.config_from_params(g[0].params, device=local, stream=stream.cuda_stream)
+        cfg = sphrt.config_from_params(g[0].params, device=local, stream=streams[d].cuda_stream)
         B = sphrt.Batch(cfg)
         for w in g:
             B.add(w.particles, w.e0, w.E0)
@@ -385,23 +389,43 @@ def run_batch(args):
     tuned, tables, tune_s = {}, {}, {}
     for d, B in batches.items():
         t0 = time.perf_counter()
-        tuned[d], tables[d] = B.autotune(dt)
+        if args.batch_shape:
+            B.set_shape(*[int(a) for a in args.batch_shape.split(",")])
+            tuned[d], tables[d] = B.get_shape(), {}
+        else:
+            tuned[d], tables[d] = B.autotune(dt)
         tune_s[d] = time.perf_counter() - t0
     infos = {d: [B.problem_info(k) for k in range(len(groups[d]))] for d, B in batches.items()}
     ps_run = sum(i["n_interior"] * T for d in infos for i in infos[d])
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(batches) + 1)]
+    # the batches run side by side, each on its own stream from its own host
+    # thread (the library's calls release the interpreter lock), as the serving
+    # loop's workers run fused batches; the run's time is from a start event
+    # both streams wait on to the later of the two end events
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev_end = {d: torch.cuda.Event(enable_timing=True) for d in batches}
 
     def one_run():
-        with torch.cuda.stream(stream):
+        main = streams[3]
+        with torch.cuda.stream(main):
             flush.zero_()  # inputs are larger than L2, and L2 is flushed between runs
+        ev0.record(main)
+        for d in batches:
+            streams[d].wait_event(ev0)
         res = {}
-        ev[0].record(stream)
-        for a, (d, B) in enumerate(batches.items()):
-            rc, st, ou, kr = B.run(dt, T)
-            ev[a + 1].record(stream)
+
+        def go(d):
+            rc, st, ou, kr = batches[d].run(dt, T)
+            ev_end[d].record(streams[d])
             res[d] = (st, ou, kr)
-        stream.synchronize()
-        ms = {d: ev[a].elapsed_time(ev[a + 1]) for a, d in enumerate(batches)}
+
+        th = [threading.Thread(target=go, args=(d,)) for d in batches]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for d in batches:
+            streams[d].synchronize()
+        ms = {d: ev0.elapsed_time(ev_end[d]) for d in batches}
         return res, ms
 
     for _ in range(args.warmup):
@@ -410,36 +434,37 @@ def run_batch(args):
     clocks.start()
     runs = [one_run() for _ in range(args.steps)]
     clk = clocks.stop()
-    ms_tot = [sum(ms.values()) for _, ms in runs]
+    ms_tot = [max(ms.values()) for _, ms in runs]
     t_ms = statistics.mean(ms_tot)
     t_max, work = aggregate_ranks(t_ms * 1e-3 * args.steps, ps_run * args.steps)
     per_dim = {}
-    byt_all, ms_all = 0.0, 0.0
+    byt_all = 0.0
     for d in batches:
         deg = tuned[d][1]
         byt = []
         for res, ms in runs:
             st, ou, kr = res[d]
             assert np.all(st == 0), f"batched {d}-D run did not converge"
-            byt.append(sum(batch_bytes(infos[d][k], int(ou[k]), int(kr[k]), deg, T)
+            byt.append(sum(batch_bytes(infos[d][k], d, int(kr[k]), deg, T)
                            for k in range(len(groups[d]))))
         mean_ms = statistics.mean(ms[d] for _, ms in runs)
         mean_b = statistics.mean(byt)
         byt_all += mean_b
-        ms_all += mean_ms
         res0 = runs[-1][0][d]
         per_dim[f"{d}d"] = {
             "problems": len(groups[d]),
             "interior_particles": sum(i["n_interior"] for i in infos[d]),
+            "problems_per_cluster_size": {str(c): sum(i["cluster"] == c for i in infos[d])
+                                          for c in (1, 2, 4, 8)},
             "operator_entries": sum(i["nnz_operator"] for i in infos[d]),
             "shape": dict(zip(("lanes_per_row", "cheb_degree", "blocks_per_sm", "rows_per_cta"),
                               tuned[d])),
             "autotune_s": tune_s[d],
             "autotune_ms": {f"W{k[0]}-deg{k[1]}-b{k[2]}-r{k[3]}": v for k, v in tables[d].items()},
-            "ms_per_run": mean_ms, "gbs": mean_b / (mean_ms * 1e-3) / 1e9,
+            "ms_to_end": mean_ms, "gbs_own_time": mean_b / (mean_ms * 1e-3) / 1e9,
             "outer_per_step": float(np.mean(res0[1])) / T,
             "krylov_per_step": float(np.mean(res0[2])) / T}
-    achieved = byt_all / (ms_all * 1e-3) / 1e9
+    achieved = byt_all / (t_ms * 1e-3) / 1e9  # both batches' bytes over the run's time
     value = work / t_max
 
     # end to end through the public API from host arrays: set-up of every problem
@@ -486,18 +511,22 @@ def run_batch(args):
             "config": {"workload": f"batched serving problems: {args.batch_k} heating-wave "
                                    "problems, 2-D/3-D, 1k..20k particles, one batch per "
                                    f"dimension, {T} steps of dt = {dt:g} per run",
-                       "step": "one CUDA-graph run of each batch (20 batched-step launches)",
+                       "step": "one CUDA-graph run of each batch (20 steps), the two batches "
+                               "side by side on two streams",
                        "l2": "flushed between runs (a 258 MB write)",
                        "setup_s": setup_s},
             "batches": per_dim,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None,
-                         "kernel": "batch_step_kernel (graph run time, 20 launches)",
+                         "kernel": "batch_step_kernel (the two batches' graph runs, side by "
+                                   "side: run time from the common start to the later end)",
                          "peak_source": peak_src},
             "e2e": {"value": ps_run / e2e_s, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "includes": "set-up of every problem from host arrays, the runs, results"},
-            "gpu_launches": args.steps * len(batches) * 2 * T, "clocks": clk,
+            "gpu_launches": args.steps * T * sum(
+                1 + len({i["cluster"] for i in infos[d]}) for d in batches),
+            "clocks": clk,
             "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
@@ -552,6 +581,8 @@ def main():
     ap.add_argument("--requests", type=int, default=512, help="serving: number of requests")
     ap.add_argument("--batch-k", type=int, default=512,
                     help="batch: number of problems (both dimensions)")
+    ap.add_argument("--batch-shape", default=None,
+                    help="batch: W,degree,blocks_per_sm,rows_per_cta instead of the autotuner")
     ap.add_argument("--workers", type=int, default=8, help="serving: worker threads")
     ap.add_argument("--max-resident", type=int, default=32, help="serving: resident cap")
     args = ap.parse_args()

@@ -491,8 +491,11 @@ sph_rt_status sph_rt_batch_get_energies(sph_rt_batch *b, int32_t index, double *
 
 /* Sizes of problem `index`: info[0] = particles (n_total), info[1] = interior
  * particles, info[2] = stored off-diagonal operator entries, info[3] =
- * neighbour-list entries.  EINVAL for an index outside the batch. */
-sph_rt_status sph_rt_batch_problem_info(const sph_rt_batch *b, int32_t index, int64_t info[4]);
+ * neighbour-list entries, info[4] = blocks of the cluster it runs on with the
+ * current shape (valid once the batch has stepped or been tuned: the GPU's
+ * largest co-schedulable cluster is known then).  EINVAL for an index
+ * outside the batch. */
+sph_rt_status sph_rt_batch_problem_info(const sph_rt_batch *b, int32_t index, int64_t info[5]);
 
 int32_t sph_rt_batch_size(const sph_rt_batch *b);
 const char *sph_rt_batch_last_error(const sph_rt_batch *b);

@@ -42,7 +42,7 @@ struct BatchView {
   const double *Qe, *QE;  // packed slot order (interior entries used)
   const int64_t *nbr_ptr;  // [n_all + 1], ghost rows empty
   const int32_t *nbr_col;
-  const double *nbr_F;
+  const double *nbr_A;  // [3][nnz_nbr]: F_ij V_j (x_i - x_j), the limiter gradient's weights
   const int64_t *mat_ptr;
   const int32_t *mat_col;
   const double *mat_G;
@@ -52,16 +52,19 @@ struct BatchView {
   const double *gh_W;
   double *T, *sigma, *f, *R, *lam, *D, *diag, *invdiag, *gb, *b, *x, *r, *z, *p, *q, *d, *t;
   double *e_old, *E_old, *e_l, *E_l, *e_new;
+  double *y;  // B x, kept through the CG updates for the next outer iteration's residual
   int32_t *status;   // [K] 0 ok, -3 not converged
   int32_t *outer;    // [K]
   int32_t *krylov;   // [K] total Krylov iterations of the step
   double *energy;    // [K*4] before, after, source, boundary
   const int32_t *run_status;  // [K] multi-step run: nonzero = failed earlier, skip (or NULL)
   const int32_t *order;       // [K] problem of each cluster of the launch, largest first
+  int64_t nnz_nbr;            // neighbour entries of the whole batch (stride of nbr_A)
 };
 
 struct BatchPhys {
-  double a, c, cv, p, T_floor, larsen_k, dt, tol_inner, tol_outer_e, tol_outer_E, tol_krylov;
+  double a, c, cv, inv_cv, p, T_floor, larsen_k, dt, tol_inner, tol_outer_e, tol_outer_E,
+      tol_krylov;
   int limiter, max_inner, max_outer, max_krylov, cheb_degree, dim;
 };
 
@@ -214,11 +217,12 @@ __device__ __forceinline__ double b_row_dot(int64_t beg, int64_t end, const int3
 
 // Operator sweep over this CTA's rows (W lanes per row, U entries in flight
 // per lane).  MODE 0: y = B xin, returns this thread's part of (xin, y);
-// MODE 1: y = rhs - B xin, returns its part of ||y / V||^2.  No barrier at the
-// end: the reduction that follows is the barrier before y is read.
+// MODE 1: y = rhs - B xin and bx = B xin, returns its part of ||y / V||^2.
+// No barrier at the end: the reduction that follows is the barrier before y
+// is read.
 template <int W, int U, int MODE>
 __device__ __forceinline__ double b_spmv(const BatchView &v, const Part &P, const double *xin,
-                                         const double *rhs, double *y) {
+                                         const double *rhs, double *y, double *bxout = nullptr) {
   const int sub = threadIdx.x % W;
   const int grp = threadIdx.x / W, ngrp = blockDim.x / W;
   double part = 0.0;
@@ -236,6 +240,7 @@ __device__ __forceinline__ double b_spmv(const BatchView &v, const Part &P, cons
       } else {
         const double yi = rhs[i] - bx;
         y[i] = yi;
+        bxout[i] = bx;
         const double yu = yi * v.invV[i];
         part += yu * yu;
       }
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
     v.t[i] = v.E[copy ? v.copysrc[i] : i];
     if (copy) continue;
     if (i < P.r1) ea += v.rho[i] * v.V[i] * v.e[i] + v.V[i] * v.E[i];
-    double Ti = v.e[i] / ph.cv;
+    double Ti = v.e[i] * ph.inv_cv;
     double Ts = Ti > ph.T_floor ? Ti : ph.T_floor;
     double sig = b_opacity(v.sigma0[i], Ts, ph.p);
     v.T[i] = Ti;
@@ -335,32 +340,39 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
   }
   const double energy_before = csum(R, P, ea);  // also the barrier after a3
   if (ph.limiter != SPH_RT_LIMITER_NONE) {
+    // grad E_i = sum_j F_ij V_j (E_j - E_i) (x_i - x_j), with the constant
+    // weights F_ij V_j (x_i - x_j) stored per pair: 4 FP64 operations a pair
+    // (3 in 2-D) instead of 9 -- the FP64 pipe bounds this kernel
+    constexpr int UL = 4;
     const double *Eg = v.t;
     const bool d3 = ph.dim == 3;
+    const int64_t na = v.nnz_nbr;
     for (int64_t wb = P.q0 + warp_first_group<W>(grp); wb < P.q1; wb += ngrp) {
       const int64_t i = wb + group_in_warp<W>(grp);
       const bool active = i < P.q1;
       const int64_t ia = active ? i : P.r0;
-      const double xi = v.px[ia], yi = v.py[ia], zi = v.pz[ia], Ei = v.E[ia];
+      const double Ei = v.E[ia];
       double gx = 0.0, gy = 0.0, gz = 0.0;
       const int64_t kb = active ? v.nbr_ptr[i] : 0, ke = active ? v.nbr_ptr[i + 1] : 0;
-      for (int64_t kk = kb + sub; kk < ke; kk += (int64_t)W * U) {
-        int32_t jj[U];
-        double F[U];
+      for (int64_t kk = kb + sub; kk < ke; kk += (int64_t)W * UL) {
+        int32_t jj[UL];
+        double ax[UL], ay[UL], az[UL];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
+        for (int u = 0; u < UL; ++u) {
           const int64_t q = kk + (int64_t)u * W;
-          jj[u] = q < ke ? __ldg(v.nbr_col + q) : -1;
-          F[u] = q < ke ? __ldg(v.nbr_F + q) : 0.0;
+          const bool in = q < ke;
+          jj[u] = in ? __ldg(v.nbr_col + q) : -1;
+          ax[u] = in ? __ldg(v.nbr_A + q) : 0.0;
+          ay[u] = in ? __ldg(v.nbr_A + na + q) : 0.0;
+          az[u] = in && d3 ? __ldg(v.nbr_A + 2 * na + q) : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
+        for (int u = 0; u < UL; ++u) {
           if (jj[u] < 0) continue;
-          const int32_t j = jj[u];
-          const double s = v.V[j] * (Eg[j] - Ei) * F[u];
-          gx += s * (xi - v.px[j]);
-          gy += s * (yi - v.py[j]);
-          if (d3) gz += s * (zi - v.pz[j]);  // 2-D: z = 0 everywhere
+          const double d = Eg[jj[u]] - Ei;
+          gx = fma(ax[u], d, gx);
+          gy = fma(ay[u], d, gy);
+          if (d3) gz = fma(az[u], d, gz);  // 2-D: no z weights
         }
       }
       gx = row_reduce<W>(gx);
@@ -428,10 +440,11 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
     gbs = row_reduce<W>(gbs);
     if (active && sub == 0) {
       double dd = v.V[i] * (1.0 / ph.dt + ph.c * v.sigma[i] * v.f[i] + wsum) - off;
+      const double inv = 1.0 / dd;
       v.diag[i] = dd;
-      v.invdiag[i] = 1.0 / dd;
+      v.invdiag[i] = inv;
       v.gb[i] = gbs;
-      gmax = fmax(gmax, -off / dd);
+      gmax = fmax(gmax, -off * inv);
     }
   }
   // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}
@@ -454,14 +467,18 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
                     double *e_out, double &ce, double &cE) {
     double mc[2] = {0.0, 0.0};
     for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
-      double cs = ph.c * v.sigma[i];
-      double Pw = cs * E_new[i] + v.Qe[i];
-      double rdt = v.rho[i] / ph.dt, eo = v.e_old[i], e0 = e_start[i], ei = e0;
+      const double cs = ph.c * v.sigma[i];
+      const double Pw = cs * E_new[i] + v.Qe[i];
+      const double rdt = v.rho[i] / ph.dt, eo = v.e_old[i], e0 = e_start[i];
+      // one FP64 division an iteration: T = e / c_v as a product, the
+      // Jacobian's factor 4 c sigma a / c_v hoisted out of the loop
+      const double ca = cs * ph.a, k1 = 4.0 * ca * ph.inv_cv;
+      double ei = e0;
       for (int it = 0; it < ph.max_inner; ++it) {
-        double T = ei / ph.cv, T3 = T * T * T;
-        double u = rdt * (ei - eo) + cs * ph.a * T3 * T - Pw;
-        double J = rdt + 4.0 * cs * ph.a * T3 / ph.cv;
-        double de = u / J;
+        const double T = ei * ph.inv_cv, T3 = T * T * T;
+        const double u = rdt * (ei - eo) + ca * T3 * T - Pw;
+        const double J = rdt + k1 * T3;
+        const double de = u / J;
         ei -= de;
         if (fabs(de) <= ph.tol_inner * fabs(ei)) break;
       }
@@ -482,7 +499,7 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
     // a7: right-hand side (B-scaled), warm start, ||b||
     double bb = 0.0;
     for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
-      double Tl = v.e_l[i] / ph.cv;
+      double Tl = v.e_l[i] * ph.inv_cv;
       double cs = ph.c * v.sigma[i];
       double bi = v.E_old[i] / ph.dt + cs * ph.a * Tl * Tl * Tl * Tl - (1.0 - v.f[i]) * cs * v.E_l[i] +
                   v.QE[i] + v.gb[i];
@@ -491,8 +508,23 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
       bb += bi * bi;
     }
     const double thresh2 = ph.tol_krylov * ph.tol_krylov * csum(R, P, bb);
-    // a6: Chebyshev-preconditioned CG on B
-    double rr = csum(R, P, b_spmv<W, U, 1>(v, P, v.x, v.b, v.r));
+    // a6: Chebyshev-preconditioned CG on B.  The start x is the last outer
+    // iteration's solution, whose product y = B x the CG updates carried
+    // (y += alpha q), so only the first outer iteration of the step sweeps
+    // the operator for its residual.
+    double rr;
+    if (outer == 0) {
+      rr = csum(R, P, b_spmv<W, U, 1>(v, P, v.x, v.b, v.r, v.y));
+    } else {
+      double part = 0.0;
+      for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
+        const double ri = v.b[i] - v.y[i];
+        v.r[i] = ri;
+        const double ru = ri * v.invV[i];
+        part += ru * ru;
+      }
+      rr = csum(R, P, part);
+    }
     int it = 0;
     bool kconv = rr <= thresh2;
     if (!kconv) {
@@ -506,6 +538,7 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
         rr = 0.0;
         for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
           v.x[i] += alpha * v.p[i];
+          v.y[i] += alpha * v.q[i];
           double ri = v.r[i] - alpha * v.q[i];
           v.r[i] = ri;
           double ru = ri * v.invV[i];
@@ -591,6 +624,28 @@ __global__ void batch_accumulate_kernel(int K, const int32_t *status, const int3
   run_outer[k] += outer[k];
   run_krylov[k] += krylov[k];
   if (status[k] != 0) run_status[k] = status[k];
+}
+
+// Weights of the limiter gradient, one per neighbour pair (i, j):
+// A_ij = F_ij V_j (x_i - x_j), stored as three arrays of nnz entries.  Rows
+// without neighbours (ghost slots) are empty.  A warp per row.
+__global__ void limiter_weights_kernel(int64_t n, const int64_t *nbr_ptr, const int32_t *nbr_col,
+                                       const double *nbr_F, const double *V, const double *px,
+                                       const double *py, const double *pz, int64_t nnz,
+                                       double *A) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w0; i < n; i += nw) {
+    const double xi = px[i], yi = py[i], zi = pz[i];
+    for (int64_t k = nbr_ptr[i] + lane; k < nbr_ptr[i + 1]; k += 32) {
+      const int32_t j = nbr_col[k];
+      const double fv = nbr_F[k] * V[j];
+      A[k] = fv * (xi - px[j]);
+      A[nnz + k] = fv * (yi - py[j]);
+      A[2 * nnz + k] = fv * (zi - pz[j]);
+    }
+  }
 }
 
 __global__ void pack_ptr_kernel(const int64_t *ptr_k, int64_t n_int, int64_t n, int64_t nnz_k,
@@ -744,7 +799,7 @@ static sph_rt_status batch_pack(sph_rt_batch *B) {
                    (double **)&v.invV, (double **)&v.rho, (double **)&v.sigma0, &v.e, &v.E,
                    (double **)&v.Qe, (double **)&v.QE, &v.T, &v.sigma, &v.f, &v.R, &v.lam, &v.D,
                    &v.diag, &v.invdiag, &v.gb, &v.b, &v.x, &v.r, &v.z, &v.p, &v.q, &v.d, &v.t,
-                   &v.e_old, &v.E_old, &v.e_l, &v.E_l, &v.e_new};
+                   &v.e_old, &v.E_old, &v.e_l, &v.E_l, &v.e_new, &v.y};
   for (double **p : dd)
     if (!(*p = D(n_all))) return SPH_RT_ENOMEM;
   int32_t *kind = dalloc<int32_t>(s, n_all), *copysrc = dalloc<int32_t>(s, n_all);
@@ -752,7 +807,8 @@ static sph_rt_status batch_pack(sph_rt_batch *B) {
           *gh_ptr = dalloc<int64_t>(s, n_all + 1);
   int32_t *nbr_col = dalloc<int32_t>(s, nb), *mat_col = dalloc<int32_t>(s, nm),
           *gh_slot = dalloc<int32_t>(s, ng);
-  double *nbr_F = D(nb), *mat_G = D(nm), *mat_val = D(nm), *gh_W = D(ng);
+  double *nbr_F = D(nb), *nbr_A = D(3 * (size_t)nb), *mat_G = D(nm), *mat_val = D(nm),
+         *gh_W = D(ng);
   B->d_slot_off = dalloc<int64_t>(s, K + 1);
   B->d_nint = dalloc<int64_t>(s, K);
   B->d_status = dalloc<int32_t>(s, K);
@@ -767,7 +823,7 @@ static sph_rt_status batch_pack(sph_rt_batch *B) {
   for (int c = 0; c < kClusterKinds - 1; ++c)
     SPH_CUDA(s, cudaEventCreateWithFlags(&B->join[c], cudaEventDisableTiming));
   if (!kind || !copysrc || !nbr_ptr || !mat_ptr || !gh_ptr || !nbr_col || !mat_col ||
-      !gh_slot || !nbr_F || !mat_G || !mat_val || !gh_W || !B->d_slot_off || !B->d_nint ||
+      !gh_slot || !nbr_F || !nbr_A || !mat_G || !mat_val || !gh_W || !B->d_slot_off || !B->d_nint ||
       !B->d_status || !B->d_outer || !B->d_krylov || !B->d_energy)
     return SPH_RT_ENOMEM;
   cudaStream_t st = s->stream;
@@ -824,7 +880,16 @@ static sph_rt_status batch_pack(sph_rt_batch *B) {
   v.copysrc = copysrc;
   v.nbr_ptr = nbr_ptr;
   v.nbr_col = nbr_col;
-  v.nbr_F = nbr_F;
+  v.nbr_A = nbr_A;
+  v.nnz_nbr = nb;
+  if (nb > 0) {
+    limiter_weights_kernel<<<std::max(1, std::min<int>((int)((n_all + 7) / 8), s->num_sms * 16)),
+                             256, 0, s->stream>>>(n_all, nbr_ptr, nbr_col, nbr_F, v.V, v.px, v.py,
+                                                  v.pz, nb, nbr_A);
+    SPH_LAUNCHED(s);
+    SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  }
+  dfree(s, nbr_F);  // only the weights are used by the steps
   v.mat_ptr = mat_ptr;
   v.mat_col = mat_col;
   v.mat_G = mat_G;
@@ -887,6 +952,7 @@ static BatchPhys batch_phys(const sph_rt_batch *B, double dt) {
   ph.a = c.a;
   ph.c = c.c;
   ph.cv = c.cv;
+  ph.inv_cv = 1.0 / c.cv;
   ph.p = c.opacity_exp;
   ph.T_floor = c.T_floor;
   ph.larsen_k = c.larsen_k;
@@ -1324,7 +1390,7 @@ extern "C" sph_rt_status sph_rt_batch_autotune(sph_rt_batch *B, double dt, float
 }
 
 extern "C" sph_rt_status sph_rt_batch_problem_info(const sph_rt_batch *B, int32_t index,
-                                                   int64_t info[4]) {
+                                                   int64_t info[5]) {
   if (!B || !info) return SPH_RT_EINVAL;
   if (index < 0 || index >= (int32_t)B->items.size()) return SPH_RT_EINVAL;
   const BatchItem &it = B->items[index];
@@ -1332,6 +1398,7 @@ extern "C" sph_rt_status sph_rt_batch_problem_info(const sph_rt_batch *B, int32_
   info[1] = it.n_int;
   info[2] = it.nnz_mat;
   info[3] = it.nnz_nbr;
+  info[4] = cluster_of(it.n_int, B->rows_per_cta, B->max_cluster);
   return SPH_RT_OK;
 }
 

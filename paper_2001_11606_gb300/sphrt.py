@@ -629,11 +629,12 @@ class Batch:
         return chosen, table
 
     def problem_info(self, index):
-        """{n_total, n_interior, nnz_operator, nnz_neighbours} of one problem."""
-        a = np.zeros(4, dtype=np.int64)
+        """{n_total, n_interior, nnz_operator, nnz_neighbours, cluster} of one problem
+        (cluster: blocks it runs on with the current shape)."""
+        a = np.zeros(5, dtype=np.int64)
         self._check(self._L.sph_rt_batch_problem_info(self._h, int(index), _ptr(a)))
         return dict(n_total=int(a[0]), n_interior=int(a[1]), nnz_operator=int(a[2]),
-                    nnz_neighbours=int(a[3]))
+                    nnz_neighbours=int(a[3]), cluster=int(a[4]))
 
     def get_energies(self, index):
         n = self._n[index]
