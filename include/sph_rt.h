@@ -56,6 +56,8 @@ enum { SPH_RT_FP64 = 0, SPH_RT_MIXED = 1 };
  * kernel with support h (Sec. 2.4, Eq. wendlandc4; the printed polynomial in
  * every dimension, normalised to a unit volume integral, Sec. 2.3). */
 enum { SPH_RT_M4_SPLINE = 0, SPH_RT_WENDLAND_C4 = 1 };
+/* cell list of the neighbour search (sph_rt_config.cell_list) */
+enum { SPH_RT_CELLS_AUTO = 0, SPH_RT_CELLS_DENSE = 1, SPH_RT_CELLS_SORTED = 2 };
 
 /*
  * Problem constants and solver controls.
@@ -138,6 +140,11 @@ typedef struct {
   double dt_growth;     /* largest factor between consecutive steps (>= 1) */
   double dt_min, dt_max;
   double dt_eta_floor;  /* added to the denominator for states that may be zero everywhere */
+  int32_t cell_list;    /* neighbour search cell list (SPH_RT_CELLS_*): AUTO (default) takes the
+                           dense key table while the grid has at most 2^26 cells and the sorted
+                           64-bit keys (radix sort, hash table of occupied cells; up to 2^58
+                           cells) beyond; DENSE refuses larger grids with EINVAL; SORTED always
+                           sorts.  Both give the same slots and neighbour lists. */
   int32_t device;       /* CUDA device ordinal */
   void *stream;         /* cudaStream_t to run on (borrowed); NULL = library-owned stream */
 } sph_rt_config;

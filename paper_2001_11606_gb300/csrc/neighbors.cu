@@ -9,10 +9,13 @@
 // order dx*dx + dy*dy + dz*dz, so the neighbour sets are bit-identical to a
 // host evaluation of the same expression.
 //
-// Layout: particles are counting-sorted by key = (ghost flag, Morton code of
-// the cell) with ties broken by caller index, giving "slots" with interior
-// particles first.  Cells have edge >= s max h, so all neighbours of a
-// particle lie in the 3^d cells around its own.
+// Layout: particles are sorted by key = (ghost flag, Morton code of the cell)
+// with ties broken by caller index, giving "slots" with interior particles
+// first.  Cells have edge >= s max h, so all neighbours of a particle lie in
+// the 3^d cells around its own.  Two cell lists give the same slots: a dense
+// table over all keys (counting sort, up to 2^27 keys), and for larger grids
+// 64-bit keys with a stable radix sort, the occupied cells by run length and
+// a hash table from cell key to cell (up to 2^58 cells).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -200,6 +203,17 @@ __device__ __forceinline__ uint64_t morton(const Grid &g, int cx, int cy, int cz
   return (uint64_t)cx;
 }
 
+// hash of a cell key (sorted cell list), and the free-entry marker
+constexpr unsigned long long kEmptyCell = ~0ull;
+__host__ __device__ inline uint64_t cell_hash(uint64_t k) {  // splitmix64 finaliser
+  k ^= k >> 30;
+  k *= 0xbf58476d1ce4e5b9ull;
+  k ^= k >> 27;
+  k *= 0x94d049bb133111ebull;
+  k ^= k >> 31;
+  return k;
+}
+
 __global__ void key_kernel(Grid g, const double *px, const double *py, const double *pz,
                            const int32_t *kind, int64_t n, uint32_t *key, unsigned *count) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -246,6 +260,117 @@ __global__ void segment_sort_kernel(const int64_t *start, const unsigned *count,
         --u;
       }
       a[u + 1] = v;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Sorted-key cell list (grids beyond the dense key table)
+// --------------------------------------------------------------------------
+__global__ void key64_kernel(Grid g, const double *px, const double *py, const double *pz,
+                             const int32_t *kind, int64_t n, uint64_t *key, int64_t *idx) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int cx = cell_coord(px[i], g.lo[0], g.inv_cell, g.nc[0]);
+    int cy = cell_coord(py[i], g.lo[1], g.inv_cell, g.nc[1]);
+    int cz = cell_coord(pz[i], g.lo[2], g.inv_cell, g.nc[2]);
+    uint64_t k = morton(g, cx, cy, cz);
+    if (kind[i] != SPH_RT_INTERIOR) k |= 1ull << g.ghost_shift;
+    key[i] = k;
+    idx[i] = i;
+  }
+}
+
+// Stable LSD radix sort of (key, index) pairs, 8 bits a pass.  A block owns a
+// contiguous tile of kRadixItems * blockDim items; pass 1 counts its digits
+// (hist[d * nb + b]); after an exclusive scan over (digit, block) the scatter
+// places the tile's items in order: round by round, each item's rank among
+// the equal digits of its warp (match_any), after those of the earlier warps
+// of the round and of the earlier rounds.  Equal keys keep their order, and
+// the index starts as the caller index, so ties end in caller order.
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kBlock * kRadixItems;
+static_assert(kBlock == 256, "the radix kernels give each of the 256 digits one thread");
+
+__global__ void radix_hist_kernel(const uint64_t *key, int64_t n, int shift, int64_t nb,
+                                  int64_t *hist) {
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0;  // blockDim == 256
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  for (int r = 0; r < kRadixItems; ++r) {
+    const int64_t i = base + (int64_t)r * kBlock + threadIdx.x;
+    if (i < n) atomicAdd(&h[(key[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void radix_scatter_kernel(const uint64_t *kin, const int64_t *vin, int64_t n, int shift,
+                                     int64_t nb, const int64_t *off, uint64_t *kout,
+                                     int64_t *vout) {
+  __shared__ unsigned wc[kWarpsPerBlock][256];
+  __shared__ int64_t run[256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  run[threadIdx.x] = off[(int64_t)threadIdx.x * nb + blockIdx.x];
+  for (int a = 0; a < kWarpsPerBlock; ++a) wc[a][threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  for (int r = 0; r < kRadixItems; ++r) {
+    const int64_t i = base + (int64_t)r * kBlock + threadIdx.x;
+    const bool valid = i < n;
+    const uint64_t k = valid ? kin[i] : 0ull;
+    const int d = valid ? (int)((k >> shift) & 255u) : 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lt);
+    if (valid && lane == __ffs(peers) - 1) wc[w][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      int64_t pos = run[d] + rank;
+      for (int a = 0; a < w; ++a) pos += wc[a][d];
+      kout[pos] = k;
+      vout[pos] = vin[i];
+    }
+    __syncthreads();
+    unsigned t = 0;
+    for (int a = 0; a < kWarpsPerBlock; ++a) {
+      t += wc[a][threadIdx.x];
+      wc[a][threadIdx.x] = 0;
+    }
+    run[threadIdx.x] += t;
+    __syncthreads();
+  }
+}
+
+__global__ void cell_head_kernel(const uint64_t *key, int64_t n, int64_t *head) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+}
+
+__global__ void cell_fill_kernel(const uint64_t *key, int64_t n, const int64_t *head,
+                                 const int64_t *cidx, uint64_t *cell_key, int64_t *cell_start) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!head[i]) continue;
+    cell_key[cidx[i]] = key[i];
+    cell_start[cidx[i]] = i;
+  }
+}
+
+__global__ void cell_hash_insert_kernel(const uint64_t *cell_key, int64_t ncells, uint64_t mask,
+                                        unsigned long long *hkey, int64_t *hcell) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = cell_key[c];
+    uint64_t h = cell_hash(k) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {  // keys are distinct: ends at a free entry
+      if (atomicCAS(&hkey[h], kEmptyCell, k) == kEmptyCell) {
+        hcell[h] = c;
+        break;
+      }
+      h = (h + 1) & mask;
     }
   }
 }
@@ -422,6 +547,39 @@ __device__ __forceinline__ uint64_t warp_sort_u64(uint64_t v) {
   return v;
 }
 
+// Cell lookup of the neighbour kernels: first slot and particle count of a key.
+struct DenseCells {  // tables over every key
+  const int64_t *start;
+  const unsigned *count;
+  __device__ __forceinline__ void find(uint64_t k, int64_t &beg, int64_t &cnt) const {
+    beg = start[k];
+    cnt = count[k];
+  }
+};
+struct HashCells {  // occupied cells only, open addressing with linear probing
+  const unsigned long long *hkey;  // [mask + 1], kEmptyCell where free
+  const int64_t *hcell;            // cell of each used entry
+  const int64_t *cstart;           // [ncells + 1] first slot of each cell
+  uint64_t mask;
+  __device__ __forceinline__ void find(uint64_t k, int64_t &beg, int64_t &cnt) const {
+    beg = 0;
+    cnt = 0;
+    uint64_t h = cell_hash(k) & mask;
+    // the table is at most half full, so a free entry ends every probe sequence
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+      const unsigned long long t = hkey[h];
+      if (t == k) {
+        const int64_t c = hcell[h];
+        beg = cstart[c];
+        cnt = cstart[c + 1] - beg;
+        return;
+      }
+      if (t == kEmptyCell) return;
+      h = (h + 1) & mask;
+    }
+  }
+};
+
 // Pair weight F_ij = W'_ij / r (two-h average) of neighbour j of i, in FP64.
 __device__ __forceinline__ double pair_weight(int kern, double xi, double yi, double zi,
                                               double ihi, double cwi, int64_t j,
@@ -444,10 +602,10 @@ __device__ __forceinline__ double pair_weight(int kern, double xi, double yi, do
 // particle instead of ~4.
 constexpr int kHitBuf = 64;  // pending hits per warp (< 32 carried + 32 new)
 
-template <bool FILL>
+template <bool FILL, typename Cells>
 __global__ void neighbor_kernel(Grid g, const double *px, const double *py, const double *pz,
-                                const double *h, const float4 *rel, const int64_t *cell_start,
-                                const unsigned *cell_count, int64_t n_int, int64_t *count,
+                                const double *h, const float4 *rel, Cells cells,
+                                int64_t n_int, int64_t *count,
                                 const int64_t *rowptr, int32_t *cols, double *F,
                                 const double *ih, const double *cw) {
   __shared__ int32_t hitbuf[kWarpsPerBlock][FILL ? kHitBuf : 1];
@@ -494,8 +652,8 @@ __global__ void neighbor_kernel(Grid g, const double *px, const double *py, cons
         const float ox = -(float)(ol % 3 - 1) * cellf;
         const float oy = g.dim > 1 ? -(float)((ol / 3) % 3 - 1) * cellf : 0.0f;
         const float oz = g.dim > 2 ? -(float)(ol / 9 - 1) * cellf : 0.0f;
-        const int64_t beg = cell_start[kk];
-        const int64_t cnt = cell_count[kk];
+        int64_t beg, cnt;
+        cells.find(kk, beg, cnt);
         for (int64_t base = 0; base < cnt; base += 32) {
           const int64_t j = beg + base + lane;
           bool hit = false;
@@ -683,43 +841,114 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   int maxnc = 1;
   for (int d = 0; d < 3; ++d) {
     g.lo[d] = hb[d];
-    double ext = hb[3 + d] - hb[d];
-    int nc = d < dim ? (int)(ext / cell) + 1 : 1;
+    const double ncd = d < dim ? floor((hb[3 + d] - hb[d]) / cell) + 1.0 : 1.0;
+    if (!(ncd <= (double)(1 << 29)))
+      return set_error(s, SPH_RT_EINVAL,
+                       "particle extent is too large relative to the support (more than 2^29 "
+                       "cells along an axis)");
+    const int nc = (int)ncd;
     g.nc[d] = nc;
     maxnc = nc > maxnc ? nc : maxnc;
   }
   int bits = 0;
   while ((1 << bits) < maxnc) ++bits;
-  int keybits = bits * dim;
-  if (keybits + 1 > 27) {
+  const int keybits = bits * dim;
+  // dense key table up to 2^27 keys (2^26 cells), else the sorted-key list
+  const bool fits_dense = keybits + 1 <= 27;
+  const bool dense = s->cfg.cell_list == SPH_RT_CELLS_DENSE ||
+                     (s->cfg.cell_list == SPH_RT_CELLS_AUTO && fits_dense);
+  if (dense && !fits_dense)
     return set_error(s, SPH_RT_EINVAL,
-                     "particle extent is too large relative to 2 max(h) for the Morton cell "
-                     "grid (more than 2^26 cells)");
-  }
+                     "particle extent is too large relative to the support for the dense cell "
+                     "table (more than 2^26 cells); use the sorted cell list");
+  if (keybits > 58)
+    return set_error(s, SPH_RT_EINVAL,
+                     "particle extent is too large relative to the support (more than 2^58 "
+                     "cells)");
   g.ghost_shift = keybits;
-  int64_t nkeys = (int64_t)1 << (keybits + 1);
+  const int64_t nkeys = dense ? (int64_t)1 << (keybits + 1) : 0;
 
-  uint32_t *key = dalloc<uint32_t>(s, n);
-  unsigned *cnt = dalloc<unsigned>(s, nkeys);
-  unsigned *cur = dalloc<unsigned>(s, nkeys);
-  int64_t *cnt64 = dalloc<int64_t>(s, nkeys);
-  int64_t *start = dalloc<int64_t>(s, nkeys + 1);
+  // dense table
+  uint32_t *key = nullptr;
+  unsigned *cnt = nullptr, *cur = nullptr;
+  int64_t *cnt64 = nullptr, *start = nullptr;
+  // sorted keys
+  uint64_t *k64[2] = {nullptr, nullptr}, *cell_key = nullptr;
+  int64_t *v64[2] = {nullptr, nullptr}, *rhist = nullptr, *head = nullptr, *cidx = nullptr;
+  int64_t *cell_start = nullptr, *hcell = nullptr;
+  unsigned long long *hkey = nullptr;
+  HashCells hcells{};
   s->slot2caller = dalloc<int64_t>(s, n);
   s->caller2slot = dalloc<int64_t>(s, n);
-  if (!key || !cnt || !cur || !cnt64 || !start || !s->slot2caller || !s->caller2slot)
-    return SPH_RT_ENOMEM;
-  SPH_CUDA(s, cudaMemsetAsync(cnt, 0, sizeof(unsigned) * nkeys, st));
-  SPH_CUDA(s, cudaMemsetAsync(cur, 0, sizeof(unsigned) * nkeys, st));
-  key_kernel<<<grid1(s, n), kBlock, 0, st>>>(g, cx, cy, cz, kind_c, n, key, cnt);
-  SPH_LAUNCHED(s);
-  u32_to_i64<<<grid1(s, nkeys), kBlock, 0, st>>>(cnt, nkeys, cnt64);
-  SPH_LAUNCHED(s);
-  sph_rt_status rc = exclusive_scan(s, cnt64, nkeys, start);
-  if (rc) return rc;
-  scatter_kernel<<<grid1(s, n), kBlock, 0, st>>>(key, n, start, cur, s->slot2caller);
-  SPH_LAUNCHED(s);
-  segment_sort_kernel<<<grid1(s, nkeys), kBlock, 0, st>>>(start, cnt, nkeys, s->slot2caller);
-  SPH_LAUNCHED(s);
+  if (!s->slot2caller || !s->caller2slot) return SPH_RT_ENOMEM;
+  sph_rt_status rc;
+  if (dense) {
+    key = dalloc<uint32_t>(s, n);
+    cnt = dalloc<unsigned>(s, nkeys);
+    cur = dalloc<unsigned>(s, nkeys);
+    cnt64 = dalloc<int64_t>(s, nkeys);
+    start = dalloc<int64_t>(s, nkeys + 1);
+    if (!key || !cnt || !cur || !cnt64 || !start) return SPH_RT_ENOMEM;
+    SPH_CUDA(s, cudaMemsetAsync(cnt, 0, sizeof(unsigned) * nkeys, st));
+    SPH_CUDA(s, cudaMemsetAsync(cur, 0, sizeof(unsigned) * nkeys, st));
+    key_kernel<<<grid1(s, n), kBlock, 0, st>>>(g, cx, cy, cz, kind_c, n, key, cnt);
+    SPH_LAUNCHED(s);
+    u32_to_i64<<<grid1(s, nkeys), kBlock, 0, st>>>(cnt, nkeys, cnt64);
+    SPH_LAUNCHED(s);
+    if ((rc = exclusive_scan(s, cnt64, nkeys, start))) return rc;
+    scatter_kernel<<<grid1(s, n), kBlock, 0, st>>>(key, n, start, cur, s->slot2caller);
+    SPH_LAUNCHED(s);
+    segment_sort_kernel<<<grid1(s, nkeys), kBlock, 0, st>>>(start, cnt, nkeys, s->slot2caller);
+    SPH_LAUNCHED(s);
+  } else {
+    const int64_t nb = ceil_div(n, (int64_t)kRadixTile);
+    for (int a = 0; a < 2; ++a) {
+      k64[a] = dalloc<uint64_t>(s, n);
+      v64[a] = dalloc<int64_t>(s, n);
+    }
+    rhist = dalloc<int64_t>(s, 256 * nb + 1);
+    int64_t *roff = dalloc<int64_t>(s, 256 * nb + 1);
+    if (!k64[0] || !k64[1] || !v64[0] || !v64[1] || !rhist || !roff) return SPH_RT_ENOMEM;
+    key64_kernel<<<grid1(s, n), kBlock, 0, st>>>(g, cx, cy, cz, kind_c, n, k64[0], v64[0]);
+    SPH_LAUNCHED(s);
+    int at = 0;
+    for (int shift = 0; shift < keybits + 1; shift += 8, at ^= 1) {
+      radix_hist_kernel<<<(unsigned)nb, kBlock, 0, st>>>(k64[at], n, shift, nb, rhist);
+      SPH_LAUNCHED(s);
+      if ((rc = exclusive_scan(s, rhist, 256 * nb, roff))) return rc;
+      radix_scatter_kernel<<<(unsigned)nb, kBlock, 0, st>>>(k64[at], v64[at], n, shift, nb, roff,
+                                                          k64[at ^ 1], v64[at ^ 1]);
+      SPH_LAUNCHED(s);
+    }
+    dfree(s, roff);
+    SPH_CUDA(s, cudaMemcpyAsync(s->slot2caller, v64[at], sizeof(int64_t) * n,
+                                cudaMemcpyDeviceToDevice, st));
+    // occupied cells: runs of equal keys
+    head = dalloc<int64_t>(s, n);
+    cidx = dalloc<int64_t>(s, n + 1);
+    if (!head || !cidx) return SPH_RT_ENOMEM;
+    cell_head_kernel<<<grid1(s, n), kBlock, 0, st>>>(k64[at], n, head);
+    SPH_LAUNCHED(s);
+    if ((rc = exclusive_scan(s, head, n, cidx))) return rc;
+    int64_t ncells = 0;
+    SPH_CUDA(s, cudaMemcpyAsync(&ncells, cidx + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SPH_CUDA(s, cudaStreamSynchronize(st));
+    cell_key = dalloc<uint64_t>(s, ncells);
+    cell_start = dalloc<int64_t>(s, ncells + 1);
+    uint64_t hsize = 2;
+    while (hsize < 2 * (uint64_t)ncells) hsize <<= 1;  // at most half full
+    hkey = dalloc<unsigned long long>(s, hsize);
+    hcell = dalloc<int64_t>(s, hsize);
+    if (!cell_key || !cell_start || !hkey || !hcell) return SPH_RT_ENOMEM;
+    cell_fill_kernel<<<grid1(s, n), kBlock, 0, st>>>(k64[at], n, head, cidx, cell_key, cell_start);
+    SPH_LAUNCHED(s);
+    SPH_CUDA(s, cudaMemcpyAsync(cell_start + ncells, &n, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    SPH_CUDA(s, cudaMemsetAsync(hkey, 0xff, sizeof(unsigned long long) * hsize, st));
+    cell_hash_insert_kernel<<<grid1(s, ncells), kBlock, 0, st>>>(cell_key, ncells, hsize - 1, hkey,
+                                                                hcell);
+    SPH_LAUNCHED(s);
+    hcells = HashCells{hkey, hcell, cell_start, hsize - 1};
+  }
   invert_perm<<<grid1(s, n), kBlock, 0, st>>>(s->slot2caller, n, s->caller2slot);
   SPH_LAUNCHED(s);
 
@@ -775,9 +1004,14 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   if (!rel) return SPH_RT_ENOMEM;
   rel_kernel<<<grid1(s, n), kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, n, rel);
   SPH_LAUNCHED(s);
-  neighbor_kernel<false><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, rel, start, cnt,
-                                                n_int, nc, nullptr, nullptr, nullptr, nullptr,
-                                                nullptr);
+  if (dense)
+    neighbor_kernel<false, DenseCells><<<gw, kBlock, 0, st>>>(
+        g, s->px, s->py, s->pz, s->h, rel, DenseCells{start, cnt}, n_int, nc, nullptr, nullptr,
+        nullptr, nullptr, nullptr);
+  else
+    neighbor_kernel<false, HashCells><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, rel,
+                                                             hcells, n_int, nc, nullptr, nullptr,
+                                                             nullptr, nullptr, nullptr);
   SPH_LAUNCHED(s);
   rc = exclusive_scan(s, nc, n_int, s->nbr_ptr);
   if (rc) return rc;
@@ -794,9 +1028,14 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   if (!ih || !cw) return SPH_RT_ENOMEM;
   kernel_coef_kernel<<<grid1(s, n), kBlock, 0, st>>>(n, dim, s->cfg.kernel, s->h, ih, cw);
   SPH_LAUNCHED(s);
-  neighbor_kernel<true><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, rel, start, cnt,
-                                               n_int, nullptr, s->nbr_ptr, s->nbr_col, s->nbr_F,
-                                               ih, cw);
+  if (dense)
+    neighbor_kernel<true, DenseCells><<<gw, kBlock, 0, st>>>(
+        g, s->px, s->py, s->pz, s->h, rel, DenseCells{start, cnt}, n_int, nullptr, s->nbr_ptr,
+        s->nbr_col, s->nbr_F, ih, cw);
+  else
+    neighbor_kernel<true, HashCells><<<gw, kBlock, 0, st>>>(g, s->px, s->py, s->pz, s->h, rel,
+                                                            hcells, n_int, nullptr, s->nbr_ptr,
+                                                            s->nbr_col, s->nbr_F, ih, cw);
   SPH_LAUNCHED(s);
 
   // operator sparsity
@@ -828,7 +1067,9 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   SPH_LAUNCHED(s);
   SPH_CUDA(s, cudaStreamSynchronize(st));
   // set-up scratch back to the free list
-  void *scratch[] = {cx, cy, cz, hc, bbox, key, cnt, cur, cnt64, start, nc, mc, gc, ih, cw, rel};
+  void *scratch[] = {cx, cy, cz, hc, bbox, key, cnt, cur, cnt64, start, nc, mc, gc, ih, cw, rel,
+                     k64[0], k64[1], v64[0], v64[1], rhist, head, cidx, cell_key, cell_start,
+                     hkey, hcell};
   for (void *p : scratch) dfree(s, p);
   return SPH_RT_OK;
 }

@@ -190,6 +190,7 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->dt_min = 0.0;
   c->dt_max = 1e300;
   c->dt_eta_floor = 1e-15;
+  c->cell_list = SPH_RT_CELLS_AUTO;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -240,6 +241,8 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
       c->dt_eta_floor < 1e300))
     return why = "time step limits: dt_growth >= 1, 0 <= dt_min <= dt_max, dt_eta_floor >= 0",
            SPH_RT_EINVAL;
+  if (c->cell_list < SPH_RT_CELLS_AUTO || c->cell_list > SPH_RT_CELLS_SORTED)
+    return why = "cell_list must be SPH_RT_CELLS_AUTO, _DENSE or _SORTED", SPH_RT_EINVAL;
   if (c->device < 0) return why = "device must be >= 0", SPH_RT_EINVAL;
   return SPH_RT_OK;
 }

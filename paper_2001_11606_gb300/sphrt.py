@@ -24,6 +24,7 @@ LIMITER_NONE, LIMITER_LEVERMORE, LIMITER_LARSEN = 0, 1, 2
 PRECOND_JACOBI, PRECOND_CHEBYSHEV, PRECOND_AMG = 0, 1, 2
 FP64, MIXED = 0, 1
 M4_SPLINE, WENDLAND_C4 = 0, 1
+CELLS_AUTO, CELLS_DENSE, CELLS_SORTED = 0, 1, 2
 # candidate shapes of sph_rt_batch_autotune: a grid, outermost first, then the
 # rows per CTA (SPH_RT_BATCH_TUNE_CANDIDATES = 2 x 4 x 5 + 4)
 BATCH_TUNE_BLOCKS = (1, 2)
@@ -64,7 +65,7 @@ class Config(C.Structure):
         ("fine_post_smooth", C.c_int32),
         ("reliable_drop", C.c_double),
         ("dt_target", C.c_double), ("dt_growth", C.c_double), ("dt_min", C.c_double),
-        ("dt_max", C.c_double), ("dt_eta_floor", C.c_double),
+        ("dt_max", C.c_double), ("dt_eta_floor", C.c_double), ("cell_list", C.c_int32),
         ("device", C.c_int32),
         ("stream", C.c_void_p),
     ]
