@@ -145,6 +145,9 @@ typedef struct {
                            64-bit keys (radix sort, hash table of occupied cells; up to 2^58
                            cells) beyond; DENSE refuses larger grids with EINVAL; SORTED always
                            sorts.  Both give the same slots and neighbour lists. */
+  int32_t index64;      /* 1: 64-bit source indices in the AMG set-up's Galerkin lists even where
+                           32 bits suffice; 0 (default): 64 bits only for a level with 2^31 - 1
+                           or more entries plus rows.  Never changes a result. */
   int32_t device;       /* CUDA device ordinal */
   void *stream;         /* cudaStream_t to run on (borrowed); NULL = library-owned stream */
 } sph_rt_config;

@@ -56,6 +56,15 @@ static_assert(1 + kMaxLevels <= kChebSlots, "one Chebyshev slot per AMG level");
 
 }  // namespace sphrt
 
+// Source indices of Galerkin sums over a level's entries (k < nnz for an
+// off-diagonal entry, nnz + i for a diagonal): 32 bits while nnz + n fits
+// (below 2^31 - 1, or unless config.index64), else 64 bits.  Exactly one of
+// the two is set.
+struct SrcList {
+  int32_t *i32 = nullptr;
+  int64_t *i64 = nullptr;
+};
+
 struct SphLevel {
   int64_t n = 0, nnz = 0;
   // operator (level 0 borrows the fine operator; others own theirs)
@@ -68,7 +77,7 @@ struct SphLevel {
   int64_t *agg_ptr = nullptr;   // [nc+1] members of each coarse row
   int32_t *agg_mem = nullptr;
   int64_t *seg_ptr = nullptr;   // [nnz_c + nc + 1] Galerkin contributions per coarse target
-  int32_t *seg_src = nullptr;   // source: k < nnz (off-diagonal entry) or nnz + i (diagonal)
+  SrcList seg_src;              // source: k < nnz (off-diagonal entry) or nnz + i (diagonal)
   // vectors of the V-cycle
   double *r = nullptr, *z = nullptr, *res = nullptr, *d = nullptr, *t = nullptr;
   float *r32 = nullptr, *z32 = nullptr, *res32 = nullptr, *d32 = nullptr, *t32 = nullptr;
@@ -78,7 +87,7 @@ struct SphLevel {
   int64_t *ap_ptr = nullptr;    // [n + 1]
   int32_t *ap_col = nullptr;    // [nnz_ap] aggregate (next-level row)
   int64_t *ap_seg_ptr = nullptr;  // [nnz_ap + 1] sources of each A P entry
-  int32_t *ap_seg_src = nullptr;  // source: k < nnz (off-diagonal entry) or nnz + i (diagonal)
+  SrcList ap_seg_src;             // source: k < nnz (off-diagonal entry) or nnz + i (diagonal)
   int64_t *apg_ptr = nullptr;     // [nnz_c + nc + 1] next level's Galerkin sums over A P entries
   int32_t *apg_src = nullptr;     // (P^T (A P): each A P entry (i, K) adds to (agg[i], K))
   double *ap_val = nullptr;     // [nnz_ap]
@@ -241,24 +250,29 @@ __global__ void assign_kernel(int64_t n, const int64_t *ptr, const int32_t *col,
 
 // counting-sort scatter + per-segment insertion sort (shared by the member
 // lists and the Galerkin contribution lists): orders each segment by value
+// S: the item index type (int32_t, or int64_t for more than 2^31 - 1 items)
+template <typename S>
 __global__ void bucket_scatter_kernel(int64_t n, const int32_t *bucket, const int64_t *start,
-                                      unsigned *cursor, int32_t *out) {
+                                      unsigned *cursor, S *out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     int32_t b = bucket[i];
     if (b < 0) continue;
     int64_t at = start[b] + atomicAdd(&cursor[b], 1u);
-    out[at] = (int32_t)i;
+    out[at] = (S)i;
   }
 }
 // Buckets of up to kSmallBucket items are insertion-sorted by one thread
 // (bucket_sort_kernel); larger ones, where a quadratic sort in one thread
 // would dominate the set-up, by a warp (bucket_rank_kernel).
 constexpr int kSmallBucket = 32;
-constexpr int kRankBucket = 1024;  // largest bucket the warp sort stages in shared memory
-__device__ __forceinline__ void insertion_sort(int32_t *a, int64_t c) {
+// largest bucket the warp sort stages in shared memory (32 KB a block)
+template <typename S>
+constexpr int rank_bucket() { return 4096 / (int)sizeof(S); }
+template <typename S>
+__device__ __forceinline__ void insertion_sort(S *a, int64_t c) {
   for (int64_t t = 1; t < c; ++t) {
-    int32_t v = a[t];
+    S v = a[t];
     int64_t u = t - 1;
     while (u >= 0 && a[u] > v) {
       a[u + 1] = a[u];
@@ -267,7 +281,8 @@ __device__ __forceinline__ void insertion_sort(int32_t *a, int64_t c) {
     a[u + 1] = v;
   }
 }
-__global__ void bucket_sort_kernel(int64_t nb, const int64_t *start, int32_t *out) {
+template <typename S>
+__global__ void bucket_sort_kernel(int64_t nb, const int64_t *start, S *out) {
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
        b += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = start[b + 1] - start[b];
@@ -276,12 +291,14 @@ __global__ void bucket_sort_kernel(int64_t nb, const int64_t *start, int32_t *ou
 }
 // A warp takes 32 consecutive buckets and sorts each larger one in turn: the
 // items (distinct indices) are staged in shared memory and each is written at
-// its rank, the number of smaller items.  Buckets beyond kRankBucket items
+// its rank, the number of smaller items.  Buckets beyond rank_bucket items
 // (not met by the aggregation levels, whose sources per target are a few
 // hundred at most) fall back to one thread.
-__global__ void bucket_rank_kernel(int64_t nb, const int64_t *start, int32_t *out) {
-  __shared__ int32_t stage[kWarpsPerBlock][kRankBucket];
-  int32_t *sm = stage[threadIdx.x >> 5];
+template <typename S>
+__global__ void bucket_rank_kernel(int64_t nb, const int64_t *start, S *out) {
+  constexpr int kRankBucket = rank_bucket<S>();
+  __shared__ S stage[kWarpsPerBlock][kRankBucket];
+  S *sm = stage[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -302,7 +319,7 @@ __global__ void bucket_rank_kernel(int64_t nb, const int64_t *start, int32_t *ou
       for (int64_t k = lane; k < cc; k += 32) sm[k] = out[s0 + k];
       __syncwarp();
       for (int64_t k = lane; k < cc; k += 32) {
-        const int32_t v = sm[k];
+        const S v = sm[k];
         int rank = 0;
         for (int q = 0; q < (int)cc; ++q) rank += sm[q] < v;
         out[s0 + rank] = v;
@@ -443,9 +460,10 @@ __global__ void target_count_kernel(int64_t nsrc, const int32_t *tgt, unsigned *
 // adding all 8 slots.
 // T: the hierarchy's value type (FP32 in the mixed form: its sums are formed
 // from the FP32 fine values directly).
-template <typename T>
+// S: the source index type (SrcList).
+template <typename T, typename S>
 __global__ void galerkin_kernel(int64_t nnz_c, int64_t nc, const int64_t *seg_ptr,
-                                const int32_t *seg_src, int64_t nnz_f, const T *val_f,
+                                const S *seg_src, int64_t nnz_f, const T *val_f,
                                 const T *diag_f, T *val_c, T *diag_c, T *invdiag_c) {
   constexpr int G = 8;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnz_c + nc;
@@ -457,9 +475,9 @@ __global__ void galerkin_kernel(int64_t nnz_c, int64_t nc, const int64_t *seg_pt
       const int64_t left = u1 - u;
       const int m = __reduce_max_sync(mask, left <= 0 ? 0 : (left < G ? (int)left : G));
       if (m == 0) break;  // uniform over the lanes of `mask`
-      int32_t src[G];
+      S src[G];
 #pragma unroll
-      for (int g = 0; g < G; ++g) src[g] = u + g < u1 ? __ldg(seg_src + u + g) : -1;
+      for (int g = 0; g < G; ++g) src[g] = u + g < u1 ? __ldg(seg_src + u + g) : S(-1);
       T v[G];
 #pragma unroll
       for (int g = 0; g < G; ++g)
@@ -1229,9 +1247,10 @@ CsrView<double> fine_view(const sph_rt *s);
 
 
 // bucket sort of ids by bucket[i] into (start, out); nb buckets
+template <typename S>
 static sph_rt_status bucket_sort(sph_rt *s, SphLevel *owner, int64_t nitems,
                                  const int32_t *bucket, int64_t nb, int64_t **start_out,
-                                 int32_t **out_out, int64_t *total_out) {
+                                 S **out_out, int64_t *total_out) {
   unsigned *cnt = scratch<unsigned>(s, nb + 1), *cur = scratch<unsigned>(s, nb + 1);
   int64_t *cnt64 = scratch<int64_t>(s, nb + 1);
   if (!cnt || !cur || !cnt64) return SPH_RT_ENOMEM;
@@ -1248,14 +1267,14 @@ static sph_rt_status bucket_sort(sph_rt *s, SphLevel *owner, int64_t nitems,
   int64_t total = 0;
   SPH_CUDA(s, cudaMemcpyAsync(&total, start + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s->stream));
   SPH_CUDA(s, cudaStreamSynchronize(s->stream));
-  int32_t *out = lalloc<int32_t>(s, owner, total);
+  S *out = lalloc<S>(s, owner, total);
   if (!out) return SPH_RT_ENOMEM;
-  bucket_scatter_kernel<<<gcap(s, nitems, kBlock), kBlock, 0, s->stream>>>(nitems, bucket, start,
-                                                                          cur, out);
+  bucket_scatter_kernel<S><<<gcap(s, nitems, kBlock), kBlock, 0, s->stream>>>(nitems, bucket,
+                                                                             start, cur, out);
   SPH_LAUNCHED(s);
-  bucket_sort_kernel<<<gcap(s, nb, kBlock), kBlock, 0, s->stream>>>(nb, start, out);
+  bucket_sort_kernel<S><<<gcap(s, nb, kBlock), kBlock, 0, s->stream>>>(nb, start, out);
   SPH_LAUNCHED(s);
-  bucket_rank_kernel<<<gcap(s, ceil_div(nb, 32), kWarpsPerBlock), kBlock, 0, s->stream>>>(
+  bucket_rank_kernel<S><<<gcap(s, ceil_div(nb, 32), kWarpsPerBlock), kBlock, 0, s->stream>>>(
       nb, start, out);
   SPH_LAUNCHED(s);
   SPH_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -1265,6 +1284,34 @@ static sph_rt_status bucket_sort(sph_rt *s, SphLevel *owner, int64_t nitems,
   *start_out = start;
   *out_out = out;
   if (total_out) *total_out = total;
+  return SPH_RT_OK;
+}
+
+// Galerkin source lists over nitems = nnz + n sources: 64-bit indices when
+// they do not fit 32 bits (or config.index64), else 32-bit.
+static sph_rt_status source_sort(sph_rt *s, SphLevel *owner, int64_t nitems,
+                                 const int32_t *bucket, int64_t nb, int64_t **start_out,
+                                 SrcList *out) {
+  *out = SrcList{};
+  if (s->cfg.index64 || nitems >= ((int64_t)1 << 31) - 1)
+    return bucket_sort<int64_t>(s, owner, nitems, bucket, nb, start_out, &out->i64, nullptr);
+  return bucket_sort<int32_t>(s, owner, nitems, bucket, nb, start_out, &out->i32, nullptr);
+}
+
+template <typename T>
+static sph_rt_status launch_galerkin(sph_rt *s, int64_t nnz_c, int64_t nc, const int64_t *seg_ptr,
+                            const SrcList &src, int64_t nnz_f, const T *val_f, const T *diag_f,
+                            T *val_c, T *diag_c, T *invdiag_c) {
+  const int g = gcap(s, nnz_c + nc, kBlock);
+  if (src.i64)
+    galerkin_kernel<T, int64_t><<<g, kBlock, 0, s->stream>>>(nnz_c, nc, seg_ptr, src.i64, nnz_f,
+                                                             val_f, diag_f, val_c, diag_c,
+                                                             invdiag_c);
+  else
+    galerkin_kernel<T, int32_t><<<g, kBlock, 0, s->stream>>>(nnz_c, nc, seg_ptr, src.i32, nnz_f,
+                                                             val_f, diag_f, val_c, diag_c,
+                                                             invdiag_c);
+  SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }
 
@@ -1330,7 +1377,7 @@ static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
   members = nullptr;
   // member lists of the coarse rows
   int64_t tot = 0;
-  if ((rc = bucket_sort(s, L, n, L->agg, nc, &L->agg_ptr, &L->agg_mem, &tot))) return rc;
+  if ((rc = bucket_sort<int32_t>(s, L, n, L->agg, nc, &L->agg_ptr, &L->agg_mem, &tot))) return rc;
 
   SphLevel *C = new SphLevel();
   C->n = nc;
@@ -1367,7 +1414,7 @@ static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
                                                     tgt + nnz, overflow);
   SPH_LAUNCHED(s);
   // Galerkin contribution lists per coarse target (nnz_c off-diagonal + nc diagonal)
-  rc = bucket_sort(s, L, nnz + n, tgt, C->nnz + nc, &L->seg_ptr, &L->seg_src, nullptr);
+  rc = source_sort(s, L, nnz + n, tgt, C->nnz + nc, &L->seg_ptr, &L->seg_src);
   SPH_CUDA(s, cudaStreamSynchronize(st));
   dfree(s, tgt);
   dfree(s, overflow);
@@ -1432,7 +1479,7 @@ static sph_rt_status build_ap(sph_rt *s, size_t l) {
                                                                   L->ap_col, map, dmap);
   SPH_LAUNCHED(s);
   // sources of each A P entry in increasing source order
-  if ((rc = bucket_sort(s, L, L->nnz + n, map, total, &L->ap_seg_ptr, &L->ap_seg_src, nullptr)))
+  if ((rc = source_sort(s, L, L->nnz + n, map, total, &L->ap_seg_ptr, &L->ap_seg_src)))
     return rc;
   // next level's Galerkin sources: the A P entries of its members' rows
   SphLevel *C = s->levels[l + 1];
@@ -1443,7 +1490,8 @@ static sph_rt_status build_ap(sph_rt *s, size_t l) {
   ap_galerkin_target_kernel<<<gcap(s, n, kBlock), kBlock, 0, s->stream>>>(
       n, L->ap_ptr, L->ap_col, L->agg, C->nnz, C->ptr, C->col, tgt, missing);
   SPH_LAUNCHED(s);
-  if ((rc = bucket_sort(s, L, total, tgt, C->nnz + C->n, &L->apg_ptr, &L->apg_src, nullptr)))
+  if ((rc = bucket_sort<int32_t>(s, L, total, tgt, C->nnz + C->n, &L->apg_ptr, &L->apg_src,
+                                 nullptr)))
     return rc;
   int miss = 0;
   SPH_CUDA(s, cudaMemcpyAsync(&miss, missing, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
@@ -1485,10 +1533,9 @@ static sph_rt_status build_structure(sph_rt *s) {
     if (!C) break;
     s->levels.push_back(C);
     // numeric Galerkin product for C so that the next strength test can run
-    galerkin_kernel<double><<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
-        C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, L->val, L->diag, C->val, C->diag,
-        C->invdiag);
-    SPH_LAUNCHED(s);
+    if ((rc = launch_galerkin<double>(s, C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, L->val,
+                                      L->diag, C->val, C->diag, C->invdiag)))
+      return rc;
     L = C;
   }
   s->amg_ready = true;
@@ -1593,20 +1640,20 @@ static sph_rt_status galerkin_levels(sph_rt *s) {
     SphLevel *L = s->levels[l], *C = s->levels[l + 1];
     const CsrView<T> Lv = LV::view(L), Cv = LV::view(C);
     if (L->ap_ptr) {  // A P of this level (its values are final: level l is done)
-      galerkin_kernel<T><<<gcap(s, L->nnz_ap, kBlock), kBlock, 0, s->stream>>>(
-          L->nnz_ap, 0, L->ap_seg_ptr, L->ap_seg_src, L->nnz, Lv.val, Lv.diag,
-          const_cast<T *>(LV::ap(L)), nullptr, nullptr);
-      SPH_LAUNCHED(s);
+      sph_rt_status rc = launch_galerkin<T>(s, L->nnz_ap, 0, L->ap_seg_ptr, L->ap_seg_src,
+                                            L->nnz, Lv.val, Lv.diag, const_cast<T *>(LV::ap(L)),
+                                            nullptr, nullptr);
+      if (rc) return rc;
     }
     T *cval = const_cast<T *>(Cv.val), *cdiag = const_cast<T *>(Cv.diag),
       *cinv = const_cast<T *>(Cv.invdiag);
-    if (L->apg_ptr)  // P^T (A P)
-      galerkin_kernel<T><<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
-          C->nnz, C->n, L->apg_ptr, L->apg_src, L->nnz_ap, LV::ap(L), nullptr, cval, cdiag, cinv);
-    else
-      galerkin_kernel<T><<<gcap(s, C->nnz + C->n, kBlock), kBlock, 0, s->stream>>>(
-          C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, Lv.val, Lv.diag, cval, cdiag, cinv);
-    SPH_LAUNCHED(s);
+    // P^T (A P): its sources are A P entries (fewer than 2^31)
+    sph_rt_status rc =
+        L->apg_ptr ? launch_galerkin<T>(s, C->nnz, C->n, L->apg_ptr, SrcList{L->apg_src, nullptr},
+                                        L->nnz_ap, LV::ap(L), nullptr, cval, cdiag, cinv)
+                   : launch_galerkin<T>(s, C->nnz, C->n, L->seg_ptr, L->seg_src, L->nnz, Lv.val,
+                                        Lv.diag, cval, cdiag, cinv);
+    if (rc) return rc;
   }
   // Gershgorin bounds of every level, turned into Chebyshev coefficients on
   // the device (slot 1 + l): no host read

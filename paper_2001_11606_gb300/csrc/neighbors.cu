@@ -1018,8 +1018,6 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
   int64_t nnz = 0;
   SPH_CUDA(s, cudaMemcpyAsync(&nnz, s->nbr_ptr + n_int, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   SPH_CUDA(s, cudaStreamSynchronize(st));
-  if (nnz >= ((int64_t)1 << 31) - 1)
-    return set_error(s, SPH_RT_EINVAL, "more than 2^31 neighbour pairs");
   s->nnz_nbr = nnz;
   s->nbr_col = dalloc<int32_t>(s, nnz);
   s->nbr_F = dalloc<double>(s, nnz);

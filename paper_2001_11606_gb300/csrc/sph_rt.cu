@@ -191,6 +191,7 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->dt_max = 1e300;
   c->dt_eta_floor = 1e-15;
   c->cell_list = SPH_RT_CELLS_AUTO;
+  c->index64 = 0;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -243,6 +244,7 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
            SPH_RT_EINVAL;
   if (c->cell_list < SPH_RT_CELLS_AUTO || c->cell_list > SPH_RT_CELLS_SORTED)
     return why = "cell_list must be SPH_RT_CELLS_AUTO, _DENSE or _SORTED", SPH_RT_EINVAL;
+  if (c->index64 < 0 || c->index64 > 1) return why = "index64 must be 0 or 1", SPH_RT_EINVAL;
   if (c->device < 0) return why = "device must be >= 0", SPH_RT_EINVAL;
   return SPH_RT_OK;
 }

@@ -66,6 +66,7 @@ class Config(C.Structure):
         ("reliable_drop", C.c_double),
         ("dt_target", C.c_double), ("dt_growth", C.c_double), ("dt_min", C.c_double),
         ("dt_max", C.c_double), ("dt_eta_floor", C.c_double), ("cell_list", C.c_int32),
+        ("index64", C.c_int32),
         ("device", C.c_int32),
         ("stream", C.c_void_p),
     ]

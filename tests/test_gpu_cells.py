@@ -1,7 +1,9 @@
-"""Neighbour search cell lists (row a1): the sorted 64-bit-key list (radix sort,
-hash table of occupied cells) gives the same slots, neighbour lists and steps
-as the dense key table, bit for bit, and takes grids the dense table refuses
-(more than 2^26 cells), where it still matches the brute-force oracle."""
+"""Size limits.  Neighbour search cell lists (row a1): the sorted 64-bit-key
+list (radix sort, hash table of occupied cells) gives the same slots,
+neighbour lists and steps as the dense key table, bit for bit, and takes grids
+the dense table refuses (more than 2^26 cells), where it still matches the
+brute-force oracle.  The AMG set-up's 64-bit source lists (for more than
+2^31 - 1 entries) change no bit."""
 import numpy as np
 import pytest
 
@@ -82,3 +84,52 @@ def test_grid_beyond_2_29_cells_along_an_axis_is_refused():
     with pytest.raises(sphrt.SphRtError) as ex:
         sphrt.solver_for(w)
     assert ex.value.status == sphrt.EINVAL and "2^29" in str(ex.value)
+
+
+# 64-bit Galerkin source lists (taken automatically for a level with 2^31 - 1
+# or more entries plus rows) give the same hierarchy and steps as 32-bit ones
+@pytest.mark.parametrize("over", [dict(precision=sphrt.FP64),
+                                  dict(precision=sphrt.MIXED),
+                                  dict(precision=sphrt.MIXED, fine_post_smooth=0,
+                                       reliable_drop=1e-6)])
+def test_index64_source_lists_change_no_bit(over):
+    w = I.mms_3d_lp(n=24, steps=2)
+    out = []
+    for wide in (0, 1):
+        S = sphrt.solver_for(w, index64=wide, **over)
+        for n in range(1, 3):
+            Qe, QE, ge, gE = w.step_inputs(n)
+            S.step(w.dt, Qe, QE, ge, gE)
+        e, E, _ = S.get_energies()
+        out.append((e, E))
+        S.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_beyond_2_31_neighbour_pairs_and_operator_entries():
+    """280^3 manufactured problem: 2.35e9 neighbour pairs and 2.32e9 operator
+    entries (both past 2^31, so the AMG lists are 64-bit); sampled neighbour
+    rows match the brute-force oracle bit for bit and a step converges.  Needs
+    about 175 GB of device memory."""
+    torch = pytest.importorskip("torch")
+    free, _ = torch.cuda.mem_get_info()
+    if free < 200e9:
+        pytest.skip(f"needs ~175 GB of free device memory ({free / 1e9:.0f} GB free)")
+    w = I.mms_3d(n=280, steps=1)
+    P = w.particles
+    S = sphrt.solver_for(w)
+    n_int, nnz_nbr, nnz_op = S.sizes()
+    assert n_int == 280**3 and nnz_nbr > 2**31 and nnz_op + n_int > 2**31
+    rp, cols = S.get_neighbors()
+    rng = np.random.default_rng(1)
+    interior = np.flatnonzero(P.kind == 0)
+    rows = np.concatenate([rng.choice(interior, 16, replace=False), interior[:4], interior[-4:]])
+    orp, ocols = O.neighbors_of_rows(P.pos, P.h, rows)
+    for k, i in enumerate(rows):
+        assert np.array_equal(cols[rp[i]:rp[i + 1]], ocols[orp[k]:orp[k + 1]].astype(np.int64))
+    del rp, cols
+    rc, st = S.step(w.dt, *w.step_inputs(1))
+    assert rc == 0 and 1 <= st.outer_iters <= 4
+    e, E, _ = S.get_energies()
+    assert np.all(np.isfinite(E)) and np.all(E[P.kind == 0] > 0)
+    S.close()
