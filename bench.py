@@ -148,16 +148,13 @@ NCU_TRAFFIC = {
 }
 
 
-# Solver settings measured best per workload (both arithmetic forms), applied
-# unless given on the command line and recorded in the line's config.  At 128^3
-# the V-cycle without finest-level post-smoothing (its sweeps give the CG
-# product) is faster in both forms; at 64^3 the symmetric V-cycle is.  In the
-# mixed form, FP64 residual replacements only at convergence (reliable_drop
-# 1e-6) measured faster than every 1e-4 (4 FP64 residual sweeps per step
-# instead of 5), with the same iteration counts.
-WORKLOAD_SETTINGS = {
-    "mms3d-128": dict(fine_post_smooth=0, reliable_drop=1e-6),
-}
+# Solver settings: unless given on the command line (--fine-post-smooth,
+# --reliable-drop), each form's timed solver tunes them itself on its first
+# warm-up step (config.autotune = 1: finest-level post-smoothing on or off,
+# Chebyshev degree, the mixed form's reliable-update threshold); the kernel-
+# timing and end-to-end passes then run the chosen settings (autotune = 2: the
+# SpMV loads in flight only).  The choice and the trial times are in the line's
+# config.solver.
 
 
 def make_workload(name: str):
@@ -621,15 +618,20 @@ def main():
     head = forms[0]
     prec_of = {"mixed": sphrt.MIXED, "fp64": sphrt.FP64}
     extra = {"check_every": args.check_every} if args.check_every else {}
-    extra.update(WORKLOAD_SETTINGS.get(args.workload, {}))
     if args.fine_post_smooth is not None:
         extra["fine_post_smooth"] = args.fine_post_smooth
     if args.reliable_drop is not None:
         extra["reliable_drop"] = args.reliable_drop
+    tune = args.fine_post_smooth is None and args.reliable_drop is None
+    chosen = {f: {} for f in forms}  # the timed solver's tuned settings, per form
+    trials = {}
 
     def make_cfg(form, **kw):
+        settings = dict(extra, **chosen[form])
+        settings["autotune"] = 1 if tune and not chosen[form] else 2
+        settings.update(kw)
         return sphrt.config_from_params(w.params, device=local, stream=stream.cuda_stream,
-                                        precond=precond, precision=prec_of[form], **extra, **kw)
+                                        precond=precond, precision=prec_of[form], **settings)
 
     # ---- inputs resident in HBM --------------------------------------------
     f64 = dict(dtype=torch.float64, device=dev)
@@ -689,6 +691,10 @@ def main():
         timed[form] = dict(value=work / t_max, t_max=t_max, launches=S.launch_count() - launches0,
                            outer=sum(i[0] for i in iters) / (args.steps * T),
                            krylov=sum(i[1] for i in iters) / (args.steps * T))
+        c = S.get_config()
+        chosen[form] = dict(fine_post_smooth=c.fine_post_smooth, cheb_degree=c.cheb_degree,
+                            reliable_drop=c.reliable_drop)
+        trials[form] = S.solver_tuning()
         S.close()
     clocks = sampler.stop()
 
@@ -789,7 +795,11 @@ def main():
                        "l2": "inputs larger than L2 (operator > 129 MB)",
                        "outer_iters_per_step": hd["outer"], "krylov_iters_per_step": hd["krylov"],
                        "ms_per_time_step": 1e3 * hd["t_max"] / (args.steps * T),
-                       "solver": {k: v for k, v in extra.items()}},
+                       "solver": {f: dict(chosen[f], tuned=tune,
+                                          trials_ms=[{"fine_post_smooth": t[0], "cheb_degree": t[1],
+                                                      "reliable_drop": t[2], "ms": t[3]}
+                                                     for t in trials.get(f, [])])
+                                  for f in forms}},
             "clocks": clocks, "e2e": e2e, "gpu_launches": hd["launches"], "roofline": roof,
             "cpu_baseline": cpu}
     if len(forms) > 1:

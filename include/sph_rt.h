@@ -94,11 +94,19 @@ typedef struct {
   double amg_theta;     /* AMG strength threshold: j strong for i if |B_ij| >= theta sqrt(B_ii B_jj) */
   int32_t check_every;  /* Krylov iterations queued between host convergence reads */
   int32_t kernel_timing;/* 1: record CUDA events around SpMV launches (sph_rt_kernel_stats) */
-  int32_t autotune;     /* 1: time the fine SpMV loads-in-flight (U = 4 or 8) on the first step
-                           of a particle set; 0 (default): U from the mean row length.  U never
-                           changes a result bit (the lanes per row, W, follow the row length).
-                           In a batch (sph_rt_batch_*): tune the batched launch's lanes per
-                           row and Chebyshev degree on its first step */
+  int32_t autotune;     /* 1: autotune on the first step.  The fine SpMV loads in flight (U = 4
+                           or 8; never changes a result bit) on the first step of a particle
+                           set, and once per handle the smoother: one timed trial step (after
+                           an untimed one that captures its graph) from the same state for
+                           each candidate -- with the AMG preconditioner finest-level
+                           post-smoothing off (fine_post_smooth = 0, cheb_degree = 1; in the
+                           mixed form with reliable_drop 1e-4 and 1e-6) or on with
+                           cheb_degree 1, 2, 3; with the Chebyshev preconditioner degrees 1,
+                           2, 3, 4, 6 -- keeping the fastest that converges in the handle's
+                           configuration (sph_rt_get_config, sph_rt_get_solver_tuning).  The
+                           state is restored after every trial.  2: the loads in flight only.
+                           0 (default): as configured.  In a batch (sph_rt_batch_*), 1 tunes
+                           the batched launch's shape on its first step */
   int32_t amg_tail;     /* 1: run the small AMG levels (each <= 600k stored entries) of every
                            V-cycle as one thread-block-cluster launch (bitwise the same result;
                            default 0: measured no faster than the per-level launches) */
@@ -330,6 +338,21 @@ int64_t sph_rt_launch_count(const sph_rt *s);
  * was captured (once per particle set / AMG hierarchy / dt while nothing else
  * changes) and launched (once per step).  Either pointer may be NULL. */
 sph_rt_status sph_rt_loop_graph_info(const sph_rt *s, int64_t *captures, int64_t *launches);
+
+/* The handle's configuration as it stands (the solver autotuner's choice
+ * included). */
+sph_rt_status sph_rt_get_config(const sph_rt *s, sph_rt_config *cfg);
+
+/* Trials of the solver autotuner (config.autotune): *count = the number of
+ * trials (0 before the first step or without autotune), the first min(cap,
+ * count) copied to trials (may be NULL).  ms is the timed trial step's CUDA-
+ * event time, -1 where the step did not converge. */
+typedef struct {
+  int32_t fine_post_smooth, cheb_degree;
+  double reliable_drop, ms;
+} sph_rt_tune_trial;
+sph_rt_status sph_rt_get_solver_tuning(const sph_rt *s, sph_rt_tune_trial *trials, int32_t cap,
+                                       int32_t *count);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: a continuous-batching request loop over many independent        */

@@ -1213,7 +1213,7 @@ static sph_rt_status batch_ready(sph_rt_batch *B, double dt) {
   sph_rt_status rc;
   if (!B->packed && (rc = batch_pack(B))) return rc;
   SPH_CUDA(B->h, cudaSetDevice(B->h->cfg.device));
-  if (B->cfg.autotune && !B->tuned && !B->shape_set && (rc = batch_autotune(B, dt, nullptr)))
+  if (B->cfg.autotune == 1 && !B->tuned && !B->shape_set && (rc = batch_autotune(B, dt, nullptr)))
     return rc;
   return batch_groups(B);
 }

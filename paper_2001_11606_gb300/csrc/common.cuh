@@ -652,6 +652,9 @@ struct sph_rt {
   // row-group shape of the fine SpMV-class kernels (autotuned or from the mean row length)
   sphrt::RowShape fine_shape{16, 6};
   bool fine_shape_set = false;
+  // solver autotuner (config.autotune): done once per handle; its trials
+  bool solver_tuned = false;
+  std::vector<sph_rt_tune_trial> tune_trials;
 
   // kernel timing
   std::vector<cudaEvent_t> ev_pool;

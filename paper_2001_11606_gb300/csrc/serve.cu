@@ -268,7 +268,7 @@ void run_fused(sph_rt_srv *S, std::vector<std::shared_ptr<Request>> &group) {
   }
   std::string shape_key;
   bool shape_known = false;
-  if (c.autotune) {
+  if (c.autotune == 1) {
     sph_rt_config kc = c;
     kc.device = 0;
     const double dt = group[0]->dt;
@@ -302,7 +302,7 @@ void run_fused(sph_rt_srv *S, std::vector<std::shared_ptr<Request>> &group) {
     std::vector<int32_t> st(K, 0), ou(K, 0), kr(K, 0);
     rc = sph_rt_batch_run(B, members[0]->dt, members[0]->steps, st.data(), ou.data(), kr.data());
     const bool hard = rc != SPH_RT_OK && rc != SPH_RT_ENOTCONV;
-    if (c.autotune && !shape_known && !hard) {
+    if (c.autotune == 1 && !shape_known && !hard) {
       sph_rt_batch_shape sh;
       if (sph_rt_batch_get_shape(B, &sh) == 0) {
         std::lock_guard<std::mutex> lk(S->mu);

@@ -245,6 +245,7 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
   if (c->cell_list < SPH_RT_CELLS_AUTO || c->cell_list > SPH_RT_CELLS_SORTED)
     return why = "cell_list must be SPH_RT_CELLS_AUTO, _DENSE or _SORTED", SPH_RT_EINVAL;
   if (c->index64 < 0 || c->index64 > 1) return why = "index64 must be 0 or 1", SPH_RT_EINVAL;
+  if (c->autotune < 0 || c->autotune > 2) return why = "autotune must be 0, 1 or 2", SPH_RT_EINVAL;
   if (c->device < 0) return why = "device must be >= 0", SPH_RT_EINVAL;
   return SPH_RT_OK;
 }
@@ -315,6 +316,20 @@ extern "C" const char *sph_rt_last_error(const sph_rt *s) {
 }
 
 extern "C" int64_t sph_rt_launch_count(const sph_rt *s) { return s ? s->launches : 0; }
+
+extern "C" sph_rt_status sph_rt_get_config(const sph_rt *s, sph_rt_config *cfg) {
+  if (!s || !cfg) return SPH_RT_EINVAL;
+  *cfg = s->cfg;
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_get_solver_tuning(const sph_rt *s, sph_rt_tune_trial *trials,
+                                                  int32_t cap, int32_t *count) {
+  if (!s || !count || cap < 0) return SPH_RT_EINVAL;
+  *count = (int32_t)s->tune_trials.size();
+  for (int32_t k = 0; trials && k < cap && k < *count; ++k) trials[k] = s->tune_trials[k];
+  return SPH_RT_OK;
+}
 
 extern "C" sph_rt_status sph_rt_loop_graph_info(const sph_rt *s, int64_t *captures,
                                                 int64_t *launches) {
@@ -658,9 +673,15 @@ static sph_rt_status read_scalars(sph_rt *s) {
   return SPH_RT_OK;
 }
 
+static sph_rt_status tune_then_step(sph_rt *s, double dt, const double *Qe_c,
+                                    const double *QE_c, const double *ge_c, const double *gE_c,
+                                    sph_rt_stats *stats);
+
 static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const double *QE_c,
                                  const double *ge_c, const double *gE_c, sph_rt_stats *stats) {
   sph_rt_status rc;
+  if (s->cfg.autotune == 1 && !s->solver_tuned)
+    return tune_then_step(s, dt, Qe_c, QE_c, ge_c, gE_c, stats);
   PhaseTimer tm{s, {}};
   double ms[5] = {0, 0, 0, 0, 0};  // setup, assembly, amg, krylov, newton
   sph_rt_stats st;
@@ -784,6 +805,102 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   st.t_newton_ms = ms[4];
   if (stats) *stats = st;
   return SPH_RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the solver (config.autotune), run once per handle on its first
+// step.  The balance between a stronger smoother (fewer Krylov iterations)
+// and its sweeps, and whether the finest level's post-smoothing pays (the
+// V-cycle-product CG drops it and takes the CG product from the V-cycle's
+// A P sweep), depends on the operator and the size: measured at 64^3 the
+// symmetric V-cycle wins, at 128^3 the V-cycle-product CG.  Each candidate
+// runs the step twice from the same state -- the first run captures its step
+// graph (and on the first candidate builds the AMG structure), the second is
+// timed with CUDA events on the handle's stream -- and the state is restored
+// from the step's own snapshot after each run.  A candidate whose step does
+// not converge is skipped; the fastest of the others is kept in s->cfg.
+// ---------------------------------------------------------------------------
+static sph_rt_status tune_then_step(sph_rt *s, double dt, const double *Qe_c,
+                                    const double *QE_c, const double *ge_c, const double *gE_c,
+                                    sph_rt_stats *stats) {
+  s->solver_tuned = true;  // the trials below are steps too
+  s->tune_trials.clear();
+  const sph_rt_config c0 = s->cfg;
+  std::vector<sph_rt_tune_trial> cand;
+  if (c0.precond == SPH_RT_PRECOND_JACOBI)  // nothing to tune
+    return step_common(s, dt, Qe_c, QE_c, ge_c, gE_c, stats);
+  if (c0.precond == SPH_RT_PRECOND_AMG) {
+    cand.push_back({0, 1, c0.reliable_drop, -1.0});
+    if (c0.precision == SPH_RT_MIXED)
+      for (double drop : {1e-4, 1e-6})
+        if (drop != c0.reliable_drop) cand.push_back({0, 1, drop, -1.0});
+    for (int deg : {1, 2, 3}) cand.push_back({1, deg, c0.reliable_drop, -1.0});
+  } else {
+    for (int deg : {1, 2, 3, 4, 6}) cand.push_back({c0.fine_post_smooth, deg, c0.reliable_drop, -1.0});
+  }
+  const size_t nb = sizeof(double) * (size_t)s->n;
+  // the step inputs, kept for every trial (a staged host input sits in a
+  // buffer that a step may also use as scratch)
+  const double *in[4] = {Qe_c, QE_c, ge_c, gE_c};
+  double *keep[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int a = 0; a < 4; ++a) {
+    if (!in[a]) continue;
+    if (!(keep[a] = dalloc<double>(s, s->n))) return SPH_RT_ENOMEM;
+    SPH_CUDA(s, cudaMemcpyAsync(keep[a], in[a], nb, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  SPH_CUDA(s, cudaEventCreate(&ev[0]));
+  if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return set_error(s, SPH_RT_EDEVICE, "autotune: cudaEventCreate failed");
+  }
+  sph_rt_status rc = SPH_RT_OK;
+  int best = -1;
+  for (size_t k = 0; k < cand.size() && !rc; ++k) {
+    s->cfg.fine_post_smooth = cand[k].fine_post_smooth;
+    s->cfg.cheb_degree = cand[k].cheb_degree;
+    s->cfg.reliable_drop = cand[k].reliable_drop;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (cudaEventRecord(ev[0], s->stream) != cudaSuccess) {
+        rc = set_error(s, SPH_RT_EDEVICE, "autotune: cudaEventRecord failed");
+        break;
+      }
+      sph_rt_status r2 = step_common(s, dt, keep[0], keep[1], keep[2], keep[3], nullptr);
+      if (r2 == SPH_RT_ENOTCONV) break;  // the step restored its snapshot itself
+      if (r2) {
+        rc = r2;
+        break;
+      }
+      float ms = -1.0f;
+      if (cudaEventRecord(ev[1], s->stream) != cudaSuccess ||
+          cudaMemcpyAsync(s->e, s->e_bak, nb, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess ||
+          cudaMemcpyAsync(s->E, s->E_bak, nb, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess ||
+          cudaStreamSynchronize(s->stream) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
+        rc = set_error(s, SPH_RT_EDEVICE, "autotune: CUDA error in a trial");
+        break;
+      }
+      if (rep == 1) cand[k].ms = ms;
+    }
+    if (!rc && cand[k].ms >= 0.0 && (best < 0 || cand[k].ms < cand[best].ms)) best = (int)k;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  s->tune_trials = cand;
+  s->cfg = c0;
+  if (best >= 0) {
+    s->cfg.fine_post_smooth = cand[best].fine_post_smooth;
+    s->cfg.cheb_degree = cand[best].cheb_degree;
+    s->cfg.reliable_drop = cand[best].reliable_drop;
+  }
+  if (!rc) {
+    // the step itself, from the kept inputs (the staged ones may be overwritten)
+    s->err.clear();
+    rc = step_common(s, dt, keep[0], keep[1], keep[2], keep[3], stats);
+  }
+  cudaStreamSynchronize(s->stream);
+  for (double *p : keep) dfree(s, p);
+  return rc;
 }
 
 static sph_rt_status step_entry(sph_rt *s, double dt, const double *Qe, const double *QE,

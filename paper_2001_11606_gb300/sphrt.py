@@ -72,6 +72,12 @@ class Config(C.Structure):
     ]
 
 
+class TuneTrial(C.Structure):
+    """sph_rt_tune_trial."""
+    _fields_ = [("fine_post_smooth", C.c_int32), ("cheb_degree", C.c_int32),
+                ("reliable_drop", C.c_double), ("ms", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [
         ("outer_iters", C.c_int32),
@@ -137,6 +143,8 @@ _SIGNATURES = [
     ("sph_rt_kernel_stats", C.c_int, [_P, _P, _P, _P, C.c_int]),
     ("sph_rt_get_amg_info", C.c_int, [_P, _P, _P, _P, C.c_int32]),
     ("sph_rt_loop_graph_info", C.c_int, [_P, _P, _P]),
+    ("sph_rt_get_config", C.c_int, [_P, _P]),
+    ("sph_rt_get_solver_tuning", C.c_int, [_P, _P, C.c_int32, _P]),
     ("sph_rt_kernel_stats_kind", C.c_int, [_P, C.c_int32, _P, _P, _P]),
     ("sph_rt_launch_count", C.c_int64, [_P]),
     ("sph_rt_last_error", C.c_char_p, [_P]),
@@ -424,6 +432,22 @@ class Solver:
         cap, lau = C.c_int64(), C.c_int64()
         self._check(self._L.sph_rt_loop_graph_info(self._h, C.byref(cap), C.byref(lau)))
         return cap.value, lau.value
+
+    def get_config(self) -> "Config":
+        """The handle's configuration as it stands (the autotuner's choice included)."""
+        cfg = Config()
+        self._check(self._L.sph_rt_get_config(self._h, C.byref(cfg)))
+        return cfg
+
+    def solver_tuning(self):
+        """Trials of the solver autotuner: [(fine_post_smooth, cheb_degree,
+        reliable_drop, ms or None if the step did not converge)]."""
+        cnt = C.c_int32()
+        self._check(self._L.sph_rt_get_solver_tuning(self._h, None, 0, C.byref(cnt)))
+        arr = (TuneTrial * max(cnt.value, 1))()
+        self._check(self._L.sph_rt_get_solver_tuning(self._h, arr, cnt.value, C.byref(cnt)))
+        return [(t.fine_post_smooth, t.cheb_degree, t.reliable_drop,
+                 t.ms if t.ms >= 0 else None) for t in arr[: cnt.value]]
 
 
 def config_from_params(params: dict, **overrides) -> Config:
