@@ -453,6 +453,22 @@ sph_rt_status sph_rt_batch_add(sph_rt_batch *b, int64_t n_total, const double *p
                                const double *sigma0, const int32_t *kind, const int64_t *copy_of,
                                const double *e0, const double *E0, int32_t *index);
 
+/* Several problems at once: their set-ups run on `threads` host threads (<= 0:
+ * 1), each problem on its own stream (the GPU work of large problems overlaps;
+ * small ones are bound by the driver's allocation calls).  The arrays
+ * are as for sph_rt_batch_add; problem k gets index *first_index + k (may be
+ * NULL).  All or none are added: on an error no problem is added, and the
+ * message names the first failing problem. */
+typedef struct {
+  int64_t n_total;
+  const double *pos, *mass, *rho, *h, *sigma0;
+  const int32_t *kind;
+  const int64_t *copy_of;
+  const double *e0, *E0;
+} sph_rt_problem;
+sph_rt_status sph_rt_batch_add_many(sph_rt_batch *b, int32_t count, const sph_rt_problem *problems,
+                                    int32_t threads, int32_t *first_index);
+
 /* Constant sources of one problem (caller order, NULL = 0), used every step. */
 sph_rt_status sph_rt_batch_set_sources(sph_rt_batch *b, int32_t index, const double *Qe,
                                        const double *QE);

@@ -21,7 +21,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -768,6 +770,74 @@ extern "C" sph_rt_status sph_rt_batch_add(sph_rt_batch *B, int64_t n_total, cons
   return SPH_RT_OK;
 }
 
+extern "C" sph_rt_status sph_rt_batch_add_many(sph_rt_batch *B, int32_t count,
+                                               const sph_rt_problem *problems, int32_t threads,
+                                               int32_t *first_index) {
+  if (!B || count < 0 || (count > 0 && !problems)) return SPH_RT_EINVAL;
+  if (B->packed) return set_error(B->h, SPH_RT_ESTATE, "batch already stepped; create a new one");
+  if (first_index) *first_index = (int32_t)B->items.size();
+  if (count == 0) return SPH_RT_OK;
+  sph_rt_config c = B->cfg;
+  c.stream = nullptr;
+  // one staging handle per problem (own stream), set up by `threads` host
+  // threads.  For problems of a few thousand particles the set-up is bound by
+  // the driver's allocation and launch calls, which do not scale with host
+  // threads (measured: 230 problems in 0.31-0.40 s with 1-16 threads); larger
+  // problems' GPU work overlaps across the threads' streams.
+  std::vector<sph_rt *> hs((size_t)count, nullptr);
+  std::vector<sph_rt_status> rcs((size_t)count, SPH_RT_OK);
+  std::vector<std::string> errs((size_t)count);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    cudaSetDevice(c.device);
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= count) break;
+      const sph_rt_problem &q = problems[k];
+      sph_rt *t = nullptr;
+      sph_rt_status rc = sph_rt_create(&c, &t);
+      if (rc) {
+        rcs[k] = rc;
+        errs[k] = sph_rt_last_error(nullptr);
+        continue;
+      }
+      rc = sph_rt_set_particles(t, q.n_total, q.pos, q.mass, q.rho, q.h, q.sigma0, q.kind,
+                                q.copy_of, q.e0, q.E0);
+      if (rc) {
+        rcs[k] = rc;
+        errs[k] = sph_rt_last_error(t);
+        sph_rt_destroy(t);
+        continue;
+      }
+      hs[k] = t;
+    }
+  };
+  int nt = threads > 0 ? threads : 1;
+  if (nt > count) nt = count;
+  std::vector<std::thread> pool;
+  for (int a = 1; a < nt; ++a) pool.emplace_back(work);
+  work();
+  for (auto &th : pool) th.join();
+  for (int k = 0; k < count; ++k) {
+    if (rcs[k] == SPH_RT_OK) continue;
+    for (sph_rt *t : hs)
+      if (t) sph_rt_destroy(t);
+    return set_error(B->h, rcs[k], "problem " + std::to_string(k) + ": " + errs[k]);
+  }
+  for (int k = 0; k < count; ++k) {
+    sph_rt *t = hs[k];
+    BatchItem it;
+    it.n = t->n;
+    it.n_int = t->n_int;
+    it.nnz_nbr = t->nnz_nbr;
+    it.nnz_mat = t->nnz_mat;
+    it.nnz_gh = t->nnz_gh;
+    B->items.push_back(it);
+    B->staging.push_back(t);
+  }
+  return SPH_RT_OK;
+}
+
 static int max_cluster_for(int bps);
 
 static sph_rt_status batch_pack(sph_rt_batch *B) {
@@ -869,8 +939,11 @@ static sph_rt_status batch_pack(sph_rt_batch *B) {
     B->items[k].slot2caller.resize(n);
     SPH_CUDA(s, cudaMemcpyAsync(B->items[k].slot2caller.data(), t->slot2caller,
                                 sizeof(int64_t) * n, cudaMemcpyDeviceToHost, st));
-    SPH_CUDA(s, cudaStreamSynchronize(st));
-    sph_rt_destroy(t);
+  }
+  // one wait for all the copies, then the staging handles go
+  SPH_CUDA(s, cudaStreamSynchronize(st));
+  for (int k = 0; k < K; ++k) {
+    sph_rt_destroy(B->staging[k]);
     B->staging[k] = nullptr;
   }
   B->staging.clear();

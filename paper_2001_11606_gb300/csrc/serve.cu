@@ -280,12 +280,25 @@ void run_fused(sph_rt_srv *S, std::vector<std::shared_ptr<Request>> &group) {
   }
   std::vector<std::shared_ptr<Request>> members;
   std::vector<int32_t> index;
-  for (auto &R : group) {
-    int32_t k = -1;
-    sph_rt_status r2 = sph_rt_batch_add(B, R->n, R->pos.data(), R->mass.data(), R->rho.data(),
-                                        R->h.data(), R->sigma0.data(), R->kind.data(),
-                                        R->has_copy ? R->copy_of.data() : nullptr,
-                                        R->e0.data(), R->E0.data(), &k);
+  // all members' set-ups at once (overlapping on the GPU); if that fails, one
+  // by one, so that only the failing requests fail
+  std::vector<sph_rt_problem> probs;
+  for (auto &R : group)
+    probs.push_back({R->n, R->pos.data(), R->mass.data(), R->rho.data(), R->h.data(),
+                     R->sigma0.data(), R->kind.data(), R->has_copy ? R->copy_of.data() : nullptr,
+                     R->e0.data(), R->E0.data()});
+  int32_t first = 0;
+  const bool all_in =
+      sph_rt_batch_add_many(B, (int32_t)probs.size(), probs.data(), 1, &first) == SPH_RT_OK;
+  for (size_t m = 0; m < group.size(); ++m) {
+    auto &R = group[m];
+    int32_t k = all_in ? first + (int32_t)m : -1;
+    sph_rt_status r2 = SPH_RT_OK;
+    if (!all_in)
+      r2 = sph_rt_batch_add(B, R->n, R->pos.data(), R->mass.data(), R->rho.data(), R->h.data(),
+                            R->sigma0.data(), R->kind.data(),
+                            R->has_copy ? R->copy_of.data() : nullptr, R->e0.data(),
+                            R->E0.data(), &k);
     if (!r2 && (R->has_Qe || R->has_QE))
       r2 = sph_rt_batch_set_sources(B, k, R->has_Qe ? R->Qe.data() : nullptr,
                                     R->has_QE ? R->QE.data() : nullptr);

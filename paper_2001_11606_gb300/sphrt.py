@@ -159,6 +159,7 @@ _SIGNATURES = [
     ("sph_rt_srv_destroy", None, [_P]),
     ("sph_rt_batch_create", C.c_int, [_P, _P]),
     ("sph_rt_batch_add", C.c_int, [_P, C.c_int64] + [_P] * 10),
+    ("sph_rt_batch_add_many", C.c_int, [_P, C.c_int32, _P, C.c_int32, _P]),
     ("sph_rt_batch_set_sources", C.c_int, [_P, C.c_int32, _P, _P]),
     ("sph_rt_batch_step", C.c_int, [_P, C.c_double, _P, _P, _P, _P]),
     ("sph_rt_batch_run", C.c_int, [_P, C.c_double, C.c_int32, _P, _P, _P]),
@@ -546,6 +547,13 @@ class Server:
             pass
 
 
+class Problem(C.Structure):
+    """sph_rt_problem (arrays as for sph_rt_batch_add)."""
+    _fields_ = [("n_total", C.c_int64)] + [(f, C.c_void_p) for f in
+                                           ("pos", "mass", "rho", "h", "sigma0", "kind",
+                                            "copy_of", "e0", "E0")]
+
+
 class BatchShape(C.Structure):
     """sph_rt_batch_shape."""
     _fields_ = [("lanes_per_row", C.c_int32), ("cheb_degree", C.c_int32),
@@ -582,6 +590,28 @@ class Batch:
                                              _ptr(_f64(E0, n)), C.byref(idx)))
         self._n.append(n)
         return idx.value
+
+    def add_many(self, problems, threads=1):
+        """Add [(particles, e0, E0)] with their set-ups on `threads` host threads;
+        returns the first index (problem k gets first + k)."""
+        keep = []
+        arr = (Problem * max(len(problems), 1))()
+        for k, (P, e0, E0) in enumerate(problems):
+            n = P.pos.shape[0]
+            a = dict(pos=_f64(P.pos), mass=_f64(P.mass, n), rho=_f64(P.rho, n), h=_f64(P.h, n),
+                     sigma0=_f64(P.sigma0, n), kind=np.ascontiguousarray(P.kind, dtype=np.int32),
+                     copy_of=(np.ascontiguousarray(P.copy_of, dtype=np.int64)
+                              if np.any(P.kind == COPY) else None),
+                     e0=_f64(e0, n), E0=_f64(E0, n))
+            keep.append(a)
+            arr[k].n_total = n
+            for f, v in a.items():
+                setattr(arr[k], f, None if v is None else v.ctypes.data)
+        first = C.c_int32()
+        self._check(self._L.sph_rt_batch_add_many(self._h, len(problems), arr, int(threads),
+                                                  C.byref(first)))
+        self._n.extend(P.pos.shape[0] for P, _, _ in problems)
+        return first.value
 
     def set_sources(self, index, Qe=None, QE=None):
         n = self._n[index]

@@ -187,3 +187,33 @@ def test_config_autotune_tunes_on_the_first_run():
     assert info["nnz_operator"] > info["n_interior"] and info["nnz_neighbours"] > 0
     ref.close()
     B.close()
+
+
+def test_add_many_equals_one_by_one_and_is_all_or_none():
+    probs = _problems(3, k=6, seed=66)
+    cfg = sphrt.config_from_params(probs[0].params, **TIGHT)
+    A = sphrt.Batch(cfg)
+    for w in probs:
+        A.add(w.particles, w.e0, w.E0)
+    B = sphrt.Batch(cfg)
+    # a bad problem in the middle: nothing is added
+    bad = probs[2].particles
+    pos = bad.pos.copy()
+    pos[5, 0] = np.nan
+    Pbad = I.Particles(dim=bad.dim, dx=bad.dx, counts=bad.counts, pos=pos, kind=bad.kind,
+                       copy_of=bad.copy_of, mass=bad.mass, rho=bad.rho, h=bad.h,
+                       sigma0=bad.sigma0)
+    with pytest.raises(sphrt.SphRtError) as ex:
+        B.add_many([(w.particles, w.e0, w.E0) for w in probs[:2]] + [(Pbad, probs[2].e0,
+                                                                      probs[2].E0)])
+    assert ex.value.status == sphrt.EINVAL and "problem 2" in str(ex.value)
+    B._n = []
+    assert B.add_many([(w.particles, w.e0, w.E0) for w in probs], threads=3) == 0
+    for X in (A, B):
+        rc, st, ou, kr = X.run(probs[0].dt, 2)
+        assert np.all(st == 0)
+    for k in range(len(probs)):
+        (e1, E1), (e2, E2) = A.get_energies(k), B.get_energies(k)
+        assert np.array_equal(e1, e2) and np.array_equal(E1, E2)
+    A.close()
+    B.close()
