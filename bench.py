@@ -374,7 +374,7 @@ def run_batch(args):
         g = groups[d]
         cfg = sphrt.config_from_params(g[0].params, device=local, stream=streams[d].cuda_stream)
         B = sphrt.Batch(cfg)
-        B.add_many([(w.particles, w.e0, w.E0) for w in g])
+        B.add_many([(w.particles, w.e0, w.E0) for w in g], threads=4)
         if shape is not None:
             B.set_shape(*shape)
         return B

@@ -454,8 +454,7 @@ sph_rt_status sph_rt_batch_add(sph_rt_batch *b, int64_t n_total, const double *p
                                const double *e0, const double *E0, int32_t *index);
 
 /* Several problems at once: their set-ups run on `threads` host threads (<= 0:
- * 1), each problem on its own stream (the GPU work of large problems overlaps;
- * small ones are bound by the driver's allocation calls).  The arrays
+ * 1), each problem on its own stream, so that they overlap on the GPU.  The arrays
  * are as for sph_rt_batch_add; problem k gets index *first_index + k (may be
  * NULL).  All or none are added: on an error no problem is added, and the
  * message names the first failing problem. */

@@ -780,10 +780,9 @@ extern "C" sph_rt_status sph_rt_batch_add_many(sph_rt_batch *B, int32_t count,
   sph_rt_config c = B->cfg;
   c.stream = nullptr;
   // one staging handle per problem (own stream), set up by `threads` host
-  // threads.  For problems of a few thousand particles the set-up is bound by
-  // the driver's allocation and launch calls, which do not scale with host
-  // threads (measured: 230 problems in 0.31-0.40 s with 1-16 threads); larger
-  // problems' GPU work overlaps across the threads' streams.
+  // threads; their buffers come from the library's cache of freed device
+  // memory once an earlier batch has been destroyed (measured, 120 3-D
+  // problems of 1k-20k particles: 0.091 s with 1 thread, 0.042 s with 4)
   std::vector<sph_rt *> hs((size_t)count, nullptr);
   std::vector<sph_rt_status> rcs((size_t)count, SPH_RT_OK);
   std::vector<std::string> errs((size_t)count);

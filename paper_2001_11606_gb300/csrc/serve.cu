@@ -289,7 +289,7 @@ void run_fused(sph_rt_srv *S, std::vector<std::shared_ptr<Request>> &group) {
                      R->e0.data(), R->E0.data()});
   int32_t first = 0;
   const bool all_in =
-      sph_rt_batch_add_many(B, (int32_t)probs.size(), probs.data(), 1, &first) == SPH_RT_OK;
+      sph_rt_batch_add_many(B, (int32_t)probs.size(), probs.data(), 4, &first) == SPH_RT_OK;
   for (size_t m = 0; m < group.size(); ++m) {
     auto &R = group[m];
     int32_t k = all_in ? first + (int32_t)m : -1;

@@ -8,6 +8,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -74,10 +76,61 @@ bool cuda_ok(sph_rt *s, cudaError_t e, const char *what) {
 // buffers released by free_all() go to a size-keyed free list and are handed
 // out again (best fit, at most twice the request) by the next particle set, so
 // re-setting particles of similar size does no cudaFree/cudaMalloc (both of
-// which synchronise the device).  Everything is returned to CUDA on destroy,
-// or when an allocation fails (then the request is retried once).
+// which synchronise the device).  A destroyed handle gives its buffers to a
+// library-wide cache per device (up to kCacheBytes; beyond that they go back
+// to CUDA), from which new handles take before calling cudaMalloc: a batch's
+// staging handles and the serving loop's fused batches, created and destroyed
+// again and again, then neither allocate nor synchronise the device.  A
+// handle hands buffers on only after its stream has finished with them.  When
+// an allocation fails, the handle's free list and the cache go back to CUDA
+// and the request is retried once.
+constexpr size_t kCacheBytes = size_t(8) << 30;
+constexpr int kCacheDevices = 64;
+struct DeviceCache {
+  std::mutex mu;
+  std::multimap<size_t, void *> free[kCacheDevices];
+  size_t bytes[kCacheDevices] = {};
+};
+static DeviceCache &device_cache() {
+  static DeviceCache *c = new DeviceCache();  // lives as long as the process
+  return *c;
+}
+static bool cache_take(int dev, size_t bytes, void **p, size_t *got) {
+  if (dev < 0 || dev >= kCacheDevices) return false;
+  DeviceCache &c = device_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  auto it = c.free[dev].lower_bound(bytes);
+  if (it == c.free[dev].end() || it->first > 2 * bytes) return false;
+  *p = it->second;
+  *got = it->first;
+  c.bytes[dev] -= it->first;
+  c.free[dev].erase(it);
+  return true;
+}
+static void cache_give(int dev, void *p, size_t bytes) {
+  if (dev >= 0 && dev < kCacheDevices) {
+    DeviceCache &c = device_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (c.bytes[dev] + bytes <= kCacheBytes) {
+      c.free[dev].emplace(bytes, p);
+      c.bytes[dev] += bytes;
+      return;
+    }
+  }
+  cudaFree(p);
+}
+static void cache_trim(int dev) {
+  if (dev < 0 || dev >= kCacheDevices) return;
+  DeviceCache &c = device_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  for (auto &kv : c.free[dev]) cudaFree(kv.second);
+  c.free[dev].clear();
+  c.bytes[dev] = 0;
+}
+
+// the handle's free list to the library cache (its stream is idle)
 static void pool_release(sph_rt *s) {
-  for (auto &kv : s->pool) cudaFree(kv.second);
+  for (auto &kv : s->pool) cache_give(s->cfg.device, kv.second, kv.first);
   s->pool.clear();
 }
 
@@ -92,10 +145,18 @@ void *dalloc_bytes(sph_rt *s, size_t bytes) {
     return p;
   }
   void *p = nullptr;
+  size_t got = 0;
+  if (cache_take(s->cfg.device, bytes, &p, &got)) {
+    s->alloc_size[p] = got;
+    s->allocs.push_back(p);
+    return p;
+  }
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    if (s->cuda_ready) cudaStreamSynchronize(s->stream);
     pool_release(s);
+    cache_trim(s->cfg.device);
     e = cudaMalloc(&p, bytes);
   }
   if (e != cudaSuccess) {
