@@ -369,11 +369,12 @@ sph_rt_status sph_rt_get_solver_tuning(const sph_rt *s, sph_rt_tune_trial *trial
 /* result, the same as in a batch of its own.  With cfg.autotune = 1 the     */
 /* first fused batch of a configuration and dt tunes its launch shape        */
 /* (sph_rt_batch_autotune) and later fused batches of that key reuse it.     */
-/* Queued */
-/* requests are admitted in FIFO order while the device footprint of the    */
-/* resident ones stays within hbm_budget_bytes (an estimate until a request */
-/* is set up, its measured allocation after).  A request's result does not  */
-/* depend on the other requests (same deterministic kernels on its own data). */
+/* Queued requests are admitted in FIFO order while the device footprint of */
+/* the resident ones stays within hbm_budget_bytes (an estimate until a     */
+/* request is set up, its measured allocation after; the library's cache of */
+/* freed device buffers, at most 8 GB per device, is outside the budget).   */
+/* A request's result does not depend on the other requests (same           */
+/* deterministic kernels on its own data).                                  */
 /* ------------------------------------------------------------------------ */
 typedef struct sph_rt_srv sph_rt_srv;
 enum { SPH_RT_SRV_QUEUED = 0, SPH_RT_SRV_ADMITTED = 1, SPH_RT_SRV_RUNNING = 2,
