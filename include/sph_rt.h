@@ -96,7 +96,8 @@ typedef struct {
   int32_t kernel_timing;/* 1: record CUDA events around SpMV launches (sph_rt_kernel_stats) */
   int32_t autotune;     /* 1: autotune on the first step.  The fine SpMV loads in flight (U = 4
                            or 8; never changes a result bit) on the first step of a particle
-                           set, and once per handle the smoother: one timed trial step (after
+                           set (kept for later particle sets within 25 % of its rows and
+                           entries), and once per handle the smoother: one timed trial step (after
                            an untimed one that captures its graph) from the same state for
                            each candidate -- with the AMG preconditioner finest-level
                            post-smoothing off (fine_post_smooth = 0, cheb_degree = 1; in the

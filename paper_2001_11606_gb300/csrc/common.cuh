@@ -652,6 +652,7 @@ struct sph_rt {
   // row-group shape of the fine SpMV-class kernels (autotuned or from the mean row length)
   sphrt::RowShape fine_shape{16, 6};
   bool fine_shape_set = false;
+  int64_t fine_shape_n = 0, fine_shape_nnz = 0;  // sizes the shape was tuned on
   // solver autotuner (config.autotune): done once per handle; its trials
   bool solver_tuned = false;
   std::vector<sph_rt_tune_trial> tune_trials;

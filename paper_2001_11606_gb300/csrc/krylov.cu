@@ -610,6 +610,8 @@ sph_rt_status autotune_fine_shape(sph_rt *s) {
   cudaEventDestroy(e1);
   s->fine_shape = pick;
   s->fine_shape_set = true;
+  s->fine_shape_n = s->n_int;
+  s->fine_shape_nnz = s->nnz_mat;
   return SPH_RT_OK;
 }
 

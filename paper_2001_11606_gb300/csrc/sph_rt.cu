@@ -537,7 +537,16 @@ static sph_rt_status set_particles_common(sph_rt *s, int64_t n, const double *po
   s->have_particles = true;
   s->have_operator = false;
   s->amg_ready = false;
-  s->fine_shape_set = false;
+  // the tuned loads in flight (they never change a result bit) carry over to
+  // a particle set within 25 % of the tuned one's rows and entries and with the
+  // same lanes per row; otherwise the first step tunes them again
+  if (s->fine_shape_set) {
+    auto near = [](int64_t a, int64_t b) { return 4 * (a > b ? a - b : b - a) <= (a > b ? a : b); };
+    const int W = lanes_for_mean(s->n_int ? (double)s->nnz_mat / (double)s->n_int : 0.0);
+    if (!near(s->n_int, s->fine_shape_n) || !near(s->nnz_mat, s->fine_shape_nnz) ||
+        W != s->fine_shape.W)
+      s->fine_shape_set = false;
+  }
   return SPH_RT_OK;
 }
 
