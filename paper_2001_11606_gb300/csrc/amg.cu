@@ -771,6 +771,73 @@ __global__ void ap_structure_kernel(int64_t n, const int64_t *ptr, const int32_t
     cnt[i] = m;
   }
 }
+// The same pass with a warp per row: the row's entries are read 32 at a time
+// (coalesced), equal aggregates within a batch are grouped with match_any, and
+// a batch's new aggregates are appended in lane order after the keys of the
+// earlier batches, which the warp keeps in shared memory -- so keys, positions
+// and counts are exactly those of ap_structure_kernel.  A row with more than
+// kApWarpKeys distinct aggregates sets *overflow; the caller then runs
+// ap_structure_kernel instead.
+constexpr int kApWarpKeys = 128;
+__global__ void ap_structure_warp_kernel(int64_t n, const int64_t *ptr, const int32_t *col,
+                                         const int32_t *agg, int32_t *tmp, int64_t *cnt,
+                                         int32_t *ap_map, int32_t *ap_dmap, int *overflow) {
+  __shared__ int32_t keys_sh[kWarpsPerBlock][kApWarpKeys];
+  int32_t *ks = keys_sh[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const int32_t a0 = agg[i];
+    int m = 0;  // keys so far (warp-uniform)
+    if (a0 >= 0) {
+      if (lane == 0) ks[0] = a0;
+      m = 1;
+    }
+    if (lane == 0) ap_dmap[i] = a0 >= 0 ? 0 : -1;
+    __syncwarp();
+    bool over = false;
+    const int64_t b = ptr[i], e = ptr[i + 1];
+    for (int64_t k0 = b; k0 < e; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const bool valid = k < e;
+      const int32_t K = valid ? agg[col[k]] : -1;
+      int pos = -1;
+      if (K >= 0)
+        for (int q = 0; q < m; ++q)
+          if (ks[q] == K) {
+            pos = q;
+            break;
+          }
+      // first lane of each group of equal new aggregates appends it
+      const unsigned peers = __match_any_sync(0xffffffffu, K);
+      const int leader = __ffs(peers) - 1;
+      const bool fresh = K >= 0 && pos < 0;
+      const bool adds = fresh && lane == leader;
+      const unsigned newmask = __ballot_sync(0xffffffffu, adds);
+      int mine = adds ? m + __popc(newmask & lt) : -1;
+      if (adds && mine < kApWarpKeys) ks[mine] = K;
+      mine = __shfl_sync(0xffffffffu, mine, leader);
+      if (fresh) pos = mine;
+      m += __popc(newmask);
+      if (m > kApWarpKeys) {  // warp-uniform; the keys past the list were not kept
+        over = true;
+        break;
+      }
+      __syncwarp();
+      if (valid) ap_map[k] = pos;
+    }
+    if (over) {
+      if (lane == 0) *overflow = 1;
+      continue;
+    }
+    int32_t *keys = tmp + b + i;
+    for (int q = lane; q < m; q += 32) keys[q] = ks[q];
+    if (lane == 0) cnt[i] = m;
+    __syncwarp();
+  }
+}
 // pass 2: compact the keys and make the positions absolute
 __global__ void ap_compact_kernel(int64_t n, const int64_t *ptr, const int32_t *tmp,
                                   const int64_t *ap_ptr, int32_t *ap_col, int32_t *ap_map,
@@ -1459,9 +1526,21 @@ static sph_rt_status build_ap(sph_rt *s, size_t l) {
   L->ap_ptr = lalloc<int64_t>(s, L, n + 1);
   if (!tmp || !cnt || !map || !L->ap_ptr) return SPH_RT_ENOMEM;
   int32_t *dmap = map + L->nnz;
-  ap_structure_kernel<<<gcap(s, n, kBlock), kBlock, 0, s->stream>>>(n, L->ptr, L->col, L->agg,
-                                                                    tmp, cnt, map, dmap);
+  int *ovf = scratch<int>(s, 1);
+  if (!ovf) return SPH_RT_ENOMEM;
+  SPH_CUDA(s, cudaMemsetAsync(ovf, 0, sizeof(int), s->stream));
+  ap_structure_warp_kernel<<<gcap(s, n, kWarpsPerBlock), kBlock, 0, s->stream>>>(
+      n, L->ptr, L->col, L->agg, tmp, cnt, map, dmap, ovf);
   SPH_LAUNCHED(s);
+  int h_ovf = 0;
+  SPH_CUDA(s, cudaMemcpyAsync(&h_ovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  dfree(s, ovf);
+  if (h_ovf) {  // a row with more distinct aggregates than the warp keeps: one thread a row
+    ap_structure_kernel<<<gcap(s, n, kBlock), kBlock, 0, s->stream>>>(n, L->ptr, L->col, L->agg,
+                                                                      tmp, cnt, map, dmap);
+    SPH_LAUNCHED(s);
+  }
   sph_rt_status rc = exclusive_scan(s, cnt, n, L->ap_ptr);
   if (rc) return rc;
   int64_t total = 0;
