@@ -151,42 +151,62 @@ __device__ __forceinline__ bool beats(uint32_t i, uint32_t j) {
 // ---------------------------------------------------------------------------
 // strength and aggregation
 // ---------------------------------------------------------------------------
+// A warp per row: the row's entries 32 at a time (coalesced), the count of
+// strong entries by ballot.
 __global__ void strength_kernel(int64_t n, const int64_t *ptr, const int32_t *col,
                                 const double *val, const double *diag, double theta2,
                                 uint8_t *strong, int *state) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
     int cnt = 0;
-    double di = diag[i];
-    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
-      int32_t j = col[k];
-      // |B_ij| >= theta sqrt(B_ii B_jj), squared: no FP64 square root per entry
-      bool st = j != i && val[k] * val[k] >= theta2 * (di * diag[j]);
-      strong[k] = st;
-      cnt += st;
+    const double di = diag[i];
+    const int64_t e = ptr[i + 1];
+    for (int64_t k0 = ptr[i]; k0 < e; k0 += 32) {
+      const int64_t k = k0 + lane;
+      bool st = false;
+      if (k < e) {
+        const int32_t j = col[k];
+        // |B_ij| >= theta sqrt(B_ii B_jj), squared: no FP64 square root per entry
+        st = j != i && val[k] * val[k] >= theta2 * (di * diag[j]);
+        strong[k] = st;
+      }
+      cnt += __popc(__ballot_sync(0xffffffffu, st));
     }
-    state[i] = cnt > 0 ? kUndecided : kIsolated;
+    if (lane == 0) state[i] = cnt > 0 ? kUndecided : kIsolated;
   }
 }
 
+// The MIS passes and the assignment with a warp per row: the row's entries
+// 32 at a time (coalesced), decisions by ballot, the assignment's strongest
+// root by a warp arg-max under the same order (largest |B_ij|, then smallest
+// j; the columns of a row are distinct, so the choice is unique).
 __global__ void mis_select_kernel(int64_t n, const int64_t *ptr, const int32_t *col,
                                   const uint8_t *strong, const int *state, uint8_t *cand) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
     uint8_t c = 0;
     if (state[i] == kUndecided) {
       c = 1;
-      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
-        if (!strong[k]) continue;
-        int32_t j = col[k];
-        int sj = state[j];
-        if (sj == kRoot || (sj == kUndecided && beats((uint32_t)j, (uint32_t)i))) {
+      const int64_t e = ptr[i + 1];
+      for (int64_t k0 = ptr[i]; k0 < e; k0 += 32) {
+        const int64_t k = k0 + lane;
+        bool block = false;
+        if (k < e && strong[k]) {
+          const int32_t j = col[k];
+          const int sj = state[j];
+          block = sj == kRoot || (sj == kUndecided && beats((uint32_t)j, (uint32_t)i));
+        }
+        if (__ballot_sync(0xffffffffu, block)) {
           c = 0;
           break;
         }
       }
     }
-    cand[i] = c;
+    if (lane == 0) cand[i] = c;
   }
 }
 
@@ -198,18 +218,23 @@ __global__ void mis_apply_kernel(int64_t n, const uint8_t *cand, int *state) {
 
 __global__ void mis_mark_kernel(int64_t n, const int64_t *ptr, const int32_t *col,
                                 const uint8_t *strong, int *state, unsigned *undecided) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned left = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (state[i] != kUndecided) continue;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    if (state[i] != kUndecided) continue;  // warp-uniform
     bool nr = false;
-    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k)
-      if (strong[k] && state[col[k]] == kRoot) {
-        nr = true;
-        break;
-      }
-    if (nr) state[i] = kNonroot;
-    else ++left;
+    const int64_t e = ptr[i + 1];
+    for (int64_t k0 = ptr[i]; k0 < e && !nr; k0 += 32) {
+      const int64_t k = k0 + lane;
+      const bool hit = k < e && strong[k] && state[col[k]] == kRoot;
+      nr = __ballot_sync(0xffffffffu, hit) != 0;
+    }
+    if (lane == 0) {
+      if (nr) state[i] = kNonroot;
+      else ++left;
+    }
   }
   if (left) atomicAdd(undecided, left);
 }
@@ -223,28 +248,41 @@ __global__ void root_flag_kernel(int64_t n, const int *state, int64_t *flag) {
 __global__ void assign_kernel(int64_t n, const int64_t *ptr, const int32_t *col, const double *val,
                               const uint8_t *strong, const int *state, const int64_t *root_id,
                               int32_t *agg, unsigned *members) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int st = state[i];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const int st = state[i];
     int32_t a = -1;
     if (st == kRoot) {
       a = (int32_t)root_id[i];
     } else if (st == kNonroot) {
       double best = -1.0;
       int32_t bj = -1;
-      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
-        int32_t j = col[k];
+      const int64_t e = ptr[i + 1];
+      for (int64_t k = ptr[i] + lane; k < e; k += 32) {
+        const int32_t j = col[k];
         if (!strong[k] || state[j] != kRoot) continue;
-        double v = fabs(val[k]);
+        const double v = fabs(val[k]);
         if (v > best || (v == best && j < bj)) {
           best = v;
           bj = j;
         }
       }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int32_t oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (oj >= 0 && (bj < 0 || ov > best || (ov == best && oj < bj))) {
+          best = ov;
+          bj = oj;
+        }
+      }
       a = bj >= 0 ? (int32_t)root_id[bj] : -1;
     }
-    agg[i] = a;
-    if (a >= 0) atomicAdd(&members[a], 1u);
+    if (lane == 0) {
+      agg[i] = a;
+      if (a >= 0) atomicAdd(&members[a], 1u);
+    }
   }
 }
 
@@ -1404,17 +1442,18 @@ static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
     if (members) dfree(s, members);
   };
   const int g = gcap(s, n, kBlock);
-  strength_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, L->val, L->diag,
+  const int gw = gcap(s, n, kWarpsPerBlock);  // a warp per row
+  strength_kernel<<<gw, kBlock, 0, st>>>(n, L->ptr, L->col, L->val, L->diag,
                                         s->cfg.amg_theta * s->cfg.amg_theta,
                                         strong, state);
   SPH_LAUNCHED(s);
   for (int round = 0; round < 200; ++round) {
-    mis_select_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, strong, state, cand);
+    mis_select_kernel<<<gw, kBlock, 0, st>>>(n, L->ptr, L->col, strong, state, cand);
     SPH_LAUNCHED(s);
     mis_apply_kernel<<<g, kBlock, 0, st>>>(n, cand, state);
     SPH_LAUNCHED(s);
     SPH_CUDA(s, cudaMemsetAsync(undec, 0, sizeof(unsigned), st));
-    mis_mark_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, strong, state, undec);
+    mis_mark_kernel<<<gw, kBlock, 0, st>>>(n, L->ptr, L->col, strong, state, undec);
     SPH_LAUNCHED(s);
     unsigned left = 0;
     SPH_CUDA(s, cudaMemcpyAsync(&left, undec, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
@@ -1437,7 +1476,7 @@ static sph_rt_status coarsen(sph_rt *s, SphLevel *L, SphLevel **next) {
   SPH_CUDA(s, cudaMemsetAsync(members, 0, sizeof(unsigned) * nc, st));
   L->agg = lalloc<int32_t>(s, L, n);
   if (!L->agg) return cleanup(), SPH_RT_ENOMEM;
-  assign_kernel<<<g, kBlock, 0, st>>>(n, L->ptr, L->col, L->val, strong, state, root_id, L->agg,
+  assign_kernel<<<gw, kBlock, 0, st>>>(n, L->ptr, L->col, L->val, strong, state, root_id, L->agg,
                                       members);
   SPH_LAUNCHED(s);
   cleanup();
