@@ -319,12 +319,32 @@ __device__ __forceinline__ void insertion_sort(S *a, int64_t c) {
     a[u + 1] = v;
   }
 }
+// A thread per small bucket, sorted in the thread's slice of shared memory
+// (one read and one write of the bucket in global memory); 64-bit items, for
+// the rare levels past 2^31 sources, are sorted in place.
 template <typename S>
-__global__ void bucket_sort_kernel(int64_t nb, const int64_t *start, S *out) {
+__global__ void __launch_bounds__(kBlock) bucket_sort_kernel(int64_t nb, const int64_t *start,
+                                                             S *out) {
+  __shared__ int32_t stage[kSmallBucket][kBlock];  // item q of thread t at [q][t]
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
        b += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = start[b + 1] - start[b];
-    if (c <= kSmallBucket) insertion_sort(out + start[b], c);
+    const int64_t s0 = start[b], c = start[b + 1] - s0;
+    if (c < 2 || c > kSmallBucket) continue;
+    if (sizeof(S) != sizeof(int32_t)) {
+      insertion_sort(out + s0, c);
+      continue;
+    }
+    for (int q = 0; q < (int)c; ++q) stage[q][threadIdx.x] = (int32_t)out[s0 + q];
+    for (int t = 1; t < (int)c; ++t) {
+      const int32_t v = stage[t][threadIdx.x];
+      int u = t - 1;
+      while (u >= 0 && stage[u][threadIdx.x] > v) {
+        stage[u + 1][threadIdx.x] = stage[u][threadIdx.x];
+        --u;
+      }
+      stage[u + 1][threadIdx.x] = v;
+    }
+    for (int q = 0; q < (int)c; ++q) out[s0 + q] = stage[q][threadIdx.x];
   }
 }
 // A warp takes 32 consecutive buckets and sorts each larger one in turn: the

@@ -588,9 +588,15 @@ __device__ __forceinline__ double pair_weight(int kern, double xi, double yi, do
                                               const double *cw) {
   const double r2 = exact_r2(xi, yi, zi, px[j], py[j], pz[j]);
   const double ir = rsqrt_fp64(r2), r = r2 * ir;
-  const double qi = r * ihi, qj = r * ih[j];
+  const double ihj = ih[j], cwj = cw[j];
+  const double qi = r * ihi;
   const double dwi = cwi * (kern == SPH_RT_WENDLAND_C4 ? wendland_dw(qi) : spline_dw(qi));
-  const double dwj = cw[j] * (kern == SPH_RT_WENDLAND_C4 ? wendland_dw(qj) : spline_dw(qj));
+  // equal smoothing lengths (the common case): the same expression, computed once
+  double dwj = dwi;
+  if (ihj != ihi || cwj != cwi) {
+    const double qj = r * ihj;
+    dwj = cwj * (kern == SPH_RT_WENDLAND_C4 ? wendland_dw(qj) : spline_dw(qj));
+  }
   return 0.5 * (dwi + dwj) * ir;
 }
 
