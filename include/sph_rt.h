@@ -556,8 +556,15 @@ void sph_rt_batch_destroy(sph_rt_batch *b);
  * call on the handle. */
 const char *sph_rt_last_error(const sph_rt *s);
 
-/* Release the handle and all its device memory (NULL is a no-op). */
+/* Release the handle (NULL is a no-op).  Its device buffers go to a
+ * library-wide cache per device (at most 8 GB; the rest back to CUDA), from
+ * which later handles take before allocating, so that handles created and
+ * destroyed again and again neither allocate nor synchronise the device. */
 void sph_rt_destroy(sph_rt *s);
+
+/* Return the cache's buffers of `device` to CUDA (cudaFree).  Safe at any
+ * time: cached buffers belong to no handle.  EINVAL for a negative device. */
+sph_rt_status sph_rt_release_cached_memory(int32_t device);
 
 #ifdef __cplusplus
 }

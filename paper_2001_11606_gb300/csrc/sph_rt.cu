@@ -372,6 +372,12 @@ extern "C" void sph_rt_destroy(sph_rt *s) {
   delete s;
 }
 
+extern "C" sph_rt_status sph_rt_release_cached_memory(int32_t device) {
+  if (device < 0) return SPH_RT_EINVAL;
+  cache_trim(device);
+  return SPH_RT_OK;
+}
+
 extern "C" const char *sph_rt_last_error(const sph_rt *s) {
   return s ? s->err.c_str() : g_create_error.c_str();
 }

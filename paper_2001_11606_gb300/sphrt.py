@@ -144,6 +144,7 @@ _SIGNATURES = [
     ("sph_rt_get_amg_info", C.c_int, [_P, _P, _P, _P, C.c_int32]),
     ("sph_rt_loop_graph_info", C.c_int, [_P, _P, _P]),
     ("sph_rt_get_config", C.c_int, [_P, _P]),
+    ("sph_rt_release_cached_memory", C.c_int, [C.c_int32]),
     ("sph_rt_get_solver_tuning", C.c_int, [_P, _P, C.c_int32, _P]),
     ("sph_rt_kernel_stats_kind", C.c_int, [_P, C.c_int32, _P, _P, _P]),
     ("sph_rt_launch_count", C.c_int64, [_P]),
@@ -449,6 +450,13 @@ class Solver:
         self._check(self._L.sph_rt_get_solver_tuning(self._h, arr, cnt.value, C.byref(cnt)))
         return [(t.fine_post_smooth, t.cheb_degree, t.reliable_drop,
                  t.ms if t.ms >= 0 else None) for t in arr[: cnt.value]]
+
+
+def release_cached_memory(device: int = 0) -> None:
+    """Return the library's cache of freed device buffers of `device` to CUDA."""
+    rc = load().sph_rt_release_cached_memory(int(device))
+    if rc != OK:
+        raise SphRtError(rc, "sph_rt_release_cached_memory")
 
 
 def config_from_params(params: dict, **overrides) -> Config:

@@ -149,3 +149,9 @@ def test_batch_tune_table_matches_header():
     src = open(HEADER).read()
     m = re.search(r"#define SPH_RT_BATCH_TUNE_CANDIDATES (\d+)", src)
     assert m and int(m.group(1)) == sphrt.BATCH_TUNE_CANDIDATES == 44
+
+
+def test_release_cached_memory_needs_no_handle():
+    sphrt.release_cached_memory(0)  # nothing cached in this process: no device call
+    with pytest.raises(sphrt.SphRtError):
+        sphrt.release_cached_memory(-1)

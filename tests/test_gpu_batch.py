@@ -217,3 +217,27 @@ def test_add_many_equals_one_by_one_and_is_all_or_none():
         assert np.array_equal(e1, e2) and np.array_equal(E1, E2)
     A.close()
     B.close()
+
+
+def test_destroyed_buffers_are_cached_and_released_on_request():
+    torch = pytest.importorskip("torch")
+    probs = _problems(3, k=4, seed=67)
+    cfg = sphrt.config_from_params(probs[0].params)
+    sphrt.release_cached_memory(0)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    B = sphrt.Batch(cfg)
+    B.add_many([(w.particles, w.e0, w.E0) for w in probs])
+    B.run(probs[0].dt, 1)
+    B.close()
+    torch.cuda.synchronize()
+    held = free0 - torch.cuda.mem_get_info()[0]
+    assert held > 0  # the destroyed handles' buffers stay in the cache
+    A = sphrt.Batch(cfg)  # and a new batch runs from them
+    A.add_many([(w.particles, w.e0, w.E0) for w in probs])
+    rc, st, ou, kr = A.run(probs[0].dt, 1)
+    assert np.all(st == 0)
+    A.close()
+    sphrt.release_cached_memory(0)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
