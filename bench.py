@@ -566,6 +566,8 @@ def main():
     ap.add_argument("--fine-post-smooth", type=int, default=None, choices=[0, 1],
                     help="AMG finest-level post-smoothing (default: the library's)")
     ap.add_argument("--reliable-drop", type=float, default=None)
+    ap.add_argument("--krylov-start", type=int, default=None, choices=[0, 1],
+                    help="start of each step's first solve: 0 E^{n-1}, 1 extrapolated in time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")
@@ -621,6 +623,8 @@ def main():
         extra["fine_post_smooth"] = args.fine_post_smooth
     if args.reliable_drop is not None:
         extra["reliable_drop"] = args.reliable_drop
+    if args.krylov_start is not None:
+        extra["krylov_start"] = args.krylov_start
     tune = args.fine_post_smooth is None and args.reliable_drop is None
     chosen = {f: {} for f in forms}  # the timed solver's tuned settings, per form
     trials = {}
@@ -790,6 +794,7 @@ def main():
             "config": {"workload": w.name, "interior_particles": n_int, "ghosts": n - n_int,
                        "time_steps_per_job": T, "dt": w.dt, "precision": head,
                        "precond": args.precond, "parallelism": f"replicas{world}",
+                       "krylov_start": make_cfg(head).krylov_start,
                        "outer_loop": "host" if args.no_graphs else "cuda-graph",
                        "l2": "inputs larger than L2 (operator > 129 MB)",
                        "outer_iters_per_step": hd["outer"], "krylov_iters_per_step": hd["krylov"],

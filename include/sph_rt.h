@@ -157,6 +157,13 @@ typedef struct {
   int32_t index64;      /* 1: 64-bit source indices in the AMG set-up's Galerkin lists even where
                            32 bits suffice; 0 (default): 64 bits only for a level with 2^31 - 1
                            or more entries plus rows.  Never changes a result. */
+  int32_t krylov_start; /* start of each step's first linear solve: 0 E^{n-1}, the state
+                           (Alg. 1's E^{n,0}); 1 (default) the linear extrapolation
+                           E^{n-1} + (dt / dt_prev) (E^{n-1} - E^{n-2}) after a converged step
+                           of the same particle set (else E^{n-1}).  Only the Krylov start
+                           changes: the stopping test (||r|| <= tol_krylov ||b||), the outer
+                           iteration and its fixed point do not.  Both the handle and the
+                           batched form (per problem) follow it. */
   int32_t device;       /* CUDA device ordinal */
   void *stream;         /* cudaStream_t to run on (borrowed); NULL = library-owned stream */
 } sph_rt_config;
@@ -237,6 +244,16 @@ sph_rt_status sph_rt_step(sph_rt *s, double dt, const double *Qe, const double *
 sph_rt_status sph_rt_step_device(sph_rt *s, double dt, const double *Qe, const double *QE,
                                  const double *ghost_e, const double *ghost_E,
                                  sph_rt_stats *stats);
+
+/* The history of the extrapolated Krylov start (krylov_start = 1): E_prev = E^{n-2}, the
+ * radiation energy at the start of the last step, caller order [n_total] (ghost entries 0
+ * on output, ignored on input but must be finite), and that step's dt (host pointers).
+ * get: ESTATE when the last step did not converge or none was taken since the particles
+ * were set.  set (after sph_rt_set_particles): the next step extrapolates from it as if
+ * the handle had taken that step, so a checkpoint of e, E and this history restarts bit
+ * for bit; EINVAL for a non-finite entry or dt_prev <= 0.  Both synchronise the stream. */
+sph_rt_status sph_rt_get_history(sph_rt *s, double *E_prev, double *dt_prev);
+sph_rt_status sph_rt_set_history(sph_rt *s, const double *E_prev, double dt_prev);
 
 /* Copy the current state out, caller order [n_total] (either may be NULL);
  * totals[0] = sum m_i e_i, totals[1] = sum V_i E_i over interior particles

@@ -61,6 +61,8 @@ struct BatchView {
   double *energy;    // [K*4] before, after, source, boundary
   const int32_t *run_status;  // [K] multi-step run: nonzero = failed earlier, skip (or NULL)
   const int32_t *order;       // [K] problem of each cluster of the launch, largest first
+  double *dt_prev;  // [K] dt of the problem's last step if it converged (E_old then holds
+                    // that step's start E^{n-2}), else 0
   int64_t nnz_nbr;            // neighbour entries of the whole batch (stride of nbr_A)
 };
 
@@ -68,6 +70,7 @@ struct BatchPhys {
   double a, c, cv, inv_cv, p, T_floor, larsen_k, dt, tol_inner, tol_outer_e, tol_outer_E,
       tol_krylov;
   int limiter, max_inner, max_outer, max_krylov, cheb_degree, dim;
+  int krylov_start;  // 1: first solve from the extrapolation in time (when dt_prev[k] > 0)
 };
 
 __device__ __forceinline__ double b_opacity(double sigma0, double Ts, double p) {
@@ -449,11 +452,16 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
       gmax = fmax(gmax, -off * inv);
     }
   }
-  // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}
+  // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}.  The first Krylov solve starts
+  // from E^{n-1} + w (E^{n-1} - E^{n-2}), w = dt / dt_prev, after a converged
+  // step (E_old still holds its start E^{n-2} here), else from E^{n-1}.
+  const double gw = (ph.krylov_start == 1 && v.dt_prev[k] > 0.0) ? ph.dt / v.dt_prev[k] : 0.0;
   for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
+    const double Ei = v.E[i];
+    if (gw != 0.0) v.x[i] = Ei + gw * (Ei - v.E_old[i]);
     v.e_old[i] = v.e[i];
-    v.E_old[i] = v.E[i];
-    v.E_l[i] = v.E[i];
+    v.E_old[i] = Ei;
+    v.E_l[i] = Ei;
   }
   {
     double m[1] = {gmax};
@@ -506,7 +514,7 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
       double bi = v.E_old[i] / ph.dt + cs * ph.a * Tl * Tl * Tl * Tl - (1.0 - v.f[i]) * cs * v.E_l[i] +
                   v.QE[i] + v.gb[i];
       v.b[i] = v.V[i] * bi;
-      v.x[i] = v.E_l[i];
+      if (outer > 0 || gw == 0.0) v.x[i] = v.E_l[i];  // else the extrapolated start
       bb += bi * bi;
     }
     const double thresh2 = ph.tol_krylov * ph.tol_krylov * csum(R, P, bb);
@@ -609,6 +617,7 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
     v.status[k] = status;
     v.outer[k] = outer;
     v.krylov[k] = kry_total;
+    v.dt_prev[k] = status == 0 ? ph.dt : 0.0;  // read above by every CTA, before many barriers
   }
   csync();  // no CTA leaves while another may still read its reduction slots
 }
@@ -885,7 +894,9 @@ static sph_rt_status batch_pack(sph_rt_batch *B) {
   B->d_krylov = dalloc<int32_t>(s, K);
   B->d_energy = D(4 * (size_t)K);
   B->d_order = dalloc<int32_t>(s, K);
-  if (!B->d_order) return SPH_RT_ENOMEM;
+  v.dt_prev = D(K);
+  if (!B->d_order || !v.dt_prev) return SPH_RT_ENOMEM;
+  SPH_CUDA(s, cudaMemsetAsync(v.dt_prev, 0, sizeof(double) * K, s->stream));
   for (int c = 0; c < kClusterKinds - 1; ++c)
     SPH_CUDA(s, cudaStreamCreateWithFlags(&B->side[c], cudaStreamNonBlocking));
   SPH_CUDA(s, cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
@@ -1039,6 +1050,7 @@ static BatchPhys batch_phys(const sph_rt_batch *B, double dt) {
   ph.max_krylov = c.max_krylov;
   ph.cheb_degree = B->degree;
   ph.dim = c.dim;
+  ph.krylov_start = c.krylov_start;
   return ph;
 }
 
@@ -1196,6 +1208,8 @@ static sph_rt_status batch_restore(sph_rt_batch *B) {
   const size_t bytes = sizeof(double) * (size_t)s->n;
   SPH_CUDA(s, cudaMemcpyAsync(B->view.e, B->d_e_save, bytes, cudaMemcpyDeviceToDevice, s->stream));
   SPH_CUDA(s, cudaMemcpyAsync(B->view.E, B->d_E_save, bytes, cudaMemcpyDeviceToDevice, s->stream));
+  // E_old now holds the trial's start, not E^{n-2}: the next step starts from E^{n-1}
+  SPH_CUDA(s, cudaMemsetAsync(B->view.dt_prev, 0, sizeof(double) * B->view.K, s->stream));
   return SPH_RT_OK;
 }
 

@@ -79,6 +79,7 @@ struct Scalars {
                    // (kept in the handle's w) is that of the next solve's start
   // time step choice of the last converged step (config.dt_target > 0)
   double dtc_ebar, dtc_Ebar, dtc_eta_e, dtc_eta_E, dtc_next;
+  double guess_w;  // first solve of a step: x = E^l + guess_w (E^l - E_prev); 0 = E^l
 };
 
 // --------------------------------------------------------------------------
@@ -651,6 +652,11 @@ struct sph_rt {
 
   // row-group shape of the fine SpMV-class kernels (autotuned or from the mean row length)
   sphrt::RowShape fine_shape{16, 6};
+  // krylov_start = 1: E at the start of the previous step (E^{n-2}), and
+  // whether the previous step converged on this particle set, with its dt
+  double *E_prev = nullptr;
+  bool prev_ok = false;
+  double dt_prev = 0.0;
   bool fine_shape_set = false;
   int64_t fine_shape_n = 0, fine_shape_nnz = 0;  // sizes the shape was tuned on
   // solver autotuner (config.autotune): done once per handle; its trials

@@ -400,7 +400,10 @@ __global__ void __launch_bounds__(kBlock, kPairMinBlocks)
 __global__ void rhs_kernel(Phys ph, int64_t n_int, const double *V, const double *sigma,
                            const double *f, const double *E_old, const double *e_l,
                            const double *E_l, const double *QE, const double *gb, double *b,
-                           double *x, double tol, Scalars *sc, double *partials) {
+                           double *x, double tol, Scalars *sc, double *partials,
+                           const double *E_prev) {
+  // the first outer iteration's solve may start from the extrapolation in time
+  const double w = sc->outer_iters == 0 ? sc->guess_w : 0.0;
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -409,7 +412,7 @@ __global__ void rhs_kernel(Phys ph, int64_t n_int, const double *V, const double
     double cs = ph.c * sigma[i];
     double bi = E_old[i] / ph.dt + cs * B - (1.0 - f[i]) * cs * E_l[i] + QE[i] + gb[i];
     b[i] = V[i] * bi;
-    x[i] = E_l[i];
+    x[i] = w != 0.0 ? E_l[i] + w * (E_l[i] - E_prev[i]) : E_l[i];
     acc += bi * bi;
   }
   __shared__ double sh[32];
@@ -737,7 +740,16 @@ sph_rt_status launch_rhs(sph_rt *s, double dt) {
   int g = grid_items(s, s->n_int, kBlock);
   rhs_kernel<<<g, kBlock, 0, s->stream>>>(ph, s->n_int, s->V, s->sigma, s->f, s->E_old, s->e_l,
                                            s->E_l, s->QE, s->gb, s->b, s->x, s->cfg.tol_krylov,
-                                           s->sc, s->partials);
+                                           s->sc, s->partials, s->E_prev);
+  SPH_LAUNCHED(s);
+  return SPH_RT_OK;
+}
+
+__global__ void set_guess_kernel(Scalars *sc, double w) { sc->guess_w = w; }
+
+// weight of the extrapolated start of the step's first solve (0: E^l)
+sph_rt_status launch_set_guess(sph_rt *s, double w) {
+  set_guess_kernel<<<1, 1, 0, s->stream>>>(s->sc, w);
   SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }

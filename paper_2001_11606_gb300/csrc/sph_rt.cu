@@ -25,6 +25,7 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
 sph_rt_status launch_properties(sph_rt *s, double dt);
 sph_rt_status launch_assembly(sph_rt *s, double dt, double *gersh_out);
 sph_rt_status launch_rhs(sph_rt *s, double dt);
+sph_rt_status launch_set_guess(sph_rt *s, double w);
 sph_rt_status launch_newton(sph_rt *s, double dt, const double *E_new, const double *E_prev,
                             const double *e_start, double *e_out);
 sph_rt_status launch_totals(sph_rt *s, const double *e, const double *E);
@@ -253,6 +254,7 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->dt_eta_floor = 1e-15;
   c->cell_list = SPH_RT_CELLS_AUTO;
   c->index64 = 0;
+  c->krylov_start = 1;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -306,6 +308,8 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
   if (c->cell_list < SPH_RT_CELLS_AUTO || c->cell_list > SPH_RT_CELLS_SORTED)
     return why = "cell_list must be SPH_RT_CELLS_AUTO, _DENSE or _SORTED", SPH_RT_EINVAL;
   if (c->index64 < 0 || c->index64 > 1) return why = "index64 must be 0 or 1", SPH_RT_EINVAL;
+  if (c->krylov_start < 0 || c->krylov_start > 1)
+    return why = "krylov_start must be 0 or 1", SPH_RT_EINVAL;
   if (c->autotune < 0 || c->autotune > 2) return why = "autotune must be 0, 1 or 2", SPH_RT_EINVAL;
   if (c->device < 0) return why = "device must be >= 0", SPH_RT_EINVAL;
   return SPH_RT_OK;
@@ -459,7 +463,7 @@ static sph_rt_status alloc_step_vectors(sph_rt *s) {
     if (!(*p = dalloc<double>(s, n))) return SPH_RT_ENOMEM;
   double **inner[] = {&s->e_old, &s->E_old, &s->e_l, &s->E_l, &s->e_new, &s->Qe, &s->QE, &s->b,
                       &s->x, &s->r, &s->z, &s->p, &s->q, &s->w, &s->diag, &s->invdiag, &s->gb,
-                      &s->z_old};
+                      &s->z_old, &s->E_prev};
   for (double **p : inner)
     if (!(*p = dalloc<double>(s, ni))) return SPH_RT_ENOMEM;
   if (!(s->gersh = dalloc<double>(s, 1))) return SPH_RT_ENOMEM;
@@ -543,6 +547,7 @@ static sph_rt_status set_particles_common(sph_rt *s, int64_t n, const double *po
   s->have_particles = true;
   s->have_operator = false;
   s->amg_ready = false;
+  s->prev_ok = false;  // no previous step of this particle set (slot order) yet
   // the tuned loads in flight (they never change a result bit) carry over to
   // a particle set within 25 % of the tuned one's rows and entries and with the
   // same lanes per row; otherwise the first step tunes them again
@@ -814,6 +819,15 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
 
   SPH_TRACE("step: preconditioner ready (levels %d)", (int)s->levels.size());
   // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}; material solve with E^{n,0}
+  // krylov_start = 1: the first solve starts from E^{n-1} + w (E^{n-1} - E^{n-2}),
+  // E^{n-2} being E_old before it is overwritten (the previous step's start)
+  double guess_w = 0.0;
+  if (s->cfg.krylov_start == 1 && s->prev_ok && s->dt_prev > 0.0) {
+    guess_w = dt / s->dt_prev;
+    SPH_CUDA(s, cudaMemcpyAsync(s->E_prev, s->E_old, nb, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  if ((rc = launch_set_guess(s, guess_w))) return rc;
+  s->prev_ok = false;  // until this step has converged
   SPH_CUDA(s, cudaMemcpyAsync(s->e_old, s->e, nb, cudaMemcpyDeviceToDevice, s->stream));
   SPH_CUDA(s, cudaMemcpyAsync(s->E_old, s->E, nb, cudaMemcpyDeviceToDevice, s->stream));
   SPH_CUDA(s, cudaMemcpyAsync(s->E_l, s->E, nb, cudaMemcpyDeviceToDevice, s->stream));
@@ -838,6 +852,7 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   if ((rc = read_scalars(s))) return rc;
   if (s->sc_host->bad_input) {
     tm.collect(ms);
+    s->prev_ok = false;
     return set_error(s, SPH_RT_EINVAL, "non-finite source or ghost value");
   }
   {
@@ -855,6 +870,8 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   }
   const bool converged = s->sc_host->outer_status == 1;
   const bool krylov_fail = s->sc_host->outer_status == 2;
+  s->prev_ok = converged;  // the next step's E^{n-2} is this step's start
+  s->dt_prev = dt;
   st.energy_before = s->sc_host->energy_before_e + s->sc_host->energy_before_E;
 
   if (!converged) {
@@ -900,6 +917,7 @@ static sph_rt_status tune_then_step(sph_rt *s, double dt, const double *Qe_c,
                                     const double *QE_c, const double *ge_c, const double *gE_c,
                                     sph_rt_stats *stats) {
   s->solver_tuned = true;  // the trials below are steps too
+  s->prev_ok = false;       // every trial starts its solves from the state
   s->tune_trials.clear();
   const sph_rt_config c0 = s->cfg;
   std::vector<sph_rt_tune_trial> cand;
@@ -941,6 +959,7 @@ static sph_rt_status tune_then_step(sph_rt *s, double dt, const double *Qe_c,
         rc = set_error(s, SPH_RT_EDEVICE, "autotune: cudaEventRecord failed");
         break;
       }
+      s->prev_ok = false;
       sph_rt_status r2 = step_common(s, dt, keep[0], keep[1], keep[2], keep[3], nullptr);
       if (r2 == SPH_RT_ENOTCONV) break;  // the step restored its snapshot itself
       if (r2) {
@@ -972,6 +991,7 @@ static sph_rt_status tune_then_step(sph_rt *s, double dt, const double *Qe_c,
   if (!rc) {
     // the step itself, from the kept inputs (the staged ones may be overwritten)
     s->err.clear();
+    s->prev_ok = false;
     rc = step_common(s, dt, keep[0], keep[1], keep[2], keep[3], stats);
   }
   cudaStreamSynchronize(s->stream);
@@ -1045,6 +1065,40 @@ extern "C" sph_rt_status sph_rt_get_energies(sph_rt *s, double *e, double *E, do
     totals[1] = s->sc_host->red[5];
   }
   SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  return SPH_RT_OK;
+}
+
+// The extrapolated Krylov start's history: E_old holds, between steps, the
+// start E^{n-2} of the last step, and prev_ok says whether that step converged.
+extern "C" sph_rt_status sph_rt_get_history(sph_rt *s, double *E_prev, double *dt_prev) {
+  if (!s || !E_prev || !dt_prev) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
+  if (!s->prev_ok) return set_error(s, SPH_RT_ESTATE, "no converged step of this particle set");
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  sph_rt_status rc;
+  SPH_CUDA(s, cudaMemsetAsync(s->tmp_n, 0, sizeof(double) * s->n, s->stream));
+  if ((rc = launch_scatter_caller(s, s->E_old, s->n_int, s->tmp_n))) return rc;
+  SPH_CUDA(s, cudaMemcpyAsync(E_prev, s->tmp_n, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  *dt_prev = s->dt_prev;
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_set_history(sph_rt *s, const double *E_prev, double dt_prev) {
+  if (!s || !E_prev) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
+  if (!(isfinite(dt_prev) && dt_prev > 0.0))
+    return set_error(s, SPH_RT_EINVAL, "dt_prev must be finite and > 0");
+  for (int64_t i = 0; i < s->n; ++i)
+    if (!isfinite(E_prev[i]))
+      return set_error(s, SPH_RT_EINVAL, "non-finite E_prev at particle " + std::to_string(i));
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  sph_rt_status rc;
+  SPH_CUDA(s, cudaMemcpyAsync(s->tmp_n, E_prev, sizeof(double) * s->n, cudaMemcpyHostToDevice, s->stream));
+  if ((rc = launch_gather_interior(s, s->tmp_n, s->E_old))) return rc;
+  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  s->prev_ok = true;
+  s->dt_prev = dt_prev;
   return SPH_RT_OK;
 }
 

@@ -66,7 +66,7 @@ class Config(C.Structure):
         ("reliable_drop", C.c_double),
         ("dt_target", C.c_double), ("dt_growth", C.c_double), ("dt_min", C.c_double),
         ("dt_max", C.c_double), ("dt_eta_floor", C.c_double), ("cell_list", C.c_int32),
-        ("index64", C.c_int32),
+        ("index64", C.c_int32), ("krylov_start", C.c_int32),
         ("device", C.c_int32),
         ("stream", C.c_void_p),
     ]
@@ -131,6 +131,8 @@ _SIGNATURES = [
     ("sph_rt_step", C.c_int, [_P, C.c_double, _P, _P, _P, _P, _P]),
     ("sph_rt_step_device", C.c_int, [_P, C.c_double, _P, _P, _P, _P, _P]),
     ("sph_rt_get_energies", C.c_int, [_P, _P, _P, _P]),
+    ("sph_rt_get_history", C.c_int, [_P, _P, _P]),
+    ("sph_rt_set_history", C.c_int, [_P, _P, C.c_double]),
     ("sph_rt_get_energies_device", C.c_int, [_P, _P, _P]),
     ("sph_rt_get_sizes", C.c_int, [_P, _P, _P, _P]),
     ("sph_rt_adapt_smoothing_lengths", C.c_int, [_P, C.c_double, C.c_double, C.c_int32, _P]),
@@ -340,6 +342,18 @@ class Solver:
         tot = np.empty(2)
         self._check(self._L.sph_rt_get_energies(self._h, _ptr(e), _ptr(E), _ptr(tot)))
         return e, E, tot
+
+    def get_history(self):
+        """(E_prev, dt_prev): E^{n-2} in caller order and the last step's dt, the
+        history of the extrapolated Krylov start."""
+        E = np.empty(self.n)
+        dt = C.c_double()
+        self._check(self._L.sph_rt_get_history(self._h, _ptr(E), C.byref(dt)))
+        return E, dt.value
+
+    def set_history(self, E_prev, dt_prev):
+        E = _f64(E_prev, self.n)
+        self._check(self._L.sph_rt_set_history(self._h, _ptr(E), float(dt_prev)))
 
     def get_energies_host_ptrs(self, e_ptr, E_ptr):
         self._check(self._L.sph_rt_get_energies(self._h, C.c_void_p(e_ptr), C.c_void_p(E_ptr),

@@ -58,7 +58,8 @@ def test_config_struct_matches_defaults():
                                          ("dt_growth", 0.5), ("dt_min", -1.0),
                                          ("dt_max", 0.0), ("dt_eta_floor", -1.0),
                                          ("cell_list", 3), ("cell_list", -1),
-                                         ("index64", 2), ("autotune", 3)])
+                                         ("index64", 2), ("autotune", 3),
+                                         ("krylov_start", 2)])
 def test_create_rejects_bad_config(field, value):
     cfg = sphrt.default_config(**{field: value})
     with pytest.raises(sphrt.SphRtError) as ei:
