@@ -566,8 +566,8 @@ def main():
     ap.add_argument("--fine-post-smooth", type=int, default=None, choices=[0, 1],
                     help="AMG finest-level post-smoothing (default: the library's)")
     ap.add_argument("--reliable-drop", type=float, default=None)
-    ap.add_argument("--krylov-start", type=int, default=None, choices=[0, 1],
-                    help="start of each step's first solve: 0 E^{n-1}, 1 extrapolated in time")
+    ap.add_argument("--krylov-start", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="start of each step's first solve: 0 E^{n-1}, p > 0 extrapolated in time (order p)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernel-timing", action="store_true")

@@ -158,12 +158,13 @@ typedef struct {
                            32 bits suffice; 0 (default): 64 bits only for a level with 2^31 - 1
                            or more entries plus rows.  Never changes a result. */
   int32_t krylov_start; /* start of each step's first linear solve: 0 E^{n-1}, the state
-                           (Alg. 1's E^{n,0}); 1 (default) the linear extrapolation
-                           E^{n-1} + (dt / dt_prev) (E^{n-1} - E^{n-2}) after a converged step
-                           of the same particle set (else E^{n-1}).  Only the Krylov start
-                           changes: the stopping test (||r|| <= tol_krylov ||b||), the outer
-                           iteration and its fixed point do not.  Both the handle and the
-                           batched form (per problem) follow it. */
+                           (Alg. 1's E^{n,0}); p = 1, 2, 3 (default 3) the value at t_n of the
+                           polynomial in time through E^{n-1}, ..., E^{n-1-p} (Lagrange
+                           extrapolation), of lower order while fewer converged steps of the
+                           same particle set are behind it.  Only the Krylov start changes:
+                           the stopping test (||r|| <= tol_krylov ||b||), the outer iteration
+                           and its fixed point do not.  The handle and the batched form (per
+                           problem) both follow it. */
   int32_t device;       /* CUDA device ordinal */
   void *stream;         /* cudaStream_t to run on (borrowed); NULL = library-owned stream */
 } sph_rt_config;
@@ -245,15 +246,27 @@ sph_rt_status sph_rt_step_device(sph_rt *s, double dt, const double *Qe, const d
                                  const double *ghost_e, const double *ghost_E,
                                  sph_rt_stats *stats);
 
-/* The history of the extrapolated Krylov start (krylov_start = 1): E_prev = E^{n-2}, the
- * radiation energy at the start of the last step, caller order [n_total] (ghost entries 0
- * on output, ignored on input but must be finite), and that step's dt (host pointers).
- * get: ESTATE when the last step did not converge or none was taken since the particles
- * were set.  set (after sph_rt_set_particles): the next step extrapolates from it as if
- * the handle had taken that step, so a checkpoint of e, E and this history restarts bit
- * for bit; EINVAL for a non-finite entry or dt_prev <= 0.  Both synchronise the stream. */
-sph_rt_status sph_rt_get_history(sph_rt *s, double *E_prev, double *dt_prev);
-sph_rt_status sph_rt_set_history(sph_rt *s, const double *E_prev, double dt_prev);
+/* The history of the extrapolated Krylov start (krylov_start = p > 0), for checkpoints.
+ * Row j of E_hist [3][n_total] (caller order, host) is E^{n-2-j}, the radiation energy at
+ * the start of the step j + 1 steps back (row 0: the last step's start), and dt_hist[j]
+ * that step's dt; depth = min(p, converged steps of this particle set behind the state)
+ * rows are valid, the ones the next step reads.
+ * get: writes *depth (0 after sph_rt_set_particles or a step that did not converge), the
+ *   valid rows (rows beyond depth and every ghost entry are 0) and dt_hist[3]; E_hist and
+ *   dt_hist may be NULL.
+ * set (after sph_rt_set_particles): installs depth rows (1 <= depth <= p, EINVAL
+ *   otherwise; every entry finite, ghost entries ignored; dt_hist[0 .. depth-1] > 0), so a
+ *   checkpoint of e, E and this history restarts bit for bit.  Both synchronise the
+ *   stream. */
+sph_rt_status sph_rt_get_history(sph_rt *s, int32_t *depth, double *E_hist, double *dt_hist);
+/* The weights of that extrapolation (host only, no device work): w[0 .. order] with
+ * sum_j w[j] E^{n-1-j} the value at t_n = t_{n-1} + dt of the polynomial of degree `order`
+ * (0..3) through E^{n-1}, ..., E^{n-1-order}; dt_hist[j] = t_{n-1-j} - t_{n-2-j} (newest
+ * first).  EINVAL for another order or a step that is not finite and > 0. */
+sph_rt_status sph_rt_extrapolation_weights(int32_t order, double dt, const double *dt_hist,
+                                           double *w);
+sph_rt_status sph_rt_set_history(sph_rt *s, int32_t depth, const double *E_hist,
+                                 const double *dt_hist);
 
 /* Copy the current state out, caller order [n_total] (either may be NULL);
  * totals[0] = sum m_i e_i, totals[1] = sum V_i E_i over interior particles

@@ -61,8 +61,12 @@ struct BatchView {
   double *energy;    // [K*4] before, after, source, boundary
   const int32_t *run_status;  // [K] multi-step run: nonzero = failed earlier, skip (or NULL)
   const int32_t *order;       // [K] problem of each cluster of the launch, largest first
-  double *dt_prev;  // [K] dt of the problem's last step if it converged (E_old then holds
-                    // that step's start E^{n-2}), else 0
+  // extrapolated Krylov start: per problem the consecutive converged steps behind
+  // the state (capped at 3) and their sizes (newest first); between steps E_old
+  // holds E^{n-2}, H0 E^{n-3} and H1 E^{n-4} of the problem's interior rows
+  int32_t *hist;     // [K]
+  double *dt_hist;   // [3K]
+  double *H0, *H1;   // [n_all]
   int64_t nnz_nbr;            // neighbour entries of the whole batch (stride of nbr_A)
 };
 
@@ -70,7 +74,7 @@ struct BatchPhys {
   double a, c, cv, inv_cv, p, T_floor, larsen_k, dt, tol_inner, tol_outer_e, tol_outer_E,
       tol_krylov;
   int limiter, max_inner, max_outer, max_krylov, cheb_degree, dim;
-  int krylov_start;  // 1: first solve from the extrapolation in time (when dt_prev[k] > 0)
+  int krylov_start;  // p > 0: first solve from the extrapolation in time of order <= p
 };
 
 __device__ __forceinline__ double b_opacity(double sigma0, double Ts, double p) {
@@ -453,12 +457,23 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
     }
   }
   // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}.  The first Krylov solve starts
-  // from E^{n-1} + w (E^{n-1} - E^{n-2}), w = dt / dt_prev, after a converged
-  // step (E_old still holds its start E^{n-2} here), else from E^{n-1}.
-  const double gw = (ph.krylov_start == 1 && v.dt_prev[k] > 0.0) ? ph.dt / v.dt_prev[k] : 0.0;
+  // from the extrapolation in time of order min(p, converged steps behind)
+  // through E^{n-1} and E^{n-2} (E_old, still the last step's start here),
+  // E^{n-3} (H0), E^{n-4} (H1); the history then moves down one place.
+  const int kp = ph.krylov_start;
+  const int ord = min(kp, v.hist[k]);
+  double gw[4] = {1.0, 0.0, 0.0, 0.0};
+  if (ord >= 1) extrap_weights(ord, ph.dt, v.dt_hist + 3 * k, gw);
   for (int64_t i = P.q0 + threadIdx.x; i < P.q1; i += blockDim.x) {
-    const double Ei = v.E[i];
-    if (gw != 0.0) v.x[i] = Ei + gw * (Ei - v.E_old[i]);
+    const double Ei = v.E[i], E2 = v.E_old[i];
+    if (ord >= 1) {
+      double xi = gw[0] * Ei + gw[1] * E2;
+      if (ord >= 2) xi += gw[2] * v.H0[i];
+      if (ord >= 3) xi += gw[3] * v.H1[i];
+      v.x[i] = xi;
+    }
+    if (kp >= 3) v.H1[i] = v.H0[i];
+    if (kp >= 2) v.H0[i] = E2;
     v.e_old[i] = v.e[i];
     v.E_old[i] = Ei;
     v.E_l[i] = Ei;
@@ -514,7 +529,7 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
       double bi = v.E_old[i] / ph.dt + cs * ph.a * Tl * Tl * Tl * Tl - (1.0 - v.f[i]) * cs * v.E_l[i] +
                   v.QE[i] + v.gb[i];
       v.b[i] = v.V[i] * bi;
-      if (outer > 0 || gw == 0.0) v.x[i] = v.E_l[i];  // else the extrapolated start
+      if (outer > 0 || ord == 0) v.x[i] = v.E_l[i];  // else the extrapolated start
       bb += bi * bi;
     }
     const double thresh2 = ph.tol_krylov * ph.tol_krylov * csum(R, P, bb);
@@ -617,7 +632,12 @@ __global__ void __launch_bounds__(512, MINB) batch_step_kernel(BatchView v, Batc
     v.status[k] = status;
     v.outer[k] = outer;
     v.krylov[k] = kry_total;
-    v.dt_prev[k] = status == 0 ? ph.dt : 0.0;  // read above by every CTA, before many barriers
+    // read above by every CTA of the cluster, many cluster barriers ago
+    v.hist[k] = status == 0 ? min(v.hist[k] + 1, 3) : 0;
+    double *d = v.dt_hist + 3 * k;
+    d[2] = d[1];
+    d[1] = d[0];
+    d[0] = ph.dt;
   }
   csync();  // no CTA leaves while another may still read its reduction slots
 }
@@ -894,9 +914,13 @@ static sph_rt_status batch_pack(sph_rt_batch *B) {
   B->d_krylov = dalloc<int32_t>(s, K);
   B->d_energy = D(4 * (size_t)K);
   B->d_order = dalloc<int32_t>(s, K);
-  v.dt_prev = D(K);
-  if (!B->d_order || !v.dt_prev) return SPH_RT_ENOMEM;
-  SPH_CUDA(s, cudaMemsetAsync(v.dt_prev, 0, sizeof(double) * K, s->stream));
+  v.hist = dalloc<int32_t>(s, K);
+  v.dt_hist = D(3 * (size_t)K);
+  v.H0 = D(n_all);
+  v.H1 = D(n_all);
+  if (!B->d_order || !v.hist || !v.dt_hist || !v.H0 || !v.H1) return SPH_RT_ENOMEM;
+  SPH_CUDA(s, cudaMemsetAsync(v.hist, 0, sizeof(int32_t) * K, s->stream));
+  SPH_CUDA(s, cudaMemsetAsync(v.dt_hist, 0, sizeof(double) * 3 * K, s->stream));
   for (int c = 0; c < kClusterKinds - 1; ++c)
     SPH_CUDA(s, cudaStreamCreateWithFlags(&B->side[c], cudaStreamNonBlocking));
   SPH_CUDA(s, cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
@@ -1209,7 +1233,7 @@ static sph_rt_status batch_restore(sph_rt_batch *B) {
   SPH_CUDA(s, cudaMemcpyAsync(B->view.e, B->d_e_save, bytes, cudaMemcpyDeviceToDevice, s->stream));
   SPH_CUDA(s, cudaMemcpyAsync(B->view.E, B->d_E_save, bytes, cudaMemcpyDeviceToDevice, s->stream));
   // E_old now holds the trial's start, not E^{n-2}: the next step starts from E^{n-1}
-  SPH_CUDA(s, cudaMemsetAsync(B->view.dt_prev, 0, sizeof(double) * B->view.K, s->stream));
+  SPH_CUDA(s, cudaMemsetAsync(B->view.hist, 0, sizeof(int32_t) * B->view.K, s->stream));
   return SPH_RT_OK;
 }
 

@@ -79,8 +79,30 @@ struct Scalars {
                    // (kept in the handle's w) is that of the next solve's start
   // time step choice of the last converged step (config.dt_target > 0)
   double dtc_ebar, dtc_Ebar, dtc_eta_e, dtc_eta_E, dtc_next;
-  double guess_w;  // first solve of a step: x = E^l + guess_w (E^l - E_prev); 0 = E^l
+  // start of the first solve of a step: x = sum_j guess_w[j] E^{n-1-j}, j <= guess_order
+  // (E^{n-1} = E^l; guess_order 0: x = E^l)
+  double guess_w[4];
+  int guess_order;
 };
+
+// Lagrange extrapolation in time of order p (0..3): the weights w[0..p] with
+// sum_j w[j] E(t_{n-1-j}) the value at t_n of the polynomial of degree p through
+// E^{n-1}, ..., E^{n-1-p}.  dt is t_n - t_{n-1}; d[j] = t_{n-1-j} - t_{n-2-j}
+// are the previous steps' sizes.  p = 1: w = (1 + dt/d0, -dt/d0).
+__host__ __device__ inline void extrap_weights(int p, double dt, const double *d, double *w) {
+  double tau[4];  // node times relative to t_{n-1}
+  tau[0] = 0.0;
+  for (int j = 1; j <= p; ++j) tau[j] = tau[j - 1] - d[j - 1];
+  for (int j = 0; j <= p; ++j) {
+    double num = 1.0, den = 1.0;
+    for (int m = 0; m <= p; ++m) {
+      if (m == j) continue;
+      num *= dt - tau[m];
+      den *= tau[j] - tau[m];
+    }
+    w[j] = num / den;
+  }
+}
 
 // --------------------------------------------------------------------------
 // Warp and block reductions (fixed order: deterministic).
@@ -652,11 +674,13 @@ struct sph_rt {
 
   // row-group shape of the fine SpMV-class kernels (autotuned or from the mean row length)
   sphrt::RowShape fine_shape{16, 6};
-  // krylov_start = 1: E at the start of the previous step (E^{n-2}), and
-  // whether the previous step converged on this particle set, with its dt
-  double *E_prev = nullptr;
-  bool prev_ok = false;
-  double dt_prev = 0.0;
+  // extrapolated Krylov start (config.krylov_start = p > 0).  Between steps E_old
+  // holds E^{n-2} (the last step's start) and E_hist[j] E^{n-3-j}; during a step
+  // E_hist[j] holds E^{n-2-j}.  hist counts the consecutive converged steps of
+  // this particle set (capped at 3), dt_hist[j] the sizes of the last ones.
+  double *E_hist[3] = {nullptr, nullptr, nullptr};
+  int hist = 0;
+  double dt_hist[3] = {0.0, 0.0, 0.0};
   bool fine_shape_set = false;
   int64_t fine_shape_n = 0, fine_shape_nnz = 0;  // sizes the shape was tuned on
   // solver autotuner (config.autotune): done once per handle; its trials

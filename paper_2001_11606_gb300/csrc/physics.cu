@@ -401,9 +401,12 @@ __global__ void rhs_kernel(Phys ph, int64_t n_int, const double *V, const double
                            const double *f, const double *E_old, const double *e_l,
                            const double *E_l, const double *QE, const double *gb, double *b,
                            double *x, double tol, Scalars *sc, double *partials,
-                           const double *E_prev) {
+                           const double *H0, const double *H1, const double *H2) {
   // the first outer iteration's solve may start from the extrapolation in time
-  const double w = sc->outer_iters == 0 ? sc->guess_w : 0.0;
+  // through E^l = E^{n-1} and H0, H1, H2 = E^{n-2}, E^{n-3}, E^{n-4}
+  const int ord = sc->outer_iters == 0 ? sc->guess_order : 0;
+  const double w0 = sc->guess_w[0], w1 = sc->guess_w[1], w2 = sc->guess_w[2],
+               w3 = sc->guess_w[3];
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_int;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -412,7 +415,13 @@ __global__ void rhs_kernel(Phys ph, int64_t n_int, const double *V, const double
     double cs = ph.c * sigma[i];
     double bi = E_old[i] / ph.dt + cs * B - (1.0 - f[i]) * cs * E_l[i] + QE[i] + gb[i];
     b[i] = V[i] * bi;
-    x[i] = w != 0.0 ? E_l[i] + w * (E_l[i] - E_prev[i]) : E_l[i];
+    double xi = E_l[i];
+    if (ord >= 1) {
+      xi = w0 * xi + w1 * H0[i];
+      if (ord >= 2) xi += w2 * H1[i];
+      if (ord >= 3) xi += w3 * H2[i];
+    }
+    x[i] = xi;
     acc += bi * bi;
   }
   __shared__ double sh[32];
@@ -740,16 +749,24 @@ sph_rt_status launch_rhs(sph_rt *s, double dt) {
   int g = grid_items(s, s->n_int, kBlock);
   rhs_kernel<<<g, kBlock, 0, s->stream>>>(ph, s->n_int, s->V, s->sigma, s->f, s->E_old, s->e_l,
                                            s->E_l, s->QE, s->gb, s->b, s->x, s->cfg.tol_krylov,
-                                           s->sc, s->partials, s->E_prev);
+                                           s->sc, s->partials, s->E_hist[0], s->E_hist[1],
+                                           s->E_hist[2]);
   SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }
 
-__global__ void set_guess_kernel(Scalars *sc, double w) { sc->guess_w = w; }
+__global__ void set_guess_kernel(Scalars *sc, int order, double w0, double w1, double w2,
+                                 double w3) {
+  sc->guess_order = order;
+  sc->guess_w[0] = w0;
+  sc->guess_w[1] = w1;
+  sc->guess_w[2] = w2;
+  sc->guess_w[3] = w3;
+}
 
-// weight of the extrapolated start of the step's first solve (0: E^l)
-sph_rt_status launch_set_guess(sph_rt *s, double w) {
-  set_guess_kernel<<<1, 1, 0, s->stream>>>(s->sc, w);
+// order and weights of the extrapolated start of the step's first solve (order 0: E^l)
+sph_rt_status launch_set_guess(sph_rt *s, int order, const double *w) {
+  set_guess_kernel<<<1, 1, 0, s->stream>>>(s->sc, order, w[0], w[1], w[2], w[3]);
   SPH_LAUNCHED(s);
   return SPH_RT_OK;
 }

@@ -25,7 +25,7 @@ sph_rt_status build_particles(sph_rt *s, int64_t n, const double *pos_c, const d
 sph_rt_status launch_properties(sph_rt *s, double dt);
 sph_rt_status launch_assembly(sph_rt *s, double dt, double *gersh_out);
 sph_rt_status launch_rhs(sph_rt *s, double dt);
-sph_rt_status launch_set_guess(sph_rt *s, double w);
+sph_rt_status launch_set_guess(sph_rt *s, int order, const double *w);
 sph_rt_status launch_newton(sph_rt *s, double dt, const double *E_new, const double *E_prev,
                             const double *e_start, double *e_out);
 sph_rt_status launch_totals(sph_rt *s, const double *e, const double *E);
@@ -254,7 +254,7 @@ extern "C" void sph_rt_default_config(sph_rt_config *c) {
   c->dt_eta_floor = 1e-15;
   c->cell_list = SPH_RT_CELLS_AUTO;
   c->index64 = 0;
-  c->krylov_start = 1;
+  c->krylov_start = 3;
   c->device = 0;
   c->stream = nullptr;
 }
@@ -308,8 +308,8 @@ static sph_rt_status check_config(const sph_rt_config *c, std::string &why) {
   if (c->cell_list < SPH_RT_CELLS_AUTO || c->cell_list > SPH_RT_CELLS_SORTED)
     return why = "cell_list must be SPH_RT_CELLS_AUTO, _DENSE or _SORTED", SPH_RT_EINVAL;
   if (c->index64 < 0 || c->index64 > 1) return why = "index64 must be 0 or 1", SPH_RT_EINVAL;
-  if (c->krylov_start < 0 || c->krylov_start > 1)
-    return why = "krylov_start must be 0 or 1", SPH_RT_EINVAL;
+  if (c->krylov_start < 0 || c->krylov_start > 3)
+    return why = "krylov_start must be 0 .. 3", SPH_RT_EINVAL;
   if (c->autotune < 0 || c->autotune > 2) return why = "autotune must be 0, 1 or 2", SPH_RT_EINVAL;
   if (c->device < 0) return why = "device must be >= 0", SPH_RT_EINVAL;
   return SPH_RT_OK;
@@ -463,7 +463,7 @@ static sph_rt_status alloc_step_vectors(sph_rt *s) {
     if (!(*p = dalloc<double>(s, n))) return SPH_RT_ENOMEM;
   double **inner[] = {&s->e_old, &s->E_old, &s->e_l, &s->E_l, &s->e_new, &s->Qe, &s->QE, &s->b,
                       &s->x, &s->r, &s->z, &s->p, &s->q, &s->w, &s->diag, &s->invdiag, &s->gb,
-                      &s->z_old, &s->E_prev};
+                      &s->z_old, &s->E_hist[0], &s->E_hist[1], &s->E_hist[2]};
   for (double **p : inner)
     if (!(*p = dalloc<double>(s, ni))) return SPH_RT_ENOMEM;
   if (!(s->gersh = dalloc<double>(s, 1))) return SPH_RT_ENOMEM;
@@ -547,7 +547,7 @@ static sph_rt_status set_particles_common(sph_rt *s, int64_t n, const double *po
   s->have_particles = true;
   s->have_operator = false;
   s->amg_ready = false;
-  s->prev_ok = false;  // no previous step of this particle set (slot order) yet
+  s->hist = 0;  // no previous step of this particle set (slot order) yet
   // the tuned loads in flight (they never change a result bit) carry over to
   // a particle set within 25 % of the tuned one's rows and entries and with the
   // same lanes per row; otherwise the first step tunes them again
@@ -819,15 +819,23 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
 
   SPH_TRACE("step: preconditioner ready (levels %d)", (int)s->levels.size());
   // Alg. 1: e^{n,0} = e^{n-1}, E^{n,0} = E^{n-1}; material solve with E^{n,0}
-  // krylov_start = 1: the first solve starts from E^{n-1} + w (E^{n-1} - E^{n-2}),
-  // E^{n-2} being E_old before it is overwritten (the previous step's start)
-  double guess_w = 0.0;
-  if (s->cfg.krylov_start == 1 && s->prev_ok && s->dt_prev > 0.0) {
-    guess_w = dt / s->dt_prev;
-    SPH_CUDA(s, cudaMemcpyAsync(s->E_prev, s->E_old, nb, cudaMemcpyDeviceToDevice, s->stream));
+  // krylov_start = p: the first solve starts from the extrapolation in time of
+  // order min(p, converged steps behind) through E^{n-1}, ..., E^{n-1-p}.  The
+  // history moves down one place: E_hist[j] <- E_hist[j-1], E_hist[0] <- E_old
+  // (E^{n-2}, the last step's start, before E_old is overwritten).
+  const int K = s->cfg.krylov_start;
+  const int order = std::min(K, s->hist);
+  if (K >= 1) {
+    for (int j = K - 1; j >= 1; --j)
+      SPH_CUDA(s, cudaMemcpyAsync(s->E_hist[j], s->E_hist[j - 1], nb, cudaMemcpyDeviceToDevice,
+                                  s->stream));
+    SPH_CUDA(s, cudaMemcpyAsync(s->E_hist[0], s->E_old, nb, cudaMemcpyDeviceToDevice, s->stream));
   }
-  if ((rc = launch_set_guess(s, guess_w))) return rc;
-  s->prev_ok = false;  // until this step has converged
+  double gw[4] = {1.0, 0.0, 0.0, 0.0};
+  if (order >= 1) extrap_weights(order, dt, s->dt_hist, gw);
+  if ((rc = launch_set_guess(s, order, gw))) return rc;
+  const int hist0 = s->hist;
+  s->hist = 0;  // until this step has converged
   SPH_CUDA(s, cudaMemcpyAsync(s->e_old, s->e, nb, cudaMemcpyDeviceToDevice, s->stream));
   SPH_CUDA(s, cudaMemcpyAsync(s->E_old, s->E, nb, cudaMemcpyDeviceToDevice, s->stream));
   SPH_CUDA(s, cudaMemcpyAsync(s->E_l, s->E, nb, cudaMemcpyDeviceToDevice, s->stream));
@@ -852,7 +860,6 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   if ((rc = read_scalars(s))) return rc;
   if (s->sc_host->bad_input) {
     tm.collect(ms);
-    s->prev_ok = false;
     return set_error(s, SPH_RT_EINVAL, "non-finite source or ghost value");
   }
   {
@@ -870,8 +877,10 @@ static sph_rt_status step_common(sph_rt *s, double dt, const double *Qe_c, const
   }
   const bool converged = s->sc_host->outer_status == 1;
   const bool krylov_fail = s->sc_host->outer_status == 2;
-  s->prev_ok = converged;  // the next step's E^{n-2} is this step's start
-  s->dt_prev = dt;
+  s->hist = converged ? std::min(hist0 + 1, 3) : 0;  // this step's start is the next E^{n-2}
+  s->dt_hist[2] = s->dt_hist[1];
+  s->dt_hist[1] = s->dt_hist[0];
+  s->dt_hist[0] = dt;
   st.energy_before = s->sc_host->energy_before_e + s->sc_host->energy_before_E;
 
   if (!converged) {
@@ -917,7 +926,7 @@ static sph_rt_status tune_then_step(sph_rt *s, double dt, const double *Qe_c,
                                     const double *QE_c, const double *ge_c, const double *gE_c,
                                     sph_rt_stats *stats) {
   s->solver_tuned = true;  // the trials below are steps too
-  s->prev_ok = false;       // every trial starts its solves from the state
+  s->hist = 0;              // every trial starts its solves from the state
   s->tune_trials.clear();
   const sph_rt_config c0 = s->cfg;
   std::vector<sph_rt_tune_trial> cand;
@@ -959,7 +968,7 @@ static sph_rt_status tune_then_step(sph_rt *s, double dt, const double *Qe_c,
         rc = set_error(s, SPH_RT_EDEVICE, "autotune: cudaEventRecord failed");
         break;
       }
-      s->prev_ok = false;
+      s->hist = 0;
       sph_rt_status r2 = step_common(s, dt, keep[0], keep[1], keep[2], keep[3], nullptr);
       if (r2 == SPH_RT_ENOTCONV) break;  // the step restored its snapshot itself
       if (r2) {
@@ -991,7 +1000,7 @@ static sph_rt_status tune_then_step(sph_rt *s, double dt, const double *Qe_c,
   if (!rc) {
     // the step itself, from the kept inputs (the staged ones may be overwritten)
     s->err.clear();
-    s->prev_ok = false;
+    s->hist = 0;
     rc = step_common(s, dt, keep[0], keep[1], keep[2], keep[3], stats);
   }
   cudaStreamSynchronize(s->stream);
@@ -1068,37 +1077,71 @@ extern "C" sph_rt_status sph_rt_get_energies(sph_rt *s, double *e, double *E, do
   return SPH_RT_OK;
 }
 
-// The extrapolated Krylov start's history: E_old holds, between steps, the
-// start E^{n-2} of the last step, and prev_ok says whether that step converged.
-extern "C" sph_rt_status sph_rt_get_history(sph_rt *s, double *E_prev, double *dt_prev) {
-  if (!s || !E_prev || !dt_prev) return SPH_RT_EINVAL;
-  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
-  if (!s->prev_ok) return set_error(s, SPH_RT_ESTATE, "no converged step of this particle set");
-  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
-  sph_rt_status rc;
-  SPH_CUDA(s, cudaMemsetAsync(s->tmp_n, 0, sizeof(double) * s->n, s->stream));
-  if ((rc = launch_scatter_caller(s, s->E_old, s->n_int, s->tmp_n))) return rc;
-  SPH_CUDA(s, cudaMemcpyAsync(E_prev, s->tmp_n, sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
-  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
-  *dt_prev = s->dt_prev;
+extern "C" sph_rt_status sph_rt_extrapolation_weights(int32_t order, double dt,
+                                                      const double *dt_hist, double *w) {
+  if (!w || order < 0 || order > 3 || (order > 0 && !dt_hist)) return SPH_RT_EINVAL;
+  if (!(isfinite(dt) && dt > 0.0)) return SPH_RT_EINVAL;
+  for (int j = 0; j < order; ++j)
+    if (!(isfinite(dt_hist[j]) && dt_hist[j] > 0.0)) return SPH_RT_EINVAL;
+  double g[4] = {1.0, 0.0, 0.0, 0.0};
+  if (order > 0) extrap_weights(order, dt, dt_hist, g);
+  for (int j = 0; j <= order; ++j) w[j] = g[j];
   return SPH_RT_OK;
 }
 
-extern "C" sph_rt_status sph_rt_set_history(sph_rt *s, const double *E_prev, double dt_prev) {
-  if (!s || !E_prev) return SPH_RT_EINVAL;
+// The extrapolated Krylov start's history between steps: row 0 is E_old (E^{n-2},
+// the last step's start), row j E_hist[j-1] (E^{n-2-j}); depth min(hist, p) rows
+// are valid, the ones the next step's extrapolation of order p reads.
+static double *history_row(sph_rt *s, int j) { return j == 0 ? s->E_old : s->E_hist[j - 1]; }
+
+extern "C" sph_rt_status sph_rt_get_history(sph_rt *s, int32_t *depth, double *E_hist,
+                                            double *dt_hist) {
+  if (!s || !depth) return SPH_RT_EINVAL;
   if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
-  if (!(isfinite(dt_prev) && dt_prev > 0.0))
-    return set_error(s, SPH_RT_EINVAL, "dt_prev must be finite and > 0");
-  for (int64_t i = 0; i < s->n; ++i)
-    if (!isfinite(E_prev[i]))
-      return set_error(s, SPH_RT_EINVAL, "non-finite E_prev at particle " + std::to_string(i));
+  const int d = std::min(s->hist, s->cfg.krylov_start);
+  *depth = d;
+  if (dt_hist)
+    for (int j = 0; j < 3; ++j) dt_hist[j] = j < d ? s->dt_hist[j] : 0.0;
+  if (!E_hist) return SPH_RT_OK;
   SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  const size_t nb = sizeof(double) * (size_t)s->n;
   sph_rt_status rc;
-  SPH_CUDA(s, cudaMemcpyAsync(s->tmp_n, E_prev, sizeof(double) * s->n, cudaMemcpyHostToDevice, s->stream));
-  if ((rc = launch_gather_interior(s, s->tmp_n, s->E_old))) return rc;
-  SPH_CUDA(s, cudaStreamSynchronize(s->stream));
-  s->prev_ok = true;
-  s->dt_prev = dt_prev;
+  for (int j = 0; j < 3; ++j) {
+    SPH_CUDA(s, cudaMemsetAsync(s->tmp_n, 0, nb, s->stream));
+    if (j < d && (rc = launch_scatter_caller(s, history_row(s, j), s->n_int, s->tmp_n))) return rc;
+    SPH_CUDA(s, cudaMemcpyAsync(E_hist + (size_t)j * s->n, s->tmp_n, nb, cudaMemcpyDeviceToHost,
+                                s->stream));
+    SPH_CUDA(s, cudaStreamSynchronize(s->stream));  // tmp_n is reused by the next row
+  }
+  return SPH_RT_OK;
+}
+
+extern "C" sph_rt_status sph_rt_set_history(sph_rt *s, int32_t depth, const double *E_hist,
+                                            const double *dt_hist) {
+  if (!s || !E_hist || !dt_hist) return SPH_RT_EINVAL;
+  if (!s->have_particles) return set_error(s, SPH_RT_ESTATE, "no particles");
+  if (depth < 1 || depth > s->cfg.krylov_start)
+    return set_error(s, SPH_RT_EINVAL, "depth must be 1 .. krylov_start");
+  for (int j = 0; j < depth; ++j)
+    if (!(isfinite(dt_hist[j]) && dt_hist[j] > 0.0))
+      return set_error(s, SPH_RT_EINVAL, "dt_hist entries must be finite and > 0");
+  const int64_t count = (int64_t)depth * s->n;
+  for (int64_t i = 0; i < count; ++i)
+    if (!isfinite(E_hist[i]))
+      return set_error(s, SPH_RT_EINVAL, "non-finite E_hist entry at row " +
+                                             std::to_string(i / s->n) + ", particle " +
+                                             std::to_string(i % s->n));
+  SPH_CUDA(s, cudaSetDevice(s->cfg.device));
+  const size_t nb = sizeof(double) * (size_t)s->n;
+  sph_rt_status rc;
+  for (int j = 0; j < depth; ++j) {
+    SPH_CUDA(s, cudaMemcpyAsync(s->tmp_n, E_hist + (size_t)j * s->n, nb, cudaMemcpyHostToDevice,
+                                s->stream));
+    if ((rc = launch_gather_interior(s, s->tmp_n, history_row(s, j)))) return rc;
+    SPH_CUDA(s, cudaStreamSynchronize(s->stream));
+  }
+  s->hist = depth;
+  for (int j = 0; j < 3; ++j) s->dt_hist[j] = j < depth ? dt_hist[j] : 0.0;
   return SPH_RT_OK;
 }
 

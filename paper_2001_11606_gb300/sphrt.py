@@ -131,8 +131,9 @@ _SIGNATURES = [
     ("sph_rt_step", C.c_int, [_P, C.c_double, _P, _P, _P, _P, _P]),
     ("sph_rt_step_device", C.c_int, [_P, C.c_double, _P, _P, _P, _P, _P]),
     ("sph_rt_get_energies", C.c_int, [_P, _P, _P, _P]),
-    ("sph_rt_get_history", C.c_int, [_P, _P, _P]),
-    ("sph_rt_set_history", C.c_int, [_P, _P, C.c_double]),
+    ("sph_rt_get_history", C.c_int, [_P, _P, _P, _P]),
+    ("sph_rt_extrapolation_weights", C.c_int, [C.c_int32, C.c_double, _P, _P]),
+    ("sph_rt_set_history", C.c_int, [_P, C.c_int32, _P, _P]),
     ("sph_rt_get_energies_device", C.c_int, [_P, _P, _P]),
     ("sph_rt_get_sizes", C.c_int, [_P, _P, _P, _P]),
     ("sph_rt_adapt_smoothing_lengths", C.c_int, [_P, C.c_double, C.c_double, C.c_int32, _P]),
@@ -344,16 +345,21 @@ class Solver:
         return e, E, tot
 
     def get_history(self):
-        """(E_prev, dt_prev): E^{n-2} in caller order and the last step's dt, the
-        history of the extrapolated Krylov start."""
-        E = np.empty(self.n)
-        dt = C.c_double()
-        self._check(self._L.sph_rt_get_history(self._h, _ptr(E), C.byref(dt)))
-        return E, dt.value
+        """(E_hist, dt_hist): the extrapolated Krylov start's history, rows
+        E^{n-2}, E^{n-3}, ... in caller order and their steps' dt, as many rows as
+        the next step reads (0 after new particles or a failed step)."""
+        E = np.zeros((3, self.n))
+        dt = np.zeros(3)
+        d = C.c_int32()
+        self._check(self._L.sph_rt_get_history(self._h, C.byref(d), _ptr(E), _ptr(dt)))
+        return E[:d.value].copy(), dt[:d.value].copy()
 
-    def set_history(self, E_prev, dt_prev):
-        E = _f64(E_prev, self.n)
-        self._check(self._L.sph_rt_set_history(self._h, _ptr(E), float(dt_prev)))
+    def set_history(self, E_hist, dt_hist):
+        E = np.ascontiguousarray(E_hist, dtype=np.float64).reshape(-1, self.n)
+        dt = np.ascontiguousarray(dt_hist, dtype=np.float64).ravel()
+        if dt.size != E.shape[0]:
+            raise ValueError("one dt per history row")
+        self._check(self._L.sph_rt_set_history(self._h, E.shape[0], _ptr(E), _ptr(dt)))
 
     def get_energies_host_ptrs(self, e_ptr, E_ptr):
         self._check(self._L.sph_rt_get_energies(self._h, C.c_void_p(e_ptr), C.c_void_p(E_ptr),
@@ -731,3 +737,18 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def extrapolation_weights(order, dt, dt_hist=()):
+    """Weights of the extrapolated Krylov start: sum_j w[j] E^{n-1-j} is the value
+    at t_{n-1} + dt of the polynomial of degree `order` through the last states;
+    dt_hist holds the previous steps' sizes, newest first."""
+    w = np.zeros(order + 1 if 0 <= order <= 3 else 1)
+    d = np.ascontiguousarray(dt_hist, dtype=np.float64)
+    if d.size < order:
+        raise ValueError("need one previous step size per order")
+    rc = load().sph_rt_extrapolation_weights(int(order), float(dt), _ptr(d) if d.size else None,
+                                             _ptr(w))
+    if rc:
+        raise SphRtError(rc, "invalid order or step sizes")
+    return w

@@ -59,7 +59,7 @@ def test_config_struct_matches_defaults():
                                          ("dt_max", 0.0), ("dt_eta_floor", -1.0),
                                          ("cell_list", 3), ("cell_list", -1),
                                          ("index64", 2), ("autotune", 3),
-                                         ("krylov_start", 2)])
+                                         ("krylov_start", 4)])
 def test_create_rejects_bad_config(field, value):
     cfg = sphrt.default_config(**{field: value})
     with pytest.raises(sphrt.SphRtError) as ei:
@@ -156,3 +156,27 @@ def test_release_cached_memory_needs_no_handle():
     sphrt.release_cached_memory(0)  # nothing cached in this process: no device call
     with pytest.raises(sphrt.SphRtError):
         sphrt.release_cached_memory(-1)
+
+
+def test_extrapolation_weights_reproduce_polynomials():
+    # the Krylov start's weights: exact at t_n for every polynomial in time of
+    # degree <= order through the last states, on non-uniform steps
+    rng = np.random.default_rng(5)
+    for order in range(4):
+        for _ in range(20):
+            dt = rng.uniform(0.1, 2.0)
+            d = rng.uniform(0.1, 2.0, size=3)
+            w = sphrt.extrapolation_weights(order, dt, d[:order])
+            tau = np.concatenate([[0.0], -np.cumsum(d[:order])])  # t_{n-1-j} - t_{n-1}
+            for q in range(order + 1):
+                assert abs(np.dot(w, tau ** q) - dt ** q) < 1e-11 * max(1.0, dt ** q)
+            if order < 3:  # and not one degree beyond
+                q = order + 1
+                assert abs(np.dot(w, tau ** q) - dt ** q) > 1e-9
+    assert np.allclose(sphrt.extrapolation_weights(1, 0.5, [2.0]), [1.25, -0.25])
+    assert np.allclose(sphrt.extrapolation_weights(2, 1.0, [1.0, 1.0]), [3, -3, 1])
+    assert np.allclose(sphrt.extrapolation_weights(3, 1.0, [1.0, 1.0, 1.0]), [4, -6, 4, -1])
+    assert list(sphrt.extrapolation_weights(0, 1.0)) == [1.0]
+    for bad in [(4, 1.0, [1.0] * 4), (1, 0.0, [1.0]), (2, 1.0, [1.0, -1.0])]:
+        with pytest.raises(sphrt.SphRtError):
+            sphrt.extrapolation_weights(*bad)

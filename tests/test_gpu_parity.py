@@ -387,47 +387,55 @@ def test_repeat_is_bitwise_identical():
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
 
-@pytest.mark.parametrize("krylov_start", [0, 1])
+@pytest.mark.parametrize("krylov_start", [0, 1, 2, 3])
 def test_restart_continues_bitwise(krylov_start):
     # a checkpoint is the state (e, E) and, for the extrapolated Krylov start,
-    # its history (E^{n-2}, dt_prev)
-    w = I.mms_2d(n=16, steps=3)
+    # its history (E^{n-2}, E^{n-3}, ... and their steps' dt)
+    w = I.mms_2d(n=16, steps=5)
     P = w.particles
-    S = sphrt.solver_for(w, amg_rebuild=1, krylov_start=krylov_start)
-    for n in (1, 2, 3):
-        S.step(w.dt, *w.step_inputs(n))
-    e3, E3, _ = S.get_energies()
-    S2 = sphrt.solver_for(w, amg_rebuild=1, krylov_start=krylov_start)
-    for n in (1, 2):
-        S2.step(w.dt, *w.step_inputs(n))
-    e2, E2, _ = S2.get_energies()
+    m = P.kind == 0
+
+    def run(steps):
+        S = sphrt.solver_for(w, amg_rebuild=1, krylov_start=krylov_start)
+        for n in range(1, steps + 1):
+            S.step(w.dt, *w.step_inputs(n))
+        return S
+
+    S = run(5)
+    e5, E5, _ = S.get_energies()
+    S2 = run(4)
+    e4, E4, _ = S2.get_energies()
     Eh, dth = S2.get_history()
-    assert dth == w.dt
+    assert len(dth) == krylov_start and Eh.shape == (krylov_start, P.n)
+    assert np.all(dth == w.dt)
     S3 = sphrt.Solver(sphrt.config_from_params(w.params, amg_rebuild=1,
                                                krylov_start=krylov_start))
-    S3.set_particles(P.pos, P.mass, P.rho, P.h, P.sigma0, P.kind, None, e2, E2)
-    with pytest.raises(sphrt.SphRtError) as ei:
-        S3.get_history()  # new particles: no history yet
-    assert ei.value.status == sphrt.ESTATE
+    S3.set_particles(P.pos, P.mass, P.rho, P.h, P.sigma0, P.kind, None, e4, E4)
+    assert len(S3.get_history()[1]) == 0  # new particles: no history yet
     if krylov_start:
         S3.set_history(Eh, dth)
-    S3.step(w.dt, *w.step_inputs(3))
-    e3b, E3b, _ = S3.get_energies()
-    assert np.array_equal(e3, e3b) and np.array_equal(E3, E3b)
-    # the history is E^{n-2}: the state after step 1, interior entries
-    S1 = sphrt.solver_for(w, amg_rebuild=1)
-    S1.step(w.dt, *w.step_inputs(1))
-    m = P.kind == 0
-    assert np.array_equal(Eh[m], S1.get_energies()[1][m]) and np.all(Eh[~m] == 0.0)
-    with pytest.raises(sphrt.SphRtError) as ei:
-        S3.set_history(Eh, 0.0)
-    assert ei.value.status == sphrt.EINVAL
-    bad = Eh.copy()
-    bad[0] = np.nan
-    with pytest.raises(sphrt.SphRtError) as ei:
-        S3.set_history(bad, w.dt)
-    assert ei.value.status == sphrt.EINVAL
-    for h in (S, S1, S2, S3):
+    S3.step(w.dt, *w.step_inputs(5))
+    e5b, E5b, _ = S3.get_energies()
+    assert np.array_equal(e5, e5b) and np.array_equal(E5, E5b)
+    # row j is E^{n-2-j}: the state three, two, one steps in (interior entries)
+    for j in range(krylov_start):
+        R = run(3 - j)
+        assert np.array_equal(Eh[j][m], R.get_energies()[1][m]) and np.all(Eh[j][~m] == 0.0)
+        R.close()
+    if krylov_start:
+        with pytest.raises(sphrt.SphRtError) as ei:
+            S3.set_history(Eh, np.zeros(krylov_start))
+        assert ei.value.status == sphrt.EINVAL
+        bad = Eh.copy()
+        bad[0, 0] = np.nan
+        with pytest.raises(sphrt.SphRtError) as ei:
+            S3.set_history(bad, dth)
+        assert ei.value.status == sphrt.EINVAL
+    if krylov_start < 3:  # deeper than the configuration reads
+        with pytest.raises(sphrt.SphRtError) as ei:
+            S3.set_history(np.ones((krylov_start + 1, P.n)), np.ones(krylov_start + 1))
+        assert ei.value.status == sphrt.EINVAL
+    for h in (S, S2, S3):
         h.close()
 
 
