@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library builds, loads, exports every
 symbol declared in include/sph_rt.h, and rejects invalid input on the host
 before any device work."""
+import ctypes
 import os
 import re
 
@@ -180,3 +181,20 @@ def test_extrapolation_weights_reproduce_polynomials():
     for bad in [(4, 1.0, [1.0] * 4), (1, 0.0, [1.0]), (2, 1.0, [1.0, -1.0])]:
         with pytest.raises(sphrt.SphRtError):
             sphrt.extrapolation_weights(*bad)
+
+
+def test_history_calls_check_their_arguments_before_the_device():
+    L = sphrt.load()
+    S = sphrt.Solver(sphrt.default_config(dim=2))
+    depth = np.zeros(1, dtype=np.int32)
+    E = np.ones((3, 4))
+    dt = np.ones(3)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    assert L.sph_rt_get_history(None, p(depth), p(E), p(dt)) == sphrt.EINVAL
+    assert L.sph_rt_get_history(S._h, None, p(E), p(dt)) == sphrt.EINVAL
+    assert L.sph_rt_set_history(S._h, 1, None, p(dt)) == sphrt.EINVAL
+    # no particles yet: a state error, whatever the depth
+    assert L.sph_rt_get_history(S._h, p(depth), p(E), p(dt)) == sphrt.ESTATE
+    assert L.sph_rt_set_history(S._h, 1, p(E), p(dt)) == sphrt.ESTATE
+    assert L.sph_rt_set_history(S._h, 9, p(E), p(dt)) == sphrt.ESTATE
+    S.close()
